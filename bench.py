@@ -1,0 +1,427 @@
+"""Benchmark of the STAR-NT per-frame hot path on B300.
+
+Default workload: 1920x1080, 20k seeded transparent triangles (mean depth
+complexity ~8), camera orbiting at 5 deg/s, 60 fps.  One step = one real
+STAR-NT frame (pass 1 at full resolution, passes 2 and 3 at the quadtree's
+scales, upscale, MLP, composite, quadtree update) plus one interpolated
+frame (depth reprojection): every stage of the hot path.  The metric is
+ms/frame = step time / 2.  The plain full-resolution neural OIT pipeline on
+the same scene is timed alongside (``plain_ms_per_frame``).
+
+``--impl reference`` times the CPU oracle (float64, host cores) on the same
+workload instead.  Multi-GPU runs are independent replicas (the frame path
+has no exchange step): each rank renders its own sequence.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_PEAKS = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0,
+                  "sm_max_mhz": 2032.0}
+N_SM = 148
+ALU_LANES_PER_SM = 128
+OPS_PER_FRAGMENT = 32     # algorithmic integer/fp operations per fragment (see design notes)
+# kernels of one step: 3 x raster (set-up, 2 x bin, 3-launch scan), 3 geometry
+# passes, upscale/features, MLP, composite, quadtree (decide, 2 relax, hist,
+# finalize), reprojection
+KERNELS_PER_STEP = 3 * 6 + 3 + 1 + 1 + 1 + 5 + 1
+
+
+def load_peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            d = json.load(f)
+        return d, "measured"
+    except (OSError, ValueError):
+        return dict(FALLBACK_PEAKS), "fallback"
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._thr = None
+
+    def start(self):
+        self._thr = threading.Thread(target=self._run, daemon=True)
+        self._thr.start()
+        return self
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([v.strip() for v in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def stop(self):
+        self._stop.set()
+        if self._thr:
+            self._thr.join(timeout=6)
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > 2 + i and s[2 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons}
+
+
+def workload_scene(name):
+    from paper_2606_16747_b300 import scenes
+    if name == "hd":
+        return scenes.hd_scene(), "1920x1080, 20k triangles, mean depth complexity ~8"
+    if name == "uhd":
+        return scenes.uhd_scene(), "3840x2160, 80k triangles, mean depth complexity ~16"
+    if name == "small":
+        return scenes.small_scene(), "256x256, 32 triangles, mean depth complexity ~4"
+    raise ValueError(name)
+
+
+def mlp_weights():
+    """Trained tail-colour weights when present, seeded Xavier weights otherwise."""
+    from paper_2606_16747_b300 import scenes
+    path = os.path.join(ROOT, "paper_2606_16747_b300", "weights", "tail_mlp.npz")
+    if os.path.exists(path):
+        d = np.load(path)
+        return {k: d[k].astype(np.float32) for k, _ in scenes.MLP_SHAPES}, "trained"
+    return scenes.mlp_xavier(2), "xavier_seed2"
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world):
+    import torch
+
+    from paper_2606_16747_b300 import build, scenes
+    from paper_2606_16747_b300 import star_nt as sn
+    from paper_2606_16747_b300.pipeline import Renderer
+
+    build.build()
+    torch.cuda.set_device(rank % max(1, torch.cuda.device_count()))
+    dev = torch.device("cuda")
+    sc, desc = workload_scene(args.workload)
+    W, H = sc.width, sc.height
+    w, wname = mlp_weights()
+    x_dtype = sn.BF16 if args.mlp == "bf16" else sn.F32
+    star = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=x_dtype, base_tile=args.base_tile)
+    plain = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=sn.F32)
+    n_frames = 2 * (args.warmup + args.steps) + 8
+    cams = scenes.orbit_cameras(W, H, n_frames)
+    vp32 = torch.tensor(np.stack([c.vp32 for c in cams]), device=dev)
+    vp64 = torch.tensor(np.stack([c.vp64.reshape(16) for c in cams]), device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 126 MB L2
+
+    # fragment count of the workload (full resolution, first camera)
+    Fcount = fragment_count(sn, star, vp32[0], W, H)
+
+    def real(k, mark=None):
+        star.vp.copy_(vp32[k])
+        star.star_frame(mark=mark)
+        star.prev_rgba.copy_(star.rgba32f)
+        star.prev_z1.copy_(star.l1["z1"])
+        star.vp64_prev.copy_(vp64[k])
+
+    def interp(k):
+        star.vp64_cur.copy_(vp64[k])
+        star.interp_frame()
+
+    # settle the tile hierarchy on the first frames, then warm up
+    for k in range(4):
+        real(k)
+    frame = 4
+    for _ in range(args.warmup):
+        real(frame)
+        interp(frame + 1)
+        frame += 2
+    torch.cuda.synchronize()
+    star.check_status()
+
+    stage_names = ["raster", "pass1", "pass2", "pass3", "features", "infer", "composite", "quadtree",
+                   "reproject"]
+    step_ms, stage_ms = [], {k: [] for k in stage_names}
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device()).start()
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1)
+        ev = {"start": torch.cuda.Event(enable_timing=True)}
+        ev["start"].record()
+
+        def mark(name):
+            e = torch.cuda.Event(enable_timing=True)
+            e.record()
+            ev[name] = e
+
+        real(frame, mark)
+        interp(frame + 1)
+        mark("reproject")
+        frame += 2
+        ev["end"] = ev["reproject"]
+        torch.cuda.synchronize()
+        step_ms.append(ev["start"].elapsed_time(ev["end"]))
+        prev = ev["start"]
+        for name in stage_names:
+            stage_ms[name].append(prev.elapsed_time(ev[name]))
+            prev = ev[name]
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    star.check_status()
+    state = star.pass_state()
+
+    # plain full-resolution FP32 pipeline on the same scene and cameras
+    plain_ms = []
+    for k in range(args.warmup + args.steps):
+        flush.fill_(1)
+        plain.vp.copy_(vp32[k])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        plain.plain_frame()
+        e1.record()
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            plain_ms.append(e0.elapsed_time(e1))
+    plain.check_status()
+
+    # end to end through the public API: host inputs in, frame out, every step
+    e2e = end_to_end(sn, torch, sc, w, x_dtype, W, H, cams, args)
+
+    t_step = float(np.mean(step_ms))
+    t_max = t_step
+    if world > 1:
+        t = torch.tensor([t_step], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    ms_frame = t_max / 2.0
+    stage_mean = {k: float(np.mean(v)) for k, v in stage_ms.items()}
+    peaks, peaks_kind = load_peaks()
+    # dominant kernel: the full-resolution geometry pass (pass 1)
+    dom_ms = stage_mean["pass1"]
+    alu_peak = N_SM * ALU_LANES_PER_SM * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12  # Tops/s
+    achieved = OPS_PER_FRAGMENT * Fcount / (dom_ms * 1e-3) / 1e12
+    psnr = psnr_vs_abuffer(star, sc, W, H, cams, args) if args.psnr else None
+    line = {
+        "metric": "ms/frame (STAR-NT, 1080p)" if args.workload == "hd" else f"ms/frame (STAR-NT, {args.workload})",
+        "value": round(ms_frame, 5),
+        "unit": "ms/frame",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(t_max, 5),
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+bf16" if x_dtype == sn.BF16 else "f32",
+        "data": "synthetic seeded triangle soup, orbit camera",
+        "config": {"workload": desc, "frames_per_step": 2, "mlp": args.mlp, "weights": wname,
+                   "base_tile": args.base_tile, "l2": "flushed between steps (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "fragments_per_s": round(Fcount / (ms_frame * 1e-3), 1),
+        "fragments_full_res": int(Fcount),
+        "plain_ms_per_frame": round(float(np.mean(plain_ms)), 5),
+        "speedup_vs_plain": round(float(np.mean(plain_ms)) / ms_frame, 4),
+        "stages_ms": {k: round(v, 5) for k, v in stage_mean.items()},
+        "pass_state": {k: state[k] for k in ("W2", "H2", "W3", "H3", "s2", "s3", "wbar", "hist")},
+        "wall_s": round(wall, 3),
+        "gpu_launches": KERNELS_PER_STEP * args.steps,
+        "clocks": clocks,
+        "e2e": e2e,
+        "roofline": {"bound": "alu", "kernel": "k_pass<kTop1> (pass 1, full resolution)",
+                     "achieved": round(achieved, 4), "peak": round(alu_peak, 3), "unit": "Tops/s",
+                     "frac": round(achieved / alu_peak, 5), "traffic": None,
+                     "peak_source": f"{N_SM} SM x {ALU_LANES_PER_SM} lanes x sm_max_mhz ({peaks_kind})",
+                     "ops_per_fragment": OPS_PER_FRAGMENT, "launch_ms": round(dom_ms, 5)},
+    }
+    if psnr is not None:
+        line["psnr_db"] = psnr
+    return line
+
+
+def fragment_count(sn, r, vp, W, H):
+    import torch
+    P = W * H
+    frags = dict(count=torch.zeros(P, dtype=torch.int32, device="cuda"),
+                 offset=torch.zeros(P + 1, dtype=torch.int32, device="cuda"),
+                 z=torch.zeros(1, dtype=torch.float32, device="cuda"),
+                 prim=torch.zeros(1, dtype=torch.int32, device="cuda"),
+                 total=torch.zeros(1, dtype=torch.int32, device="cuda"))
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    sn.raster(r.scene, vp, r.full_size, W, H, r.bins[0], frags, st)
+    torch.cuda.synchronize()
+    return int(frags["total"].cpu().numpy().view(np.uint32)[0])
+
+
+def end_to_end(sn, torch, sc, w, x_dtype, W, H, cams, args):
+    """Same metric through the public API from host memory: per step the
+    triangle soup is copied host->device, one real and one interpolated frame
+    are rendered, and the 8-bit frame is read back."""
+    from paper_2606_16747_b300.pipeline import Renderer
+    r = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=x_dtype, base_tile=args.base_tile)
+    hv = torch.from_numpy(np.ascontiguousarray(sc.verts)).pin_memory()
+    hc = torch.from_numpy(np.ascontiguousarray(sc.rgba8).view(np.int32)).pin_memory()
+    hvp = [torch.from_numpy(np.ascontiguousarray(c.vp32)).pin_memory() for c in cams]
+    hvp64 = [torch.from_numpy(np.ascontiguousarray(c.vp64.reshape(16))).pin_memory() for c in cams]
+    out = torch.empty(W * H, dtype=torch.int32).pin_memory()
+    times = []
+    for k in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r.verts.copy_(hv, non_blocking=True)
+        r.rgba8.copy_(hc, non_blocking=True)
+        r.vp.copy_(hvp[2 * k], non_blocking=True)
+        r.star_frame()
+        r.prev_rgba.copy_(r.rgba32f)
+        r.prev_z1.copy_(r.l1["z1"])
+        r.vp64_prev.copy_(hvp64[2 * k], non_blocking=True)
+        r.vp64_cur.copy_(hvp64[2 * k + 1], non_blocking=True)
+        r.interp_frame()
+        out.copy_(r.rgba8_out, non_blocking=True)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    r.check_status()
+    h2d = hv.numel() * 4 + hc.numel() * 4 + 64 + 2 * 128
+    return {"value": round(float(np.mean(times)) * 1e3 / 2.0, 5), "unit": "ms/frame",
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(out.numel() * 4)}
+
+
+def psnr_vs_abuffer(r, sc, W, H, cams, args):
+    """PSNR of the last real frame against the exact A-buffer (CPU oracle)."""
+    import oracle
+    k = 2 * (args.warmup + args.steps) + 2
+    r.vp.copy_(__import__("torch").tensor(cams[k].vp32, device="cuda"))
+    r.star_frame()
+    rgb = r.rgba32f.cpu().numpy().reshape(-1, 4)[:, :3].astype(np.float64)
+    fr = oracle.raster(sc.verts, cams[k].vp32, W, H, threads=os.cpu_count() or 1)
+    ab = oracle.resolve(fr, sc.rgba8, threads=os.cpu_count() or 1)["abuf"]
+    mse = float(np.mean((rgb - ab) ** 2))
+    return round(10.0 * math.log10(1.0 / max(mse, 1e-30)), 3)
+
+
+# ---------------------------------------------------------------------------
+def cpu_oracle_frame(sc, w, cam, threads):
+    import oracle
+    from paper_2606_16747_b300 import scenes
+    return oracle.frame_full(sc.verts, sc.rgba8, cam.vp32, sc.width, sc.height, scenes.mlp_flat(w),
+                             threads=threads)
+
+
+def run_cpu_baseline(args):
+    """The oracle as it stands on the host cores, bounded sample of the workload."""
+    from paper_2606_16747_b300 import scenes
+    sc, desc = workload_scene(args.workload)
+    w, _ = mlp_weights()
+    cams = scenes.orbit_cameras(sc.width, sc.height, 4)
+    threads = os.cpu_count() or 1
+    cpu_oracle_frame(sc, w, cams[0], threads)          # build / page in
+    t0 = time.perf_counter()
+    n = 0
+    while n < 2 or (time.perf_counter() - t0 < 10.0 and n < 8):
+        cpu_oracle_frame(sc, w, cams[n % 4], threads)
+        n += 1
+    dt = (time.perf_counter() - t0) / n
+    return {"value": round(dt * 1e3, 3), "unit": "ms/frame", "cores": threads, "kind": "oracle",
+            "sample": f"{n} full frames of the plain full-resolution neural pipeline ({desc}), "
+                      "float64 oracle, threads over rows"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    cb = run_cpu_baseline_steps(args)
+    return cb
+
+
+def run_cpu_baseline_steps(args):
+    from paper_2606_16747_b300 import scenes
+    sc, desc = workload_scene(args.workload)
+    w, _ = mlp_weights()
+    cams = scenes.orbit_cameras(sc.width, sc.height, 2 * (args.warmup + args.steps) + 2)
+    threads = os.cpu_count() or 1
+    for k in range(args.warmup):
+        cpu_oracle_frame(sc, w, cams[k], threads)
+    times = []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        cpu_oracle_frame(sc, w, cams[args.warmup + k], threads)
+        times.append(time.perf_counter() - t0)
+    v = float(np.mean(times)) * 1e3
+    return {"impl": "reference", "metric": "ms/frame (STAR-NT, 1080p)" if args.workload == "hd" else
+            f"ms/frame (STAR-NT, {args.workload})", "value": round(v, 3), "unit": "ms/frame",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v, 3),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic seeded triangle soup",
+            "config": {"workload": desc, "frames_per_step": 1},
+            "cpu_baseline": {"value": round(v, 3), "unit": "ms/frame", "cores": threads, "kind": "oracle",
+                             "sample": "one full frame per step (plain full-resolution pipeline), "
+                                       "float64 oracle"},
+            "e2e": {"value": round(v, 3), "unit": "ms/frame", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="hd", choices=["hd", "uhd", "small"])
+    ap.add_argument("--mlp", default="bf16", choices=["bf16", "f32"])
+    ap.add_argument("--base-tile", type=int, default=16)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--psnr", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+        if rank == 0 and line is not None:
+            print(json.dumps(line))
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    line = run_ours(args, rank, world)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = run_cpu_baseline(args)
+        print(json.dumps(line))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

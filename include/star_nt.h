@@ -1,0 +1,284 @@
+/*
+ * star_nt.h -- C ABI of the STAR-NT per-frame hot path on one B300 (sm_103a).
+ *
+ * STAR-NT (arXiv 2606.16747) renders order-independent transparency with
+ * three geometry passes (nearest fragment, second-nearest fragment, tail
+ * statistics), a small MLP that predicts the colour of the fragments behind
+ * the two nearest ones, and the decoupled composite of Eq. 4.  Passes 2 and 3
+ * run at reduced resolution chosen by an adaptive quadtree over the previous
+ * frame (Sec. 3.1, 3.2, Eq. 2); interpolated frames reuse the last real frame
+ * through depth-based reprojection (Sec. 3.3, last paragraph).
+ *
+ * Conventions common to every call
+ *  - All buffers are caller-owned device memory given as plain pointers.  The
+ *    library never allocates, frees or synchronises, and enqueues all work on
+ *    the stream it is given (a cudaStream_t passed as void*).
+ *  - Pointers must be 16-byte aligned; workspaces 256-byte aligned.
+ *  - Every call returns a star_nt_status.  Bad host arguments are rejected
+ *    before anything is enqueued (STAR_NT_ERR_ARG).  A failed launch returns
+ *    STAR_NT_ERR_CUDA.  Conditions found on the device (capacity overflow, an
+ *    expired wait) are written to a caller-provided device int32 status word
+ *    (first error wins) that the caller reads after its own synchronisation;
+ *    later calls that depend on a failed one do no work.  Nothing traps.
+ *  - Sizes that change from frame to frame (the reduced pass resolutions) are
+ *    read on the device, so one captured CUDA graph replays every frame.
+ *  - Images are row-major, pixel p = y * width + x, y pointing down.
+ *  - Colours are straight RGBA8 packed in a uint32 (R bits 0-7, G 8-15,
+ *    B 16-23, A 24-31); c = c8 / 255, alpha = a8 / 255.
+ */
+#ifndef STAR_NT_H
+#define STAR_NT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define STAR_NT_VERSION 1
+
+typedef int32_t star_nt_status;
+#define STAR_NT_OK 0
+#define STAR_NT_ERR_ARG 1
+#define STAR_NT_ERR_CAPACITY 2
+#define STAR_NT_ERR_CUDA 3
+#define STAR_NT_ERR_TIMEOUT 4
+#define STAR_NT_ERR_UNSUPPORTED 5
+
+/* element types of the network input */
+#define STAR_NT_F32 0  /* [P][8] float32: x0..x4, tail flag, 0, 0 */
+#define STAR_NT_BF16 1 /* [P][16] bfloat16: x0..x4, tail flag, zeros */
+
+/* Quadtree tiles: base tile side (pixels) and levels (Sec. 3.1). */
+#define STAR_NT_QT_LEVELS 4
+
+int32_t star_nt_version(void);
+const char *star_nt_status_string(int32_t status);
+
+/* ------------------------------------------------------------------------ */
+/* Inputs                                                                    */
+
+/* A soup of flat-coloured transparent triangles (device memory).
+ * verts: [n_tris][3][4] float32 world-space (x, y, z, w); rgba8: [n_tris].
+ * The primitive id of a triangle is its index. */
+typedef struct {
+    const float *verts;
+    const uint32_t *rgba8;
+    int32_t n_tris;
+} star_nt_scene;
+
+/* Render target of one geometry pass.
+ * view_proj: device, 16 float32, row-major, clip = M (x, y, z, w)^T; the
+ *   projection maps the visible depth range to NDC z in [0, 1].
+ * size: device, {W_p, H_p}, the pass's resolution (read on the device).
+ * max_w, max_h: host upper bounds of size[]; they size the launches. */
+typedef struct {
+    const float *view_proj;
+    const int32_t *size;
+    int32_t max_w, max_h;
+} star_nt_target;
+
+/* Parameters of the method.  Defaults (star_nt_default_params):
+ * bg = (1, 1, 1), kappa_n = 1/64, tau_split = 24, tau_merge = 12,
+ * delta2 = 2.2, delta3 = 3.0 (Eq. 2), base_tile = 16, relax_iters = 2. */
+typedef struct {
+    float bg[3];       /* background colour C_b of Eq. 4 */
+    float kappa_n;     /* feature x0 = kappa_n * N */
+    double tau_split;  /* split a leaf when D_i > tau_split (8-bit units) */
+    double tau_merge;  /* merge a node when D_i < tau_merge, tau_merge < tau_split */
+    double delta2;     /* Eq. 2 offset of pass 2 */
+    double delta3;     /* Eq. 2 offset of pass 3 */
+    int32_t base_tile; /* quadtree base tile side: 16 or 64 pixels */
+    int32_t relax_iters;
+} star_nt_params;
+
+void star_nt_default_params(star_nt_params *p);
+
+/* ------------------------------------------------------------------------ */
+/* star_nt_raster -- geometry front end of one pass (Sec. 3, Fig. 1).         */
+/*                                                                           */
+/* Transforms and snaps every triangle to the pass's render target (1/256    */
+/* pixel fixed point), drops triangles with a vertex outside the depth range */
+/* or behind the camera and degenerate ones (no back-face culling), and bins */
+/* the rest to 16 x 16-pixel tiles.  Optionally materialises every fragment  */
+/* (per-pixel lists in CSR form).  Coverage is exact: a pixel centre is      */
+/* covered when all three edge functions are positive, or zero on an edge    */
+/* with dy > 0 or (dy == 0 and dx < 0).  Depth is the NDC z interpolated in  */
+/* screen space with fixed float32 operations.                               */
+
+/* Workspace of binned triangles for one pass: caller allocates
+ * star_nt_bins_bytes(...) bytes of device memory (256-byte aligned). */
+typedef struct {
+    void *mem;
+    size_t bytes;
+    int32_t max_w, max_h;   /* largest render target this workspace serves */
+    int32_t max_tris;       /* largest scene */
+    int64_t pair_capacity;  /* (triangle, tile) pairs it can hold */
+} star_nt_bins;
+
+star_nt_status star_nt_bins_bytes(int32_t max_w, int32_t max_h, int32_t max_tris,
+                                  int64_t pair_capacity, size_t *bytes);
+
+/* Materialised fragments of a pass (optional output of star_nt_raster).
+ * count [max_w * max_h], offset [max_w * max_h + 1] (exclusive prefix sum of
+ * count over the pass's W_p * H_p pixels), z / prim [capacity], total: device
+ * uint32 receiving the fragment count (also when it exceeds capacity, in
+ * which case STAR_NT_ERR_CAPACITY is raised and no fragment is written).
+ * The order of a pixel's fragments is unspecified. */
+typedef struct {
+    uint32_t *count;
+    uint32_t *offset;
+    float *z;
+    int32_t *prim;
+    int64_t capacity;
+    uint32_t *total;
+} star_nt_frags;
+
+star_nt_status star_nt_raster(const star_nt_scene *scene, const star_nt_target *target,
+                              const star_nt_bins *bins, const star_nt_frags *frags_or_null,
+                              int32_t *d_status, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* star_nt_build_inputs -- the three geometry passes and the network input    */
+/* (Sec. 3.2, Sec. 3.3, Eq. 4).                                              */
+/*                                                                           */
+/* Per pixel of each pass (at its own resolution), fragments are ordered by   */
+/* (z, primitive id).  Pass 1 keeps the nearest (id1, z1); pass 2 the second  */
+/* nearest (id2); pass 3 the fragment count N and, over the tail (all but the */
+/* two nearest), sum a8, sum a8 c8 per channel and the tail transmittance    */
+/* t_tail = prod (1 - alpha_i).  The planes of passes 2 and 3 are upscaled   */
+/* bilinearly to W x H (half-pixel centres, clamp to edge), then             */
+/*   x     = [kappa_n N, t_tail, sum a8 c8 / (255 sum a8)]  (zero colour when */
+/*           the tail has no alpha) plus a tail flag (upscaled N > 2);       */
+/*   front = (C_exact,2 + T_2 t_tail C_b, T_2), C_exact,2 = a1 c1 + (1-a1) a2 c2, */
+/*           T_2 = (1 - a1)(1 - a2).                                         */
+/* When the three bins are the same object every pass runs at full           */
+/* resolution in one fused kernel (the plain neural OIT pipeline).           */
+
+/* Per-pass planes at the pass's resolution; members may be NULL when not
+ * wanted.  tail is [P][4] uint32: sum a8, sum a8 r8, sum a8 g8, sum a8 b8. */
+typedef struct {
+    int32_t *id1;
+    float *z1;
+    int32_t *id2;
+    uint32_t *n;
+    uint32_t *tail;
+    float *t_tail;
+} star_nt_layers;
+
+/* Full-resolution network input and front terms. */
+typedef struct {
+    void *x;         /* [W*H][8] float32 or [W*H][16] bfloat16 (x_dtype) */
+    int32_t x_dtype; /* STAR_NT_F32 or STAR_NT_BF16 */
+    float *front;    /* [W*H][4] */
+} star_nt_features;
+
+/* bins1/2/3: the binned passes (written by star_nt_raster); layers1/2/3: the
+ * per-pass planes (layers1 needs id1 and z1 unless fused; layers2 needs id2;
+ * layers3 needs n, tail, t_tail).  W, H: full resolution. */
+star_nt_status star_nt_build_inputs(const star_nt_scene *scene, const star_nt_bins *bins1,
+                                    const star_nt_bins *bins2, const star_nt_bins *bins3,
+                                    const star_nt_layers *layers1, const star_nt_layers *layers2,
+                                    const star_nt_layers *layers3, int32_t W, int32_t H,
+                                    const star_nt_params *params, const star_nt_features *out,
+                                    int32_t *d_status, void *stream);
+
+/* The two halves of star_nt_build_inputs, callable on their own (for example
+ * to schedule or time the passes separately).
+ * star_nt_geometry_pass: one pass over one bins object at its resolution;
+ *   mode 1 writes id1/z1 (nearest fragment), mode 2 id2 (second nearest),
+ *   mode 3 n, tail and t_tail (tail statistics).  Members of layers that the
+ *   mode does not write may be NULL.
+ * star_nt_upscale_features: bilinear upscale of passes 2 and 3 (resolutions read
+ *   from their bins) and the full-resolution network input and front terms. */
+star_nt_status star_nt_geometry_pass(const star_nt_scene *scene, const star_nt_bins *bins,
+                                     int32_t mode, const star_nt_layers *layers,
+                                     int32_t *d_status, void *stream);
+star_nt_status star_nt_upscale_features(const star_nt_scene *scene, const star_nt_bins *bins2,
+                                const star_nt_bins *bins3, const star_nt_layers *layers1,
+                                const star_nt_layers *layers2, const star_nt_layers *layers3,
+                                int32_t W, int32_t H, const star_nt_params *params,
+                                const star_nt_features *out, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* star_nt_infer -- tail-colour MLP 5 -> 32 -> 16 -> 3, ReLU on every layer   */
+/* (Sec. 3.3).  f = 0 where the tail flag of x is zero.                      */
+
+/* float32 weights, row-major [out][in], device memory. */
+typedef struct {
+    const float *w1, *b1; /* [32][5], [32] */
+    const float *w2, *b2; /* [16][32], [16] */
+    const float *w3, *b3; /* [3][16], [3] */
+} star_nt_mlp;
+
+/* x: [P] rows in x_dtype layout; f: [P][4] float32 (rgb, 0).
+ * STAR_NT_F32 evaluates in float32 on the CUDA cores; STAR_NT_BF16 runs the
+ * three layers on the tcgen05 tensor cores (bf16 operands, fp32 accumulation
+ * in tensor memory); x must then be 256-byte aligned. */
+star_nt_status star_nt_infer(const star_nt_mlp *w, int32_t x_dtype, const void *x, float *f,
+                             int64_t P, int32_t *d_status, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* star_nt_composite -- Eq. 4: C = C_exact,2 + T_2 f(x) + T_all C_b.          */
+/* front: [P][4] (from star_nt_build_inputs), f: [P][4].  Writes rgba32f      */
+/* [P][4] (alpha = 1) and rgba8 [P] (round half to even of clamp(c,0,1)*255). */
+star_nt_status star_nt_composite(const float *front, const float *f, int64_t P, float *rgba32f,
+                                 uint32_t *rgba8, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* star_nt_quadtree -- adaptive screen-space tiles and tile-guided            */
+/* resolution (Sec. 3.1, Sec. 3.2, Eq. 2).                                   */
+/*                                                                           */
+/* Each base tile keeps a 21-bit mask of "split" bits (root; 4 level-1 nodes; */
+/* 16 level-2 nodes, children numbered 2 * y_half + x_half); level-3 nodes    */
+/* are leaves.  From mask_prev and the 8-bit composited frame: a leaf splits  */
+/* when D > tau_split; a node whose children are leaves, none of them        */
+/* splitting, merges when D < tau_merge (every decision on mask_prev, so a   */
+/* pixel's level changes by at most one).  D is the mean of the six pairwise */
+/* Euclidean RGB distances of the node's four corner pixels.  Then          */
+/* relax_iters Jacobi iterations split any leaf with an edge-neighbour leaf  */
+/* two or more levels deeper.  Finally N_l counts leaves at level l holding  */
+/* a pixel with id1 >= 0, wbar = sum l N_l / sum N_l and                     */
+/* s_p = clamp(2^(wbar - delta_p), 0.25, 1), W_p = ceil(s_p W).              */
+
+/* Device-resident resolution state read by the next frame's passes. */
+typedef struct {
+    int32_t W, H;     /* full resolution */
+    int32_t W2, H2;   /* pass 2 resolution */
+    int32_t W3, H3;   /* pass 3 resolution */
+    float s2, s3;
+    double wbar;
+    uint32_t hist[4];
+} star_nt_pass_state;
+
+star_nt_status star_nt_quadtree_ws_bytes(int32_t W, int32_t H, int32_t base_tile,
+                                         size_t *bytes);
+
+/* rgba8, id1: [W*H]; mask_prev, mask_out: [ceil(W/B) * ceil(H/B)] (distinct
+ * buffers); state: device star_nt_pass_state, fully rewritten; ws: workspace
+ * of star_nt_quadtree_ws_bytes bytes. */
+star_nt_status star_nt_quadtree(const uint32_t *rgba8, const int32_t *id1, int32_t W, int32_t H,
+                                const star_nt_params *params, const uint32_t *mask_prev,
+                                uint32_t *mask_out, star_nt_pass_state *state, void *ws,
+                                size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* star_nt_reproject -- interpolated frame by depth-based reprojection        */
+/* (Sec. 3.3, last paragraph; Fig. 1).                                       */
+/*                                                                           */
+/* For pixel (x, y): d = prev_z1 (first-fragment NDC depth of the last real   */
+/* frame, 1.0 where empty); the point (ndc(x, y), d) is unprojected with the */
+/* current camera and projected with the previous one; the previous frame is */
+/* sampled there bilinearly with clamp to edge.  A point behind the previous */
+/* camera keeps its own previous colour.                                    */
+/* prev_rgba, out_rgba: [W*H][4] float32 (distinct); prev_z1: [W*H];           */
+/* vp_prev, vp_cur: device, 16 float64 row-major view-projections.           */
+star_nt_status star_nt_reproject(const float *prev_rgba, const float *prev_z1,
+                                 const double *vp_prev, const double *vp_cur, int32_t W,
+                                 int32_t H, float *out_rgba, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STAR_NT_H */

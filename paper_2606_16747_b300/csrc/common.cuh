@@ -1,0 +1,132 @@
+// common.cuh -- shared device-side definitions of the STAR-NT CUDA path.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "star_nt.h"
+
+namespace star {
+
+constexpr int kSub = 256;         // sub-pixel steps per pixel (1/256 px fixed point)
+constexpr float kGuard = 32768.f; // |screen coordinate| limit, pixels
+constexpr int kTile = 16;         // raster tile side (pixels)
+constexpr int kChunk = 128;       // triangles staged in shared memory per round
+
+// Triangle set up for one render target.  Edge e runs from vertex e to vertex
+// e+1 (mod 3) after the vertices are ordered for a positive area; its
+// function E_e(P) = dx * Py - dy * Px + c is exact in int64, and c already
+// holds the tie bias (own_e - 1) so that a pixel centre is covered iff all
+// three biased values are >= 0.
+struct __align__(16) TriSetup {
+  int32_t dx[3], dy[3];
+  long long c[3];
+  float z0, dz1, dz2, r;      // depth plane: z = (z0 + b1 dz1) + b2 dz2, r = 1/area
+  int16_t xa, xb, ya, yb;     // covered-pixel bounding box (clamped), empty if xa > xb
+  uint32_t own;               // bit e set: edge e owns ties
+  uint32_t opq;               // 1 when a8 == 255
+  unsigned long long rg;      // a8*r8 | (a8*g8) << 32
+  unsigned long long ba;      // a8*b8 | a8 << 32
+  unsigned long long lg;      // round(-log2(1 - a8/255) * 2^32), 0 when opaque
+};
+static_assert(sizeof(TriSetup) == 112, "TriSetup layout");
+
+// Header at the start of a bins workspace.
+struct __align__(16) BinsHeader {
+  int32_t size[2];     // render-target size of the pass (copied from the target)
+  int32_t tiles_x, tiles_y;
+  int32_t n_tiles;     // tiles_x * tiles_y
+  int32_t n_pixels;    // size[0] * size[1]
+  uint32_t n_pairs;    // (triangle, tile) pairs needed
+  int32_t n_tris;
+  uint32_t pad[8];
+};
+static_assert(sizeof(BinsHeader) == 64, "BinsHeader layout");
+
+// Offsets of the parts of a bins workspace.
+struct BinsLayout {
+  size_t header, setups, tile_count, tile_offset, tile_cursor, pairs, scan_tmp, total;
+  int32_t max_tiles;
+};
+
+__host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+inline BinsLayout bins_layout(int32_t max_w, int32_t max_h, int32_t max_tris, int64_t pairs) {
+  BinsLayout L;
+  int32_t tx = (max_w + kTile - 1) / kTile, ty = (max_h + kTile - 1) / kTile;
+  L.max_tiles = tx * ty;
+  size_t o = 0;
+  L.header = o;      o = align_up(o + sizeof(BinsHeader), 256);
+  L.setups = o;      o = align_up(o + sizeof(TriSetup) * (size_t)max_tris, 256);
+  L.tile_count = o;  o = align_up(o + 4 * (size_t)(L.max_tiles + 1), 256);
+  L.tile_offset = o; o = align_up(o + 4 * (size_t)(L.max_tiles + 1), 256);
+  L.tile_cursor = o; o = align_up(o + 4 * (size_t)L.max_tiles, 256);
+  L.pairs = o;       o = align_up(o + 4 * (size_t)pairs, 256);
+  L.scan_tmp = o;    o = align_up(o + 4 * 8192, 256);
+  L.total = o;
+  return L;
+}
+
+// Device view of a bins workspace.
+struct BinsView {
+  BinsHeader *hd;
+  TriSetup *setups;
+  uint32_t *tile_count, *tile_offset, *tile_cursor, *pairs, *scan_tmp;
+  int32_t max_tiles;
+  int32_t max_w, max_h;
+  int64_t pair_capacity;
+};
+
+inline BinsView bins_view(const star_nt_bins &b) {
+  BinsLayout L = bins_layout(b.max_w, b.max_h, b.max_tris, b.pair_capacity);
+  char *m = (char *)b.mem;
+  BinsView v;
+  v.hd = (BinsHeader *)(m + L.header);
+  v.setups = (TriSetup *)(m + L.setups);
+  v.tile_count = (uint32_t *)(m + L.tile_count);
+  v.tile_offset = (uint32_t *)(m + L.tile_offset);
+  v.tile_cursor = (uint32_t *)(m + L.tile_cursor);
+  v.pairs = (uint32_t *)(m + L.pairs);
+  v.scan_tmp = (uint32_t *)(m + L.scan_tmp);
+  v.max_tiles = L.max_tiles;
+  v.max_w = b.max_w;
+  v.max_h = b.max_h;
+  v.pair_capacity = b.pair_capacity;
+  return v;
+}
+
+// First error wins.
+__device__ inline void raise_status(int32_t *status, int32_t code) {
+  if (status) atomicCAS(status, STAR_NT_OK, code);
+}
+
+__device__ inline long long floor_div_ll(long long a, long long b) {  // b > 0
+  long long q = a / b;
+  if ((a % b) != 0 && a < 0) --q;
+  return q;
+}
+
+// Bilinear source axis of the upscale: u * 2W = (2x + 1) Wp - W (exact).
+struct Axis {
+  int i0, i1;
+  int rem, den;
+};
+__device__ inline Axis upscale_axis(int x, int Wp, int W) {
+  long long num = (long long)(2 * x + 1) * Wp - W;
+  long long den = 2LL * W;
+  long long q = floor_div_ll(num, den);
+  Axis a;
+  a.rem = (int)(num - q * den);
+  a.den = (int)den;
+  a.i0 = (int)(q < 0 ? 0 : (q > Wp - 1 ? Wp - 1 : q));
+  a.i1 = (int)(q + 1 < 0 ? 0 : (q + 1 > Wp - 1 ? Wp - 1 : q + 1));
+  return a;
+}
+
+// Exclusive scan of up to 8192 * 8192 uint32 values (n read on the device),
+// total written to *total.  Three launches; tmp holds 8192 block sums.
+cudaError_t scan_exclusive_u32(const uint32_t *in, uint32_t *out, const int32_t *n_dev,
+                               int32_t n_max, uint32_t *tmp, uint32_t *total,
+                               cudaStream_t st);
+
+}  // namespace star

@@ -1,0 +1,251 @@
+// frame.cu -- float32 tail-colour MLP on the CUDA cores (Sec. 3.3), the
+// composite of Eq. 4, depth-based reprojection (Sec. 3.3, last paragraph)
+// and the small C-ABI utilities.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace star {
+
+// ---------------------------------------------------------------------------
+// MLP 5 -> 32 -> 16 -> 3, ReLU everywhere, float32 with the weights in
+// shared memory (every lane reads the same weight: broadcast).
+constexpr int kW1 = 0, kB1 = 160, kW2 = 192, kB2 = 704, kW3 = 720, kB3 = 768;
+
+__global__ void __launch_bounds__(256) k_mlp_f32(const float *__restrict__ w1, const float *__restrict__ b1,
+                                                 const float *__restrict__ w2, const float *__restrict__ b2,
+                                                 const float *__restrict__ w3, const float *__restrict__ b3,
+                                                 const float4 *__restrict__ X, float4 *__restrict__ F,
+                                                 long long P) {
+  __shared__ __align__(16) float s[776];
+  for (int i = threadIdx.x; i < 160; i += 256) s[kW1 + i] = w1[i];
+  for (int i = threadIdx.x; i < 512; i += 256) s[kW2 + i] = w2[i];
+  if (threadIdx.x < 32) s[kB1 + threadIdx.x] = b1[threadIdx.x];
+  if (threadIdx.x < 16) s[kB2 + threadIdx.x] = b2[threadIdx.x];
+  if (threadIdx.x < 48) s[kW3 + threadIdx.x] = w3[threadIdx.x];
+  if (threadIdx.x < 3) s[kB3 + threadIdx.x] = b3[threadIdx.x];
+  __syncthreads();
+  for (long long p = (long long)blockIdx.x * 256 + threadIdx.x; p < P; p += (long long)gridDim.x * 256) {
+    const float4 xa = X[2 * p], xb = X[2 * p + 1];
+    if (xb.y == 0.0f) {  // empty tail
+      F[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+      continue;
+    }
+    const float x[5] = {xa.x, xa.y, xa.z, xa.w, xb.x};
+    float h1[32];
+#pragma unroll
+    for (int o = 0; o < 32; ++o) {
+      float a = s[kB1 + o];
+#pragma unroll
+      for (int i = 0; i < 5; ++i) a = fmaf(s[kW1 + 5 * o + i], x[i], a);
+      h1[o] = fmaxf(a, 0.0f);
+    }
+    float h2[16];
+#pragma unroll
+    for (int o = 0; o < 16; ++o) {
+      float a = s[kB2 + o];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) a = fmaf(s[kW2 + 32 * o + i], h1[i], a);
+      h2[o] = fmaxf(a, 0.0f);
+    }
+    float f[3];
+#pragma unroll
+    for (int o = 0; o < 3; ++o) {
+      float a = s[kB3 + o];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) a = fmaf(s[kW3 + 16 * o + i], h2[i], a);
+      f[o] = fmaxf(a, 0.0f);
+    }
+    F[p] = make_float4(f[0], f[1], f[2], 0.0f);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Eq. 4 with the first and last terms already in front.rgb.
+__global__ void __launch_bounds__(256) k_composite(const float4 *__restrict__ front,
+                                                   const float4 *__restrict__ f, long long P,
+                                                   float4 *__restrict__ out, uint32_t *__restrict__ q) {
+  for (long long p = (long long)blockIdx.x * 256 + threadIdx.x; p < P; p += (long long)gridDim.x * 256) {
+    const float4 a = front[p], b = f[p];
+    const float r = fmaf(a.w, b.x, a.x), g = fmaf(a.w, b.y, a.y), bl = fmaf(a.w, b.z, a.z);
+    if (out) out[p] = make_float4(r, g, bl, 1.0f);
+    if (q) {
+      const uint32_t R = __float2uint_rn(__saturatef(r) * 255.0f);
+      const uint32_t G = __float2uint_rn(__saturatef(g) * 255.0f);
+      const uint32_t B = __float2uint_rn(__saturatef(bl) * 255.0f);
+      q[p] = R | (G << 8) | (B << 16) | (255u << 24);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Reprojection.  With M = VP_prev inv(VP_cur) and E = M - I, the previous
+// clip position of v = (ndc_x, ndc_y, d, 1) is v + E v, so the screen offset
+// is dx = (W/2) (E0 v - ndc_x E3 v) / (1 + E3 v) (and likewise in y).  Every
+// term is small for small camera motion, which keeps float32 accurate where
+// absolute pixel coordinates would not be.
+__device__ void inverse4(const double *a, double *inv) {
+  const double s0 = a[0] * a[5] - a[4] * a[1], s1 = a[0] * a[6] - a[4] * a[2];
+  const double s2 = a[0] * a[7] - a[4] * a[3], s3 = a[1] * a[6] - a[5] * a[2];
+  const double s4 = a[1] * a[7] - a[5] * a[3], s5 = a[2] * a[7] - a[6] * a[3];
+  const double c5 = a[10] * a[15] - a[14] * a[11], c4 = a[9] * a[15] - a[13] * a[11];
+  const double c3 = a[9] * a[14] - a[13] * a[10], c2 = a[8] * a[15] - a[12] * a[11];
+  const double c1 = a[8] * a[14] - a[12] * a[10], c0 = a[8] * a[13] - a[12] * a[9];
+  const double id = 1.0 / (s0 * c5 - s1 * c4 + s2 * c3 + s3 * c2 - s4 * c1 + s5 * c0);
+  inv[0] = (a[5] * c5 - a[6] * c4 + a[7] * c3) * id;
+  inv[1] = (-a[1] * c5 + a[2] * c4 - a[3] * c3) * id;
+  inv[2] = (a[13] * s5 - a[14] * s4 + a[15] * s3) * id;
+  inv[3] = (-a[9] * s5 + a[10] * s4 - a[11] * s3) * id;
+  inv[4] = (-a[4] * c5 + a[6] * c2 - a[7] * c1) * id;
+  inv[5] = (a[0] * c5 - a[2] * c2 + a[3] * c1) * id;
+  inv[6] = (-a[12] * s5 + a[14] * s2 - a[15] * s1) * id;
+  inv[7] = (a[8] * s5 - a[10] * s2 + a[11] * s1) * id;
+  inv[8] = (a[4] * c4 - a[5] * c2 + a[7] * c0) * id;
+  inv[9] = (-a[0] * c4 + a[1] * c2 - a[3] * c0) * id;
+  inv[10] = (a[12] * s4 - a[13] * s2 + a[15] * s0) * id;
+  inv[11] = (-a[8] * s4 + a[9] * s2 - a[11] * s0) * id;
+  inv[12] = (-a[4] * c3 + a[5] * c1 - a[6] * c0) * id;
+  inv[13] = (a[0] * c3 - a[1] * c1 + a[2] * c0) * id;
+  inv[14] = (-a[12] * s3 + a[13] * s1 - a[14] * s0) * id;
+  inv[15] = (a[8] * s3 - a[9] * s1 + a[10] * s0) * id;
+}
+
+__global__ void __launch_bounds__(256) k_reproject(const float4 *__restrict__ prev,
+                                                   const float *__restrict__ z1,
+                                                   const double *__restrict__ vp_prev,
+                                                   const double *__restrict__ vp_cur, int W, int H,
+                                                   float4 *__restrict__ out) {
+  __shared__ float sE[16];
+  if (threadIdx.x == 0) {
+    double a[16], inv[16];
+    for (int i = 0; i < 16; ++i) a[i] = vp_cur[i];
+    inverse4(a, inv);
+    for (int r = 0; r < 4; ++r)
+      for (int c = 0; c < 4; ++c) {
+        double m = 0.0;
+        for (int k = 0; k < 4; ++k) m += vp_prev[4 * r + k] * inv[4 * k + c];
+        sE[4 * r + c] = (float)(m - (r == c ? 1.0 : 0.0));
+      }
+  }
+  __syncthreads();
+  const int x = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
+  if (x >= W || y >= H) return;
+  const size_t p = (size_t)y * W + x;
+  const float nx = (float)(2 * x + 1) / (float)W - 1.0f;
+  const float ny = 1.0f - (float)(2 * y + 1) / (float)H;
+  const float d = z1[p];
+  const float a0 = fmaf(sE[0], nx, fmaf(sE[1], ny, fmaf(sE[2], d, sE[3])));
+  const float a1 = fmaf(sE[4], nx, fmaf(sE[5], ny, fmaf(sE[6], d, sE[7])));
+  const float a3 = fmaf(sE[12], nx, fmaf(sE[13], ny, fmaf(sE[14], d, sE[15])));
+  const float den = 1.0f + a3;
+  if (!(den > 0.0f)) {
+    out[p] = prev[p];
+    return;
+  }
+  float dx = 0.5f * (float)W * (a0 - nx * a3) / den;
+  float dy = -0.5f * (float)H * (a1 - ny * a3) / den;
+  dx = fminf(fmaxf(dx, -2.0f * W - 2.0f), 2.0f * W + 2.0f);
+  dy = fminf(fmaxf(dy, -2.0f * H - 2.0f), 2.0f * H + 2.0f);
+  const float fx0 = floorf(dx), fy0 = floorf(dy);
+  const float fx = dx - fx0, fy = dy - fy0;
+  const int ix = x + (int)fx0, iy = y + (int)fy0;
+  const int x0 = min(max(ix, 0), W - 1), x1 = min(max(ix + 1, 0), W - 1);
+  const int y0 = min(max(iy, 0), H - 1), y1 = min(max(iy + 1, 0), H - 1);
+  const float4 v00 = prev[(size_t)y0 * W + x0], v10 = prev[(size_t)y0 * W + x1];
+  const float4 v01 = prev[(size_t)y1 * W + x0], v11 = prev[(size_t)y1 * W + x1];
+  float4 o;
+  o.x = (1.f - fy) * ((1.f - fx) * v00.x + fx * v10.x) + fy * ((1.f - fx) * v01.x + fx * v11.x);
+  o.y = (1.f - fy) * ((1.f - fx) * v00.y + fx * v10.y) + fy * ((1.f - fx) * v01.y + fx * v11.y);
+  o.z = (1.f - fy) * ((1.f - fx) * v00.z + fx * v10.z) + fy * ((1.f - fx) * v01.z + fx * v11.z);
+  o.w = (1.f - fy) * ((1.f - fx) * v00.w + fx * v10.w) + fy * ((1.f - fx) * v01.w + fx * v11.w);
+  out[p] = o;
+}
+
+static int grid_for(long long P) {
+  long long g = (P + 255) / 256;
+  if (g > 148 * 16) g = 148 * 16;
+  return g < 1 ? 1 : (int)g;
+}
+
+}  // namespace star
+
+using namespace star;
+
+cudaError_t star_launch_mlp_bf16(const star_nt_mlp *w, const void *x, float *f, int64_t P,
+                                 int32_t *d_status, cudaStream_t st);
+
+extern "C" int32_t star_nt_version(void) { return STAR_NT_VERSION; }
+
+extern "C" const char *star_nt_status_string(int32_t s) {
+  switch (s) {
+    case STAR_NT_OK: return "ok";
+    case STAR_NT_ERR_ARG: return "invalid argument";
+    case STAR_NT_ERR_CAPACITY: return "capacity exceeded";
+    case STAR_NT_ERR_CUDA: return "CUDA error";
+    case STAR_NT_ERR_TIMEOUT: return "device wait timed out";
+    case STAR_NT_ERR_UNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+  }
+}
+
+extern "C" void star_nt_default_params(star_nt_params *p) {
+  if (!p) return;
+  p->bg[0] = p->bg[1] = p->bg[2] = 1.0f;
+  p->kappa_n = 1.0f / 64.0f;
+  p->tau_split = 24.0;
+  p->tau_merge = 12.0;
+  p->delta2 = 2.2;
+  p->delta3 = 3.0;
+  p->base_tile = 16;
+  p->relax_iters = 2;
+}
+
+extern "C" star_nt_status star_nt_infer(const star_nt_mlp *w, int32_t x_dtype, const void *x,
+                                        float *f, int64_t P, int32_t *d_status, void *stream) {
+  if (!w || !w->w1 || !w->b1 || !w->w2 || !w->b2 || !w->w3 || !w->b3 || P < 0) return STAR_NT_ERR_ARG;
+  if (P > 0 && (!x || !f)) return STAR_NT_ERR_ARG;
+  if (((uintptr_t)x & 15u) || ((uintptr_t)f & 15u)) return STAR_NT_ERR_ARG;
+  if (P == 0) return STAR_NT_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (x_dtype == STAR_NT_F32) {
+    k_mlp_f32<<<grid_for(P), 256, 0, st>>>(w->w1, w->b1, w->w2, w->b2, w->w3, w->b3,
+                                           reinterpret_cast<const float4 *>(x),
+                                           reinterpret_cast<float4 *>(f), P);
+    return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
+  }
+  if (x_dtype == STAR_NT_BF16) {
+    if ((uintptr_t)x & 255u) return STAR_NT_ERR_ARG;
+    return star_launch_mlp_bf16(w, x, f, P, d_status, st) == cudaSuccess ? STAR_NT_OK
+                                                                          : STAR_NT_ERR_CUDA;
+  }
+  return STAR_NT_ERR_ARG;
+}
+
+extern "C" star_nt_status star_nt_composite(const float *front, const float *f, int64_t P,
+                                            float *rgba32f, uint32_t *rgba8, void *stream) {
+  if (P < 0 || (P > 0 && (!front || !f || (!rgba32f && !rgba8)))) return STAR_NT_ERR_ARG;
+  if (((uintptr_t)front & 15u) || ((uintptr_t)f & 15u) || ((uintptr_t)rgba32f & 15u))
+    return STAR_NT_ERR_ARG;
+  if (P == 0) return STAR_NT_OK;
+  k_composite<<<grid_for(P), 256, 0, (cudaStream_t)stream>>>(
+      reinterpret_cast<const float4 *>(front), reinterpret_cast<const float4 *>(f), P,
+      reinterpret_cast<float4 *>(rgba32f), rgba8);
+  return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
+}
+
+extern "C" star_nt_status star_nt_reproject(const float *prev_rgba, const float *prev_z1,
+                                            const double *vp_prev, const double *vp_cur, int32_t W,
+                                            int32_t H, float *out_rgba, void *stream) {
+  if (W <= 0 || H <= 0 || !prev_rgba || !prev_z1 || !vp_prev || !vp_cur || !out_rgba ||
+      prev_rgba == out_rgba)
+    return STAR_NT_ERR_ARG;
+  if (((uintptr_t)prev_rgba & 15u) || ((uintptr_t)out_rgba & 15u) || ((uintptr_t)vp_prev & 7u) ||
+      ((uintptr_t)vp_cur & 7u))
+    return STAR_NT_ERR_ARG;
+  dim3 grid((W + 31) / 32, (H + 7) / 8);
+  k_reproject<<<grid, 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const float4 *>(prev_rgba),
+                                                      prev_z1, vp_prev, vp_cur, W, H,
+                                                      reinterpret_cast<float4 *>(out_rgba));
+  return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
+}

@@ -1,0 +1,403 @@
+// mlp_tc.cu -- the tail-colour MLP 5 -> 32 -> 16 -> 3 (Sec. 3.3) on the
+// tcgen05 tensor cores: bf16 operands, fp32 accumulation in tensor memory.
+//
+// One CTA of 128 threads runs a persistent loop over 128-pixel tiles.  Per
+// tile, three chained MMAs (M = 128 pixels):
+//   D1[128x32] = X[128x16]  W1^T   (K padded 5 -> 16; the upper half of K is a
+//                                    zero block in shared memory)
+//   D2[128x16] = H1[128x32] W2^T   (two K = 16 steps)
+//   D3[128x16] = H2[128x16] W3^T   (N padded 3 -> 16)
+// X tiles arrive by TMA (double buffered, one tile ahead); after each MMA
+// the four warps read their 32 accumulator rows from tensor memory, apply
+// bias and ReLU, and write the next layer's bf16 operand to shared memory.
+// Operands use the no-swizzle K-major layout: 8-row x 16-byte core matrices,
+// LBO = distance between K-adjacent core matrices, SBO = between 8-row
+// groups.  Every mbarrier wait is bounded (1 s); on expiry the kernel sets
+// STAR_NT_ERR_TIMEOUT, stops, frees its tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace star {
+
+constexpr int kMlpThreads = 128;
+constexpr int kRows = 128;
+constexpr uint32_t kTmemCols = 64;          // D1: 0..31, D2: 32..47, D3: 48..63
+constexpr int kMlpCtasPerSm = 8;            // 8 x 64 columns = all of tensor memory
+constexpr unsigned long long kWaitNs = 1000000000ull;
+
+// shared memory map (bytes from a 1024-aligned base)
+constexpr uint32_t kSX = 0;         // 2 x (X tile 2048 + zero block 2048)
+constexpr uint32_t kSH1 = 8192;     // 4 core columns x 2048
+constexpr uint32_t kSH2 = 16384;    // 2 core columns x 2048
+constexpr uint32_t kSW1 = 20480;    // N=32, K=16: 2 x 512
+constexpr uint32_t kSW2 = 21504;    // N=16, K=32: 4 x 256
+constexpr uint32_t kSW3 = 22528;    // N=16, K=16: 2 x 256
+constexpr uint32_t kSB = 23040;     // b1[32], b2[16], b3[16] float
+constexpr uint32_t kSBar = 23296;   // tma[2], mma, tmem slot
+constexpr uint32_t kSmemUsed = 23360;
+// requested dynamic shared memory: caps residency at 8 CTAs per SM so that
+// the 8 x 64 tensor-memory columns always suffice
+constexpr uint32_t kSmemBytes = 26 * 1024;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait: false when the phase did not complete within kWaitNs
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
+  if (mbar_try(bar, phase)) return true;
+  const unsigned long long t0 = globaltimer();
+  while (!mbar_try(bar, phase))
+    if (globaltimer() - t0 > kWaitNs) return false;
+  return true;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version of this architecture; no swizzle
+  return d;
+}
+
+// kind::f16 instruction descriptor: bf16 A and B, fp32 D, K-major, M = 128
+__host__ __device__ constexpr uint32_t idesc_bf16(uint32_t n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t *>(&h);
+}
+
+// one bf16 weight into the K-major core-matrix layout of a B operand
+__device__ __forceinline__ void put_w(uint8_t *base, int n, int k, int lbo, float v) {
+  __nv_bfloat16 h = __float2bfloat16_rn(v);
+  *reinterpret_cast<__nv_bfloat16 *>(base + (k >> 3) * lbo + n * 16 + (k & 7) * 2) = h;
+}
+
+__global__ void __launch_bounds__(kMlpThreads, kMlpCtasPerSm)
+    k_mlp_bf16(const __grid_constant__ CUtensorMap xmap, const float *__restrict__ w1,
+               const float *__restrict__ b1, const float *__restrict__ w2,
+               const float *__restrict__ b2, const float *__restrict__ w3,
+               const float *__restrict__ b3, float4 *__restrict__ F, long long P,
+               int32_t *status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                            ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t sbase = smem_u32(sm);
+  const uint32_t bar_tma0 = sbase + kSBar, bar_tma1 = sbase + kSBar + 8, bar_mma = sbase + kSBar + 16;
+  uint32_t *s_tmem = reinterpret_cast<uint32_t *>(sm + kSBar + 24);
+  volatile int *s_abort = reinterpret_cast<volatile int *>(sm + kSBar + 28);
+  float *sb = reinterpret_cast<float *>(sm + kSB);
+
+  // weights (bf16, zero padded), biases, zero K blocks of the X buffers
+  for (int i = tid; i < (int)(kSBar - kSW1) / 4; i += kMlpThreads)
+    reinterpret_cast<uint32_t *>(sm + kSW1)[i] = 0u;
+  for (int i = tid; i < 512; i += kMlpThreads) {  // 2 x 2048-byte zero blocks
+    reinterpret_cast<uint32_t *>(sm + kSX + 2048)[i] = 0u;
+    reinterpret_cast<uint32_t *>(sm + kSX + 6144)[i] = 0u;
+  }
+  __syncthreads();
+  for (int i = tid; i < 32 * 5; i += kMlpThreads) put_w(sm + kSW1, i / 5, i % 5, 512, w1[i]);
+  for (int i = tid; i < 16 * 32; i += kMlpThreads) put_w(sm + kSW2, i / 32, i % 32, 256, w2[i]);
+  for (int i = tid; i < 3 * 16; i += kMlpThreads) put_w(sm + kSW3, i / 16, i % 16, 256, w3[i]);
+  if (tid < 32) sb[tid] = b1[tid];
+  if (tid < 16) sb[32 + tid] = b2[tid];
+  if (tid < 16) sb[48 + tid] = tid < 3 ? b3[tid] : 0.0f;
+  if (tid == 0) {
+    mbar_init(bar_tma0, 1);
+    mbar_init(bar_tma1, 1);
+    mbar_init(bar_mma, 1);
+    *s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(s_tmem)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *s_tmem;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const int row = warp * 32 + (tid & 31);
+
+  const long long ntiles = (P + kRows - 1) / kRows;
+  long long tile = blockIdx.x;
+  uint32_t ph_tma[2] = {0u, 0u}, ph_mma = 0u;
+  int buf = 0;
+  bool tma_pending = false;
+  const uint64_t dW1 = smem_desc(sbase + kSW1, 512, 128);
+  const uint64_t dW2a = smem_desc(sbase + kSW2, 256, 128), dW2b = smem_desc(sbase + kSW2 + 512, 256, 128);
+  const uint64_t dW3 = smem_desc(sbase + kSW3, 256, 128);
+  const uint64_t dH1a = smem_desc(sbase + kSH1, 2048, 128), dH1b = smem_desc(sbase + kSH1 + 4096, 2048, 128);
+  const uint64_t dH2 = smem_desc(sbase + kSH2, 2048, 128);
+
+  if (tid == 0 && tile < ntiles) {
+    mbar_expect_tx(bar_tma0, 2048);
+    tma_load_2d(sbase + kSX, &xmap, 0, (int)(tile * kRows), bar_tma0);
+    tma_pending = true;
+  }
+  while (tile < ntiles) {
+    const long long next = tile + gridDim.x;
+    const uint32_t xs = sbase + kSX + buf * 4096;
+    // ---- layer 1
+    if (tid == 0) {
+      if (!mbar_wait(buf ? bar_tma1 : bar_tma0, ph_tma[buf])) {
+        *s_abort = 1;
+      } else {
+        tma_pending = false;
+        ph_tma[buf] ^= 1u;
+        fence_after();
+        mma_bf16(tmem + 0, smem_desc(xs, 2048, 128), dW1, idesc_bf16(32), 0u);
+        mma_commit(bar_mma);
+        if (next < ntiles) {
+          const uint32_t nb = buf ? bar_tma0 : bar_tma1;
+          mbar_expect_tx(nb, 2048);
+          tma_load_2d(sbase + kSX + (buf ^ 1) * 4096, &xmap, 0, (int)(next * kRows), nb);
+          tma_pending = true;
+        }
+      }
+    }
+    __syncthreads();
+    if (*s_abort) break;
+    if (!mbar_wait(bar_mma, ph_mma)) *s_abort = 1;
+    ph_mma ^= 1u;
+    fence_after();
+    const float flag = __bfloat162float(
+        *reinterpret_cast<const __nv_bfloat16 *>(sm + kSX + buf * 4096 + row * 16 + 10));
+    {
+      float d[32];
+      tmem_ld32(tmem + lane_base + 0, d);
+      uint32_t pk[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        pk[j] = pack_bf16(fmaxf(d[2 * j] + sb[2 * j], 0.0f), fmaxf(d[2 * j + 1] + sb[2 * j + 1], 0.0f));
+#pragma unroll
+      for (int kc = 0; kc < 4; ++kc)
+        *reinterpret_cast<uint4 *>(sm + kSH1 + kc * 2048 + row * 16) =
+            make_uint4(pk[4 * kc], pk[4 * kc + 1], pk[4 * kc + 2], pk[4 * kc + 3]);
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    if (*s_abort) break;
+    // ---- layer 2
+    if (tid == 0) {
+      fence_after();
+      mma_bf16(tmem + 32, dH1a, dW2a, idesc_bf16(16), 0u);
+      mma_bf16(tmem + 32, dH1b, dW2b, idesc_bf16(16), 1u);
+      mma_commit(bar_mma);
+    }
+    if (!mbar_wait(bar_mma, ph_mma)) *s_abort = 1;
+    ph_mma ^= 1u;
+    fence_after();
+    {
+      float d[16];
+      tmem_ld16(tmem + lane_base + 32, d);
+      uint32_t pk[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        pk[j] = pack_bf16(fmaxf(d[2 * j] + sb[32 + 2 * j], 0.0f),
+                          fmaxf(d[2 * j + 1] + sb[32 + 2 * j + 1], 0.0f));
+#pragma unroll
+      for (int kc = 0; kc < 2; ++kc)
+        *reinterpret_cast<uint4 *>(sm + kSH2 + kc * 2048 + row * 16) =
+            make_uint4(pk[4 * kc], pk[4 * kc + 1], pk[4 * kc + 2], pk[4 * kc + 3]);
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    if (*s_abort) break;
+    // ---- layer 3
+    if (tid == 0) {
+      fence_after();
+      mma_bf16(tmem + 48, dH2, dW3, idesc_bf16(16), 0u);
+      mma_commit(bar_mma);
+    }
+    if (!mbar_wait(bar_mma, ph_mma)) *s_abort = 1;
+    ph_mma ^= 1u;
+    fence_after();
+    {
+      float d[16];
+      tmem_ld16(tmem + lane_base + 48, d);
+      const long long p = tile * kRows + row;
+      if (p < P) {
+        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (flag != 0.0f) {
+          o.x = fmaxf(d[0] + sb[48], 0.0f);
+          o.y = fmaxf(d[1] + sb[49], 0.0f);
+          o.z = fmaxf(d[2] + sb[50], 0.0f);
+        }
+        F[p] = o;
+      }
+    }
+    fence_before();
+    __syncthreads();
+    if (*s_abort) break;
+    buf ^= 1;
+    tile = next;
+  }
+  if (*s_abort && tid == 0) {
+    raise_status(status, STAR_NT_ERR_TIMEOUT);
+    if (tma_pending) mbar_wait(buf ? bar_tma0 : bar_tma1, ph_tma[buf ^ 1]);
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
+                 : "memory");
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void *p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+}  // namespace star
+
+using namespace star;
+
+cudaError_t star_launch_mlp_bf16(const star_nt_mlp *w, const void *x, float *f, int64_t P,
+                                 int32_t *d_status, cudaStream_t st) {
+  static_assert(kSmemUsed + 1024 <= kSmemBytes, "shared memory map");
+  if (P <= 0) return cudaSuccess;
+  if (P > 0x7fffffffLL) return cudaErrorInvalidValue;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  CUtensorMap map;
+  const cuuint64_t dims[2] = {8, (cuuint64_t)P};
+  const cuuint64_t strides[1] = {16};
+  const cuuint32_t box[2] = {8, (cuuint32_t)kRows};
+  const cuuint32_t estr[2] = {1, 1};
+  if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(x), dims, strides, box, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_mlp_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) !=
+        cudaSuccess)
+      return cudaErrorInvalidValue;
+    attr = true;
+  }
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long ntiles = (P + kRows - 1) / kRows;
+  long long grid = (long long)sms * kMlpCtasPerSm;
+  if (grid > ntiles) grid = ntiles;
+  k_mlp_bf16<<<(unsigned)grid, kMlpThreads, kSmemBytes, st>>>(map, w->w1, w->b1, w->w2, w->b2, w->w3,
+                                                              w->b3, reinterpret_cast<float4 *>(f), P,
+                                                              d_status);
+  return cudaGetLastError();
+}

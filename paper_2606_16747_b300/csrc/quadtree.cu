@@ -1,0 +1,286 @@
+// quadtree.cu -- star_nt_quadtree: adaptive screen-space tiles (Sec. 3.1)
+// and tile-guided pass resolution (Sec. 3.2, Eq. 2).
+//
+// One warp per base tile; lane k < 21 owns the node whose split bit is bit k
+// of the tile's mask (bit 0 root, bits 1..4 level-1 nodes, bits 5..20
+// level-2 nodes), so ballots assemble new masks directly.  All decisions are
+// taken on integer colour differences with correctly rounded float64 square
+// roots summed in a fixed order, so they are reproducible bit for bit.
+#include <math.h>
+
+#include "common.cuh"
+
+namespace star {
+
+struct QtLayout {
+  size_t hist, mask_a, mask_b, total;
+  int32_t tiles_x, tiles_y;
+};
+
+inline QtLayout qt_layout(int32_t W, int32_t H, int32_t B) {
+  QtLayout L;
+  L.tiles_x = (W + B - 1) / B;
+  L.tiles_y = (H + B - 1) / B;
+  const size_t nt = (size_t)L.tiles_x * L.tiles_y;
+  L.hist = 0;
+  L.mask_a = 256;
+  L.mask_b = align_up(L.mask_a + 4 * nt, 256);
+  L.total = align_up(L.mask_b + 4 * nt, 256);
+  return L;
+}
+
+// node of bit k: level and position (i, j) in units of the node size
+__device__ __forceinline__ void node_of_bit(int k, int &l, int &i, int &j) {
+  if (k == 0) { l = 0; i = 0; j = 0; return; }
+  if (k < 5) { const int c = k - 1; l = 1; i = c & 1; j = c >> 1; return; }
+  const int q = k - 5, c1 = q >> 2, c2 = q & 3;
+  l = 2;
+  i = (c1 & 1) * 2 + (c2 & 1);
+  j = (c1 >> 1) * 2 + (c2 >> 1);
+}
+
+__device__ __forceinline__ bool node_exists(uint32_t m, int k) {
+  if (k == 0) return true;
+  if (k < 5) return m & 1u;
+  const int c1 = (k - 5) >> 2;
+  return (m & 1u) && ((m >> (1 + c1)) & 1u);
+}
+
+// level of the leaf covering level-3 cell (cx, cy) of a tile, 0 <= cx, cy < 8
+__device__ __forceinline__ int cell_level(uint32_t m, int cx, int cy) {
+  if (!(m & 1u)) return 0;
+  const int c1 = ((cy >> 2) << 1) | (cx >> 2);
+  if (!((m >> (1 + c1)) & 1u)) return 1;
+  const int c2 = (((cy >> 1) & 1) << 1) | ((cx >> 1) & 1);
+  if (!((m >> (5 + 4 * c1 + c2)) & 1u)) return 2;
+  return 3;
+}
+
+// sum of the six pairwise RGB distances of the node's corner pixels
+__device__ double corner_dsum(const uint32_t *__restrict__ img, int W, int H, int x0, int y0, int S) {
+  const int xs[4] = {x0, x0 + S - 1, x0, x0 + S - 1};
+  const int ys[4] = {y0, y0, y0 + S - 1, y0 + S - 1};
+  int c[4][3];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int x = min(max(xs[k], 0), W - 1), y = min(max(ys[k], 0), H - 1);
+    const uint32_t v = img[(size_t)y * W + x];
+    c[k][0] = v & 255u;
+    c[k][1] = (v >> 8) & 255u;
+    c[k][2] = (v >> 16) & 255u;
+  }
+  const int pa[6] = {0, 0, 0, 1, 1, 2}, pb[6] = {1, 2, 3, 2, 3, 3};
+  double s = 0.0;
+#pragma unroll
+  for (int e = 0; e < 6; ++e) {
+    int q = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int d = c[pa[e]][k] - c[pb[e]][k];
+      q += d * d;
+    }
+    s = __dadd_rn(s, __dsqrt_rn((double)q));
+  }
+  return s;
+}
+
+__global__ void __launch_bounds__(256) k_qt_decide(const uint32_t *__restrict__ img, int W, int H,
+                                                   int B, int tiles_x, int n_tiles, double split6,
+                                                   double merge6, const uint32_t *__restrict__ mprev,
+                                                   uint32_t *__restrict__ mout) {
+  const int tile = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (tile >= n_tiles) return;
+  const uint32_t m = mprev[tile];
+  const int tx = tile % tiles_x, ty = tile / tiles_x;
+  bool leaf = false, split_node = false;
+  double ds = 0.0;
+  if (lane < 21) {
+    int l, i, j;
+    node_of_bit(lane, l, i, j);
+    const bool ex = node_exists(m, lane);
+    split_node = ex && ((m >> lane) & 1u);
+    leaf = ex && !split_node;
+    if (ex) {
+      const int S = B >> l;
+      ds = corner_dsum(img, W, H, tx * B + i * S, ty * B + j * S, S);
+    }
+  }
+  const uint32_t split_bits = __ballot_sync(0xffffffffu, leaf && ds > split6);
+  bool merge = false;
+  if (lane < 21 && split_node && ds < merge6) {
+    if (lane == 0) {
+      merge = ((m >> 1) & 15u) == 0u && ((split_bits >> 1) & 15u) == 0u;
+    } else if (lane < 5) {
+      const int c1 = lane - 1;
+      merge = ((m >> (5 + 4 * c1)) & 15u) == 0u && ((split_bits >> (5 + 4 * c1)) & 15u) == 0u;
+    } else {
+      merge = true;  // children are level-3 leaves
+    }
+  }
+  const uint32_t merge_bits = __ballot_sync(0xffffffffu, merge);
+  if (lane == 0) mout[tile] = (m | split_bits) & ~merge_bits;
+}
+
+__global__ void __launch_bounds__(256) k_qt_relax(int tiles_x, int tiles_y,
+                                                  const uint32_t *__restrict__ min,
+                                                  uint32_t *__restrict__ mout) {
+  const int tile = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (tile >= tiles_x * tiles_y) return;
+  const int tx = tile % tiles_x, ty = tile / tiles_x;
+  const uint32_t m = min[tile];
+  const uint32_t mL = tx > 0 ? min[tile - 1] : 0u, mR = tx + 1 < tiles_x ? min[tile + 1] : 0u;
+  const uint32_t mU = ty > 0 ? min[tile - tiles_x] : 0u;
+  const uint32_t mD = ty + 1 < tiles_y ? min[tile + tiles_x] : 0u;
+  bool split = false;
+  if (lane < 21) {
+    int l, i, j;
+    node_of_bit(lane, l, i, j);
+    if (node_exists(m, lane) && !((m >> lane) & 1u)) {
+      const int span = 8 >> l, cx0 = i * span, cy0 = j * span;
+      int deepest = 0;
+      for (int k = 0; k < span; ++k) {
+        // left / right columns and top / bottom rows just outside the leaf
+        if (cx0 > 0) deepest = max(deepest, cell_level(m, cx0 - 1, cy0 + k));
+        else if (tx > 0) deepest = max(deepest, cell_level(mL, 7, cy0 + k));
+        if (cx0 + span < 8) deepest = max(deepest, cell_level(m, cx0 + span, cy0 + k));
+        else if (tx + 1 < tiles_x) deepest = max(deepest, cell_level(mR, 0, cy0 + k));
+        if (cy0 > 0) deepest = max(deepest, cell_level(m, cx0 + k, cy0 - 1));
+        else if (ty > 0) deepest = max(deepest, cell_level(mU, cx0 + k, 7));
+        if (cy0 + span < 8) deepest = max(deepest, cell_level(m, cx0 + k, cy0 + span));
+        else if (ty + 1 < tiles_y) deepest = max(deepest, cell_level(mD, cx0 + k, 0));
+      }
+      split = deepest >= l + 2;
+    }
+  }
+  const uint32_t bits = __ballot_sync(0xffffffffu, split);
+  if (lane == 0) mout[tile] = m | bits;
+}
+
+// Occupied leaves per level: a leaf is occupied when one of its pixels has
+// a nearest fragment (id1 >= 0).  One CTA per tile; occupancy is gathered
+// per level-3 cell (B/8 pixels wide) into a 64-bit mask.
+__global__ void __launch_bounds__(256) k_qt_hist(const int32_t *__restrict__ id1, int W, int H, int B,
+                                                 int tiles_x, const uint32_t *__restrict__ mask,
+                                                 uint32_t *__restrict__ hist) {
+  __shared__ uint32_t s_occ[2];
+  __shared__ uint32_t s_hist[4];
+  const int tile = blockIdx.x;
+  const int tx = tile % tiles_x, ty = tile / tiles_x;
+  if (threadIdx.x < 2) s_occ[threadIdx.x] = 0u;
+  if (threadIdx.x < 4) s_hist[threadIdx.x] = 0u;
+  __syncthreads();
+  const int cs = B / 8;
+  uint32_t lo = 0, hi = 0;
+  for (int k = threadIdx.x; k < B * B; k += 256) {
+    const int lx = k % B, ly = k / B;
+    const int x = tx * B + lx, y = ty * B + ly;
+    if (x < W && y < H && id1[(size_t)y * W + x] >= 0) {
+      const int cell = (ly / cs) * 8 + (lx / cs);
+      if (cell < 32) lo |= 1u << cell;
+      else hi |= 1u << (cell - 32);
+    }
+  }
+  if (lo) atomicOr(&s_occ[0], lo);
+  if (hi) atomicOr(&s_occ[1], hi);
+  __syncthreads();
+  const unsigned long long occ = (unsigned long long)s_occ[0] | ((unsigned long long)s_occ[1] << 32);
+  const uint32_t m = mask[tile];
+  const int k = threadIdx.x;
+  if (k < 21 + 64) {
+    int l, i, j;
+    bool isleaf;
+    if (k < 21) {
+      node_of_bit(k, l, i, j);
+      isleaf = node_exists(m, k) && !((m >> k) & 1u);
+    } else {
+      l = 3;
+      i = (k - 21) & 7;
+      j = (k - 21) >> 3;
+      isleaf = cell_level(m, i, j) == 3;
+    }
+    if (isleaf) {
+      const int span = 8 >> l;
+      unsigned long long reg = 0;
+      for (int b = 0; b < span; ++b)
+        for (int a = 0; a < span; ++a) reg |= 1ull << ((j * span + b) * 8 + (i * span + a));
+      if (occ & reg) atomicAdd(&s_hist[l], 1u);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 4 && s_hist[threadIdx.x]) atomicAdd(hist + threadIdx.x, s_hist[threadIdx.x]);
+}
+
+// Eq. 2 and the next frame's pass sizes.
+__global__ void k_qt_finalize(const uint32_t *__restrict__ hist, int W, int H, double delta2,
+                              double delta3, star_nt_pass_state *state) {
+  if (threadIdx.x != 0) return;
+  const uint32_t h0 = hist[0], h1 = hist[1], h2 = hist[2], h3 = hist[3];
+  const double tot = (double)h0 + (double)h1 + (double)h2 + (double)h3;
+  const double wbar = tot > 0.0 ? ((double)h1 + 2.0 * (double)h2 + 3.0 * (double)h3) / tot : 0.0;
+  double s2 = exp2(wbar - delta2), s3 = exp2(wbar - delta3);
+  s2 = s2 < 0.25 ? 0.25 : (s2 > 1.0 ? 1.0 : s2);
+  s3 = s3 < 0.25 ? 0.25 : (s3 > 1.0 ? 1.0 : s3);
+  state->W = W;
+  state->H = H;
+  state->W2 = (int32_t)ceil(s2 * (double)W);
+  state->H2 = (int32_t)ceil(s2 * (double)H);
+  state->W3 = (int32_t)ceil(s3 * (double)W);
+  state->H3 = (int32_t)ceil(s3 * (double)H);
+  state->s2 = (float)s2;
+  state->s3 = (float)s3;
+  state->wbar = wbar;
+  state->hist[0] = h0;
+  state->hist[1] = h1;
+  state->hist[2] = h2;
+  state->hist[3] = h3;
+}
+
+}  // namespace star
+
+using namespace star;
+
+extern "C" star_nt_status star_nt_quadtree_ws_bytes(int32_t W, int32_t H, int32_t base_tile,
+                                                    size_t *bytes) {
+  if (!bytes || W <= 0 || H <= 0 || (base_tile != 16 && base_tile != 64)) return STAR_NT_ERR_ARG;
+  *bytes = qt_layout(W, H, base_tile).total;
+  return STAR_NT_OK;
+}
+
+extern "C" star_nt_status star_nt_quadtree(const uint32_t *rgba8, const int32_t *id1, int32_t W,
+                                           int32_t H, const star_nt_params *params,
+                                           const uint32_t *mask_prev, uint32_t *mask_out,
+                                           star_nt_pass_state *state, void *ws, size_t ws_bytes,
+                                           void *stream) {
+  if (!rgba8 || !id1 || !params || !mask_prev || !mask_out || !state || !ws || mask_prev == mask_out)
+    return STAR_NT_ERR_ARG;
+  const int B = params->base_tile;
+  size_t need = 0;
+  if (star_nt_quadtree_ws_bytes(W, H, B, &need) != STAR_NT_OK || ws_bytes < need ||
+      ((uintptr_t)ws & 255u))
+    return STAR_NT_ERR_ARG;
+  if (params->relax_iters < 0 || params->relax_iters > 8 || !(params->tau_merge < params->tau_split))
+    return STAR_NT_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const QtLayout L = qt_layout(W, H, B);
+  char *m = (char *)ws;
+  uint32_t *hist = (uint32_t *)(m + L.hist);
+  uint32_t *ma = (uint32_t *)(m + L.mask_a), *mb = (uint32_t *)(m + L.mask_b);
+  const int nt = L.tiles_x * L.tiles_y;
+  const int wblocks = (nt + 7) / 8;
+  const int iters = params->relax_iters;
+  cudaMemsetAsync(hist, 0, 16, st);
+  uint32_t *dst = iters == 0 ? mask_out : ma;
+  k_qt_decide<<<wblocks, 256, 0, st>>>(rgba8, W, H, B, L.tiles_x, nt, 6.0 * params->tau_split,
+                                       6.0 * params->tau_merge, mask_prev, dst);
+  const uint32_t *src = dst;
+  for (int it = 0; it < iters; ++it) {
+    uint32_t *d = it == iters - 1 ? mask_out : (src == ma ? mb : ma);
+    k_qt_relax<<<wblocks, 256, 0, st>>>(L.tiles_x, L.tiles_y, src, d);
+    src = d;
+  }
+  k_qt_hist<<<nt, 256, 0, st>>>(id1, W, H, B, L.tiles_x, mask_out, hist);
+  k_qt_finalize<<<1, 32, 0, st>>>(hist, W, H, params->delta2, params->delta3, state);
+  return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
+}

@@ -1,0 +1,379 @@
+// raster.cu -- star_nt_raster: triangle set-up, tile binning and the optional
+// materialised fragment lists of one geometry pass (Sec. 3, Fig. 1).
+#include <math.h>
+
+#include "common.cuh"
+#include "raster_tile.cuh"
+
+namespace star {
+
+// ---------------------------------------------------------------------------
+// Triangle set-up: one thread per triangle.  Transform with float32 and one
+// rounding per operation (order fixed), drop triangles with a vertex behind
+// the camera, outside NDC z in [0, 1] or outside the guard band, snap to
+// 1/256 pixel, order the vertices for a positive area, then store the biased
+// edge functions, depth plane, pixel bounding box and colour sums.
+__global__ void k_setup(const float *__restrict__ verts, const uint32_t *__restrict__ rgba8,
+                        int n_tris, const float *__restrict__ vp, const int32_t *__restrict__ size,
+                        BinsView bv, int32_t *status) {
+  // a device-side size beyond the workspace empties the pass instead of
+  // writing out of bounds
+  const bool size_ok = size[0] > 0 && size[1] > 0 && size[0] <= bv.max_w && size[1] <= bv.max_h;
+  const int W = size_ok ? size[0] : 0, H = size_ok ? size[1] : 0;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t == 0) {
+    BinsHeader *hd = bv.hd;
+    hd->size[0] = W;
+    hd->size[1] = H;
+    hd->tiles_x = (W + kTile - 1) / kTile;
+    hd->tiles_y = (H + kTile - 1) / kTile;
+    hd->n_tiles = hd->tiles_x * hd->tiles_y;
+    hd->n_pixels = W * H;
+    hd->n_tris = n_tris;
+    if (!size_ok) raise_status(status, STAR_NT_ERR_ARG);
+  }
+  if (t >= n_tris) return;
+  float m[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) m[i] = __ldg(vp + i);
+  const float4 *V = reinterpret_cast<const float4 *>(verts) + 3 * (size_t)t;
+  float sx[3], sy[3], zn[3];
+  bool ok = size_ok;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float4 p = __ldg(V + k);
+    float c[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float acc = __fmul_rn(m[4 * i + 0], p.x);
+      acc = __fadd_rn(acc, __fmul_rn(m[4 * i + 1], p.y));
+      acc = __fadd_rn(acc, __fmul_rn(m[4 * i + 2], p.z));
+      acc = __fadd_rn(acc, __fmul_rn(m[4 * i + 3], p.w));
+      c[i] = acc;
+    }
+    if (!(c[3] > 0.0f)) ok = false;
+    const float nx = __fdiv_rn(c[0], c[3]), ny = __fdiv_rn(c[1], c[3]), nz = __fdiv_rn(c[2], c[3]);
+    if (!(nz >= 0.0f && nz <= 1.0f)) ok = false;
+    sx[k] = __fmul_rn(__fadd_rn(__fmul_rn(nx, 0.5f), 0.5f), (float)W);
+    sy[k] = __fmul_rn(__fsub_rn(0.5f, __fmul_rn(ny, 0.5f)), (float)H);
+    if (!(fabsf(sx[k]) <= kGuard && fabsf(sy[k]) <= kGuard)) ok = false;
+    zn[k] = __fadd_rn(nz, 0.0f);
+  }
+  TriSetup S;
+  S.xa = 1;
+  S.xb = 0;
+  S.ya = 1;
+  S.yb = 0;
+  long long X[3] = {0, 0, 0}, Y[3] = {0, 0, 0}, area = 0;
+  if (ok) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      X[k] = __float2ll_rn(__fmul_rn(sx[k], (float)kSub));
+      Y[k] = __float2ll_rn(__fmul_rn(sy[k], (float)kSub));
+    }
+    area = (X[1] - X[0]) * (Y[2] - Y[0]) - (Y[1] - Y[0]) * (X[2] - X[0]);
+    if (area == 0) ok = false;
+  }
+  if (ok) {
+    if (area < 0) {  // no culling: swap v1 and v2 for a positive area
+      long long tx = X[1], ty = Y[1];
+      X[1] = X[2]; Y[1] = Y[2]; X[2] = tx; Y[2] = ty;
+      float tz = zn[1]; zn[1] = zn[2]; zn[2] = tz;
+      area = -area;
+    }
+    uint32_t own = 0;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      const int a = e, b = (e + 1) % 3;
+      const long long dx = X[b] - X[a], dy = Y[b] - Y[a];
+      const uint32_t o = (dy > 0 || (dy == 0 && dx < 0)) ? 1u : 0u;
+      own |= o << e;
+      S.dx[e] = (int32_t)dx;
+      S.dy[e] = (int32_t)dy;
+      S.c[e] = dy * X[a] - dx * Y[a] + (long long)o - 1;
+    }
+    S.own = own;
+    S.z0 = zn[0];
+    S.dz1 = __fsub_rn(zn[1], zn[0]);
+    S.dz2 = __fsub_rn(zn[2], zn[0]);
+    S.r = __frcp_rn(__ll2float_rn(area));
+    long long minx = min(X[0], min(X[1], X[2])), maxx = max(X[0], max(X[1], X[2]));
+    long long miny = min(Y[0], min(Y[1], Y[2])), maxy = max(Y[0], max(Y[1], Y[2]));
+    long long xa = -floor_div_ll(-(minx - kSub / 2), kSub), xb = floor_div_ll(maxx - kSub / 2, kSub);
+    long long ya = -floor_div_ll(-(miny - kSub / 2), kSub), yb = floor_div_ll(maxy - kSub / 2, kSub);
+    xa = max(xa, 0LL); ya = max(ya, 0LL);
+    xb = min(xb, (long long)W - 1); yb = min(yb, (long long)H - 1);
+    if (xa <= xb && ya <= yb) {
+      S.xa = (int16_t)xa; S.xb = (int16_t)xb; S.ya = (int16_t)ya; S.yb = (int16_t)yb;
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < 3; ++e) { S.dx[e] = 0; S.dy[e] = 0; S.c[e] = -1; }
+    S.own = 0; S.z0 = S.dz1 = S.dz2 = S.r = 0.0f;
+  }
+  const uint32_t col = __ldg(rgba8 + t);
+  const unsigned long long a8 = col >> 24, r8 = col & 255u, g8 = (col >> 8) & 255u,
+                           b8 = (col >> 16) & 255u;
+  S.opq = a8 == 255 ? 1u : 0u;
+  S.rg = (a8 * r8) | ((a8 * g8) << 32);
+  S.ba = (a8 * b8) | (a8 << 32);
+  S.lg = a8 == 255 ? 0ull
+                   : __double2ull_rn((log2(255.0) - log2((double)(255 - a8))) * 4294967296.0);
+  bv.setups[t] = S;
+}
+
+// Bin triangles to tiles: one warp per triangle, lanes stride over the
+// tiles of its bounding box.  A tile is kept unless one edge function is
+// negative at every pixel centre of the tile (its maximum over the tile's
+// corner centres is negative), which never drops a covered pixel.
+// fill == 0 counts pairs per tile; fill == 1 writes them.
+__global__ void k_bin(BinsView bv, int n_tris, int fill, int32_t *status) {
+  const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (warp >= n_tris) return;
+  const BinsHeader *hd = bv.hd;
+  if (fill && (int64_t)hd->n_pairs > bv.pair_capacity) {
+    if (warp == 0 && lane == 0) raise_status(status, STAR_NT_ERR_CAPACITY);
+    return;
+  }
+  const TriSetup &T = bv.setups[warp];
+  const int xa = T.xa, xb = T.xb, ya = T.ya, yb = T.yb;
+  if (xa > xb || ya > yb) return;
+  const int tiles_x = hd->tiles_x;
+  const int tx0 = xa / kTile, tx1 = xb / kTile, ty0 = ya / kTile, ty1 = yb / kTile;
+  const int ntx = tx1 - tx0 + 1, nt = ntx * (ty1 - ty0 + 1);
+  int dx[3], dy[3];
+  long long c[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) { dx[e] = T.dx[e]; dy[e] = T.dy[e]; c[e] = T.c[e]; }
+  for (int k = lane; k < nt; k += 32) {
+    const int tx = tx0 + k % ntx, ty = ty0 + k / ntx;
+    const int xlo = max(tx * kTile, xa), xhi = min(tx * kTile + kTile - 1, xb);
+    const int ylo = max(ty * kTile, ya), yhi = min(ty * kTile + kTile - 1, yb);
+    const int Pxlo = xlo * kSub + kSub / 2, Pxhi = xhi * kSub + kSub / 2;
+    const int Pylo = ylo * kSub + kSub / 2, Pyhi = yhi * kSub + kSub / 2;
+    bool hit = true;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      const long long mx = c[e] + (long long)dx[e] * (dx[e] > 0 ? Pyhi : Pylo) -
+                           (long long)dy[e] * (dy[e] > 0 ? Pxlo : Pxhi);
+      if (mx < 0) hit = false;
+    }
+    if (!hit) continue;
+    const int tile = ty * tiles_x + tx;
+    if (!fill) {
+      atomicAdd(bv.tile_count + tile, 1u);
+    } else {
+      const uint32_t pos = bv.tile_offset[tile] + atomicAdd(bv.tile_cursor + tile, 1u);
+      bv.pairs[pos] = (uint32_t)warp;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan (three launches).  Block b of the first and last launches
+// covers items [8192 b, 8192 (b + 1)); 1024 threads x 8 items.
+constexpr int kScanThreads = 1024, kScanItems = 8, kScanBlock = kScanThreads * kScanItems;
+
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *s_warp, uint32_t *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = s_warp[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    s_warp[lane] = w;
+  }
+  __syncthreads();
+  const uint32_t before = warp ? s_warp[warp - 1] : 0u;
+  if (total) *total = s_warp[31];
+  return before + x - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t *__restrict__ in,
+                                                              const int32_t *n_dev, uint32_t *tmp) {
+  __shared__ uint32_t s_warp[32];
+  const int n = *n_dev;
+  const size_t b0 = (size_t)blockIdx.x * kScanBlock;
+  if (b0 >= (size_t)n) return;
+  uint32_t s = 0;
+  const size_t i0 = b0 + (size_t)threadIdx.x * kScanItems;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k)
+    if (i0 + k < (size_t)n) s += in[i0 + k];
+  uint32_t tot;
+  block_excl_scan(s, s_warp, &tot);
+  if (threadIdx.x == 0) tmp[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_blocks(uint32_t *tmp, const int32_t *n_dev,
+                                                              uint32_t *out, uint32_t *total) {
+  __shared__ uint32_t s_warp[32];
+  const int n = *n_dev;
+  const int nb = (n + kScanBlock - 1) / kScanBlock;
+  uint32_t v[kScanItems], s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const int i = threadIdx.x * kScanItems + k;
+    v[k] = i < nb ? tmp[i] : 0u;
+    s += v[k];
+  }
+  uint32_t tot;
+  uint32_t run = block_excl_scan(s, s_warp, &tot);
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    const int i = threadIdx.x * kScanItems + k;
+    if (i < nb) tmp[i] = run;
+    run += v[k];
+  }
+  if (threadIdx.x == 0) {
+    out[n] = tot;
+    if (total) *total = tot;
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_final(const uint32_t *__restrict__ in,
+                                                             uint32_t *__restrict__ out,
+                                                             const int32_t *n_dev,
+                                                             const uint32_t *tmp) {
+  __shared__ uint32_t s_warp[32];
+  const int n = *n_dev;
+  const size_t b0 = (size_t)blockIdx.x * kScanBlock;
+  if (b0 >= (size_t)n) return;
+  const size_t i0 = b0 + (size_t)threadIdx.x * kScanItems;
+  uint32_t v[kScanItems], s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    v[k] = i0 + k < (size_t)n ? in[i0 + k] : 0u;
+    s += v[k];
+  }
+  uint32_t run = block_excl_scan(s, s_warp, nullptr) + tmp[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    if (i0 + k < (size_t)n) out[i0 + k] = run;
+    run += v[k];
+  }
+}
+
+cudaError_t scan_exclusive_u32(const uint32_t *in, uint32_t *out, const int32_t *n_dev, int32_t n_max,
+                               uint32_t *tmp, uint32_t *total, cudaStream_t st) {
+  const int nb = (n_max + kScanBlock - 1) / kScanBlock;
+  if (nb > kScanBlock) return cudaErrorInvalidValue;
+  const int g = nb > 0 ? nb : 1;
+  k_scan_reduce<<<g, kScanThreads, 0, st>>>(in, n_dev, tmp);
+  k_scan_blocks<<<1, kScanThreads, 0, st>>>(tmp, n_dev, out, total);
+  k_scan_final<<<g, kScanThreads, 0, st>>>(in, out, n_dev, tmp);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Materialised fragments: per-pixel counts, then the lists themselves.
+__global__ void __launch_bounds__(256) k_frag_count(BinsView bv, uint32_t *count) {
+  __shared__ TriSetup s_tri[kChunk];
+  __shared__ uint32_t s_id[kChunk];
+  const BinsHeader *hd = bv.hd;
+  if ((int64_t)hd->n_pairs > bv.pair_capacity) return;
+  const int tile = blockIdx.x;
+  if (tile >= hd->n_tiles) return;
+  const int W = hd->size[0], H = hd->size[1];
+  const TilePixel tp = tile_pixel(tile, hd->tiles_x);
+  uint32_t n = 0;
+  for_each_fragment(bv, tile, tp, s_tri, s_id, [&](const TriSetup &, uint32_t, float) { ++n; });
+  if (tp.px < W && tp.py < H) count[tp.py * W + tp.px] = n;
+}
+
+__global__ void __launch_bounds__(256) k_frag_fill(BinsView bv, const uint32_t *offset,
+                                                   const uint32_t *total, int64_t capacity,
+                                                   float *zs, int32_t *prims, int32_t *status) {
+  __shared__ TriSetup s_tri[kChunk];
+  __shared__ uint32_t s_id[kChunk];
+  const BinsHeader *hd = bv.hd;
+  if ((int64_t)hd->n_pairs > bv.pair_capacity) return;
+  if ((int64_t)*total > capacity) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) raise_status(status, STAR_NT_ERR_CAPACITY);
+    return;
+  }
+  const int tile = blockIdx.x;
+  if (tile >= hd->n_tiles) return;
+  const int W = hd->size[0], H = hd->size[1];
+  const TilePixel tp = tile_pixel(tile, hd->tiles_x);
+  const bool inside = tp.px < W && tp.py < H;
+  uint32_t pos = inside ? offset[tp.py * W + tp.px] : 0u;
+  for_each_fragment(bv, tile, tp, s_tri, s_id, [&](const TriSetup &, uint32_t id, float z) {
+    if (inside) {
+      zs[pos] = z;
+      prims[pos] = (int32_t)id;
+      ++pos;
+    }
+  });
+}
+
+}  // namespace star
+
+using namespace star;
+
+extern "C" star_nt_status star_nt_bins_bytes(int32_t max_w, int32_t max_h, int32_t max_tris,
+                                             int64_t pair_capacity, size_t *bytes) {
+  if (!bytes || max_w <= 0 || max_h <= 0 || max_tris < 0 || pair_capacity < 0 ||
+      max_w > 16384 || max_h > 16384 || pair_capacity > 0xffffffffLL)
+    return STAR_NT_ERR_ARG;
+  *bytes = bins_layout(max_w, max_h, max_tris, pair_capacity).total;
+  return STAR_NT_OK;
+}
+
+extern "C" star_nt_status star_nt_raster(const star_nt_scene *scene, const star_nt_target *target,
+                                         const star_nt_bins *bins, const star_nt_frags *frags,
+                                         int32_t *d_status, void *stream) {
+  if (!scene || !target || !bins || !bins->mem || !target->view_proj || !target->size)
+    return STAR_NT_ERR_ARG;
+  if (scene->n_tris < 0 || scene->n_tris > bins->max_tris ||
+      (scene->n_tris > 0 && (!scene->verts || !scene->rgba8)))
+    return STAR_NT_ERR_ARG;
+  if (target->max_w <= 0 || target->max_h <= 0 || target->max_w > bins->max_w ||
+      target->max_h > bins->max_h)
+    return STAR_NT_ERR_ARG;
+  size_t need = 0;
+  if (star_nt_bins_bytes(bins->max_w, bins->max_h, bins->max_tris, bins->pair_capacity, &need) !=
+          STAR_NT_OK ||
+      bins->bytes < need || ((uintptr_t)bins->mem & 255u))
+    return STAR_NT_ERR_ARG;
+  if (((uintptr_t)scene->verts & 15u))
+    return STAR_NT_ERR_ARG;
+  if (frags && (!frags->count || !frags->offset || !frags->total ||
+                (frags->capacity > 0 && (!frags->z || !frags->prim)) || frags->capacity < 0))
+    return STAR_NT_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  BinsView bv = bins_view(*bins);
+  const int T = scene->n_tris;
+  cudaMemsetAsync(bv.tile_count, 0, 4 * (size_t)(bv.max_tiles + 1), st);
+  cudaMemsetAsync(bv.tile_cursor, 0, 4 * (size_t)bv.max_tiles, st);
+  k_setup<<<(T + 255) / 256 > 0 ? (T + 255) / 256 : 1, 256, 0, st>>>(
+      scene->verts, scene->rgba8, T, target->view_proj, target->size, bv, d_status);
+  const int bin_blocks = T > 0 ? (T + 7) / 8 : 1;  // 8 warps per block
+  k_bin<<<bin_blocks, 256, 0, st>>>(bv, T, 0, d_status);
+  if (scan_exclusive_u32(bv.tile_count, bv.tile_offset, &bv.hd->n_tiles, bv.max_tiles,
+                         bv.scan_tmp, &bv.hd->n_pairs, st) != cudaSuccess)
+    return STAR_NT_ERR_CUDA;
+  k_bin<<<bin_blocks, 256, 0, st>>>(bv, T, 1, d_status);
+  if (frags) {
+    const int P = target->max_w * target->max_h;
+    const int tiles = ((target->max_w + kTile - 1) / kTile) * ((target->max_h + kTile - 1) / kTile);
+    k_frag_count<<<tiles, 256, 0, st>>>(bv, frags->count);
+    if (scan_exclusive_u32(frags->count, frags->offset, &bv.hd->n_pixels, P, bv.scan_tmp,
+                           frags->total, st) != cudaSuccess)
+      return STAR_NT_ERR_CUDA;
+    k_frag_fill<<<tiles, 256, 0, st>>>(bv, frags->offset, frags->total, frags->capacity, frags->z,
+                                       frags->prim, d_status);
+  }
+  return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
+}

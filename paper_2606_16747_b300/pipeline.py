@@ -1,0 +1,167 @@
+"""Frame driver of the STAR-NT hot path on one GPU.
+
+Owns the device buffers (torch allocations) and sequences the C-ABI calls:
+
+  plain frame     raster (full res) -> fused build_inputs -> infer -> composite
+  STAR-NT frame   raster x3 (full, s2, s3) -> build_inputs (3 passes + upscale)
+                  -> infer -> composite -> quadtree (next frame's s2, s3)
+  interpolated    reproject from the last real frame (Sec. 3.3, last paragraph)
+
+Pass resolutions live on the device (``state``), so one captured CUDA graph
+per frame kind replays any resolution.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+
+from . import star_nt as sn
+
+STATE_W2, STATE_W3 = 8, 16   # byte offsets of {W2, H2} and {W3, H3} in star_nt_pass_state
+
+
+def _i32(vals, device):
+    return torch.tensor(vals, dtype=torch.int32, device=device)
+
+
+class Renderer:
+    def __init__(self, verts, rgba8, W, H, params=None, x_dtype=sn.F32, mlp=None,
+                 pair_capacity=None, device="cuda", base_tile=None, keep_layers=False):
+        self.device = device
+        self.W, self.H = int(W), int(H)
+        self.P = self.W * self.H
+        self.verts = torch.as_tensor(np.ascontiguousarray(verts, np.float32)).to(device)
+        self.rgba8 = torch.as_tensor(np.ascontiguousarray(rgba8, np.uint32).view(np.int32)).to(device)
+        self.T = int(self.rgba8.shape[0])
+        self.scene = sn.scene_struct(self.verts, self.rgba8)
+        self.params = params if params is not None else sn.default_params()
+        if base_tile is not None:
+            self.params.base_tile = base_tile
+        self.x_dtype = x_dtype
+        cap = pair_capacity if pair_capacity is not None else max(1 << 20, 96 * self.T)
+        self.bins = [sn.BinsBuffer(self.W, self.H, self.T, cap, device) for _ in range(3)]
+        P = self.P
+        f32 = dict(dtype=torch.float32, device=device)
+        i32 = dict(dtype=torch.int32, device=device)
+        self.status = torch.zeros(1, **i32)
+        self.vp = torch.zeros(16, **f32)
+        self.full_size = _i32([self.W, self.H], device)
+        # per-pass planes (sized for full resolution)
+        self.l1 = dict(id1=torch.empty(P, **i32), z1=torch.empty(P, **f32))
+        self.l2 = dict(id2=torch.empty(P, **i32))
+        self.l3 = dict(n=torch.empty(P, **i32), tail=torch.empty(P * 4, **i32),
+                       t_tail=torch.empty(P, **f32))
+        xw = 8 if x_dtype == sn.F32 else 16
+        xdt = torch.float32 if x_dtype == sn.F32 else torch.bfloat16
+        self.x = torch.empty(P * xw, dtype=xdt, device=device)
+        self.front = torch.empty(P * 4, **f32)
+        self.f = torch.empty(P * 4, **f32)
+        self.rgba32f = torch.empty(P * 4, **f32)
+        self.rgba8_out = torch.empty(P, **i32)
+        # quadtree state: pass sizes live in ``state`` on the device
+        self.state = torch.zeros(64, dtype=torch.uint8, device=device)
+        self.state.view(torch.int32)[:6] = torch.tensor([self.W, self.H] * 3, dtype=torch.int32)
+        B = self.params.base_tile
+        self.n_tiles = math.ceil(self.W / B) * math.ceil(self.H / B)
+        self.mask = [torch.zeros(self.n_tiles, **i32), torch.zeros(self.n_tiles, **i32)]
+        self.mask_cur = 0
+        self.qt_ws = torch.zeros(sn.quadtree_ws_bytes(self.W, self.H, B), dtype=torch.uint8, device=device)
+        self.mlp_tensors = None
+        if mlp is not None:
+            self.set_mlp(mlp)
+        # reprojection
+        self.prev_rgba = torch.zeros(P * 4, **f32)
+        self.prev_z1 = torch.ones(P, **f32)
+        self.interp_out = torch.zeros(P * 4, **f32)
+        self.vp64_prev = torch.zeros(16, dtype=torch.float64, device=device)
+        self.vp64_cur = torch.zeros(16, dtype=torch.float64, device=device)
+
+    # -- inputs -------------------------------------------------------------
+    def set_mlp(self, w: dict):
+        self.mlp_tensors = {k: torch.as_tensor(np.ascontiguousarray(v, np.float32)).to(self.device)
+                            for k, v in w.items()}
+        self.mlp = sn.mlp_struct(self.mlp_tensors)
+
+    def set_camera(self, vp32):
+        self.vp.copy_(torch.as_tensor(np.asarray(vp32, np.float32).reshape(16)))
+
+    def state_size(self, which):
+        off = {1: None, 2: STATE_W2, 3: STATE_W3}[which]
+        if off is None:
+            return self.full_size
+        return self.state[off:off + 8].view(torch.int32)
+
+    # -- frames -------------------------------------------------------------
+    def plain_frame(self, stream=None, mark=None):
+        """All passes at full resolution, fused (the plain neural OIT pipeline)."""
+        mark = mark or (lambda name: None)
+        b = self.bins[0]
+        sn.raster(self.scene, self.vp, self.full_size, self.W, self.H, b, None, self.status, stream)
+        mark("raster")
+        sn.build_inputs(self.scene, b, b, b, self.l1, None, None, self.W, self.H, self.params,
+                        self.x, self.x_dtype, self.front, self.status, stream)
+        mark("pass_fused")
+        sn.infer(self.mlp, self.x_dtype, self.x, self.f, self.P, self.status, stream)
+        mark("infer")
+        sn.composite(self.front, self.f, self.P, self.rgba32f, self.rgba8_out, stream)
+        mark("composite")
+
+    def star_frame(self, stream=None, update_tiles=True, mark=None):
+        """Pass 1 at full resolution, passes 2 and 3 at the device-held scales.
+        ``mark(name)`` (optional) is called after each stage is enqueued."""
+        mark = mark or (lambda name: None)
+        b1, b2, b3 = self.bins
+        sn.raster(self.scene, self.vp, self.full_size, self.W, self.H, b1, None, self.status, stream)
+        sn.raster(self.scene, self.vp, self.state_size(2), self.W, self.H, b2, None, self.status, stream)
+        sn.raster(self.scene, self.vp, self.state_size(3), self.W, self.H, b3, None, self.status, stream)
+        mark("raster")
+        sn.geometry_pass(self.scene, b1, 1, self.l1, self.status, stream)
+        mark("pass1")
+        sn.geometry_pass(self.scene, b2, 2, self.l2, self.status, stream)
+        mark("pass2")
+        sn.geometry_pass(self.scene, b3, 3, self.l3, self.status, stream)
+        mark("pass3")
+        sn.upscale_features(self.scene, b2, b3, self.l1, self.l2, self.l3, self.W, self.H,
+                            self.params, self.x, self.x_dtype, self.front, stream)
+        mark("features")
+        sn.infer(self.mlp, self.x_dtype, self.x, self.f, self.P, self.status, stream)
+        mark("infer")
+        sn.composite(self.front, self.f, self.P, self.rgba32f, self.rgba8_out, stream)
+        mark("composite")
+        if update_tiles:
+            self.update_tiles(stream)
+            mark("quadtree")
+
+    def update_tiles(self, stream=None):
+        src, dst = self.mask[self.mask_cur], self.mask[1 - self.mask_cur]
+        sn.quadtree(self.rgba8_out, self.l1["id1"], self.W, self.H, self.params, src, dst,
+                    self.state, self.qt_ws, stream)
+        self.mask_cur = 1 - self.mask_cur
+
+    def _infer_composite(self, stream):
+        if self.mlp_tensors is None:
+            raise RuntimeError("no MLP weights: call set_mlp first")
+        sn.infer(self.mlp, self.x_dtype, self.x, self.f, self.P, self.status, stream)
+        sn.composite(self.front, self.f, self.P, self.rgba32f, self.rgba8_out, stream)
+
+    def keep_as_previous(self, vp64):
+        """Remember this real frame for later interpolated frames."""
+        self.prev_rgba.copy_(self.rgba32f)
+        self.prev_z1.copy_(self.l1["z1"])
+        self.vp64_prev.copy_(torch.as_tensor(np.asarray(vp64, np.float64).reshape(16)))
+
+    def interp_frame(self, vp64_cur=None, stream=None):
+        if vp64_cur is not None:
+            self.vp64_cur.copy_(torch.as_tensor(np.asarray(vp64_cur, np.float64).reshape(16)))
+        sn.reproject(self.prev_rgba, self.prev_z1, self.vp64_prev, self.vp64_cur, self.W, self.H,
+                     self.interp_out, stream)
+
+    def pass_state(self):
+        return sn.read_pass_state(self.state)
+
+    def check_status(self):
+        s = int(self.status.item())
+        if s != sn.OK:
+            raise sn.StarNTError("device", s)

@@ -1,0 +1,256 @@
+"""ctypes binding of libstar_nt.so (the C ABI in include/star_nt.h).
+
+Argument marshalling only: every step of the frame runs in the library's
+CUDA kernels.  Tensors are torch CUDA tensors; their device pointers are
+passed as plain addresses together with the current CUDA stream.  There is
+no fallback: if the library is missing or a call fails, an exception is
+raised.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libstar_nt.so")
+
+OK, ERR_ARG, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = range(6)
+F32, BF16 = 0, 1
+
+# every entry point declared in include/star_nt.h
+EXPORTS = ("star_nt_version", "star_nt_status_string", "star_nt_default_params",
+           "star_nt_bins_bytes", "star_nt_raster", "star_nt_build_inputs", "star_nt_infer",
+           "star_nt_composite", "star_nt_quadtree_ws_bytes", "star_nt_quadtree",
+           "star_nt_reproject", "star_nt_geometry_pass", "star_nt_upscale_features")
+
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+
+
+class Scene(ctypes.Structure):
+    _fields_ = [("verts", _P), ("rgba8", _P), ("n_tris", _I32)]
+
+
+class Target(ctypes.Structure):
+    _fields_ = [("view_proj", _P), ("size", _P), ("max_w", _I32), ("max_h", _I32)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("bg", ctypes.c_float * 3), ("kappa_n", ctypes.c_float),
+                ("tau_split", ctypes.c_double), ("tau_merge", ctypes.c_double),
+                ("delta2", ctypes.c_double), ("delta3", ctypes.c_double),
+                ("base_tile", _I32), ("relax_iters", _I32)]
+
+
+class Bins(ctypes.Structure):
+    _fields_ = [("mem", _P), ("bytes", ctypes.c_size_t), ("max_w", _I32), ("max_h", _I32),
+                ("max_tris", _I32), ("pair_capacity", _I64)]
+
+
+class Frags(ctypes.Structure):
+    _fields_ = [("count", _P), ("offset", _P), ("z", _P), ("prim", _P), ("capacity", _I64),
+                ("total", _P)]
+
+
+class Layers(ctypes.Structure):
+    _fields_ = [("id1", _P), ("z1", _P), ("id2", _P), ("n", _P), ("tail", _P), ("t_tail", _P)]
+
+
+class Features(ctypes.Structure):
+    _fields_ = [("x", _P), ("x_dtype", _I32), ("front", _P)]
+
+
+class Mlp(ctypes.Structure):
+    _fields_ = [("w1", _P), ("b1", _P), ("w2", _P), ("b2", _P), ("w3", _P), ("b3", _P)]
+
+
+class PassState(ctypes.Structure):
+    _fields_ = [("W", _I32), ("H", _I32), ("W2", _I32), ("H2", _I32), ("W3", _I32), ("H3", _I32),
+                ("s2", ctypes.c_float), ("s3", ctypes.c_float), ("wbar", ctypes.c_double),
+                ("hist", ctypes.c_uint32 * 4)]
+
+
+PASS_STATE_BYTES = ctypes.sizeof(PassState)
+
+_lib = None
+
+
+class StarNTError(RuntimeError):
+    def __init__(self, call, status):
+        self.status = status
+        super().__init__(f"{call} failed: {status_string(status)} ({status})")
+
+
+def lib():
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() "
+                               "(or python paper_2606_16747_b300/build.py)")
+        L = ctypes.CDLL(LIB_PATH)
+        L.star_nt_version.restype = _I32
+        L.star_nt_status_string.restype = ctypes.c_char_p
+        L.star_nt_status_string.argtypes = [_I32]
+        L.star_nt_default_params.argtypes = [ctypes.POINTER(Params)]
+        L.star_nt_bins_bytes.argtypes = [_I32, _I32, _I32, _I64, ctypes.POINTER(ctypes.c_size_t)]
+        L.star_nt_raster.argtypes = [ctypes.POINTER(Scene), ctypes.POINTER(Target),
+                                     ctypes.POINTER(Bins), ctypes.POINTER(Frags), _P, _P]
+        L.star_nt_build_inputs.argtypes = [ctypes.POINTER(Scene)] + [ctypes.POINTER(Bins)] * 3 + \
+            [ctypes.POINTER(Layers)] * 3 + [_I32, _I32, ctypes.POINTER(Params),
+                                            ctypes.POINTER(Features), _P, _P]
+        L.star_nt_geometry_pass.argtypes = [ctypes.POINTER(Scene), ctypes.POINTER(Bins), _I32,
+                                            ctypes.POINTER(Layers), _P, _P]
+        L.star_nt_upscale_features.argtypes = [ctypes.POINTER(Scene)] + [ctypes.POINTER(Bins)] * 2 + \
+            [ctypes.POINTER(Layers)] * 3 + [_I32, _I32, ctypes.POINTER(Params),
+                                            ctypes.POINTER(Features), _P]
+        L.star_nt_infer.argtypes = [ctypes.POINTER(Mlp), _I32, _P, _P, _I64, _P, _P]
+        L.star_nt_composite.argtypes = [_P, _P, _I64, _P, _P, _P]
+        L.star_nt_quadtree_ws_bytes.argtypes = [_I32, _I32, _I32, ctypes.POINTER(ctypes.c_size_t)]
+        L.star_nt_quadtree.argtypes = [_P, _P, _I32, _I32, ctypes.POINTER(Params), _P, _P, _P, _P,
+                                       ctypes.c_size_t, _P]
+        L.star_nt_reproject.argtypes = [_P, _P, _P, _P, _I32, _I32, _P, _P]
+        for name in EXPORTS:
+            if name not in ("star_nt_default_params", "star_nt_status_string", "star_nt_version"):
+                getattr(L, name).restype = _I32
+        _lib = L
+    return _lib
+
+
+def status_string(s: int) -> str:
+    return lib().star_nt_status_string(int(s)).decode()
+
+
+def _check(call, s):
+    if s != OK:
+        raise StarNTError(call, s)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    lib().star_nt_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if k == "bg":
+            p.bg = (ctypes.c_float * 3)(*v)
+        else:
+            setattr(p, k, v)
+    return p
+
+
+class BinsBuffer:
+    """Device workspace of one pass's binned triangles."""
+
+    def __init__(self, max_w, max_h, max_tris, pair_capacity, device="cuda"):
+        n = ctypes.c_size_t()
+        _check("star_nt_bins_bytes", lib().star_nt_bins_bytes(max_w, max_h, max_tris, pair_capacity,
+                                                              ctypes.byref(n)))
+        self.mem = torch.empty(n.value, dtype=torch.uint8, device=device)
+        self.c = Bins(self.mem.data_ptr(), n.value, max_w, max_h, max_tris, pair_capacity)
+
+    def header(self):
+        """size[2], tiles_x, tiles_y, n_tiles, n_pixels, n_pairs, n_tris (device int32 view)."""
+        return self.mem[:32].view(torch.int32)
+
+
+def scene_struct(verts, rgba8) -> Scene:
+    return Scene(verts.data_ptr(), rgba8.data_ptr(), int(rgba8.shape[0]))
+
+
+def raster(scene: Scene, vp, size, max_w, max_h, bins: BinsBuffer, frags=None, status=None, stream=None):
+    tgt = Target(vp.data_ptr(), size.data_ptr(), max_w, max_h)
+    fr = None
+    if frags is not None:
+        fr = Frags(frags["count"].data_ptr(), frags["offset"].data_ptr(), frags["z"].data_ptr(),
+                   frags["prim"].data_ptr(), int(frags["z"].numel()), frags["total"].data_ptr())
+    _check("star_nt_raster", lib().star_nt_raster(ctypes.byref(scene), ctypes.byref(tgt),
+                                                  ctypes.byref(bins.c),
+                                                  ctypes.byref(fr) if fr is not None else None,
+                                                  _ptr(status), _stream(stream)))
+
+
+def layers_struct(d) -> Layers:
+    if d is None:
+        return None
+    g = lambda k: d[k].data_ptr() if d.get(k) is not None else None
+    return Layers(g("id1"), g("z1"), g("id2"), g("n"), g("tail"), g("t_tail"))
+
+
+def build_inputs(scene: Scene, bins1, bins2, bins3, layers1, layers2, layers3, W, H, params: Params,
+                 x, x_dtype, front, status=None, stream=None):
+    ls = [layers_struct(l) for l in (layers1, layers2, layers3)]
+    feat = Features(x.data_ptr(), x_dtype, front.data_ptr())
+    _check("star_nt_build_inputs", lib().star_nt_build_inputs(
+        ctypes.byref(scene), ctypes.byref(bins1.c), ctypes.byref(bins2.c), ctypes.byref(bins3.c),
+        *[ctypes.byref(l) if l is not None else None for l in ls], W, H, ctypes.byref(params),
+        ctypes.byref(feat), _ptr(status), _stream(stream)))
+
+
+def geometry_pass(scene: Scene, bins, mode, layers, status=None, stream=None):
+    l = layers_struct(layers)
+    _check("star_nt_geometry_pass", lib().star_nt_geometry_pass(ctypes.byref(scene), ctypes.byref(bins.c),
+                                                                mode, ctypes.byref(l), _ptr(status),
+                                                                _stream(stream)))
+
+
+def upscale_features(scene: Scene, bins2, bins3, layers1, layers2, layers3, W, H, params: Params,
+                     x, x_dtype, front, stream=None):
+    ls = [layers_struct(l) for l in (layers1, layers2, layers3)]
+    feat = Features(x.data_ptr(), x_dtype, front.data_ptr())
+    _check("star_nt_upscale_features", lib().star_nt_upscale_features(
+        ctypes.byref(scene), ctypes.byref(bins2.c), ctypes.byref(bins3.c),
+        *[ctypes.byref(l) for l in ls], W, H, ctypes.byref(params), ctypes.byref(feat),
+        _stream(stream)))
+
+
+def mlp_struct(w) -> Mlp:
+    return Mlp(*[w[k].data_ptr() for k in ("w1", "b1", "w2", "b2", "w3", "b3")])
+
+
+def infer(w: Mlp, x_dtype, x, f, P, status=None, stream=None):
+    _check("star_nt_infer", lib().star_nt_infer(ctypes.byref(w), x_dtype, _ptr(x), _ptr(f), int(P),
+                                                _ptr(status), _stream(stream)))
+
+
+def composite(front, f, P, rgba32f=None, rgba8=None, stream=None):
+    _check("star_nt_composite", lib().star_nt_composite(_ptr(front), _ptr(f), int(P), _ptr(rgba32f),
+                                                        _ptr(rgba8), _stream(stream)))
+
+
+def quadtree_ws_bytes(W, H, base):
+    n = ctypes.c_size_t()
+    _check("star_nt_quadtree_ws_bytes", lib().star_nt_quadtree_ws_bytes(W, H, base, ctypes.byref(n)))
+    return n.value
+
+
+def quadtree(rgba8, id1, W, H, params: Params, mask_prev, mask_out, state, ws, stream=None):
+    _check("star_nt_quadtree", lib().star_nt_quadtree(_ptr(rgba8), _ptr(id1), W, H, ctypes.byref(params),
+                                                      _ptr(mask_prev), _ptr(mask_out), _ptr(state),
+                                                      _ptr(ws), ws.numel(), _stream(stream)))
+
+
+def reproject(prev_rgba, prev_z1, vp_prev, vp_cur, W, H, out_rgba, stream=None):
+    _check("star_nt_reproject", lib().star_nt_reproject(_ptr(prev_rgba), _ptr(prev_z1), _ptr(vp_prev),
+                                                        _ptr(vp_cur), W, H, _ptr(out_rgba),
+                                                        _stream(stream)))
+
+
+def read_pass_state(state_tensor) -> dict:
+    """Decode a device star_nt_pass_state (uint8 tensor) on the host."""
+    raw = bytes(state_tensor.cpu().numpy().tobytes())
+    st = PassState.from_buffer_copy(raw[:PASS_STATE_BYTES])
+    return dict(W=st.W, H=st.H, W2=st.W2, H2=st.H2, W3=st.W3, H3=st.H3, s2=st.s2, s3=st.s3,
+                wbar=st.wbar, hist=list(st.hist))

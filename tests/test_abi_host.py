@@ -1,0 +1,81 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports
+every entry point declared in include/star_nt.h, and rejects bad arguments
+before enqueuing any work."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "star_nt.h")
+
+
+@pytest.fixture(scope="module")
+def sn():
+    from paper_2606_16747_b300 import build, star_nt
+    build.build()
+    return star_nt
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(star_nt_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_six_calls():
+    names = declared_functions()
+    for call in ("star_nt_raster", "star_nt_build_inputs", "star_nt_infer", "star_nt_quadtree",
+                 "star_nt_reproject", "star_nt_composite"):
+        assert call in names
+
+
+def test_library_exports_every_declared_symbol(sn):
+    L = sn.lib()
+    for name in declared_functions():
+        assert hasattr(L, name), name
+    assert set(sn.EXPORTS) <= set(declared_functions())
+
+
+def test_version_status_and_defaults(sn):
+    assert sn.lib().star_nt_version() == 1
+    assert sn.status_string(sn.ERR_CAPACITY) == "capacity exceeded"
+    p = sn.default_params()
+    assert list(p.bg) == [1.0, 1.0, 1.0] and p.kappa_n == pytest.approx(1 / 64)
+    assert (p.delta2, p.delta3, p.base_tile, p.relax_iters) == (2.2, 3.0, 16, 2)
+    assert p.tau_merge < p.tau_split
+
+
+def test_workspace_sizes(sn):
+    L = sn.lib()
+    n = ctypes.c_size_t()
+    assert L.star_nt_bins_bytes(1920, 1080, 20000, 1 << 20, ctypes.byref(n)) == sn.OK
+    a = n.value
+    assert L.star_nt_bins_bytes(1920, 1080, 20000, 2 << 20, ctypes.byref(n)) == sn.OK
+    assert n.value - a == 4 << 20
+    assert L.star_nt_bins_bytes(0, 1080, 10, 10, ctypes.byref(n)) == sn.ERR_ARG
+    assert L.star_nt_bins_bytes(100, 100, 10, 10, None) == sn.ERR_ARG
+    assert sn.quadtree_ws_bytes(1920, 1080, 16) >= 2 * 120 * 68 * 4
+    assert L.star_nt_quadtree_ws_bytes(1920, 1080, 32, ctypes.byref(n)) == sn.ERR_ARG
+
+
+def test_bad_arguments_rejected_before_launch(sn):
+    L = sn.lib()
+    # null / inconsistent structures: rejected on the host
+    assert L.star_nt_raster(None, None, None, None, None, None) == sn.ERR_ARG
+    sc = sn.Scene(16, 16, 5)
+    tgt = sn.Target(64, 64, 64, 64)
+    bins = sn.Bins(256, 10, 64, 64, 4, 100)        # too small a workspace, too few triangles
+    assert L.star_nt_raster(ctypes.byref(sc), ctypes.byref(tgt), ctypes.byref(bins), None, None, None) == sn.ERR_ARG
+    w = sn.Mlp(16, 16, 16, 16, 16, 16)
+    assert L.star_nt_infer(ctypes.byref(w), 7, 16, 16, 10, None, None) == sn.ERR_ARG     # bad dtype
+    assert L.star_nt_infer(ctypes.byref(w), sn.F32, 8, 16, 10, None, None) == sn.ERR_ARG  # misaligned
+    assert L.star_nt_infer(ctypes.byref(w), sn.BF16, 16, 16, 10, None, None) == sn.ERR_ARG  # not 256-aligned
+    assert L.star_nt_composite(16, 16, -1, 16, 16, None) == sn.ERR_ARG
+    assert L.star_nt_reproject(16, 16, 16, 16, 0, 10, 32, None) == sn.ERR_ARG
+    assert L.star_nt_reproject(16, 16, 16, 16, 10, 10, 16, None) == sn.ERR_ARG           # in place
+    p = sn.default_params()
+    assert L.star_nt_quadtree(16, 16, 64, 64, ctypes.byref(p), 16, 16, 16, 256, 1 << 20, None) == sn.ERR_ARG
+    p.tau_merge = 30.0
+    assert L.star_nt_quadtree(16, 16, 64, 64, ctypes.byref(p), 16, 32, 16, 256, 1 << 20, None) == sn.ERR_ARG
