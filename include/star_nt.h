@@ -48,7 +48,7 @@ typedef int32_t star_nt_status;
 
 /* element types of the network input */
 #define STAR_NT_F32 0  /* [P][8] float32: x0..x4, tail flag, 0, 0 */
-#define STAR_NT_BF16 1 /* [P][16] bfloat16: x0..x4, tail flag, zeros */
+#define STAR_NT_BF16 1 /* [P][8] bfloat16: x0..x4, tail flag, 0, 0 */
 
 /* Quadtree tiles: base tile side (pixels) and levels (Sec. 3.1). */
 #define STAR_NT_QT_LEVELS 4
@@ -169,7 +169,7 @@ typedef struct {
 
 /* Full-resolution network input and front terms. */
 typedef struct {
-    void *x;         /* [W*H][8] float32 or [W*H][16] bfloat16 (x_dtype) */
+    void *x;         /* [W*H][8] float32 or [W*H][8] bfloat16 (x_dtype) */
     int32_t x_dtype; /* STAR_NT_F32 or STAR_NT_BF16 */
     float *front;    /* [W*H][4] */
 } star_nt_features;
@@ -273,10 +273,14 @@ star_nt_status star_nt_quadtree(const uint32_t *rgba8, const int32_t *id1, int32
 /* sampled there bilinearly with clamp to edge.  A point behind the previous */
 /* camera keeps its own previous colour.                                    */
 /* prev_rgba, out_rgba: [W*H][4] float32 (distinct); prev_z1: [W*H];           */
-/* vp_prev, vp_cur: device, 16 float64 row-major view-projections.           */
+/* vp_prev, vp_cur: device, 16 float64 row-major view-projections; ws: device */
+/* scratch of STAR_NT_REPROJECT_WS_BYTES bytes (16-byte aligned) that holds  */
+/* VP_prev inv(VP_cur) - I for the call (two launches: that matrix in       */
+/* float64, then the per-pixel pass in float32 on offsets from the pixel).  */
+#define STAR_NT_REPROJECT_WS_BYTES 64
 star_nt_status star_nt_reproject(const float *prev_rgba, const float *prev_z1,
                                  const double *vp_prev, const double *vp_cur, int32_t W,
-                                 int32_t H, float *out_rgba, void *stream);
+                                 int32_t H, float *out_rgba, void *ws, void *stream);
 
 #ifdef __cplusplus
 }

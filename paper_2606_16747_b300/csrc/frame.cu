@@ -110,23 +110,30 @@ __device__ void inverse4(const double *a, double *inv) {
   inv[15] = (a[8] * s3 - a[9] * s1 + a[10] * s0) * id;
 }
 
-__global__ void __launch_bounds__(256) k_reproject(const float4 *__restrict__ prev,
-                                                   const float *__restrict__ z1,
-                                                   const double *__restrict__ vp_prev,
-                                                   const double *__restrict__ vp_cur, int W, int H,
-                                                   float4 *__restrict__ out) {
-  __shared__ float sE[16];
+// E = VP_prev inv(VP_cur) - I, once per call, in float64, rounded to float32.
+__global__ void k_reproject_matrix(const double *__restrict__ vp_prev, const double *__restrict__ vp_cur,
+                                   float *__restrict__ E) {
+  __shared__ double inv[16];
   if (threadIdx.x == 0) {
-    double a[16], inv[16];
+    double a[16];
     for (int i = 0; i < 16; ++i) a[i] = vp_cur[i];
     inverse4(a, inv);
-    for (int r = 0; r < 4; ++r)
-      for (int c = 0; c < 4; ++c) {
-        double m = 0.0;
-        for (int k = 0; k < 4; ++k) m += vp_prev[4 * r + k] * inv[4 * k + c];
-        sE[4 * r + c] = (float)(m - (r == c ? 1.0 : 0.0));
-      }
   }
+  __syncthreads();
+  if (threadIdx.x < 16) {
+    const int r = threadIdx.x >> 2, c = threadIdx.x & 3;
+    double m = 0.0;
+    for (int k = 0; k < 4; ++k) m += vp_prev[4 * r + k] * inv[4 * k + c];
+    E[threadIdx.x] = (float)(m - (r == c ? 1.0 : 0.0));
+  }
+}
+
+__global__ void __launch_bounds__(256) k_reproject(const float4 *__restrict__ prev,
+                                                   const float *__restrict__ z1,
+                                                   const float *__restrict__ Eg, int W, int H,
+                                                   float4 *__restrict__ out) {
+  __shared__ float sE[16];
+  if (threadIdx.x < 16) sE[threadIdx.x] = Eg[threadIdx.x];
   __syncthreads();
   const int x = blockIdx.x * 32 + (threadIdx.x & 31);
   const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
@@ -236,16 +243,18 @@ extern "C" star_nt_status star_nt_composite(const float *front, const float *f, 
 
 extern "C" star_nt_status star_nt_reproject(const float *prev_rgba, const float *prev_z1,
                                             const double *vp_prev, const double *vp_cur, int32_t W,
-                                            int32_t H, float *out_rgba, void *stream) {
-  if (W <= 0 || H <= 0 || !prev_rgba || !prev_z1 || !vp_prev || !vp_cur || !out_rgba ||
+                                            int32_t H, float *out_rgba, void *ws, void *stream) {
+  if (W <= 0 || H <= 0 || !prev_rgba || !prev_z1 || !vp_prev || !vp_cur || !out_rgba || !ws ||
       prev_rgba == out_rgba)
     return STAR_NT_ERR_ARG;
   if (((uintptr_t)prev_rgba & 15u) || ((uintptr_t)out_rgba & 15u) || ((uintptr_t)vp_prev & 7u) ||
-      ((uintptr_t)vp_cur & 7u))
+      ((uintptr_t)vp_cur & 7u) || ((uintptr_t)ws & 15u))
     return STAR_NT_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  float *E = reinterpret_cast<float *>(ws);
+  k_reproject_matrix<<<1, 32, 0, st>>>(vp_prev, vp_cur, E);
   dim3 grid((W + 31) / 32, (H + 7) / 8);
-  k_reproject<<<grid, 256, 0, (cudaStream_t)stream>>>(reinterpret_cast<const float4 *>(prev_rgba),
-                                                      prev_z1, vp_prev, vp_cur, W, H,
-                                                      reinterpret_cast<float4 *>(out_rgba));
+  k_reproject<<<grid, 256, 0, st>>>(reinterpret_cast<const float4 *>(prev_rgba), prev_z1, E, W, H,
+                                    reinterpret_cast<float4 *>(out_rgba));
   return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
 }

@@ -225,7 +225,8 @@ __global__ void __launch_bounds__(kMlpThreads, kMlpCtasPerSm)
   long long tile = blockIdx.x;
   uint32_t ph_tma[2] = {0u, 0u}, ph_mma = 0u;
   int buf = 0;
-  bool tma_pending = false;
+  bool tma_pending = false;          // a TMA load in flight (thread 0)
+  uint32_t pend_bar = 0, pend_ph = 0;
   const uint64_t dW1 = smem_desc(sbase + kSW1, 512, 128);
   const uint64_t dW2a = smem_desc(sbase + kSW2, 256, 128), dW2b = smem_desc(sbase + kSW2 + 512, 256, 128);
   const uint64_t dW3 = smem_desc(sbase + kSW3, 256, 128);
@@ -236,6 +237,8 @@ __global__ void __launch_bounds__(kMlpThreads, kMlpCtasPerSm)
     mbar_expect_tx(bar_tma0, 2048);
     tma_load_2d(sbase + kSX, &xmap, 0, (int)(tile * kRows), bar_tma0);
     tma_pending = true;
+    pend_bar = bar_tma0;
+    pend_ph = 0u;
   }
   while (tile < ntiles) {
     const long long next = tile + gridDim.x;
@@ -255,6 +258,8 @@ __global__ void __launch_bounds__(kMlpThreads, kMlpCtasPerSm)
           mbar_expect_tx(nb, 2048);
           tma_load_2d(sbase + kSX + (buf ^ 1) * 4096, &xmap, 0, (int)(next * kRows), nb);
           tma_pending = true;
+          pend_bar = nb;
+          pend_ph = ph_tma[buf ^ 1];
         }
       }
     }
@@ -339,7 +344,7 @@ __global__ void __launch_bounds__(kMlpThreads, kMlpCtasPerSm)
   }
   if (*s_abort && tid == 0) {
     raise_status(status, STAR_NT_ERR_TIMEOUT);
-    if (tma_pending) mbar_wait(buf ? bar_tma0 : bar_tma1, ph_tma[buf ^ 1]);
+    if (tma_pending) mbar_wait(pend_bar, pend_ph);  // let the copy land before exiting
   }
   fence_before();
   __syncthreads();

@@ -85,9 +85,7 @@ __device__ __forceinline__ void write_features(const FeatOut &fo, size_t p, floa
     v.y = *reinterpret_cast<uint32_t *>(&h1);
     v.z = *reinterpret_cast<uint32_t *>(&h2);
     v.w = 0u;
-    uint4 *X = reinterpret_cast<uint4 *>(fo.x) + 2 * p;
-    X[0] = v;
-    X[1] = make_uint4(0u, 0u, 0u, 0u);
+    reinterpret_cast<uint4 *>(fo.x)[p] = v;
   }
 }
 

@@ -56,8 +56,10 @@ __device__ __forceinline__ int cell_level(uint32_t m, int cx, int cy) {
   return 3;
 }
 
-// sum of the six pairwise RGB distances of the node's corner pixels
-__device__ double corner_dsum(const uint32_t *__restrict__ img, int W, int H, int x0, int y0, int S) {
+// Corner colours of a node (clamped to the image) and the six integer
+// squared distances in the fixed pair order 01, 02, 03, 12, 13, 23.
+__device__ __forceinline__ void corner_q(const uint32_t *__restrict__ img, int W, int H, int x0, int y0,
+                                         int S, int (&q)[6]) {
   const int xs[4] = {x0, x0 + S - 1, x0, x0 + S - 1};
   const int ys[4] = {y0, y0, y0 + S - 1, y0 + S - 1};
   int c[4][3];
@@ -70,17 +72,32 @@ __device__ double corner_dsum(const uint32_t *__restrict__ img, int W, int H, in
     c[k][2] = (v >> 16) & 255u;
   }
   const int pa[6] = {0, 0, 0, 1, 1, 2}, pb[6] = {1, 2, 3, 2, 3, 3};
-  double s = 0.0;
 #pragma unroll
   for (int e = 0; e < 6; ++e) {
-    int q = 0;
+    int s = 0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       const int d = c[pa[e]][k] - c[pb[e]][k];
-      q += d * d;
+      s += d * d;
     }
-    s = __dadd_rn(s, __dsqrt_rn((double)q));
+    q[e] = s;
   }
+}
+
+// The decision quantity: sum of the six distances, as a float64 sum of
+// correctly rounded square roots in the fixed order.  A float32 estimate
+// (error below 1e-3 for 8-bit colours) decides whenever it is farther than
+// 2e-3 from both thresholds; otherwise the float64 sum decides, so every
+// decision equals the float64 one.
+__device__ __forceinline__ double decision_dsum(const int (&q)[6], double split6, double merge6) {
+  float f = 0.0f;
+#pragma unroll
+  for (int e = 0; e < 6; ++e) f = __fadd_rn(f, __fsqrt_rn((float)q[e]));
+  const double fd = (double)f;
+  if (fabs(fd - split6) > 2e-3 && fabs(fd - merge6) > 2e-3) return fd;
+  double s = 0.0;
+#pragma unroll
+  for (int e = 0; e < 6; ++e) s = __dadd_rn(s, __dsqrt_rn((double)q[e]));
   return s;
 }
 
@@ -103,7 +120,9 @@ __global__ void __launch_bounds__(256) k_qt_decide(const uint32_t *__restrict__ 
     leaf = ex && !split_node;
     if (ex) {
       const int S = B >> l;
-      ds = corner_dsum(img, W, H, tx * B + i * S, ty * B + j * S, S);
+      int q[6];
+      corner_q(img, W, H, tx * B + i * S, ty * B + j * S, S, q);
+      ds = decision_dsum(q, split6, merge6);
     }
   }
   const uint32_t split_bits = __ballot_sync(0xffffffffu, leaf && ds > split6);

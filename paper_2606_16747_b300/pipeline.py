@@ -53,9 +53,8 @@ class Renderer:
         self.l2 = dict(id2=torch.empty(P, **i32))
         self.l3 = dict(n=torch.empty(P, **i32), tail=torch.empty(P * 4, **i32),
                        t_tail=torch.empty(P, **f32))
-        xw = 8 if x_dtype == sn.F32 else 16
         xdt = torch.float32 if x_dtype == sn.F32 else torch.bfloat16
-        self.x = torch.empty(P * xw, dtype=xdt, device=device)
+        self.x = torch.empty(P * 8, dtype=xdt, device=device)
         self.front = torch.empty(P * 4, **f32)
         self.f = torch.empty(P * 4, **f32)
         self.rgba32f = torch.empty(P * 4, **f32)
@@ -77,6 +76,7 @@ class Renderer:
         self.interp_out = torch.zeros(P * 4, **f32)
         self.vp64_prev = torch.zeros(16, dtype=torch.float64, device=device)
         self.vp64_cur = torch.zeros(16, dtype=torch.float64, device=device)
+        self.reproj_ws = torch.zeros(sn.REPROJECT_WS_BYTES, dtype=torch.uint8, device=device)
 
     # -- inputs -------------------------------------------------------------
     def set_mlp(self, w: dict):
@@ -156,7 +156,7 @@ class Renderer:
         if vp64_cur is not None:
             self.vp64_cur.copy_(torch.as_tensor(np.asarray(vp64_cur, np.float64).reshape(16)))
         sn.reproject(self.prev_rgba, self.prev_z1, self.vp64_prev, self.vp64_cur, self.W, self.H,
-                     self.interp_out, stream)
+                     self.interp_out, self.reproj_ws, stream)
 
     def pass_state(self):
         return sn.read_pass_state(self.state)

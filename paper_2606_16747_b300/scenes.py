@@ -122,13 +122,26 @@ def frustum_scene(seed: int, n_tris: int, width: int, height: int,
     return Scene(np.ascontiguousarray(v), rgba, width, height, seed, camera(width, height))
 
 
+def _coherent_rgb(rng: np.random.Generator, u, v, jitter: float = 12.0, freq: float = 1.5):
+    """Colours that vary smoothly over the screen (a low-frequency sinusoid per
+    channel of the triangle's normalised centre (u, v)) plus uniform jitter:
+    neighbouring surfaces share a material-like hue, as in real scenes."""
+    ph = rng.uniform(0.0, 2.0 * math.pi, 3)
+    base = np.stack([127.5 + 100.0 * np.sin(2 * math.pi * freq * u + ph[0]),
+                     127.5 + 100.0 * np.sin(2 * math.pi * freq * v + ph[1]),
+                     127.5 + 100.0 * np.sin(2 * math.pi * freq * (u + v) + ph[2])], axis=-1)
+    return np.clip(np.rint(base + rng.uniform(-jitter, jitter, base.shape)), 0, 255).astype(np.uint32)
+
+
 def screen_scene(seed: int, n_tris: int, width: int, height: int,
                  size_px=(4.0, 400.0), size_scale: float = 1.0,
-                 alpha=(0.1, 0.9), depth=(1.0, 10.0)) -> Scene:
+                 alpha=(0.1, 0.9), depth=(1.0, 10.0), colours: str = "uniform") -> Scene:
     """Triangles sized in screen space: centre uniform on screen, size s
     log-uniform in ``size_px`` (times ``size_scale``), the three vertices uniform
     in the s x s square around the centre, per-vertex view depth uniform in
-    ``depth``, unprojected to world space (frame-0 camera)."""
+    ``depth``, unprojected to world space (frame-0 camera).  ``colours`` is
+    "uniform" (each channel uniform in 0..255) or "coherent" (smooth over the
+    screen, see _coherent_rgb)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     cx = rng.uniform(0.0, width, size=n_tris)
     cy = rng.uniform(0.0, height, size=n_tris)
@@ -141,6 +154,12 @@ def screen_scene(seed: int, n_tris: int, width: int, height: int,
     d = rng.uniform(depth[0], depth[1], size=(n_tris, 3))
     v = _unproject(ndc_x, ndc_y, d, width / height).astype(np.float32)
     rgba = _pack_rgba(rng, n_tris, *alpha)
+    if colours == "coherent":
+        rgb = _coherent_rgb(rng, cx / width, cy / height)
+        rgba = ((rgba & np.uint32(0xFF000000)) | rgb[:, 0] | (rgb[:, 1] << 8) |
+                (rgb[:, 2] << 16)).astype(np.uint32)
+    elif colours != "uniform":
+        raise ValueError(colours)
     return Scene(np.ascontiguousarray(v), rgba, width, height, seed, camera(width, height))
 
 
@@ -153,14 +172,14 @@ def small_scene(seed: int = 1) -> Scene:
     return frustum_scene(seed, 32, 256, 256)
 
 
-def hd_scene(seed: int = 3) -> Scene:
+def hd_scene(seed: int = 3, colours: str = "coherent") -> Scene:
     """1920x1080, 20k triangles, sizes log-uniform 4-400 px, alpha 0.1-0.9."""
-    return screen_scene(seed, 20000, 1920, 1080, size_scale=HD_SIZE_SCALE)
+    return screen_scene(seed, 20000, 1920, 1080, size_scale=HD_SIZE_SCALE, colours=colours)
 
 
-def uhd_scene(seed: int = 4) -> Scene:
+def uhd_scene(seed: int = 4, colours: str = "coherent") -> Scene:
     """3840x2160, 80k triangles, mean depth complexity ~16."""
-    return screen_scene(seed, 80000, 3840, 2160, size_scale=UHD_SIZE_SCALE)
+    return screen_scene(seed, 80000, 3840, 2160, size_scale=UHD_SIZE_SCALE, colours=colours)
 
 
 def training_scene(seed: int, width: int = 512, height: int = 512) -> Scene:

@@ -112,7 +112,7 @@ def lib():
         L.star_nt_quadtree_ws_bytes.argtypes = [_I32, _I32, _I32, ctypes.POINTER(ctypes.c_size_t)]
         L.star_nt_quadtree.argtypes = [_P, _P, _I32, _I32, ctypes.POINTER(Params), _P, _P, _P, _P,
                                        ctypes.c_size_t, _P]
-        L.star_nt_reproject.argtypes = [_P, _P, _P, _P, _I32, _I32, _P, _P]
+        L.star_nt_reproject.argtypes = [_P, _P, _P, _P, _I32, _I32, _P, _P, _P]
         for name in EXPORTS:
             if name not in ("star_nt_default_params", "star_nt_status_string", "star_nt_version"):
                 getattr(L, name).restype = _I32
@@ -242,9 +242,14 @@ def quadtree(rgba8, id1, W, H, params: Params, mask_prev, mask_out, state, ws, s
                                                       _ptr(ws), ws.numel(), _stream(stream)))
 
 
-def reproject(prev_rgba, prev_z1, vp_prev, vp_cur, W, H, out_rgba, stream=None):
+REPROJECT_WS_BYTES = 64
+
+
+def reproject(prev_rgba, prev_z1, vp_prev, vp_cur, W, H, out_rgba, ws=None, stream=None):
+    if ws is None:
+        ws = torch.empty(REPROJECT_WS_BYTES, dtype=torch.uint8, device=out_rgba.device)
     _check("star_nt_reproject", lib().star_nt_reproject(_ptr(prev_rgba), _ptr(prev_z1), _ptr(vp_prev),
-                                                        _ptr(vp_cur), W, H, _ptr(out_rgba),
+                                                        _ptr(vp_cur), W, H, _ptr(out_rgba), _ptr(ws),
                                                         _stream(stream)))
 
 

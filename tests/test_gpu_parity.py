@@ -411,3 +411,57 @@ def test_plain_frame_hd_full_size(orc, sn):
     assert np.max(np.abs(X[:, :5] - o["x"])) <= TOL_FEAT
     rgb = r.rgba32f.cpu().numpy().reshape(-1, 4)[:, :3]
     assert np.max(np.abs(rgb - o["rgb"])) <= TOL_FRAME
+
+
+# ---------------------------------------------------------------------------
+# star_nt_infer on the tcgen05 tensor cores (bf16 operands, fp32 accumulate)
+
+TOL_BF16 = 2.0 / 255.0
+
+
+def bf16_inputs(rng, P):
+    x = synthetic_x(rng, P)
+    xb = torch.from_numpy(x).to(torch.bfloat16)          # the input as the GPU receives it
+    return xb, xb.to(torch.float64).numpy()
+
+
+@pytest.mark.parametrize("P", [1, 127, 128, 129, 4099, 1 << 20])
+def test_infer_bf16_tcgen05(orc, sn, P):
+    rng = np.random.default_rng(1000 + P)
+    xb, x64 = bf16_inputs(rng, P)
+    w = scenes.mlp_xavier(7)
+    flat = scenes.mlp_flat(w).astype(np.float64)
+    X = xb.reshape(-1).cuda()
+    F = torch.full((P * 4,), -1.0, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    tw = {k: dev(v) for k, v in w.items()}
+    sn.infer(sn.mlp_struct(tw), sn.BF16, X, F, P, st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    ref = orc.mlp_forward(flat, x64[:, :5], x64[:, 5].astype(np.uint8))
+    got = F.cpu().numpy().reshape(P, 4)
+    err = np.abs(got[:, :3] - ref)
+    assert err.max() <= TOL_BF16, (err.max(), np.quantile(err, 0.999))
+    assert np.all(got[x64[:, 5] == 0, :3] == 0) and np.all(got[:, 3] == 0)
+    # repeated calls give identical bits
+    F2 = torch.zeros_like(F)
+    sn.infer(sn.mlp_struct(tw), sn.BF16, X, F2, P, st)
+    torch.cuda.synchronize()
+    assert torch.equal(F, F2)
+
+
+def test_plain_frame_bf16(orc, sn):
+    sc = scenes.screen_scene(17, 3000, 320, 208, size_scale=0.6)
+    W, H = sc.width, sc.height
+    mlp = scenes.mlp_xavier(2)
+    r = run_plain(sn, sc.verts, sc.rgba8, sc.cam.vp32, W, H, mlp, x_dtype=sn.BF16)
+    o = orc.frame_full(sc.verts, sc.rgba8, sc.cam.vp32, W, H, scenes.mlp_flat(mlp), threads=4)
+    X = r.x.view(torch.bfloat16).to(torch.float64).cpu().numpy().reshape(-1, 8)
+    ref_b = torch.from_numpy(o["x"]).to(torch.bfloat16).to(torch.float64).numpy()
+    # float32 features rounded to bf16 may land one bf16 step away from the
+    # float64 features rounded to bf16
+    assert np.max(np.abs(X[:, :5] - ref_b) / np.maximum(np.abs(ref_b), 1e-3)) <= 2.0 ** -7
+    assert np.array_equal(X[:, 5] == 1.0, o["res"]["n"] > 2)
+    rgb = r.rgba32f.cpu().numpy().reshape(-1, 4)[:, :3]
+    # frame error is the MLP error scaled by T_2 <= 1
+    assert np.max(np.abs(rgb - o["rgb"])) <= TOL_BF16
