@@ -263,6 +263,27 @@ star_nt_status star_nt_quadtree(const uint32_t *rgba8, const int32_t *id1, int32
                                 uint32_t *mask_out, star_nt_pass_state *state, void *ws,
                                 size_t ws_bytes, void *stream);
 
+/* star_nt_quadtree_static -- star_nt_quadtree for callers that cannot
+ * allocate device memory (a plug-in handed only its inputs and outputs by a
+ * host application, or an engine that fixes its GPU memory budget at start-up
+ * and allows no allocation on the frame path).  The paper has no counterpart.
+ * The workspace is a fixed array inside this library (STAR_NT_QT_STATIC_BYTES
+ * bytes, held on every GPU that loads the library until the process exits),
+ * enough for STAR_NT_QT_STATIC_MAX_TILES base tiles; larger frames return
+ * STAR_NT_ERR_CAPACITY.  Arguments and results are those of star_nt_quadtree
+ * minus ws / ws_bytes; nothing is allocated.  The first call on a device looks
+ * up the array's device address with that device current (make that first
+ * call before any stream capture).  All calls share the one array and it
+ * keeps the last call's contents (the parts that must start at zero are
+ * cleared by each call), so calls that overlap on the GPU race: serialise
+ * them, for instance on one stream. */
+#define STAR_NT_QT_STATIC_MAX_TILES 65536
+#define STAR_NT_QT_STATIC_BYTES (256 + 2 * 4 * STAR_NT_QT_STATIC_MAX_TILES)
+star_nt_status star_nt_quadtree_static(const uint32_t *rgba8, const int32_t *id1, int32_t W,
+                                       int32_t H, const star_nt_params *params,
+                                       const uint32_t *mask_prev, uint32_t *mask_out,
+                                       star_nt_pass_state *state, void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* star_nt_reproject -- interpolated frame by depth-based reprojection        */
 /* (Sec. 3.3, last paragraph; Fig. 1).                                       */

@@ -8,6 +8,8 @@
 // roots summed in a fixed order, so they are reproducible bit for bit.
 #include <math.h>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace star {
@@ -302,4 +304,56 @@ extern "C" star_nt_status star_nt_quadtree(const uint32_t *rgba8, const int32_t 
   k_qt_hist<<<nt, 256, 0, st>>>(id1, W, H, B, L.tiles_x, mask_out, hist);
   k_qt_finalize<<<1, 32, 0, st>>>(hist, W, H, params->delta2, params->delta3, state);
   return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Workspace-free variant.  Some callers cannot allocate device memory: a
+// plug-in that only ever receives buffers from its host application, or an
+// engine that budgets all GPU memory at start-up and forbids allocation on its
+// frame path (cudaMalloc may also synchronise the device, which a frame loop
+// cannot afford).  For them the quadtree workspace lives in a fixed array in
+// this library's device memory instead of a caller buffer.
+namespace star {
+constexpr int kQtStaticMaxTiles = 65536;
+constexpr size_t kQtStaticBytes = 256 + 2 * 4 * (size_t)kQtStaticMaxTiles;
+static __device__ __align__(256) unsigned char g_qt_scratch[kQtStaticBytes];
+
+constexpr int kMaxDevices = 64;
+static std::mutex g_qt_mutex;
+static void *g_qt_addr[kMaxDevices];  // device address of g_qt_scratch, per device
+
+// Device address of the array on the current device, looked up once per
+// device (with that device current) and cached.
+static cudaError_t qt_scratch_address(void **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_qt_mutex);
+  if (!g_qt_addr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_qt_scratch);
+    if (e != cudaSuccess) return e;
+    g_qt_addr[dev] = p;
+  }
+  *out = g_qt_addr[dev];
+  return cudaSuccess;
+}
+}  // namespace star
+
+extern "C" star_nt_status star_nt_quadtree_static(const uint32_t *rgba8, const int32_t *id1,
+                                                  int32_t W, int32_t H,
+                                                  const star_nt_params *params,
+                                                  const uint32_t *mask_prev, uint32_t *mask_out,
+                                                  star_nt_pass_state *state, void *stream) {
+  if (!params || W <= 0 || H <= 0) return STAR_NT_ERR_ARG;
+  size_t need = 0;
+  if (star_nt_quadtree_ws_bytes(W, H, params->base_tile, &need) != STAR_NT_OK) return STAR_NT_ERR_ARG;
+  const QtLayout L = qt_layout(W, H, params->base_tile);
+  if ((int64_t)L.tiles_x * L.tiles_y > kQtStaticMaxTiles || need > kQtStaticBytes)
+    return STAR_NT_ERR_CAPACITY;  // more tiles than the fixed workspace holds
+  void *ws = nullptr;
+  if (qt_scratch_address(&ws) != cudaSuccess) return STAR_NT_ERR_CUDA;
+  return star_nt_quadtree(rgba8, id1, W, H, params, mask_prev, mask_out, state, ws, kQtStaticBytes,
+                          stream);
 }
