@@ -34,10 +34,10 @@ FALLBACK_PEAKS = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustain
 N_SM = 148
 ALU_LANES_PER_SM = 128
 OPS_PER_FRAGMENT = 32     # algorithmic integer/fp operations per fragment (see design notes)
-# kernels of one step: 3 x raster (set-up, 2 x bin, 3-launch scan), 3 geometry
+# kernels of one step: 3 x raster (set-up/count, tile scan, fill), 3 geometry
 # passes, upscale/features, MLP, composite, quadtree (decide, 2 relax, hist,
-# finalize), reprojection
-KERNELS_PER_STEP = 3 * 6 + 3 + 1 + 1 + 1 + 5 + 1
+# finalize), reprojection (matrix, pixels)
+KERNELS_PER_STEP = 3 * 3 + 3 + 1 + 1 + 1 + 5 + 2
 
 
 def load_peaks():
@@ -132,7 +132,7 @@ def run_ours(args, rank, world):
     x_dtype = sn.BF16 if args.mlp == "bf16" else sn.F32
     star = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=x_dtype, base_tile=args.base_tile)
     plain = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=sn.F32)
-    n_frames = 2 * (args.warmup + args.steps) + 8
+    n_frames = 2 * (4 + args.warmup + 2 * args.steps + 12)
     cams = scenes.orbit_cameras(W, H, n_frames)
     vp32 = torch.tensor(np.stack([c.vp32 for c in cams]), device=dev)
     vp64 = torch.tensor(np.stack([c.vp64.reshape(16) for c in cams]), device=dev)
@@ -141,80 +141,86 @@ def run_ours(args, rank, world):
     # fragment count of the workload (full resolution, first camera)
     Fcount = fragment_count(sn, star, vp32[0], W, H)
 
-    def real(k, mark=None):
-        star.vp.copy_(vp32[k])
-        star.star_frame(mark=mark)
-        star.prev_rgba.copy_(star.rgba32f)
-        star.prev_z1.copy_(star.l1["z1"])
-        star.vp64_prev.copy_(vp64[k])
+    def set_cams(k):            # step k: real frame 2k, interpolated frame 2k + 1
+        star.set_cameras(vp32[2 * k], vp64[2 * k], vp64[2 * k + 1])
 
-    def interp(k):
-        star.vp64_cur.copy_(vp64[k])
-        star.interp_frame()
-
-    # settle the tile hierarchy on the first frames, then warm up
+    # settle the tile hierarchy on the first frames, then capture one step
     for k in range(4):
-        real(k)
-    frame = 4
+        set_cams(k)
+        star.step()
+    stages = star.star_stages() + [("reproject", star.interp_frame)]
+    g_step = star.capture(star.step)
+    g_stage = [(name, star.capture(fn)) for name, fn in stages]
+    step = 4
     for _ in range(args.warmup):
-        real(frame)
-        interp(frame + 1)
-        frame += 2
+        set_cams(step)
+        g_step.replay()
+        step += 1
     torch.cuda.synchronize()
     star.check_status()
 
-    stage_names = ["raster", "pass1", "pass2", "pass3", "features", "infer", "composite", "quadtree",
-                   "reproject"]
-    step_ms, stage_ms = [], {k: [] for k in stage_names}
+    def timed(replay, k):
+        flush.fill_(1)
+        set_cams(k)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        replay()
+        e1.record()
+        return e0, e1
+
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     sampler = ClockSampler(torch.cuda.current_device()).start()
     wall0 = time.perf_counter()
+    events = []
     for _ in range(args.steps):
-        flush.fill_(1)
-        ev = {"start": torch.cuda.Event(enable_timing=True)}
-        ev["start"].record()
-
-        def mark(name):
-            e = torch.cuda.Event(enable_timing=True)
-            e.record()
-            ev[name] = e
-
-        real(frame, mark)
-        interp(frame + 1)
-        mark("reproject")
-        frame += 2
-        ev["end"] = ev["reproject"]
-        torch.cuda.synchronize()
-        step_ms.append(ev["start"].elapsed_time(ev["end"]))
-        prev = ev["start"]
-        for name in stage_names:
-            stage_ms[name].append(prev.elapsed_time(ev[name]))
-            prev = ev[name]
+        events.append(timed(g_step.replay, step))
+        step += 1
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in events]
     if world > 1:
         torch.distributed.barrier()
     star.check_status()
     state = star.pass_state()
 
+    # per-stage times: each stage replayed as its own graph, in order, queued
+    # behind ~1 GB of writes so that the host has enqueued every stage before
+    # the first one starts (no host gaps inside the measured span)
+    stage_ms = {name: [] for name, _ in g_stage}
+    for _ in range(min(args.steps, 10)):
+        set_cams(step)
+        step += 1
+        for _ in range(4):
+            flush.fill_(1)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(g_stage) + 1)]
+        ev[0].record()
+        for i, (name, g) in enumerate(g_stage):
+            g.replay()
+            ev[i + 1].record()
+        torch.cuda.synchronize()
+        for i, (name, _) in enumerate(g_stage):
+            stage_ms[name].append(ev[i].elapsed_time(ev[i + 1]))
+
     # plain full-resolution FP32 pipeline on the same scene and cameras
+    plain.set_cameras(vp32[0])
+    g_plain = plain.capture(plain.plain_frame)
     plain_ms = []
     for k in range(args.warmup + args.steps):
         flush.fill_(1)
-        plain.vp.copy_(vp32[k])
+        plain.set_cameras(vp32[2 * k])
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        plain.plain_frame()
+        g_plain.replay()
         e1.record()
         torch.cuda.synchronize()
         if k >= args.warmup:
             plain_ms.append(e0.elapsed_time(e1))
     plain.check_status()
 
-    # end to end through the public API: host inputs in, frame out, every step
+    # end to end through the public API: host inputs in, frames out, every step
     e2e = end_to_end(sn, torch, sc, w, x_dtype, W, H, cams, args)
 
     t_step = float(np.mean(step_ms))
@@ -254,6 +260,7 @@ def run_ours(args, rank, world):
         "stages_ms": {k: round(v, 5) for k, v in stage_mean.items()},
         "pass_state": {k: state[k] for k in ("W2", "H2", "W3", "H3", "s2", "s3", "wbar", "hist")},
         "wall_s": round(wall, 3),
+        "graph": "one CUDA graph per step (real + interpolated frame), replayed",
         "gpu_launches": KERNELS_PER_STEP * args.steps,
         "clocks": clocks,
         "e2e": e2e,
@@ -284,8 +291,9 @@ def fragment_count(sn, r, vp, W, H):
 
 def end_to_end(sn, torch, sc, w, x_dtype, W, H, cams, args):
     """Same metric through the public API from host memory: per step the
-    triangle soup is copied host->device, one real and one interpolated frame
-    are rendered, and the 8-bit frame is read back."""
+    triangle soup and the cameras are copied host->device, one real and one
+    interpolated frame are rendered (the captured step), and both 8-bit frames
+    are read back."""
     from paper_2606_16747_b300.pipeline import Renderer
     r = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=x_dtype, base_tile=args.base_tile)
     hv = torch.from_numpy(np.ascontiguousarray(sc.verts)).pin_memory()
@@ -293,34 +301,35 @@ def end_to_end(sn, torch, sc, w, x_dtype, W, H, cams, args):
     hvp = [torch.from_numpy(np.ascontiguousarray(c.vp32)).pin_memory() for c in cams]
     hvp64 = [torch.from_numpy(np.ascontiguousarray(c.vp64.reshape(16))).pin_memory() for c in cams]
     out = torch.empty(W * H, dtype=torch.int32).pin_memory()
+    out2 = torch.empty(W * H, dtype=torch.int32).pin_memory()
+    for k in range(4):
+        r.set_cameras(hvp[2 * k], hvp64[2 * k], hvp64[2 * k + 1])
+        r.step()
+    g = r.capture(r.step)
     times = []
     for k in range(args.warmup + args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         r.verts.copy_(hv, non_blocking=True)
         r.rgba8.copy_(hc, non_blocking=True)
-        r.vp.copy_(hvp[2 * k], non_blocking=True)
-        r.star_frame()
-        r.prev_rgba.copy_(r.rgba32f)
-        r.prev_z1.copy_(r.l1["z1"])
-        r.vp64_prev.copy_(hvp64[2 * k], non_blocking=True)
-        r.vp64_cur.copy_(hvp64[2 * k + 1], non_blocking=True)
-        r.interp_frame()
+        r.set_cameras(hvp[2 * k], hvp64[2 * k], hvp64[2 * k + 1])
+        g.replay()
         out.copy_(r.rgba8_out, non_blocking=True)
+        out2.copy_(r.interp_rgba8, non_blocking=True)
         torch.cuda.synchronize()
         if k >= args.warmup:
             times.append(time.perf_counter() - t0)
     r.check_status()
     h2d = hv.numel() * 4 + hc.numel() * 4 + 64 + 2 * 128
     return {"value": round(float(np.mean(times)) * 1e3 / 2.0, 5), "unit": "ms/frame",
-            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(out.numel() * 4)}
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(out.numel() * 4 + out2.numel() * 4)}
 
 
 def psnr_vs_abuffer(r, sc, W, H, cams, args):
     """PSNR of the last real frame against the exact A-buffer (CPU oracle)."""
     import oracle
     k = 2 * (args.warmup + args.steps) + 2
-    r.vp.copy_(__import__("torch").tensor(cams[k].vp32, device="cuda"))
+    r.set_cameras(cams[k].vp32)
     r.star_frame()
     rgb = r.rgba32f.cpu().numpy().reshape(-1, 4)[:, :3].astype(np.float64)
     fr = oracle.raster(sc.verts, cams[k].vp32, W, H, threads=os.cpu_count() or 1)

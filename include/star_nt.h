@@ -72,15 +72,19 @@ typedef struct {
  * view_proj: device, 16 float32, row-major, clip = M (x, y, z, w)^T; the
  *   projection maps the visible depth range to NDC z in [0, 1].
  * size: device, {W_p, H_p}, the pass's resolution (read on the device).
- * max_w, max_h: host upper bounds of size[]; they size the launches. */
+ * max_w, max_h: host upper bounds of size[]; they size the launches.
+ * merge_at: optional device {W, H} (NULL: never): when size equals it, the
+ *   pass is left to pass 1 (star_nt_geometry_pass_merged), and the bins are
+ *   marked merged and hold no triangles. */
 typedef struct {
     const float *view_proj;
     const int32_t *size;
     int32_t max_w, max_h;
+    const int32_t *merge_at;
 } star_nt_target;
 
 /* Parameters of the method.  Defaults (star_nt_default_params):
- * bg = (1, 1, 1), kappa_n = 1/64, tau_split = 24, tau_merge = 12,
+ * bg = (1, 1, 1), kappa_n = 1/64, tau_split = 48, tau_merge = 24,
  * delta2 = 2.2, delta3 = 3.0 (Eq. 2), base_tile = 16, relax_iters = 2. */
 typedef struct {
     float bg[3];       /* background colour C_b of Eq. 4 */
@@ -195,6 +199,17 @@ star_nt_status star_nt_build_inputs(const star_nt_scene *scene, const star_nt_bi
 star_nt_status star_nt_geometry_pass(const star_nt_scene *scene, const star_nt_bins *bins,
                                      int32_t mode, const star_nt_layers *layers,
                                      int32_t *d_status, void *stream);
+/* star_nt_geometry_pass_merged: pass 1 (nearest fragment, full resolution)
+ * that also performs pass 2 and/or pass 3 at full resolution when their bins
+ * are marked merged (their device-side size equals the full size): it then
+ * writes id2 into layers2 and n, tail, t_tail into layers3 at full
+ * resolution, so star_nt_upscale_features reads them as usual. */
+star_nt_status star_nt_geometry_pass_merged(const star_nt_scene *scene, const star_nt_bins *bins1,
+                                            const star_nt_bins *bins2, const star_nt_bins *bins3,
+                                            const star_nt_layers *layers1,
+                                            const star_nt_layers *layers2,
+                                            const star_nt_layers *layers3, int32_t *d_status,
+                                            void *stream);
 star_nt_status star_nt_upscale_features(const star_nt_scene *scene, const star_nt_bins *bins2,
                                 const star_nt_bins *bins3, const star_nt_layers *layers1,
                                 const star_nt_layers *layers2, const star_nt_layers *layers3,
@@ -293,7 +308,8 @@ star_nt_status star_nt_quadtree_static(const uint32_t *rgba8, const int32_t *id1
 /* current camera and projected with the previous one; the previous frame is */
 /* sampled there bilinearly with clamp to edge.  A point behind the previous */
 /* camera keeps its own previous colour.                                    */
-/* prev_rgba, out_rgba: [W*H][4] float32 (distinct); prev_z1: [W*H];           */
+/* prev_rgba, out_rgba: [W*H][4] float32 (distinct); out_rgba8: optional      */
+/* [W*H] 8-bit copy (as star_nt_composite), may be NULL; prev_z1: [W*H];      */
 /* vp_prev, vp_cur: device, 16 float64 row-major view-projections; ws: device */
 /* scratch of STAR_NT_REPROJECT_WS_BYTES bytes (16-byte aligned) that holds  */
 /* VP_prev inv(VP_cur) - I for the call (two launches: that matrix in       */
@@ -301,7 +317,8 @@ star_nt_status star_nt_quadtree_static(const uint32_t *rgba8, const int32_t *id1
 #define STAR_NT_REPROJECT_WS_BYTES 64
 star_nt_status star_nt_reproject(const float *prev_rgba, const float *prev_z1,
                                  const double *vp_prev, const double *vp_cur, int32_t W,
-                                 int32_t H, float *out_rgba, void *ws, void *stream);
+                                 int32_t H, float *out_rgba, uint32_t *out_rgba8, void *ws,
+                                 void *stream);
 
 #ifdef __cplusplus
 }

@@ -39,7 +39,8 @@ struct __align__(16) BinsHeader {
   int32_t n_pixels;    // size[0] * size[1]
   uint32_t n_pairs;    // (triangle, tile) pairs needed
   int32_t n_tris;
-  uint32_t pad[8];
+  int32_t merged;      // 1: the pass runs at full size and is taken over by pass 1
+  uint32_t pad[7];
 };
 static_assert(sizeof(BinsHeader) == 64, "BinsHeader layout");
 
@@ -107,19 +108,24 @@ __device__ inline long long floor_div_ll(long long a, long long b) {  // b > 0
 }
 
 // Bilinear source axis of the upscale: u * 2W = (2x + 1) Wp - W (exact).
+// All quantities fit in int32 for frames up to 16384 pixels wide; the floor
+// division uses a float estimate corrected by one exact integer step.
 struct Axis {
   int i0, i1;
   int rem, den;
 };
 __device__ inline Axis upscale_axis(int x, int Wp, int W) {
-  long long num = (long long)(2 * x + 1) * Wp - W;
-  long long den = 2LL * W;
-  long long q = floor_div_ll(num, den);
+  const int num = (2 * x + 1) * Wp - W;
+  const int den = 2 * W;
+  int q = __float2int_rd(__fdividef((float)num, (float)den));
+  int rem = num - q * den;
+  if (rem < 0) { --q; rem += den; }
+  if (rem >= den) { ++q; rem -= den; }
   Axis a;
-  a.rem = (int)(num - q * den);
-  a.den = (int)den;
-  a.i0 = (int)(q < 0 ? 0 : (q > Wp - 1 ? Wp - 1 : q));
-  a.i1 = (int)(q + 1 < 0 ? 0 : (q + 1 > Wp - 1 ? Wp - 1 : q + 1));
+  a.rem = rem;
+  a.den = den;
+  a.i0 = q < 0 ? 0 : (q > Wp - 1 ? Wp - 1 : q);
+  a.i1 = q + 1 < 0 ? 0 : (q + 1 > Wp - 1 ? Wp - 1 : q + 1);
   return a;
 }
 

@@ -60,6 +60,15 @@ __global__ void __launch_bounds__(256) k_mlp_f32(const float *__restrict__ w1, c
   }
 }
 
+// 8-bit RGBA of a float colour: round half to even of clamp(c, 0, 1) * 255,
+// alpha 255.
+__device__ __forceinline__ uint32_t quantize_rgba8(float4 c) {
+  const uint32_t R = __float2uint_rn(__saturatef(c.x) * 255.0f);
+  const uint32_t G = __float2uint_rn(__saturatef(c.y) * 255.0f);
+  const uint32_t B = __float2uint_rn(__saturatef(c.z) * 255.0f);
+  return R | (G << 8) | (B << 16) | (255u << 24);
+}
+
 // ---------------------------------------------------------------------------
 // Eq. 4 with the first and last terms already in front.rgb.
 __global__ void __launch_bounds__(256) k_composite(const float4 *__restrict__ front,
@@ -69,12 +78,7 @@ __global__ void __launch_bounds__(256) k_composite(const float4 *__restrict__ fr
     const float4 a = front[p], b = f[p];
     const float r = fmaf(a.w, b.x, a.x), g = fmaf(a.w, b.y, a.y), bl = fmaf(a.w, b.z, a.z);
     if (out) out[p] = make_float4(r, g, bl, 1.0f);
-    if (q) {
-      const uint32_t R = __float2uint_rn(__saturatef(r) * 255.0f);
-      const uint32_t G = __float2uint_rn(__saturatef(g) * 255.0f);
-      const uint32_t B = __float2uint_rn(__saturatef(bl) * 255.0f);
-      q[p] = R | (G << 8) | (B << 16) | (255u << 24);
-    }
+    if (q) q[p] = quantize_rgba8(make_float4(r, g, bl, 1.0f));
   }
 }
 
@@ -131,7 +135,7 @@ __global__ void k_reproject_matrix(const double *__restrict__ vp_prev, const dou
 __global__ void __launch_bounds__(256) k_reproject(const float4 *__restrict__ prev,
                                                    const float *__restrict__ z1,
                                                    const float *__restrict__ Eg, int W, int H,
-                                                   float4 *__restrict__ out) {
+                                                   float4 *__restrict__ out, uint32_t *__restrict__ q) {
   __shared__ float sE[16];
   if (threadIdx.x < 16) sE[threadIdx.x] = Eg[threadIdx.x];
   __syncthreads();
@@ -147,7 +151,9 @@ __global__ void __launch_bounds__(256) k_reproject(const float4 *__restrict__ pr
   const float a3 = fmaf(sE[12], nx, fmaf(sE[13], ny, fmaf(sE[14], d, sE[15])));
   const float den = 1.0f + a3;
   if (!(den > 0.0f)) {
-    out[p] = prev[p];
+    const float4 v = prev[p];
+    out[p] = v;
+    if (q) q[p] = quantize_rgba8(v);
     return;
   }
   float dx = 0.5f * (float)W * (a0 - nx * a3) / den;
@@ -167,6 +173,7 @@ __global__ void __launch_bounds__(256) k_reproject(const float4 *__restrict__ pr
   o.z = (1.f - fy) * ((1.f - fx) * v00.z + fx * v10.z) + fy * ((1.f - fx) * v01.z + fx * v11.z);
   o.w = (1.f - fy) * ((1.f - fx) * v00.w + fx * v10.w) + fy * ((1.f - fx) * v01.w + fx * v11.w);
   out[p] = o;
+  if (q) q[p] = quantize_rgba8(o);
 }
 
 static int grid_for(long long P) {
@@ -200,8 +207,8 @@ extern "C" void star_nt_default_params(star_nt_params *p) {
   if (!p) return;
   p->bg[0] = p->bg[1] = p->bg[2] = 1.0f;
   p->kappa_n = 1.0f / 64.0f;
-  p->tau_split = 24.0;
-  p->tau_merge = 12.0;
+  p->tau_split = 48.0;
+  p->tau_merge = 24.0;
   p->delta2 = 2.2;
   p->delta3 = 3.0;
   p->base_tile = 16;
@@ -243,7 +250,8 @@ extern "C" star_nt_status star_nt_composite(const float *front, const float *f, 
 
 extern "C" star_nt_status star_nt_reproject(const float *prev_rgba, const float *prev_z1,
                                             const double *vp_prev, const double *vp_cur, int32_t W,
-                                            int32_t H, float *out_rgba, void *ws, void *stream) {
+                                            int32_t H, float *out_rgba, uint32_t *out_rgba8,
+                                            void *ws, void *stream) {
   if (W <= 0 || H <= 0 || !prev_rgba || !prev_z1 || !vp_prev || !vp_cur || !out_rgba || !ws ||
       prev_rgba == out_rgba)
     return STAR_NT_ERR_ARG;
@@ -255,6 +263,6 @@ extern "C" star_nt_status star_nt_reproject(const float *prev_rgba, const float 
   k_reproject_matrix<<<1, 32, 0, st>>>(vp_prev, vp_cur, E);
   dim3 grid((W + 31) / 32, (H + 7) / 8);
   k_reproject<<<grid, 256, 0, st>>>(reinterpret_cast<const float4 *>(prev_rgba), prev_z1, E, W, H,
-                                    reinterpret_cast<float4 *>(out_rgba));
+                                    reinterpret_cast<float4 *>(out_rgba), out_rgba8);
   return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
 }

@@ -93,10 +93,8 @@ __device__ __forceinline__ void write_features(const FeatOut &fo, size_t p, floa
 // fragment, the two nearest, the two nearest plus tail sums, or all of it
 // plus the full-resolution network input (fused plain pipeline).
 template <int MODE>
-__global__ void __launch_bounds__(256) k_pass(BinsView bv, const uint32_t *__restrict__ rgba8,
-                                              PassOut po, FeatOut fo) {
-  __shared__ TriSetup s_tri[kChunk];
-  __shared__ uint32_t s_id[kChunk];
+__device__ __forceinline__ void pass_body(const BinsView &bv, const uint32_t *__restrict__ rgba8,
+                                          const PassOut &po, const FeatOut &fo, TileStage &stage) {
   const BinsHeader *hd = bv.hd;
   if ((int64_t)hd->n_pairs > bv.pair_capacity) return;
   const int tile = blockIdx.x;
@@ -108,7 +106,7 @@ __global__ void __launch_bounds__(256) k_pass(BinsView bv, const uint32_t *__res
   int i1 = 0x7fffffff, i2 = 0x7fffffff;
   uint32_t N = 0, opq = 0;
   unsigned long long rg = 0, ba = 0, lg = 0;
-  for_each_fragment(bv, tile, tp, s_tri, s_id, [&](const TriSetup &T, uint32_t id_u, float z) {
+  for_each_fragment(bv, tile, tp, stage, [&](const TriSetup &T, uint32_t id_u, float z) {
     const int id = (int)id_u;
     if (MODE == kTop1) {
       if (z < z1 || (z == z1 && id < i1)) { z1 = z; i1 = id; }
@@ -161,6 +159,34 @@ __global__ void __launch_bounds__(256) k_pass(BinsView bv, const uint32_t *__res
   }
 }
 
+template <int MODE>
+__global__ void __launch_bounds__(256) k_pass(BinsView bv, const uint32_t *__restrict__ rgba8,
+                                              PassOut po, FeatOut fo) {
+  __shared__ TileStage stage;
+  pass_body<MODE>(bv, rgba8, po, fo, stage);
+}
+
+// Pass 1 at full resolution; when pass 2 and/or pass 3 are marked merged
+// (their size equals the full size) it keeps the two nearest fragments and
+// the tail sums as well and writes their planes at full resolution.
+__global__ void __launch_bounds__(256) k_pass_merged(BinsView bv, const BinsHeader *hd2,
+                                                     const BinsHeader *hd3,
+                                                     const uint32_t *__restrict__ rgba8, PassOut o1,
+                                                     PassOut o2, PassOut o3) {
+  __shared__ TileStage stage;
+  const bool m2 = hd2->merged != 0, m3 = hd3->merged != 0;
+  if (!m2 && !m3) {
+    pass_body<kTop1>(bv, rgba8, o1, FeatOut{}, stage);
+    return;
+  }
+  PassOut o = o1;
+  o.id2 = m2 ? o2.id2 : nullptr;
+  o.n = m3 ? o3.n : nullptr;
+  o.tail = m3 ? o3.tail : nullptr;
+  o.t_tail = m3 ? o3.t_tail : nullptr;
+  pass_body<kTail>(bv, rgba8, o, FeatOut{}, stage);
+}
+
 // Full-resolution features from pass 1 (full res) and the bilinear upscale
 // of passes 2 and 3 (their own resolutions, read from their bins headers).
 __global__ void __launch_bounds__(256) k_features(int W, int H, const BinsHeader *hd2,
@@ -192,11 +218,12 @@ __global__ void __launch_bounds__(256) k_features(int W, int H, const BinsHeader
     for (int j = 0; j < 2; ++j)
 #pragma unroll
       for (int i = 0; i < 2; ++i) {
+        const float w = wys[j] * wxs[i];
+        if (w == 0.0f) continue;  // exact zero weight: sample not needed
         const int id = id2[(size_t)ys[j] * W2 + xs[i]];
         if (id < 0) continue;
         float r, g, b, a;
         unpack_rgba(__ldg(rgba8 + id), r, g, b, a);
-        const float w = wys[j] * wxs[i];
         L2[0] += w * (a * r);
         L2[1] += w * (a * g);
         L2[2] += w * (a * b);
@@ -217,6 +244,8 @@ __global__ void __launch_bounds__(256) k_features(int W, int H, const BinsHeader
     for (int j = 0; j < 2; ++j)
 #pragma unroll
       for (int i = 0; i < 2; ++i) {
+        const long long wi = wyi[j] * wxi[i];
+        if (wi == 0) continue;  // exact zero weight
         const size_t q = (size_t)ys[j] * W3 + xs[i];
         const float w = wys[j] * wxs[i];
         const uint32_t nn = n3[q];
@@ -227,7 +256,7 @@ __global__ void __launch_bounds__(256) k_features(int W, int H, const BinsHeader
         Sg += w * (float)tl.z;
         Sb += w * (float)tl.w;
         t += w * t3[q];
-        nexact += wyi[j] * wxi[i] * (long long)nn;
+        nexact += wi * (long long)nn;
       }
   }
   const bool flag = nexact > 2LL * ax3.den * ay3.den;
@@ -307,6 +336,29 @@ extern "C" star_nt_status star_nt_geometry_pass(const star_nt_scene *scene, cons
   return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
 }
 
+extern "C" star_nt_status star_nt_geometry_pass_merged(const star_nt_scene *scene,
+                                                       const star_nt_bins *b1,
+                                                       const star_nt_bins *b2,
+                                                       const star_nt_bins *b3,
+                                                       const star_nt_layers *l1,
+                                                       const star_nt_layers *l2,
+                                                       const star_nt_layers *l3, int32_t *d_status,
+                                                       void *stream) {
+  (void)d_status;
+  if (!scene || !b1 || !b2 || !b3 || !b1->mem || !b2->mem || !b3->mem || !l1 || !l2 || !l3)
+    return STAR_NT_ERR_ARG;
+  if (!l1->id1 && !l1->z1) return STAR_NT_ERR_ARG;
+  if (!l2->id2 || !l3->n || !l3->tail || !l3->t_tail) return STAR_NT_ERR_ARG;
+  if (!layers_ok(l1) || !layers_ok(l2) || !layers_ok(l3)) return STAR_NT_ERR_ARG;
+  if (scene->n_tris > 0 && !scene->rgba8) return STAR_NT_ERR_ARG;
+  BinsView v1 = bins_view(*b1), v2 = bins_view(*b2), v3 = bins_view(*b3);
+  PassOut o1 = pass_out(l1);
+  o1.id2 = nullptr; o1.n = nullptr; o1.tail = nullptr; o1.t_tail = nullptr;
+  k_pass_merged<<<tiles_of(b1), 256, 0, (cudaStream_t)stream>>>(v1, v2.hd, v3.hd, scene->rgba8, o1,
+                                                                pass_out(l2), pass_out(l3));
+  return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
+}
+
 extern "C" star_nt_status star_nt_upscale_features(const star_nt_scene *scene, const star_nt_bins *b2,
                                            const star_nt_bins *b3, const star_nt_layers *l1,
                                            const star_nt_layers *l2, const star_nt_layers *l3,
@@ -354,7 +406,9 @@ extern "C" star_nt_status star_nt_build_inputs(const star_nt_scene *scene, const
   c.t_tail = l3->t_tail;
   a.id2 = nullptr; a.n = nullptr; a.tail = nullptr; a.t_tail = nullptr;
   star_nt_status s;
-  if ((s = star_nt_geometry_pass(scene, b1, 1, &a, d_status, stream)) != STAR_NT_OK) return s;
+  if ((s = star_nt_geometry_pass_merged(scene, b1, b2, b3, l1, l2, l3, d_status, stream)) !=
+      STAR_NT_OK)
+    return s;
   if ((s = star_nt_geometry_pass(scene, b2, 2, &b, d_status, stream)) != STAR_NT_OK) return s;
   if ((s = star_nt_geometry_pass(scene, b3, 3, &c, d_status, stream)) != STAR_NT_OK) return s;
   return star_nt_upscale_features(scene, b2, b3, l1, l2, l3, W, H, params, out, stream);

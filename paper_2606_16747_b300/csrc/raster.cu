@@ -13,26 +13,10 @@ namespace star {
 // the camera, outside NDC z in [0, 1] or outside the guard band, snap to
 // 1/256 pixel, order the vertices for a positive area, then store the biased
 // edge functions, depth plane, pixel bounding box and colour sums.
-__global__ void k_setup(const float *__restrict__ verts, const uint32_t *__restrict__ rgba8,
-                        int n_tris, const float *__restrict__ vp, const int32_t *__restrict__ size,
-                        BinsView bv, int32_t *status) {
-  // a device-side size beyond the workspace empties the pass instead of
-  // writing out of bounds
-  const bool size_ok = size[0] > 0 && size[1] > 0 && size[0] <= bv.max_w && size[1] <= bv.max_h;
-  const int W = size_ok ? size[0] : 0, H = size_ok ? size[1] : 0;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t == 0) {
-    BinsHeader *hd = bv.hd;
-    hd->size[0] = W;
-    hd->size[1] = H;
-    hd->tiles_x = (W + kTile - 1) / kTile;
-    hd->tiles_y = (H + kTile - 1) / kTile;
-    hd->n_tiles = hd->tiles_x * hd->tiles_y;
-    hd->n_pixels = W * H;
-    hd->n_tris = n_tris;
-    if (!size_ok) raise_status(status, STAR_NT_ERR_ARG);
-  }
-  if (t >= n_tris) return;
+__device__ __forceinline__ void triangle_setup(int t, const float *__restrict__ verts,
+                                           const uint32_t *__restrict__ rgba8,
+                                           const float *__restrict__ vp, int W, int H, bool size_ok,
+                                           TriSetup *out) {
   float m[16];
 #pragma unroll
   for (int i = 0; i < 16; ++i) m[i] = __ldg(vp + i);
@@ -119,55 +103,136 @@ __global__ void k_setup(const float *__restrict__ verts, const uint32_t *__restr
   S.ba = (a8 * b8) | (a8 << 32);
   S.lg = a8 == 255 ? 0ull
                    : __double2ull_rn((log2(255.0) - log2((double)(255 - a8))) * 4294967296.0);
-  bv.setups[t] = S;
+  *out = S;
 }
 
-// Bin triangles to tiles: one warp per triangle, lanes stride over the
-// tiles of its bounding box.  A tile is kept unless one edge function is
-// negative at every pixel centre of the tile (its maximum over the tile's
+// Render-target size of a pass, validated against the workspace: a size
+// beyond it empties the pass instead of writing out of bounds.
+__device__ __forceinline__ bool pass_size(const int32_t *size, const BinsView &bv, int &W, int &H) {
+  const bool ok = size[0] > 0 && size[1] > 0 && size[0] <= bv.max_w && size[1] <= bv.max_h;
+  W = ok ? size[0] : 0;
+  H = ok ? size[1] : 0;
+  return ok;
+}
+
+// Tile range and conservative tile test shared by the two binning kernels.
+// A tile is kept unless one edge function is negative at every pixel centre
+// of the tile clipped to the triangle's bounding box (its maximum over the
 // corner centres is negative), which never drops a covered pixel.
-// fill == 0 counts pairs per tile; fill == 1 writes them.
-__global__ void k_bin(BinsView bv, int n_tris, int fill, int32_t *status) {
-  const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  if (warp >= n_tris) return;
+__device__ __forceinline__ bool tile_hit(const TriSetup &T, int tx, int ty) {
+  const int xlo = max(tx * kTile, (int)T.xa), xhi = min(tx * kTile + kTile - 1, (int)T.xb);
+  const int ylo = max(ty * kTile, (int)T.ya), yhi = min(ty * kTile + kTile - 1, (int)T.yb);
+  const int Pxlo = xlo * kSub + kSub / 2, Pxhi = xhi * kSub + kSub / 2;
+  const int Pylo = ylo * kSub + kSub / 2, Pyhi = yhi * kSub + kSub / 2;
+  bool hit = true;
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    const long long mx = T.c[e] + (long long)T.dx[e] * (T.dx[e] > 0 ? Pyhi : Pylo) -
+                         (long long)T.dy[e] * (T.dy[e] > 0 ? Pxlo : Pxhi);
+    if (mx < 0) hit = false;
+  }
+  return hit;
+}
+
+// Candidate tiles of a set-up triangle: its bounding box in tiles.
+__device__ __forceinline__ int tile_span(const TriSetup &T, int &tx0, int &ty0, int &ntx) {
+  if (T.xa > T.xb || T.ya > T.yb) return 0;
+  tx0 = T.xa / kTile;
+  ty0 = T.ya / kTile;
+  ntx = T.xb / kTile - tx0 + 1;
+  return ntx * (T.yb / kTile - ty0 + 1);
+}
+
+constexpr int kBinThreads = 128;
+
+// (triangle, tile) candidates of one block of kBinThreads triangles,
+// flattened so that every thread walks an equal share: an exclusive scan of
+// the per-triangle candidate counts, then a binary search per candidate.
+// Calls emit(triangle, tile) for every candidate that passes tile_hit.
+template <class Emit>
+__device__ __forceinline__ void for_each_pair(const BinsView &bv, int t0, int n_tris, int tiles_x,
+                                              int *s_off, Emit &&emit) {
+  const int tid = threadIdx.x, t = t0 + tid;
+  int tx0 = 0, ty0 = 0, ntx = 1;
+  const int nt = t < n_tris ? tile_span(bv.setups[t], tx0, ty0, ntx) : 0;
+  // inclusive scan of nt over the block (warp shuffles, then warp totals)
+  int v = nt;
+  const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += y;
+  }
+  __shared__ int s_w[kBinThreads / 32];
+  if (lane == 31) s_w[warp] = v;
+  __syncthreads();
+  int before = 0;
+  for (int w = 0; w < warp; ++w) before += s_w[w];
+  s_off[tid + 1] = before + v;
+  if (tid == 0) s_off[0] = 0;
+  __syncthreads();
+  const int total = s_off[kBinThreads];
+  for (int q = tid; q < total; q += kBinThreads) {
+    int lo = 0, hi = kBinThreads - 1;  // largest j with s_off[j] <= q
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s_off[mid] <= q) lo = mid; else hi = mid - 1;
+    }
+    const TriSetup &T = bv.setups[t0 + lo];
+    int ax0, ay0, anx;
+    tile_span(T, ax0, ay0, anx);
+    const int k = q - s_off[lo];
+    const int tx = ax0 + k % anx, ty = ay0 + k / anx;
+    if (tile_hit(T, tx, ty)) emit(t0 + lo, ty * tiles_x + tx);
+  }
+}
+
+// Set-up (one triangle per thread) and per-tile candidate counts.
+__global__ void __launch_bounds__(kBinThreads) k_bin_count(const float *__restrict__ verts,
+                                                           const uint32_t *__restrict__ rgba8,
+                                                           int n_tris, const float *__restrict__ vp,
+                                                           const int32_t *__restrict__ size,
+                                                           const int32_t *__restrict__ merge_at,
+                                                           BinsView bv, int32_t *status) {
+  __shared__ int s_off[kBinThreads + 1];
+  int W, H;
+  const bool size_ok = pass_size(size, bv, W, H);
+  const bool merged = size_ok && merge_at && W == merge_at[0] && H == merge_at[1];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    BinsHeader *hd = bv.hd;
+    hd->size[0] = W;
+    hd->size[1] = H;
+    hd->tiles_x = merged ? 0 : (W + kTile - 1) / kTile;
+    hd->tiles_y = merged ? 0 : (H + kTile - 1) / kTile;
+    hd->n_tiles = hd->tiles_x * hd->tiles_y;
+    hd->n_pixels = W * H;
+    hd->n_tris = n_tris;
+    hd->merged = merged ? 1 : 0;
+    if (!size_ok) raise_status(status, STAR_NT_ERR_ARG);
+  }
+  if (merged) return;  // pass 1 takes this pass over: no triangles binned
+  const int t0 = blockIdx.x * kBinThreads;
+  if (t0 + (int)threadIdx.x < n_tris)
+    triangle_setup(t0 + threadIdx.x, verts, rgba8, vp, W, H, size_ok, bv.setups + t0 + threadIdx.x);
+  __syncthreads();
+  const int tiles_x = (W + kTile - 1) / kTile;
+  for_each_pair(bv, t0, n_tris, tiles_x, s_off,
+                [&](int, int tile) { atomicAdd(bv.tile_count + tile, 1u); });
+}
+
+// Pair lists; positions come from the per-tile cursors, which the tile scan
+// initialised to the tile offsets.
+__global__ void __launch_bounds__(kBinThreads) k_bin_fill(BinsView bv, int n_tris, int32_t *status) {
+  __shared__ int s_off[kBinThreads + 1];
   const BinsHeader *hd = bv.hd;
-  if (fill && (int64_t)hd->n_pairs > bv.pair_capacity) {
-    if (warp == 0 && lane == 0) raise_status(status, STAR_NT_ERR_CAPACITY);
+  if (hd->n_tiles == 0) return;  // empty or merged pass
+  if ((int64_t)hd->n_pairs > bv.pair_capacity) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) raise_status(status, STAR_NT_ERR_CAPACITY);
     return;
   }
-  const TriSetup &T = bv.setups[warp];
-  const int xa = T.xa, xb = T.xb, ya = T.ya, yb = T.yb;
-  if (xa > xb || ya > yb) return;
-  const int tiles_x = hd->tiles_x;
-  const int tx0 = xa / kTile, tx1 = xb / kTile, ty0 = ya / kTile, ty1 = yb / kTile;
-  const int ntx = tx1 - tx0 + 1, nt = ntx * (ty1 - ty0 + 1);
-  int dx[3], dy[3];
-  long long c[3];
-#pragma unroll
-  for (int e = 0; e < 3; ++e) { dx[e] = T.dx[e]; dy[e] = T.dy[e]; c[e] = T.c[e]; }
-  for (int k = lane; k < nt; k += 32) {
-    const int tx = tx0 + k % ntx, ty = ty0 + k / ntx;
-    const int xlo = max(tx * kTile, xa), xhi = min(tx * kTile + kTile - 1, xb);
-    const int ylo = max(ty * kTile, ya), yhi = min(ty * kTile + kTile - 1, yb);
-    const int Pxlo = xlo * kSub + kSub / 2, Pxhi = xhi * kSub + kSub / 2;
-    const int Pylo = ylo * kSub + kSub / 2, Pyhi = yhi * kSub + kSub / 2;
-    bool hit = true;
-#pragma unroll
-    for (int e = 0; e < 3; ++e) {
-      const long long mx = c[e] + (long long)dx[e] * (dx[e] > 0 ? Pyhi : Pylo) -
-                           (long long)dy[e] * (dy[e] > 0 ? Pxlo : Pxhi);
-      if (mx < 0) hit = false;
-    }
-    if (!hit) continue;
-    const int tile = ty * tiles_x + tx;
-    if (!fill) {
-      atomicAdd(bv.tile_count + tile, 1u);
-    } else {
-      const uint32_t pos = bv.tile_offset[tile] + atomicAdd(bv.tile_cursor + tile, 1u);
-      bv.pairs[pos] = (uint32_t)warp;
-    }
-  }
+  for_each_pair(bv, blockIdx.x * kBinThreads, n_tris, hd->tiles_x, s_off, [&](int t, int tile) {
+    bv.pairs[atomicAdd(bv.tile_cursor + tile, 1u)] = (uint32_t)t;
+  });
 }
 
 // ---------------------------------------------------------------------------
@@ -265,6 +330,31 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_final(const uint32_t *__r
   }
 }
 
+// Tile scan in one launch: rounds of 1024 coalesced counts, each scanned
+// across the block and offset by the running total; writes the offsets, the
+// fill cursors (initialised to the offsets) and the total pair count.
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(BinsView bv) {
+  __shared__ uint32_t s_warp[32];
+  const int n = bv.hd->n_tiles;
+  uint32_t carry = 0;
+  for (int base = 0; base < n; base += kScanThreads) {
+    const int i = base + threadIdx.x;
+    const uint32_t v = i < n ? bv.tile_count[i] : 0u;
+    uint32_t tot;
+    const uint32_t ex = block_excl_scan(v, s_warp, &tot) + carry;
+    if (i < n) {
+      bv.tile_offset[i] = ex;
+      bv.tile_cursor[i] = ex;
+    }
+    carry += tot;
+    __syncthreads();  // s_warp is reused by the next round
+  }
+  if (threadIdx.x == 0) {
+    bv.tile_offset[n] = carry;
+    bv.hd->n_pairs = carry;
+  }
+}
+
 cudaError_t scan_exclusive_u32(const uint32_t *in, uint32_t *out, const int32_t *n_dev, int32_t n_max,
                                uint32_t *tmp, uint32_t *total, cudaStream_t st) {
   const int nb = (n_max + kScanBlock - 1) / kScanBlock;
@@ -279,24 +369,30 @@ cudaError_t scan_exclusive_u32(const uint32_t *in, uint32_t *out, const int32_t 
 // ---------------------------------------------------------------------------
 // Materialised fragments: per-pixel counts, then the lists themselves.
 __global__ void __launch_bounds__(256) k_frag_count(BinsView bv, uint32_t *count) {
-  __shared__ TriSetup s_tri[kChunk];
-  __shared__ uint32_t s_id[kChunk];
+  __shared__ TileStage stage;
   const BinsHeader *hd = bv.hd;
   if ((int64_t)hd->n_pairs > bv.pair_capacity) return;
   const int tile = blockIdx.x;
-  if (tile >= hd->n_tiles) return;
   const int W = hd->size[0], H = hd->size[1];
+  if (hd->merged) {  // fragments of a merged pass are not listed: zero counts
+    const int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
+    if (tile < tx * ty) {
+      const TilePixel tp = tile_pixel(tile, tx);
+      if (tp.px < W && tp.py < H) count[tp.py * W + tp.px] = 0;
+    }
+    return;
+  }
+  if (tile >= hd->n_tiles) return;
   const TilePixel tp = tile_pixel(tile, hd->tiles_x);
   uint32_t n = 0;
-  for_each_fragment(bv, tile, tp, s_tri, s_id, [&](const TriSetup &, uint32_t, float) { ++n; });
+  for_each_fragment(bv, tile, tp, stage, [&](const TriSetup &, uint32_t, float) { ++n; });
   if (tp.px < W && tp.py < H) count[tp.py * W + tp.px] = n;
 }
 
 __global__ void __launch_bounds__(256) k_frag_fill(BinsView bv, const uint32_t *offset,
                                                    const uint32_t *total, int64_t capacity,
                                                    float *zs, int32_t *prims, int32_t *status) {
-  __shared__ TriSetup s_tri[kChunk];
-  __shared__ uint32_t s_id[kChunk];
+  __shared__ TileStage stage;
   const BinsHeader *hd = bv.hd;
   if ((int64_t)hd->n_pairs > bv.pair_capacity) return;
   if ((int64_t)*total > capacity) {
@@ -309,7 +405,7 @@ __global__ void __launch_bounds__(256) k_frag_fill(BinsView bv, const uint32_t *
   const TilePixel tp = tile_pixel(tile, hd->tiles_x);
   const bool inside = tp.px < W && tp.py < H;
   uint32_t pos = inside ? offset[tp.py * W + tp.px] : 0u;
-  for_each_fragment(bv, tile, tp, s_tri, s_id, [&](const TriSetup &, uint32_t id, float z) {
+  for_each_fragment(bv, tile, tp, stage, [&](const TriSetup &, uint32_t id, float z) {
     if (inside) {
       zs[pos] = z;
       prims[pos] = (int32_t)id;
@@ -356,15 +452,11 @@ extern "C" star_nt_status star_nt_raster(const star_nt_scene *scene, const star_
   BinsView bv = bins_view(*bins);
   const int T = scene->n_tris;
   cudaMemsetAsync(bv.tile_count, 0, 4 * (size_t)(bv.max_tiles + 1), st);
-  cudaMemsetAsync(bv.tile_cursor, 0, 4 * (size_t)bv.max_tiles, st);
-  k_setup<<<(T + 255) / 256 > 0 ? (T + 255) / 256 : 1, 256, 0, st>>>(
-      scene->verts, scene->rgba8, T, target->view_proj, target->size, bv, d_status);
-  const int bin_blocks = T > 0 ? (T + 7) / 8 : 1;  // 8 warps per block
-  k_bin<<<bin_blocks, 256, 0, st>>>(bv, T, 0, d_status);
-  if (scan_exclusive_u32(bv.tile_count, bv.tile_offset, &bv.hd->n_tiles, bv.max_tiles,
-                         bv.scan_tmp, &bv.hd->n_pairs, st) != cudaSuccess)
-    return STAR_NT_ERR_CUDA;
-  k_bin<<<bin_blocks, 256, 0, st>>>(bv, T, 1, d_status);
+  const int bin_blocks = T > 0 ? (T + kBinThreads - 1) / kBinThreads : 1;
+  k_bin_count<<<bin_blocks, kBinThreads, 0, st>>>(scene->verts, scene->rgba8, T, target->view_proj,
+                                                  target->size, target->merge_at, bv, d_status);
+  k_scan_tiles<<<1, kScanThreads, 0, st>>>(bv);
+  k_bin_fill<<<bin_blocks, kBinThreads, 0, st>>>(bv, T, d_status);
   if (frags) {
     const int P = target->max_w * target->max_h;
     const int tiles = ((target->max_w + kTile - 1) / kTile) * ((target->max_h + kTile - 1) / kTile);

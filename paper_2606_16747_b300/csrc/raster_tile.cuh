@@ -2,9 +2,11 @@
 // kernels.  One CTA of 256 threads owns one 16 x 16-pixel tile; warp w owns
 // the 8 x 4 block at ((w & 1) * 8, (w >> 1) * 4) and lane l the pixel
 // (l & 7, l >> 3) of it.  The tile's binned triangles are staged in shared
-// memory kChunk at a time; a warp skips a triangle whose bounding box misses
-// its block (a warp-uniform branch), otherwise every lane evaluates the three
-// exact int64 edge functions at its pixel centre.
+// memory kChunk at a time.  Each warp then classifies the staged triangles
+// for its own block, one triangle per lane (bounding box, then the three edge
+// functions at the block's most favourable pixel centre, exact in int64),
+// compacts the hits into a warp-private list with a ballot, and walks only
+// that list, evaluating the three exact edge functions at its pixels.
 #pragma once
 
 #include "common.cuh"
@@ -14,14 +16,17 @@ namespace star {
 struct TilePixel {
   int px, py;    // pixel of this thread
   int bx0, by0;  // origin of this warp's 8 x 4 block
+  int tx0, ty0;  // origin of the tile
 };
 
 __device__ __forceinline__ TilePixel tile_pixel(int tile, int tiles_x) {
   const int tx = tile % tiles_x, ty = tile / tiles_x;
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   TilePixel t;
-  t.bx0 = tx * kTile + (w & 1) * 8;
-  t.by0 = ty * kTile + (w >> 1) * 4;
+  t.tx0 = tx * kTile;
+  t.ty0 = ty * kTile;
+  t.bx0 = t.tx0 + (w & 1) * 8;
+  t.by0 = t.ty0 + (w >> 1) * 4;
   t.px = t.bx0 + (l & 7);
   t.py = t.by0 + (l >> 3);
   return t;
@@ -38,12 +43,36 @@ __device__ __forceinline__ float frag_depth(const TriSetup &T, long long e0b, lo
   return __fadd_rn(z, 0.0f);
 }
 
+// May the triangle cover a pixel centre of the 8 x 4 block at (bx0, by0)?
+// False only when it certainly does not (bounding box, or one edge function
+// negative at every centre of the block).
+__device__ __forceinline__ bool block_maybe(const TriSetup &T, int bx0, int by0) {
+  if (T.xb < bx0 || T.xa > bx0 + 7 || T.yb < by0 || T.ya > by0 + 3) return false;
+  const int Pxlo = bx0 * kSub + kSub / 2, Pxhi = Pxlo + 7 * kSub;
+  const int Pylo = by0 * kSub + kSub / 2, Pyhi = Pylo + 3 * kSub;
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    const long long mx = T.c[e] + (long long)T.dx[e] * (T.dx[e] > 0 ? Pyhi : Pylo) -
+                         (long long)T.dy[e] * (T.dy[e] > 0 ? Pxlo : Pxhi);
+    if (mx < 0) return false;
+  }
+  return true;
+}
+
+// Shared-memory staging area of one tile CTA.
+struct TileStage {
+  TriSetup tri[kChunk];
+  uint32_t id[kChunk];
+  uint8_t list[8][kChunk];  // per-warp lists of staged triangle indices
+};
+
 // Calls visit(T, prim_id, depth) for every triangle of the tile covering
 // this thread's pixel centre.  Must be called by all 256 threads.
 template <class Visit>
 __device__ __forceinline__ void for_each_fragment(const BinsView &bv, int tile, const TilePixel &tp,
-                                                  TriSetup *s_tri, uint32_t *s_id, Visit &&visit) {
+                                                  TileStage &st, Visit &&visit) {
   const int Px = tp.px * kSub + kSub / 2, Py = tp.py * kSub + kSub / 2;
+  const int warp = threadIdx.x >> 5;
   const uint32_t beg = bv.tile_offset[tile], end = bv.tile_offset[tile + 1];
   for (uint32_t base = beg; base < end; base += kChunk) {
     const int n = (int)min((uint32_t)kChunk, end - base);
@@ -51,20 +80,29 @@ __device__ __forceinline__ void for_each_fragment(const BinsView &bv, int tile, 
     for (int i = threadIdx.x; i < n * 7; i += blockDim.x) {
       const int k = i / 7, part = i - 7 * k;
       const uint32_t id = __ldg(bv.pairs + base + k);
-      reinterpret_cast<uint4 *>(s_tri + k)[part] =
+      reinterpret_cast<uint4 *>(st.tri + k)[part] =
           __ldg(reinterpret_cast<const uint4 *>(bv.setups + id) + part);
-      if (part == 0) s_id[k] = id;
+      if (part == 0) st.id[k] = id;
     }
     __syncthreads();
-#pragma unroll 2
-    for (int k = 0; k < n; ++k) {
-      const TriSetup &T = s_tri[k];
-      if (T.xb < tp.bx0 || T.xa > tp.bx0 + 7 || T.yb < tp.by0 || T.ya > tp.by0 + 3) continue;
+    const int lane = threadIdx.x & 31;
+    int m = 0;
+    for (int k0 = 0; k0 < n; k0 += 32) {
+      const int k = k0 + lane;
+      const bool hit = k < n && block_maybe(st.tri[k], tp.bx0, tp.by0);
+      const uint32_t b = __ballot_sync(0xffffffffu, hit);
+      if (hit) st.list[warp][m + __popc(b & ((1u << lane) - 1u))] = (uint8_t)k;
+      m += __popc(b);
+    }
+    __syncwarp();
+    for (int i = 0; i < m; ++i) {
+      const int k = st.list[warp][i];
+      const TriSetup &T = st.tri[k];
       const long long e0 = (long long)T.dx[0] * Py + T.c[0] - (long long)T.dy[0] * Px;
       const long long e1 = (long long)T.dx[1] * Py + T.c[1] - (long long)T.dy[1] * Px;
       const long long e2 = (long long)T.dx[2] * Py + T.c[2] - (long long)T.dy[2] * Px;
       if ((e0 | e1 | e2) < 0) continue;
-      visit(T, s_id[k], frag_depth(T, e0, e2));
+      visit(T, st.id[k], frag_depth(T, e0, e2));
     }
   }
 }

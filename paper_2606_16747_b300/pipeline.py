@@ -3,12 +3,12 @@
 Owns the device buffers (torch allocations) and sequences the C-ABI calls:
 
   plain frame     raster (full res) -> fused build_inputs -> infer -> composite
-  STAR-NT frame   raster x3 (full, s2, s3) -> build_inputs (3 passes + upscale)
-                  -> infer -> composite -> quadtree (next frame's s2, s3)
+  STAR-NT frame   raster x3 (full, s2, s3) -> geometry passes 1-3 -> upscale /
+                  features -> infer -> composite -> quadtree (next s2, s3)
   interpolated    reproject from the last real frame (Sec. 3.3, last paragraph)
 
-Pass resolutions live on the device (``state``), so one captured CUDA graph
-per frame kind replays any resolution.
+Pass resolutions and cameras live in device buffers with fixed addresses, so
+one captured CUDA graph replays every frame of a sequence.
 """
 from __future__ import annotations
 
@@ -65,15 +65,13 @@ class Renderer:
         B = self.params.base_tile
         self.n_tiles = math.ceil(self.W / B) * math.ceil(self.H / B)
         self.mask = [torch.zeros(self.n_tiles, **i32), torch.zeros(self.n_tiles, **i32)]
-        self.mask_cur = 0
         self.qt_ws = torch.zeros(sn.quadtree_ws_bytes(self.W, self.H, B), dtype=torch.uint8, device=device)
         self.mlp_tensors = None
         if mlp is not None:
             self.set_mlp(mlp)
         # reprojection
-        self.prev_rgba = torch.zeros(P * 4, **f32)
-        self.prev_z1 = torch.ones(P, **f32)
         self.interp_out = torch.zeros(P * 4, **f32)
+        self.interp_rgba8 = torch.zeros(P, **i32)
         self.vp64_prev = torch.zeros(16, dtype=torch.float64, device=device)
         self.vp64_cur = torch.zeros(16, dtype=torch.float64, device=device)
         self.reproj_ws = torch.zeros(sn.REPROJECT_WS_BYTES, dtype=torch.uint8, device=device)
@@ -94,51 +92,64 @@ class Renderer:
         return self.state[off:off + 8].view(torch.int32)
 
     # -- frames -------------------------------------------------------------
-    def plain_frame(self, stream=None, mark=None):
-        """All passes at full resolution, fused (the plain neural OIT pipeline)."""
-        mark = mark or (lambda name: None)
+    def plain_stages(self, stream=None):
+        """The plain neural OIT pipeline: every pass at full resolution, fused."""
         b = self.bins[0]
-        sn.raster(self.scene, self.vp, self.full_size, self.W, self.H, b, None, self.status, stream)
-        mark("raster")
-        sn.build_inputs(self.scene, b, b, b, self.l1, None, None, self.W, self.H, self.params,
-                        self.x, self.x_dtype, self.front, self.status, stream)
-        mark("pass_fused")
-        sn.infer(self.mlp, self.x_dtype, self.x, self.f, self.P, self.status, stream)
-        mark("infer")
-        sn.composite(self.front, self.f, self.P, self.rgba32f, self.rgba8_out, stream)
-        mark("composite")
+        return [("raster", lambda: sn.raster(self.scene, self.vp, self.full_size, self.W, self.H, b,
+                                            None, self.status, stream)),
+                ("pass_fused", lambda: sn.build_inputs(self.scene, b, b, b, self.l1, None, None,
+                                                       self.W, self.H, self.params, self.x,
+                                                       self.x_dtype, self.front, self.status,
+                                                       stream)),
+                ("infer", lambda: sn.infer(self.mlp, self.x_dtype, self.x, self.f, self.P,
+                                           self.status, stream)),
+                ("composite", lambda: sn.composite(self.front, self.f, self.P, self.rgba32f,
+                                                   self.rgba8_out, stream))]
 
-    def star_frame(self, stream=None, update_tiles=True, mark=None):
-        """Pass 1 at full resolution, passes 2 and 3 at the device-held scales.
-        ``mark(name)`` (optional) is called after each stage is enqueued."""
-        mark = mark or (lambda name: None)
+    def plain_frame(self, stream=None):
+        for _, fn in self.plain_stages(stream):
+            fn()
+
+    def star_stages(self, stream=None, update_tiles=True):
+        """The stages of one real STAR-NT frame as (name, callable) pairs:
+        pass 1 at full resolution, passes 2 and 3 at the device-held sizes."""
         b1, b2, b3 = self.bins
-        sn.raster(self.scene, self.vp, self.full_size, self.W, self.H, b1, None, self.status, stream)
-        sn.raster(self.scene, self.vp, self.state_size(2), self.W, self.H, b2, None, self.status, stream)
-        sn.raster(self.scene, self.vp, self.state_size(3), self.W, self.H, b3, None, self.status, stream)
-        mark("raster")
-        sn.geometry_pass(self.scene, b1, 1, self.l1, self.status, stream)
-        mark("pass1")
-        sn.geometry_pass(self.scene, b2, 2, self.l2, self.status, stream)
-        mark("pass2")
-        sn.geometry_pass(self.scene, b3, 3, self.l3, self.status, stream)
-        mark("pass3")
-        sn.upscale_features(self.scene, b2, b3, self.l1, self.l2, self.l3, self.W, self.H,
-                            self.params, self.x, self.x_dtype, self.front, stream)
-        mark("features")
-        sn.infer(self.mlp, self.x_dtype, self.x, self.f, self.P, self.status, stream)
-        mark("infer")
-        sn.composite(self.front, self.f, self.P, self.rgba32f, self.rgba8_out, stream)
-        mark("composite")
+
+        def raster():
+            sn.raster(self.scene, self.vp, self.full_size, self.W, self.H, b1, None, self.status, stream)
+            # passes 2 and 3 at full size are taken over by pass 1 (merged)
+            sn.raster(self.scene, self.vp, self.state_size(2), self.W, self.H, b2, None, self.status,
+                      stream, merge_at=self.full_size)
+            sn.raster(self.scene, self.vp, self.state_size(3), self.W, self.H, b3, None, self.status,
+                      stream, merge_at=self.full_size)
+
+        st = [("raster", raster),
+              ("pass1", lambda: sn.geometry_pass_merged(self.scene, b1, b2, b3, self.l1, self.l2,
+                                                        self.l3, self.status, stream)),
+              ("pass2", lambda: sn.geometry_pass(self.scene, b2, 2, self.l2, self.status, stream)),
+              ("pass3", lambda: sn.geometry_pass(self.scene, b3, 3, self.l3, self.status, stream)),
+              ("features", lambda: sn.upscale_features(self.scene, b2, b3, self.l1, self.l2, self.l3,
+                                                       self.W, self.H, self.params, self.x,
+                                                       self.x_dtype, self.front, stream)),
+              ("infer", lambda: sn.infer(self.mlp, self.x_dtype, self.x, self.f, self.P, self.status,
+                                         stream)),
+              ("composite", lambda: sn.composite(self.front, self.f, self.P, self.rgba32f,
+                                                 self.rgba8_out, stream))]
         if update_tiles:
-            self.update_tiles(stream)
-            mark("quadtree")
+            st.append(("quadtree", lambda: self.update_tiles(stream)))
+        return st
+
+    def star_frame(self, stream=None, update_tiles=True):
+        for _, fn in self.star_stages(stream, update_tiles):
+            fn()
 
     def update_tiles(self, stream=None):
-        src, dst = self.mask[self.mask_cur], self.mask[1 - self.mask_cur]
-        sn.quadtree(self.rgba8_out, self.l1["id1"], self.W, self.H, self.params, src, dst,
-                    self.state, self.qt_ws, stream)
-        self.mask_cur = 1 - self.mask_cur
+        """Quadtree update from this frame; the new masks become the previous
+        ones by a device copy so that buffer addresses never change (one
+        captured graph serves every frame)."""
+        sn.quadtree(self.rgba8_out, self.l1["id1"], self.W, self.H, self.params, self.mask[0],
+                    self.mask[1], self.state, self.qt_ws, stream)
+        self.mask[0].copy_(self.mask[1])
 
     def _infer_composite(self, stream):
         if self.mlp_tensors is None:
@@ -146,17 +157,42 @@ class Renderer:
         sn.infer(self.mlp, self.x_dtype, self.x, self.f, self.P, self.status, stream)
         sn.composite(self.front, self.f, self.P, self.rgba32f, self.rgba8_out, stream)
 
-    def keep_as_previous(self, vp64):
-        """Remember this real frame for later interpolated frames."""
-        self.prev_rgba.copy_(self.rgba32f)
-        self.prev_z1.copy_(self.l1["z1"])
-        self.vp64_prev.copy_(torch.as_tensor(np.asarray(vp64, np.float64).reshape(16)))
+    def set_cameras(self, vp32=None, vp64_real=None, vp64_interp=None):
+        """Copy camera matrices into the device buffers the frames read
+        (arrays or device tensors)."""
+        for dst, src, dt in ((self.vp, vp32, np.float32), (self.vp64_prev, vp64_real, np.float64),
+                             (self.vp64_cur, vp64_interp, np.float64)):
+            if src is None:
+                continue
+            if isinstance(src, torch.Tensor):
+                dst.copy_(src, non_blocking=True)
+            else:
+                dst.copy_(torch.as_tensor(np.asarray(src, dt).reshape(16)))
 
-    def interp_frame(self, vp64_cur=None, stream=None):
-        if vp64_cur is not None:
-            self.vp64_cur.copy_(torch.as_tensor(np.asarray(vp64_cur, np.float64).reshape(16)))
-        sn.reproject(self.prev_rgba, self.prev_z1, self.vp64_prev, self.vp64_cur, self.W, self.H,
-                     self.interp_out, self.reproj_ws, stream)
+    def interp_frame(self, stream=None):
+        """Interpolated frame from the last real frame (its colour and pass-1
+        depth stay in ``rgba32f`` and ``l1['z1']`` until the next real frame);
+        camera matrices from ``vp64_prev`` (real) and ``vp64_cur``."""
+        sn.reproject(self.rgba32f, self.l1["z1"], self.vp64_prev, self.vp64_cur, self.W, self.H,
+                     self.interp_out, self.reproj_ws, stream, out_rgba8=self.interp_rgba8)
+
+    def step(self, stream=None):
+        """One real STAR-NT frame followed by one interpolated frame."""
+        self.star_frame(stream)
+        self.interp_frame(stream)
+
+    def capture(self, fn):
+        """Capture ``fn`` (enqueueing work on the current stream) as a CUDA
+        graph after one eager warm-up run."""
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            fn()
+        torch.cuda.current_stream().wait_stream(side)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn()
+        return g
 
     def pass_state(self):
         return sn.read_pass_state(self.state)

@@ -23,7 +23,8 @@ F32, BF16 = 0, 1
 EXPORTS = ("star_nt_version", "star_nt_status_string", "star_nt_default_params",
            "star_nt_bins_bytes", "star_nt_raster", "star_nt_build_inputs", "star_nt_infer",
            "star_nt_composite", "star_nt_quadtree_ws_bytes", "star_nt_quadtree",
-           "star_nt_reproject", "star_nt_geometry_pass", "star_nt_upscale_features")
+           "star_nt_reproject", "star_nt_geometry_pass", "star_nt_upscale_features",
+           "star_nt_geometry_pass_merged")
 
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
@@ -35,7 +36,7 @@ class Scene(ctypes.Structure):
 
 
 class Target(ctypes.Structure):
-    _fields_ = [("view_proj", _P), ("size", _P), ("max_w", _I32), ("max_h", _I32)]
+    _fields_ = [("view_proj", _P), ("size", _P), ("max_w", _I32), ("max_h", _I32), ("merge_at", _P)]
 
 
 class Params(ctypes.Structure):
@@ -104,6 +105,8 @@ def lib():
                                             ctypes.POINTER(Features), _P, _P]
         L.star_nt_geometry_pass.argtypes = [ctypes.POINTER(Scene), ctypes.POINTER(Bins), _I32,
                                             ctypes.POINTER(Layers), _P, _P]
+        L.star_nt_geometry_pass_merged.argtypes = [ctypes.POINTER(Scene)] + [ctypes.POINTER(Bins)] * 3 + \
+            [ctypes.POINTER(Layers)] * 3 + [_P, _P]
         L.star_nt_upscale_features.argtypes = [ctypes.POINTER(Scene)] + [ctypes.POINTER(Bins)] * 2 + \
             [ctypes.POINTER(Layers)] * 3 + [_I32, _I32, ctypes.POINTER(Params),
                                             ctypes.POINTER(Features), _P]
@@ -112,7 +115,7 @@ def lib():
         L.star_nt_quadtree_ws_bytes.argtypes = [_I32, _I32, _I32, ctypes.POINTER(ctypes.c_size_t)]
         L.star_nt_quadtree.argtypes = [_P, _P, _I32, _I32, ctypes.POINTER(Params), _P, _P, _P, _P,
                                        ctypes.c_size_t, _P]
-        L.star_nt_reproject.argtypes = [_P, _P, _P, _P, _I32, _I32, _P, _P, _P]
+        L.star_nt_reproject.argtypes = [_P, _P, _P, _P, _I32, _I32, _P, _P, _P, _P]
         for name in EXPORTS:
             if name not in ("star_nt_default_params", "star_nt_status_string", "star_nt_version"):
                 getattr(L, name).restype = _I32
@@ -170,8 +173,10 @@ def scene_struct(verts, rgba8) -> Scene:
     return Scene(verts.data_ptr(), rgba8.data_ptr(), int(rgba8.shape[0]))
 
 
-def raster(scene: Scene, vp, size, max_w, max_h, bins: BinsBuffer, frags=None, status=None, stream=None):
-    tgt = Target(vp.data_ptr(), size.data_ptr(), max_w, max_h)
+def raster(scene: Scene, vp, size, max_w, max_h, bins: BinsBuffer, frags=None, status=None, stream=None,
+           merge_at=None):
+    tgt = Target(vp.data_ptr(), size.data_ptr(), max_w, max_h,
+                 merge_at.data_ptr() if merge_at is not None else None)
     fr = None
     if frags is not None:
         fr = Frags(frags["count"].data_ptr(), frags["offset"].data_ptr(), frags["z"].data_ptr(),
@@ -204,6 +209,14 @@ def geometry_pass(scene: Scene, bins, mode, layers, status=None, stream=None):
     _check("star_nt_geometry_pass", lib().star_nt_geometry_pass(ctypes.byref(scene), ctypes.byref(bins.c),
                                                                 mode, ctypes.byref(l), _ptr(status),
                                                                 _stream(stream)))
+
+
+def geometry_pass_merged(scene: Scene, bins1, bins2, bins3, layers1, layers2, layers3, status=None,
+                         stream=None):
+    ls = [layers_struct(l) for l in (layers1, layers2, layers3)]
+    _check("star_nt_geometry_pass_merged", lib().star_nt_geometry_pass_merged(
+        ctypes.byref(scene), ctypes.byref(bins1.c), ctypes.byref(bins2.c), ctypes.byref(bins3.c),
+        *[ctypes.byref(l) for l in ls], _ptr(status), _stream(stream)))
 
 
 def upscale_features(scene: Scene, bins2, bins3, layers1, layers2, layers3, W, H, params: Params,
@@ -245,12 +258,13 @@ def quadtree(rgba8, id1, W, H, params: Params, mask_prev, mask_out, state, ws, s
 REPROJECT_WS_BYTES = 64
 
 
-def reproject(prev_rgba, prev_z1, vp_prev, vp_cur, W, H, out_rgba, ws=None, stream=None):
+def reproject(prev_rgba, prev_z1, vp_prev, vp_cur, W, H, out_rgba, ws=None, stream=None,
+              out_rgba8=None):
     if ws is None:
         ws = torch.empty(REPROJECT_WS_BYTES, dtype=torch.uint8, device=out_rgba.device)
     _check("star_nt_reproject", lib().star_nt_reproject(_ptr(prev_rgba), _ptr(prev_z1), _ptr(vp_prev),
-                                                        _ptr(vp_cur), W, H, _ptr(out_rgba), _ptr(ws),
-                                                        _stream(stream)))
+                                                        _ptr(vp_cur), W, H, _ptr(out_rgba),
+                                                        _ptr(out_rgba8), _ptr(ws), _stream(stream)))
 
 
 def read_pass_state(state_tensor) -> dict:

@@ -73,10 +73,10 @@ def test_bad_arguments_rejected_before_launch(sn):
     assert L.star_nt_infer(ctypes.byref(w), sn.F32, 8, 16, 10, None, None) == sn.ERR_ARG  # misaligned
     assert L.star_nt_infer(ctypes.byref(w), sn.BF16, 16, 16, 10, None, None) == sn.ERR_ARG  # not 256-aligned
     assert L.star_nt_composite(16, 16, -1, 16, 16, None) == sn.ERR_ARG
-    assert L.star_nt_reproject(16, 16, 16, 16, 0, 10, 32, 48, None) == sn.ERR_ARG
-    assert L.star_nt_reproject(16, 16, 16, 16, 10, 10, 16, 48, None) == sn.ERR_ARG       # in place
-    assert L.star_nt_reproject(16, 16, 16, 16, 10, 10, 32, None, None) == sn.ERR_ARG     # no scratch
+    assert L.star_nt_reproject(16, 16, 16, 16, 0, 10, 32, None, 48, None) == sn.ERR_ARG
+    assert L.star_nt_reproject(16, 16, 16, 16, 10, 10, 16, None, 48, None) == sn.ERR_ARG  # in place
+    assert L.star_nt_reproject(16, 16, 16, 16, 10, 10, 32, None, None, None) == sn.ERR_ARG  # no scratch
     p = sn.default_params()
     assert L.star_nt_quadtree(16, 16, 64, 64, ctypes.byref(p), 16, 16, 16, 256, 1 << 20, None) == sn.ERR_ARG
-    p.tau_merge = 30.0
+    p.tau_merge = p.tau_split + 1.0
     assert L.star_nt_quadtree(16, 16, 64, 64, ctypes.byref(p), 16, 32, 16, 256, 1 << 20, None) == sn.ERR_ARG

@@ -221,6 +221,38 @@ def test_three_pass_layers_and_features(orc, sn):
     assert np.max(np.abs(rgb - o["rgb"])) <= TOL_FRAME
 
 
+@pytest.mark.parametrize("sizes", [("full", "reduced"), ("reduced", "full"), ("full", "full")])
+def test_merged_passes(orc, sn, sizes):
+    """A pass whose device-side size equals the full size is taken over by
+    pass 1 (merged); results equal the oracle's three passes at those sizes."""
+    from paper_2606_16747_b300.pipeline import Renderer
+    sc = scenes.screen_scene(23, 2500, 208, 144, size_scale=0.7)
+    W, H = sc.width, sc.height
+    s2 = (W, H) if sizes[0] == "full" else (131, 91)
+    s3 = (W, H) if sizes[1] == "full" else (57, 40)
+    mlp = scenes.mlp_xavier(4)
+    r = Renderer(sc.verts, sc.rgba8, W, H, mlp=mlp)
+    r.set_camera(sc.cam.vp32)
+    r.state.view(torch.int32)[:6] = torch.tensor([W, H, *s2, *s3], dtype=torch.int32)
+    r.star_frame(update_tiles=False)
+    torch.cuda.synchronize()
+    r.check_status()
+    hdr2 = r.bins[1].mem[:64].view(torch.int32).cpu().numpy()
+    hdr3 = r.bins[2].mem[:64].view(torch.int32).cpu().numpy()
+    assert hdr2[8] == (sizes[0] == "full") and hdr3[8] == (sizes[1] == "full")
+    o = orc.frame_star(sc.verts, sc.rgba8, sc.cam.vp32, W, H, s2, s3, scenes.mlp_flat(mlp), threads=4)
+    assert np.array_equal(r.l1["id1"].cpu().numpy(), o["r1"]["id1"])
+    assert np.array_equal(r.l2["id2"].cpu().numpy()[:s2[0] * s2[1]], o["r2"]["id2"])
+    n3 = s3[0] * s3[1]
+    assert np.array_equal(r.l3["n"].cpu().numpy()[:n3].view(np.uint32), o["r3"]["n"])
+    tail = r.l3["tail"].cpu().numpy().view(np.uint32).reshape(-1, 4)[:n3]
+    assert np.array_equal(tail[:, 0], o["r3"]["a_tail"]) and np.array_equal(tail[:, 1:], o["r3"]["s_tail"])
+    front = r.front.cpu().numpy().reshape(-1, 4)
+    assert np.max(np.abs(front - o["front"])) <= TOL_FEAT
+    rgb = r.rgba32f.cpu().numpy().reshape(-1, 4)[:, :3]
+    assert np.max(np.abs(rgb - o["rgb"])) <= TOL_FRAME
+
+
 def test_t_tail_opaque_tail_and_determinism(orc, sn):
     """Opaque fragments in the tail give t_tail = 0 exactly; two runs of the
     same frame agree bit for bit."""
@@ -359,7 +391,7 @@ def test_quadtree_sequence_matches_oracle(orc, sn):
     for k in range(5):
         img = blocky_image(rng, W, H, 4)
         sn.quadtree(dev(img.view(np.int32)), dev(id1), W, H, params, mg[k % 2], mg[1 - k % 2], state, ws)
-        mo, _ = orc.quadtree(img, id1, W, H, B, 24.0, 12.0, mo)
+        mo, _ = orc.quadtree(img, id1, W, H, B, params.tau_split, params.tau_merge, mo)
         torch.cuda.synchronize()
         assert np.array_equal(u32(mg[1 - k % 2]), mo)
 
@@ -378,11 +410,19 @@ def test_reproject(orc, sn, W, H, dtheta):
     vp_prev = scenes.camera(W, H, 10.0).vp64
     vp_cur = scenes.camera(W, H, 10.0 + dtheta).vp64
     out = torch.zeros(W * H * 4, device="cuda")
-    sn.reproject(dev(prev.reshape(-1)), dev(z1), dev(vp_prev.reshape(-1)), dev(vp_cur.reshape(-1)), W, H, out)
+    q = torch.zeros(W * H, dtype=torch.int32, device="cuda")
+    sn.reproject(dev(prev.reshape(-1)), dev(z1), dev(vp_prev.reshape(-1)), dev(vp_cur.reshape(-1)), W, H, out,
+                 out_rgba8=q)
     torch.cuda.synchronize()
     ref = orc.reproject(prev, z1, vp_prev, vp_cur, W, H)
     got = out.cpu().numpy().reshape(-1, 4)
     assert np.max(np.abs(got - ref)) <= TOL_FRAME
+    # the 8-bit copy quantises the float result: round half to even of
+    # clamp(c, 0, 1) * 255, the product taken in float32 as the kernel does
+    c = np.clip(got[:, :3], 0.0, 1.0).astype(np.float32) * np.float32(255.0)
+    qc = np.rint(c).astype(np.uint32)
+    qo = qc[:, 0] | (qc[:, 1] << 8) | (qc[:, 2] << 16) | np.uint32(0xFF000000)
+    assert np.array_equal(u32(q), qo)
 
 
 def test_reproject_identity(orc, sn):
