@@ -320,6 +320,40 @@ star_nt_status star_nt_reproject(const float *prev_rgba, const float *prev_z1,
                                  int32_t H, float *out_rgba, uint32_t *out_rgba8, void *ws,
                                  void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* Exact resolve and training of the tail network.                          */
+
+/* star_nt_abuffer -- exact order-independent transparency, the ground truth
+ * of the evaluation (Sec. 4): each pixel's materialised fragments (frags of a
+ * W x H pass, from star_nt_raster) sorted by (z, primitive id) and
+ * composited front to back over bg.  rgb: [P][4] (colour, total
+ * transmittance) or NULL; tail: [P][4] the exact tail colour (fragments 3..N
+ * composited among themselves, the quantity f(x) predicts in Eq. 4) and the
+ * tail transmittance, or NULL.  float32 arithmetic. */
+star_nt_status star_nt_abuffer(const star_nt_frags *frags, const uint32_t *rgba8, int32_t W,
+                               int32_t H, const float *bg, float *rgb, float *tail, void *stream);
+
+/* Training of the tail MLP with MSE and Adam (Sec. 3.3).  All buffers device
+ * memory; ws: scratch of star_nt_train_ws_bytes(B) bytes (256-byte aligned).
+ * star_nt_mse_grad: f, y [B][4] (rgb used) -> dy [B][4] = dL/df and the loss
+ *   L = mean over B x 3 of (f - y)^2 (one float).
+ * star_nt_mlp_backward: gradient of L with respect to the 771 parameters
+ *   (w1, b1, w2, b2, w3, b3 order) for inputs x [B][8] float32 (STAR_NT_F32
+ *   layout) and dy; the forward pass is recomputed in float32 with w;
+ *   deterministic (fixed summation order).
+ * star_nt_adam: bias-corrected Adam step `step` (from 1) on the float32
+ *   master parameters; bf16_rounded (may be NULL) receives them rounded to
+ *   bfloat16 precision, stored as float32 (the weights of the next forward). */
+size_t star_nt_train_ws_bytes(int64_t B);
+star_nt_status star_nt_mse_grad(const float *f, const float *y, int64_t B, float *dy, float *loss,
+                                void *ws, size_t ws_bytes, void *stream);
+star_nt_status star_nt_mlp_backward(const star_nt_mlp *w, const float *x, const float *dy,
+                                    int64_t B, float *grad, void *ws, size_t ws_bytes,
+                                    void *stream);
+star_nt_status star_nt_adam(float *params, const float *grad, float *m, float *v, int64_t n,
+                            int64_t step, float lr, float beta1, float beta2, float eps,
+                            float *bf16_rounded, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -24,7 +24,8 @@ EXPORTS = ("star_nt_version", "star_nt_status_string", "star_nt_default_params",
            "star_nt_bins_bytes", "star_nt_raster", "star_nt_build_inputs", "star_nt_infer",
            "star_nt_composite", "star_nt_quadtree_ws_bytes", "star_nt_quadtree",
            "star_nt_reproject", "star_nt_geometry_pass", "star_nt_upscale_features",
-           "star_nt_geometry_pass_merged")
+           "star_nt_geometry_pass_merged", "star_nt_abuffer", "star_nt_train_ws_bytes",
+           "star_nt_mse_grad", "star_nt_mlp_backward", "star_nt_adam")
 
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
@@ -116,8 +117,16 @@ def lib():
         L.star_nt_quadtree.argtypes = [_P, _P, _I32, _I32, ctypes.POINTER(Params), _P, _P, _P, _P,
                                        ctypes.c_size_t, _P]
         L.star_nt_reproject.argtypes = [_P, _P, _P, _P, _I32, _I32, _P, _P, _P, _P]
+        L.star_nt_abuffer.argtypes = [ctypes.POINTER(Frags), _P, _I32, _I32, _P, _P, _P, _P]
+        L.star_nt_train_ws_bytes.argtypes = [_I64]
+        L.star_nt_train_ws_bytes.restype = ctypes.c_size_t
+        L.star_nt_mse_grad.argtypes = [_P, _P, _I64, _P, _P, _P, ctypes.c_size_t, _P]
+        L.star_nt_mlp_backward.argtypes = [ctypes.POINTER(Mlp), _P, _P, _I64, _P, _P, ctypes.c_size_t, _P]
+        L.star_nt_adam.argtypes = [_P, _P, _P, _P, _I64, _I64, ctypes.c_float, ctypes.c_float,
+                                   ctypes.c_float, ctypes.c_float, _P, _P]
         for name in EXPORTS:
-            if name not in ("star_nt_default_params", "star_nt_status_string", "star_nt_version"):
+            if name not in ("star_nt_default_params", "star_nt_status_string", "star_nt_version",
+                            "star_nt_train_ws_bytes"):
                 getattr(L, name).restype = _I32
         _lib = L
     return _lib
@@ -273,3 +282,40 @@ def read_pass_state(state_tensor) -> dict:
     st = PassState.from_buffer_copy(raw[:PASS_STATE_BYTES])
     return dict(W=st.W, H=st.H, W2=st.W2, H2=st.H2, W3=st.W3, H3=st.H3, s2=st.s2, s3=st.s3,
                 wbar=st.wbar, hist=list(st.hist))
+
+
+# ---------------------------------------------------------------------------
+# exact resolve and training
+
+def frags_struct(frags) -> Frags:
+    return Frags(frags["count"].data_ptr(), frags["offset"].data_ptr(), frags["z"].data_ptr(),
+                 frags["prim"].data_ptr(), int(frags["z"].numel()), frags["total"].data_ptr())
+
+
+def abuffer(frags, rgba8, W, H, bg, rgb=None, tail=None, stream=None):
+    f = frags_struct(frags)
+    bgt = (ctypes.c_float * 3)(*bg)
+    _check("star_nt_abuffer", lib().star_nt_abuffer(ctypes.byref(f), _ptr(rgba8), W, H, bgt, _ptr(rgb),
+                                                    _ptr(tail), _stream(stream)))
+
+
+def train_ws_bytes(B):
+    return int(lib().star_nt_train_ws_bytes(int(B)))
+
+
+def mse_grad(f, y, B, dy, loss, ws, stream=None):
+    _check("star_nt_mse_grad", lib().star_nt_mse_grad(_ptr(f), _ptr(y), int(B), _ptr(dy), _ptr(loss),
+                                                      _ptr(ws), ws.numel(), _stream(stream)))
+
+
+def mlp_backward(w: Mlp, x, dy, B, grad, ws, stream=None):
+    _check("star_nt_mlp_backward", lib().star_nt_mlp_backward(ctypes.byref(w), _ptr(x), _ptr(dy), int(B),
+                                                              _ptr(grad), _ptr(ws), ws.numel(),
+                                                              _stream(stream)))
+
+
+def adam(params, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, bf16_rounded=None,
+         stream=None):
+    _check("star_nt_adam", lib().star_nt_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), params.numel(),
+                                              int(step), lr, beta1, beta2, eps, _ptr(bf16_rounded),
+                                              _stream(stream)))
