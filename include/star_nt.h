@@ -143,6 +143,13 @@ star_nt_status star_nt_raster(const star_nt_scene *scene, const star_nt_target *
                               const star_nt_bins *bins, const star_nt_frags *frags_or_null,
                               int32_t *d_status, void *stream);
 
+/* The front end of up to three passes at once (targets[i] into bins[i],
+ * distinct workspaces), in the same three launches: the frame's passes share
+ * each launch instead of running one after another.  No fragment lists. */
+star_nt_status star_nt_raster_passes(const star_nt_scene *scene, int32_t n_passes,
+                                     const star_nt_target *targets, const star_nt_bins *bins,
+                                     int32_t *d_status, void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* star_nt_build_inputs -- the three geometry passes and the network input    */
 /* (Sec. 3.2, Sec. 3.3, Eq. 4).                                              */

@@ -12,7 +12,50 @@ namespace star {
 // shared memory (every lane reads the same weight: broadcast).
 constexpr int kW1 = 0, kB1 = 160, kW2 = 192, kB2 = 704, kW3 = 720, kB3 = 768;
 
-__global__ void __launch_bounds__(256) k_mlp_f32(const float *__restrict__ w1, const float *__restrict__ b1,
+// Two pixels per thread: every shared-memory weight read feeds two FMAs.
+__device__ __forceinline__ void mlp_f32_pair(const float *s, const float (&xa)[5], const float (&xb)[5],
+                                             float (&fa)[3], float (&fb)[3]) {
+  float ha[32], hb[32];
+#pragma unroll
+  for (int o = 0; o < 32; ++o) {
+    float a = s[kB1 + o], b = a;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      const float w = s[kW1 + 5 * o + i];
+      a = fmaf(w, xa[i], a);
+      b = fmaf(w, xb[i], b);
+    }
+    ha[o] = fmaxf(a, 0.0f);
+    hb[o] = fmaxf(b, 0.0f);
+  }
+  float ga[16], gb[16];
+#pragma unroll
+  for (int o = 0; o < 16; ++o) {
+    float a = s[kB2 + o], b = a;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      const float w = s[kW2 + 32 * o + i];
+      a = fmaf(w, ha[i], a);
+      b = fmaf(w, hb[i], b);
+    }
+    ga[o] = fmaxf(a, 0.0f);
+    gb[o] = fmaxf(b, 0.0f);
+  }
+#pragma unroll
+  for (int o = 0; o < 3; ++o) {
+    float a = s[kB3 + o], b = a;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const float w = s[kW3 + 16 * o + i];
+      a = fmaf(w, ga[i], a);
+      b = fmaf(w, gb[i], b);
+    }
+    fa[o] = fmaxf(a, 0.0f);
+    fb[o] = fmaxf(b, 0.0f);
+  }
+}
+
+__global__ void __launch_bounds__(256, 2) k_mlp_f32(const float *__restrict__ w1, const float *__restrict__ b1,
                                                  const float *__restrict__ w2, const float *__restrict__ b2,
                                                  const float *__restrict__ w3, const float *__restrict__ b3,
                                                  const float4 *__restrict__ X, float4 *__restrict__ F,
@@ -25,41 +68,26 @@ __global__ void __launch_bounds__(256) k_mlp_f32(const float *__restrict__ w1, c
   if (threadIdx.x < 48) s[kW3 + threadIdx.x] = w3[threadIdx.x];
   if (threadIdx.x < 3) s[kB3 + threadIdx.x] = b3[threadIdx.x];
   __syncthreads();
-  for (long long p = (long long)blockIdx.x * 256 + threadIdx.x; p < P; p += (long long)gridDim.x * 256) {
-    const float4 xa = X[2 * p], xb = X[2 * p + 1];
-    if (xb.y == 0.0f) {  // empty tail
-      F[p] = make_float4(0.f, 0.f, 0.f, 0.f);
-      continue;
+  const long long half = (P + 1) / 2;  // thread i takes pixels i and i + half
+  for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < half; i += (long long)gridDim.x * 256) {
+    const long long pa = i, pb = i + half;
+    const bool hb = pb < P;
+    const float4 xa0 = X[2 * pa], xa1 = X[2 * pa + 1];
+    float4 xb0 = make_float4(0.f, 0.f, 0.f, 0.f), xb1 = xb0;
+    if (hb) {
+      xb0 = X[2 * pb];
+      xb1 = X[2 * pb + 1];
     }
-    const float x[5] = {xa.x, xa.y, xa.z, xa.w, xb.x};
-    float h1[32];
-#pragma unroll
-    for (int o = 0; o < 32; ++o) {
-      float a = s[kB1 + o];
-#pragma unroll
-      for (int i = 0; i < 5; ++i) a = fmaf(s[kW1 + 5 * o + i], x[i], a);
-      h1[o] = fmaxf(a, 0.0f);
-    }
-    float h2[16];
-#pragma unroll
-    for (int o = 0; o < 16; ++o) {
-      float a = s[kB2 + o];
-#pragma unroll
-      for (int i = 0; i < 32; ++i) a = fmaf(s[kW2 + 32 * o + i], h1[i], a);
-      h2[o] = fmaxf(a, 0.0f);
-    }
-    float f[3];
-#pragma unroll
-    for (int o = 0; o < 3; ++o) {
-      float a = s[kB3 + o];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) a = fmaf(s[kW3 + 16 * o + i], h2[i], a);
-      f[o] = fmaxf(a, 0.0f);
-    }
-    F[p] = make_float4(f[0], f[1], f[2], 0.0f);
+    const float xa[5] = {xa0.x, xa0.y, xa0.z, xa0.w, xa1.x};
+    const float xb[5] = {xb0.x, xb0.y, xb0.z, xb0.w, xb1.x};
+    float fa[3], fb[3];
+    mlp_f32_pair(s, xa, xb, fa, fb);
+    F[pa] = xa1.y == 0.0f ? make_float4(0.f, 0.f, 0.f, 0.f) : make_float4(fa[0], fa[1], fa[2], 0.0f);
+    if (hb) F[pb] = xb1.y == 0.0f ? make_float4(0.f, 0.f, 0.f, 0.f) : make_float4(fb[0], fb[1], fb[2], 0.0f);
   }
 }
 
+// ---------------------------------------------------------------------------
 // 8-bit RGBA of a float colour: round half to even of clamp(c, 0, 1) * 255,
 // alpha 255.
 __device__ __forceinline__ uint32_t quantize_rgba8(float4 c) {

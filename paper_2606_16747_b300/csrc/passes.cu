@@ -44,11 +44,14 @@ __device__ __forceinline__ float tail_transmittance(unsigned long long lg, uint3
   return ldexpf(exp2f(-frac), -(int)k);
 }
 
+// straight RGBA8 to float (c8 / 255, by a multiply: within one rounding of
+// the quotient)
 __device__ __forceinline__ void unpack_rgba(uint32_t c, float &r, float &g, float &b, float &a) {
-  r = (float)(c & 255u) / 255.0f;
-  g = (float)((c >> 8) & 255u) / 255.0f;
-  b = (float)((c >> 16) & 255u) / 255.0f;
-  a = (float)(c >> 24) / 255.0f;
+  constexpr float k = 1.0f / 255.0f;
+  r = (float)(c & 255u) * k;
+  g = (float)((c >> 8) & 255u) * k;
+  b = (float)((c >> 16) & 255u) * k;
+  a = (float)(c >> 24) * k;
 }
 
 // Network input row and front terms of one full-resolution pixel.
@@ -67,10 +70,10 @@ __device__ __forceinline__ void write_features(const FeatOut &fo, size_t p, floa
   float x[6];
   x[0] = n * fo.kappa;
   x[1] = t;
-  const float den = 255.0f * A;
-  x[2] = A > 0.0f ? Sr / den : 0.0f;
-  x[3] = A > 0.0f ? Sg / den : 0.0f;
-  x[4] = A > 0.0f ? Sb / den : 0.0f;
+  const float inv = A > 0.0f ? __frcp_rn(255.0f * A) : 0.0f;
+  x[2] = Sr * inv;
+  x[3] = Sg * inv;
+  x[4] = Sb * inv;
   x[5] = flag ? 1.0f : 0.0f;
   if (fo.x_dtype == STAR_NT_F32) {
     float4 *X = reinterpret_cast<float4 *>(fo.x) + 2 * p;
@@ -169,7 +172,7 @@ __global__ void __launch_bounds__(256) k_pass(BinsView bv, const uint32_t *__res
 // Pass 1 at full resolution; when pass 2 and/or pass 3 are marked merged
 // (their size equals the full size) it keeps the two nearest fragments and
 // the tail sums as well and writes their planes at full resolution.
-__global__ void __launch_bounds__(256) k_pass_merged(BinsView bv, const BinsHeader *hd2,
+__global__ void __launch_bounds__(256, 6) k_pass_merged(BinsView bv, const BinsHeader *hd2,
                                                      const BinsHeader *hd3,
                                                      const uint32_t *__restrict__ rgba8, PassOut o1,
                                                      PassOut o2, PassOut o3) {
@@ -189,6 +192,9 @@ __global__ void __launch_bounds__(256) k_pass_merged(BinsView bv, const BinsHead
 
 // Full-resolution features from pass 1 (full res) and the bilinear upscale
 // of passes 2 and 3 (their own resolutions, read from their bins headers).
+// All plane loads are issued before any of them is used (the sample indices
+// are clamped, so every load is valid) to keep many requests in flight; zero
+// bilinear weights then drop their samples exactly.
 __global__ void __launch_bounds__(256) k_features(int W, int H, const BinsHeader *hd2,
                                                   const BinsHeader *hd3,
                                                   const uint32_t *__restrict__ rgba8,
@@ -202,62 +208,67 @@ __global__ void __launch_bounds__(256) k_features(int W, int H, const BinsHeader
   if (x >= W || y >= H) return;
   if (hd2->n_pixels <= 0 || hd3->n_pixels <= 0) return;  // a pass was rejected
   const size_t p = (size_t)y * W + x;
-  float r1 = 0, g1 = 0, b1 = 0, a1 = 0;
-  const int i1 = id1[p];
-  if (i1 >= 0) unpack_rgba(__ldg(rgba8 + i1), r1, g1, b1, a1);
-
-  // pass 2: premultiplied second layer and its alpha
   const int W2 = hd2->size[0], H2 = hd2->size[1];
-  const Axis ax2 = upscale_axis(x, W2, W), ay2 = upscale_axis(y, H2, H);
-  const float wx2 = (float)ax2.rem / (float)ax2.den, wy2 = (float)ay2.rem / (float)ay2.den;
-  float L2[4] = {0, 0, 0, 0};
-  {
-    const int xs[2] = {ax2.i0, ax2.i1}, ys[2] = {ay2.i0, ay2.i1};
-    const float wxs[2] = {1.0f - wx2, wx2}, wys[2] = {1.0f - wy2, wy2};
-#pragma unroll
-    for (int j = 0; j < 2; ++j)
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const float w = wys[j] * wxs[i];
-        if (w == 0.0f) continue;  // exact zero weight: sample not needed
-        const int id = id2[(size_t)ys[j] * W2 + xs[i]];
-        if (id < 0) continue;
-        float r, g, b, a;
-        unpack_rgba(__ldg(rgba8 + id), r, g, b, a);
-        L2[0] += w * (a * r);
-        L2[1] += w * (a * g);
-        L2[2] += w * (a * b);
-        L2[3] += w * a;
-      }
-  }
-  // pass 3: count, tail sums and tail transmittance
   const int W3 = hd3->size[0], H3 = hd3->size[1];
+  const Axis ax2 = upscale_axis(x, W2, W), ay2 = upscale_axis(y, H2, H);
   const Axis ax3 = upscale_axis(x, W3, W), ay3 = upscale_axis(y, H3, H);
-  const float wx3 = (float)ax3.rem / (float)ax3.den, wy3 = (float)ay3.rem / (float)ay3.den;
+  size_t q2[4], q3[4];
+  q2[0] = (size_t)ay2.i0 * W2 + ax2.i0; q2[1] = (size_t)ay2.i0 * W2 + ax2.i1;
+  q2[2] = (size_t)ay2.i1 * W2 + ax2.i0; q2[3] = (size_t)ay2.i1 * W2 + ax2.i1;
+  q3[0] = (size_t)ay3.i0 * W3 + ax3.i0; q3[1] = (size_t)ay3.i0 * W3 + ax3.i1;
+  q3[2] = (size_t)ay3.i1 * W3 + ax3.i0; q3[3] = (size_t)ay3.i1 * W3 + ax3.i1;
+  // issue every plane load
+  const int i1 = __ldg(id1 + p);
+  int i2[4];
+  uint32_t nn[4];
+  uint4 tl[4];
+  float tt[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    i2[k] = __ldg(id2 + q2[k]);
+    nn[k] = __ldg(n3 + q3[k]);
+    tl[k] = __ldg(tail3 + q3[k]);
+    tt[k] = __ldg(t3 + q3[k]);
+  }
+  // colour gathers (independent of each other)
+  const uint32_t c1 = i1 >= 0 ? __ldg(rgba8 + i1) : 0u;
+  uint32_t c2[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) c2[k] = i2[k] >= 0 ? __ldg(rgba8 + i2[k]) : 0u;
+
+  float r1, g1, b1, a1;
+  unpack_rgba(c1, r1, g1, b1, a1);
+  const float rx = __frcp_rn((float)ax2.den), ry = __frcp_rn((float)ay2.den);
+  const float wx2 = (float)ax2.rem * rx, wy2 = (float)ay2.rem * ry;
+  const float w2[4] = {(1.0f - wy2) * (1.0f - wx2), (1.0f - wy2) * wx2, wy2 * (1.0f - wx2), wy2 * wx2};
+  float L2[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (w2[k] == 0.0f || i2[k] < 0) continue;
+    float r, g, b, a;
+    unpack_rgba(c2[k], r, g, b, a);
+    L2[0] += w2[k] * (a * r);
+    L2[1] += w2[k] * (a * g);
+    L2[2] += w2[k] * (a * b);
+    L2[3] += w2[k] * a;
+  }
+  const float wx3 = (float)ax3.rem * rx, wy3 = (float)ay3.rem * ry;  // same denominators 2W, 2H
+  const float w3[4] = {(1.0f - wy3) * (1.0f - wx3), (1.0f - wy3) * wx3, wy3 * (1.0f - wx3), wy3 * wx3};
+  const long long wi3[4] = {(long long)(ay3.den - ay3.rem) * (ax3.den - ax3.rem),
+                            (long long)(ay3.den - ay3.rem) * ax3.rem,
+                            (long long)ay3.rem * (ax3.den - ax3.rem), (long long)ay3.rem * ax3.rem};
   float nf = 0, A = 0, Sr = 0, Sg = 0, Sb = 0, t = 0;
   long long nexact = 0;  // upscaled N times (2W)(2H), exact
-  {
-    const int xs[2] = {ax3.i0, ax3.i1}, ys[2] = {ay3.i0, ay3.i1};
-    const float wxs[2] = {1.0f - wx3, wx3}, wys[2] = {1.0f - wy3, wy3};
-    const long long wxi[2] = {ax3.den - ax3.rem, ax3.rem}, wyi[2] = {ay3.den - ay3.rem, ay3.rem};
 #pragma unroll
-    for (int j = 0; j < 2; ++j)
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const long long wi = wyi[j] * wxi[i];
-        if (wi == 0) continue;  // exact zero weight
-        const size_t q = (size_t)ys[j] * W3 + xs[i];
-        const float w = wys[j] * wxs[i];
-        const uint32_t nn = n3[q];
-        const uint4 tl = tail3[q];
-        nf += w * (float)nn;
-        A += w * (float)tl.x;
-        Sr += w * (float)tl.y;
-        Sg += w * (float)tl.z;
-        Sb += w * (float)tl.w;
-        t += w * t3[q];
-        nexact += wi * (long long)nn;
-      }
+  for (int k = 0; k < 4; ++k) {
+    if (wi3[k] == 0) continue;  // exact zero weight
+    nf += w3[k] * (float)nn[k];
+    A += w3[k] * (float)tl[k].x;
+    Sr += w3[k] * (float)tl[k].y;
+    Sg += w3[k] * (float)tl[k].z;
+    Sb += w3[k] * (float)tl[k].w;
+    t += w3[k] * tt[k];
+    nexact += wi3[k] * (long long)nn[k];
   }
   const bool flag = nexact > 2LL * ax3.den * ay3.den;
   write_features(fo, p, a1, r1, g1, b1, L2[0], L2[1], L2[2], L2[3], nf, A, Sr, Sg, Sb, t, flag);

@@ -48,6 +48,35 @@ __device__ __forceinline__ bool node_exists(uint32_t m, int k) {
   return (m & 1u) && ((m >> (1 + c1)) & 1u);
 }
 
+// Cells (level-3 cells, row-major bit index 8 cy + cx) covered by node k:
+// k < 21 is the node of mask bit k, k >= 21 the level-3 cell k - 21.
+struct RegionTable {
+  unsigned long long m[85];
+};
+constexpr RegionTable make_regions() {
+  RegionTable t{};
+  for (int k = 0; k < 85; ++k) {
+    int l = 3, i = 0, j = 0;
+    if (k == 0) {
+      l = 0;
+    } else if (k < 5) {
+      l = 1; i = (k - 1) & 1; j = (k - 1) >> 1;
+    } else if (k < 21) {
+      const int q = k - 5, c1 = q >> 2, c2 = q & 3;
+      l = 2; i = (c1 & 1) * 2 + (c2 & 1); j = (c1 >> 1) * 2 + (c2 >> 1);
+    } else {
+      i = (k - 21) & 7; j = (k - 21) >> 3;
+    }
+    const int span = 8 >> l;
+    unsigned long long r = 0;
+    for (int b = 0; b < span; ++b)
+      for (int a = 0; a < span; ++a) r |= 1ull << ((j * span + b) * 8 + (i * span + a));
+    t.m[k] = r;
+  }
+  return t;
+}
+__constant__ RegionTable kRegions = make_regions();
+
 // level of the leaf covering level-3 cell (cx, cy) of a tile, 0 <= cx, cy < 8
 __device__ __forceinline__ int cell_level(uint32_t m, int cx, int cy) {
   if (!(m & 1u)) return 0;
@@ -143,119 +172,124 @@ __global__ void __launch_bounds__(256) k_qt_decide(const uint32_t *__restrict__ 
   if (lane == 0) mout[tile] = (m | split_bits) & ~merge_bits;
 }
 
-__global__ void __launch_bounds__(256) k_qt_relax(int tiles_x, int tiles_y,
+// One relaxation iteration (Jacobi: reads min, writes mout), warp per tile.
+// With LAST, the warp then counts the occupied leaves of its tile's final
+// mask, and the last block to finish applies Eq. 2 and writes the state.
+__device__ __forceinline__ bool relax_split(uint32_t m, uint32_t mL, uint32_t mR, uint32_t mU,
+                                            uint32_t mD, int tx, int ty, int tiles_x, int tiles_y,
+                                            int lane) {
+  if (lane >= 21) return false;
+  int l, i, j;
+  node_of_bit(lane, l, i, j);
+  if (!(node_exists(m, lane) && !((m >> lane) & 1u))) return false;
+  const int span = 8 >> l, cx0 = i * span, cy0 = j * span;
+  int deepest = 0;
+  for (int k = 0; k < span; ++k) {
+    // left / right columns and top / bottom rows just outside the leaf
+    if (cx0 > 0) deepest = max(deepest, cell_level(m, cx0 - 1, cy0 + k));
+    else if (tx > 0) deepest = max(deepest, cell_level(mL, 7, cy0 + k));
+    if (cx0 + span < 8) deepest = max(deepest, cell_level(m, cx0 + span, cy0 + k));
+    else if (tx + 1 < tiles_x) deepest = max(deepest, cell_level(mR, 0, cy0 + k));
+    if (cy0 > 0) deepest = max(deepest, cell_level(m, cx0 + k, cy0 - 1));
+    else if (ty > 0) deepest = max(deepest, cell_level(mU, cx0 + k, 7));
+    if (cy0 + span < 8) deepest = max(deepest, cell_level(m, cx0 + k, cy0 + span));
+    else if (ty + 1 < tiles_y) deepest = max(deepest, cell_level(mD, cx0 + k, 0));
+  }
+  return deepest >= l + 2;
+}
+
+template <bool RELAX, bool LAST>
+__global__ void __launch_bounds__(256) k_qt_relax(const int32_t *__restrict__ id1, int W, int H, int B,
+                                                  int tiles_x, int tiles_y,
                                                   const uint32_t *__restrict__ min,
-                                                  uint32_t *__restrict__ mout) {
+                                                  uint32_t *__restrict__ mout,
+                                                  uint32_t *__restrict__ hist, uint32_t *ticket,
+                                                  double delta2, double delta3,
+                                                  star_nt_pass_state *state) {
+  __shared__ uint32_t s_hist[4];
+  if (LAST) {
+    if (threadIdx.x < 4) s_hist[threadIdx.x] = 0u;
+    __syncthreads();
+  }
   const int tile = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
-  if (tile >= tiles_x * tiles_y) return;
-  const int tx = tile % tiles_x, ty = tile / tiles_x;
-  const uint32_t m = min[tile];
-  const uint32_t mL = tx > 0 ? min[tile - 1] : 0u, mR = tx + 1 < tiles_x ? min[tile + 1] : 0u;
-  const uint32_t mU = ty > 0 ? min[tile - tiles_x] : 0u;
-  const uint32_t mD = ty + 1 < tiles_y ? min[tile + tiles_x] : 0u;
-  bool split = false;
-  if (lane < 21) {
-    int l, i, j;
-    node_of_bit(lane, l, i, j);
-    if (node_exists(m, lane) && !((m >> lane) & 1u)) {
-      const int span = 8 >> l, cx0 = i * span, cy0 = j * span;
-      int deepest = 0;
-      for (int k = 0; k < span; ++k) {
-        // left / right columns and top / bottom rows just outside the leaf
-        if (cx0 > 0) deepest = max(deepest, cell_level(m, cx0 - 1, cy0 + k));
-        else if (tx > 0) deepest = max(deepest, cell_level(mL, 7, cy0 + k));
-        if (cx0 + span < 8) deepest = max(deepest, cell_level(m, cx0 + span, cy0 + k));
-        else if (tx + 1 < tiles_x) deepest = max(deepest, cell_level(mR, 0, cy0 + k));
-        if (cy0 > 0) deepest = max(deepest, cell_level(m, cx0 + k, cy0 - 1));
-        else if (ty > 0) deepest = max(deepest, cell_level(mU, cx0 + k, 7));
-        if (cy0 + span < 8) deepest = max(deepest, cell_level(m, cx0 + k, cy0 + span));
-        else if (ty + 1 < tiles_y) deepest = max(deepest, cell_level(mD, cx0 + k, 0));
+  if (tile < tiles_x * tiles_y) {
+    const int tx = tile % tiles_x, ty = tile / tiles_x;
+    uint32_t m = min[tile];
+    if (RELAX) {
+      const uint32_t mL = tx > 0 ? min[tile - 1] : 0u, mR = tx + 1 < tiles_x ? min[tile + 1] : 0u;
+      const uint32_t mU = ty > 0 ? min[tile - tiles_x] : 0u;
+      const uint32_t mD = ty + 1 < tiles_y ? min[tile + tiles_x] : 0u;
+      m |= __ballot_sync(0xffffffffu, relax_split(m, mL, mR, mU, mD, tx, ty, tiles_x, tiles_y, lane));
+    }
+    if (lane == 0) mout[tile] = m;
+    if (LAST) {
+      // occupancy of the tile's 64 level-3 cells (B/8 pixels wide)
+      const int cs = B / 8;
+      unsigned long long occ = 0;
+      for (int k = lane; k < B * B; k += 32) {
+        const int lx = k % B, ly = k / B;
+        const int x = tx * B + lx, y = ty * B + ly;
+        if (x < W && y < H && id1[(size_t)y * W + x] >= 0) occ |= 1ull << ((ly / cs) * 8 + (lx / cs));
       }
-      split = deepest >= l + 2;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) occ |= __shfl_xor_sync(0xffffffffu, occ, o);
+      // leaves: lanes own the 21 nodes of levels 0..2, then the 64 level-3 cells
+      uint32_t cnt[4] = {0, 0, 0, 0};
+      for (int k = lane; k < 21 + 64; k += 32) {
+        int l, i, j;
+        bool isleaf;
+        if (k < 21) {
+          node_of_bit(k, l, i, j);
+          isleaf = node_exists(m, k) && !((m >> k) & 1u);
+        } else {
+          l = 3;
+          i = (k - 21) & 7;
+          j = (k - 21) >> 3;
+          isleaf = cell_level(m, i, j) == 3;
+        }
+        if (isleaf && (occ & kRegions.m[k])) ++cnt[l];
+      }
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        uint32_t c = cnt[l];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (lane == 0 && c) atomicAdd(&s_hist[l], c);
+      }
     }
   }
-  const uint32_t bits = __ballot_sync(0xffffffffu, split);
-  if (lane == 0) mout[tile] = m | bits;
-}
-
-// Occupied leaves per level: a leaf is occupied when one of its pixels has
-// a nearest fragment (id1 >= 0).  One CTA per tile; occupancy is gathered
-// per level-3 cell (B/8 pixels wide) into a 64-bit mask.
-__global__ void __launch_bounds__(256) k_qt_hist(const int32_t *__restrict__ id1, int W, int H, int B,
-                                                 int tiles_x, const uint32_t *__restrict__ mask,
-                                                 uint32_t *__restrict__ hist) {
-  __shared__ uint32_t s_occ[2];
-  __shared__ uint32_t s_hist[4];
-  const int tile = blockIdx.x;
-  const int tx = tile % tiles_x, ty = tile / tiles_x;
-  if (threadIdx.x < 2) s_occ[threadIdx.x] = 0u;
-  if (threadIdx.x < 4) s_hist[threadIdx.x] = 0u;
+  if (!LAST) return;
   __syncthreads();
-  const int cs = B / 8;
-  uint32_t lo = 0, hi = 0;
-  for (int k = threadIdx.x; k < B * B; k += 256) {
-    const int lx = k % B, ly = k / B;
-    const int x = tx * B + lx, y = ty * B + ly;
-    if (x < W && y < H && id1[(size_t)y * W + x] >= 0) {
-      const int cell = (ly / cs) * 8 + (lx / cs);
-      if (cell < 32) lo |= 1u << cell;
-      else hi |= 1u << (cell - 32);
+  if (threadIdx.x == 0) {
+    for (int l = 0; l < 4; ++l)
+      if (s_hist[l]) atomicAdd(hist + l, s_hist[l]);
+    __threadfence();
+    const uint32_t done = atomicAdd(ticket, 1u);
+    if (done == gridDim.x - 1) {  // last block: every histogram update is visible
+      __threadfence();
+      const uint32_t h0 = atomicAdd(hist + 0, 0u), h1 = atomicAdd(hist + 1, 0u);
+      const uint32_t h2 = atomicAdd(hist + 2, 0u), h3 = atomicAdd(hist + 3, 0u);
+      const double tot = (double)h0 + (double)h1 + (double)h2 + (double)h3;
+      const double wbar = tot > 0.0 ? ((double)h1 + 2.0 * (double)h2 + 3.0 * (double)h3) / tot : 0.0;
+      double s2 = exp2(wbar - delta2), s3 = exp2(wbar - delta3);
+      s2 = s2 < 0.25 ? 0.25 : (s2 > 1.0 ? 1.0 : s2);
+      s3 = s3 < 0.25 ? 0.25 : (s3 > 1.0 ? 1.0 : s3);
+      state->W = W;
+      state->H = H;
+      state->W2 = (int32_t)ceil(s2 * (double)W);
+      state->H2 = (int32_t)ceil(s2 * (double)H);
+      state->W3 = (int32_t)ceil(s3 * (double)W);
+      state->H3 = (int32_t)ceil(s3 * (double)H);
+      state->s2 = (float)s2;
+      state->s3 = (float)s3;
+      state->wbar = wbar;
+      state->hist[0] = h0;
+      state->hist[1] = h1;
+      state->hist[2] = h2;
+      state->hist[3] = h3;
     }
   }
-  if (lo) atomicOr(&s_occ[0], lo);
-  if (hi) atomicOr(&s_occ[1], hi);
-  __syncthreads();
-  const unsigned long long occ = (unsigned long long)s_occ[0] | ((unsigned long long)s_occ[1] << 32);
-  const uint32_t m = mask[tile];
-  const int k = threadIdx.x;
-  if (k < 21 + 64) {
-    int l, i, j;
-    bool isleaf;
-    if (k < 21) {
-      node_of_bit(k, l, i, j);
-      isleaf = node_exists(m, k) && !((m >> k) & 1u);
-    } else {
-      l = 3;
-      i = (k - 21) & 7;
-      j = (k - 21) >> 3;
-      isleaf = cell_level(m, i, j) == 3;
-    }
-    if (isleaf) {
-      const int span = 8 >> l;
-      unsigned long long reg = 0;
-      for (int b = 0; b < span; ++b)
-        for (int a = 0; a < span; ++a) reg |= 1ull << ((j * span + b) * 8 + (i * span + a));
-      if (occ & reg) atomicAdd(&s_hist[l], 1u);
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x < 4 && s_hist[threadIdx.x]) atomicAdd(hist + threadIdx.x, s_hist[threadIdx.x]);
-}
-
-// Eq. 2 and the next frame's pass sizes.
-__global__ void k_qt_finalize(const uint32_t *__restrict__ hist, int W, int H, double delta2,
-                              double delta3, star_nt_pass_state *state) {
-  if (threadIdx.x != 0) return;
-  const uint32_t h0 = hist[0], h1 = hist[1], h2 = hist[2], h3 = hist[3];
-  const double tot = (double)h0 + (double)h1 + (double)h2 + (double)h3;
-  const double wbar = tot > 0.0 ? ((double)h1 + 2.0 * (double)h2 + 3.0 * (double)h3) / tot : 0.0;
-  double s2 = exp2(wbar - delta2), s3 = exp2(wbar - delta3);
-  s2 = s2 < 0.25 ? 0.25 : (s2 > 1.0 ? 1.0 : s2);
-  s3 = s3 < 0.25 ? 0.25 : (s3 > 1.0 ? 1.0 : s3);
-  state->W = W;
-  state->H = H;
-  state->W2 = (int32_t)ceil(s2 * (double)W);
-  state->H2 = (int32_t)ceil(s2 * (double)H);
-  state->W3 = (int32_t)ceil(s3 * (double)W);
-  state->H3 = (int32_t)ceil(s3 * (double)H);
-  state->s2 = (float)s2;
-  state->s3 = (float)s3;
-  state->wbar = wbar;
-  state->hist[0] = h0;
-  state->hist[1] = h1;
-  state->hist[2] = h2;
-  state->hist[3] = h3;
 }
 
 }  // namespace star
@@ -291,18 +325,25 @@ extern "C" star_nt_status star_nt_quadtree(const uint32_t *rgba8, const int32_t 
   const int nt = L.tiles_x * L.tiles_y;
   const int wblocks = (nt + 7) / 8;
   const int iters = params->relax_iters;
-  cudaMemsetAsync(hist, 0, 16, st);
-  uint32_t *dst = iters == 0 ? mask_out : ma;
+  cudaMemsetAsync(hist, 0, 32, st);  // histogram and the last-block ticket
+  uint32_t *ticket = hist + 4;
   k_qt_decide<<<wblocks, 256, 0, st>>>(rgba8, W, H, B, L.tiles_x, nt, 6.0 * params->tau_split,
-                                       6.0 * params->tau_merge, mask_prev, dst);
-  const uint32_t *src = dst;
-  for (int it = 0; it < iters; ++it) {
-    uint32_t *d = it == iters - 1 ? mask_out : (src == ma ? mb : ma);
-    k_qt_relax<<<wblocks, 256, 0, st>>>(L.tiles_x, L.tiles_y, src, d);
+                                       6.0 * params->tau_merge, mask_prev, ma);
+  const uint32_t *src = ma;
+  for (int it = 0; it + 1 < iters; ++it) {  // all but the last relaxation
+    uint32_t *d = src == ma ? mb : ma;
+    k_qt_relax<true, false><<<wblocks, 256, 0, st>>>(id1, W, H, B, L.tiles_x, L.tiles_y, src, d, hist,
+                                                     ticket, params->delta2, params->delta3, state);
     src = d;
   }
-  k_qt_hist<<<nt, 256, 0, st>>>(id1, W, H, B, L.tiles_x, mask_out, hist);
-  k_qt_finalize<<<1, 32, 0, st>>>(hist, W, H, params->delta2, params->delta3, state);
+  // the last relaxation (a plain copy when there is none), the histogram of
+  // occupied leaves and Eq. 2, in one launch
+  if (iters > 0)
+    k_qt_relax<true, true><<<wblocks, 256, 0, st>>>(id1, W, H, B, L.tiles_x, L.tiles_y, src, mask_out,
+                                                    hist, ticket, params->delta2, params->delta3, state);
+  else
+    k_qt_relax<false, true><<<wblocks, 256, 0, st>>>(id1, W, H, B, L.tiles_x, L.tiles_y, src, mask_out,
+                                                     hist, ticket, params->delta2, params->delta3, state);
   return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
 }
 

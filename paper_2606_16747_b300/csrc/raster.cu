@@ -187,14 +187,23 @@ __device__ __forceinline__ void for_each_pair(const BinsView &bv, int t0, int n_
   }
 }
 
+// Up to three passes are binned by the same launches (blockIdx.y = pass).
+constexpr int kMaxPasses = 3;
+struct PassSet {
+  BinsView bv[kMaxPasses];
+  const float *vp[kMaxPasses];
+  const int32_t *size[kMaxPasses];
+  const int32_t *merge_at[kMaxPasses];
+};
+
 // Set-up (one triangle per thread) and per-tile candidate counts.
 __global__ void __launch_bounds__(kBinThreads) k_bin_count(const float *__restrict__ verts,
                                                            const uint32_t *__restrict__ rgba8,
-                                                           int n_tris, const float *__restrict__ vp,
-                                                           const int32_t *__restrict__ size,
-                                                           const int32_t *__restrict__ merge_at,
-                                                           BinsView bv, int32_t *status) {
+                                                           int n_tris, PassSet ps, int32_t *status) {
   __shared__ int s_off[kBinThreads + 1];
+  const BinsView &bv = ps.bv[blockIdx.y];
+  const int32_t *size = ps.size[blockIdx.y];
+  const int32_t *merge_at = ps.merge_at[blockIdx.y];
   int W, H;
   const bool size_ok = pass_size(size, bv, W, H);
   const bool merged = size_ok && merge_at && W == merge_at[0] && H == merge_at[1];
@@ -213,7 +222,8 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(const float *__restri
   if (merged) return;  // pass 1 takes this pass over: no triangles binned
   const int t0 = blockIdx.x * kBinThreads;
   if (t0 + (int)threadIdx.x < n_tris)
-    triangle_setup(t0 + threadIdx.x, verts, rgba8, vp, W, H, size_ok, bv.setups + t0 + threadIdx.x);
+    triangle_setup(t0 + threadIdx.x, verts, rgba8, ps.vp[blockIdx.y], W, H, size_ok,
+                   bv.setups + t0 + threadIdx.x);
   __syncthreads();
   const int tiles_x = (W + kTile - 1) / kTile;
   for_each_pair(bv, t0, n_tris, tiles_x, s_off,
@@ -222,8 +232,9 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(const float *__restri
 
 // Pair lists; positions come from the per-tile cursors, which the tile scan
 // initialised to the tile offsets.
-__global__ void __launch_bounds__(kBinThreads) k_bin_fill(BinsView bv, int n_tris, int32_t *status) {
+__global__ void __launch_bounds__(kBinThreads) k_bin_fill(PassSet ps, int n_tris, int32_t *status) {
   __shared__ int s_off[kBinThreads + 1];
+  const BinsView &bv = ps.bv[blockIdx.y];
   const BinsHeader *hd = bv.hd;
   if (hd->n_tiles == 0) return;  // empty or merged pass
   if ((int64_t)hd->n_pairs > bv.pair_capacity) {
@@ -333,8 +344,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_final(const uint32_t *__r
 // Tile scan in one launch: rounds of 1024 coalesced counts, each scanned
 // across the block and offset by the running total; writes the offsets, the
 // fill cursors (initialised to the offsets) and the total pair count.
-__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(BinsView bv) {
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(PassSet ps) {
   __shared__ uint32_t s_warp[32];
+  const BinsView &bv = ps.bv[blockIdx.x];
   const int n = bv.hd->n_tiles;
   uint32_t carry = 0;
   for (int base = 0; base < n; base += kScanThreads) {
@@ -427,14 +439,10 @@ extern "C" star_nt_status star_nt_bins_bytes(int32_t max_w, int32_t max_h, int32
   return STAR_NT_OK;
 }
 
-extern "C" star_nt_status star_nt_raster(const star_nt_scene *scene, const star_nt_target *target,
-                                         const star_nt_bins *bins, const star_nt_frags *frags,
-                                         int32_t *d_status, void *stream) {
-  if (!scene || !target || !bins || !bins->mem || !target->view_proj || !target->size)
-    return STAR_NT_ERR_ARG;
-  if (scene->n_tris < 0 || scene->n_tris > bins->max_tris ||
-      (scene->n_tris > 0 && (!scene->verts || !scene->rgba8)))
-    return STAR_NT_ERR_ARG;
+static star_nt_status check_pass(const star_nt_scene *scene, const star_nt_target *target,
+                                 const star_nt_bins *bins) {
+  if (!target || !bins || !bins->mem || !target->view_proj || !target->size) return STAR_NT_ERR_ARG;
+  if (scene->n_tris > bins->max_tris) return STAR_NT_ERR_ARG;
   if (target->max_w <= 0 || target->max_h <= 0 || target->max_w > bins->max_w ||
       target->max_h > bins->max_h)
     return STAR_NT_ERR_ARG;
@@ -443,29 +451,57 @@ extern "C" star_nt_status star_nt_raster(const star_nt_scene *scene, const star_
           STAR_NT_OK ||
       bins->bytes < need || ((uintptr_t)bins->mem & 255u))
     return STAR_NT_ERR_ARG;
-  if (((uintptr_t)scene->verts & 15u))
+  return STAR_NT_OK;
+}
+
+extern "C" star_nt_status star_nt_raster_passes(const star_nt_scene *scene, int32_t n_passes,
+                                                const star_nt_target *targets,
+                                                const star_nt_bins *bins, int32_t *d_status,
+                                                void *stream) {
+  if (!scene || !targets || !bins || n_passes < 1 || n_passes > kMaxPasses) return STAR_NT_ERR_ARG;
+  if (scene->n_tris < 0 || (scene->n_tris > 0 && (!scene->verts || !scene->rgba8)) ||
+      ((uintptr_t)scene->verts & 15u))
     return STAR_NT_ERR_ARG;
+  PassSet ps = {};
+  for (int i = 0; i < n_passes; ++i) {
+    const star_nt_status s = check_pass(scene, targets + i, bins + i);
+    if (s != STAR_NT_OK) return s;
+    for (int j = 0; j < i; ++j)
+      if (bins[j].mem == bins[i].mem) return STAR_NT_ERR_ARG;  // distinct workspaces
+    ps.bv[i] = bins_view(bins[i]);
+    ps.vp[i] = targets[i].view_proj;
+    ps.size[i] = targets[i].size;
+    ps.merge_at[i] = targets[i].merge_at;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int T = scene->n_tris;
+  for (int i = 0; i < n_passes; ++i)
+    cudaMemsetAsync(ps.bv[i].tile_count, 0, 4 * (size_t)(ps.bv[i].max_tiles + 1), st);
+  const dim3 grid(T > 0 ? (T + kBinThreads - 1) / kBinThreads : 1, n_passes);
+  k_bin_count<<<grid, kBinThreads, 0, st>>>(scene->verts, scene->rgba8, T, ps, d_status);
+  k_scan_tiles<<<n_passes, kScanThreads, 0, st>>>(ps);
+  k_bin_fill<<<grid, kBinThreads, 0, st>>>(ps, T, d_status);
+  return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
+}
+
+extern "C" star_nt_status star_nt_raster(const star_nt_scene *scene, const star_nt_target *target,
+                                         const star_nt_bins *bins, const star_nt_frags *frags,
+                                         int32_t *d_status, void *stream) {
+  if (!scene || !target || !bins) return STAR_NT_ERR_ARG;
   if (frags && (!frags->count || !frags->offset || !frags->total ||
                 (frags->capacity > 0 && (!frags->z || !frags->prim)) || frags->capacity < 0))
     return STAR_NT_ERR_ARG;
+  star_nt_status s = star_nt_raster_passes(scene, 1, target, bins, d_status, stream);
+  if (s != STAR_NT_OK || !frags) return s;
   cudaStream_t st = (cudaStream_t)stream;
   BinsView bv = bins_view(*bins);
-  const int T = scene->n_tris;
-  cudaMemsetAsync(bv.tile_count, 0, 4 * (size_t)(bv.max_tiles + 1), st);
-  const int bin_blocks = T > 0 ? (T + kBinThreads - 1) / kBinThreads : 1;
-  k_bin_count<<<bin_blocks, kBinThreads, 0, st>>>(scene->verts, scene->rgba8, T, target->view_proj,
-                                                  target->size, target->merge_at, bv, d_status);
-  k_scan_tiles<<<1, kScanThreads, 0, st>>>(bv);
-  k_bin_fill<<<bin_blocks, kBinThreads, 0, st>>>(bv, T, d_status);
-  if (frags) {
-    const int P = target->max_w * target->max_h;
-    const int tiles = ((target->max_w + kTile - 1) / kTile) * ((target->max_h + kTile - 1) / kTile);
-    k_frag_count<<<tiles, 256, 0, st>>>(bv, frags->count);
-    if (scan_exclusive_u32(frags->count, frags->offset, &bv.hd->n_pixels, P, bv.scan_tmp,
-                           frags->total, st) != cudaSuccess)
-      return STAR_NT_ERR_CUDA;
-    k_frag_fill<<<tiles, 256, 0, st>>>(bv, frags->offset, frags->total, frags->capacity, frags->z,
-                                       frags->prim, d_status);
-  }
+  const int P = target->max_w * target->max_h;
+  const int tiles = ((target->max_w + kTile - 1) / kTile) * ((target->max_h + kTile - 1) / kTile);
+  k_frag_count<<<tiles, 256, 0, st>>>(bv, frags->count);
+  if (scan_exclusive_u32(frags->count, frags->offset, &bv.hd->n_pixels, P, bv.scan_tmp, frags->total,
+                         st) != cudaSuccess)
+    return STAR_NT_ERR_CUDA;
+  k_frag_fill<<<tiles, 256, 0, st>>>(bv, frags->offset, frags->total, frags->capacity, frags->z,
+                                     frags->prim, d_status);
   return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
 }

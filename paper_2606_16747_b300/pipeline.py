@@ -116,12 +116,12 @@ class Renderer:
         b1, b2, b3 = self.bins
 
         def raster():
-            sn.raster(self.scene, self.vp, self.full_size, self.W, self.H, b1, None, self.status, stream)
-            # passes 2 and 3 at full size are taken over by pass 1 (merged)
-            sn.raster(self.scene, self.vp, self.state_size(2), self.W, self.H, b2, None, self.status,
-                      stream, merge_at=self.full_size)
-            sn.raster(self.scene, self.vp, self.state_size(3), self.W, self.H, b3, None, self.status,
-                      stream, merge_at=self.full_size)
+            # the three passes share the binning launches; passes 2 and 3 at
+            # full size are taken over by pass 1 (merged)
+            sn.raster_passes(self.scene, [
+                (self.vp, self.full_size, self.W, self.H, b1, None),
+                (self.vp, self.state_size(2), self.W, self.H, b2, self.full_size),
+                (self.vp, self.state_size(3), self.W, self.H, b3, self.full_size)], self.status, stream)
 
         st = [("raster", raster),
               ("pass1", lambda: sn.geometry_pass_merged(self.scene, b1, b2, b3, self.l1, self.l2,

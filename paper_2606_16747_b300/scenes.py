@@ -135,13 +135,16 @@ def _coherent_rgb(rng: np.random.Generator, u, v, jitter: float = 12.0, freq: fl
 
 def screen_scene(seed: int, n_tris: int, width: int, height: int,
                  size_px=(4.0, 400.0), size_scale: float = 1.0,
-                 alpha=(0.1, 0.9), depth=(1.0, 10.0), colours: str = "uniform") -> Scene:
+                 alpha=(0.1, 0.9), depth=(1.0, 10.0), colours: str = "uniform",
+                 depth_jitter: float = 0.05) -> Scene:
     """Triangles sized in screen space: centre uniform on screen, size s
     log-uniform in ``size_px`` (times ``size_scale``), the three vertices uniform
-    in the s x s square around the centre, per-vertex view depth uniform in
-    ``depth``, unprojected to world space (frame-0 camera).  ``colours`` is
-    "uniform" (each channel uniform in 0..255) or "coherent" (smooth over the
-    screen, see _coherent_rgb)."""
+    in the s x s square around the centre; each triangle gets a view depth
+    uniform in ``depth`` and each vertex that depth times 1 + U(-j, j), so
+    triangles roughly face the camera (a moving camera sees them at a similar
+    size instead of as long slivers); unprojected to world space (frame-0
+    camera).  ``colours`` is "uniform" (each channel uniform in 0..255) or
+    "coherent" (smooth over the screen, see _coherent_rgb)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     cx = rng.uniform(0.0, width, size=n_tris)
     cy = rng.uniform(0.0, height, size=n_tris)
@@ -151,7 +154,8 @@ def screen_scene(seed: int, n_tris: int, width: int, height: int,
     sy = cy[:, None] + off[..., 1]
     ndc_x = 2.0 * sx / width - 1.0
     ndc_y = 1.0 - 2.0 * sy / height
-    d = rng.uniform(depth[0], depth[1], size=(n_tris, 3))
+    dc = rng.uniform(depth[0], depth[1], size=(n_tris, 1))
+    d = dc * (1.0 + rng.uniform(-depth_jitter, depth_jitter, size=(n_tris, 3)))
     v = _unproject(ndc_x, ndc_y, d, width / height).astype(np.float32)
     rgba = _pack_rgba(rng, n_tris, *alpha)
     if colours == "coherent":

@@ -25,7 +25,7 @@ EXPORTS = ("star_nt_version", "star_nt_status_string", "star_nt_default_params",
            "star_nt_composite", "star_nt_quadtree_ws_bytes", "star_nt_quadtree",
            "star_nt_reproject", "star_nt_geometry_pass", "star_nt_upscale_features",
            "star_nt_geometry_pass_merged", "star_nt_abuffer", "star_nt_train_ws_bytes",
-           "star_nt_mse_grad", "star_nt_mlp_backward", "star_nt_adam")
+           "star_nt_mse_grad", "star_nt_mlp_backward", "star_nt_adam", "star_nt_raster_passes")
 
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
@@ -101,6 +101,8 @@ def lib():
         L.star_nt_bins_bytes.argtypes = [_I32, _I32, _I32, _I64, ctypes.POINTER(ctypes.c_size_t)]
         L.star_nt_raster.argtypes = [ctypes.POINTER(Scene), ctypes.POINTER(Target),
                                      ctypes.POINTER(Bins), ctypes.POINTER(Frags), _P, _P]
+        L.star_nt_raster_passes.argtypes = [ctypes.POINTER(Scene), _I32, ctypes.POINTER(Target),
+                                            ctypes.POINTER(Bins), _P, _P]
         L.star_nt_build_inputs.argtypes = [ctypes.POINTER(Scene)] + [ctypes.POINTER(Bins)] * 3 + \
             [ctypes.POINTER(Layers)] * 3 + [_I32, _I32, ctypes.POINTER(Params),
                                             ctypes.POINTER(Features), _P, _P]
@@ -194,6 +196,17 @@ def raster(scene: Scene, vp, size, max_w, max_h, bins: BinsBuffer, frags=None, s
                                                   ctypes.byref(bins.c),
                                                   ctypes.byref(fr) if fr is not None else None,
                                                   _ptr(status), _stream(stream)))
+
+
+def raster_passes(scene: Scene, passes, status=None, stream=None):
+    """passes: list of (vp, size, max_w, max_h, bins, merge_at or None)."""
+    n = len(passes)
+    tgts = (Target * n)(*[Target(vp.data_ptr(), size.data_ptr(), mw, mh,
+                                 ma.data_ptr() if ma is not None else None)
+                          for vp, size, mw, mh, _, ma in passes])
+    bins = (Bins * n)(*[b.c for _, _, _, _, b, _ in passes])
+    _check("star_nt_raster_passes", lib().star_nt_raster_passes(ctypes.byref(scene), n, tgts, bins,
+                                                                _ptr(status), _stream(stream)))
 
 
 def layers_struct(d) -> Layers:
