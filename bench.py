@@ -37,7 +37,7 @@ OPS_PER_FRAGMENT = 32     # algorithmic integer/fp operations per fragment (see 
 # kernels of one step: raster of the three passes (set-up/count, tile scan,
 # fill), 3 geometry passes, upscale/features, MLP, composite, quadtree
 # (decide, relax, relax + histogram + Eq. 2), reprojection (matrix, pixels)
-KERNELS_PER_STEP = 3 + 3 + 1 + 1 + 1 + 3 + 2
+KERNELS_PER_STEP = 3 + 3 + 1 + 3 + 2   # fused resolve; 3 + 3 + 3 + 3 + 2 separate
 STAGE_REPS = 20
 
 
@@ -131,7 +131,8 @@ def run_ours(args, rank, world):
     W, H = sc.width, sc.height
     w, wname = mlp_weights()
     x_dtype = sn.BF16 if args.mlp == "bf16" else sn.F32
-    star = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=x_dtype, base_tile=args.base_tile)
+    star = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=x_dtype, base_tile=args.base_tile,
+                    fused=args.fused and x_dtype == sn.BF16)
     plain = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=sn.F32)
     n_frames = 2 * (4 + args.warmup + 2 * args.steps + 12)
     cams = scenes.orbit_cameras(W, H, n_frames)
@@ -254,6 +255,7 @@ def run_ours(args, rank, world):
         "dtype": "f32+bf16" if x_dtype == sn.BF16 else "f32",
         "data": "synthetic seeded triangle soup, orbit camera",
         "config": {"workload": desc, "frames_per_step": 2, "mlp": args.mlp, "weights": wname,
+                   "resolve": "fused" if star.fused else "separate",
                    "base_tile": args.base_tile, "l2": "flushed between steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "fragments_per_s": round(Fcount / (ms_frame * 1e-3), 1),
@@ -265,7 +267,7 @@ def run_ours(args, rank, world):
         "pass_state": {k: state[k] for k in ("W2", "H2", "W3", "H3", "s2", "s3", "wbar", "hist")},
         "wall_s": round(wall, 3),
         "graph": "one CUDA graph per step (real + interpolated frame), replayed",
-        "gpu_launches": KERNELS_PER_STEP * args.steps,
+        "gpu_launches": (KERNELS_PER_STEP + (0 if star.fused else 2)) * args.steps,
         "clocks": clocks,
         "e2e": e2e,
         "roofline": {"bound": "alu", "kernel": "k_pass<kTop1> (pass 1, full resolution)",
@@ -298,7 +300,8 @@ def end_to_end(sn, torch, sc, w, x_dtype, W, H, cams, args):
     interpolated frame are rendered (the captured step), and both 8-bit frames
     are read back."""
     from paper_2606_16747_b300.pipeline import Renderer
-    r = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=x_dtype, base_tile=args.base_tile)
+    r = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=x_dtype, base_tile=args.base_tile,
+                 fused=args.fused and x_dtype == sn.BF16)
     hv = torch.from_numpy(np.ascontiguousarray(sc.verts)).pin_memory()
     hc = torch.from_numpy(np.ascontiguousarray(sc.rgba8).view(np.int32)).pin_memory()
     hvp = [torch.from_numpy(np.ascontiguousarray(c.vp32)).pin_memory() for c in cams]
@@ -444,6 +447,8 @@ def main():
     ap.add_argument("--workload", default="hd", choices=["hd", "uhd", "small"])
     ap.add_argument("--mlp", default="bf16", choices=["bf16", "f32"])
     ap.add_argument("--base-tile", type=int, default=16)
+    ap.add_argument("--unfused", dest="fused", action="store_false",
+                    help="separate upscale/features, MLP and composite kernels")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)

@@ -242,6 +242,21 @@ star_nt_status star_nt_infer(const star_nt_mlp *w, int32_t x_dtype, const void *
                              int64_t P, int32_t *d_status, void *stream);
 
 /* ------------------------------------------------------------------------ */
+/* star_nt_resolve -- the full-resolution end of a real frame fused in one    */
+/* kernel: the bilinear upscale and network input of star_nt_upscale_features,*/
+/* the tail MLP of star_nt_infer on the tcgen05 tensor cores (bf16 operands,   */
+/* fp32 accumulation) and the composite of Eq. 4.  The network input, f(x) and */
+/* the front terms stay on chip.  Arguments as star_nt_upscale_features, plus  */
+/* the float32 weights w and the frame outputs (rgba32f [P][4], rgba8 [P];     */
+/* either may be NULL).                                                       */
+star_nt_status star_nt_resolve(const star_nt_scene *scene, const star_nt_bins *bins2,
+                               const star_nt_bins *bins3, const star_nt_layers *layers1,
+                               const star_nt_layers *layers2, const star_nt_layers *layers3,
+                               int32_t W, int32_t H, const star_nt_params *params,
+                               const star_nt_mlp *w, float *rgba32f, uint32_t *rgba8,
+                               int32_t *d_status, void *stream);
+
+/* ------------------------------------------------------------------------ */
 /* star_nt_composite -- Eq. 4: C = C_exact,2 + T_2 f(x) + T_all C_b.          */
 /* front: [P][4] (from star_nt_build_inputs), f: [P][4].  Writes rgba32f      */
 /* [P][4] (alpha = 1) and rgba8 [P] (round half to even of clamp(c,0,1)*255). */

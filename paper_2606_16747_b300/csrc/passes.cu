@@ -13,6 +13,7 @@
 #include <cuda_bf16.h>
 
 #include "common.cuh"
+#include "features.cuh"
 #include "raster_tile.cuh"
 
 namespace star {
@@ -27,70 +28,6 @@ struct PassOut {
   uint4 *tail;
   float *t_tail;
 };
-
-struct FeatOut {
-  void *x;
-  int x_dtype;
-  float4 *front;
-  float bg0, bg1, bg2;
-  float kappa;
-};
-
-__device__ __forceinline__ float tail_transmittance(unsigned long long lg, uint32_t opq) {
-  if (opq) return 0.0f;
-  const uint32_t k = (uint32_t)(lg >> 32);
-  if (k >= 160u) return 0.0f;
-  const float frac = __uint2float_rn((uint32_t)lg) * 2.3283064365386963e-10f;  // 2^-32
-  return ldexpf(exp2f(-frac), -(int)k);
-}
-
-// straight RGBA8 to float (c8 / 255, by a multiply: within one rounding of
-// the quotient)
-__device__ __forceinline__ void unpack_rgba(uint32_t c, float &r, float &g, float &b, float &a) {
-  constexpr float k = 1.0f / 255.0f;
-  r = (float)(c & 255u) * k;
-  g = (float)((c >> 8) & 255u) * k;
-  b = (float)((c >> 16) & 255u) * k;
-  a = (float)(c >> 24) * k;
-}
-
-// Network input row and front terms of one full-resolution pixel.
-__device__ __forceinline__ void write_features(const FeatOut &fo, size_t p, float a1, float r1,
-                                               float g1, float b1, float pr2, float pg2, float pb2,
-                                               float a2, float n, float A, float Sr, float Sg,
-                                               float Sb, float t, bool flag) {
-  const float T2 = (1.0f - a1) * (1.0f - a2);
-  const float Tall = T2 * t;
-  float4 fr;
-  fr.x = a1 * r1 + (1.0f - a1) * pr2 + Tall * fo.bg0;
-  fr.y = a1 * g1 + (1.0f - a1) * pg2 + Tall * fo.bg1;
-  fr.z = a1 * b1 + (1.0f - a1) * pb2 + Tall * fo.bg2;
-  fr.w = T2;
-  fo.front[p] = fr;
-  float x[6];
-  x[0] = n * fo.kappa;
-  x[1] = t;
-  const float inv = A > 0.0f ? __frcp_rn(255.0f * A) : 0.0f;
-  x[2] = Sr * inv;
-  x[3] = Sg * inv;
-  x[4] = Sb * inv;
-  x[5] = flag ? 1.0f : 0.0f;
-  if (fo.x_dtype == STAR_NT_F32) {
-    float4 *X = reinterpret_cast<float4 *>(fo.x) + 2 * p;
-    X[0] = make_float4(x[0], x[1], x[2], x[3]);
-    X[1] = make_float4(x[4], x[5], 0.0f, 0.0f);
-  } else {
-    __nv_bfloat162 h0 = __floats2bfloat162_rn(x[0], x[1]);
-    __nv_bfloat162 h1 = __floats2bfloat162_rn(x[2], x[3]);
-    __nv_bfloat162 h2 = __floats2bfloat162_rn(x[4], x[5]);
-    uint4 v;
-    v.x = *reinterpret_cast<uint32_t *>(&h0);
-    v.y = *reinterpret_cast<uint32_t *>(&h1);
-    v.z = *reinterpret_cast<uint32_t *>(&h2);
-    v.w = 0u;
-    reinterpret_cast<uint4 *>(fo.x)[p] = v;
-  }
-}
 
 // One geometry pass over one tile.  MODE selects what is kept: the nearest
 // fragment, the two nearest, the two nearest plus tail sums, or all of it
@@ -192,86 +129,15 @@ __global__ void __launch_bounds__(256, 6) k_pass_merged(BinsView bv, const BinsH
 
 // Full-resolution features from pass 1 (full res) and the bilinear upscale
 // of passes 2 and 3 (their own resolutions, read from their bins headers).
-// All plane loads are issued before any of them is used (the sample indices
-// are clamped, so every load is valid) to keep many requests in flight; zero
-// bilinear weights then drop their samples exactly.
-__global__ void __launch_bounds__(256) k_features(int W, int H, const BinsHeader *hd2,
-                                                  const BinsHeader *hd3,
-                                                  const uint32_t *__restrict__ rgba8,
-                                                  const int32_t *__restrict__ id1,
-                                                  const int32_t *__restrict__ id2,
-                                                  const uint32_t *__restrict__ n3,
-                                                  const uint4 *__restrict__ tail3,
-                                                  const float *__restrict__ t3, FeatOut fo) {
+__global__ void __launch_bounds__(256) k_features(FeatIn in, FeatOut fo) {
   const int x = blockIdx.x * 32 + (threadIdx.x & 31);
   const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
-  if (x >= W || y >= H) return;
-  if (hd2->n_pixels <= 0 || hd3->n_pixels <= 0) return;  // a pass was rejected
-  const size_t p = (size_t)y * W + x;
-  const int W2 = hd2->size[0], H2 = hd2->size[1];
-  const int W3 = hd3->size[0], H3 = hd3->size[1];
-  const Axis ax2 = upscale_axis(x, W2, W), ay2 = upscale_axis(y, H2, H);
-  const Axis ax3 = upscale_axis(x, W3, W), ay3 = upscale_axis(y, H3, H);
-  size_t q2[4], q3[4];
-  q2[0] = (size_t)ay2.i0 * W2 + ax2.i0; q2[1] = (size_t)ay2.i0 * W2 + ax2.i1;
-  q2[2] = (size_t)ay2.i1 * W2 + ax2.i0; q2[3] = (size_t)ay2.i1 * W2 + ax2.i1;
-  q3[0] = (size_t)ay3.i0 * W3 + ax3.i0; q3[1] = (size_t)ay3.i0 * W3 + ax3.i1;
-  q3[2] = (size_t)ay3.i1 * W3 + ax3.i0; q3[3] = (size_t)ay3.i1 * W3 + ax3.i1;
-  // issue every plane load
-  const int i1 = __ldg(id1 + p);
-  int i2[4];
-  uint32_t nn[4];
-  uint4 tl[4];
-  float tt[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    i2[k] = __ldg(id2 + q2[k]);
-    nn[k] = __ldg(n3 + q3[k]);
-    tl[k] = __ldg(tail3 + q3[k]);
-    tt[k] = __ldg(t3 + q3[k]);
-  }
-  // colour gathers (independent of each other)
-  const uint32_t c1 = i1 >= 0 ? __ldg(rgba8 + i1) : 0u;
-  uint32_t c2[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) c2[k] = i2[k] >= 0 ? __ldg(rgba8 + i2[k]) : 0u;
-
-  float r1, g1, b1, a1;
-  unpack_rgba(c1, r1, g1, b1, a1);
-  const float rx = __frcp_rn((float)ax2.den), ry = __frcp_rn((float)ay2.den);
-  const float wx2 = (float)ax2.rem * rx, wy2 = (float)ay2.rem * ry;
-  const float w2[4] = {(1.0f - wy2) * (1.0f - wx2), (1.0f - wy2) * wx2, wy2 * (1.0f - wx2), wy2 * wx2};
-  float L2[4] = {0, 0, 0, 0};
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    if (w2[k] == 0.0f || i2[k] < 0) continue;
-    float r, g, b, a;
-    unpack_rgba(c2[k], r, g, b, a);
-    L2[0] += w2[k] * (a * r);
-    L2[1] += w2[k] * (a * g);
-    L2[2] += w2[k] * (a * b);
-    L2[3] += w2[k] * a;
-  }
-  const float wx3 = (float)ax3.rem * rx, wy3 = (float)ay3.rem * ry;  // same denominators 2W, 2H
-  const float w3[4] = {(1.0f - wy3) * (1.0f - wx3), (1.0f - wy3) * wx3, wy3 * (1.0f - wx3), wy3 * wx3};
-  const long long wi3[4] = {(long long)(ay3.den - ay3.rem) * (ax3.den - ax3.rem),
-                            (long long)(ay3.den - ay3.rem) * ax3.rem,
-                            (long long)ay3.rem * (ax3.den - ax3.rem), (long long)ay3.rem * ax3.rem};
-  float nf = 0, A = 0, Sr = 0, Sg = 0, Sb = 0, t = 0;
-  long long nexact = 0;  // upscaled N times (2W)(2H), exact
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    if (wi3[k] == 0) continue;  // exact zero weight
-    nf += w3[k] * (float)nn[k];
-    A += w3[k] * (float)tl[k].x;
-    Sr += w3[k] * (float)tl[k].y;
-    Sg += w3[k] * (float)tl[k].z;
-    Sb += w3[k] * (float)tl[k].w;
-    t += w3[k] * tt[k];
-    nexact += wi3[k] * (long long)nn[k];
-  }
-  const bool flag = nexact > 2LL * ax3.den * ay3.den;
-  write_features(fo, p, a1, r1, g1, b1, L2[0], L2[1], L2[2], L2[3], nf, A, Sr, Sg, Sb, t, flag);
+  if (x >= in.W || y >= in.H) return;
+  if (in.hd2->n_pixels <= 0 || in.hd3->n_pixels <= 0) return;  // a pass was rejected
+  float xv[6];
+  float4 fr;
+  pixel_features(in, fo.bg0, fo.bg1, fo.bg2, fo.kappa, x, y, xv, fr);
+  store_features(fo, (size_t)y * in.W + x, xv, fr);
 }
 
 }  // namespace star
@@ -383,9 +249,9 @@ extern "C" star_nt_status star_nt_upscale_features(const star_nt_scene *scene, c
   if (scene->n_tris > 0 && !scene->rgba8) return STAR_NT_ERR_ARG;
   BinsView v2 = bins_view(*b2), v3 = bins_view(*b3);
   dim3 grid((W + 31) / 32, (H + 7) / 8);
-  k_features<<<grid, 256, 0, (cudaStream_t)stream>>>(W, H, v2.hd, v3.hd, scene->rgba8, l1->id1, l2->id2,
-                                                     l3->n, reinterpret_cast<const uint4 *>(l3->tail),
-                                                     l3->t_tail, fo);
+  FeatIn in{W, H, v2.hd, v3.hd, scene->rgba8, l1->id1, l2->id2, l3->n,
+            reinterpret_cast<const uint4 *>(l3->tail), l3->t_tail};
+  k_features<<<grid, 256, 0, (cudaStream_t)stream>>>(in, fo);
   return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
 }
 

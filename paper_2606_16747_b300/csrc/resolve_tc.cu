@@ -1,0 +1,282 @@
+// resolve_tc.cu -- star_nt_resolve: the full-resolution end of a real frame
+// in one kernel (Sec. 3.2 last paragraph, Sec. 3.3, Eq. 4): bilinear upscale
+// of passes 2 and 3, network input, the tail-colour MLP on the tcgen05 tensor
+// cores, and the composite.  The network input, f(x) and the front terms
+// never leave the SM: per pixel the kernel reads the pass planes and writes
+// the frame.
+//
+// One CTA of 128 threads works on rounds of two 128-pixel tiles (thread r
+// owns row r of both).  Each round: features into shared memory as the bf16
+// A operand; layer 1 for both tiles (two MMAs, one commit); bias + ReLU into
+// the bf16 operand of layer 2; and so on; the composite in registers.  Tensor
+// memory holds 32 columns per tile: D1 in columns [0, 32), then D2 in [0, 16)
+// and D3 in [16, 32) once D1 has been read.  Every mbarrier wait is bounded.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "features.cuh"
+#include "tc_primitives.cuh"
+
+namespace star {
+
+constexpr int kRThreads = 128;
+constexpr int kRRows = 128;
+constexpr int kRTiles = 2;                  // tiles per round
+constexpr uint32_t kRTmemCols = 64;         // 32 per tile
+constexpr int kRCtasPerSm = 8;              // 8 x 64 columns = all of tensor memory
+
+// shared memory map (bytes from a 1024-aligned base)
+constexpr uint32_t kQX = 0;         // X of tile 0 (2048), of tile 1 (2048), zero block (2048)
+constexpr uint32_t kQZ = 4096;
+constexpr uint32_t kQH = 6144;      // per tile 8192: H1 (4 core columns), later H2 (2)
+constexpr uint32_t kQW1 = 22528;    // N=32, K=16: 2 x 512
+constexpr uint32_t kQW2 = 23552;    // N=16, K=32: 4 x 256
+constexpr uint32_t kQW3 = 24576;    // N=16, K=16: 2 x 256
+constexpr uint32_t kQB = 25088;     // b1[32], b2[16], b3[16]
+constexpr uint32_t kQBar = 25344;   // mma barrier, tmem slot, abort flag
+constexpr uint32_t kQUsed = 25360;
+constexpr uint32_t kQSmem = 27 * 1024;  // caps residency at 8 CTAs per SM
+
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
+  uint32_t r[4];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t quantize8(float r, float g, float b) {
+  const uint32_t R = __float2uint_rn(__saturatef(r) * 255.0f);
+  const uint32_t G = __float2uint_rn(__saturatef(g) * 255.0f);
+  const uint32_t B = __float2uint_rn(__saturatef(b) * 255.0f);
+  return R | (G << 8) | (B << 16) | (255u << 24);
+}
+
+__global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
+    k_resolve(FeatIn in, float bg0, float bg1, float bg2, float kappa, const float *__restrict__ w1,
+              const float *__restrict__ b1, const float *__restrict__ w2,
+              const float *__restrict__ b2, const float *__restrict__ w3,
+              const float *__restrict__ b3, float4 *__restrict__ out, uint32_t *__restrict__ out8,
+              int32_t *status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                            ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t sbase = smem_u32(sm);
+  const uint32_t bar = sbase + kQBar;
+  uint32_t *s_tmem = reinterpret_cast<uint32_t *>(sm + kQBar + 8);
+  volatile int *s_abort = reinterpret_cast<volatile int *>(sm + kQBar + 12);
+  float *sb = reinterpret_cast<float *>(sm + kQB);
+  if (in.hd2->n_pixels <= 0 || in.hd3->n_pixels <= 0) return;  // a pass was rejected
+
+  // weights (bf16, zero padded), biases, the zero K block of layer 1
+  for (int i = tid; i < (int)(kQBar - kQW1) / 4; i += kRThreads)
+    reinterpret_cast<uint32_t *>(sm + kQW1)[i] = 0u;
+  for (int i = tid; i < 512; i += kRThreads) reinterpret_cast<uint32_t *>(sm + kQZ)[i] = 0u;
+  __syncthreads();
+  for (int i = tid; i < 32 * 5; i += kRThreads) put_w(sm + kQW1, i / 5, i % 5, 512, w1[i]);
+  for (int i = tid; i < 16 * 32; i += kRThreads) put_w(sm + kQW2, i / 32, i % 32, 256, w2[i]);
+  for (int i = tid; i < 3 * 16; i += kRThreads) put_w(sm + kQW3, i / 16, i % 16, 256, w3[i]);
+  if (tid < 32) sb[tid] = b1[tid];
+  if (tid < 16) sb[32 + tid] = b2[tid];
+  if (tid < 16) sb[48 + tid] = tid < 3 ? b3[tid] : 0.0f;
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    *s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(s_tmem)),
+                 "r"(kRTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *s_tmem;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const int row = tid;
+
+  const uint64_t dW1 = smem_desc(sbase + kQW1, 512, 128);
+  const uint64_t dW2a = smem_desc(sbase + kQW2, 256, 128), dW2b = smem_desc(sbase + kQW2 + 512, 256, 128);
+  const uint64_t dW3 = smem_desc(sbase + kQW3, 256, 128);
+  const long long P = (long long)in.W * in.H;
+  const long long nrounds = (P + kRTiles * kRRows - 1) / (kRTiles * kRRows);
+  uint32_t ph = 0u;
+
+  for (long long round = blockIdx.x; round < nrounds; round += gridDim.x) {
+    const long long base = round * (kRTiles * kRRows);
+    // ---- features of this thread's row in both tiles
+    float4 front[kRTiles];
+    bool flag[kRTiles];
+#pragma unroll
+    for (int t = 0; t < kRTiles; ++t) {
+      const long long p = base + t * kRRows + row;
+      float xv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      front[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (p < P) {
+        const int y = (int)(p / in.W), x = (int)(p - (long long)y * in.W);
+        pixel_features(in, bg0, bg1, bg2, kappa, x, y, xv, front[t]);
+      }
+      flag[t] = xv[5] != 0.0f;
+      __nv_bfloat162 h0 = __floats2bfloat162_rn(xv[0], xv[1]);
+      __nv_bfloat162 h1 = __floats2bfloat162_rn(xv[2], xv[3]);
+      __nv_bfloat162 h2 = __floats2bfloat162_rn(xv[4], xv[5]);
+      *reinterpret_cast<uint4 *>(sm + kQX + t * 2048 + row * 16) =
+          make_uint4(*reinterpret_cast<uint32_t *>(&h0), *reinterpret_cast<uint32_t *>(&h1),
+                     *reinterpret_cast<uint32_t *>(&h2), 0u);
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    // ---- layer 1
+    if (tid == 0) {
+      fence_after();
+#pragma unroll
+      for (int t = 0; t < kRTiles; ++t)
+        mma_bf16(tmem + 32 * t, smem_desc(sbase + kQX + t * 2048, kQZ - (kQX + t * 2048), 128), dW1,
+                 idesc_bf16(32), 0u);
+      mma_commit(bar);
+    }
+    if (!mbar_wait(bar, ph)) *s_abort = 1;
+    ph ^= 1u;
+    fence_after();
+#pragma unroll
+    for (int t = 0; t < kRTiles; ++t) {
+      float d[32];
+      tmem_ld32(tmem + lane_base + 32 * t, d);
+      uint32_t pk[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        pk[j] = pack_bf16(fmaxf(d[2 * j] + sb[2 * j], 0.0f), fmaxf(d[2 * j + 1] + sb[2 * j + 1], 0.0f));
+#pragma unroll
+      for (int kc = 0; kc < 4; ++kc)
+        *reinterpret_cast<uint4 *>(sm + kQH + t * 8192 + kc * 2048 + row * 16) =
+            make_uint4(pk[4 * kc], pk[4 * kc + 1], pk[4 * kc + 2], pk[4 * kc + 3]);
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    if (*s_abort) break;
+    // ---- layer 2 (D2 over D1's first 16 columns)
+    if (tid == 0) {
+      fence_after();
+#pragma unroll
+      for (int t = 0; t < kRTiles; ++t) {
+        const uint32_t h = sbase + kQH + t * 8192;
+        mma_bf16(tmem + 32 * t, smem_desc(h, 2048, 128), dW2a, idesc_bf16(16), 0u);
+        mma_bf16(tmem + 32 * t, smem_desc(h + 4096, 2048, 128), dW2b, idesc_bf16(16), 1u);
+      }
+      mma_commit(bar);
+    }
+    if (!mbar_wait(bar, ph)) *s_abort = 1;
+    ph ^= 1u;
+    fence_after();
+#pragma unroll
+    for (int t = 0; t < kRTiles; ++t) {
+      float d[16];
+      tmem_ld16(tmem + lane_base + 32 * t, d);
+      uint32_t pk[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        pk[j] = pack_bf16(fmaxf(d[2 * j] + sb[32 + 2 * j], 0.0f),
+                          fmaxf(d[2 * j + 1] + sb[32 + 2 * j + 1], 0.0f));
+#pragma unroll
+      for (int kc = 0; kc < 2; ++kc)
+        *reinterpret_cast<uint4 *>(sm + kQH + t * 8192 + kc * 2048 + row * 16) =
+            make_uint4(pk[4 * kc], pk[4 * kc + 1], pk[4 * kc + 2], pk[4 * kc + 3]);
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    if (*s_abort) break;
+    // ---- layer 3 (D3 in columns 16..31 of the tile)
+    if (tid == 0) {
+      fence_after();
+#pragma unroll
+      for (int t = 0; t < kRTiles; ++t)
+        mma_bf16(tmem + 32 * t + 16, smem_desc(sbase + kQH + t * 8192, 2048, 128), dW3, idesc_bf16(16),
+                 0u);
+      mma_commit(bar);
+    }
+    if (!mbar_wait(bar, ph)) *s_abort = 1;
+    ph ^= 1u;
+    fence_after();
+    // ---- composite, Eq. 4
+#pragma unroll
+    for (int t = 0; t < kRTiles; ++t) {
+      float d[4];
+      tmem_ld4(tmem + lane_base + 32 * t + 16, d);
+      const long long p = base + t * kRRows + row;
+      if (p < P) {
+        float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+        if (flag[t]) {
+          f0 = fmaxf(d[0] + sb[48], 0.0f);
+          f1 = fmaxf(d[1] + sb[49], 0.0f);
+          f2 = fmaxf(d[2] + sb[50], 0.0f);
+        }
+        const float4 fr = front[t];
+        const float r = fmaf(fr.w, f0, fr.x), g = fmaf(fr.w, f1, fr.y), b = fmaf(fr.w, f2, fr.z);
+        if (out) out[p] = make_float4(r, g, b, 1.0f);
+        if (out8) out8[p] = quantize8(r, g, b);
+      }
+    }
+    fence_before();
+    __syncthreads();
+    if (*s_abort) break;
+  }
+  if (*s_abort && tid == 0) raise_status(status, STAR_NT_ERR_TIMEOUT);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kRTmemCols)
+                 : "memory");
+}
+
+}  // namespace star
+
+using namespace star;
+
+extern "C" star_nt_status star_nt_resolve(const star_nt_scene *scene, const star_nt_bins *b2,
+                                          const star_nt_bins *b3, const star_nt_layers *l1,
+                                          const star_nt_layers *l2, const star_nt_layers *l3,
+                                          int32_t W, int32_t H, const star_nt_params *params,
+                                          const star_nt_mlp *w, float *rgba32f, uint32_t *rgba8,
+                                          int32_t *d_status, void *stream) {
+  static_assert(kQUsed + 1024 <= kQSmem, "shared memory map");
+  if (!scene || !b2 || !b3 || !b2->mem || !b3->mem || !params || !w || W <= 0 || H <= 0)
+    return STAR_NT_ERR_ARG;
+  if (!w->w1 || !w->b1 || !w->w2 || !w->b2 || !w->w3 || !w->b3 || (!rgba32f && !rgba8))
+    return STAR_NT_ERR_ARG;
+  if (!l1 || !l1->id1 || !l2 || !l2->id2 || !l3 || !l3->n || !l3->tail || !l3->t_tail)
+    return STAR_NT_ERR_ARG;
+  if (((uintptr_t)rgba32f & 15u) || ((uintptr_t)l3->tail & 15u)) return STAR_NT_ERR_ARG;
+  if (scene->n_tris > 0 && !scene->rgba8) return STAR_NT_ERR_ARG;
+  if ((long long)W * H > 0x7fffffffLL) return STAR_NT_ERR_ARG;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_resolve, cudaFuncAttributeMaxDynamicSharedMemorySize, kQSmem) !=
+        cudaSuccess)
+      return STAR_NT_ERR_CUDA;
+    attr = true;
+  }
+  BinsView v2 = bins_view(*b2), v3 = bins_view(*b3);
+  FeatIn in{W, H, v2.hd, v3.hd, scene->rgba8, l1->id1, l2->id2, l3->n,
+            reinterpret_cast<const uint4 *>(l3->tail), l3->t_tail};
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long rounds = ((long long)W * H + kRTiles * kRRows - 1) / (kRTiles * kRRows);
+  long long grid = (long long)sms * kRCtasPerSm;
+  if (grid > rounds) grid = rounds;
+  k_resolve<<<(unsigned)grid, kRThreads, kQSmem, (cudaStream_t)stream>>>(
+      in, params->bg[0], params->bg[1], params->bg[2], params->kappa_n, w->w1, w->b1, w->w2, w->b2,
+      w->w3, w->b3, reinterpret_cast<float4 *>(rgba32f), rgba8, d_status);
+  return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
+}

@@ -28,7 +28,7 @@ def _i32(vals, device):
 
 class Renderer:
     def __init__(self, verts, rgba8, W, H, params=None, x_dtype=sn.F32, mlp=None,
-                 pair_capacity=None, device="cuda", base_tile=None, keep_layers=False):
+                 pair_capacity=None, device="cuda", base_tile=None, fused=False):
         self.device = device
         self.W, self.H = int(W), int(H)
         self.P = self.W * self.H
@@ -40,6 +40,10 @@ class Renderer:
         if base_tile is not None:
             self.params.base_tile = base_tile
         self.x_dtype = x_dtype
+        # fused: upscale + features + BF16 MLP + composite in one kernel
+        self.fused = bool(fused)
+        if self.fused and x_dtype != sn.BF16:
+            raise ValueError("the fused resolve runs the BF16 tensor-core MLP")
         cap = pair_capacity if pair_capacity is not None else max(1 << 20, 96 * self.T)
         self.bins = [sn.BinsBuffer(self.W, self.H, self.T, cap, device) for _ in range(3)]
         P = self.P
@@ -128,13 +132,21 @@ class Renderer:
                                                         self.l3, self.status, stream)),
               ("pass2", lambda: sn.geometry_pass(self.scene, b2, 2, self.l2, self.status, stream)),
               ("pass3", lambda: sn.geometry_pass(self.scene, b3, 3, self.l3, self.status, stream)),
-              ("features", lambda: sn.upscale_features(self.scene, b2, b3, self.l1, self.l2, self.l3,
-                                                       self.W, self.H, self.params, self.x,
-                                                       self.x_dtype, self.front, stream)),
-              ("infer", lambda: sn.infer(self.mlp, self.x_dtype, self.x, self.f, self.P, self.status,
-                                         stream)),
-              ("composite", lambda: sn.composite(self.front, self.f, self.P, self.rgba32f,
-                                                 self.rgba8_out, stream))]
+              ]
+        if self.fused:
+            st.append(("resolve", lambda: sn.resolve(self.scene, b2, b3, self.l1, self.l2, self.l3,
+                                                     self.W, self.H, self.params, self.mlp,
+                                                     self.rgba32f, self.rgba8_out, self.status,
+                                                     stream)))
+        else:
+            st += [("features", lambda: sn.upscale_features(self.scene, b2, b3, self.l1, self.l2,
+                                                            self.l3, self.W, self.H, self.params,
+                                                            self.x, self.x_dtype, self.front,
+                                                            stream)),
+                   ("infer", lambda: sn.infer(self.mlp, self.x_dtype, self.x, self.f, self.P,
+                                              self.status, stream)),
+                   ("composite", lambda: sn.composite(self.front, self.f, self.P, self.rgba32f,
+                                                      self.rgba8_out, stream))]
         if update_tiles:
             st.append(("quadtree", lambda: self.update_tiles(stream)))
         return st

@@ -505,3 +505,27 @@ def test_plain_frame_bf16(orc, sn):
     rgb = r.rgba32f.cpu().numpy().reshape(-1, 4)[:, :3]
     # frame error is the MLP error scaled by T_2 <= 1
     assert np.max(np.abs(rgb - o["rgb"])) <= TOL_BF16
+
+
+def test_fused_resolve_equals_separate_kernels(orc, sn):
+    """star_nt_resolve (upscale + features + tcgen05 MLP + composite in one
+    kernel) gives the same frame as the three separate calls, and stays within
+    the BF16 tolerance of the oracle's float64 frame."""
+    from paper_2606_16747_b300.pipeline import Renderer
+    sc = scenes.screen_scene(29, 3000, 333, 197, size_scale=0.7)   # ragged: 65601 px, partial tiles
+    W, H = sc.width, sc.height
+    mlp = scenes.mlp_xavier(4)
+    outs = []
+    for fused in (False, True):
+        r = Renderer(sc.verts, sc.rgba8, W, H, mlp=mlp, x_dtype=sn.BF16, fused=fused)
+        r.set_camera(sc.cam.vp32)
+        r.state.view(torch.int32)[:6] = torch.tensor([W, H, 201, 119, 97, 57], dtype=torch.int32)
+        r.star_frame(update_tiles=False)
+        torch.cuda.synchronize()
+        r.check_status()
+        outs.append((r.rgba32f.clone(), r.rgba8_out.clone()))
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+    o = orc.frame_star(sc.verts, sc.rgba8, sc.cam.vp32, W, H, (201, 119), (97, 57), scenes.mlp_flat(mlp),
+                       threads=4)
+    rgb = outs[1][0].cpu().numpy().reshape(-1, 4)[:, :3]
+    assert np.max(np.abs(rgb - o["rgb"])) <= TOL_BF16
