@@ -34,10 +34,10 @@ FALLBACK_PEAKS = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustain
 N_SM = 148
 ALU_LANES_PER_SM = 128
 OPS_PER_FRAGMENT = 32     # algorithmic integer/fp operations per fragment (see design notes)
-# kernels of one step: raster of the three passes (set-up/count, tile scan,
-# fill), 3 geometry passes, upscale/features, MLP, composite, quadtree
-# (decide, relax, relax + histogram + Eq. 2), reprojection (matrix, pixels)
-KERNELS_PER_STEP = 3 + 3 + 1 + 3 + 2   # fused resolve; 3 + 3 + 3 + 3 + 2 separate
+# kernels of one step (persistent passes, fused resolve): raster of the three
+# passes (set-up/count, tile scan, fill), passes 1-3 (one launch), resolve,
+# quadtree (decide, relax, relax + histogram + Eq. 2), reprojection (matrix, pixels)
+KERNELS_PER_STEP = 3 + 1 + 1 + 3 + 2
 STAGE_REPS = 20
 
 
@@ -132,7 +132,7 @@ def run_ours(args, rank, world):
     w, wname = mlp_weights()
     x_dtype = sn.BF16 if args.mlp == "bf16" else sn.F32
     star = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=x_dtype, base_tile=args.base_tile,
-                    fused=args.fused and x_dtype == sn.BF16)
+                    fused=args.fused and x_dtype == sn.BF16, persistent=args.persistent)
     plain = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=sn.F32)
     n_frames = 2 * (4 + args.warmup + 2 * args.steps + 12)
     cams = scenes.orbit_cameras(W, H, n_frames)
@@ -144,10 +144,16 @@ def run_ours(args, rank, world):
     def set_cams(k):            # step k: real frame 2k, interpolated frame 2k + 1
         star.set_cameras(vp32[2 * k], vp64[2 * k], vp64[2 * k + 1])
 
-    # settle the tile hierarchy on the first frames, then capture one step
+    # settle the tile hierarchy on the first frames, tune the pass launch on
+    # this workload, then capture one step
     for k in range(4):
         set_cams(k)
         star.step()
+    tuned = None
+    if args.persistent and not args.no_tune:
+        from paper_2606_16747_b300 import autotune
+        tuned = autotune.tune(star)
+        star.tuning = (tuned["block_w"], tuned["ctas_per_sm"])
     stages = star.star_stages() + [("reproject", star.interp_frame)]
     g_step = star.capture(star.step)
     g_stage = [(name, star.capture(fn)) for name, fn in stages]
@@ -198,6 +204,7 @@ def run_ours(args, rank, world):
     set_cams(step)
     step += 1
     g_step.replay()
+    stage_state = star.pass_state()
     for name, g in g_stage:
         g.replay()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -225,7 +232,7 @@ def run_ours(args, rank, world):
     plain.check_status()
 
     # end to end through the public API: host inputs in, frames out, every step
-    e2e = end_to_end(sn, torch, sc, w, x_dtype, W, H, cams, args)
+    e2e = end_to_end(sn, torch, sc, w, x_dtype, W, H, cams, args, star.tuning)
 
     t_step = float(np.mean(step_ms))
     t_max = t_step
@@ -236,10 +243,23 @@ def run_ours(args, rank, world):
     ms_frame = t_max / 2.0
     stage_mean = {k: float(np.mean(v)) for k, v in stage_ms.items()}
     peaks, peaks_kind = load_peaks()
-    # dominant kernel: the full-resolution geometry pass (pass 1)
-    dom_ms = stage_mean["pass1"]
+    # dominant kernel: the geometry passes (one persistent launch, or pass 1)
     alu_peak = N_SM * ALU_LANES_PER_SM * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12  # Tops/s
-    achieved = OPS_PER_FRAGMENT * Fcount / (dom_ms * 1e-3) / 1e12
+    if "passes" in stage_mean:
+        # fragments the timed launch processed: the stage graphs ran on the
+        # cameras of the last step, at the pass sizes in force then
+        dom_ms = stage_mean["passes"]
+        vp_last = vp32[2 * (step - 1)]
+        dom_frags = fragment_count(sn, star, vp_last, W, H)
+        for wp, hp in ((stage_state["W2"], stage_state["H2"]), (stage_state["W3"], stage_state["H3"])):
+            if (wp, hp) != (W, H):
+                dom_frags += fragment_count(sn, star, vp_last, W, H, (wp, hp))
+        dom_name = "k_passes (passes 1-3, one persistent launch)"
+    else:
+        dom_ms = stage_mean["pass1"]
+        dom_frags = Fcount
+        dom_name = "k_pass_merged (pass 1, full resolution)"
+    achieved = OPS_PER_FRAGMENT * dom_frags / (dom_ms * 1e-3) / 1e12
     psnr = psnr_measured
     line = {
         "metric": "ms/frame (STAR-NT, 1080p)" if args.workload == "hd" else f"ms/frame (STAR-NT, {args.workload})",
@@ -256,6 +276,8 @@ def run_ours(args, rank, world):
         "data": "synthetic seeded triangle soup, orbit camera",
         "config": {"workload": desc, "frames_per_step": 2, "mlp": args.mlp, "weights": wname,
                    "resolve": "fused" if star.fused else "separate",
+                   "passes": "persistent" if star.persistent else "separate",
+                   "pass_tuning": tuned,
                    "base_tile": args.base_tile, "l2": "flushed between steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "fragments_per_s": round(Fcount / (ms_frame * 1e-3), 1),
@@ -267,10 +289,10 @@ def run_ours(args, rank, world):
         "pass_state": {k: state[k] for k in ("W2", "H2", "W3", "H3", "s2", "s3", "wbar", "hist")},
         "wall_s": round(wall, 3),
         "graph": "one CUDA graph per step (real + interpolated frame), replayed",
-        "gpu_launches": (KERNELS_PER_STEP + (0 if star.fused else 2)) * args.steps,
+        "gpu_launches": (KERNELS_PER_STEP + (0 if star.fused else 2) + (0 if star.persistent else 2)) * args.steps,
         "clocks": clocks,
         "e2e": e2e,
-        "roofline": {"bound": "alu", "kernel": "k_pass<kTop1> (pass 1, full resolution)",
+        "roofline": {"bound": "alu", "kernel": dom_name, "fragments": int(dom_frags),
                      "achieved": round(achieved, 4), "peak": round(alu_peak, 3), "unit": "Tops/s",
                      "frac": round(achieved / alu_peak, 5), "traffic": None,
                      "peak_source": f"{N_SM} SM x {ALU_LANES_PER_SM} lanes x sm_max_mhz ({peaks_kind})",
@@ -280,28 +302,30 @@ def run_ours(args, rank, world):
     return line
 
 
-def fragment_count(sn, r, vp, W, H):
+def fragment_count(sn, r, vp, W, H, size=None):
+    """Fragments of the scene under camera vp at W x H (or at ``size``)."""
     import torch
     P = W * H
+    size_t = r.full_size if size is None else torch.tensor(list(size), dtype=torch.int32, device="cuda")
     frags = dict(count=torch.zeros(P, dtype=torch.int32, device="cuda"),
                  offset=torch.zeros(P + 1, dtype=torch.int32, device="cuda"),
                  z=torch.zeros(1, dtype=torch.float32, device="cuda"),
                  prim=torch.zeros(1, dtype=torch.int32, device="cuda"),
                  total=torch.zeros(1, dtype=torch.int32, device="cuda"))
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
-    sn.raster(r.scene, vp, r.full_size, W, H, r.bins[0], frags, st)
+    sn.raster(r.scene, vp, size_t, W, H, r.bins[0], frags, st)
     torch.cuda.synchronize()
     return int(frags["total"].cpu().numpy().view(np.uint32)[0])
 
 
-def end_to_end(sn, torch, sc, w, x_dtype, W, H, cams, args):
+def end_to_end(sn, torch, sc, w, x_dtype, W, H, cams, args, tuning=None):
     """Same metric through the public API from host memory: per step the
     triangle soup and the cameras are copied host->device, one real and one
     interpolated frame are rendered (the captured step), and both 8-bit frames
     are read back."""
     from paper_2606_16747_b300.pipeline import Renderer
     r = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=x_dtype, base_tile=args.base_tile,
-                 fused=args.fused and x_dtype == sn.BF16)
+                 fused=args.fused and x_dtype == sn.BF16, persistent=args.persistent, tuning=tuning)
     hv = torch.from_numpy(np.ascontiguousarray(sc.verts)).pin_memory()
     hc = torch.from_numpy(np.ascontiguousarray(sc.rgba8).view(np.int32)).pin_memory()
     hvp = [torch.from_numpy(np.ascontiguousarray(c.vp32)).pin_memory() for c in cams]
@@ -447,6 +471,9 @@ def main():
     ap.add_argument("--workload", default="hd", choices=["hd", "uhd", "small"])
     ap.add_argument("--mlp", default="bf16", choices=["bf16", "f32"])
     ap.add_argument("--base-tile", type=int, default=16)
+    ap.add_argument("--separate-passes", dest="persistent", action="store_false",
+                    help="three geometry-pass launches instead of one persistent launch")
+    ap.add_argument("--no-tune", action="store_true", help="skip the pass-launch autotuner")
     ap.add_argument("--unfused", dest="fused", action="store_false",
                     help="separate upscale/features, MLP and composite kernels")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -217,6 +217,28 @@ star_nt_status star_nt_geometry_pass_merged(const star_nt_scene *scene, const st
                                             const star_nt_layers *layers2,
                                             const star_nt_layers *layers3, int32_t *d_status,
                                             void *stream);
+/* Tile shape and launch size of star_nt_geometry_passes (NULL: defaults).
+ * block_w: width of the pixel block a warp owns inside a 16 x 16 tile
+ *   (4, 8 or 16; the block is block_w x 32/block_w); default 8.
+ * ctas_per_sm: resident CTAs per SM of the persistent launch (1..8, capped
+ *   by occupancy; 0: as many as fit). */
+typedef struct {
+    int32_t block_w;
+    int32_t ctas_per_sm;
+} star_nt_tuning;
+
+/* star_nt_geometry_passes: the three geometry passes of a real frame in one
+ * persistent launch (the same results as star_nt_geometry_pass_merged, then
+ * modes 2 and 3): CTAs take tiles of pass 1, then pass 2, then pass 3 from
+ * a work counter kept in bins1's workspace, so uneven tiles and passes of
+ * different sizes share the launch.  bins1..3 must be distinct. */
+star_nt_status star_nt_geometry_passes(const star_nt_scene *scene, const star_nt_bins *bins1,
+                                       const star_nt_bins *bins2, const star_nt_bins *bins3,
+                                       const star_nt_layers *layers1,
+                                       const star_nt_layers *layers2,
+                                       const star_nt_layers *layers3,
+                                       const star_nt_tuning *tuning, int32_t *d_status,
+                                       void *stream);
 star_nt_status star_nt_upscale_features(const star_nt_scene *scene, const star_nt_bins *bins2,
                                 const star_nt_bins *bins3, const star_nt_layers *layers1,
                                 const star_nt_layers *layers2, const star_nt_layers *layers3,

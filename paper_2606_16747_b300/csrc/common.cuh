@@ -40,7 +40,8 @@ struct __align__(16) BinsHeader {
   uint32_t n_pairs;    // (triangle, tile) pairs needed
   int32_t n_tris;
   int32_t merged;      // 1: the pass runs at full size and is taken over by pass 1
-  uint32_t pad[7];
+  uint32_t queue;      // work counter of the persistent pass launch
+  uint32_t pad[6];
 };
 static_assert(sizeof(BinsHeader) == 64, "BinsHeader layout");
 

@@ -32,21 +32,21 @@ struct PassOut {
 // One geometry pass over one tile.  MODE selects what is kept: the nearest
 // fragment, the two nearest, the two nearest plus tail sums, or all of it
 // plus the full-resolution network input (fused plain pipeline).
-template <int MODE>
+template <int MODE, int BW = 8>
 __device__ __forceinline__ void pass_body(const BinsView &bv, const uint32_t *__restrict__ rgba8,
-                                          const PassOut &po, const FeatOut &fo, TileStage &stage) {
+                                          const PassOut &po, const FeatOut &fo, TileStage &stage,
+                                          int tile) {
   const BinsHeader *hd = bv.hd;
   if ((int64_t)hd->n_pairs > bv.pair_capacity) return;
-  const int tile = blockIdx.x;
   if (tile >= hd->n_tiles) return;
   const int W = hd->size[0], H = hd->size[1];
-  const TilePixel tp = tile_pixel(tile, hd->tiles_x);
+  const TilePixel tp = tile_pixel<BW>(tile, hd->tiles_x);
 
   float z1 = INFINITY, z2 = INFINITY;
   int i1 = 0x7fffffff, i2 = 0x7fffffff;
   uint32_t N = 0, opq = 0;
   unsigned long long rg = 0, ba = 0, lg = 0;
-  for_each_fragment(bv, tile, tp, stage, [&](const TriSetup &T, uint32_t id_u, float z) {
+  for_each_fragment<BW>(bv, tile, tp, stage, [&](const TriSetup &T, uint32_t id_u, float z) {
     const int id = (int)id_u;
     if (MODE == kTop1) {
       if (z < z1 || (z == z1 && id < i1)) { z1 = z; i1 = id; }
@@ -103,7 +103,7 @@ template <int MODE>
 __global__ void __launch_bounds__(256) k_pass(BinsView bv, const uint32_t *__restrict__ rgba8,
                                               PassOut po, FeatOut fo) {
   __shared__ TileStage stage;
-  pass_body<MODE>(bv, rgba8, po, fo, stage);
+  pass_body<MODE>(bv, rgba8, po, fo, stage, blockIdx.x);
 }
 
 // Pass 1 at full resolution; when pass 2 and/or pass 3 are marked merged
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(256, 6) k_pass_merged(BinsView bv, const BinsH
   __shared__ TileStage stage;
   const bool m2 = hd2->merged != 0, m3 = hd3->merged != 0;
   if (!m2 && !m3) {
-    pass_body<kTop1>(bv, rgba8, o1, FeatOut{}, stage);
+    pass_body<kTop1>(bv, rgba8, o1, FeatOut{}, stage, blockIdx.x);
     return;
   }
   PassOut o = o1;
@@ -124,7 +124,48 @@ __global__ void __launch_bounds__(256, 6) k_pass_merged(BinsView bv, const BinsH
   o.n = m3 ? o3.n : nullptr;
   o.tail = m3 ? o3.tail : nullptr;
   o.t_tail = m3 ? o3.t_tail : nullptr;
-  pass_body<kTail>(bv, rgba8, o, FeatOut{}, stage);
+  pass_body<kTail>(bv, rgba8, o, FeatOut{}, stage, blockIdx.x);
+}
+
+// All geometry passes of a real frame in one persistent launch: CTAs take
+// (pass, tile) items from a queue counter in order - every tile of pass 1,
+// then of pass 2, then of pass 3 - until the items run out, so tiles of uneven
+// cost and passes of different resolutions share one launch without a tail
+// between passes.  Pass 1 takes over merged passes as k_pass_merged does.
+template <int BW>
+__global__ void __launch_bounds__(256, 6) k_passes(BinsView v1, BinsView v2, BinsView v3,
+                                                   const uint32_t *__restrict__ rgba8, PassOut o1,
+                                                   PassOut o2, PassOut o3, uint32_t *queue) {
+  __shared__ TileStage stage;
+  __shared__ int s_item;
+  const bool m2 = v2.hd->merged != 0, m3 = v3.hd->merged != 0;
+  const int n1 = v1.hd->n_tiles, n2 = v2.hd->n_tiles, n3 = v3.hd->n_tiles;
+  const int total = n1 + n2 + n3;
+  PassOut om = o1;  // pass 1 with the merged passes' outputs
+  om.id2 = m2 ? o2.id2 : nullptr;
+  om.n = m3 ? o3.n : nullptr;
+  om.tail = m3 ? o3.tail : nullptr;
+  om.t_tail = m3 ? o3.t_tail : nullptr;
+  o2.id1 = nullptr;
+  o2.z1 = nullptr;
+  o3.id1 = nullptr;
+  o3.z1 = nullptr;
+  o3.id2 = nullptr;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(queue, 1u);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();  // every thread has the item before s_item is reused
+    if (item >= total) break;
+    if (item < n1) {
+      if (m2 || m3) pass_body<kTail, BW>(v1, rgba8, om, FeatOut{}, stage, item);
+      else pass_body<kTop1, BW>(v1, rgba8, o1, FeatOut{}, stage, item);
+    } else if (item < n1 + n2) {
+      pass_body<kTop2, BW>(v2, rgba8, o2, FeatOut{}, stage, item - n1);
+    } else {
+      pass_body<kTail, BW>(v3, rgba8, o3, FeatOut{}, stage, item - n1 - n2);
+    }
+  }
 }
 
 // Full-resolution features from pass 1 (full res) and the bilinear upscale
@@ -233,6 +274,45 @@ extern "C" star_nt_status star_nt_geometry_pass_merged(const star_nt_scene *scen
   o1.id2 = nullptr; o1.n = nullptr; o1.tail = nullptr; o1.t_tail = nullptr;
   k_pass_merged<<<tiles_of(b1), 256, 0, (cudaStream_t)stream>>>(v1, v2.hd, v3.hd, scene->rgba8, o1,
                                                                 pass_out(l2), pass_out(l3));
+  return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
+}
+
+extern "C" star_nt_status star_nt_geometry_passes(const star_nt_scene *scene,
+                                                  const star_nt_bins *b1, const star_nt_bins *b2,
+                                                  const star_nt_bins *b3, const star_nt_layers *l1,
+                                                  const star_nt_layers *l2,
+                                                  const star_nt_layers *l3,
+                                                  const star_nt_tuning *tuning, int32_t *d_status,
+                                                  void *stream) {
+  (void)d_status;
+  if (!scene || !b1 || !b2 || !b3 || !b1->mem || !b2->mem || !b3->mem || !l1 || !l2 || !l3)
+    return STAR_NT_ERR_ARG;
+  if ((!l1->id1 && !l1->z1) || !l2->id2 || !l3->n || !l3->tail || !l3->t_tail) return STAR_NT_ERR_ARG;
+  if (!layers_ok(l1) || !layers_ok(l2) || !layers_ok(l3)) return STAR_NT_ERR_ARG;
+  if (scene->n_tris > 0 && !scene->rgba8) return STAR_NT_ERR_ARG;
+  if (b1->mem == b2->mem || b1->mem == b3->mem || b2->mem == b3->mem) return STAR_NT_ERR_ARG;
+  const int bw = tuning ? tuning->block_w : 8;
+  int per_sm = tuning ? tuning->ctas_per_sm : 0;
+  if (bw != 4 && bw != 8 && bw != 16) return STAR_NT_ERR_ARG;
+  if (per_sm < 0 || per_sm > 8) return STAR_NT_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  BinsView v1 = bins_view(*b1), v2 = bins_view(*b2), v3 = bins_view(*b3);
+  PassOut o1 = pass_out(l1), o2 = pass_out(l2), o3 = pass_out(l3);
+  o1.id2 = nullptr; o1.n = nullptr; o1.tail = nullptr; o1.t_tail = nullptr;
+  uint32_t *queue = &v1.hd->queue;
+  cudaMemsetAsync(queue, 0, 4, st);
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  auto launch = [&](auto kern) {
+    int occ = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, 0);
+    const int k = per_sm > 0 ? (per_sm < occ ? per_sm : occ) : occ;
+    kern<<<sms * (k > 0 ? k : 1), 256, 0, st>>>(v1, v2, v3, scene->rgba8, o1, o2, o3, queue);
+  };
+  if (bw == 8) launch(k_passes<8>);
+  else if (bw == 16) launch(k_passes<16>);
+  else launch(k_passes<4>);
   return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
 }
 

@@ -389,13 +389,13 @@ __global__ void __launch_bounds__(256) k_frag_count(BinsView bv, uint32_t *count
   if (hd->merged) {  // fragments of a merged pass are not listed: zero counts
     const int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
     if (tile < tx * ty) {
-      const TilePixel tp = tile_pixel(tile, tx);
+      const TilePixel tp = tile_pixel<8>(tile, tx);
       if (tp.px < W && tp.py < H) count[tp.py * W + tp.px] = 0;
     }
     return;
   }
   if (tile >= hd->n_tiles) return;
-  const TilePixel tp = tile_pixel(tile, hd->tiles_x);
+  const TilePixel tp = tile_pixel<8>(tile, hd->tiles_x);
   uint32_t n = 0;
   for_each_fragment(bv, tile, tp, stage, [&](const TriSetup &, uint32_t, float) { ++n; });
   if (tp.px < W && tp.py < H) count[tp.py * W + tp.px] = n;
@@ -414,7 +414,7 @@ __global__ void __launch_bounds__(256) k_frag_fill(BinsView bv, const uint32_t *
   const int tile = blockIdx.x;
   if (tile >= hd->n_tiles) return;
   const int W = hd->size[0], H = hd->size[1];
-  const TilePixel tp = tile_pixel(tile, hd->tiles_x);
+  const TilePixel tp = tile_pixel<8>(tile, hd->tiles_x);
   const bool inside = tp.px < W && tp.py < H;
   uint32_t pos = inside ? offset[tp.py * W + tp.px] : 0u;
   for_each_fragment(bv, tile, tp, stage, [&](const TriSetup &, uint32_t id, float z) {

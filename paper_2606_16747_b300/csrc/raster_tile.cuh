@@ -1,7 +1,7 @@
 // raster_tile.cuh -- per-tile fragment traversal shared by the geometry-pass
-// kernels.  One CTA of 256 threads owns one 16 x 16-pixel tile; warp w owns
-// the 8 x 4 block at ((w & 1) * 8, (w >> 1) * 4) and lane l the pixel
-// (l & 7, l >> 3) of it.  The tile's binned triangles are staged in shared
+// kernels.  One CTA of 256 threads owns one 16 x 16-pixel tile; each warp owns
+// a BW x (32 / BW) block of it (BW = 8 by default, the tile shape the tuner
+// chooses from) and lane l the pixel (l % BW, l / BW) of that block.  The tile's binned triangles are staged in shared
 // memory kChunk at a time.  Each warp then classifies the staged triangles
 // for its own block, one triangle per lane (bounding box, then the three edge
 // functions at the block's most favourable pixel centre, exact in int64),
@@ -19,16 +19,18 @@ struct TilePixel {
   int tx0, ty0;  // origin of the tile
 };
 
+template <int BW = 8>
 __device__ __forceinline__ TilePixel tile_pixel(int tile, int tiles_x) {
+  constexpr int BH = 32 / BW, PER_ROW = kTile / BW;
   const int tx = tile % tiles_x, ty = tile / tiles_x;
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   TilePixel t;
   t.tx0 = tx * kTile;
   t.ty0 = ty * kTile;
-  t.bx0 = t.tx0 + (w & 1) * 8;
-  t.by0 = t.ty0 + (w >> 1) * 4;
-  t.px = t.bx0 + (l & 7);
-  t.py = t.by0 + (l >> 3);
+  t.bx0 = t.tx0 + (w % PER_ROW) * BW;
+  t.by0 = t.ty0 + (w / PER_ROW) * BH;
+  t.px = t.bx0 + (l % BW);
+  t.py = t.by0 + (l / BW);
   return t;
 }
 
@@ -43,13 +45,15 @@ __device__ __forceinline__ float frag_depth(const TriSetup &T, long long e0b, lo
   return __fadd_rn(z, 0.0f);
 }
 
-// May the triangle cover a pixel centre of the 8 x 4 block at (bx0, by0)?
-// False only when it certainly does not (bounding box, or one edge function
-// negative at every centre of the block).
+// May the triangle cover a pixel centre of the BW x (32 / BW) block at
+// (bx0, by0)?  False only when it certainly does not (bounding box, or one
+// edge function negative at every centre of the block).
+template <int BW = 8>
 __device__ __forceinline__ bool block_maybe(const TriSetup &T, int bx0, int by0) {
-  if (T.xb < bx0 || T.xa > bx0 + 7 || T.yb < by0 || T.ya > by0 + 3) return false;
-  const int Pxlo = bx0 * kSub + kSub / 2, Pxhi = Pxlo + 7 * kSub;
-  const int Pylo = by0 * kSub + kSub / 2, Pyhi = Pylo + 3 * kSub;
+  constexpr int BH = 32 / BW;
+  if (T.xb < bx0 || T.xa > bx0 + BW - 1 || T.yb < by0 || T.ya > by0 + BH - 1) return false;
+  const int Pxlo = bx0 * kSub + kSub / 2, Pxhi = Pxlo + (BW - 1) * kSub;
+  const int Pylo = by0 * kSub + kSub / 2, Pyhi = Pylo + (BH - 1) * kSub;
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
     const long long mx = T.c[e] + (long long)T.dx[e] * (T.dx[e] > 0 ? Pyhi : Pylo) -
@@ -68,7 +72,7 @@ struct TileStage {
 
 // Calls visit(T, prim_id, depth) for every triangle of the tile covering
 // this thread's pixel centre.  Must be called by all 256 threads.
-template <class Visit>
+template <int BW = 8, class Visit>
 __device__ __forceinline__ void for_each_fragment(const BinsView &bv, int tile, const TilePixel &tp,
                                                   TileStage &st, Visit &&visit) {
   const int Px = tp.px * kSub + kSub / 2, Py = tp.py * kSub + kSub / 2;
@@ -89,7 +93,7 @@ __device__ __forceinline__ void for_each_fragment(const BinsView &bv, int tile, 
     int m = 0;
     for (int k0 = 0; k0 < n; k0 += 32) {
       const int k = k0 + lane;
-      const bool hit = k < n && block_maybe(st.tri[k], tp.bx0, tp.by0);
+      const bool hit = k < n && block_maybe<BW>(st.tri[k], tp.bx0, tp.by0);
       const uint32_t b = __ballot_sync(0xffffffffu, hit);
       if (hit) st.list[warp][m + __popc(b & ((1u << lane) - 1u))] = (uint8_t)k;
       m += __popc(b);

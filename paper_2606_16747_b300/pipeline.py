@@ -28,7 +28,8 @@ def _i32(vals, device):
 
 class Renderer:
     def __init__(self, verts, rgba8, W, H, params=None, x_dtype=sn.F32, mlp=None,
-                 pair_capacity=None, device="cuda", base_tile=None, fused=False):
+                 pair_capacity=None, device="cuda", base_tile=None, fused=False,
+                 persistent=False, tuning=None):
         self.device = device
         self.W, self.H = int(W), int(H)
         self.P = self.W * self.H
@@ -42,6 +43,9 @@ class Renderer:
         self.x_dtype = x_dtype
         # fused: upscale + features + BF16 MLP + composite in one kernel
         self.fused = bool(fused)
+        # persistent: the three geometry passes in one launch (tuning: (block_w, ctas_per_sm))
+        self.persistent = bool(persistent)
+        self.tuning = tuning
         if self.fused and x_dtype != sn.BF16:
             raise ValueError("the fused resolve runs the BF16 tensor-core MLP")
         cap = pair_capacity if pair_capacity is not None else max(1 << 20, 96 * self.T)
@@ -127,12 +131,19 @@ class Renderer:
                 (self.vp, self.state_size(2), self.W, self.H, b2, self.full_size),
                 (self.vp, self.state_size(3), self.W, self.H, b3, self.full_size)], self.status, stream)
 
-        st = [("raster", raster),
-              ("pass1", lambda: sn.geometry_pass_merged(self.scene, b1, b2, b3, self.l1, self.l2,
-                                                        self.l3, self.status, stream)),
-              ("pass2", lambda: sn.geometry_pass(self.scene, b2, 2, self.l2, self.status, stream)),
-              ("pass3", lambda: sn.geometry_pass(self.scene, b3, 3, self.l3, self.status, stream)),
-              ]
+        st = [("raster", raster)]
+        if self.persistent:
+            st.append(("passes", lambda: sn.geometry_passes(self.scene, b1, b2, b3, self.l1, self.l2,
+                                                            self.l3, self.tuning, self.status,
+                                                            stream)))
+        else:
+            st += [("pass1", lambda: sn.geometry_pass_merged(self.scene, b1, b2, b3, self.l1,
+                                                             self.l2, self.l3, self.status,
+                                                             stream)),
+                   ("pass2", lambda: sn.geometry_pass(self.scene, b2, 2, self.l2, self.status,
+                                                      stream)),
+                   ("pass3", lambda: sn.geometry_pass(self.scene, b3, 3, self.l3, self.status,
+                                                      stream))]
         if self.fused:
             st.append(("resolve", lambda: sn.resolve(self.scene, b2, b3, self.l1, self.l2, self.l3,
                                                      self.W, self.H, self.params, self.mlp,

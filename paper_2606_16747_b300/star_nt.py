@@ -26,7 +26,7 @@ EXPORTS = ("star_nt_version", "star_nt_status_string", "star_nt_default_params",
            "star_nt_reproject", "star_nt_geometry_pass", "star_nt_upscale_features",
            "star_nt_geometry_pass_merged", "star_nt_abuffer", "star_nt_train_ws_bytes",
            "star_nt_mse_grad", "star_nt_mlp_backward", "star_nt_adam", "star_nt_raster_passes",
-           "star_nt_resolve")
+           "star_nt_resolve", "star_nt_geometry_passes")
 
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
@@ -70,6 +70,10 @@ class Mlp(ctypes.Structure):
     _fields_ = [("w1", _P), ("b1", _P), ("w2", _P), ("b2", _P), ("w3", _P), ("b3", _P)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("block_w", _I32), ("ctas_per_sm", _I32)]
+
+
 class PassState(ctypes.Structure):
     _fields_ = [("W", _I32), ("H", _I32), ("W2", _I32), ("H2", _I32), ("W3", _I32), ("H3", _I32),
                 ("s2", ctypes.c_float), ("s3", ctypes.c_float), ("wbar", ctypes.c_double),
@@ -111,6 +115,8 @@ def lib():
                                             ctypes.POINTER(Layers), _P, _P]
         L.star_nt_geometry_pass_merged.argtypes = [ctypes.POINTER(Scene)] + [ctypes.POINTER(Bins)] * 3 + \
             [ctypes.POINTER(Layers)] * 3 + [_P, _P]
+        L.star_nt_geometry_passes.argtypes = [ctypes.POINTER(Scene)] + [ctypes.POINTER(Bins)] * 3 + \
+            [ctypes.POINTER(Layers)] * 3 + [ctypes.POINTER(Tuning), _P, _P]
         L.star_nt_upscale_features.argtypes = [ctypes.POINTER(Scene)] + [ctypes.POINTER(Bins)] * 2 + \
             [ctypes.POINTER(Layers)] * 3 + [_I32, _I32, ctypes.POINTER(Params),
                                             ctypes.POINTER(Features), _P]
@@ -243,6 +249,16 @@ def geometry_pass_merged(scene: Scene, bins1, bins2, bins3, layers1, layers2, la
     _check("star_nt_geometry_pass_merged", lib().star_nt_geometry_pass_merged(
         ctypes.byref(scene), ctypes.byref(bins1.c), ctypes.byref(bins2.c), ctypes.byref(bins3.c),
         *[ctypes.byref(l) for l in ls], _ptr(status), _stream(stream)))
+
+
+def geometry_passes(scene: Scene, bins1, bins2, bins3, layers1, layers2, layers3, tuning=None,
+                    status=None, stream=None):
+    ls = [layers_struct(l) for l in (layers1, layers2, layers3)]
+    t = Tuning(*tuning) if tuning is not None else None
+    _check("star_nt_geometry_passes", lib().star_nt_geometry_passes(
+        ctypes.byref(scene), ctypes.byref(bins1.c), ctypes.byref(bins2.c), ctypes.byref(bins3.c),
+        *[ctypes.byref(l) for l in ls], ctypes.byref(t) if t is not None else None, _ptr(status),
+        _stream(stream)))
 
 
 def upscale_features(scene: Scene, bins2, bins3, layers1, layers2, layers3, W, H, params: Params,

@@ -529,3 +529,29 @@ def test_fused_resolve_equals_separate_kernels(orc, sn):
                        threads=4)
     rgb = outs[1][0].cpu().numpy().reshape(-1, 4)[:, :3]
     assert np.max(np.abs(rgb - o["rgb"])) <= TOL_BF16
+
+
+@pytest.mark.parametrize("tuning", [None, (16, 0), (4, 3)])
+@pytest.mark.parametrize("sizes", [((131, 91), (57, 40)), ("full", (57, 40)), ("full", "full")])
+def test_persistent_passes_equal_separate(sn, tuning, sizes):
+    """The three passes in one persistent launch give the same planes bit for
+    bit as the separate pass kernels, for every tile shape."""
+    from paper_2606_16747_b300.pipeline import Renderer
+    sc = scenes.screen_scene(37, 2500, 208, 144, size_scale=0.7)
+    W, H = sc.width, sc.height
+    s2 = (W, H) if sizes[0] == "full" else sizes[0]
+    s3 = (W, H) if sizes[1] == "full" else sizes[1]
+    res = []
+    for persistent in (False, True):
+        r = Renderer(sc.verts, sc.rgba8, W, H, mlp=scenes.mlp_xavier(4), x_dtype=sn.BF16,
+                     persistent=persistent, tuning=tuning if persistent else None)
+        r.set_camera(sc.cam.vp32)
+        r.state.view(torch.int32)[:6] = torch.tensor([W, H, *s2, *s3], dtype=torch.int32)
+        r.star_frame(update_tiles=False)
+        torch.cuda.synchronize()
+        r.check_status()
+        res.append([r.l1["id1"].clone(), r.l1["z1"].clone(), r.l2["id2"][:s2[0] * s2[1]].clone(),
+                    r.l3["n"][:s3[0] * s3[1]].clone(), r.l3["tail"][:4 * s3[0] * s3[1]].clone(),
+                    r.l3["t_tail"][:s3[0] * s3[1]].clone(), r.rgba32f.clone()])
+    for a, b in zip(*res):
+        assert torch.equal(a, b)
