@@ -28,6 +28,8 @@ struct __align__(16) TriSetup {
   unsigned long long rg;      // a8*r8 | (a8*g8) << 32
   unsigned long long ba;      // a8*b8 | a8 << 32
   unsigned long long lg;      // round(-log2(1 - a8/255) * 2^32), 0 when opaque
+  float zlo;                  // lower bound of every fragment depth of the triangle
+  uint32_t pad;
 };
 static_assert(sizeof(TriSetup) == 112, "TriSetup layout");
 

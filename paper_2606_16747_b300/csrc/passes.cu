@@ -46,11 +46,31 @@ __device__ __forceinline__ void pass_body(const BinsView &bv, const uint32_t *__
   int i1 = 0x7fffffff, i2 = 0x7fffffff;
   uint32_t N = 0, opq = 0;
   unsigned long long rg = 0, ba = 0, lg = 0;
-  for_each_fragment<BW>(bv, tile, tp, stage, [&](const TriSetup &T, uint32_t id_u, float z) {
+  // A fragment deeper than the current k-th nearest cannot enter the top k:
+  // the passes without tail sums let the warp skip a triangle whose depth
+  // lower bound exceeds every lane's k-th depth (lanes outside the target
+  // never store, so they never hold a skip back); the tail passes must see
+  // every fragment and only skip the depth of such fragments.
+  const bool inside = tp.px < W && tp.py < H;
+  auto bound = [&] {
+    if (MODE >= kTail) return INFINITY;
+    return inside ? (MODE == kTop1 ? z1 : z2) : -INFINITY;
+  };
+  for_each_fragment<BW, true>(bv, tile, tp, stage, bound,
+                              [&](const TriSetup &T, uint32_t id_u, long long e0, long long e2) {
     const int id = (int)id_u;
+    if (MODE >= kTail) {
+      ++N;
+      rg += T.rg;
+      ba += T.ba;
+      lg += T.lg;
+      opq += T.opq;
+    }
     if (MODE == kTop1) {
+      const float z = frag_depth(T, e0, e2);
       if (z < z1 || (z == z1 && id < i1)) { z1 = z; i1 = id; }
-    } else {
+    } else if (!(T.zlo > z2)) {
+      const float z = frag_depth(T, e0, e2);
       if (z < z2 || (z == z2 && id < i2)) {
         if (z < z1 || (z == z1 && id < i1)) {
           z2 = z1; i2 = i1; z1 = z; i1 = id;
@@ -59,15 +79,8 @@ __device__ __forceinline__ void pass_body(const BinsView &bv, const uint32_t *__
         }
       }
     }
-    if (MODE >= kTail) {
-      ++N;
-      rg += T.rg;
-      ba += T.ba;
-      lg += T.lg;
-      opq += T.opq;
-    }
   });
-  if (tp.px >= W || tp.py >= H) return;
+  if (!inside) return;
   const size_t p = (size_t)tp.py * W + tp.px;
   const bool has1 = i1 != 0x7fffffff, has2 = i2 != 0x7fffffff;
   if (po.id1) po.id1[p] = has1 ? i1 : -1;

@@ -81,6 +81,10 @@ __device__ __forceinline__ void triangle_setup(int t, const float *__restrict__ 
     S.dz1 = __fsub_rn(zn[1], zn[0]);
     S.dz2 = __fsub_rn(zn[2], zn[0]);
     S.r = __frcp_rn(__ll2float_rn(area));
+    // Every fragment depth is an interpolation of the vertex depths in [0, 1]
+    // with barycentric weights >= 0 summing to 1 up to a few roundings of
+    // 2^-24, so it is at least min(z) - 2^-21; 2^-16 leaves ample room.
+    S.zlo = __fsub_rn(fminf(zn[0], fminf(zn[1], zn[2])), 1.52587890625e-05f);
     long long minx = min(X[0], min(X[1], X[2])), maxx = max(X[0], max(X[1], X[2]));
     long long miny = min(Y[0], min(Y[1], Y[2])), maxy = max(Y[0], max(Y[1], Y[2]));
     long long xa = -floor_div_ll(-(minx - kSub / 2), kSub), xb = floor_div_ll(maxx - kSub / 2, kSub);
@@ -94,6 +98,7 @@ __device__ __forceinline__ void triangle_setup(int t, const float *__restrict__ 
 #pragma unroll
     for (int e = 0; e < 3; ++e) { S.dx[e] = 0; S.dy[e] = 0; S.c[e] = -1; }
     S.own = 0; S.z0 = S.dz1 = S.dz2 = S.r = 0.0f;
+    S.zlo = INFINITY;
   }
   const uint32_t col = __ldg(rgba8 + t);
   const unsigned long long a8 = col >> 24, r8 = col & 255u, g8 = (col >> 8) & 255u,
@@ -101,6 +106,7 @@ __device__ __forceinline__ void triangle_setup(int t, const float *__restrict__ 
   S.opq = a8 == 255 ? 1u : 0u;
   S.rg = (a8 * r8) | ((a8 * g8) << 32);
   S.ba = (a8 * b8) | (a8 << 32);
+  S.pad = 0;
   S.lg = a8 == 255 ? 0ull
                    : __double2ull_rn((log2(255.0) - log2((double)(255 - a8))) * 4294967296.0);
   *out = S;
@@ -397,7 +403,8 @@ __global__ void __launch_bounds__(256) k_frag_count(BinsView bv, uint32_t *count
   if (tile >= hd->n_tiles) return;
   const TilePixel tp = tile_pixel<8>(tile, hd->tiles_x);
   uint32_t n = 0;
-  for_each_fragment(bv, tile, tp, stage, [&](const TriSetup &, uint32_t, float) { ++n; });
+  for_each_fragment(bv, tile, tp, stage, [] { return INFINITY; },
+                    [&](const TriSetup &, uint32_t, long long, long long) { ++n; });
   if (tp.px < W && tp.py < H) count[tp.py * W + tp.px] = n;
 }
 
@@ -417,9 +424,10 @@ __global__ void __launch_bounds__(256) k_frag_fill(BinsView bv, const uint32_t *
   const TilePixel tp = tile_pixel<8>(tile, hd->tiles_x);
   const bool inside = tp.px < W && tp.py < H;
   uint32_t pos = inside ? offset[tp.py * W + tp.px] : 0u;
-  for_each_fragment(bv, tile, tp, stage, [&](const TriSetup &, uint32_t id, float z) {
+  for_each_fragment(bv, tile, tp, stage, [] { return INFINITY; },
+                    [&](const TriSetup &T, uint32_t id, long long e0, long long e2) {
     if (inside) {
-      zs[pos] = z;
+      zs[pos] = frag_depth(T, e0, e2);
       prims[pos] = (int32_t)id;
       ++pos;
     }

@@ -67,26 +67,66 @@ __device__ __forceinline__ bool block_maybe(const TriSetup &T, int bx0, int by0)
 struct TileStage {
   TriSetup tri[kChunk];
   uint32_t id[kChunk];
+  uint32_t src[kChunk];     // binned ids before the depth sort
+  float key[kChunk];        // their depth lower bounds
+  uint8_t rank[kChunk];     // staged position of each binned entry
   uint8_t list[8][kChunk];  // per-warp lists of staged triangle indices
 };
 
-// Calls visit(T, prim_id, depth) for every triangle of the tile covering
-// this thread's pixel centre.  Must be called by all 256 threads.
-template <int BW = 8, class Visit>
+// Calls visit(T, prim_id, e0, e2) for every triangle of the tile covering
+// this thread's pixel centre, with the biased edge functions 0 and 2 there
+// (frag_depth gives the fragment's depth from them).  Must be called by all
+// 256 threads.
+//
+// bound() is this thread's depth bound: a staged triangle is skipped by the
+// whole warp when its depth lower bound exceeds bound() on every lane (no
+// fragment of it can then matter to the caller); return INFINITY to visit
+// every fragment.  With SORTED, each staged chunk is ordered by depth lower
+// bound (ties by binned position) first, so that near triangles come first
+// and raise the bounds early; the set of fragments visited is the same.
+template <int BW = 8, bool SORTED = false, class Bound, class Visit>
 __device__ __forceinline__ void for_each_fragment(const BinsView &bv, int tile, const TilePixel &tp,
-                                                  TileStage &st, Visit &&visit) {
+                                                  TileStage &st, Bound &&bound, Visit &&visit) {
   const int Px = tp.px * kSub + kSub / 2, Py = tp.py * kSub + kSub / 2;
   const int warp = threadIdx.x >> 5;
   const uint32_t beg = bv.tile_offset[tile], end = bv.tile_offset[tile + 1];
   for (uint32_t base = beg; base < end; base += kChunk) {
     const int n = (int)min((uint32_t)kChunk, end - base);
     __syncthreads();
-    for (int i = threadIdx.x; i < n * 7; i += blockDim.x) {
-      const int k = i / 7, part = i - 7 * k;
-      const uint32_t id = __ldg(bv.pairs + base + k);
-      reinterpret_cast<uint4 *>(st.tri + k)[part] =
-          __ldg(reinterpret_cast<const uint4 *>(bv.setups + id) + part);
-      if (part == 0) st.id[k] = id;
+    if (SORTED) {
+      const int t = threadIdx.x;
+      if (t < n) {
+        const uint32_t id = __ldg(bv.pairs + base + t);
+        st.src[t] = id;
+        st.key[t] = __ldg(&bv.setups[id].zlo);
+      }
+      __syncthreads();
+      if (t < n) {  // rank by (key, position): a permutation of 0 .. n-1
+        const float kt = st.key[t];
+        int r = 0;
+        for (int j = 0; j < n; ++j) {
+          const float kj = st.key[j];
+          r += (kj < kt || (kj == kt && j < t)) ? 1 : 0;
+        }
+        st.rank[t] = (uint8_t)r;
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < n * 7; i += blockDim.x) {
+        const int k = i / 7, part = i - 7 * k;
+        const uint32_t id = st.src[k];
+        const int d = st.rank[k];
+        reinterpret_cast<uint4 *>(st.tri + d)[part] =
+            __ldg(reinterpret_cast<const uint4 *>(bv.setups + id) + part);
+        if (part == 0) st.id[d] = id;
+      }
+    } else {
+      for (int i = threadIdx.x; i < n * 7; i += blockDim.x) {
+        const int k = i / 7, part = i - 7 * k;
+        const uint32_t id = __ldg(bv.pairs + base + k);
+        reinterpret_cast<uint4 *>(st.tri + k)[part] =
+            __ldg(reinterpret_cast<const uint4 *>(bv.setups + id) + part);
+        if (part == 0) st.id[k] = id;
+      }
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
@@ -99,14 +139,15 @@ __device__ __forceinline__ void for_each_fragment(const BinsView &bv, int tile, 
       m += __popc(b);
     }
     __syncwarp();
-    for (int i = 0; i < m; ++i) {
+    for (int i = 0; i < m; ++i) {  // m is warp-uniform
       const int k = st.list[warp][i];
       const TriSetup &T = st.tri[k];
+      if (__all_sync(0xffffffffu, T.zlo > bound())) continue;
       const long long e0 = (long long)T.dx[0] * Py + T.c[0] - (long long)T.dy[0] * Px;
       const long long e1 = (long long)T.dx[1] * Py + T.c[1] - (long long)T.dy[1] * Px;
       const long long e2 = (long long)T.dx[2] * Py + T.c[2] - (long long)T.dy[2] * Px;
       if ((e0 | e1 | e2) < 0) continue;
-      visit(T, st.id[k], frag_depth(T, e0, e2));
+      visit(T, st.id[k], e0, e2);
     }
   }
 }
