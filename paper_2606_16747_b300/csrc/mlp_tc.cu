@@ -2,18 +2,18 @@
 // tcgen05 tensor cores: bf16 operands, fp32 accumulation in tensor memory.
 //
 // One CTA of 128 threads runs a persistent loop over 128-pixel tiles.  Per
-// tile, three chained MMAs (M = 128 pixels):
-//   D1[128x32] = X[128x16]  W1^T   (K padded 5 -> 16; the upper half of K is a
-//                                    zero block in shared memory)
-//   D2[128x16] = H1[128x32] W2^T   (two K = 16 steps)
-//   D3[128x16] = H2[128x16] W3^T   (N padded 3 -> 16)
+// tile, three chained MMAs (M = 128 pixels); each bias rides in its MMA as two
+// weight columns against a constant operand block whose rows are (1, 1, 0, ...):
+//   D1[128x32] = [X | 1]    [W1 | b1]^T   (K = 16: 5 inputs, then the ones block)
+//   D2[128x16] = [H1 | 1 0] [W2 | b2]^T   (K = 48: three K = 16 steps)
+//   D3[128x16] = [H2 | 1 0] [W3 | b3]^T   (K = 32; N padded 3 -> 16)
 // X tiles arrive by TMA (double buffered, one tile ahead); after each MMA
 // the four warps read their 32 accumulator rows from tensor memory, apply
-// bias and ReLU, and write the next layer's bf16 operand to shared memory.
-// Operands use the no-swizzle K-major layout: 8-row x 16-byte core matrices,
-// LBO = distance between K-adjacent core matrices, SBO = between 8-row
-// groups.  Every mbarrier wait is bounded (1 s); on expiry the kernel sets
-// STAR_NT_ERR_TIMEOUT, stops, frees its tensor memory and returns.
+// ReLU while packing to bf16, and write the next layer's operand to shared
+// memory.  Operands use the no-swizzle K-major layout: 8-row x 16-byte core
+// matrices, LBO = distance between K-adjacent core matrices, SBO = between
+// 8-row groups.  Every mbarrier wait is bounded (1 s); on expiry the kernel
+// sets STAR_NT_ERR_TIMEOUT, stops, frees its tensor memory and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -30,15 +30,16 @@ constexpr uint32_t kTmemCols = 64;          // D1: 0..31, D2: 32..47, D3: 48..63
 constexpr int kMlpCtasPerSm = 8;            // 8 x 64 columns = all of tensor memory
 
 // shared memory map (bytes from a 1024-aligned base)
-constexpr uint32_t kSX = 0;         // 2 x (X tile 2048 + zero block 2048)
+constexpr uint32_t kSX = 0;         // 2 X tiles of 2048 (TMA targets)
+constexpr uint32_t kSC = 4096;      // ones block: rows (1, 1, 0, ...)
+constexpr uint32_t kSZ = 6144;      // zero block
 constexpr uint32_t kSH1 = 8192;     // 4 core columns x 2048
 constexpr uint32_t kSH2 = 16384;    // 2 core columns x 2048
-constexpr uint32_t kSW1 = 20480;    // N=32, K=16: 2 x 512
-constexpr uint32_t kSW2 = 21504;    // N=16, K=32: 4 x 256
-constexpr uint32_t kSW3 = 22528;    // N=16, K=16: 2 x 256
-constexpr uint32_t kSB = 23040;     // b1[32], b2[16], b3[16] float
-constexpr uint32_t kSBar = 23296;   // tma[2], mma, tmem slot
-constexpr uint32_t kSmemUsed = 23360;
+constexpr uint32_t kSW1 = 20480;    // N=32, K=16 (bias in K 8, 9): 2 x 512
+constexpr uint32_t kSW2 = 21504;    // N=16, K=48 (bias in K 32, 33): 6 x 256
+constexpr uint32_t kSW3 = 23040;    // N=16, K=32 (bias in K 16, 17): 4 x 256
+constexpr uint32_t kSBar = 24064;   // tma[2], mma, tmem slot, abort flag
+constexpr uint32_t kSmemUsed = 24096;
 // requested dynamic shared memory: caps residency at 8 CTAs per SM so that
 // the 8 x 64 tensor-memory columns always suffice
 constexpr uint32_t kSmemBytes = 26 * 1024;
@@ -57,22 +58,18 @@ __global__ void __launch_bounds__(kMlpThreads, kMlpCtasPerSm)
   const uint32_t bar_tma0 = sbase + kSBar, bar_tma1 = sbase + kSBar + 8, bar_mma = sbase + kSBar + 16;
   uint32_t *s_tmem = reinterpret_cast<uint32_t *>(sm + kSBar + 24);
   volatile int *s_abort = reinterpret_cast<volatile int *>(sm + kSBar + 28);
-  float *sb = reinterpret_cast<float *>(sm + kSB);
 
-  // weights (bf16, zero padded), biases, zero K blocks of the X buffers
-  for (int i = tid; i < (int)(kSBar - kSW1) / 4; i += kMlpThreads)
-    reinterpret_cast<uint32_t *>(sm + kSW1)[i] = 0u;
-  for (int i = tid; i < 512; i += kMlpThreads) {  // 2 x 2048-byte zero blocks
-    reinterpret_cast<uint32_t *>(sm + kSX + 2048)[i] = 0u;
-    reinterpret_cast<uint32_t *>(sm + kSX + 6144)[i] = 0u;
-  }
+  // weights and bias columns (bf16, zero padded), the ones and zero blocks
+  for (int i = tid; i < (int)(kSBar - kSC) / 4; i += kMlpThreads)
+    reinterpret_cast<uint32_t *>(sm + kSC)[i] = 0u;
   __syncthreads();
+  put_ones_block(sm + kSC, tid, kMlpThreads);
   for (int i = tid; i < 32 * 5; i += kMlpThreads) put_w(sm + kSW1, i / 5, i % 5, 512, w1[i]);
   for (int i = tid; i < 16 * 32; i += kMlpThreads) put_w(sm + kSW2, i / 32, i % 32, 256, w2[i]);
   for (int i = tid; i < 3 * 16; i += kMlpThreads) put_w(sm + kSW3, i / 16, i % 16, 256, w3[i]);
-  if (tid < 32) sb[tid] = b1[tid];
-  if (tid < 16) sb[32 + tid] = b2[tid];
-  if (tid < 16) sb[48 + tid] = tid < 3 ? b3[tid] : 0.0f;
+  if (tid < 32) put_bias(sm + kSW1, tid, 8, 512, b1[tid]);
+  if (tid < 16) put_bias(sm + kSW2, tid, 32, 256, b2[tid]);
+  if (tid < 3) put_bias(sm + kSW3, tid, 16, 256, b3[tid]);
   if (tid == 0) {
     mbar_init(bar_tma0, 1);
     mbar_init(bar_tma1, 1);
@@ -102,10 +99,12 @@ __global__ void __launch_bounds__(kMlpThreads, kMlpCtasPerSm)
   bool tma_pending = false;          // a TMA load in flight (thread 0)
   uint32_t pend_bar = 0, pend_ph = 0;
   const uint64_t dW1 = smem_desc(sbase + kSW1, 512, 128);
-  const uint64_t dW2a = smem_desc(sbase + kSW2, 256, 128), dW2b = smem_desc(sbase + kSW2 + 512, 256, 128);
-  const uint64_t dW3 = smem_desc(sbase + kSW3, 256, 128);
+  const uint64_t dW2[3] = {smem_desc(sbase + kSW2, 256, 128), smem_desc(sbase + kSW2 + 512, 256, 128),
+                           smem_desc(sbase + kSW2 + 1024, 256, 128)};
+  const uint64_t dW3[2] = {smem_desc(sbase + kSW3, 256, 128), smem_desc(sbase + kSW3 + 512, 256, 128)};
   const uint64_t dH1a = smem_desc(sbase + kSH1, 2048, 128), dH1b = smem_desc(sbase + kSH1 + 4096, 2048, 128);
   const uint64_t dH2 = smem_desc(sbase + kSH2, 2048, 128);
+  const uint64_t dOnes = smem_desc(sbase + kSC, kSZ - kSC, 128);  // K block: ones, then zeros
 
   if (tid == 0 && tile < ntiles) {
     mbar_expect_tx(bar_tma0, 2048);
@@ -116,7 +115,7 @@ __global__ void __launch_bounds__(kMlpThreads, kMlpCtasPerSm)
   }
   while (tile < ntiles) {
     const long long next = tile + gridDim.x;
-    const uint32_t xs = sbase + kSX + buf * 4096;
+    const uint32_t xs = sbase + kSX + buf * 2048;
     // ---- layer 1
     if (tid == 0) {
       if (!mbar_wait(buf ? bar_tma1 : bar_tma0, ph_tma[buf])) {
@@ -125,12 +124,12 @@ __global__ void __launch_bounds__(kMlpThreads, kMlpCtasPerSm)
         tma_pending = false;
         ph_tma[buf] ^= 1u;
         fence_after();
-        mma_bf16(tmem + 0, smem_desc(xs, 2048, 128), dW1, idesc_bf16(32), 0u);
+        mma_bf16(tmem + 0, smem_desc(xs, sbase + kSC - xs, 128), dW1, idesc_bf16(32), 0u);
         mma_commit(bar_mma);
         if (next < ntiles) {
           const uint32_t nb = buf ? bar_tma0 : bar_tma1;
           mbar_expect_tx(nb, 2048);
-          tma_load_2d(sbase + kSX + (buf ^ 1) * 4096, &xmap, 0, (int)(next * kRows), nb);
+          tma_load_2d(sbase + kSX + (buf ^ 1) * 2048, &xmap, 0, (int)(next * kRows), nb);
           tma_pending = true;
           pend_bar = nb;
           pend_ph = ph_tma[buf ^ 1];
@@ -143,14 +142,14 @@ __global__ void __launch_bounds__(kMlpThreads, kMlpCtasPerSm)
     ph_mma ^= 1u;
     fence_after();
     const float flag = __bfloat162float(
-        *reinterpret_cast<const __nv_bfloat16 *>(sm + kSX + buf * 4096 + row * 16 + 10));
+        *reinterpret_cast<const __nv_bfloat16 *>(sm + kSX + buf * 2048 + row * 16 + 10));
     {
       float d[32];
       tmem_ld32(tmem + lane_base + 0, d);
       uint32_t pk[16];
 #pragma unroll
       for (int j = 0; j < 16; ++j)
-        pk[j] = pack_bf16(fmaxf(d[2 * j] + sb[2 * j], 0.0f), fmaxf(d[2 * j + 1] + sb[2 * j + 1], 0.0f));
+        pk[j] = pack_relu_bf16(d[2 * j], d[2 * j + 1]);
 #pragma unroll
       for (int kc = 0; kc < 4; ++kc)
         *reinterpret_cast<uint4 *>(sm + kSH1 + kc * 2048 + row * 16) =
@@ -163,8 +162,9 @@ __global__ void __launch_bounds__(kMlpThreads, kMlpCtasPerSm)
     // ---- layer 2
     if (tid == 0) {
       fence_after();
-      mma_bf16(tmem + 32, dH1a, dW2a, idesc_bf16(16), 0u);
-      mma_bf16(tmem + 32, dH1b, dW2b, idesc_bf16(16), 1u);
+      mma_bf16(tmem + 32, dH1a, dW2[0], idesc_bf16(16), 0u);
+      mma_bf16(tmem + 32, dH1b, dW2[1], idesc_bf16(16), 1u);
+      mma_bf16(tmem + 32, dOnes, dW2[2], idesc_bf16(16), 1u);
       mma_commit(bar_mma);
     }
     if (!mbar_wait(bar_mma, ph_mma)) *s_abort = 1;
@@ -176,8 +176,7 @@ __global__ void __launch_bounds__(kMlpThreads, kMlpCtasPerSm)
       uint32_t pk[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j)
-        pk[j] = pack_bf16(fmaxf(d[2 * j] + sb[32 + 2 * j], 0.0f),
-                          fmaxf(d[2 * j + 1] + sb[32 + 2 * j + 1], 0.0f));
+        pk[j] = pack_relu_bf16(d[2 * j], d[2 * j + 1]);
 #pragma unroll
       for (int kc = 0; kc < 2; ++kc)
         *reinterpret_cast<uint4 *>(sm + kSH2 + kc * 2048 + row * 16) =
@@ -190,7 +189,8 @@ __global__ void __launch_bounds__(kMlpThreads, kMlpCtasPerSm)
     // ---- layer 3
     if (tid == 0) {
       fence_after();
-      mma_bf16(tmem + 48, dH2, dW3, idesc_bf16(16), 0u);
+      mma_bf16(tmem + 48, dH2, dW3[0], idesc_bf16(16), 0u);
+      mma_bf16(tmem + 48, dOnes, dW3[1], idesc_bf16(16), 1u);
       mma_commit(bar_mma);
     }
     if (!mbar_wait(bar_mma, ph_mma)) *s_abort = 1;
@@ -203,9 +203,9 @@ __global__ void __launch_bounds__(kMlpThreads, kMlpCtasPerSm)
       if (p < P) {
         float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
         if (flag != 0.0f) {
-          o.x = fmaxf(d[0] + sb[48], 0.0f);
-          o.y = fmaxf(d[1] + sb[49], 0.0f);
-          o.z = fmaxf(d[2] + sb[50], 0.0f);
+          o.x = fmaxf(d[0], 0.0f);
+          o.y = fmaxf(d[1], 0.0f);
+          o.z = fmaxf(d[2], 0.0f);
         }
         F[p] = o;
       }

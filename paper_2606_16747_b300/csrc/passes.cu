@@ -369,12 +369,11 @@ extern "C" star_nt_status star_nt_build_inputs(const star_nt_scene *scene, const
   }
   if (!l1 || !l1->id1 || !l2 || !l2->id2 || !l3 || !l3->n || !l3->tail || !l3->t_tail)
     return STAR_NT_ERR_ARG;
-  star_nt_layers a = *l1, b = {}, c = {};
+  star_nt_layers b = {}, c = {};
   b.id2 = l2->id2;
   c.n = l3->n;
   c.tail = l3->tail;
   c.t_tail = l3->t_tail;
-  a.id2 = nullptr; a.n = nullptr; a.tail = nullptr; a.t_tail = nullptr;
   star_nt_status s;
   if ((s = star_nt_geometry_pass_merged(scene, b1, b2, b3, l1, l2, l3, d_status, stream)) !=
       STAR_NT_OK)

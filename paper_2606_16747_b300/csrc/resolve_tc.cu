@@ -7,8 +7,10 @@
 //
 // One CTA of 128 threads works on rounds of two 128-pixel tiles (thread r
 // owns row r of both).  Each round: features into shared memory as the bf16
-// A operand; layer 1 for both tiles (two MMAs, one commit); bias + ReLU into
-// the bf16 operand of layer 2; and so on; the composite in registers.  Tensor
+// A operand; layer 1 for both tiles (two MMAs, one commit); ReLU into the
+// bf16 operand of layer 2; and so on; the composite in registers.  Biases
+// ride in the MMAs (a constant-ones operand block against two bias weight
+// columns), so each epilogue is one ReLU-and-pack per two values.  Tensor
 // memory holds 32 columns per tile: D1 in columns [0, 32), then D2 in [0, 16)
 // and D3 in [16, 32) once D1 has been read.  Every mbarrier wait is bounded.
 #include <cuda_bf16.h>
@@ -25,17 +27,18 @@ constexpr int kRTiles = 2;                  // tiles per round
 constexpr uint32_t kRTmemCols = 64;         // 32 per tile
 constexpr int kRCtasPerSm = 8;              // 8 x 64 columns = all of tensor memory
 
-// shared memory map (bytes from a 1024-aligned base)
-constexpr uint32_t kQX = 0;         // X of tile 0 (2048), of tile 1 (2048), zero block (2048)
-constexpr uint32_t kQZ = 4096;
-constexpr uint32_t kQH = 6144;      // per tile 8192: H1 (4 core columns), later H2 (2)
-constexpr uint32_t kQW1 = 22528;    // N=32, K=16: 2 x 512
-constexpr uint32_t kQW2 = 23552;    // N=16, K=32: 4 x 256
-constexpr uint32_t kQW3 = 24576;    // N=16, K=16: 2 x 256
-constexpr uint32_t kQB = 25088;     // b1[32], b2[16], b3[16]
-constexpr uint32_t kQBar = 25344;   // mma barrier, tmem slot, abort flag
-constexpr uint32_t kQUsed = 25360;
-constexpr uint32_t kQSmem = 27 * 1024;  // caps residency at 8 CTAs per SM
+// shared memory map (bytes from a 1024-aligned base).  A tile's network
+// input X lives in the first core column of its H area: layer 1 consumes it
+// before H1 is written.
+constexpr uint32_t kQH = 0;         // per tile 8192: X, then H1 (4 core columns), then H2 (2)
+constexpr uint32_t kQC = 16384;     // ones block: rows (1, 1, 0, ...), the bias operand
+constexpr uint32_t kQZ = 18432;     // zero block
+constexpr uint32_t kQW1 = 20480;    // N=32, K=16 (bias in K 8, 9): 2 x 512
+constexpr uint32_t kQW2 = 21504;    // N=16, K=48 (bias in K 32, 33): 6 x 256
+constexpr uint32_t kQW3 = 23040;    // N=16, K=32 (bias in K 16, 17): 4 x 256
+constexpr uint32_t kQBar = 24064;   // mma barrier, tmem slot, abort flag
+constexpr uint32_t kQUsed = 24080;
+constexpr uint32_t kQSmem = 26 * 1024;  // caps residency at 8 CTAs per SM
 
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
   uint32_t r[4];
@@ -68,20 +71,19 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
   const uint32_t bar = sbase + kQBar;
   uint32_t *s_tmem = reinterpret_cast<uint32_t *>(sm + kQBar + 8);
   volatile int *s_abort = reinterpret_cast<volatile int *>(sm + kQBar + 12);
-  float *sb = reinterpret_cast<float *>(sm + kQB);
   if (in.hd2->n_pixels <= 0 || in.hd3->n_pixels <= 0) return;  // a pass was rejected
 
-  // weights (bf16, zero padded), biases, the zero K block of layer 1
-  for (int i = tid; i < (int)(kQBar - kQW1) / 4; i += kRThreads)
-    reinterpret_cast<uint32_t *>(sm + kQW1)[i] = 0u;
-  for (int i = tid; i < 512; i += kRThreads) reinterpret_cast<uint32_t *>(sm + kQZ)[i] = 0u;
+  // weights and bias columns (bf16, zero padded), the ones and zero blocks
+  for (int i = tid; i < (int)(kQBar - kQC) / 4; i += kRThreads)
+    reinterpret_cast<uint32_t *>(sm + kQC)[i] = 0u;
   __syncthreads();
+  put_ones_block(sm + kQC, tid, kRThreads);
   for (int i = tid; i < 32 * 5; i += kRThreads) put_w(sm + kQW1, i / 5, i % 5, 512, w1[i]);
   for (int i = tid; i < 16 * 32; i += kRThreads) put_w(sm + kQW2, i / 32, i % 32, 256, w2[i]);
   for (int i = tid; i < 3 * 16; i += kRThreads) put_w(sm + kQW3, i / 16, i % 16, 256, w3[i]);
-  if (tid < 32) sb[tid] = b1[tid];
-  if (tid < 16) sb[32 + tid] = b2[tid];
-  if (tid < 16) sb[48 + tid] = tid < 3 ? b3[tid] : 0.0f;
+  if (tid < 32) put_bias(sm + kQW1, tid, 8, 512, b1[tid]);
+  if (tid < 16) put_bias(sm + kQW2, tid, 32, 256, b2[tid]);
+  if (tid < 3) put_bias(sm + kQW3, tid, 16, 256, b3[tid]);
   if (tid == 0) {
     mbar_init(bar, 1);
     *s_abort = 0;
@@ -103,44 +105,47 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
   const int row = tid;
 
   const uint64_t dW1 = smem_desc(sbase + kQW1, 512, 128);
-  const uint64_t dW2a = smem_desc(sbase + kQW2, 256, 128), dW2b = smem_desc(sbase + kQW2 + 512, 256, 128);
-  const uint64_t dW3 = smem_desc(sbase + kQW3, 256, 128);
-  const long long P = (long long)in.W * in.H;
-  const long long nrounds = (P + kRTiles * kRRows - 1) / (kRTiles * kRRows);
+  const uint64_t dW2[3] = {smem_desc(sbase + kQW2, 256, 128), smem_desc(sbase + kQW2 + 512, 256, 128),
+                           smem_desc(sbase + kQW2 + 1024, 256, 128)};
+  const uint64_t dW3[2] = {smem_desc(sbase + kQW3, 256, 128), smem_desc(sbase + kQW3 + 512, 256, 128)};
+  const uint64_t dOnes = smem_desc(sbase + kQC, kQZ - kQC, 128);  // K block: ones, then zeros
+  const int P = in.W * in.H;  // < 2^31, checked by the host
+  const int nrounds = (P + kRTiles * kRRows - 1) / (kRTiles * kRRows);
   uint32_t ph = 0u;
 
-  for (long long round = blockIdx.x; round < nrounds; round += gridDim.x) {
-    const long long base = round * (kRTiles * kRRows);
+  for (int round = blockIdx.x; round < nrounds; round += gridDim.x) {
+    const int base = round * (kRTiles * kRRows);
     // ---- features of this thread's row in both tiles
     float4 front[kRTiles];
     bool flag[kRTiles];
 #pragma unroll
     for (int t = 0; t < kRTiles; ++t) {
-      const long long p = base + t * kRRows + row;
+      const int p = base + t * kRRows + row;
       float xv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       front[t] = make_float4(0.f, 0.f, 0.f, 0.f);
       if (p < P) {
-        const int y = (int)(p / in.W), x = (int)(p - (long long)y * in.W);
+        const int y = (int)((unsigned)p / (unsigned)in.W), x = p - y * in.W;
         pixel_features(in, bg0, bg1, bg2, kappa, x, y, xv, front[t]);
       }
       flag[t] = xv[5] != 0.0f;
       __nv_bfloat162 h0 = __floats2bfloat162_rn(xv[0], xv[1]);
       __nv_bfloat162 h1 = __floats2bfloat162_rn(xv[2], xv[3]);
       __nv_bfloat162 h2 = __floats2bfloat162_rn(xv[4], xv[5]);
-      *reinterpret_cast<uint4 *>(sm + kQX + t * 2048 + row * 16) =
+      *reinterpret_cast<uint4 *>(sm + kQH + t * 8192 + row * 16) =
           make_uint4(*reinterpret_cast<uint32_t *>(&h0), *reinterpret_cast<uint32_t *>(&h1),
                      *reinterpret_cast<uint32_t *>(&h2), 0u);
     }
     fence_async_smem();
     fence_before();
     __syncthreads();
-    // ---- layer 1
+    // ---- layer 1: [X | ones] (K = 16) against [W1 | b1]
     if (tid == 0) {
       fence_after();
 #pragma unroll
-      for (int t = 0; t < kRTiles; ++t)
-        mma_bf16(tmem + 32 * t, smem_desc(sbase + kQX + t * 2048, kQZ - (kQX + t * 2048), 128), dW1,
-                 idesc_bf16(32), 0u);
+      for (int t = 0; t < kRTiles; ++t) {
+        const uint32_t h = kQH + t * 8192;
+        mma_bf16(tmem + 32 * t, smem_desc(sbase + h, kQC - h, 128), dW1, idesc_bf16(32), 0u);
+      }
       mma_commit(bar);
     }
     if (!mbar_wait(bar, ph)) *s_abort = 1;
@@ -152,8 +157,7 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
       tmem_ld32(tmem + lane_base + 32 * t, d);
       uint32_t pk[16];
 #pragma unroll
-      for (int j = 0; j < 16; ++j)
-        pk[j] = pack_bf16(fmaxf(d[2 * j] + sb[2 * j], 0.0f), fmaxf(d[2 * j + 1] + sb[2 * j + 1], 0.0f));
+      for (int j = 0; j < 16; ++j) pk[j] = pack_relu_bf16(d[2 * j], d[2 * j + 1]);
 #pragma unroll
       for (int kc = 0; kc < 4; ++kc)
         *reinterpret_cast<uint4 *>(sm + kQH + t * 8192 + kc * 2048 + row * 16) =
@@ -163,14 +167,15 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
     fence_before();
     __syncthreads();
     if (*s_abort) break;
-    // ---- layer 2 (D2 over D1's first 16 columns)
+    // ---- layer 2: [H1 | ones | 0] (K = 48) against [W2 | b2], D2 over D1's first 16 columns
     if (tid == 0) {
       fence_after();
 #pragma unroll
       for (int t = 0; t < kRTiles; ++t) {
         const uint32_t h = sbase + kQH + t * 8192;
-        mma_bf16(tmem + 32 * t, smem_desc(h, 2048, 128), dW2a, idesc_bf16(16), 0u);
-        mma_bf16(tmem + 32 * t, smem_desc(h + 4096, 2048, 128), dW2b, idesc_bf16(16), 1u);
+        mma_bf16(tmem + 32 * t, smem_desc(h, 2048, 128), dW2[0], idesc_bf16(16), 0u);
+        mma_bf16(tmem + 32 * t, smem_desc(h + 4096, 2048, 128), dW2[1], idesc_bf16(16), 1u);
+        mma_bf16(tmem + 32 * t, dOnes, dW2[2], idesc_bf16(16), 1u);
       }
       mma_commit(bar);
     }
@@ -183,9 +188,7 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
       tmem_ld16(tmem + lane_base + 32 * t, d);
       uint32_t pk[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j)
-        pk[j] = pack_bf16(fmaxf(d[2 * j] + sb[32 + 2 * j], 0.0f),
-                          fmaxf(d[2 * j + 1] + sb[32 + 2 * j + 1], 0.0f));
+      for (int j = 0; j < 8; ++j) pk[j] = pack_relu_bf16(d[2 * j], d[2 * j + 1]);
 #pragma unroll
       for (int kc = 0; kc < 2; ++kc)
         *reinterpret_cast<uint4 *>(sm + kQH + t * 8192 + kc * 2048 + row * 16) =
@@ -195,13 +198,15 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
     fence_before();
     __syncthreads();
     if (*s_abort) break;
-    // ---- layer 3 (D3 in columns 16..31 of the tile)
+    // ---- layer 3: [H2 | ones | 0] (K = 32) against [W3 | b3], D3 in columns 16..31
     if (tid == 0) {
       fence_after();
 #pragma unroll
-      for (int t = 0; t < kRTiles; ++t)
-        mma_bf16(tmem + 32 * t + 16, smem_desc(sbase + kQH + t * 8192, 2048, 128), dW3, idesc_bf16(16),
-                 0u);
+      for (int t = 0; t < kRTiles; ++t) {
+        mma_bf16(tmem + 32 * t + 16, smem_desc(sbase + kQH + t * 8192, 2048, 128), dW3[0],
+                 idesc_bf16(16), 0u);
+        mma_bf16(tmem + 32 * t + 16, dOnes, dW3[1], idesc_bf16(16), 1u);
+      }
       mma_commit(bar);
     }
     if (!mbar_wait(bar, ph)) *s_abort = 1;
@@ -212,13 +217,13 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
     for (int t = 0; t < kRTiles; ++t) {
       float d[4];
       tmem_ld4(tmem + lane_base + 32 * t + 16, d);
-      const long long p = base + t * kRRows + row;
+      const int p = base + t * kRRows + row;
       if (p < P) {
         float f0 = 0.f, f1 = 0.f, f2 = 0.f;
         if (flag[t]) {
-          f0 = fmaxf(d[0] + sb[48], 0.0f);
-          f1 = fmaxf(d[1] + sb[49], 0.0f);
-          f2 = fmaxf(d[2] + sb[50], 0.0f);
+          f0 = fmaxf(d[0], 0.0f);
+          f1 = fmaxf(d[1], 0.0f);
+          f2 = fmaxf(d[2], 0.0f);
         }
         const float4 fr = front[t];
         const float r = fmaf(fr.w, f0, fr.x), g = fmaf(fr.w, f1, fr.y), b = fmaf(fr.w, f2, fr.z);
@@ -258,7 +263,7 @@ extern "C" star_nt_status star_nt_resolve(const star_nt_scene *scene, const star
     return STAR_NT_ERR_ARG;
   if (((uintptr_t)rgba32f & 15u) || ((uintptr_t)l3->tail & 15u)) return STAR_NT_ERR_ARG;
   if (scene->n_tris > 0 && !scene->rgba8) return STAR_NT_ERR_ARG;
-  if ((long long)W * H > 0x7fffffffLL) return STAR_NT_ERR_ARG;
+  if ((long long)W * H > 0x7fffffffLL - 256) return STAR_NT_ERR_ARG;
   static bool attr = false;
   if (!attr) {
     if (cudaFuncSetAttribute(k_resolve, cudaFuncAttributeMaxDynamicSharedMemorySize, kQSmem) !=

@@ -130,10 +130,35 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   return *reinterpret_cast<uint32_t *>(&h);
 }
 
+// ReLU of two fp32 values packed as bf16x2 (lo in the low half), round to
+// nearest even: one cvt
+__device__ __forceinline__ uint32_t pack_relu_bf16(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+
 // one bf16 weight into the K-major core-matrix layout of a B operand
 __device__ __forceinline__ void put_w(uint8_t *base, int n, int k, int lbo, float v) {
   __nv_bfloat16 h = __float2bfloat16_rn(v);
   *reinterpret_cast<__nv_bfloat16 *>(base + (k >> 3) * lbo + n * 16 + (k & 7) * 2) = h;
+}
+
+// A bias enters an MMA as two weight columns (k, k + 1) against an A operand
+// block whose rows hold (1, 1, 0, ...): b = hi + lo with hi = bf16(b) and
+// lo = bf16(b - hi), so the bias reaches the fp32 accumulator to about 2^-16
+// of its size and no epilogue add is needed.
+__device__ __forceinline__ void put_bias(uint8_t *base, int n, int k, int lbo, float b) {
+  const float hi = __bfloat162float(__float2bfloat16_rn(b));
+  put_w(base, n, k, lbo, hi);
+  put_w(base, n, k + 1, lbo, b - hi);
+}
+
+// rows (1, 1, 0, 0, 0, 0, 0, 0) in bf16: the constant core-matrix column of
+// the bias columns, 128 rows x 16 bytes
+__device__ __forceinline__ void put_ones_block(uint8_t *base, int tid, int nthreads) {
+  for (int r = tid; r < 128; r += nthreads)
+    *reinterpret_cast<uint4 *>(base + r * 16) = make_uint4(0x3F803F80u, 0u, 0u, 0u);
 }
 
 }  // namespace star
