@@ -8,6 +8,43 @@
 namespace star {
 
 // ---------------------------------------------------------------------------
+// Fixed-point tail weights: lg[a] = round(-log2(1 - a/255) * 2^32) for
+// a = 0 .. 254, tabulated at compile time so that set-up does no float64
+// arithmetic (slow on this part).  log2 x = k + ln(m) / ln 2 with x = 2^k m,
+// m in [1, 2), and ln m = 2 atanh z = 2 (z + z^3/3 + z^5/5 + ...) with
+// z = (m - 1) / (m + 1) <= 1/3: 40 terms are far below double rounding.
+struct LgTable {
+  unsigned long long v[256];
+};
+
+constexpr double series_log2(double x) {  // x >= 1
+  int k = 0;
+  while (x >= 2.0) {
+    x *= 0.5;
+    ++k;
+  }
+  const double z = (x - 1.0) / (x + 1.0), z2 = z * z;
+  double term = z, sum = 0.0;
+  for (int n = 0; n < 40; ++n) {
+    sum += term / (2 * n + 1);
+    term *= z2;
+  }
+  return k + 2.0 * sum / 0.69314718055994530942;  // ln 2
+}
+
+constexpr LgTable make_lg_table() {
+  LgTable t{};
+  for (int a = 0; a < 255; ++a) {
+    const double v = series_log2(255.0 / (255.0 - a)) * 4294967296.0;
+    t.v[a] = (unsigned long long)(v + 0.5);
+  }
+  t.v[255] = 0ull;  // opaque: counted apart
+  return t;
+}
+
+__device__ const LgTable g_lg = make_lg_table();
+
+// ---------------------------------------------------------------------------
 // Triangle set-up: one thread per triangle.  Transform with float32 and one
 // rounding per operation (order fixed), drop triangles with a vertex behind
 // the camera, outside NDC z in [0, 1] or outside the guard band, snap to
@@ -107,8 +144,7 @@ __device__ __forceinline__ void triangle_setup(int t, const float *__restrict__ 
   S.rg = (a8 * r8) | ((a8 * g8) << 32);
   S.ba = (a8 * b8) | (a8 << 32);
   S.pad = 0;
-  S.lg = a8 == 255 ? 0ull
-                   : __double2ull_rn((log2(255.0) - log2((double)(255 - a8))) * 4294967296.0);
+  S.lg = g_lg.v[a8];
   *out = S;
 }
 

@@ -54,6 +54,7 @@ class Renderer:
         f32 = dict(dtype=torch.float32, device=device)
         i32 = dict(dtype=torch.int32, device=device)
         self.status = torch.zeros(1, **i32)
+        self.side = torch.cuda.Stream(device=device)  # interpolated frame beside the quadtree
         self.vp = torch.zeros(16, **f32)
         self.full_size = _i32([self.W, self.H], device)
         # per-pass planes (sized for full resolution)
@@ -200,9 +201,17 @@ class Renderer:
                      self.interp_out, self.reproj_ws, stream, out_rgba8=self.interp_rgba8)
 
     def step(self, stream=None):
-        """One real STAR-NT frame followed by one interpolated frame."""
-        self.star_frame(stream)
-        self.interp_frame(stream)
+        """One real STAR-NT frame followed by one interpolated frame.  The
+        interpolated frame needs only the real frame's colour and depth, so it
+        runs on a second stream beside the quadtree update; the step ends when
+        both are done (both branches land in one captured graph)."""
+        main = stream if stream is not None else torch.cuda.current_stream()
+        self.star_frame(main, update_tiles=False)
+        self.side.wait_stream(main)
+        self.interp_frame(self.side)
+        with torch.cuda.stream(main):
+            self.update_tiles(main)
+        main.wait_stream(self.side)
 
     def capture(self, fn):
         """Capture ``fn`` (enqueueing work on the current stream) as a CUDA
