@@ -62,7 +62,7 @@ inline BinsLayout bins_layout(int32_t max_w, int32_t max_h, int32_t max_tris, in
   size_t o = 0;
   L.header = o;      o = align_up(o + sizeof(BinsHeader), 256);
   L.setups = o;      o = align_up(o + sizeof(TriSetup) * (size_t)max_tris, 256);
-  L.tile_count = o;  o = align_up(o + 4 * (size_t)(L.max_tiles + 1), 256);
+  L.tile_count = o;  o = align_up(o + 4 * (size_t)(L.max_tiles + 4), 256);  // + ticket, + vector tail
   L.tile_offset = o; o = align_up(o + 4 * (size_t)(L.max_tiles + 1), 256);
   L.tile_cursor = o; o = align_up(o + 4 * (size_t)L.max_tiles, 256);
   L.pairs = o;       o = align_up(o + 4 * (size_t)pairs, 256);

@@ -186,46 +186,102 @@ __device__ __forceinline__ int tile_span(const TriSetup &T, int &tx0, int &ty0, 
 }
 
 constexpr int kBinThreads = 128;
+constexpr int kBinTris = 32;  // triangles per binning block: four threads per triangle walk pairs
 
-// (triangle, tile) candidates of one block of kBinThreads triangles,
-// flattened so that every thread walks an equal share: an exclusive scan of
-// the per-triangle candidate counts, then a binary search per candidate.
-// Calls emit(triangle, tile) for every candidate that passes tile_hit.
+// (triangle, tile) candidates of one block's kBinTris triangles, whose
+// set-ups are staged in shared memory (tri[i] = triangle t0 + i), flattened
+// so that all kBinThreads threads walk an equal share: a warp scan of the
+// per-triangle candidate counts, then a binary search per candidate.  Calls
+// emit(triangle, tile) for every candidate that passes tile_hit.
 template <class Emit>
-__device__ __forceinline__ void for_each_pair(const BinsView &bv, int t0, int n_tris, int tiles_x,
+__device__ __forceinline__ void for_each_pair(const TriSetup *tri, int t0, int n_tris, int tiles_x,
                                               int *s_off, Emit &&emit) {
-  const int tid = threadIdx.x, t = t0 + tid;
-  int tx0 = 0, ty0 = 0, ntx = 1;
-  const int nt = t < n_tris ? tile_span(bv.setups[t], tx0, ty0, ntx) : 0;
-  // inclusive scan of nt over the block (warp shuffles, then warp totals)
-  int v = nt;
-  const int lane = tid & 31, warp = tid >> 5;
+  static_assert(kBinTris == 32, "one warp scans the candidate counts");
+  const int tid = threadIdx.x;
+  if (tid < 32) {
+    int tx0 = 0, ty0 = 0, ntx = 1;
+    const int nt = t0 + tid < n_tris ? tile_span(tri[tid], tx0, ty0, ntx) : 0;
+    int v = nt;
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, v, o);
-    if (lane >= o) v += y;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, v, o);
+      if (tid >= o) v += y;
+    }
+    s_off[tid + 1] = v;
+    if (tid == 0) s_off[0] = 0;
   }
-  __shared__ int s_w[kBinThreads / 32];
-  if (lane == 31) s_w[warp] = v;
   __syncthreads();
-  int before = 0;
-  for (int w = 0; w < warp; ++w) before += s_w[w];
-  s_off[tid + 1] = before + v;
-  if (tid == 0) s_off[0] = 0;
-  __syncthreads();
-  const int total = s_off[kBinThreads];
+  const int total = s_off[kBinTris];
   for (int q = tid; q < total; q += kBinThreads) {
-    int lo = 0, hi = kBinThreads - 1;  // largest j with s_off[j] <= q
+    int lo = 0, hi = kBinTris - 1;  // largest j with s_off[j] <= q
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
       if (s_off[mid] <= q) lo = mid; else hi = mid - 1;
     }
-    const TriSetup &T = bv.setups[t0 + lo];
+    const TriSetup &T = tri[lo];
     int ax0, ay0, anx;
     tile_span(T, ax0, ay0, anx);
     const int k = q - s_off[lo];
     const int tx = ax0 + k % anx, ty = ay0 + k / anx;
     if (tile_hit(T, tx, ty)) emit(t0 + lo, ty * tiles_x + tx);
+  }
+}
+
+// Exclusive scan of the tile counts of one pass by one block of kBinThreads
+// threads; thread i owns the run [i * per, (i + 1) * per) with per a multiple
+// of 4, read as batches of eight 16-byte loads in flight.  Writes the offsets,
+// the fill cursors (initialised to the offsets) and the total pair count.
+// The counts are read from L2, where the atomics landed.
+__device__ __forceinline__ uint32_t run_counts(const uint32_t *cnt, int j, int end, uint4 &v) {
+  v = j < end ? __ldcg(reinterpret_cast<const uint4 *>(cnt + j)) : make_uint4(0u, 0u, 0u, 0u);
+  if (j + 1 >= end) v.y = 0u;
+  if (j + 2 >= end) v.z = 0u;
+  if (j + 3 >= end) v.w = 0u;
+  return v.x + v.y + v.z + v.w;
+}
+
+__device__ void scan_tile_counts(const BinsView &bv, int n) {
+  __shared__ uint32_t s_sum[kBinThreads];
+  const int tid = threadIdx.x;
+  const int per = (((n + kBinThreads - 1) / kBinThreads) + 3) & ~3;
+  const int i0 = tid * per, i1 = min(n, i0 + per);
+  uint32_t sum = 0;
+  for (int j = i0; j < i1; j += 32) {
+    uint4 v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sum += run_counts(bv.tile_count, j + 4 * k, i1, v[k]);
+  }
+  s_sum[tid] = sum;
+  __syncthreads();
+  // inclusive scan of the run sums (Hillis-Steele in shared memory)
+  for (int o = 1; o < kBinThreads; o <<= 1) {
+    const uint32_t y = tid >= o ? s_sum[tid - o] : 0u;
+    __syncthreads();
+    s_sum[tid] += y;
+    __syncthreads();
+  }
+  uint32_t run = s_sum[tid] - sum;
+  for (int j = i0; j < i1; j += 32) {
+    uint4 v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) run_counts(bv.tile_count, j + 4 * k, i1, v[k]);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const uint32_t c[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int i = j + 4 * k + e;
+        if (i < i1) {
+          bv.tile_offset[i] = run;
+          bv.tile_cursor[i] = run;
+        }
+        run += c[e];
+      }
+    }
+  }
+  if (tid == kBinThreads - 1) {
+    bv.tile_offset[n] = s_sum[tid];
+    bv.hd->n_pairs = s_sum[tid];
   }
 }
 
@@ -238,44 +294,64 @@ struct PassSet {
   const int32_t *merge_at[kMaxPasses];
 };
 
-// Set-up (one triangle per thread) and per-tile candidate counts.
+// Set-up (one triangle per thread of the first warp, kept in shared memory
+// for the candidate walk) and per-tile candidate counts; the last block of each pass to finish
+// scans that pass's counts (its ticket is the spare count slot
+// tile_count[max_tiles], zeroed with the counts).
 __global__ void __launch_bounds__(kBinThreads) k_bin_count(const float *__restrict__ verts,
                                                            const uint32_t *__restrict__ rgba8,
                                                            int n_tris, PassSet ps, int32_t *status) {
-  __shared__ int s_off[kBinThreads + 1];
+  __shared__ int s_off[kBinTris + 1];
+  __shared__ TriSetup s_tri[kBinTris];
+  __shared__ bool s_last;
   const BinsView &bv = ps.bv[blockIdx.y];
   const int32_t *size = ps.size[blockIdx.y];
   const int32_t *merge_at = ps.merge_at[blockIdx.y];
   int W, H;
   const bool size_ok = pass_size(size, bv, W, H);
   const bool merged = size_ok && merge_at && W == merge_at[0] && H == merge_at[1];
+  const int tiles_x = merged ? 0 : (W + kTile - 1) / kTile;
+  const int n_tiles = tiles_x * (merged ? 0 : (H + kTile - 1) / kTile);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     BinsHeader *hd = bv.hd;
     hd->size[0] = W;
     hd->size[1] = H;
-    hd->tiles_x = merged ? 0 : (W + kTile - 1) / kTile;
+    hd->tiles_x = tiles_x;
     hd->tiles_y = merged ? 0 : (H + kTile - 1) / kTile;
-    hd->n_tiles = hd->tiles_x * hd->tiles_y;
+    hd->n_tiles = n_tiles;
     hd->n_pixels = W * H;
     hd->n_tris = n_tris;
     hd->merged = merged ? 1 : 0;
     if (!size_ok) raise_status(status, STAR_NT_ERR_ARG);
   }
-  if (merged) return;  // pass 1 takes this pass over: no triangles binned
-  const int t0 = blockIdx.x * kBinThreads;
-  if (t0 + (int)threadIdx.x < n_tris)
-    triangle_setup(t0 + threadIdx.x, verts, rgba8, ps.vp[blockIdx.y], W, H, size_ok,
-                   bv.setups + t0 + threadIdx.x);
+  if (!merged) {  // a merged pass is taken over by pass 1: no triangles binned
+    const int t0 = blockIdx.x * kBinTris;
+    if (threadIdx.x < kBinTris && t0 + (int)threadIdx.x < n_tris) {
+      triangle_setup(t0 + threadIdx.x, verts, rgba8, ps.vp[blockIdx.y], W, H, size_ok,
+                     s_tri + threadIdx.x);
+      bv.setups[t0 + threadIdx.x] = s_tri[threadIdx.x];
+    }
+    __syncthreads();
+    for_each_pair(s_tri, t0, n_tris, tiles_x, s_off,
+                  [&](int, int tile) { atomicAdd(bv.tile_count + tile, 1u); });
+  }
+  // last block of this pass: every count is final
+  __threadfence();
   __syncthreads();
-  const int tiles_x = (W + kTile - 1) / kTile;
-  for_each_pair(bv, t0, n_tris, tiles_x, s_off,
-                [&](int, int tile) { atomicAdd(bv.tile_count + tile, 1u); });
+  if (threadIdx.x == 0)
+    s_last = atomicAdd(bv.tile_count + bv.max_tiles, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  scan_tile_counts(bv, n_tiles);
 }
 
 // Pair lists; positions come from the per-tile cursors, which the tile scan
-// initialised to the tile offsets.
+// initialised to the tile offsets.  The block's set-ups are staged in shared
+// memory first.
 __global__ void __launch_bounds__(kBinThreads) k_bin_fill(PassSet ps, int n_tris, int32_t *status) {
-  __shared__ int s_off[kBinThreads + 1];
+  __shared__ int s_off[kBinTris + 1];
+  __shared__ TriSetup s_tri[kBinTris];
   const BinsView &bv = ps.bv[blockIdx.y];
   const BinsHeader *hd = bv.hd;
   if (hd->n_tiles == 0) return;  // empty or merged pass
@@ -283,7 +359,12 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_fill(PassSet ps, int n_tris
     if (blockIdx.x == 0 && threadIdx.x == 0) raise_status(status, STAR_NT_ERR_CAPACITY);
     return;
   }
-  for_each_pair(bv, blockIdx.x * kBinThreads, n_tris, hd->tiles_x, s_off, [&](int t, int tile) {
+  const int t0 = blockIdx.x * kBinTris;
+  const int nb = min(kBinTris, n_tris - t0);
+  for (int i = threadIdx.x; i < nb * 7; i += kBinThreads)
+    reinterpret_cast<uint4 *>(s_tri)[i] = __ldg(reinterpret_cast<const uint4 *>(bv.setups + t0) + i);
+  __syncthreads();
+  for_each_pair(s_tri, t0, n_tris, hd->tiles_x, s_off, [&](int t, int tile) {
     bv.pairs[atomicAdd(bv.tile_cursor + tile, 1u)] = (uint32_t)t;
   });
 }
@@ -380,32 +461,6 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_final(const uint32_t *__r
   for (int k = 0; k < kScanItems; ++k) {
     if (i0 + k < (size_t)n) out[i0 + k] = run;
     run += v[k];
-  }
-}
-
-// Tile scan in one launch: rounds of 1024 coalesced counts, each scanned
-// across the block and offset by the running total; writes the offsets, the
-// fill cursors (initialised to the offsets) and the total pair count.
-__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(PassSet ps) {
-  __shared__ uint32_t s_warp[32];
-  const BinsView &bv = ps.bv[blockIdx.x];
-  const int n = bv.hd->n_tiles;
-  uint32_t carry = 0;
-  for (int base = 0; base < n; base += kScanThreads) {
-    const int i = base + threadIdx.x;
-    const uint32_t v = i < n ? bv.tile_count[i] : 0u;
-    uint32_t tot;
-    const uint32_t ex = block_excl_scan(v, s_warp, &tot) + carry;
-    if (i < n) {
-      bv.tile_offset[i] = ex;
-      bv.tile_cursor[i] = ex;
-    }
-    carry += tot;
-    __syncthreads();  // s_warp is reused by the next round
-  }
-  if (threadIdx.x == 0) {
-    bv.tile_offset[n] = carry;
-    bv.hd->n_pairs = carry;
   }
 }
 
@@ -521,9 +576,8 @@ extern "C" star_nt_status star_nt_raster_passes(const star_nt_scene *scene, int3
   const int T = scene->n_tris;
   for (int i = 0; i < n_passes; ++i)
     cudaMemsetAsync(ps.bv[i].tile_count, 0, 4 * (size_t)(ps.bv[i].max_tiles + 1), st);
-  const dim3 grid(T > 0 ? (T + kBinThreads - 1) / kBinThreads : 1, n_passes);
+  const dim3 grid(T > 0 ? (T + kBinTris - 1) / kBinTris : 1, n_passes);
   k_bin_count<<<grid, kBinThreads, 0, st>>>(scene->verts, scene->rgba8, T, ps, d_status);
-  k_scan_tiles<<<n_passes, kScanThreads, 0, st>>>(ps);
   k_bin_fill<<<grid, kBinThreads, 0, st>>>(ps, T, d_status);
   return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
 }
