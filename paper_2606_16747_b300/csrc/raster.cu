@@ -45,24 +45,32 @@ constexpr LgTable make_lg_table() {
 __device__ const LgTable g_lg = make_lg_table();
 
 // ---------------------------------------------------------------------------
-// Triangle set-up: one thread per triangle.  Transform with float32 and one
-// rounding per operation (order fixed), drop triangles with a vertex behind
-// the camera, outside NDC z in [0, 1] or outside the guard band, snap to
-// 1/256 pixel, order the vertices for a positive area, then store the biased
-// edge functions, depth plane, pixel bounding box and colour sums.
-__device__ __forceinline__ void triangle_setup(int t, const float *__restrict__ verts,
-                                           const uint32_t *__restrict__ rgba8,
-                                           const float *__restrict__ vp, int W, int H, bool size_ok,
-                                           TriSetup *out) {
+// Triangle set-up by four lanes of a warp (q = lane % 4): lanes 0..2 each
+// transform one vertex, lane 3 fetches the colour; the snapped vertices are
+// exchanged by shuffles; lanes 0..2 each set up one edge and lane 3 the depth
+// plane, bounding box and colour sums.  The arithmetic is that of one thread
+// doing it all: float32 with one rounding per operation (order fixed), drop
+// triangles with a vertex behind the camera, outside NDC z in [0, 1] or
+// outside the guard band, snap to 1/256 pixel, order the vertices for a
+// positive area, then store the biased edge functions, depth plane, pixel
+// bounding box and colour sums.  All 32 lanes of the warp must call it;
+// `store` false (a triangle index past the end) skips the writes.
+__device__ __forceinline__ void triangle_setup_x4(int t, bool store, const float *__restrict__ verts,
+                                                  const uint32_t *__restrict__ rgba8,
+                                                  const float *__restrict__ vp, int W, int H,
+                                                  bool size_ok, TriSetup *out) {
+  const unsigned full = 0xffffffffu;
+  const int q = threadIdx.x & 3;
   float m[16];
 #pragma unroll
   for (int i = 0; i < 16; ++i) m[i] = __ldg(vp + i);
   const float4 *V = reinterpret_cast<const float4 *>(verts) + 3 * (size_t)t;
-  float sx[3], sy[3], zn[3];
-  bool ok = size_ok;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const float4 p = __ldg(V + k);
+  const uint32_t col = (store && q == 3) ? __ldg(rgba8 + t) : 0u;
+  // ---- lanes 0..2: vertex q
+  bool okq = true;
+  float sxq = 0.0f, syq = 0.0f, znq = 0.0f;
+  if (store && q < 3) {
+    const float4 p = __ldg(V + q);
     float c[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -72,47 +80,62 @@ __device__ __forceinline__ void triangle_setup(int t, const float *__restrict__ 
       acc = __fadd_rn(acc, __fmul_rn(m[4 * i + 3], p.w));
       c[i] = acc;
     }
-    if (!(c[3] > 0.0f)) ok = false;
+    if (!(c[3] > 0.0f)) okq = false;
     const float nx = __fdiv_rn(c[0], c[3]), ny = __fdiv_rn(c[1], c[3]), nz = __fdiv_rn(c[2], c[3]);
-    if (!(nz >= 0.0f && nz <= 1.0f)) ok = false;
-    sx[k] = __fmul_rn(__fadd_rn(__fmul_rn(nx, 0.5f), 0.5f), (float)W);
-    sy[k] = __fmul_rn(__fsub_rn(0.5f, __fmul_rn(ny, 0.5f)), (float)H);
-    if (!(fabsf(sx[k]) <= kGuard && fabsf(sy[k]) <= kGuard)) ok = false;
-    zn[k] = __fadd_rn(nz, 0.0f);
+    if (!(nz >= 0.0f && nz <= 1.0f)) okq = false;
+    sxq = __fmul_rn(__fadd_rn(__fmul_rn(nx, 0.5f), 0.5f), (float)W);
+    syq = __fmul_rn(__fsub_rn(0.5f, __fmul_rn(ny, 0.5f)), (float)H);
+    if (!(fabsf(sxq) <= kGuard && fabsf(syq) <= kGuard)) okq = false;
+    znq = __fadd_rn(nz, 0.0f);
   }
-  TriSetup S;
+  const long long Xq = okq ? __float2ll_rn(__fmul_rn(sxq, (float)kSub)) : 0ll;
+  const long long Yq = okq ? __float2ll_rn(__fmul_rn(syq, (float)kSub)) : 0ll;
+  // ---- exchange within the group of four lanes
+  bool ok = size_ok;
+  long long X[3], Y[3];
+  float zn[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    ok = ok && __shfl_sync(full, (int)okq, k, 4);
+    X[k] = __shfl_sync(full, Xq, k, 4);
+    Y[k] = __shfl_sync(full, Yq, k, 4);
+    zn[k] = __shfl_sync(full, znq, k, 4);
+  }
+  long long area = 0;
+  if (ok) {
+    area = (X[1] - X[0]) * (Y[2] - Y[0]) - (Y[1] - Y[0]) * (X[2] - X[0]);
+    if (area == 0) ok = false;
+  }
+  if (ok && area < 0) {  // no culling: swap v1 and v2 for a positive area
+    long long tx = X[1], ty = Y[1];
+    X[1] = X[2]; Y[1] = Y[2]; X[2] = tx; Y[2] = ty;
+    float tz = zn[1]; zn[1] = zn[2]; zn[2] = tz;
+    area = -area;
+  }
+  // ---- lanes 0..2: edge q
+  // edge from vertex q to vertex q + 1 (mod 3); selects keep X, Y in registers
+  const long long Xa = q == 1 ? X[1] : (q == 2 ? X[2] : X[0]);
+  const long long Ya = q == 1 ? Y[1] : (q == 2 ? Y[2] : Y[0]);
+  const long long Xb = q == 0 ? X[1] : (q == 1 ? X[2] : X[0]);
+  const long long Yb = q == 0 ? Y[1] : (q == 1 ? Y[2] : Y[0]);
+  const long long dx = Xb - Xa, dy = Yb - Ya;
+  const uint32_t o = (dy > 0 || (dy == 0 && dx < 0)) ? 1u : 0u;
+  const uint32_t own = __shfl_sync(full, o, 0, 4) | (__shfl_sync(full, o, 1, 4) << 1) |
+                       (__shfl_sync(full, o, 2, 4) << 2);
+  if (!store) return;
+  if (q < 3) {
+    out->dx[q] = ok ? (int32_t)dx : 0;
+    out->dy[q] = ok ? (int32_t)dy : 0;
+    out->c[q] = ok ? dy * Xa - dx * Ya + (long long)o - 1 : -1ll;
+    return;
+  }
+  // ---- lane 3: depth plane, bounding box, colour sums
+  TriSetup &S = *out;
   S.xa = 1;
   S.xb = 0;
   S.ya = 1;
   S.yb = 0;
-  long long X[3] = {0, 0, 0}, Y[3] = {0, 0, 0}, area = 0;
   if (ok) {
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      X[k] = __float2ll_rn(__fmul_rn(sx[k], (float)kSub));
-      Y[k] = __float2ll_rn(__fmul_rn(sy[k], (float)kSub));
-    }
-    area = (X[1] - X[0]) * (Y[2] - Y[0]) - (Y[1] - Y[0]) * (X[2] - X[0]);
-    if (area == 0) ok = false;
-  }
-  if (ok) {
-    if (area < 0) {  // no culling: swap v1 and v2 for a positive area
-      long long tx = X[1], ty = Y[1];
-      X[1] = X[2]; Y[1] = Y[2]; X[2] = tx; Y[2] = ty;
-      float tz = zn[1]; zn[1] = zn[2]; zn[2] = tz;
-      area = -area;
-    }
-    uint32_t own = 0;
-#pragma unroll
-    for (int e = 0; e < 3; ++e) {
-      const int a = e, b = (e + 1) % 3;
-      const long long dx = X[b] - X[a], dy = Y[b] - Y[a];
-      const uint32_t o = (dy > 0 || (dy == 0 && dx < 0)) ? 1u : 0u;
-      own |= o << e;
-      S.dx[e] = (int32_t)dx;
-      S.dy[e] = (int32_t)dy;
-      S.c[e] = dy * X[a] - dx * Y[a] + (long long)o - 1;
-    }
     S.own = own;
     S.z0 = zn[0];
     S.dz1 = __fsub_rn(zn[1], zn[0]);
@@ -132,12 +155,9 @@ __device__ __forceinline__ void triangle_setup(int t, const float *__restrict__ 
       S.xa = (int16_t)xa; S.xb = (int16_t)xb; S.ya = (int16_t)ya; S.yb = (int16_t)yb;
     }
   } else {
-#pragma unroll
-    for (int e = 0; e < 3; ++e) { S.dx[e] = 0; S.dy[e] = 0; S.c[e] = -1; }
     S.own = 0; S.z0 = S.dz1 = S.dz2 = S.r = 0.0f;
     S.zlo = INFINITY;
   }
-  const uint32_t col = __ldg(rgba8 + t);
   const unsigned long long a8 = col >> 24, r8 = col & 255u, g8 = (col >> 8) & 255u,
                            b8 = (col >> 16) & 255u;
   S.opq = a8 == 255 ? 1u : 0u;
@@ -145,7 +165,6 @@ __device__ __forceinline__ void triangle_setup(int t, const float *__restrict__ 
   S.ba = (a8 * b8) | (a8 << 32);
   S.pad = 0;
   S.lg = g_lg.v[a8];
-  *out = S;
 }
 
 // Render-target size of a pass, validated against the workspace: a size
@@ -196,7 +215,8 @@ constexpr int kBinTris = 32;  // triangles per binning block: four threads per t
 template <class Emit>
 __device__ __forceinline__ void for_each_pair(const TriSetup *tri, int t0, int n_tris, int tiles_x,
                                               int *s_off, Emit &&emit) {
-  static_assert(kBinTris == 32, "one warp scans the candidate counts");
+  static_assert(kBinTris == 32 && kBinThreads == 4 * kBinTris,
+                "one warp scans the candidate counts; four set-up lanes per triangle");
   const int tid = threadIdx.x;
   if (tid < 32) {
     int tx0 = 0, ty0 = 0, ntx = 1;
@@ -227,64 +247,6 @@ __device__ __forceinline__ void for_each_pair(const TriSetup *tri, int t0, int n
   }
 }
 
-// Exclusive scan of the tile counts of one pass by one block of kBinThreads
-// threads; thread i owns the run [i * per, (i + 1) * per) with per a multiple
-// of 4, read as batches of eight 16-byte loads in flight.  Writes the offsets,
-// the fill cursors (initialised to the offsets) and the total pair count.
-// The counts are read from L2, where the atomics landed.
-__device__ __forceinline__ uint32_t run_counts(const uint32_t *cnt, int j, int end, uint4 &v) {
-  v = j < end ? __ldcg(reinterpret_cast<const uint4 *>(cnt + j)) : make_uint4(0u, 0u, 0u, 0u);
-  if (j + 1 >= end) v.y = 0u;
-  if (j + 2 >= end) v.z = 0u;
-  if (j + 3 >= end) v.w = 0u;
-  return v.x + v.y + v.z + v.w;
-}
-
-__device__ void scan_tile_counts(const BinsView &bv, int n) {
-  __shared__ uint32_t s_sum[kBinThreads];
-  const int tid = threadIdx.x;
-  const int per = (((n + kBinThreads - 1) / kBinThreads) + 3) & ~3;
-  const int i0 = tid * per, i1 = min(n, i0 + per);
-  uint32_t sum = 0;
-  for (int j = i0; j < i1; j += 32) {
-    uint4 v[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) sum += run_counts(bv.tile_count, j + 4 * k, i1, v[k]);
-  }
-  s_sum[tid] = sum;
-  __syncthreads();
-  // inclusive scan of the run sums (Hillis-Steele in shared memory)
-  for (int o = 1; o < kBinThreads; o <<= 1) {
-    const uint32_t y = tid >= o ? s_sum[tid - o] : 0u;
-    __syncthreads();
-    s_sum[tid] += y;
-    __syncthreads();
-  }
-  uint32_t run = s_sum[tid] - sum;
-  for (int j = i0; j < i1; j += 32) {
-    uint4 v[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) run_counts(bv.tile_count, j + 4 * k, i1, v[k]);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const uint32_t c[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int i = j + 4 * k + e;
-        if (i < i1) {
-          bv.tile_offset[i] = run;
-          bv.tile_cursor[i] = run;
-        }
-        run += c[e];
-      }
-    }
-  }
-  if (tid == kBinThreads - 1) {
-    bv.tile_offset[n] = s_sum[tid];
-    bv.hd->n_pairs = s_sum[tid];
-  }
-}
-
 // Up to three passes are binned by the same launches (blockIdx.y = pass).
 constexpr int kMaxPasses = 3;
 struct PassSet {
@@ -294,16 +256,14 @@ struct PassSet {
   const int32_t *merge_at[kMaxPasses];
 };
 
-// Set-up (one triangle per thread of the first warp, kept in shared memory
-// for the candidate walk) and per-tile candidate counts; the last block of each pass to finish
-// scans that pass's counts (its ticket is the spare count slot
-// tile_count[max_tiles], zeroed with the counts).
+// Set-up (four threads per triangle, kept in shared memory for the
+// candidate walk and copied out for the pass kernels) and per-tile candidate
+// counts.
 __global__ void __launch_bounds__(kBinThreads) k_bin_count(const float *__restrict__ verts,
                                                            const uint32_t *__restrict__ rgba8,
                                                            int n_tris, PassSet ps, int32_t *status) {
   __shared__ int s_off[kBinTris + 1];
   __shared__ TriSetup s_tri[kBinTris];
-  __shared__ bool s_last;
   const BinsView &bv = ps.bv[blockIdx.y];
   const int32_t *size = ps.size[blockIdx.y];
   const int32_t *merge_at = ps.merge_at[blockIdx.y];
@@ -326,24 +286,16 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(const float *__restri
   }
   if (!merged) {  // a merged pass is taken over by pass 1: no triangles binned
     const int t0 = blockIdx.x * kBinTris;
-    if (threadIdx.x < kBinTris && t0 + (int)threadIdx.x < n_tris) {
-      triangle_setup(t0 + threadIdx.x, verts, rgba8, ps.vp[blockIdx.y], W, H, size_ok,
-                     s_tri + threadIdx.x);
-      bv.setups[t0 + threadIdx.x] = s_tri[threadIdx.x];
-    }
+    const int j = threadIdx.x >> 2;  // four lanes per triangle
+    triangle_setup_x4(t0 + j, t0 + j < n_tris, verts, rgba8, ps.vp[blockIdx.y], W, H, size_ok,
+                      s_tri + j);
     __syncthreads();
+    const int nb = min(kBinTris, n_tris - t0);
+    for (int i = threadIdx.x; i < nb * 7; i += kBinThreads)
+      reinterpret_cast<uint4 *>(bv.setups + t0)[i] = reinterpret_cast<const uint4 *>(s_tri)[i];
     for_each_pair(s_tri, t0, n_tris, tiles_x, s_off,
                   [&](int, int tile) { atomicAdd(bv.tile_count + tile, 1u); });
   }
-  // last block of this pass: every count is final
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0)
-    s_last = atomicAdd(bv.tile_count + bv.max_tiles, 1u) == gridDim.x - 1;
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  scan_tile_counts(bv, n_tiles);
 }
 
 // Pair lists; positions come from the per-tile cursors, which the tile scan
@@ -367,6 +319,58 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_fill(PassSet ps, int n_tris
   for_each_pair(s_tri, t0, n_tris, hd->tiles_x, s_off, [&](int t, int tile) {
     bv.pairs[atomicAdd(bv.tile_cursor + tile, 1u)] = (uint32_t)t;
   });
+}
+
+// Exclusive scan of the tile counts, one block of 1024 threads per pass in one
+// round: thread i owns the run [i * per, (i + 1) * per) (per a multiple of
+// 4, read as 16-byte loads).  Writes the offsets, the fill cursors
+// (initialised to the offsets) and the total pair count.
+__device__ __forceinline__ uint32_t run4(const uint32_t *cnt, int j, int end, uint4 &v) {
+  v = j < end ? *reinterpret_cast<const uint4 *>(cnt + j) : make_uint4(0u, 0u, 0u, 0u);
+  if (j + 1 >= end) v.y = 0u;
+  if (j + 2 >= end) v.z = 0u;
+  if (j + 3 >= end) v.w = 0u;
+  return v.x + v.y + v.z + v.w;
+}
+
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *s_warp, uint32_t *total);
+
+__global__ void __launch_bounds__(1024) k_scan_tiles(PassSet ps) {
+  __shared__ uint32_t s_warp[32];
+  const BinsView &bv = ps.bv[blockIdx.x];
+  const int n = bv.hd->n_tiles;
+  const int per = (((n + 1023) / 1024) + 3) & ~3;
+  const int i0 = threadIdx.x * per, i1 = min(n, i0 + per);
+  uint32_t sum = 0;
+  for (int j = i0; j < i1; j += 32) {
+    uint4 v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sum += run4(bv.tile_count, j + 4 * k, i1, v[k]);
+  }
+  uint32_t tot;
+  uint32_t run = block_excl_scan(sum, s_warp, &tot);
+  for (int j = i0; j < i1; j += 32) {
+    uint4 v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) run4(bv.tile_count, j + 4 * k, i1, v[k]);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const uint32_t c[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int i = j + 4 * k + e;
+        if (i < i1) {
+          bv.tile_offset[i] = run;
+          bv.tile_cursor[i] = run;
+        }
+        run += c[e];
+      }
+    }
+  }
+  if (threadIdx.x == 0) {
+    bv.tile_offset[n] = tot;
+    bv.hd->n_pairs = tot;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -578,6 +582,7 @@ extern "C" star_nt_status star_nt_raster_passes(const star_nt_scene *scene, int3
     cudaMemsetAsync(ps.bv[i].tile_count, 0, 4 * (size_t)(ps.bv[i].max_tiles + 1), st);
   const dim3 grid(T > 0 ? (T + kBinTris - 1) / kBinTris : 1, n_passes);
   k_bin_count<<<grid, kBinThreads, 0, st>>>(scene->verts, scene->rgba8, T, ps, d_status);
+  k_scan_tiles<<<n_passes, 1024, 0, st>>>(ps);
   k_bin_fill<<<grid, kBinThreads, 0, st>>>(ps, T, d_status);
   return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
 }
