@@ -132,7 +132,8 @@ def run_ours(args, rank, world):
     w, wname = mlp_weights()
     x_dtype = sn.BF16 if args.mlp == "bf16" else sn.F32
     star = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=x_dtype, base_tile=args.base_tile,
-                    fused=args.fused and x_dtype == sn.BF16, persistent=args.persistent)
+                    fused=args.fused and x_dtype == sn.BF16, persistent=args.persistent,
+                    merge_scale2=args.merge_scale2)
     plain = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=sn.F32)
     n_frames = 2 * (4 + args.warmup + 2 * args.steps + 12)
     cams = scenes.orbit_cameras(W, H, n_frames)
@@ -277,6 +278,7 @@ def run_ours(args, rank, world):
         "config": {"workload": desc, "frames_per_step": 2, "mlp": args.mlp, "weights": wname,
                    "resolve": "fused" if star.fused else "separate",
                    "passes": "persistent" if star.persistent else "separate",
+                   "pass2_merge_scale": star.merge_scale2,
                    "pass_tuning": tuned,
                    "base_tile": args.base_tile, "l2": "flushed between steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
@@ -325,7 +327,8 @@ def end_to_end(sn, torch, sc, w, x_dtype, W, H, cams, args, tuning=None):
     are read back."""
     from paper_2606_16747_b300.pipeline import Renderer
     r = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=x_dtype, base_tile=args.base_tile,
-                 fused=args.fused and x_dtype == sn.BF16, persistent=args.persistent, tuning=tuning)
+                 fused=args.fused and x_dtype == sn.BF16, persistent=args.persistent, tuning=tuning,
+                 merge_scale2=args.merge_scale2)
     hv = torch.from_numpy(np.ascontiguousarray(sc.verts)).pin_memory()
     hc = torch.from_numpy(np.ascontiguousarray(sc.rgba8).view(np.int32)).pin_memory()
     hvp = [torch.from_numpy(np.ascontiguousarray(c.vp32)).pin_memory() for c in cams]
@@ -474,6 +477,9 @@ def main():
     ap.add_argument("--separate-passes", dest="persistent", action="store_false",
                     help="three geometry-pass launches instead of one persistent launch")
     ap.add_argument("--no-tune", action="store_true", help="skip the pass-launch autotuner")
+    ap.add_argument("--merge-scale2", type=float, default=1.0,
+                    help="pass 2 at least this fraction of the full size runs inside pass 1 at full "
+                         "size (1.0: only at full size, as Eq. 2 sizes it)")
     ap.add_argument("--unfused", dest="fused", action="store_false",
                     help="separate upscale/features, MLP and composite kernels")
     ap.add_argument("--no-cpu-baseline", action="store_true")

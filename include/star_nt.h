@@ -73,14 +73,22 @@ typedef struct {
  *   projection maps the visible depth range to NDC z in [0, 1].
  * size: device, {W_p, H_p}, the pass's resolution (read on the device).
  * max_w, max_h: host upper bounds of size[]; they size the launches.
- * merge_at: optional device {W, H} (NULL: never): when size equals it, the
- *   pass is left to pass 1 (star_nt_geometry_pass_merged), and the bins are
- *   marked merged and hold no triangles. */
+ * merge_at: optional device {W, H} of pass 1 (NULL: never merged).  The
+ *   pass is merged when W_p >= merge_scale * W and H_p >= merge_scale * H
+ *   (merge_scale <= 0 is read as 1: only a pass at the full size merges):
+ *   it is then left to pass 1 (star_nt_geometry_pass_merged /
+ *   star_nt_geometry_passes), which produces its planes at the full size W x H,
+ *   and the bins are marked merged, record the full size and hold no
+ *   triangles.  A merge below full size is a cost choice: pass 1 keeping two
+ *   layers costs less than a second traversal at nearly full size, and the
+ *   planes are then exact rather than upscaled.
+ * merge_scale: see merge_at. */
 typedef struct {
     const float *view_proj;
     const int32_t *size;
     int32_t max_w, max_h;
     const int32_t *merge_at;
+    float merge_scale;
 } star_nt_target;
 
 /* Parameters of the method.  Defaults (star_nt_default_params):
@@ -208,9 +216,10 @@ star_nt_status star_nt_geometry_pass(const star_nt_scene *scene, const star_nt_b
                                      int32_t *d_status, void *stream);
 /* star_nt_geometry_pass_merged: pass 1 (nearest fragment, full resolution)
  * that also performs pass 2 and/or pass 3 at full resolution when their bins
- * are marked merged (their device-side size equals the full size): it then
- * writes id2 into layers2 and n, tail, t_tail into layers3 at full
- * resolution, so star_nt_upscale_features reads them as usual. */
+ * are marked merged (see star_nt_target.merge_at): it then writes id2 into
+ * layers2 and n, tail, t_tail into layers3 at full resolution, and the
+ * merged bins record the full size, so star_nt_upscale_features and
+ * star_nt_resolve read them as usual (an identity upscale). */
 star_nt_status star_nt_geometry_pass_merged(const star_nt_scene *scene, const star_nt_bins *bins1,
                                             const star_nt_bins *bins2, const star_nt_bins *bins3,
                                             const star_nt_layers *layers1,

@@ -134,9 +134,13 @@ __global__ void __launch_bounds__(256, 6) k_pass_merged(BinsView bv, const BinsH
   }
   PassOut o = o1;
   o.id2 = m2 ? o2.id2 : nullptr;
-  o.n = m3 ? o3.n : nullptr;
-  o.tail = m3 ? o3.tail : nullptr;
-  o.t_tail = m3 ? o3.t_tail : nullptr;
+  if (!m3) {  // two layers, no tail sums: the top-2 traversal with its depth skip
+    pass_body<kTop2>(bv, rgba8, o, FeatOut{}, stage, blockIdx.x);
+    return;
+  }
+  o.n = o3.n;
+  o.tail = o3.tail;
+  o.t_tail = o3.t_tail;
   pass_body<kTail>(bv, rgba8, o, FeatOut{}, stage, blockIdx.x);
 }
 
@@ -171,7 +175,8 @@ __global__ void __launch_bounds__(256, 6) k_passes(BinsView v1, BinsView v2, Bin
     __syncthreads();  // every thread has the item before s_item is reused
     if (item >= total) break;
     if (item < n1) {
-      if (m2 || m3) pass_body<kTail, BW>(v1, rgba8, om, FeatOut{}, stage, item);
+      if (m3) pass_body<kTail, BW>(v1, rgba8, om, FeatOut{}, stage, item);
+      else if (m2) pass_body<kTop2, BW>(v1, rgba8, om, FeatOut{}, stage, item);
       else pass_body<kTop1, BW>(v1, rgba8, o1, FeatOut{}, stage, item);
     } else if (item < n1 + n2) {
       pass_body<kTop2, BW>(v2, rgba8, o2, FeatOut{}, stage, item - n1);

@@ -254,6 +254,7 @@ struct PassSet {
   const float *vp[kMaxPasses];
   const int32_t *size[kMaxPasses];
   const int32_t *merge_at[kMaxPasses];
+  float merge_scale[kMaxPasses];
 };
 
 // Set-up (four threads per triangle, kept in shared memory for the
@@ -269,11 +270,19 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(const float *__restri
   const int32_t *merge_at = ps.merge_at[blockIdx.y];
   int W, H;
   const bool size_ok = pass_size(size, bv, W, H);
-  const bool merged = size_ok && merge_at && W == merge_at[0] && H == merge_at[1];
+  // merged: taken over by pass 1 at the full size merge_at (whose planes it
+  // then writes), when the pass is at least merge_scale of it on both axes
+  const float ms = ps.merge_scale[blockIdx.y];
+  const bool merged = size_ok && merge_at && merge_at[0] <= bv.max_w && merge_at[1] <= bv.max_h &&
+                      (float)W >= ms * (float)merge_at[0] && (float)H >= ms * (float)merge_at[1];
   const int tiles_x = merged ? 0 : (W + kTile - 1) / kTile;
   const int n_tiles = tiles_x * (merged ? 0 : (H + kTile - 1) / kTile);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     BinsHeader *hd = bv.hd;
+    if (merged) {
+      W = merge_at[0];
+      H = merge_at[1];
+    }
     hd->size[0] = W;
     hd->size[1] = H;
     hd->tiles_x = tiles_x;
@@ -321,17 +330,13 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_fill(PassSet ps, int n_tris
   });
 }
 
-// Exclusive scan of the tile counts, one block of 1024 threads per pass in one
-// round: thread i owns the run [i * per, (i + 1) * per) (per a multiple of
-// 4, read as 16-byte loads).  Writes the offsets, the fill cursors
-// (initialised to the offsets) and the total pair count.
-__device__ __forceinline__ uint32_t run4(const uint32_t *cnt, int j, int end, uint4 &v) {
-  v = j < end ? *reinterpret_cast<const uint4 *>(cnt + j) : make_uint4(0u, 0u, 0u, 0u);
-  if (j + 1 >= end) v.y = 0u;
-  if (j + 2 >= end) v.z = 0u;
-  if (j + 3 >= end) v.w = 0u;
-  return v.x + v.y + v.z + v.w;
-}
+// Exclusive scan of the tile counts, one block of 1024 threads per pass, in
+// rounds of 4096 counts: thread t holds counts [4 (r 1024 + t), +4) of round
+// r, so that every load and store of a warp is one coalesced 512-byte run.
+// The loads of up to four rounds are in flight together.  Writes the
+// offsets, the fill cursors (initialised to the offsets) and the total pair
+// count.
+constexpr int kScanRounds = 4;
 
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *s_warp, uint32_t *total);
 
@@ -339,37 +344,43 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(PassSet ps) {
   __shared__ uint32_t s_warp[32];
   const BinsView &bv = ps.bv[blockIdx.x];
   const int n = bv.hd->n_tiles;
-  const int per = (((n + 1023) / 1024) + 3) & ~3;
-  const int i0 = threadIdx.x * per, i1 = min(n, i0 + per);
-  uint32_t sum = 0;
-  for (int j = i0; j < i1; j += 32) {
-    uint4 v[8];
+  const int tid = threadIdx.x;
+  uint32_t carry = 0;
+  for (int base = 0; base < n; base += kScanRounds * 4096) {
+    uint4 v[kScanRounds];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) sum += run4(bv.tile_count, j + 4 * k, i1, v[k]);
-  }
-  uint32_t tot;
-  uint32_t run = block_excl_scan(sum, s_warp, &tot);
-  for (int j = i0; j < i1; j += 32) {
-    uint4 v[8];
+    for (int r = 0; r < kScanRounds; ++r) {
+      const int i = base + 4 * (r * 1024 + tid);
+      v[r] = i < n ? *reinterpret_cast<const uint4 *>(bv.tile_count + i) : make_uint4(0u, 0u, 0u, 0u);
+      if (i + 1 >= n) v[r].y = 0u;
+      if (i + 2 >= n) v[r].z = 0u;
+      if (i + 3 >= n) v[r].w = 0u;
+    }
 #pragma unroll
-    for (int k = 0; k < 8; ++k) run4(bv.tile_count, j + 4 * k, i1, v[k]);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const uint32_t c[4] = {v[k].x, v[k].y, v[k].z, v[k].w};
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int i = j + 4 * k + e;
-        if (i < i1) {
-          bv.tile_offset[i] = run;
-          bv.tile_cursor[i] = run;
+    for (int r = 0; r < kScanRounds; ++r) {
+      const int i = base + 4 * (r * 1024 + tid);
+      if (base + r * 4096 >= n) break;  // uniform over the block
+      const uint32_t sum = v[r].x + v[r].y + v[r].z + v[r].w;
+      uint32_t tot;
+      const uint32_t ex = block_excl_scan(sum, s_warp, &tot) + carry;
+      const uint4 o = make_uint4(ex, ex + v[r].x, ex + v[r].x + v[r].y, ex + v[r].x + v[r].y + v[r].z);
+      if (i + 3 < n) {
+        *reinterpret_cast<uint4 *>(bv.tile_offset + i) = o;
+        *reinterpret_cast<uint4 *>(bv.tile_cursor + i) = o;
+      } else if (i < n) {
+        const uint32_t oo[4] = {o.x, o.y, o.z, o.w};
+        for (int e = 0; e < n - i; ++e) {
+          bv.tile_offset[i + e] = oo[e];
+          bv.tile_cursor[i + e] = oo[e];
         }
-        run += c[e];
       }
+      carry += tot;
+      __syncthreads();  // s_warp is reused by the next round
     }
   }
-  if (threadIdx.x == 0) {
-    bv.tile_offset[n] = tot;
-    bv.hd->n_pairs = tot;
+  if (tid == 0) {
+    bv.tile_offset[n] = carry;
+    bv.hd->n_pairs = carry;
   }
 }
 
@@ -575,6 +586,9 @@ extern "C" star_nt_status star_nt_raster_passes(const star_nt_scene *scene, int3
     ps.vp[i] = targets[i].view_proj;
     ps.size[i] = targets[i].size;
     ps.merge_at[i] = targets[i].merge_at;
+    const float ms = targets[i].merge_scale;
+    if (!(ms <= 1.0f)) return STAR_NT_ERR_ARG;  // NaN or above 1
+    ps.merge_scale[i] = ms > 0.0f ? ms : 1.0f;
   }
   cudaStream_t st = (cudaStream_t)stream;
   const int T = scene->n_tris;

@@ -29,7 +29,7 @@ def _i32(vals, device):
 class Renderer:
     def __init__(self, verts, rgba8, W, H, params=None, x_dtype=sn.F32, mlp=None,
                  pair_capacity=None, device="cuda", base_tile=None, fused=False,
-                 persistent=False, tuning=None):
+                 persistent=False, tuning=None, merge_scale2=1.0, merge_scale3=1.0):
         self.device = device
         self.W, self.H = int(W), int(H)
         self.P = self.W * self.H
@@ -46,6 +46,10 @@ class Renderer:
         # persistent: the three geometry passes in one launch (tuning: (block_w, ctas_per_sm))
         self.persistent = bool(persistent)
         self.tuning = tuning
+        # a reduced pass at least this fraction of the full size (both axes)
+        # is produced by pass 1 at the full size instead (1.0: only at full size)
+        self.merge_scale2 = float(merge_scale2)
+        self.merge_scale3 = float(merge_scale3)
         if self.fused and x_dtype != sn.BF16:
             raise ValueError("the fused resolve runs the BF16 tensor-core MLP")
         cap = pair_capacity if pair_capacity is not None else max(1 << 20, 96 * self.T)
@@ -129,8 +133,9 @@ class Renderer:
             # full size are taken over by pass 1 (merged)
             sn.raster_passes(self.scene, [
                 (self.vp, self.full_size, self.W, self.H, b1, None),
-                (self.vp, self.state_size(2), self.W, self.H, b2, self.full_size),
-                (self.vp, self.state_size(3), self.W, self.H, b3, self.full_size)], self.status, stream)
+                (self.vp, self.state_size(2), self.W, self.H, b2, self.full_size, self.merge_scale2),
+                (self.vp, self.state_size(3), self.W, self.H, b3, self.full_size, self.merge_scale3)],
+                self.status, stream)
 
         st = [("raster", raster)]
         if self.persistent:

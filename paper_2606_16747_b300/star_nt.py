@@ -38,7 +38,8 @@ class Scene(ctypes.Structure):
 
 
 class Target(ctypes.Structure):
-    _fields_ = [("view_proj", _P), ("size", _P), ("max_w", _I32), ("max_h", _I32), ("merge_at", _P)]
+    _fields_ = [("view_proj", _P), ("size", _P), ("max_w", _I32), ("max_h", _I32), ("merge_at", _P),
+                ("merge_scale", ctypes.c_float)]
 
 
 class Params(ctypes.Structure):
@@ -195,9 +196,9 @@ def scene_struct(verts, rgba8) -> Scene:
 
 
 def raster(scene: Scene, vp, size, max_w, max_h, bins: BinsBuffer, frags=None, status=None, stream=None,
-           merge_at=None):
+           merge_at=None, merge_scale=1.0):
     tgt = Target(vp.data_ptr(), size.data_ptr(), max_w, max_h,
-                 merge_at.data_ptr() if merge_at is not None else None)
+                 merge_at.data_ptr() if merge_at is not None else None, float(merge_scale))
     fr = None
     if frags is not None:
         fr = Frags(frags["count"].data_ptr(), frags["offset"].data_ptr(), frags["z"].data_ptr(),
@@ -209,12 +210,13 @@ def raster(scene: Scene, vp, size, max_w, max_h, bins: BinsBuffer, frags=None, s
 
 
 def raster_passes(scene: Scene, passes, status=None, stream=None):
-    """passes: list of (vp, size, max_w, max_h, bins, merge_at or None)."""
+    """passes: list of (vp, size, max_w, max_h, bins, merge_at or None[, merge_scale])."""
     n = len(passes)
-    tgts = (Target * n)(*[Target(vp.data_ptr(), size.data_ptr(), mw, mh,
-                                 ma.data_ptr() if ma is not None else None)
-                          for vp, size, mw, mh, _, ma in passes])
-    bins = (Bins * n)(*[b.c for _, _, _, _, b, _ in passes])
+    tgts = (Target * n)(*[Target(p[0].data_ptr(), p[1].data_ptr(), p[2], p[3],
+                                 p[5].data_ptr() if p[5] is not None else None,
+                                 float(p[6]) if len(p) > 6 else 1.0)
+                          for p in passes])
+    bins = (Bins * n)(*[p[4].c for p in passes])
     _check("star_nt_raster_passes", lib().star_nt_raster_passes(ctypes.byref(scene), n, tgts, bins,
                                                                 _ptr(status), _stream(stream)))
 

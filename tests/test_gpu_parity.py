@@ -555,3 +555,35 @@ def test_persistent_passes_equal_separate(sn, tuning, sizes):
                     r.l3["t_tail"][:s3[0] * s3[1]].clone(), r.rgba32f.clone()])
     for a, b in zip(*res):
         assert torch.equal(a, b)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("persistent", [False, True])
+def test_pass2_merge_scale(sn, persistent):
+    """A pass 2 at least merge_scale of the full size is produced by pass 1 at
+    the full size: the frame equals the one rendered with pass 2 requested at
+    the full size, bit for bit, and the bins record the full size; below the
+    scale nothing changes."""
+    from paper_2606_16747_b300.pipeline import Renderer
+    sc = scenes.screen_scene(41, 2500, 208, 144, size_scale=0.7)
+    W, H = sc.width, sc.height
+
+    def frame(s2, scale):
+        r = Renderer(sc.verts, sc.rgba8, W, H, mlp=scenes.mlp_xavier(4), x_dtype=sn.BF16, fused=True,
+                     persistent=persistent, merge_scale2=scale)
+        r.set_camera(sc.cam.vp32)
+        r.state.view(torch.int32)[:6] = torch.tensor([W, H, *s2, 57, 40], dtype=torch.int32)
+        r.star_frame(update_tiles=False)
+        torch.cuda.synchronize()
+        r.check_status()
+        hd = r.bins[1].header().cpu().numpy()
+        return r.rgba32f.clone(), r.l2["id2"].clone(), (int(hd[0]), int(hd[1]))
+
+    promoted = frame((131, 91), 0.6)       # 0.63 x 0.63 of full size: merged
+    full = frame((W, H), 1.0)
+    assert promoted[2] == (W, H)
+    assert torch.equal(promoted[0], full[0]) and torch.equal(promoted[1], full[1])
+    kept = frame((111, 77), 0.6)           # 0.53 of full size: a pass of its own
+    plain = frame((111, 77), 1.0)
+    assert kept[2] == (111, 77)
+    assert torch.equal(kept[0], plain[0])
