@@ -135,7 +135,7 @@ def run_ours(args, rank, world):
                     fused=args.fused and x_dtype == sn.BF16, persistent=args.persistent,
                     merge_scale2=args.merge_scale2)
     plain = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=sn.F32)
-    n_frames = 2 * (4 + args.warmup + 2 * args.steps + 12)
+    n_frames = 2 * (20 + 2 * args.warmup + 2 * args.steps)
     cams = scenes.orbit_cameras(W, H, n_frames)
     vp32 = torch.tensor(np.stack([c.vp32 for c in cams]), device=dev)
     vp64 = torch.tensor(np.stack([c.vp64.reshape(16) for c in cams]), device=dev)
@@ -216,6 +216,24 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         stage_ms[name] = [e0.elapsed_time(e1) / STAGE_REPS]
 
+    # the same step with pass 2 at the size Eq. 2 gives (no merge below full size)
+    eq2_ms = None
+    if star.merge_scale2 < 1.0:
+        star.merge_scale2 = 1.0
+        g_eq2 = star.capture(star.step)
+        for _ in range(args.warmup):
+            set_cams(step)
+            g_eq2.replay()
+            step += 1
+        ev = []
+        for _ in range(args.steps):
+            ev.append(timed(g_eq2.replay, step))
+            step += 1
+        torch.cuda.synchronize()
+        eq2_ms = float(np.mean([a.elapsed_time(b) for a, b in ev])) / 2.0
+        star.merge_scale2 = args.merge_scale2
+        star.check_status()
+
     # plain full-resolution FP32 pipeline on the same scene and cameras
     plain.set_cameras(vp32[0])
     g_plain = plain.capture(plain.plain_frame)
@@ -285,6 +303,8 @@ def run_ours(args, rank, world):
         "fragments_per_s": round(Fcount / (ms_frame * 1e-3), 1),
         "fragments_full_res": int(Fcount),
         "fragments_note": "mean full-resolution fragment count of the timed real frames",
+        "eq2_sizes_ms_per_frame": round(eq2_ms, 5) if eq2_ms is not None else None,
+        "eq2_sizes_note": "the same step with pass 2 always at the Eq. 2 size (merge scale 1.0)",
         "plain_ms_per_frame": round(float(np.mean(plain_ms)), 5),
         "speedup_vs_plain": round(float(np.mean(plain_ms)) / ms_frame, 4),
         "stages_ms": {k: round(v, 5) for k, v in stage_mean.items()},
@@ -477,7 +497,7 @@ def main():
     ap.add_argument("--separate-passes", dest="persistent", action="store_false",
                     help="three geometry-pass launches instead of one persistent launch")
     ap.add_argument("--no-tune", action="store_true", help="skip the pass-launch autotuner")
-    ap.add_argument("--merge-scale2", type=float, default=1.0,
+    ap.add_argument("--merge-scale2", type=float, default=0.5,
                     help="pass 2 at least this fraction of the full size runs inside pass 1 at full "
                          "size (1.0: only at full size, as Eq. 2 sizes it)")
     ap.add_argument("--unfused", dest="fused", action="store_false",

@@ -23,7 +23,7 @@ struct __align__(16) TriSetup {
   long long c[3];
   float z0, dz1, dz2, r;      // depth plane: z = (z0 + b1 dz1) + b2 dz2, r = 1/area
   int16_t xa, xb, ya, yb;     // covered-pixel bounding box (clamped), empty if xa > xb
-  uint32_t own;               // bit e set: edge e owns ties
+  uint32_t own;               // bit e set: edge e owns ties; kOwnSmall: area < 2^31
   uint32_t opq;               // 1 when a8 == 255
   unsigned long long rg;      // a8*r8 | (a8*g8) << 32
   unsigned long long ba;      // a8*b8 | a8 << 32
@@ -32,6 +32,10 @@ struct __align__(16) TriSetup {
   uint32_t pad;
 };
 static_assert(sizeof(TriSetup) == 112, "TriSetup layout");
+
+// TriSetup::own flag: the doubled area (and so every edge value of a covered
+// pixel) fits int32, so fragment depths may convert edge values as int32.
+constexpr uint32_t kOwnSmall = 8u;
 
 // Header at the start of a bins workspace.
 struct __align__(16) BinsHeader {

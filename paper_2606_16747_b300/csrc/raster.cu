@@ -136,7 +136,7 @@ __device__ __forceinline__ void triangle_setup_x4(int t, bool store, const float
   S.ya = 1;
   S.yb = 0;
   if (ok) {
-    S.own = own;
+    S.own = own | (area <= 0x7fffffffLL ? kOwnSmall : 0u);
     S.z0 = zn[0];
     S.dz1 = __fsub_rn(zn[1], zn[0]);
     S.dz2 = __fsub_rn(zn[2], zn[0]);

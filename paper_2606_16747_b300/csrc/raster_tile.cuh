@@ -36,11 +36,22 @@ __device__ __forceinline__ TilePixel tile_pixel(int tile, int tiles_x) {
 
 // Canonical float32 depth of a covered pixel: b1 = E_20 / A, b2 = E_01 / A,
 // z = (z0 + b1 dz1) + b2 dz2, one rounding per operation, -0 folded to +0.
+// The edge values of a covered pixel lie in [0, A]; when A fits int32 they
+// are converted as int32 (the same correctly rounded float; the int64
+// conversion runs on the float64 pipe, which is narrow on this part).
 __device__ __forceinline__ float frag_depth(const TriSetup &T, long long e0b, long long e2b) {
   const long long e01 = e0b - (long long)(T.own & 1u) + 1;
   const long long e20 = e2b - (long long)((T.own >> 2) & 1u) + 1;
-  const float b1 = __fmul_rn(__ll2float_rn(e20), T.r);
-  const float b2 = __fmul_rn(__ll2float_rn(e01), T.r);
+  float f20, f01;
+  if (T.own & kOwnSmall) {
+    f20 = __int2float_rn((int)e20);
+    f01 = __int2float_rn((int)e01);
+  } else {
+    f20 = __ll2float_rn(e20);
+    f01 = __ll2float_rn(e01);
+  }
+  const float b1 = __fmul_rn(f20, T.r);
+  const float b2 = __fmul_rn(f01, T.r);
   float z = __fadd_rn(__fadd_rn(T.z0, __fmul_rn(b1, T.dz1)), __fmul_rn(b2, T.dz2));
   return __fadd_rn(z, 0.0f);
 }
