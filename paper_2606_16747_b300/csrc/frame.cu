@@ -116,47 +116,70 @@ __global__ void __launch_bounds__(256) k_composite(const float4 *__restrict__ fr
 // is dx = (W/2) (E0 v - ndc_x E3 v) / (1 + E3 v) (and likewise in y).  Every
 // term is small for small camera motion, which keeps float32 accurate where
 // absolute pixel coordinates would not be.
-__device__ void inverse4(const double *a, double *inv) {
-  const double s0 = a[0] * a[5] - a[4] * a[1], s1 = a[0] * a[6] - a[4] * a[2];
-  const double s2 = a[0] * a[7] - a[4] * a[3], s3 = a[1] * a[6] - a[5] * a[2];
-  const double s4 = a[1] * a[7] - a[5] * a[3], s5 = a[2] * a[7] - a[6] * a[3];
-  const double c5 = a[10] * a[15] - a[14] * a[11], c4 = a[9] * a[15] - a[13] * a[11];
-  const double c3 = a[9] * a[14] - a[13] * a[10], c2 = a[8] * a[15] - a[12] * a[11];
-  const double c1 = a[8] * a[14] - a[12] * a[10], c0 = a[8] * a[13] - a[12] * a[9];
-  const double id = 1.0 / (s0 * c5 - s1 * c4 + s2 * c3 + s3 * c2 - s4 * c1 + s5 * c0);
-  inv[0] = (a[5] * c5 - a[6] * c4 + a[7] * c3) * id;
-  inv[1] = (-a[1] * c5 + a[2] * c4 - a[3] * c3) * id;
-  inv[2] = (a[13] * s5 - a[14] * s4 + a[15] * s3) * id;
-  inv[3] = (-a[9] * s5 + a[10] * s4 - a[11] * s3) * id;
-  inv[4] = (-a[4] * c5 + a[6] * c2 - a[7] * c1) * id;
-  inv[5] = (a[0] * c5 - a[2] * c2 + a[3] * c1) * id;
-  inv[6] = (-a[12] * s5 + a[14] * s2 - a[15] * s1) * id;
-  inv[7] = (a[8] * s5 - a[10] * s2 + a[11] * s1) * id;
-  inv[8] = (a[4] * c4 - a[5] * c2 + a[7] * c0) * id;
-  inv[9] = (-a[0] * c4 + a[1] * c2 - a[3] * c0) * id;
-  inv[10] = (a[12] * s4 - a[13] * s2 + a[15] * s0) * id;
-  inv[11] = (-a[8] * s4 + a[9] * s2 - a[11] * s0) * id;
-  inv[12] = (-a[4] * c3 + a[5] * c1 - a[6] * c0) * id;
-  inv[13] = (a[0] * c3 - a[1] * c1 + a[2] * c0) * id;
-  inv[14] = (-a[12] * s3 + a[13] * s1 - a[14] * s0) * id;
-  inv[15] = (a[8] * s3 - a[9] * s1 + a[10] * s0) * id;
+// inv(a) by cofactors: twelve 2x2 minors of rows 0-1 (s) and rows 2-3 (c),
+// the determinant, then one entry of the adjugate per thread.  Sixteen
+// threads; every value is the same expression as a one-thread evaluation.
+__device__ __forceinline__ double minor2(const double *a, int k) {
+  switch (k) {
+    case 0: return a[0] * a[5] - a[4] * a[1];
+    case 1: return a[0] * a[6] - a[4] * a[2];
+    case 2: return a[0] * a[7] - a[4] * a[3];
+    case 3: return a[1] * a[6] - a[5] * a[2];
+    case 4: return a[1] * a[7] - a[5] * a[3];
+    case 5: return a[2] * a[7] - a[6] * a[3];
+    case 6: return a[8] * a[13] - a[12] * a[9];     // c0
+    case 7: return a[8] * a[14] - a[12] * a[10];    // c1
+    case 8: return a[8] * a[15] - a[12] * a[11];    // c2
+    case 9: return a[9] * a[14] - a[13] * a[10];    // c3
+    case 10: return a[9] * a[15] - a[13] * a[11];   // c4
+    default: return a[10] * a[15] - a[14] * a[11];  // c5
+  }
+}
+
+__device__ __forceinline__ double adjugate(const double *a, const double *s, const double *c, int k) {
+  switch (k) {
+    case 0: return a[5] * c[5] - a[6] * c[4] + a[7] * c[3];
+    case 1: return -a[1] * c[5] + a[2] * c[4] - a[3] * c[3];
+    case 2: return a[13] * s[5] - a[14] * s[4] + a[15] * s[3];
+    case 3: return -a[9] * s[5] + a[10] * s[4] - a[11] * s[3];
+    case 4: return -a[4] * c[5] + a[6] * c[2] - a[7] * c[1];
+    case 5: return a[0] * c[5] - a[2] * c[2] + a[3] * c[1];
+    case 6: return -a[12] * s[5] + a[14] * s[2] - a[15] * s[1];
+    case 7: return a[8] * s[5] - a[10] * s[2] + a[11] * s[1];
+    case 8: return a[4] * c[4] - a[5] * c[2] + a[7] * c[0];
+    case 9: return -a[0] * c[4] + a[1] * c[2] - a[3] * c[0];
+    case 10: return a[12] * s[4] - a[13] * s[2] + a[15] * s[0];
+    case 11: return -a[8] * s[4] + a[9] * s[2] - a[11] * s[0];
+    case 12: return -a[4] * c[3] + a[5] * c[1] - a[6] * c[0];
+    case 13: return a[0] * c[3] - a[1] * c[1] + a[2] * c[0];
+    case 14: return -a[12] * s[3] + a[13] * s[1] - a[14] * s[0];
+    default: return a[8] * s[3] - a[9] * s[1] + a[10] * s[0];
+  }
 }
 
 // E = VP_prev inv(VP_cur) - I, once per call, in float64, rounded to float32.
-__global__ void k_reproject_matrix(const double *__restrict__ vp_prev, const double *__restrict__ vp_cur,
-                                   float *__restrict__ E) {
-  __shared__ double inv[16];
-  if (threadIdx.x == 0) {
-    double a[16];
-    for (int i = 0; i < 16; ++i) a[i] = vp_cur[i];
-    inverse4(a, inv);
+// One warp: threads 0..15 own one matrix entry each.
+__global__ void __launch_bounds__(32) k_reproject_matrix(const double *__restrict__ vp_prev,
+                                                         const double *__restrict__ vp_cur,
+                                                         float *__restrict__ E) {
+  __shared__ double a[16], sc[12], inv[16], s_id;
+  const int t = threadIdx.x;
+  if (t < 16) a[t] = vp_cur[t];
+  __syncwarp();
+  if (t < 12) sc[t] = minor2(a, t);
+  __syncwarp();
+  if (t == 0) {
+    const double *s = sc, *c = sc + 6;
+    s_id = 1.0 / (s[0] * c[5] - s[1] * c[4] + s[2] * c[3] + s[3] * c[2] - s[4] * c[1] + s[5] * c[0]);
   }
-  __syncthreads();
-  if (threadIdx.x < 16) {
-    const int r = threadIdx.x >> 2, c = threadIdx.x & 3;
+  __syncwarp();
+  if (t < 16) inv[t] = adjugate(a, sc, sc + 6, t) * s_id;
+  __syncwarp();
+  if (t < 16) {
+    const int r = t >> 2, c = t & 3;
     double m = 0.0;
     for (int k = 0; k < 4; ++k) m += vp_prev[4 * r + k] * inv[4 * k + c];
-    E[threadIdx.x] = (float)(m - (r == c ? 1.0 : 0.0));
+    E[t] = (float)(m - (r == c ? 1.0 : 0.0));
   }
 }
 

@@ -1,11 +1,14 @@
 // quadtree.cu -- star_nt_quadtree: adaptive screen-space tiles (Sec. 3.1)
 // and tile-guided pass resolution (Sec. 3.2, Eq. 2).
 //
-// One warp per base tile; lane k < 21 owns the node whose split bit is bit k
-// of the tile's mask (bit 0 root, bits 1..4 level-1 nodes, bits 5..20
-// level-2 nodes), so ballots assemble new masks directly.  All decisions are
-// taken on integer colour differences with correctly rounded float64 square
-// roots summed in a fixed order, so they are reproducible bit for bit.
+// Split/merge decisions: one warp per base tile; lane k < 21 owns the node
+// whose split bit is bit k of the tile's mask (bit 0 root, bits 1..4 level-1
+// nodes, bits 5..20 level-2 nodes), so ballots assemble new masks directly.
+// Relaxation and the leaf histogram work bit-parallel on the tile's 8 x 8
+// level-3 cells (one 64-bit word per level), one thread per tile.  All
+// decisions are taken on integer colour differences with correctly rounded
+// float64 square roots summed in a fixed order, so they are reproducible bit
+// for bit.
 #include <math.h>
 
 #include <mutex>
@@ -46,45 +49,6 @@ __device__ __forceinline__ bool node_exists(uint32_t m, int k) {
   if (k < 5) return m & 1u;
   const int c1 = (k - 5) >> 2;
   return (m & 1u) && ((m >> (1 + c1)) & 1u);
-}
-
-// Cells (level-3 cells, row-major bit index 8 cy + cx) covered by node k:
-// k < 21 is the node of mask bit k, k >= 21 the level-3 cell k - 21.
-struct RegionTable {
-  unsigned long long m[85];
-};
-constexpr RegionTable make_regions() {
-  RegionTable t{};
-  for (int k = 0; k < 85; ++k) {
-    int l = 3, i = 0, j = 0;
-    if (k == 0) {
-      l = 0;
-    } else if (k < 5) {
-      l = 1; i = (k - 1) & 1; j = (k - 1) >> 1;
-    } else if (k < 21) {
-      const int q = k - 5, c1 = q >> 2, c2 = q & 3;
-      l = 2; i = (c1 & 1) * 2 + (c2 & 1); j = (c1 >> 1) * 2 + (c2 >> 1);
-    } else {
-      i = (k - 21) & 7; j = (k - 21) >> 3;
-    }
-    const int span = 8 >> l;
-    unsigned long long r = 0;
-    for (int b = 0; b < span; ++b)
-      for (int a = 0; a < span; ++a) r |= 1ull << ((j * span + b) * 8 + (i * span + a));
-    t.m[k] = r;
-  }
-  return t;
-}
-__constant__ RegionTable kRegions = make_regions();
-
-// level of the leaf covering level-3 cell (cx, cy) of a tile, 0 <= cx, cy < 8
-__device__ __forceinline__ int cell_level(uint32_t m, int cx, int cy) {
-  if (!(m & 1u)) return 0;
-  const int c1 = ((cy >> 2) << 1) | (cx >> 2);
-  if (!((m >> (1 + c1)) & 1u)) return 1;
-  const int c2 = (((cy >> 1) & 1) << 1) | ((cx >> 1) & 1);
-  if (!((m >> (5 + 4 * c1 + c2)) & 1u)) return 2;
-  return 3;
 }
 
 // Corner colours of a node (clamped to the image) and the six integer
@@ -172,94 +136,152 @@ __global__ void __launch_bounds__(256) k_qt_decide(const uint32_t *__restrict__ 
   if (lane == 0) mout[tile] = (m | split_bits) & ~merge_bits;
 }
 
-// One relaxation iteration (Jacobi: reads min, writes mout), warp per tile.
-// With LAST, the warp then counts the occupied leaves of its tile's final
-// mask, and the last block to finish applies Eq. 2 and writes the state.
-__device__ __forceinline__ bool relax_split(uint32_t m, uint32_t mL, uint32_t mR, uint32_t mU,
-                                            uint32_t mD, int tx, int ty, int tiles_x, int tiles_y,
-                                            int lane) {
-  if (lane >= 21) return false;
-  int l, i, j;
-  node_of_bit(lane, l, i, j);
-  if (!(node_exists(m, lane) && !((m >> lane) & 1u))) return false;
-  const int span = 8 >> l, cx0 = i * span, cy0 = j * span;
-  int deepest = 0;
-  for (int k = 0; k < span; ++k) {
-    // left / right columns and top / bottom rows just outside the leaf
-    if (cx0 > 0) deepest = max(deepest, cell_level(m, cx0 - 1, cy0 + k));
-    else if (tx > 0) deepest = max(deepest, cell_level(mL, 7, cy0 + k));
-    if (cx0 + span < 8) deepest = max(deepest, cell_level(m, cx0 + span, cy0 + k));
-    else if (tx + 1 < tiles_x) deepest = max(deepest, cell_level(mR, 0, cy0 + k));
-    if (cy0 > 0) deepest = max(deepest, cell_level(m, cx0 + k, cy0 - 1));
-    else if (ty > 0) deepest = max(deepest, cell_level(mU, cx0 + k, 7));
-    if (cy0 + span < 8) deepest = max(deepest, cell_level(m, cx0 + k, cy0 + span));
-    else if (ty + 1 < tiles_y) deepest = max(deepest, cell_level(mD, cx0 + k, 0));
-  }
-  return deepest >= l + 2;
+// ---------------------------------------------------------------------------
+// Relaxation and the leaf histogram, bit-parallel over the 8 x 8 level-3
+// cells of a tile (bit 8 cy + cx of a 64-bit word).
+
+constexpr unsigned long long kCol0 = 0x0101010101010101ull, kCol7 = kCol0 << 7;
+constexpr unsigned long long kRow0 = 0xFFull, kRow7 = kRow0 << 56;
+
+// cells of level-1 quadrant q (child index 2 y_half + x_half)
+__device__ __forceinline__ unsigned long long quad_cells(int q) {
+  return 0x0F0F0F0Full << ((q & 1) * 4 + (q >> 1) * 32);
+}
+// cells of level-2 node q2 = 4 c1 + c2 (mask bit 5 + q2)
+__device__ __forceinline__ unsigned long long node2_cells(int q2) {
+  const int c1 = q2 >> 2, c2 = q2 & 3;
+  const int i = (c1 & 1) * 2 + (c2 & 1), j = (c1 >> 1) * 2 + (c2 >> 1);
+  return 0x0303ull << (2 * i + 16 * j);
 }
 
-template <bool RELAX, bool LAST>
-__global__ void __launch_bounds__(256) k_qt_relax(const int32_t *__restrict__ id1, int W, int H, int B,
-                                                  int tiles_x, int tiles_y,
-                                                  const uint32_t *__restrict__ min,
-                                                  uint32_t *__restrict__ mout,
-                                                  uint32_t *__restrict__ hist, uint32_t *ticket,
-                                                  double delta2, double delta3,
-                                                  star_nt_pass_state *state) {
-  __shared__ uint32_t s_hist[4];
-  if (LAST) {
-    if (threadIdx.x < 4) s_hist[threadIdx.x] = 0u;
-    __syncthreads();
+// Cells whose leaf is at level >= 2 (d2) and at level 3 (d3) under mask m.
+__device__ __forceinline__ void deep_cells(uint32_t m, unsigned long long &d2, unsigned long long &d3) {
+  d2 = 0ull;
+  d3 = 0ull;
+  if (!(m & 1u)) return;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (!((m >> (1 + q)) & 1u)) continue;
+    d2 |= quad_cells(q);
+#pragma unroll
+    for (int c2 = 0; c2 < 4; ++c2)
+      if ((m >> (5 + 4 * q + c2)) & 1u) d3 |= node2_cells(4 * q + c2);
   }
+}
+
+// One Jacobi relaxation step of a tile: a leaf splits when an edge-adjacent
+// cell (in the tile or across its border) lies two or more levels deeper.
+// Only the root (level 0) and level-1 leaves can split: a level-2 leaf would
+// need a level-4 neighbour.  nb* = 0 where the tile has no neighbour.
+__device__ __forceinline__ uint32_t relax_mask(uint32_t m, uint32_t mL, uint32_t mR, uint32_t mU,
+                                               uint32_t mD) {
+  unsigned long long d2, d3, l2, l3, r2, r3, u2, u3, w2, w3;
+  deep_cells(m, d2, d3);
+  deep_cells(mL, l2, l3);
+  deep_cells(mR, r2, r3);
+  deep_cells(mU, u2, u3);
+  deep_cells(mD, w2, w3);
+  if (!(m & 1u)) {  // root leaf: neighbours' border cells at level >= 2
+    const bool s = (l2 & kCol7) | (r2 & kCol0) | (u2 & kRow7) | (w2 & kRow0);
+    return s ? (m | 1u) : m;
+  }
+  uint32_t out = m;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if ((m >> (1 + q)) & 1u) continue;  // split: not a leaf
+    const unsigned long long R = quad_cells(q);
+    const unsigned long long ring = (((R << 1) & ~kCol0) | ((R >> 1) & ~kCol7) | (R << 8) | (R >> 8)) & ~R;
+    const unsigned long long rows = 0xFFFFFFFFull << ((q >> 1) * 32);
+    const unsigned long long cols = 0x0F0F0F0F0F0F0F0Full << ((q & 1) * 4);
+    bool s = (d3 & ring) != 0ull;
+    if ((q & 1) == 0) s |= (l3 & kCol7 & rows) != 0ull;
+    else s |= (r3 & kCol0 & rows) != 0ull;
+    if ((q >> 1) == 0) s |= (u3 & kRow7 & cols) != 0ull;
+    else s |= (w3 & kRow0 & cols) != 0ull;
+    if (s) out |= 1u << (1 + q);
+  }
+  return out;
+}
+
+// neighbour masks of tile (tx, ty), 0 outside the image
+__device__ __forceinline__ uint32_t relax_tile(const uint32_t *__restrict__ min, int tile, int tx,
+                                               int ty, int tiles_x, int tiles_y) {
+  const uint32_t m = min[tile];
+  const uint32_t mL = tx > 0 ? min[tile - 1] : 0u, mR = tx + 1 < tiles_x ? min[tile + 1] : 0u;
+  const uint32_t mU = ty > 0 ? min[tile - tiles_x] : 0u;
+  const uint32_t mD = ty + 1 < tiles_y ? min[tile + tiles_x] : 0u;
+  return relax_mask(m, mL, mR, mU, mD);
+}
+
+// One relaxation iteration (Jacobi: reads min, writes mout), thread per tile.
+__global__ void __launch_bounds__(256) k_qt_relax(const uint32_t *__restrict__ min,
+                                                  uint32_t *__restrict__ mout, int tiles_x,
+                                                  int tiles_y) {
+  const int tile = blockIdx.x * 256 + threadIdx.x;
+  if (tile >= tiles_x * tiles_y) return;
+  mout[tile] = relax_tile(min, tile, tile % tiles_x, tile / tiles_x, tiles_x, tiles_y);
+}
+
+// Occupied leaves of a tile per level under its final mask m; occ = the
+// level-3 cells holding a pass-1 fragment.
+__device__ __forceinline__ void count_leaves(uint32_t m, unsigned long long occ, uint32_t (&cnt)[4]) {
+  if (!(m & 1u)) {
+    cnt[0] += occ != 0ull ? 1u : 0u;
+    return;
+  }
+  unsigned long long d2, d3;
+  deep_cells(m, d2, d3);
+  cnt[3] += __popcll(occ & d3);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (!((m >> (1 + q)) & 1u)) {
+      cnt[1] += (occ & quad_cells(q)) != 0ull ? 1u : 0u;
+      continue;
+    }
+#pragma unroll
+    for (int c2 = 0; c2 < 4; ++c2)
+      if (!((m >> (5 + 4 * q + c2)) & 1u)) cnt[2] += (occ & node2_cells(4 * q + c2)) != 0ull ? 1u : 0u;
+  }
+}
+
+// The last relaxation (or a copy), then the histogram of occupied leaves; the
+// last block to finish applies Eq. 2 and writes the state.  A warp per tile
+// reads the tile's pass-1 ids for the occupancy; lane 0 does the rest.
+template <bool RELAX>
+__global__ void __launch_bounds__(256) k_qt_last(const int32_t *__restrict__ id1, int W, int H, int B,
+                                                 int tiles_x, int tiles_y,
+                                                 const uint32_t *__restrict__ min,
+                                                 uint32_t *__restrict__ mout,
+                                                 uint32_t *__restrict__ hist, uint32_t *ticket,
+                                                 double delta2, double delta3,
+                                                 star_nt_pass_state *state) {
+  __shared__ uint32_t s_hist[4];
+  if (threadIdx.x < 4) s_hist[threadIdx.x] = 0u;
+  __syncthreads();
   const int tile = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (tile < tiles_x * tiles_y) {
     const int tx = tile % tiles_x, ty = tile / tiles_x;
-    uint32_t m = min[tile];
-    if (RELAX) {
-      const uint32_t mL = tx > 0 ? min[tile - 1] : 0u, mR = tx + 1 < tiles_x ? min[tile + 1] : 0u;
-      const uint32_t mU = ty > 0 ? min[tile - tiles_x] : 0u;
-      const uint32_t mD = ty + 1 < tiles_y ? min[tile + tiles_x] : 0u;
-      m |= __ballot_sync(0xffffffffu, relax_split(m, mL, mR, mU, mD, tx, ty, tiles_x, tiles_y, lane));
+    // occupancy of the tile's 64 level-3 cells (B/8 pixels wide)
+    const int cs = B / 8;
+    unsigned long long occ = 0;
+    for (int k = lane; k < B * B; k += 32) {
+      const int lx = k % B, ly = k / B;
+      const int x = tx * B + lx, y = ty * B + ly;
+      if (x < W && y < H && id1[(size_t)y * W + x] >= 0) occ |= 1ull << ((ly / cs) * 8 + (lx / cs));
     }
-    if (lane == 0) mout[tile] = m;
-    if (LAST) {
-      // occupancy of the tile's 64 level-3 cells (B/8 pixels wide)
-      const int cs = B / 8;
-      unsigned long long occ = 0;
-      for (int k = lane; k < B * B; k += 32) {
-        const int lx = k % B, ly = k / B;
-        const int x = tx * B + lx, y = ty * B + ly;
-        if (x < W && y < H && id1[(size_t)y * W + x] >= 0) occ |= 1ull << ((ly / cs) * 8 + (lx / cs));
-      }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) occ |= __shfl_xor_sync(0xffffffffu, occ, o);
-      // leaves: lanes own the 21 nodes of levels 0..2, then the 64 level-3 cells
-      uint32_t cnt[4] = {0, 0, 0, 0};
-      for (int k = lane; k < 21 + 64; k += 32) {
-        int l, i, j;
-        bool isleaf;
-        if (k < 21) {
-          node_of_bit(k, l, i, j);
-          isleaf = node_exists(m, k) && !((m >> k) & 1u);
-        } else {
-          l = 3;
-          i = (k - 21) & 7;
-          j = (k - 21) >> 3;
-          isleaf = cell_level(m, i, j) == 3;
-        }
-        if (isleaf && (occ & kRegions.m[k])) ++cnt[l];
-      }
+    for (int o = 16; o > 0; o >>= 1) occ |= __shfl_xor_sync(0xffffffffu, occ, o);
+    if (lane == 0) {
+      const uint32_t m = RELAX ? relax_tile(min, tile, tx, ty, tiles_x, tiles_y) : min[tile];
+      mout[tile] = m;
+      uint32_t cnt[4] = {0u, 0u, 0u, 0u};
+      count_leaves(m, occ, cnt);
 #pragma unroll
-      for (int l = 0; l < 4; ++l) {
-        uint32_t c = cnt[l];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-        if (lane == 0 && c) atomicAdd(&s_hist[l], c);
-      }
+      for (int l = 0; l < 4; ++l)
+        if (cnt[l]) atomicAdd(&s_hist[l], cnt[l]);
     }
   }
-  if (!LAST) return;
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int l = 0; l < 4; ++l)
@@ -330,20 +352,20 @@ extern "C" star_nt_status star_nt_quadtree(const uint32_t *rgba8, const int32_t 
   k_qt_decide<<<wblocks, 256, 0, st>>>(rgba8, W, H, B, L.tiles_x, nt, 6.0 * params->tau_split,
                                        6.0 * params->tau_merge, mask_prev, ma);
   const uint32_t *src = ma;
+  const int tblocks = (nt + 255) / 256;
   for (int it = 0; it + 1 < iters; ++it) {  // all but the last relaxation
     uint32_t *d = src == ma ? mb : ma;
-    k_qt_relax<true, false><<<wblocks, 256, 0, st>>>(id1, W, H, B, L.tiles_x, L.tiles_y, src, d, hist,
-                                                     ticket, params->delta2, params->delta3, state);
+    k_qt_relax<<<tblocks, 256, 0, st>>>(src, d, L.tiles_x, L.tiles_y);
     src = d;
   }
   // the last relaxation (a plain copy when there is none), the histogram of
   // occupied leaves and Eq. 2, in one launch
   if (iters > 0)
-    k_qt_relax<true, true><<<wblocks, 256, 0, st>>>(id1, W, H, B, L.tiles_x, L.tiles_y, src, mask_out,
-                                                    hist, ticket, params->delta2, params->delta3, state);
+    k_qt_last<true><<<wblocks, 256, 0, st>>>(id1, W, H, B, L.tiles_x, L.tiles_y, src, mask_out, hist,
+                                             ticket, params->delta2, params->delta3, state);
   else
-    k_qt_relax<false, true><<<wblocks, 256, 0, st>>>(id1, W, H, B, L.tiles_x, L.tiles_y, src, mask_out,
-                                                     hist, ticket, params->delta2, params->delta3, state);
+    k_qt_last<false><<<wblocks, 256, 0, st>>>(id1, W, H, B, L.tiles_x, L.tiles_y, src, mask_out, hist,
+                                              ticket, params->delta2, params->delta3, state);
   return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
 }
 
