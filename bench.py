@@ -130,9 +130,11 @@ def run_ours(args, rank, world):
     sc, desc = workload_scene(args.workload)
     W, H = sc.width, sc.height
     w, wname = mlp_weights()
-    x_dtype = sn.BF16 if args.mlp == "bf16" else sn.F32
+    x_dtype = sn.F32 if args.mlp == "f32" else sn.BF16
+    # fused resolve: bf16 or fp8 operands on tcgen05 (f32 runs the separate kernels)
+    fused_kind = (args.mlp if args.mlp == "fp8" else True) if args.fused and x_dtype == sn.BF16 else False
     star = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=x_dtype, base_tile=args.base_tile,
-                    fused=args.fused and x_dtype == sn.BF16, persistent=args.persistent,
+                    fused=fused_kind, persistent=args.persistent,
                     merge_scale2=args.merge_scale2)
     plain = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=sn.F32)
     n_frames = 2 * (20 + 2 * args.warmup + 2 * args.steps)
@@ -291,7 +293,7 @@ def run_ours(args, rank, world):
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32+bf16" if x_dtype == sn.BF16 else "f32",
+        "dtype": {"bf16": "f32+bf16", "fp8": "f32+e4m3", "f32": "f32"}[args.mlp],
         "data": "synthetic seeded triangle soup, orbit camera",
         "config": {"workload": desc, "frames_per_step": 2, "mlp": args.mlp, "weights": wname,
                    "resolve": "fused" if star.fused else "separate",
@@ -347,7 +349,8 @@ def end_to_end(sn, torch, sc, w, x_dtype, W, H, cams, args, tuning=None):
     are read back."""
     from paper_2606_16747_b300.pipeline import Renderer
     r = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=x_dtype, base_tile=args.base_tile,
-                 fused=args.fused and x_dtype == sn.BF16, persistent=args.persistent, tuning=tuning,
+                 fused=(args.mlp if args.mlp == "fp8" else True) if args.fused and x_dtype == sn.BF16 else False,
+                 persistent=args.persistent, tuning=tuning,
                  merge_scale2=args.merge_scale2)
     hv = torch.from_numpy(np.ascontiguousarray(sc.verts)).pin_memory()
     hc = torch.from_numpy(np.ascontiguousarray(sc.rgba8).view(np.int32)).pin_memory()
@@ -492,7 +495,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="hd", choices=["hd", "uhd", "small"])
-    ap.add_argument("--mlp", default="bf16", choices=["bf16", "f32"])
+    ap.add_argument("--mlp", default="bf16", choices=["bf16", "fp8", "f32"])
     ap.add_argument("--base-tile", type=int, default=16)
     ap.add_argument("--separate-passes", dest="persistent", action="store_false",
                     help="three geometry-pass launches instead of one persistent launch")

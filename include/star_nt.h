@@ -287,6 +287,18 @@ star_nt_status star_nt_resolve(const star_nt_scene *scene, const star_nt_bins *b
                                const star_nt_mlp *w, float *rgba32f, uint32_t *rgba8,
                                int32_t *d_status, void *stream);
 
+/* star_nt_resolve_fp8 -- star_nt_resolve with the MLP in FP8: e4m3 operands  */
+/* on the tcgen05 tensor cores (fp32 accumulation), one power-of-two scale per */
+/* weight tensor and per operand row (pixel), biases, rescale and ReLU in     */
+/* fp32.  Same arguments and errors as star_nt_resolve.  e4m3 keeps 3 mantissa */
+/* bits, so f(x) is coarser than with bf16; the parity test states the bound. */
+star_nt_status star_nt_resolve_fp8(const star_nt_scene *scene, const star_nt_bins *bins2,
+                                   const star_nt_bins *bins3, const star_nt_layers *layers1,
+                                   const star_nt_layers *layers2, const star_nt_layers *layers3,
+                                   int32_t W, int32_t H, const star_nt_params *params,
+                                   const star_nt_mlp *w, float *rgba32f, uint32_t *rgba8,
+                                   int32_t *d_status, void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* star_nt_composite -- Eq. 4: C = C_exact,2 + T_2 f(x) + T_all C_b.          */
 /* front: [P][4] (from star_nt_build_inputs), f: [P][4].  Writes rgba32f      */

@@ -244,17 +244,257 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
                  : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// FP8 variant: e4m3 operands on the tcgen05 tensor cores (kind::f8f6f4, K = 32
+// per MMA), fp32 accumulation.  Every weight row (output unit) carries its own
+// power-of-two scale (largest |w| of the row mapped below 448, the e4m3
+// maximum), and so does every operand row (a pixel's input or hidden
+// activations), so each accumulator is exact to rescale.  Bias, the rescale and
+// ReLU run in the fp32 epilogue.
+
+// shared memory map (bytes from a 1024-aligned base); per tile 6144 bytes:
+// X (later H2) in one core column, H1 in two
+constexpr uint32_t kF8X = 0;          // tile t: kF8X + 6144 t
+constexpr uint32_t kF8H1 = 2048;      // tile t: kF8H1 + 6144 t
+constexpr uint32_t kF8Z = 12288;      // zero block
+constexpr uint32_t kF8W1 = 14336;     // N=32, K=32: 2 x 512
+constexpr uint32_t kF8W2 = 15360;     // N=16, K=32: 2 x 256
+constexpr uint32_t kF8W3 = 15872;     // N=16, K=32 (3 rows, K 16 used): 2 x 256
+constexpr uint32_t kF8B = 16384;      // b1[32], b2[16], b3[16]
+constexpr uint32_t kF8S = 16640;      // inverse weight-row scales: 1/s1[32], 1/s2[16], 1/s3[16]
+constexpr uint32_t kF8Bar = 16896;    // mma barrier, tmem slot, abort flag
+constexpr uint32_t kF8Used = 16912;
+
+// power of two s with max |v| * s <= 448 (1 when max is 0)
+__device__ __forceinline__ float row_scale(float mx) {
+  if (!(mx > 0.0f)) return 1.0f;
+  int k = __float2int_rd(__log2f(448.0f / mx));
+  k = max(-120, min(120, k));
+  if (mx * ldexpf(1.0f, k) > 448.0f) --k;
+  return ldexpf(1.0f, k);
+}
+
+// row n of a [rows][cols] weight matrix into an e4m3 B operand (row scale
+// s = row_scale(max |w_n.|), stored as 1/s in inv)
+__device__ __forceinline__ void put_row8(uint8_t *base, int lbo, const float *w, int n, int cols,
+                                         float *inv) {
+  float mx = 0.0f;
+  for (int k = 0; k < cols; ++k) mx = fmaxf(mx, fabsf(w[n * cols + k]));
+  const float sc = row_scale(mx);
+  for (int k = 0; k < cols; ++k) put_w8(base, n, k, lbo, w[n * cols + k] * sc);
+  inv[n] = 1.0f / sc;  // exact: a power of two
+}
+
+__global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
+    k_resolve_fp8(FeatIn in, float bg0, float bg1, float bg2, float kappa,
+                  const float *__restrict__ w1, const float *__restrict__ b1,
+                  const float *__restrict__ w2, const float *__restrict__ b2,
+                  const float *__restrict__ w3, const float *__restrict__ b3,
+                  float4 *__restrict__ out, uint32_t *__restrict__ out8, int32_t *status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                            ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t sbase = smem_u32(sm);
+  const uint32_t bar = sbase + kF8Bar;
+  uint32_t *s_tmem = reinterpret_cast<uint32_t *>(sm + kF8Bar + 8);
+  volatile int *s_abort = reinterpret_cast<volatile int *>(sm + kF8Bar + 12);
+  float *sb = reinterpret_cast<float *>(sm + kF8B);
+  if (in.hd2->n_pixels <= 0 || in.hd3->n_pixels <= 0) return;  // a pass was rejected
+
+  // weights: e4m3 rows with power-of-two row scales, zero padded; biases fp32
+  float *si = reinterpret_cast<float *>(sm + kF8S);
+  for (int i = tid; i < (int)(kF8B - kF8Z) / 4; i += kRThreads)
+    reinterpret_cast<uint32_t *>(sm + kF8Z)[i] = 0u;
+  __syncthreads();
+  if (tid < 32) put_row8(sm + kF8W1, 512, w1, tid, 5, si);
+  else if (tid < 48) put_row8(sm + kF8W2, 256, w2, tid - 32, 32, si + 32);
+  else if (tid < 51) put_row8(sm + kF8W3, 256, w3, tid - 48, 16, si + 48);
+  else if (tid < 64) si[tid] = 0.0f;
+  if (tid < 32) sb[tid] = b1[tid];
+  if (tid < 16) sb[32 + tid] = b2[tid];
+  if (tid < 16) sb[48 + tid] = tid < 3 ? b3[tid] : 0.0f;
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    *s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(s_tmem)),
+                 "r"(kRTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *s_tmem;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const int row = tid;
+
+  const uint64_t dW1 = smem_desc(sbase + kF8W1, 512, 128);
+  const uint64_t dW2 = smem_desc(sbase + kF8W2, 256, 128);
+  const uint64_t dW3 = smem_desc(sbase + kF8W3, 256, 128);
+  const int P = in.W * in.H;  // < 2^31, checked by the host
+  const int nrounds = (P + kRTiles * kRRows - 1) / (kRTiles * kRRows);
+  uint32_t ph = 0u;
+
+  for (int round = blockIdx.x; round < nrounds; round += gridDim.x) {
+    const int base = round * (kRTiles * kRRows);
+    float4 front[kRTiles];
+    bool flag[kRTiles];
+    float sx[kRTiles], sh[kRTiles];  // row scales of the operand of the next MMA
+#pragma unroll
+    for (int t = 0; t < kRTiles; ++t) {
+      const int p = base + t * kRRows + row;
+      float xv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      front[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (p < P) {
+        const int y = (int)((unsigned)p / (unsigned)in.W), x = p - y * in.W;
+        pixel_features(in, bg0, bg1, bg2, kappa, x, y, xv, front[t]);
+      }
+      flag[t] = xv[5] != 0.0f;
+      float mx = 0.0f;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) mx = fmaxf(mx, fabsf(xv[k]));
+      sx[t] = row_scale(mx);
+      const uint32_t q0 = pack4_e4m3(xv[0] * sx[t], xv[1] * sx[t], xv[2] * sx[t], xv[3] * sx[t]);
+      const uint32_t q1 = pack4_e4m3(xv[4] * sx[t], 0.f, 0.f, 0.f);
+      *reinterpret_cast<uint4 *>(sm + kF8X + t * 6144 + row * 16) = make_uint4(q0, q1, 0u, 0u);
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    // ---- layer 1: [X | 0] (K = 32) against W1
+    if (tid == 0) {
+      fence_after();
+#pragma unroll
+      for (int t = 0; t < kRTiles; ++t) {
+        const uint32_t x = kF8X + t * 6144;
+        mma_e4m3(tmem + 32 * t, smem_desc(sbase + x, kF8Z - x, 128), dW1, idesc_e4m3(32), 0u);
+      }
+      mma_commit(bar);
+    }
+    if (!mbar_wait(bar, ph)) *s_abort = 1;
+    ph ^= 1u;
+    fence_after();
+#pragma unroll
+    for (int t = 0; t < kRTiles; ++t) {
+      float d[32];
+      tmem_ld32(tmem + lane_base + 32 * t, d);
+      const float k1 = 1.0f / sx[t];  // exact: a power of two
+      float mx = 0.0f;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        d[j] = fmaxf(fmaf(d[j], k1 * si[j], sb[j]), 0.0f);
+        mx = fmaxf(mx, d[j]);
+      }
+      sh[t] = row_scale(mx);
+      uint32_t pk[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        pk[j] = pack4_e4m3(d[4 * j] * sh[t], d[4 * j + 1] * sh[t], d[4 * j + 2] * sh[t], d[4 * j + 3] * sh[t]);
+      uint8_t *h = sm + kF8H1 + t * 6144 + row * 16;
+      *reinterpret_cast<uint4 *>(h) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      *reinterpret_cast<uint4 *>(h + 2048) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    if (*s_abort) break;
+    // ---- layer 2: H1 (K = 32) against W2
+    if (tid == 0) {
+      fence_after();
+#pragma unroll
+      for (int t = 0; t < kRTiles; ++t)
+        mma_e4m3(tmem + 32 * t, smem_desc(sbase + kF8H1 + t * 6144, 2048, 128), dW2, idesc_e4m3(16), 0u);
+      mma_commit(bar);
+    }
+    if (!mbar_wait(bar, ph)) *s_abort = 1;
+    ph ^= 1u;
+    fence_after();
+#pragma unroll
+    for (int t = 0; t < kRTiles; ++t) {
+      float d[16];
+      tmem_ld16(tmem + lane_base + 32 * t, d);
+      const float k2 = 1.0f / sh[t];
+      float mx = 0.0f;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        d[j] = fmaxf(fmaf(d[j], k2 * si[32 + j], sb[32 + j]), 0.0f);
+        mx = fmaxf(mx, d[j]);
+      }
+      sh[t] = row_scale(mx);
+      uint32_t pk[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        pk[j] = pack4_e4m3(d[4 * j] * sh[t], d[4 * j + 1] * sh[t], d[4 * j + 2] * sh[t], d[4 * j + 3] * sh[t]);
+      *reinterpret_cast<uint4 *>(sm + kF8X + t * 6144 + row * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    if (*s_abort) break;
+    // ---- layer 3: [H2 | 0] (K = 32) against W3, D3 in columns 16..31
+    if (tid == 0) {
+      fence_after();
+#pragma unroll
+      for (int t = 0; t < kRTiles; ++t) {
+        const uint32_t x = kF8X + t * 6144;
+        mma_e4m3(tmem + 32 * t + 16, smem_desc(sbase + x, kF8Z - x, 128), dW3, idesc_e4m3(16), 0u);
+      }
+      mma_commit(bar);
+    }
+    if (!mbar_wait(bar, ph)) *s_abort = 1;
+    ph ^= 1u;
+    fence_after();
+    // ---- composite, Eq. 4
+#pragma unroll
+    for (int t = 0; t < kRTiles; ++t) {
+      float d[4];
+      tmem_ld4(tmem + lane_base + 32 * t + 16, d);
+      const int p = base + t * kRRows + row;
+      if (p < P) {
+        const float k3 = 1.0f / sh[t];
+        float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+        if (flag[t]) {
+          f0 = fmaxf(fmaf(d[0], k3 * si[48], sb[48]), 0.0f);
+          f1 = fmaxf(fmaf(d[1], k3 * si[49], sb[49]), 0.0f);
+          f2 = fmaxf(fmaf(d[2], k3 * si[50], sb[50]), 0.0f);
+        }
+        const float4 fr = front[t];
+        const float r = fmaf(fr.w, f0, fr.x), g = fmaf(fr.w, f1, fr.y), b = fmaf(fr.w, f2, fr.z);
+        if (out) out[p] = make_float4(r, g, b, 1.0f);
+        if (out8) out8[p] = quantize8(r, g, b);
+      }
+    }
+    fence_before();
+    __syncthreads();
+    if (*s_abort) break;
+  }
+  if (*s_abort && tid == 0) raise_status(status, STAR_NT_ERR_TIMEOUT);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kRTmemCols)
+                 : "memory");
+}
+
 }  // namespace star
 
 using namespace star;
 
-extern "C" star_nt_status star_nt_resolve(const star_nt_scene *scene, const star_nt_bins *b2,
-                                          const star_nt_bins *b3, const star_nt_layers *l1,
-                                          const star_nt_layers *l2, const star_nt_layers *l3,
-                                          int32_t W, int32_t H, const star_nt_params *params,
-                                          const star_nt_mlp *w, float *rgba32f, uint32_t *rgba8,
-                                          int32_t *d_status, void *stream) {
+static star_nt_status launch_resolve(bool fp8, const star_nt_scene *scene, const star_nt_bins *b2,
+                                     const star_nt_bins *b3, const star_nt_layers *l1,
+                                     const star_nt_layers *l2, const star_nt_layers *l3, int32_t W,
+                                     int32_t H, const star_nt_params *params, const star_nt_mlp *w,
+                                     float *rgba32f, uint32_t *rgba8, int32_t *d_status,
+                                     void *stream) {
   static_assert(kQUsed + 1024 <= kQSmem, "shared memory map");
+  static_assert(kF8Used + 1024 <= kQSmem, "shared memory map");
   if (!scene || !b2 || !b3 || !b2->mem || !b3->mem || !params || !w || W <= 0 || H <= 0)
     return STAR_NT_ERR_ARG;
   if (!w->w1 || !w->b1 || !w->w2 || !w->b2 || !w->w3 || !w->b3 || (!rgba32f && !rgba8))
@@ -264,12 +504,12 @@ extern "C" star_nt_status star_nt_resolve(const star_nt_scene *scene, const star
   if (((uintptr_t)rgba32f & 15u) || ((uintptr_t)l3->tail & 15u)) return STAR_NT_ERR_ARG;
   if (scene->n_tris > 0 && !scene->rgba8) return STAR_NT_ERR_ARG;
   if ((long long)W * H > 0x7fffffffLL - 256) return STAR_NT_ERR_ARG;
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(k_resolve, cudaFuncAttributeMaxDynamicSharedMemorySize, kQSmem) !=
-        cudaSuccess)
+  auto kern = fp8 ? k_resolve_fp8 : k_resolve;
+  static bool attr[2] = {false, false};
+  if (!attr[fp8]) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kQSmem) != cudaSuccess)
       return STAR_NT_ERR_CUDA;
-    attr = true;
+    attr[fp8] = true;
   }
   BinsView v2 = bins_view(*b2), v3 = bins_view(*b3);
   FeatIn in{W, H, v2.hd, v3.hd, scene->rgba8, l1->id1, l2->id2, l3->n,
@@ -280,8 +520,28 @@ extern "C" star_nt_status star_nt_resolve(const star_nt_scene *scene, const star
   const long long rounds = ((long long)W * H + kRTiles * kRRows - 1) / (kRTiles * kRRows);
   long long grid = (long long)sms * kRCtasPerSm;
   if (grid > rounds) grid = rounds;
-  k_resolve<<<(unsigned)grid, kRThreads, kQSmem, (cudaStream_t)stream>>>(
+  kern<<<(unsigned)grid, kRThreads, kQSmem, (cudaStream_t)stream>>>(
       in, params->bg[0], params->bg[1], params->bg[2], params->kappa_n, w->w1, w->b1, w->w2, w->b2,
       w->w3, w->b3, reinterpret_cast<float4 *>(rgba32f), rgba8, d_status);
   return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
+}
+
+extern "C" star_nt_status star_nt_resolve(const star_nt_scene *scene, const star_nt_bins *b2,
+                                          const star_nt_bins *b3, const star_nt_layers *l1,
+                                          const star_nt_layers *l2, const star_nt_layers *l3,
+                                          int32_t W, int32_t H, const star_nt_params *params,
+                                          const star_nt_mlp *w, float *rgba32f, uint32_t *rgba8,
+                                          int32_t *d_status, void *stream) {
+  return launch_resolve(false, scene, b2, b3, l1, l2, l3, W, H, params, w, rgba32f, rgba8, d_status,
+                        stream);
+}
+
+extern "C" star_nt_status star_nt_resolve_fp8(const star_nt_scene *scene, const star_nt_bins *b2,
+                                              const star_nt_bins *b3, const star_nt_layers *l1,
+                                              const star_nt_layers *l2, const star_nt_layers *l3,
+                                              int32_t W, int32_t H, const star_nt_params *params,
+                                              const star_nt_mlp *w, float *rgba32f, uint32_t *rgba8,
+                                              int32_t *d_status, void *stream) {
+  return launch_resolve(true, scene, b2, b3, l1, l2, l3, W, H, params, w, rgba32f, rgba8, d_status,
+                        stream);
 }

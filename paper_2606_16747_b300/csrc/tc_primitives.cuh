@@ -81,6 +81,33 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b
       : "memory");
 }
 
+// kind::f8f6f4 instruction descriptor: e4m3 A and B (format code 0), fp32 D,
+// K-major, M = 128 (K = 32 per instruction)
+__host__ __device__ constexpr uint32_t idesc_e4m3(uint32_t n) {
+  return (1u << 4) | ((n >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// four fp32 values to e4m3 (round to nearest even, saturating), byte i = v_i
+__device__ __forceinline__ uint32_t pack4_e4m3(float v0, float v1, float v2, float v3) {
+  uint32_t r;
+  asm("{\n .reg .b16 lo, hi;\n"
+      " cvt.rn.satfinite.e4m3x2.f32 lo, %2, %1;\n"
+      " cvt.rn.satfinite.e4m3x2.f32 hi, %4, %3;\n"
+      " mov.b32 %0, {lo, hi};\n}\n"
+      : "=r"(r)
+      : "f"(v0), "f"(v1), "f"(v2), "f"(v3));
+  return r;
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                : "memory");
@@ -142,6 +169,12 @@ __device__ __forceinline__ uint32_t pack_relu_bf16(float lo, float hi) {
 __device__ __forceinline__ void put_w(uint8_t *base, int n, int k, int lbo, float v) {
   __nv_bfloat16 h = __float2bfloat16_rn(v);
   *reinterpret_cast<__nv_bfloat16 *>(base + (k >> 3) * lbo + n * 16 + (k & 7) * 2) = h;
+}
+
+// one e4m3 weight into the K-major core-matrix layout of a B operand
+// (16 elements per 16-byte core-matrix row)
+__device__ __forceinline__ void put_w8(uint8_t *base, int n, int k, int lbo, float v) {
+  base[(k >> 4) * lbo + n * 16 + (k & 15)] = (uint8_t)(pack4_e4m3(v, 0.f, 0.f, 0.f) & 255u);
 }
 
 // A bias enters an MMA as two weight columns (k, k + 1) against an A operand

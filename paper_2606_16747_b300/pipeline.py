@@ -41,8 +41,10 @@ class Renderer:
         if base_tile is not None:
             self.params.base_tile = base_tile
         self.x_dtype = x_dtype
-        # fused: upscale + features + BF16 MLP + composite in one kernel
+        # fused: upscale + features + MLP on tcgen05 + composite in one kernel
+        # (True or "bf16": bf16 operands; "fp8": e4m3 operands)
         self.fused = bool(fused)
+        self.fused_fp8 = fused == "fp8"
         # persistent: the three geometry passes in one launch (tuning: (block_w, ctas_per_sm))
         self.persistent = bool(persistent)
         self.tuning = tuning
@@ -151,10 +153,10 @@ class Renderer:
                    ("pass3", lambda: sn.geometry_pass(self.scene, b3, 3, self.l3, self.status,
                                                       stream))]
         if self.fused:
-            st.append(("resolve", lambda: sn.resolve(self.scene, b2, b3, self.l1, self.l2, self.l3,
-                                                     self.W, self.H, self.params, self.mlp,
-                                                     self.rgba32f, self.rgba8_out, self.status,
-                                                     stream)))
+            res = sn.resolve_fp8 if self.fused_fp8 else sn.resolve
+            st.append(("resolve", lambda: res(self.scene, b2, b3, self.l1, self.l2, self.l3,
+                                              self.W, self.H, self.params, self.mlp,
+                                              self.rgba32f, self.rgba8_out, self.status, stream)))
         else:
             st += [("features", lambda: sn.upscale_features(self.scene, b2, b3, self.l1, self.l2,
                                                             self.l3, self.W, self.H, self.params,

@@ -26,7 +26,7 @@ EXPORTS = ("star_nt_version", "star_nt_status_string", "star_nt_default_params",
            "star_nt_reproject", "star_nt_geometry_pass", "star_nt_upscale_features",
            "star_nt_geometry_pass_merged", "star_nt_abuffer", "star_nt_train_ws_bytes",
            "star_nt_mse_grad", "star_nt_mlp_backward", "star_nt_adam", "star_nt_raster_passes",
-           "star_nt_resolve", "star_nt_geometry_passes")
+           "star_nt_resolve", "star_nt_geometry_passes", "star_nt_resolve_fp8")
 
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
@@ -124,6 +124,7 @@ def lib():
         L.star_nt_resolve.argtypes = [ctypes.POINTER(Scene)] + [ctypes.POINTER(Bins)] * 2 + \
             [ctypes.POINTER(Layers)] * 3 + [_I32, _I32, ctypes.POINTER(Params), ctypes.POINTER(Mlp),
                                             _P, _P, _P, _P]
+        L.star_nt_resolve_fp8.argtypes = L.star_nt_resolve.argtypes
         L.star_nt_infer.argtypes = [ctypes.POINTER(Mlp), _I32, _P, _P, _I64, _P, _P]
         L.star_nt_composite.argtypes = [_P, _P, _I64, _P, _P, _P]
         L.star_nt_quadtree_ws_bytes.argtypes = [_I32, _I32, _I32, ctypes.POINTER(ctypes.c_size_t)]
@@ -277,6 +278,15 @@ def resolve(scene: Scene, bins2, bins3, layers1, layers2, layers3, W, H, params:
             rgba32f=None, rgba8=None, status=None, stream=None):
     ls = [layers_struct(l) for l in (layers1, layers2, layers3)]
     _check("star_nt_resolve", lib().star_nt_resolve(
+        ctypes.byref(scene), ctypes.byref(bins2.c), ctypes.byref(bins3.c), *[ctypes.byref(l) for l in ls],
+        W, H, ctypes.byref(params), ctypes.byref(w), _ptr(rgba32f), _ptr(rgba8), _ptr(status),
+        _stream(stream)))
+
+
+def resolve_fp8(scene: Scene, bins2, bins3, layers1, layers2, layers3, W, H, params: Params, w: Mlp,
+                rgba32f=None, rgba8=None, status=None, stream=None):
+    ls = [layers_struct(l) for l in (layers1, layers2, layers3)]
+    _check("star_nt_resolve_fp8", lib().star_nt_resolve_fp8(
         ctypes.byref(scene), ctypes.byref(bins2.c), ctypes.byref(bins3.c), *[ctypes.byref(l) for l in ls],
         W, H, ctypes.byref(params), ctypes.byref(w), _ptr(rgba32f), _ptr(rgba8), _ptr(status),
         _stream(stream)))
