@@ -107,6 +107,14 @@ typedef struct {
 
 void star_nt_default_params(star_nt_params *p);
 
+/* star_nt_preload: load every kernel of the library onto the current device.
+ * Optional; call once per device before the first frame.  CUDA loads modules
+ * lazily on first use; a first use inside a stream capture, or beside work
+ * on other streams, can stall the calling thread while the module loads.
+ * Returns STAR_NT_ERR_CUDA if a kernel cannot be loaded (no device, or a
+ * device of another architecture). */
+star_nt_status star_nt_preload(void);
+
 /* ------------------------------------------------------------------------ */
 /* star_nt_raster -- geometry front end of one pass (Sec. 3, Fig. 1).         */
 /*                                                                           */

@@ -317,3 +317,37 @@ extern "C" star_nt_status star_nt_reproject(const float *prev_rgba, const float 
                                     reinterpret_cast<float4 *>(out_rgba), out_rgba8);
   return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
 }
+
+namespace star {
+// Loads this file's kernels onto the current device (see star_nt_preload).
+cudaError_t preload_frame() {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaSuccess, r;
+  if ((r = cudaFuncGetAttributes(&a, k_mlp_f32)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_composite)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_reproject_matrix)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_reproject)) != cudaSuccess) e = r;
+  return e;
+}
+}  // namespace star
+
+namespace star {
+cudaError_t preload_raster();
+cudaError_t preload_passes();
+cudaError_t preload_mlp_tc();
+cudaError_t preload_resolve_tc();
+cudaError_t preload_quadtree();
+cudaError_t preload_train();
+}  // namespace star
+
+extern "C" star_nt_status star_nt_preload(void) {
+  cudaError_t e = cudaSuccess, r;
+  if ((r = preload_raster()) != cudaSuccess) e = r;
+  if ((r = preload_passes()) != cudaSuccess) e = r;
+  if ((r = preload_frame()) != cudaSuccess) e = r;
+  if ((r = preload_mlp_tc()) != cudaSuccess) e = r;
+  if ((r = preload_resolve_tc()) != cudaSuccess) e = r;
+  if ((r = preload_quadtree()) != cudaSuccess) e = r;
+  if ((r = preload_train()) != cudaSuccess) e = r;
+  return e == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
+}

@@ -280,3 +280,13 @@ cudaError_t star_launch_mlp_bf16(const star_nt_mlp *w, const void *x, float *f, 
                                                               d_status);
   return cudaGetLastError();
 }
+
+namespace star {
+// Loads this file's kernels onto the current device (see star_nt_preload).
+cudaError_t preload_mlp_tc() {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaSuccess, r;
+  if ((r = cudaFuncGetAttributes(&a, k_mlp_bf16)) != cudaSuccess) e = r;
+  return e;
+}
+}  // namespace star

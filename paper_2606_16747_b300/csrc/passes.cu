@@ -413,3 +413,21 @@ extern "C" star_nt_status star_nt_build_inputs(const star_nt_scene *scene, const
   if ((s = star_nt_geometry_pass(scene, b3, 3, &c, d_status, stream)) != STAR_NT_OK) return s;
   return star_nt_upscale_features(scene, b2, b3, l1, l2, l3, W, H, params, out, stream);
 }
+
+namespace star {
+// Loads this file's kernels onto the current device (see star_nt_preload).
+cudaError_t preload_passes() {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaSuccess, r;
+  if ((r = cudaFuncGetAttributes(&a, k_pass<kTop1>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_pass<kTop2>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_pass<kTail>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_pass<kFused>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_pass_merged)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_passes<4>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_passes<8>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_passes<16>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_features)) != cudaSuccess) e = r;
+  return e;
+}
+}  // namespace star

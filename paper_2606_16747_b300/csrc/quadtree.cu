@@ -420,3 +420,16 @@ extern "C" star_nt_status star_nt_quadtree_static(const uint32_t *rgba8, const i
   return star_nt_quadtree(rgba8, id1, W, H, params, mask_prev, mask_out, state, ws, kQtStaticBytes,
                           stream);
 }
+
+namespace star {
+// Loads this file's kernels onto the current device (see star_nt_preload).
+cudaError_t preload_quadtree() {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaSuccess, r;
+  if ((r = cudaFuncGetAttributes(&a, k_qt_decide)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_qt_relax)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_qt_last<true>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_qt_last<false>)) != cudaSuccess) e = r;
+  return e;
+}
+}  // namespace star

@@ -96,7 +96,9 @@ __device__ __forceinline__ void triangle_setup_x4(int t, bool store, const float
   float zn[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    ok = ok && __shfl_sync(full, (int)okq, k, 4);
+    // every lane takes part in every shuffle (no short-circuit around them)
+    const int okk = __shfl_sync(full, (int)okq, k, 4);
+    ok = ok && okk != 0;
     X[k] = __shfl_sync(full, Xq, k, 4);
     Y[k] = __shfl_sync(full, Yq, k, 4);
     zn[k] = __shfl_sync(full, znq, k, 4);
@@ -622,3 +624,20 @@ extern "C" star_nt_status star_nt_raster(const star_nt_scene *scene, const star_
                                      frags->prim, d_status);
   return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
 }
+
+namespace star {
+// Loads this file's kernels onto the current device (see star_nt_preload).
+cudaError_t preload_raster() {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaSuccess, r;
+  if ((r = cudaFuncGetAttributes(&a, k_bin_count)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_bin_fill)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_scan_tiles)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_scan_reduce)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_scan_blocks)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_scan_final)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_frag_count)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_frag_fill)) != cudaSuccess) e = r;
+  return e;
+}
+}  // namespace star

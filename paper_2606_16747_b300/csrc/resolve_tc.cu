@@ -545,3 +545,14 @@ extern "C" star_nt_status star_nt_resolve_fp8(const star_nt_scene *scene, const 
   return launch_resolve(true, scene, b2, b3, l1, l2, l3, W, H, params, w, rgba32f, rgba8, d_status,
                         stream);
 }
+
+namespace star {
+// Loads this file's kernels onto the current device (see star_nt_preload).
+cudaError_t preload_resolve_tc() {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaSuccess, r;
+  if ((r = cudaFuncGetAttributes(&a, k_resolve)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_resolve_fp8)) != cudaSuccess) e = r;
+  return e;
+}
+}  // namespace star

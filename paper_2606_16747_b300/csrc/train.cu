@@ -340,3 +340,19 @@ extern "C" star_nt_status star_nt_adam(float *params, const float *grad, float *
       params, grad, m, v, n, lr, beta1, beta2, eps, c1, c2, bf16_rounded);
   return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
 }
+
+namespace star {
+// Loads this file's kernels onto the current device (see star_nt_preload).
+cudaError_t preload_train() {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaSuccess, r;
+  if ((r = cudaFuncGetAttributes(&a, k_abuffer)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_mse)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_sum_partials)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_mlp_bwd_rows)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_mlp_bwd_partial)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_mlp_bwd_reduce)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_adam)) != cudaSuccess) e = r;
+  return e;
+}
+}  // namespace star

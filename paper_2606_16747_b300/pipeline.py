@@ -31,6 +31,7 @@ class Renderer:
                  pair_capacity=None, device="cuda", base_tile=None, fused=False,
                  persistent=False, tuning=None, merge_scale2=1.0, merge_scale3=1.0):
         self.device = device
+        sn.preload(torch.device(device).index)
         self.W, self.H = int(W), int(H)
         self.P = self.W * self.H
         self.verts = torch.as_tensor(np.ascontiguousarray(verts, np.float32)).to(device)
@@ -240,3 +241,99 @@ class Renderer:
         s = int(self.status.item())
         if s != sn.OK:
             raise sn.StarNTError("device", s)
+
+
+class AdaptiveInterval:
+    """Interpolation interval of Sec. 3.3 (last paragraph): the number n of
+    interpolated frames after each real frame, adapted to the measured frame
+    times and capped at four; below the target frame rate it falls back to
+    real frames only.
+
+    Reading: a real frame must still arrive at least at the target rate, so
+    one real frame and its n interpolated frames share the budget 1 / target:
+    n = floor((1/target - t_real) / t_interp), clamped to [0, max_interp],
+    with t_real and t_interp exponential moving averages of measured frame
+    times.  When t_real alone exceeds the budget, n = 0 (standard rendering)."""
+
+    def __init__(self, target_fps: float = 60.0, max_interp: int = 4, smoothing: float = 0.25):
+        if target_fps <= 0 or not 0 <= max_interp <= 4 or not 0 < smoothing <= 1:
+            raise ValueError("target_fps > 0, max_interp in [0, 4], smoothing in (0, 1]")
+        self.budget_ms = 1000.0 / target_fps
+        self.max_interp = max_interp
+        self.smoothing = smoothing
+        self.t_real = None
+        self.t_interp = None
+
+    def _ema(self, old, new):
+        return new if old is None else old + self.smoothing * (new - old)
+
+    def observe(self, real_ms=None, interp_ms=None):
+        if real_ms is not None:
+            self.t_real = self._ema(self.t_real, float(real_ms))
+        if interp_ms is not None:
+            self.t_interp = self._ema(self.t_interp, float(interp_ms))
+
+    def interval(self) -> int:
+        if self.t_real is None:
+            return 0
+        spare = self.budget_ms - self.t_real
+        if spare <= 0.0:
+            return 0
+        if self.t_interp is None or self.t_interp <= 0.0:
+            return 1 if self.max_interp > 0 else 0  # one interpolated frame to measure it
+        return int(min(self.max_interp, max(0, math.floor(spare / self.t_interp))))
+
+
+class Sequence:
+    """Renders a camera sequence with real and interpolated frames: each real
+    frame is followed by n interpolated frames reprojected from it (n from an
+    AdaptiveInterval, or fixed), every frame timed with CUDA events.  Frame
+    times are read back one frame late (event queries, no synchronisation on
+    the frame path), so decisions use the previous measurements."""
+
+    def __init__(self, renderer: Renderer, controller: AdaptiveInterval = None, fixed_interval=None):
+        self.r = renderer
+        self.ctl = controller
+        self.fixed = fixed_interval
+        self.left = 0          # interpolated frames left before the next real frame
+        self.pending = []      # (kind, start event, end event) not yet read back
+        self.kinds = []        # "real" / "interp" per rendered frame
+        self.real_graph = renderer.capture(lambda: renderer.star_frame())
+        self.interp_graph = renderer.capture(renderer.interp_frame)
+
+    def _collect(self):
+        keep = []
+        for kind, e0, e1 in self.pending:
+            if e1.query():
+                ms = e0.elapsed_time(e1)
+                if self.ctl is not None:
+                    self.ctl.observe(real_ms=ms if kind == "real" else None,
+                                     interp_ms=ms if kind == "interp" else None)
+            else:
+                keep.append((kind, e0, e1))
+        self.pending = keep
+
+    def frame(self, vp32, vp64):
+        """Render the next frame for camera (vp32, vp64); returns "real" or
+        "interp".  The frame is in renderer.rgba32f / rgba8_out (real) or
+        renderer.interp_out / interp_rgba8 (interpolated)."""
+        self._collect()
+        r = self.r
+        kind = "interp" if self.left > 0 else "real"
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if kind == "real":
+            r.set_cameras(vp32=vp32, vp64_real=vp64)
+            e0.record()
+            self.real_graph.replay()
+            e1.record()
+            n = self.fixed if self.fixed is not None else (self.ctl.interval() if self.ctl else 0)
+            self.left = int(n)
+        else:
+            r.set_cameras(vp64_interp=vp64)
+            e0.record()
+            self.interp_graph.replay()
+            e1.record()
+            self.left -= 1
+        self.pending.append((kind, e0, e1))
+        self.kinds.append(kind)
+        return kind

@@ -26,7 +26,7 @@ EXPORTS = ("star_nt_version", "star_nt_status_string", "star_nt_default_params",
            "star_nt_reproject", "star_nt_geometry_pass", "star_nt_upscale_features",
            "star_nt_geometry_pass_merged", "star_nt_abuffer", "star_nt_train_ws_bytes",
            "star_nt_mse_grad", "star_nt_mlp_backward", "star_nt_adam", "star_nt_raster_passes",
-           "star_nt_resolve", "star_nt_geometry_passes", "star_nt_resolve_fp8")
+           "star_nt_resolve", "star_nt_geometry_passes", "star_nt_resolve_fp8", "star_nt_preload")
 
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
@@ -190,6 +190,20 @@ class BinsBuffer:
     def header(self):
         """size[2], tiles_x, tiles_y, n_tiles, n_pixels, n_pairs, n_tris (device int32 view)."""
         return self.mem[:32].view(torch.int32)
+
+
+_preloaded = set()
+
+
+def preload(device=None):
+    """Load every kernel onto the device (once per device), before any frame
+    is captured."""
+    d = torch.cuda.current_device() if device is None else int(device)
+    if d in _preloaded:
+        return
+    with torch.cuda.device(d):
+        _check("star_nt_preload", lib().star_nt_preload())
+    _preloaded.add(d)
 
 
 def scene_struct(verts, rgba8) -> Scene:

@@ -120,6 +120,26 @@ def test_raster_screen_scene(orc, sn):
     assert_frags_equal(orc, sn, sc.verts, sc.rgba8, sc.cam.vp32, 320, 200)
 
 
+@pytest.mark.parametrize("n_tris", [1500, 77])
+def test_raster_culled_triangles(orc, sn, n_tris):
+    """Set-up lanes of culled triangles, of visible ones and of the padding
+    past the last triangle share warps (n_tris not a multiple of the 32
+    triangles of a binning block): a camera that culls every triangle, one
+    that sees none of them (all behind it), and a camera that culls part of
+    the scene all match the oracle."""
+    W, H = 96, 64
+    sc = scenes.screen_scene(7, n_tris, W, H, size_scale=0.7)
+    frags, st, _, _ = gpu_raster(sn, sc.verts, sc.rgba8, np.zeros(16, np.float32), W, H)
+    assert st == 0 and int(u32(frags["total"])[0]) == 0
+    behind = np.asarray(sc.cam.vp32, np.float32).reshape(4, 4) * np.array([1, 1, 1, -1], np.float32)[:, None]
+    frags, st, _, _ = gpu_raster(sn, sc.verts, sc.rgba8, behind, W, H)
+    assert st == 0 and int(u32(frags["total"])[0]) == 0
+    # move every third triangle behind the camera: visible and culled triangles mix in a warp
+    v = sc.verts.copy()
+    v[::3, :, 2] = -v[::3, :, 2]
+    assert_frags_equal(orc, sn, v, sc.rgba8, sc.cam.vp32, W, H)
+
+
 def test_raster_empty_scene(orc, sn):
     W, H = 48, 40
     v = np.zeros((0, 3, 4), np.float32)
