@@ -252,6 +252,25 @@ def run_ours(args, rank, world):
             plain_ms.append(e0.elapsed_time(e1))
     plain.check_status()
 
+    # weighted blended OIT (the evaluation's baseline OIT method): raster + one pass
+    def wboit_frame():
+        sn.raster(plain.scene, plain.vp, plain.full_size, W, H, plain.bins[0], None, plain.status)
+        sn.wboit(plain.bins[0], scenes.NEAR, scenes.FAR, tuple(plain.params.bg), plain.rgba32f,
+                 plain.rgba8_out)
+    g_wb = plain.capture(wboit_frame)
+    wboit_ms = []
+    for k in range(args.warmup + args.steps):
+        flush.fill_(1)
+        plain.set_cameras(vp32[2 * k])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g_wb.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            wboit_ms.append(e0.elapsed_time(e1))
+    plain.check_status()
+
     # end to end through the public API: host inputs in, frames out, every step
     e2e = end_to_end(sn, torch, sc, w, x_dtype, W, H, cams, args, star.tuning)
 
@@ -308,6 +327,7 @@ def run_ours(args, rank, world):
         "eq2_sizes_ms_per_frame": round(eq2_ms, 5) if eq2_ms is not None else None,
         "eq2_sizes_note": "the same step with pass 2 always at the Eq. 2 size (merge scale 1.0)",
         "plain_ms_per_frame": round(float(np.mean(plain_ms)), 5),
+        "wboit_ms_per_frame": round(float(np.mean(wboit_ms)), 5),
         "speedup_vs_plain": round(float(np.mean(plain_ms)) / ms_frame, 4),
         "stages_ms": {k: round(v, 5) for k, v in stage_mean.items()},
         "pass_state": {k: state[k] for k in ("W2", "H2", "W3", "H3", "s2", "s3", "wbar", "hist")},
@@ -322,7 +342,12 @@ def run_ours(args, rank, world):
                      "peak_source": f"{N_SM} SM x {ALU_LANES_PER_SM} lanes x sm_max_mhz ({peaks_kind})",
                      "ops_per_fragment": OPS_PER_FRAGMENT, "launch_ms": round(dom_ms, 5)},
     }
-    line["psnr_db_vs_exact_abuffer"] = psnr
+    line["psnr_db_vs_exact_abuffer"] = psnr["psnr_db"]
+    line["quality"] = {"mse_vs_exact_abuffer": psnr["mse"],
+                       "error_reduction_vs_unsorted_pct": psnr["error_reduction_vs_unsorted_pct"],
+                       "note": "one real frame and the following interpolated frame after the timed "
+                               "steps; unsorted_over = naive blending in submission order (E_random "
+                               "of the Q measure); wboit = weighted blended OIT, one pass"}
     return line
 
 
@@ -381,8 +406,9 @@ def end_to_end(sn, torch, sc, w, x_dtype, W, H, cams, args, tuning=None):
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(out.numel() * 4 + out2.numel() * 4)}
 
 
-def exact_frame(sn, r, vp32, W, H):
-    """Exact A-buffer of the scene under camera vp32 (GPU, sorted fragments)."""
+def exact_frame(sn, r, vp32, W, H, keep_frags=False):
+    """Exact A-buffer of the scene under camera vp32 (GPU, sorted fragments);
+    with keep_frags also the fragment lists (bins of r hold the raster)."""
     import torch
     P = W * H
     r.set_cameras(vp32)
@@ -401,6 +427,8 @@ def exact_frame(sn, r, vp32, W, H):
     out = torch.empty(P * 4, device="cuda")
     sn.abuffer(frags, r.rgba8, W, H, tuple(r.params.bg), out, None)
     torch.cuda.synchronize()
+    if keep_frags:
+        return out.view(P, 4)[:, :3], frags
     return out.view(P, 4)[:, :3]
 
 
@@ -421,10 +449,26 @@ def quality(sn, star, plain, W, H, cams, k):
     plain.set_cameras(cams[2 * k].vp32)
     plain.plain_frame()
     pl = plain.rgba32f.view(-1, 4)[:, :3].clone()
-    ex_real = exact_frame(sn, plain, cams[2 * k].vp32, W, H)
+    ex_real, frags = exact_frame(sn, plain, cams[2 * k].vp32, W, H, keep_frags=True)
+    # comparison renderers of the evaluation: naive unsorted blending (E_random)
+    # and weighted blended OIT, on the same frame
+    from paper_2606_16747_b300 import scenes
+    bg = tuple(plain.params.bg)
+    un = torch.empty(W * H * 4, device="cuda")
+    sn.unsorted_over(frags, plain.rgba8, W, H, bg, un)
+    wb = torch.empty(W * H * 4, device="cuda")
+    sn.wboit(plain.bins[0], scenes.NEAR, scenes.FAR, bg, wb)
+    torch.cuda.synchronize()
+    un, wb = un.view(-1, 4)[:, :3], wb.view(-1, 4)[:, :3]
     ex_interp = exact_frame(sn, plain, cams[2 * k + 1].vp32, W, H)
-    return {"star_real": psnr_db(real, ex_real), "star_interpolated": psnr_db(interp, ex_interp),
-            "plain": psnr_db(pl, ex_real)}
+    frames = {"star_real": (real, ex_real), "star_interpolated": (interp, ex_interp),
+              "plain": (pl, ex_real), "wboit": (wb, ex_real), "unsorted_over": (un, ex_real)}
+    mse = {k: float(torch.mean((a - b) ** 2).item()) for k, (a, b) in frames.items()}
+    e_random = mse["unsorted_over"]
+    return {"psnr_db": {k: round(10.0 * math.log10(1.0 / max(v, 1e-30)), 3) for k, v in mse.items()},
+            "mse": {k: float(f"{v:.4e}") for k, v in mse.items()},
+            "error_reduction_vs_unsorted_pct": {k: round(100.0 * (e_random - v) / e_random, 2)
+                                                for k, v in mse.items() if k != "unsorted_over"}}
 
 
 # ---------------------------------------------------------------------------

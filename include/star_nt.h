@@ -394,6 +394,27 @@ star_nt_status star_nt_reproject(const float *prev_rgba, const float *prev_z1,
                                  void *stream);
 
 /* ------------------------------------------------------------------------ */
+/* Comparison renderers of the evaluation (Sec. 4); not on the STAR-NT path. */
+
+/* star_nt_unsorted_over -- a renderer without OIT: each pixel's materialised
+ * fragments (star_nt_raster) composited with "over" in submission order
+ * (increasing primitive id) over bg.  Its error against the A-buffer is the
+ * E_random of the paper's Q measure.  rgb: [P][4] (colour, transmittance),
+ * 16-byte aligned.  float32 arithmetic. */
+star_nt_status star_nt_unsorted_over(const star_nt_frags *frags, const uint32_t *rgba8, int32_t W,
+                                     int32_t H, const float *bg, float *rgb, void *stream);
+
+/* star_nt_wboit -- weighted blended OIT (McGuire and Bavoil 2013), the
+ * paper's baseline OIT method, in one pass over a full-resolution binned
+ * target (bins from star_nt_raster, no fragment lists):
+ * C = (sum (a c) w / max(sum a w, 1e-5)) (1 - T) + T C_b, T = prod (1 - a),
+ * w = a clamp(10 / (1e-5 + (d/5)^2 + (d/200)^6), 1e-2, 3e3), d the view
+ * depth recovered from NDC z with the projection's znear, zfar
+ * (0 < znear < zfar).  rgba32f [P][4] (colour, T) and/or rgba8 [P]. */
+star_nt_status star_nt_wboit(const star_nt_bins *bins, float znear, float zfar, const float *bg,
+                             float *rgba32f, uint32_t *rgba8, void *stream);
+
+/* ------------------------------------------------------------------------ */
 /* Exact resolve and training of the tail network.                          */
 
 /* star_nt_abuffer -- exact order-independent transparency, the ground truth

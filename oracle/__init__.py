@@ -14,6 +14,8 @@ code with the CUDA path.  Functions mirror the paper's steps:
   composite      Eq. 4
   quadtree       adaptive screen-space tiles (Sec. 3.1) and Eq. 2
   reproject      depth-based temporal reprojection (Sec. 3.3, last paragraph)
+  unsorted_over, wboit
+                 the evaluation's comparison renderers (Sec. 4)
 """
 from __future__ import annotations
 
@@ -67,6 +69,7 @@ def _declare(L):
     L.orc_resolve.argtypes = [_P, _P, _P, _P, _I32, _I32, _I32, _P] + [_P] * 12
     L.orc_resolve.restype = None
     L.orc_unsorted_over.argtypes = [_P, _P, _P, _I64, _P, _P]
+    L.orc_wboit.argtypes = [_P, _P, _P, _P, _I64, ctypes.c_double, ctypes.c_double, _P, _P]
     L.orc_upscale.argtypes = [_P, _I32, _I32, _I32, _I32, _I32, _P]
     L.orc_tail_flag.argtypes = [_P, _I32, _I32, _I32, _I32, _P]
     L.orc_features.argtypes = [_I64, _P, _P, _P, _P, _P, _P, _P, _P, _D, _P, _P]
@@ -165,6 +168,17 @@ def unsorted_over(fr: Frags, rgba8, bg=(1.0, 1.0, 1.0)):
     out = np.empty((P, 3), np.float64)
     L.orc_unsorted_over(_ptr(fr.offsets), _ptr(fr.prim), _ptr(_c(rgba8, np.uint32)), P,
                         _ptr(_c(bg, np.float64)), _ptr(out))
+    return out
+
+
+def wboit(fr: Frags, rgba8, znear, zfar, bg=(1.0, 1.0, 1.0)):
+    """Weighted blended OIT of each pixel's fragments (the evaluation's
+    baseline OIT method), float64; the fragment depths are the raster's."""
+    L = lib()
+    P = fr.W * fr.H
+    out = np.empty((P, 3), np.float64)
+    L.orc_wboit(_ptr(fr.offsets), _ptr(_c(fr.z, np.float32)), _ptr(fr.prim), _ptr(_c(rgba8, np.uint32)),
+                P, float(znear), float(zfar), _ptr(_c(bg, np.float64)), _ptr(out))
     return out
 
 

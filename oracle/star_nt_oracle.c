@@ -299,6 +299,41 @@ void orc_unsorted_over(const int64_t *offsets, const int32_t *prim, const uint32
 }
 
 /* ------------------------------------------------------------------------ */
+/* Weighted blended OIT (McGuire and Bavoil 2013), the baseline OIT method of */
+/* the evaluation (Sec. 4), with the authors' recommended depth weight:      */
+/* w(d, a) = a clamp(10 / (1e-5 + (d/5)^2 + (d/200)^6), 1e-2, 3e3), d the     */
+/* view depth.  C = (sum (a c) w / max(sum a w, 1e-5)) (1 - T) + T C_b with   */
+/* T = prod (1 - a).  NDC depth z in [0, 1] maps back to the view depth       */
+/* d = n f / (f - z (f - n)).                                                */
+
+static double wboit_weight(double d, double a)
+{
+    double w = 10.0 / (1e-5 + pow(d / 5.0, 2.0) + pow(d / 200.0, 6.0));
+    if (w < 1e-2) w = 1e-2;
+    if (w > 3e3) w = 3e3;
+    return a * w;
+}
+
+void orc_wboit(const int64_t *offsets, const float *z, const int32_t *prim, const uint32_t *rgba8,
+               int64_t P, double znear, double zfar, const double *bg, double *out)
+{
+    for (int64_t p = 0; p < P; ++p) {
+        double num[3] = {0, 0, 0}, den = 0.0, T = 1.0;
+        for (int64_t i = offsets[p]; i < offsets[p + 1]; ++i) {
+            uint32_t c = rgba8[prim[i]];
+            double a = ch(c, 3);
+            double d = znear * zfar / (zfar - (double)z[i] * (zfar - znear));
+            double w = wboit_weight(d, a);
+            for (int k = 0; k < 3; ++k) num[k] += a * ch(c, k) * w;
+            den += a * w;
+            T *= 1.0 - a;
+        }
+        double inv = 1.0 / (den > 1e-5 ? den : 1e-5);
+        for (int k = 0; k < 3; ++k) out[3 * p + k] = num[k] * inv * (1.0 - T) + T * bg[k];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Bilinear upscale of a reduced-resolution pass to the framebuffer          */
 /* (Sec. 3.2, last paragraph).  Half-pixel centres, clamp to edge: the       */
 /* source coordinate of output pixel x is u = (x + 0.5) Wp / W - 0.5, i.e.    */

@@ -338,6 +338,7 @@ cudaError_t preload_mlp_tc();
 cudaError_t preload_resolve_tc();
 cudaError_t preload_quadtree();
 cudaError_t preload_train();
+cudaError_t preload_baselines();
 }  // namespace star
 
 extern "C" star_nt_status star_nt_preload(void) {
@@ -349,5 +350,6 @@ extern "C" star_nt_status star_nt_preload(void) {
   if ((r = preload_resolve_tc()) != cudaSuccess) e = r;
   if ((r = preload_quadtree()) != cudaSuccess) e = r;
   if ((r = preload_train()) != cudaSuccess) e = r;
+  if ((r = preload_baselines()) != cudaSuccess) e = r;
   return e == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
 }

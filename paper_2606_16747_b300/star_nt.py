@@ -26,7 +26,8 @@ EXPORTS = ("star_nt_version", "star_nt_status_string", "star_nt_default_params",
            "star_nt_reproject", "star_nt_geometry_pass", "star_nt_upscale_features",
            "star_nt_geometry_pass_merged", "star_nt_abuffer", "star_nt_train_ws_bytes",
            "star_nt_mse_grad", "star_nt_mlp_backward", "star_nt_adam", "star_nt_raster_passes",
-           "star_nt_resolve", "star_nt_geometry_passes", "star_nt_resolve_fp8", "star_nt_preload")
+           "star_nt_resolve", "star_nt_geometry_passes", "star_nt_resolve_fp8", "star_nt_preload",
+           "star_nt_unsorted_over", "star_nt_wboit")
 
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
@@ -132,6 +133,8 @@ def lib():
                                        ctypes.c_size_t, _P]
         L.star_nt_reproject.argtypes = [_P, _P, _P, _P, _I32, _I32, _P, _P, _P, _P]
         L.star_nt_abuffer.argtypes = [ctypes.POINTER(Frags), _P, _I32, _I32, _P, _P, _P, _P]
+        L.star_nt_unsorted_over.argtypes = [ctypes.POINTER(Frags), _P, _I32, _I32, _P, _P, _P]
+        L.star_nt_wboit.argtypes = [ctypes.POINTER(Bins), ctypes.c_float, ctypes.c_float, _P, _P, _P, _P]
         L.star_nt_train_ws_bytes.argtypes = [_I64]
         L.star_nt_train_ws_bytes.restype = ctypes.c_size_t
         L.star_nt_mse_grad.argtypes = [_P, _P, _I64, _P, _P, _P, ctypes.c_size_t, _P]
@@ -365,6 +368,19 @@ def abuffer(frags, rgba8, W, H, bg, rgb=None, tail=None, stream=None):
     bgt = (ctypes.c_float * 3)(*bg)
     _check("star_nt_abuffer", lib().star_nt_abuffer(ctypes.byref(f), _ptr(rgba8), W, H, bgt, _ptr(rgb),
                                                     _ptr(tail), _stream(stream)))
+
+
+def unsorted_over(frags, rgba8, W, H, bg, rgb, stream=None):
+    f = frags_struct(frags)
+    bgt = (ctypes.c_float * 3)(*bg)
+    _check("star_nt_unsorted_over", lib().star_nt_unsorted_over(ctypes.byref(f), _ptr(rgba8), W, H, bgt,
+                                                                _ptr(rgb), _stream(stream)))
+
+
+def wboit(bins, znear, zfar, bg, rgba32f=None, rgba8=None, stream=None):
+    bgt = (ctypes.c_float * 3)(*bg)
+    _check("star_nt_wboit", lib().star_nt_wboit(ctypes.byref(bins.c), float(znear), float(zfar), bgt,
+                                                _ptr(rgba32f), _ptr(rgba8), _stream(stream)))
 
 
 def train_ws_bytes(B):

@@ -646,3 +646,39 @@ def test_fused_resolve_fp8(orc, sn, weights):
     if no_tail.any():
         e0 = np.abs(r.rgba32f.cpu().numpy().reshape(-1, 4)[:, :3] - o["rgb"])[no_tail]
         assert e0.max() <= 1e-5
+
+
+# ---------------------------------------------------------------------------
+# Comparison renderers of the evaluation (Sec. 4)
+
+def test_unsorted_over_matches_oracle(orc, sn):
+    sc = scenes.screen_scene(12, 800, 160, 96, size_scale=0.7)
+    W, H = sc.width, sc.height
+    frags, st, _, _ = gpu_raster(sn, sc.verts, sc.rgba8, sc.cam.vp32, W, H)
+    assert st == 0
+    out = torch.empty(W * H * 4, device="cuda")
+    c = dev(sc.rgba8.astype(np.uint32).view(np.int32))
+    bg = (0.2, 0.5, 1.0)
+    sn.unsorted_over(frags, c, W, H, bg, out)
+    torch.cuda.synchronize()
+    fr = orc.raster(sc.verts, sc.cam.vp32, W, H, threads=4)
+    ref = orc.unsorted_over(fr, sc.rgba8, bg)
+    got = out.cpu().numpy().reshape(-1, 4)[:, :3]
+    assert np.max(np.abs(got - ref)) <= TOL_FRAME
+
+
+def test_wboit_matches_oracle(orc, sn):
+    sc = scenes.screen_scene(13, 800, 160, 96, size_scale=0.7)
+    W, H = sc.width, sc.height
+    _, st, bins, keep = gpu_raster(sn, sc.verts, sc.rgba8, sc.cam.vp32, W, H)
+    assert st == 0
+    out = torch.empty(W * H * 4, device="cuda")
+    out8 = torch.empty(W * H, dtype=torch.int32, device="cuda")
+    bg = (0.2, 0.5, 1.0)
+    sn.wboit(bins, scenes.NEAR, scenes.FAR, bg, out, out8)
+    torch.cuda.synchronize()
+    fr = orc.raster(sc.verts, sc.cam.vp32, W, H, threads=4)
+    ref = orc.wboit(fr, sc.rgba8, scenes.NEAR, scenes.FAR, bg)
+    got = out.cpu().numpy().reshape(-1, 4)[:, :3]
+    # float32 sums of weights up to 3e3 in any order against float64
+    assert np.max(np.abs(got - ref)) <= 1e-4
