@@ -441,6 +441,12 @@ star_nt_status star_nt_abuffer(const star_nt_frags *frags, const uint32_t *rgba8
 size_t star_nt_train_ws_bytes(int64_t B);
 star_nt_status star_nt_mse_grad(const float *f, const float *y, int64_t B, float *dy, float *loss,
                                 void *ws, size_t ws_bytes, void *stream);
+/* star_nt_wmse_grad: star_nt_mse_grad with a weight per sample, w [B] float32:
+ *   L = sum_i w_i |f_i - y_i|^2 / (3B), dy_i = 2 w_i (f_i - y_i) / (3B).  With
+ *   w_i = T_2^2 of the pixel, L is the error of the composited frame (Eq. 4
+ *   adds T_2 f), so the network is fitted where its output is visible. */
+star_nt_status star_nt_wmse_grad(const float *f, const float *y, const float *w, int64_t B, float *dy,
+                                 float *loss, void *ws, size_t ws_bytes, void *stream);
 star_nt_status star_nt_mlp_backward(const star_nt_mlp *w, const float *x, const float *dy,
                                     int64_t B, float *grad, void *ws, size_t ws_bytes,
                                     void *stream);

@@ -83,18 +83,21 @@ __global__ void __launch_bounds__(128) k_abuffer(const uint32_t *__restrict__ co
 }
 
 // ---------------------------------------------------------------------------
-// MSE over B samples x 3 channels: dL/df = 2 (f - y) / (3B) and the loss.
+// MSE over B samples x 3 channels, optionally weighted per sample (w NULL:
+// all 1): L = sum_i w_i |f_i - y_i|^2 / (3B), dL/df_i = 2 w_i (f_i - y_i) / (3B).
 __global__ void __launch_bounds__(256) k_mse(const float4 *__restrict__ f, const float4 *__restrict__ y,
-                                             long long B, float4 *__restrict__ dy,
-                                             float *__restrict__ partial) {
+                                             const float *__restrict__ w, long long B,
+                                             float4 *__restrict__ dy, float *__restrict__ partial) {
   __shared__ float s[8];
   const float scale = 1.0f / (3.0f * (float)B);
   float acc = 0.0f;
   for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < B; i += (long long)gridDim.x * 256) {
     const float4 a = f[i], t = y[i];
+    const float wi = w ? w[i] : 1.0f;
     const float dx = a.x - t.x, dyv = a.y - t.y, dz = a.z - t.z;
-    acc += dx * dx + dyv * dyv + dz * dz;
-    dy[i] = make_float4(2.0f * dx * scale, 2.0f * dyv * scale, 2.0f * dz * scale, 0.0f);
+    acc += wi * (dx * dx + dyv * dyv + dz * dz);
+    const float k = 2.0f * wi * scale;
+    dy[i] = make_float4(k * dx, k * dyv, k * dz, 0.0f);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
@@ -296,8 +299,8 @@ extern "C" size_t star_nt_train_ws_bytes(int64_t B) {
   return align_up(rows, 256) + align_up(chunks * 771 * 4, 256) + align_up(4 * 1024, 256);
 }
 
-extern "C" star_nt_status star_nt_mse_grad(const float *f, const float *y, int64_t B, float *dy,
-                                           float *loss, void *ws, size_t ws_bytes, void *stream) {
+static star_nt_status mse_grad(const float *f, const float *y, const float *w, int64_t B, float *dy,
+                               float *loss, void *ws, size_t ws_bytes, void *stream) {
   if (B <= 0 || !f || !y || !dy || !loss || !ws || ws_bytes < star_nt_train_ws_bytes(B))
     return STAR_NT_ERR_ARG;
   if (((uintptr_t)f & 15u) || ((uintptr_t)y & 15u) || ((uintptr_t)dy & 15u) || ((uintptr_t)ws & 255u))
@@ -305,10 +308,22 @@ extern "C" star_nt_status star_nt_mse_grad(const float *f, const float *y, int64
   cudaStream_t st = (cudaStream_t)stream;
   float *partial = reinterpret_cast<float *>((char *)ws + star_nt_train_ws_bytes(B) - 4 * 1024);
   const int g = mse_blocks(B);
-  k_mse<<<g, 256, 0, st>>>(reinterpret_cast<const float4 *>(f), reinterpret_cast<const float4 *>(y), B,
-                           reinterpret_cast<float4 *>(dy), partial);
+  k_mse<<<g, 256, 0, st>>>(reinterpret_cast<const float4 *>(f), reinterpret_cast<const float4 *>(y), w,
+                           B, reinterpret_cast<float4 *>(dy), partial);
   k_sum_partials<<<1, 32, 0, st>>>(partial, g, loss);
   return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
+}
+
+extern "C" star_nt_status star_nt_mse_grad(const float *f, const float *y, int64_t B, float *dy,
+                                           float *loss, void *ws, size_t ws_bytes, void *stream) {
+  return mse_grad(f, y, nullptr, B, dy, loss, ws, ws_bytes, stream);
+}
+
+extern "C" star_nt_status star_nt_wmse_grad(const float *f, const float *y, const float *w, int64_t B,
+                                            float *dy, float *loss, void *ws, size_t ws_bytes,
+                                            void *stream) {
+  if (!w) return STAR_NT_ERR_ARG;
+  return mse_grad(f, y, w, B, dy, loss, ws, ws_bytes, stream);
 }
 
 extern "C" star_nt_status star_nt_mlp_backward(const star_nt_mlp *w, const float *x, const float *dy,

@@ -27,7 +27,7 @@ EXPORTS = ("star_nt_version", "star_nt_status_string", "star_nt_default_params",
            "star_nt_geometry_pass_merged", "star_nt_abuffer", "star_nt_train_ws_bytes",
            "star_nt_mse_grad", "star_nt_mlp_backward", "star_nt_adam", "star_nt_raster_passes",
            "star_nt_resolve", "star_nt_geometry_passes", "star_nt_resolve_fp8", "star_nt_preload",
-           "star_nt_unsorted_over", "star_nt_wboit")
+           "star_nt_unsorted_over", "star_nt_wboit", "star_nt_wmse_grad")
 
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
@@ -138,6 +138,7 @@ def lib():
         L.star_nt_train_ws_bytes.argtypes = [_I64]
         L.star_nt_train_ws_bytes.restype = ctypes.c_size_t
         L.star_nt_mse_grad.argtypes = [_P, _P, _I64, _P, _P, _P, ctypes.c_size_t, _P]
+        L.star_nt_wmse_grad.argtypes = [_P, _P, _P, _I64, _P, _P, _P, ctypes.c_size_t, _P]
         L.star_nt_mlp_backward.argtypes = [ctypes.POINTER(Mlp), _P, _P, _I64, _P, _P, ctypes.c_size_t, _P]
         L.star_nt_adam.argtypes = [_P, _P, _P, _P, _I64, _I64, ctypes.c_float, ctypes.c_float,
                                    ctypes.c_float, ctypes.c_float, _P, _P]
@@ -387,9 +388,14 @@ def train_ws_bytes(B):
     return int(lib().star_nt_train_ws_bytes(int(B)))
 
 
-def mse_grad(f, y, B, dy, loss, ws, stream=None):
-    _check("star_nt_mse_grad", lib().star_nt_mse_grad(_ptr(f), _ptr(y), int(B), _ptr(dy), _ptr(loss),
-                                                      _ptr(ws), ws.numel(), _stream(stream)))
+def mse_grad(f, y, B, dy, loss, ws, stream=None, w=None):
+    if w is None:
+        _check("star_nt_mse_grad", lib().star_nt_mse_grad(_ptr(f), _ptr(y), int(B), _ptr(dy), _ptr(loss),
+                                                          _ptr(ws), ws.numel(), _stream(stream)))
+    else:
+        _check("star_nt_wmse_grad", lib().star_nt_wmse_grad(_ptr(f), _ptr(y), _ptr(w), int(B), _ptr(dy),
+                                                            _ptr(loss), _ptr(ws), ws.numel(),
+                                                            _stream(stream)))
 
 
 def mlp_backward(w: Mlp, x, dy, B, grad, ws, stream=None):

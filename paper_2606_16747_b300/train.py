@@ -81,21 +81,22 @@ class TailMLPFunction(torch.autograd.Function):
 
 class MSEFunction(torch.autograd.Function):
     """Mean squared error over B samples x 3 channels with the library's
-    kernel; its backward is the kernel's dL/df."""
+    kernel, optionally weighted per sample (w [B]); its backward is the
+    kernel's dL/df."""
 
     @staticmethod
-    def forward(ctx, f, y):
+    def forward(ctx, f, y, w=None):
         B = f.numel() // 4
         dy = torch.empty_like(f)
         loss = torch.empty(1, dtype=torch.float32, device=f.device)
-        sn.mse_grad(f, y, B, dy, loss, _WS.get(B, f.device))
+        sn.mse_grad(f, y, B, dy, loss, _WS.get(B, f.device), w=w)
         ctx.save_for_backward(dy)
         return loss
 
     @staticmethod
     def backward(ctx, grad_loss):
         (dy,) = ctx.saved_tensors
-        return dy * grad_loss, None
+        return dy * grad_loss, None, None
 
 
 # ---------------------------------------------------------------------------
@@ -133,17 +134,22 @@ def render_samples(scene: scenes.Scene, device="cuda"):
                 abuf=abuf.view(P, 4), fragments=F)
 
 
-def build_dataset(seeds, width=512, height=512, device="cuda", log=print):
-    xs, ys, n_frag = [], [], 0
+def build_dataset(seeds, width=512, height=512, device="cuda", log=print, with_t2=False):
+    """Network inputs and exact tail colours of the pixels with a tail; with
+    with_t2 also each pixel's T_2 (the factor of f in Eq. 4)."""
+    xs, ys, ts, n_frag = [], [], [], 0
     t0 = time.time()
     for i, seed in enumerate(seeds):
         d = render_samples(scenes.training_scene(seed, width, height), device)
         keep = d["x"][:, 5] == 1.0                   # pixels with a tail (N > 2)
         xs.append(d["x"][keep].contiguous())
         ys.append(d["tail"][keep].contiguous())
+        ts.append(d["front"][keep, 3].contiguous())
         n_frag += d["fragments"]
         if log and (i + 1) % 50 == 0:
             log(f"  scene {i + 1}/{len(seeds)}: {sum(x.shape[0] for x in xs)} samples, {time.time() - t0:.1f} s")
+    if with_t2:
+        return torch.cat(xs), torch.cat(ys), n_frag, torch.cat(ts)
     return torch.cat(xs), torch.cat(ys), n_frag
 
 
@@ -162,9 +168,9 @@ def initial_weights(seed=0):
     return w
 
 
-def train(x, y, steps=3000, batch=65536, lr=3e-3, seed=0, init=None, log=print, every=500):
+def train(x, y, steps=3000, batch=65536, lr=3e-3, seed=0, init=None, log=print, every=500, w=None):
     """Adam on float32 master weights (cosine-decayed learning rate); the
-    forward uses the bf16-rounded copy."""
+    forward uses the bf16-rounded copy.  w [N]: per-sample loss weights."""
     device = x.device
     g = torch.Generator(device="cpu").manual_seed(seed)
     flat0 = scenes.mlp_flat(init if init is not None else initial_weights(seed))
@@ -181,7 +187,7 @@ def train(x, y, steps=3000, batch=65536, lr=3e-3, seed=0, init=None, log=print, 
         yb = y[idx].reshape(-1)
         p = rounded.clone().requires_grad_(True)
         f = TailMLPFunction.apply(xb, p)
-        loss = MSEFunction.apply(f, yb)
+        loss = MSEFunction.apply(f, yb, w[idx].contiguous() if w is not None else None)
         loss.backward()
         lr_t = lr * 0.5 * (1.0 + math.cos(math.pi * (step - 1) / steps))
         sn.adam(master, p.grad, m, v, step, lr=lr_t, bf16_rounded=rounded)
@@ -253,18 +259,22 @@ def main():
     ap.add_argument("--lr", type=float, default=3e-3)
     ap.add_argument("--out", default=os.path.join(os.path.dirname(__file__), "weights"))
     ap.add_argument("--report", default=None)
+    ap.add_argument("--loss", default="frame", choices=["frame", "tail"],
+                    help="frame: squared error of the composited frame (weights T_2^2); "
+                         "tail: squared error of the tail colour")
     args = ap.parse_args()
     torch.cuda.set_device(0)
     t0 = time.time()
-    x, y, nf = build_dataset(range(args.first_seed, args.first_seed + args.scenes))
+    x, y, nf, t2 = build_dataset(range(args.first_seed, args.first_seed + args.scenes), with_t2=True)
     print(f"dataset: {x.shape[0]} samples from {args.scenes} scenes ({nf} fragments), {time.time() - t0:.1f} s")
-    state = train(x, y, steps=args.steps, batch=args.batch, lr=args.lr)
+    state = train(x, y, steps=args.steps, batch=args.batch, lr=args.lr,
+                  w=(t2 * t2).contiguous() if args.loss == "frame" else None)
     save_checkpoint(state, args.out)
     heldout = range(args.heldout_seed, args.heldout_seed + args.heldout)
     ev = evaluate(flat_to_dict(state["master"]), heldout)
     ev_init = evaluate(scenes.mlp_xavier(2), heldout)
     report = {"samples": int(x.shape[0]), "scenes": args.scenes, "steps": args.steps, "batch": args.batch,
-              "lr": args.lr, "loss_history": state["history"], "heldout_psnr_db": ev,
+              "lr": args.lr, "loss": args.loss, "loss_history": state["history"], "heldout_psnr_db": ev,
               "heldout_psnr_db_untrained_xavier": ev_init, "seconds": round(time.time() - t0, 1)}
     print(json.dumps(report))
     if args.report:

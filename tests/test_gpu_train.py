@@ -126,3 +126,28 @@ def test_short_training_beats_no_network(sn):
     assert ev["mlp_f32"] > ev["zero"] + 10.0          # what the network adds to Eq. 4
     assert ev["mlp_f32"] > ev["heuristic"] - 3.0       # close to the plain tail estimate after a short run
     assert abs(ev["mlp_bf16"] - ev["mlp_f32"]) < 0.5
+
+
+def test_weighted_mse_kernel(sn):
+    """star_nt_wmse_grad: w = 1 reproduces star_nt_mse_grad bit for bit, and
+    general weights give the definition's loss and gradient."""
+    from paper_2606_16747_b300.train import _WS
+    rng = np.random.default_rng(11)
+    B = 5000
+    f = torch.tensor(rng.uniform(-1, 2, size=(B, 4)).astype(np.float32), device="cuda")
+    y = torch.tensor(rng.uniform(0, 1, size=(B, 4)).astype(np.float32), device="cuda")
+    w = torch.tensor(rng.uniform(0, 1, size=B).astype(np.float32), device="cuda")
+    ws = _WS.get(B, "cuda")
+    dy0, l0 = torch.empty_like(f), torch.empty(1, device="cuda")
+    dy1, l1 = torch.empty_like(f), torch.empty(1, device="cuda")
+    sn.mse_grad(f, y, B, dy0, l0, ws)
+    sn.mse_grad(f, y, B, dy1, l1, ws, w=torch.ones(B, device="cuda"))
+    torch.cuda.synchronize()
+    assert torch.equal(dy0, dy1) and torch.equal(l0, l1)
+    sn.mse_grad(f, y, B, dy1, l1, ws, w=w)
+    torch.cuda.synchronize()
+    fd, yd, wd = (t.cpu().numpy().astype(np.float64) for t in (f, y, w))
+    e = fd[:, :3] - yd[:, :3]
+    assert abs(float(l1.item()) - (wd[:, None] * e * e).sum() / (3 * B)) <= 1e-5 * (1 + abs(float(l1.item())))
+    assert np.allclose(dy1.cpu().numpy()[:, :3], 2 * wd[:, None] * e / (3 * B), rtol=1e-5, atol=1e-9)
+    assert np.all(dy1.cpu().numpy()[:, 3] == 0)
