@@ -128,7 +128,10 @@ star_nt_status star_nt_preload(void);
 /* screen space with fixed float32 operations.                               */
 
 /* Workspace of binned triangles for one pass: caller allocates
- * star_nt_bins_bytes(...) bytes of device memory (256-byte aligned). */
+ * star_nt_bins_bytes(...) bytes of device memory (256-byte aligned) and
+ * zero-fills it once before its first use.  Every call leaves the per-tile
+ * counters and the work counters in it at zero again, so no call has to clear
+ * them (one fewer graph node per pass). */
 typedef struct {
     void *mem;
     size_t bytes;
@@ -343,9 +346,10 @@ typedef struct {
 star_nt_status star_nt_quadtree_ws_bytes(int32_t W, int32_t H, int32_t base_tile,
                                          size_t *bytes);
 
-/* rgba8, id1: [W*H]; mask_prev, mask_out: [ceil(W/B) * ceil(H/B)] (distinct
- * buffers); state: device star_nt_pass_state, fully rewritten; ws: workspace
- * of star_nt_quadtree_ws_bytes bytes. */
+/* rgba8, id1: [W*H]; mask_prev, mask_out: [ceil(W/B) * ceil(H/B)] (may be
+ * the same buffer: the masks are updated in place); state: device
+ * star_nt_pass_state, fully rewritten; ws: workspace of
+ * star_nt_quadtree_ws_bytes bytes. */
 star_nt_status star_nt_quadtree(const uint32_t *rgba8, const int32_t *id1, int32_t W, int32_t H,
                                 const star_nt_params *params, const uint32_t *mask_prev,
                                 uint32_t *mask_out, star_nt_pass_state *state, void *ws,

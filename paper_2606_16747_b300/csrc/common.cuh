@@ -46,8 +46,9 @@ struct __align__(16) BinsHeader {
   uint32_t n_pairs;    // (triangle, tile) pairs needed
   int32_t n_tris;
   int32_t merged;      // 1: the pass runs at full size and is taken over by pass 1
-  uint32_t queue;      // work counter of the persistent pass launch
-  uint32_t pad[6];
+  uint32_t queue;      // work counter of the persistent pass launch (zero between launches)
+  uint32_t queue_exit; // CTAs done with the launch (zero between launches)
+  uint32_t pad[5];
 };
 static_assert(sizeof(BinsHeader) == 64, "BinsHeader layout");
 

@@ -199,7 +199,14 @@ __global__ void __launch_bounds__(256, 6) k_passes(BinsView v1, BinsView v2, Bin
     __syncthreads();
     const int item = s_item;
     __syncthreads();  // every thread has the item before s_item is reused
-    if (item >= total) break;
+    if (item >= total) {
+      // the last CTA out resets the queue and the exit count for the next launch
+      if (threadIdx.x == 0 && atomicAdd(queue + 1, 1u) == gridDim.x - 1) {
+        queue[0] = 0u;
+        queue[1] = 0u;
+      }
+      break;
+    }
     if (item < n1) {
       if (m3) pass_body<kTail, BW>(v1, rgba8, om, FeatOut{}, stage, item);
       else if (m2) pass_body<kTop2, BW>(v1, rgba8, om, FeatOut{}, stage, item);
@@ -343,8 +350,7 @@ extern "C" star_nt_status star_nt_geometry_passes(const star_nt_scene *scene,
   BinsView v1 = bins_view(*b1), v2 = bins_view(*b2), v3 = bins_view(*b3);
   PassOut o1 = pass_out(l1), o2 = pass_out(l2), o3 = pass_out(l3);
   o1.id2 = nullptr; o1.n = nullptr; o1.tail = nullptr; o1.t_tail = nullptr;
-  uint32_t *queue = &v1.hd->queue;
-  cudaMemsetAsync(queue, 0, 4, st);
+  uint32_t *queue = &v1.hd->queue;  // queue[0] work counter, queue[1] exit count (pad[0])
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

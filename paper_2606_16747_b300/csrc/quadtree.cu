@@ -99,7 +99,10 @@ __device__ __forceinline__ double decision_dsum(const int (&q)[6], double split6
 __global__ void __launch_bounds__(256) k_qt_decide(const uint32_t *__restrict__ img, int W, int H,
                                                    int B, int tiles_x, int n_tiles, double split6,
                                                    double merge6, const uint32_t *__restrict__ mprev,
-                                                   uint32_t *__restrict__ mout) {
+                                                   uint32_t *__restrict__ mout,
+                                                   uint32_t *__restrict__ hist) {
+  // the histogram and the last-block ticket of k_qt_last start from zero
+  if (blockIdx.x == 0 && threadIdx.x < 8) hist[threadIdx.x] = 0u;
   const int tile = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (tile >= n_tiles) return;
@@ -330,8 +333,7 @@ extern "C" star_nt_status star_nt_quadtree(const uint32_t *rgba8, const int32_t 
                                            const uint32_t *mask_prev, uint32_t *mask_out,
                                            star_nt_pass_state *state, void *ws, size_t ws_bytes,
                                            void *stream) {
-  if (!rgba8 || !id1 || !params || !mask_prev || !mask_out || !state || !ws || mask_prev == mask_out)
-    return STAR_NT_ERR_ARG;
+  if (!rgba8 || !id1 || !params || !mask_prev || !mask_out || !state || !ws) return STAR_NT_ERR_ARG;
   const int B = params->base_tile;
   size_t need = 0;
   if (star_nt_quadtree_ws_bytes(W, H, B, &need) != STAR_NT_OK || ws_bytes < need ||
@@ -347,10 +349,10 @@ extern "C" star_nt_status star_nt_quadtree(const uint32_t *rgba8, const int32_t 
   const int nt = L.tiles_x * L.tiles_y;
   const int wblocks = (nt + 7) / 8;
   const int iters = params->relax_iters;
-  cudaMemsetAsync(hist, 0, 32, st);  // histogram and the last-block ticket
   uint32_t *ticket = hist + 4;
+  // mask_prev is read only here, so mask_out may be the same buffer
   k_qt_decide<<<wblocks, 256, 0, st>>>(rgba8, W, H, B, L.tiles_x, nt, 6.0 * params->tau_split,
-                                       6.0 * params->tau_merge, mask_prev, ma);
+                                       6.0 * params->tau_merge, mask_prev, ma, hist);
   const uint32_t *src = ma;
   const int tblocks = (nt + 255) / 256;
   for (int it = 0; it + 1 < iters; ++it) {  // all but the last relaxation

@@ -337,7 +337,8 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_fill(PassSet ps, int n_tris
 // r, so that every load and store of a warp is one coalesced 512-byte run.
 // The loads of up to four rounds are in flight together.  Writes the
 // offsets, the fill cursors (initialised to the offsets) and the total pair
-// count.
+// count, and zeroes the counts it consumed: the workspace leaves every call
+// with zero counts, ready for the next (no clearing launch).
 constexpr int kScanRounds = 4;
 
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *s_warp, uint32_t *total);
@@ -369,11 +370,13 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(PassSet ps) {
       if (i + 3 < n) {
         *reinterpret_cast<uint4 *>(bv.tile_offset + i) = o;
         *reinterpret_cast<uint4 *>(bv.tile_cursor + i) = o;
+        *reinterpret_cast<uint4 *>(bv.tile_count + i) = make_uint4(0u, 0u, 0u, 0u);
       } else if (i < n) {
         const uint32_t oo[4] = {o.x, o.y, o.z, o.w};
         for (int e = 0; e < n - i; ++e) {
           bv.tile_offset[i + e] = oo[e];
           bv.tile_cursor[i + e] = oo[e];
+          bv.tile_count[i + e] = 0u;  // consumed: zero again for the next call
         }
       }
       carry += tot;
@@ -594,8 +597,6 @@ extern "C" star_nt_status star_nt_raster_passes(const star_nt_scene *scene, int3
   }
   cudaStream_t st = (cudaStream_t)stream;
   const int T = scene->n_tris;
-  for (int i = 0; i < n_passes; ++i)
-    cudaMemsetAsync(ps.bv[i].tile_count, 0, 4 * (size_t)(ps.bv[i].max_tiles + 1), st);
   const dim3 grid(T > 0 ? (T + kBinTris - 1) / kBinTris : 1, n_passes);
   k_bin_count<<<grid, kBinThreads, 0, st>>>(scene->verts, scene->rgba8, T, ps, d_status);
   k_scan_tiles<<<n_passes, 1024, 0, st>>>(ps);

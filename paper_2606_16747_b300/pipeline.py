@@ -176,12 +176,10 @@ class Renderer:
             fn()
 
     def update_tiles(self, stream=None):
-        """Quadtree update from this frame; the new masks become the previous
-        ones by a device copy so that buffer addresses never change (one
-        captured graph serves every frame)."""
+        """Quadtree update from this frame, in place: the masks keep one
+        buffer, so one captured graph serves every frame."""
         sn.quadtree(self.rgba8_out, self.l1["id1"], self.W, self.H, self.params, self.mask[0],
-                    self.mask[1], self.state, self.qt_ws, stream)
-        self.mask[0].copy_(self.mask[1])
+                    self.mask[0], self.state, self.qt_ws, stream)
 
     def _infer_composite(self, stream):
         if self.mlp_tensors is None:

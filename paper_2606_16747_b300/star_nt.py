@@ -188,7 +188,7 @@ class BinsBuffer:
         n = ctypes.c_size_t()
         _check("star_nt_bins_bytes", lib().star_nt_bins_bytes(max_w, max_h, max_tris, pair_capacity,
                                                               ctypes.byref(n)))
-        self.mem = torch.empty(n.value, dtype=torch.uint8, device=device)
+        self.mem = torch.zeros(n.value, dtype=torch.uint8, device=device)  # zero before first use
         self.c = Bins(self.mem.data_ptr(), n.value, max_w, max_h, max_tris, pair_capacity)
 
     def header(self):

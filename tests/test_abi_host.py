@@ -77,6 +77,7 @@ def test_bad_arguments_rejected_before_launch(sn):
     assert L.star_nt_reproject(16, 16, 16, 16, 10, 10, 16, None, 48, None) == sn.ERR_ARG  # in place
     assert L.star_nt_reproject(16, 16, 16, 16, 10, 10, 32, None, None, None) == sn.ERR_ARG  # no scratch
     p = sn.default_params()
-    assert L.star_nt_quadtree(16, 16, 64, 64, ctypes.byref(p), 16, 16, 16, 256, 1 << 20, None) == sn.ERR_ARG
+    assert L.star_nt_quadtree(16, 16, 64, 64, ctypes.byref(p), 16, 16, 16, 256, 16, None) == sn.ERR_ARG  # small ws
+    assert L.star_nt_quadtree(16, 16, 64, 64, ctypes.byref(p), 16, 16, 16, 272, 1 << 20, None) == sn.ERR_ARG  # ws alignment
     p.tau_merge = p.tau_split + 1.0
     assert L.star_nt_quadtree(16, 16, 64, 64, ctypes.byref(p), 16, 32, 16, 256, 1 << 20, None) == sn.ERR_ARG

@@ -417,6 +417,50 @@ def test_quadtree_sequence_matches_oracle(orc, sn):
         assert np.array_equal(u32(mg[1 - k % 2]), mo)
 
 
+def test_quadtree_in_place(orc, sn):
+    """mask_out may be mask_prev: a sequence updated in place matches the
+    oracle frame by frame (the histogram is cleared inside the call)."""
+    rng = np.random.default_rng(9)
+    W, H, B = 200, 120, 16
+    params = sn.default_params()
+    ws = torch.zeros(sn.quadtree_ws_bytes(W, H, B), dtype=torch.uint8, device="cuda")
+    state = torch.zeros(64, dtype=torch.uint8, device="cuda")
+    m = torch.zeros(math.ceil(W / B) * math.ceil(H / B), dtype=torch.int32, device="cuda")
+    mo = np.zeros(m.numel(), np.uint32)
+    id1 = np.where(rng.random(W * H) < 0.8, 0, -1).astype(np.int32)
+    for k in range(4):
+        img = blocky_image(rng, W, H, 4)
+        sn.quadtree(dev(img.view(np.int32)), dev(id1), W, H, params, m, m, state, ws)
+        mo, ho = orc.quadtree(img, id1, W, H, B, params.tau_split, params.tau_merge, mo)
+        torch.cuda.synchronize()
+        assert np.array_equal(u32(m), mo)
+        assert sn.read_pass_state(state)["hist"] == ho.tolist()
+
+
+def test_workspaces_reused_across_calls(orc, sn):
+    """The binning counters and the persistent launch's work counters clear
+    themselves: one set of workspaces serves different scenes, cameras and
+    pass sizes in a row with the results of fresh workspaces."""
+    from paper_2606_16747_b300.pipeline import Renderer
+    sc = scenes.screen_scene(17, 2000, 176, 112, size_scale=0.7)
+    W, H = sc.width, sc.height
+    cams = scenes.orbit_cameras(W, H, 40)
+    sizes = [((W, H), (W, H)), ((131, 83), (61, 40)), ((99, 64), (W, H)), ((W, H), (88, 56))]
+    reused = Renderer(sc.verts, sc.rgba8, W, H, mlp=scenes.mlp_xavier(4), x_dtype=sn.BF16, fused=True,
+                      persistent=True)
+    for k, (s2, s3) in enumerate(sizes):
+        outs = []
+        for r in (reused, Renderer(sc.verts, sc.rgba8, W, H, mlp=scenes.mlp_xavier(4), x_dtype=sn.BF16,
+                                   fused=True, persistent=True)):
+            r.set_camera(cams[10 * k].vp32)
+            r.state.view(torch.int32)[:6] = torch.tensor([W, H, *s2, *s3], dtype=torch.int32)
+            r.star_frame(update_tiles=False)
+            torch.cuda.synchronize()
+            r.check_status()
+            outs.append((r.rgba32f.clone(), r.l1["id1"].clone()))
+        assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+
+
 # ---------------------------------------------------------------------------
 # star_nt_reproject
 
