@@ -240,8 +240,9 @@ star_nt_status star_nt_geometry_pass_merged(const star_nt_scene *scene, const st
 /* Tile shape and launch size of star_nt_geometry_passes (NULL: defaults).
  * block_w: width of the pixel block a warp owns inside a 16 x 16 tile
  *   (4, 8 or 16; the block is block_w x 32/block_w); default 8.
- * ctas_per_sm: resident CTAs per SM of the persistent launch (1..8, capped
- *   by occupancy; 0: as many as fit). */
+ * ctas_per_sm: 0 or 8: full occupancy with an 8-CTA-per-SM register budget
+ *   (32 per thread); 1..7: a 6-CTA budget (40 per thread) and the grid capped
+ *   at that many CTAs per SM.  Default 0. */
 typedef struct {
     int32_t block_w;
     int32_t ctas_per_sm;

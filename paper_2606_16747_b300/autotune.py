@@ -10,7 +10,7 @@ import os
 import torch
 
 TUNED_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
-CANDIDATES = [(8, 0), (16, 0), (4, 0), (8, 4), (16, 4), (8, 5)]
+CANDIDATES = [(8, 0), (16, 0), (4, 0), (8, 6), (16, 6), (4, 6)]
 
 
 def workload_key(renderer) -> str:

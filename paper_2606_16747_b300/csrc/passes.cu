@@ -175,8 +175,11 @@ __global__ void __launch_bounds__(256, 6) k_pass_merged(BinsView bv, const BinsH
 // then of pass 2, then of pass 3 - until the items run out, so tiles of uneven
 // cost and passes of different resolutions share one launch without a tail
 // between passes.  Pass 1 takes over merged passes as k_pass_merged does.
-template <int BW>
-__global__ void __launch_bounds__(256, 6) k_passes(BinsView v1, BinsView v2, BinsView v3,
+// MINB: CTAs per SM the register budget is cut for (6: 40 registers per
+// thread; 8: 32 registers, a few spilled, more warps to cover the barrier
+// waits of uneven pixel blocks).
+template <int BW, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_passes(BinsView v1, BinsView v2, BinsView v3,
                                                    const uint32_t *__restrict__ rgba8, PassOut o1,
                                                    PassOut o2, PassOut o3, uint32_t *queue) {
   __shared__ TileStage stage;
@@ -360,9 +363,12 @@ extern "C" star_nt_status star_nt_geometry_passes(const star_nt_scene *scene,
     const int k = per_sm > 0 ? (per_sm < occ ? per_sm : occ) : occ;
     kern<<<sms * (k > 0 ? k : 1), 256, 0, st>>>(v1, v2, v3, scene->rgba8, o1, o2, o3, queue);
   };
-  if (bw == 8) launch(k_passes<8>);
-  else if (bw == 16) launch(k_passes<16>);
-  else launch(k_passes<4>);
+  // ctas_per_sm 0 or 8: the 8-CTA register budget at full occupancy; 1..7: the
+  // 6-CTA budget, grid capped at that many CTAs per SM
+  const bool wide = per_sm == 0 || per_sm == 8;
+  if (bw == 8) wide ? launch(k_passes<8, 8>) : launch(k_passes<8, 6>);
+  else if (bw == 16) wide ? launch(k_passes<16, 8>) : launch(k_passes<16, 6>);
+  else wide ? launch(k_passes<4, 8>) : launch(k_passes<4, 6>);
   return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
 }
 
@@ -430,9 +436,12 @@ cudaError_t preload_passes() {
   if ((r = cudaFuncGetAttributes(&a, k_pass<kTail>)) != cudaSuccess) e = r;
   if ((r = cudaFuncGetAttributes(&a, k_pass<kFused>)) != cudaSuccess) e = r;
   if ((r = cudaFuncGetAttributes(&a, k_pass_merged)) != cudaSuccess) e = r;
-  if ((r = cudaFuncGetAttributes(&a, k_passes<4>)) != cudaSuccess) e = r;
-  if ((r = cudaFuncGetAttributes(&a, k_passes<8>)) != cudaSuccess) e = r;
-  if ((r = cudaFuncGetAttributes(&a, k_passes<16>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_passes<4, 6>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_passes<8, 6>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_passes<16, 6>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_passes<4, 8>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_passes<8, 8>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_passes<16, 8>)) != cudaSuccess) e = r;
   if ((r = cudaFuncGetAttributes(&a, k_features)) != cudaSuccess) e = r;
   return e;
 }
