@@ -136,6 +136,7 @@ def run_ours(args, rank, world):
     star = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=x_dtype, base_tile=args.base_tile,
                     fused=fused_kind, persistent=args.persistent,
                     merge_scale2=args.merge_scale2)
+    star.interp_float = False   # a display takes the 8-bit interpolated frame
     plain = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=sn.F32)
     n_frames = 2 * (20 + 2 * args.warmup + 2 * args.steps)
     cams = scenes.orbit_cameras(W, H, n_frames)
@@ -377,6 +378,7 @@ def end_to_end(sn, torch, sc, w, x_dtype, W, H, cams, args, tuning=None):
                  fused=(args.mlp if args.mlp == "fp8" else True) if args.fused and x_dtype == sn.BF16 else False,
                  persistent=args.persistent, tuning=tuning,
                  merge_scale2=args.merge_scale2)
+    r.interp_float = False      # both frames leave as 8-bit
     hv = torch.from_numpy(np.ascontiguousarray(sc.verts)).pin_memory()
     hc = torch.from_numpy(np.ascontiguousarray(sc.rgba8).view(np.int32)).pin_memory()
     hvp = [torch.from_numpy(np.ascontiguousarray(c.vp32)).pin_memory() for c in cams]
@@ -443,7 +445,10 @@ def quality(sn, star, plain, W, H, cams, k):
     frame 2k + 1, and the plain pipeline at frame 2k (after the timed runs)."""
     import torch
     star.set_cameras(cams[2 * k].vp32, cams[2 * k].vp64.reshape(16), cams[2 * k + 1].vp64.reshape(16))
+    keep = star.interp_float
+    star.interp_float = True
     star.step()
+    star.interp_float = keep
     real = star.rgba32f.view(-1, 4)[:, :3].clone()
     interp = star.interp_out.view(-1, 4)[:, :3].clone()
     plain.set_cameras(cams[2 * k].vp32)

@@ -386,8 +386,9 @@ star_nt_status star_nt_quadtree_static(const uint32_t *rgba8, const int32_t *id1
 /* current camera and projected with the previous one; the previous frame is */
 /* sampled there bilinearly with clamp to edge.  A point behind the previous */
 /* camera keeps its own previous colour.                                    */
-/* prev_rgba, out_rgba: [W*H][4] float32 (distinct); out_rgba8: optional      */
-/* [W*H] 8-bit copy (as star_nt_composite), may be NULL; prev_z1: [W*H];      */
+/* prev_rgba, out_rgba: [W*H][4] float32 (distinct); out_rgba8: [W*H] 8-bit  */
+/* frame (as star_nt_composite); either output may be NULL, not both (a      */
+/* display needs only the 8-bit frame); prev_z1: [W*H];                      */
 /* vp_prev, vp_cur: device, 16 float64 row-major view-projections; ws: device */
 /* scratch of STAR_NT_REPROJECT_WS_BYTES bytes (16-byte aligned) that holds  */
 /* VP_prev inv(VP_cur) - I for the call (two launches: that matrix in       */

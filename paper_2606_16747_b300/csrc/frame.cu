@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(256) k_reproject(const float4 *__restrict__ pr
   const float den = 1.0f + a3;
   if (!(den > 0.0f)) {
     const float4 v = prev[p];
-    out[p] = v;
+    if (out) out[p] = v;
     if (q) q[p] = quantize_rgba8(v);
     return;
   }
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(256) k_reproject(const float4 *__restrict__ pr
   o.y = (1.f - fy) * ((1.f - fx) * v00.y + fx * v10.y) + fy * ((1.f - fx) * v01.y + fx * v11.y);
   o.z = (1.f - fy) * ((1.f - fx) * v00.z + fx * v10.z) + fy * ((1.f - fx) * v01.z + fx * v11.z);
   o.w = (1.f - fy) * ((1.f - fx) * v00.w + fx * v10.w) + fy * ((1.f - fx) * v01.w + fx * v11.w);
-  out[p] = o;
+  if (out) out[p] = o;
   if (q) q[p] = quantize_rgba8(o);
 }
 
@@ -303,8 +303,8 @@ extern "C" star_nt_status star_nt_reproject(const float *prev_rgba, const float 
                                             const double *vp_prev, const double *vp_cur, int32_t W,
                                             int32_t H, float *out_rgba, uint32_t *out_rgba8,
                                             void *ws, void *stream) {
-  if (W <= 0 || H <= 0 || !prev_rgba || !prev_z1 || !vp_prev || !vp_cur || !out_rgba || !ws ||
-      prev_rgba == out_rgba)
+  if (W <= 0 || H <= 0 || !prev_rgba || !prev_z1 || !vp_prev || !vp_cur || (!out_rgba && !out_rgba8) ||
+      !ws || prev_rgba == out_rgba)
     return STAR_NT_ERR_ARG;
   if (((uintptr_t)prev_rgba & 15u) || ((uintptr_t)out_rgba & 15u) || ((uintptr_t)vp_prev & 7u) ||
       ((uintptr_t)vp_cur & 7u) || ((uintptr_t)ws & 15u))

@@ -87,6 +87,7 @@ class Renderer:
             self.set_mlp(mlp)
         # reprojection
         self.interp_out = torch.zeros(P * 4, **f32)
+        self.interp_float = True   # float copy of interpolated frames (analysis; displays use 8-bit)
         self.interp_rgba8 = torch.zeros(P, **i32)
         self.vp64_prev = torch.zeros(16, dtype=torch.float64, device=device)
         self.vp64_cur = torch.zeros(16, dtype=torch.float64, device=device)
@@ -202,9 +203,12 @@ class Renderer:
     def interp_frame(self, stream=None):
         """Interpolated frame from the last real frame (its colour and pass-1
         depth stay in ``rgba32f`` and ``l1['z1']`` until the next real frame);
-        camera matrices from ``vp64_prev`` (real) and ``vp64_cur``."""
+        camera matrices from ``vp64_prev`` (real) and ``vp64_cur``.  The
+        8-bit frame always, the float frame (``interp_out``) when
+        ``interp_float`` is set."""
         sn.reproject(self.rgba32f, self.l1["z1"], self.vp64_prev, self.vp64_cur, self.W, self.H,
-                     self.interp_out, self.reproj_ws, stream, out_rgba8=self.interp_rgba8)
+                     self.interp_out if self.interp_float else None, self.reproj_ws, stream,
+                     out_rgba8=self.interp_rgba8)
 
     def step(self, stream=None):
         """One real STAR-NT frame followed by one interpolated frame.  The

@@ -342,7 +342,7 @@ REPROJECT_WS_BYTES = 64
 def reproject(prev_rgba, prev_z1, vp_prev, vp_cur, W, H, out_rgba, ws=None, stream=None,
               out_rgba8=None):
     if ws is None:
-        ws = torch.empty(REPROJECT_WS_BYTES, dtype=torch.uint8, device=out_rgba.device)
+        ws = torch.empty(REPROJECT_WS_BYTES, dtype=torch.uint8, device=prev_rgba.device)
     _check("star_nt_reproject", lib().star_nt_reproject(_ptr(prev_rgba), _ptr(prev_z1), _ptr(vp_prev),
                                                         _ptr(vp_cur), W, H, _ptr(out_rgba),
                                                         _ptr(out_rgba8), _ptr(ws), _stream(stream)))
