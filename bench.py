@@ -39,6 +39,9 @@ OPS_PER_FRAGMENT = 32     # algorithmic integer/fp operations per fragment (see 
 # quadtree (decide, relax, relax + histogram + Eq. 2), reprojection (matrix, pixels)
 KERNELS_PER_STEP = 3 + 1 + 1 + 3 + 2
 STAGE_REPS = 20
+# DRAM bytes (read + write) of one k_passes launch at 1080p, from the ncu
+# capture summarised in profiles/passes_hd.md (same kernel build)
+PASSES_DRAM_BYTES = 9361664
 
 
 def load_peaks():
@@ -339,7 +342,10 @@ def run_ours(args, rank, world):
         "e2e": e2e,
         "roofline": {"bound": "alu", "kernel": dom_name, "fragments": int(dom_frags),
                      "achieved": round(achieved, 4), "peak": round(alu_peak, 3), "unit": "Tops/s",
-                     "frac": round(achieved / alu_peak, 5), "traffic": None,
+                     "frac": round(achieved / alu_peak, 5),
+                     "traffic": PASSES_DRAM_BYTES if "passes" in stage_mean else None,
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
+                                       "k_passes launch (profiles/passes_hd.md, 1080p orbit step 6)",
                      "peak_source": f"{N_SM} SM x {ALU_LANES_PER_SM} lanes x sm_max_mhz ({peaks_kind})",
                      "ops_per_fragment": OPS_PER_FRAGMENT, "launch_ms": round(dom_ms, 5)},
     }
