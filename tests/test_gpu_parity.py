@@ -518,6 +518,41 @@ def test_plain_frame_hd_full_size(orc, sn):
     assert np.max(np.abs(rgb - o["rgb"])) <= TOL_FRAME
 
 
+@pytest.mark.parametrize("workload", ["hd", "uhd"])
+def test_star_frame_full_size(orc, sn, workload):
+    """A real STAR-NT frame at full size in the benchmark's launch
+    configuration (persistent passes, fused BF16 resolve, pass 2 merged
+    above half size): pass-1 ids and depths and the merged pass-2 ids are
+    bit-exact at full resolution, the pass-3 planes at their own size, and the
+    frame is within the BF16 tolerance of the oracle's float64 frame."""
+    from paper_2606_16747_b300.pipeline import Renderer
+    sc = scenes.hd_scene() if workload == "hd" else scenes.uhd_scene()
+    W, H = sc.width, sc.height
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                        "paper_2606_16747_b300", "weights", "tail_mlp.npz")
+    mlp = dict(np.load(path))
+    s2 = (math.ceil(0.71 * W), math.ceil(0.71 * H))      # merged into pass 1 (>= 0.5)
+    s3 = (math.ceil(0.41 * W), math.ceil(0.41 * H))
+    r = Renderer(sc.verts, sc.rgba8, W, H, mlp=mlp, x_dtype=sn.BF16, fused=True, persistent=True,
+                 merge_scale2=0.5)
+    r.set_camera(sc.cam.vp32)
+    r.state.view(torch.int32)[:6] = torch.tensor([W, H, *s2, *s3], dtype=torch.int32)
+    r.star_frame(update_tiles=False)
+    torch.cuda.synchronize()
+    r.check_status()
+    o = orc.frame_star(sc.verts, sc.rgba8, sc.cam.vp32, W, H, (W, H), s3, scenes.mlp_flat(mlp),
+                       threads=os.cpu_count() or 4)
+    check_layers_full(o["r1"], r, W, H)
+    assert np.array_equal(r.l2["id2"].cpu().numpy(), o["r2"]["id2"])
+    P3 = s3[0] * s3[1]
+    assert np.array_equal(u32(r.l3["n"])[:P3], o["r3"]["n"])
+    tail = u32(r.l3["tail"])[:4 * P3].reshape(-1, 4)
+    assert np.array_equal(tail[:, 0], o["r3"]["a_tail"]) and np.array_equal(tail[:, 1:], o["r3"]["s_tail"])
+    rgb = r.rgba32f.cpu().numpy().reshape(-1, 4)[:, :3]
+    err = np.abs(rgb - o["rgb"])
+    assert err.max() <= TOL_BF16, (err.max() * 255, np.quantile(err, 0.999) * 255)
+
+
 # ---------------------------------------------------------------------------
 # star_nt_infer on the tcgen05 tensor cores (bf16 operands, fp32 accumulate)
 
