@@ -83,7 +83,8 @@ def _declare(L):
     L.orc_pass_scale.restype = _D
     L.orc_pass_size.argtypes = [_D, _I32]
     L.orc_pass_size.restype = _I32
-    L.orc_quadtree.argtypes = [_P, _P, _I32, _I32, _I32, _D, _D, _I32, _P, _P, _P]
+    L.orc_quadtree.argtypes = [_P, _P, _I32, _I32, _I32, _D, _D, _I32, _P, _P, _P, _P]
+    L.orc_tile_grid.argtypes = [_P, _I64, _D, _P]
     L.orc_inverse4.argtypes = [_P, _P]
     L.orc_inverse4.restype = ctypes.c_int
     L.orc_reproject.argtypes = [_P, _P, _P, _P, _I32, _I32, _P]
@@ -268,17 +269,70 @@ def wbar(hist):
     return 0.0 if tot == 0 else sum(l * h[l] for l in range(4)) / tot
 
 
-def quadtree(img, id1, W, H, base, tau_split, tau_merge, mask_prev, relax_iters=2):
-    """One frame of tile evaluation; returns (mask, hist[4])."""
+def quadtree(img, id1, W, H, base, tau_split, tau_merge, mask_prev, relax_iters=2, per_tile=False):
+    """One frame of tile evaluation; returns (mask, hist[4]), and with
+    per_tile also the per-tile histograms [tiles][4]."""
     L = lib()
     TX, TY = (W + base - 1) // base, (H + base - 1) // base
     mp = _c(mask_prev, np.uint32)
     assert mp.size == TX * TY
     mask = np.empty(TX * TY, np.uint32)
     hist = np.zeros(4, np.uint32)
+    th = np.zeros((TX * TY, 4), np.uint32) if per_tile else None
     L.orc_quadtree(_ptr(_c(img, np.uint32)), _ptr(_c(id1, np.int32)), W, H, base, float(tau_split),
-                   float(tau_merge), relax_iters, _ptr(mp), _ptr(mask), _ptr(hist))
-    return mask, hist
+                   float(tau_merge), relax_iters, _ptr(mp), _ptr(mask), _ptr(hist),
+                   _ptr(th) if per_tile else None)
+    return (mask, hist, th) if per_tile else (mask, hist)
+
+
+def tile_grid(tile_hist, delta):
+    """Per-tile grid spacing g in {1, 2, 4} from the per-tile Eq. 2."""
+    th = _c(tile_hist, np.uint32).reshape(-1, 4)
+    g = np.empty(th.shape[0], np.uint8)
+    lib().orc_tile_grid(_ptr(th), th.shape[0], float(delta), _ptr(g))
+    return g
+
+
+def frame_star_tiled(verts, rgba8, vp32, W, H, g2, g3, params, bg=(1.0, 1.0, 1.0), threads=1, B=16):
+    """STAR-NT real frame with per-tile resolution: pass 1 at W x H; for each
+    base tile (B x B pixels) passes 2 and 3 come from the full-, half- or
+    quarter-resolution target (grid spacing g2, g3 of the tile), each target
+    upscaled bilinearly to the frame, before the features and the composite.
+    W and H must be multiples of 4."""
+    assert W % 4 == 0 and H % 4 == 0
+    g2 = np.asarray(g2, np.uint8)
+    g3 = np.asarray(g3, np.uint8)
+    TX = (W + B - 1) // B
+    yy, xx = np.divmod(np.arange(W * H), W)
+    tile = (yy // B) * TX + (xx // B)
+    gp2, gp3 = g2[tile], g3[tile]
+    res = {1: resolve(raster(verts, vp32, W, H, threads), rgba8, bg, threads)}
+    for g in (2, 4):
+        if np.any(g2 == g) or np.any(g3 == g):
+            res[g] = resolve(raster(verts, vp32, W // g, H // g, threads), rgba8, bg, threads)
+    r1 = res[1]
+    layer2 = np.empty((W * H, 4))
+    n_up = np.empty(W * H)
+    a_up = np.empty(W * H)
+    s_up = np.empty((W * H, 3))
+    t_up = np.empty(W * H)
+    flag = np.empty(W * H, np.uint8)
+    for g, r in res.items():
+        Wg, Hg = W // g, H // g
+        sel = gp2 == g
+        if sel.any():
+            layer2[sel] = upscale(r["layer2"], Wg, Hg, W, H)[sel]
+        sel = gp3 == g
+        if sel.any():
+            n_up[sel] = upscale(r["n"].astype(np.float64), Wg, Hg, W, H)[sel]
+            a_up[sel] = upscale(r["a_tail"].astype(np.float64), Wg, Hg, W, H)[sel]
+            s_up[sel] = upscale(r["s_tail"].astype(np.float64), Wg, Hg, W, H)[sel]
+            t_up[sel] = upscale(r["t_tail"], Wg, Hg, W, H)[sel]
+            flag[sel] = tail_flag(r["n"], Wg, Hg, W, H)[sel]
+    x, front = features(r1["id1"], rgba8, layer2, n_up, a_up, s_up, t_up, bg)
+    f = mlp_forward(params64(params), x, flag)
+    rgb = composite(front, f)
+    return dict(res=res, layer2=layer2, n_up=n_up, flag=flag, x=x, front=front, f=f, rgb=rgb)
 
 
 def next_pass_sizes(hist, W, H, delta2=DELTA2, delta3=DELTA3):
