@@ -83,8 +83,7 @@ def _declare(L):
     L.orc_pass_scale.restype = _D
     L.orc_pass_size.argtypes = [_D, _I32]
     L.orc_pass_size.restype = _I32
-    L.orc_quadtree.argtypes = [_P, _P, _I32, _I32, _I32, _D, _D, _I32, _P, _P, _P, _P]
-    L.orc_tile_grid.argtypes = [_P, _I64, _D, _P]
+    L.orc_quadtree.argtypes = [_P, _P, _I32, _I32, _I32, _D, _D, _I32, _P, _P, _P]
     L.orc_inverse4.argtypes = [_P, _P]
     L.orc_inverse4.restype = ctypes.c_int
     L.orc_reproject.argtypes = [_P, _P, _P, _P, _I32, _I32, _P]
@@ -269,66 +268,91 @@ def wbar(hist):
     return 0.0 if tot == 0 else sum(l * h[l] for l in range(4)) / tot
 
 
-def quadtree(img, id1, W, H, base, tau_split, tau_merge, mask_prev, relax_iters=2, per_tile=False):
-    """One frame of tile evaluation; returns (mask, hist[4]), and with
-    per_tile also the per-tile histograms [tiles][4]."""
+def quadtree(img, id1, W, H, base, tau_split, tau_merge, mask_prev, relax_iters=2):
+    """One frame of tile evaluation; returns (mask, hist[4])."""
     L = lib()
     TX, TY = (W + base - 1) // base, (H + base - 1) // base
     mp = _c(mask_prev, np.uint32)
     assert mp.size == TX * TY
     mask = np.empty(TX * TY, np.uint32)
     hist = np.zeros(4, np.uint32)
-    th = np.zeros((TX * TY, 4), np.uint32) if per_tile else None
     L.orc_quadtree(_ptr(_c(img, np.uint32)), _ptr(_c(id1, np.int32)), W, H, base, float(tau_split),
-                   float(tau_merge), relax_iters, _ptr(mp), _ptr(mask), _ptr(hist),
-                   _ptr(th) if per_tile else None)
-    return (mask, hist, th) if per_tile else (mask, hist)
+                   float(tau_merge), relax_iters, _ptr(mp), _ptr(mask), _ptr(hist))
+    return mask, hist
 
 
-def tile_grid(tile_hist, delta):
-    """Per-tile grid spacing g in {1, 2, 4} from the per-tile Eq. 2."""
-    th = _c(tile_hist, np.uint32).reshape(-1, 4)
-    g = np.empty(th.shape[0], np.uint8)
-    lib().orc_tile_grid(_ptr(th), th.shape[0], float(delta), _ptr(g))
-    return g
+# ---------------------------------------------------------------------------
+# Per-leaf pass resolution: Eq. 2 with the scene index wbar replaced by the
+# level l of the quadtree leaf holding the pixel, s_p(l) = clamp(2^(l -
+# delta_p), 1/4, 1); each pixel takes passes 2 and 3 from the render target of
+# its own leaf's scale (size ceil(s W) x ceil(s H), as for the global scale),
+# upscaled bilinearly.
+
+def leaf_levels(mask, W, H, base):
+    """Level (0..3) of the leaf holding each pixel, [H*W] uint8, read from the
+    per-tile split masks (bit 0 root; bits 1..4 the level-1 children; bits
+    5..20 the level-2 nodes, 4 per level-1 child; child index 2 y_half + x_half)."""
+    m = np.asarray(mask, np.uint32)
+    TX = (W + base - 1) // base
+    yy, xx = np.divmod(np.arange(W * H, dtype=np.int64), W)
+    mt = m[(yy // base) * TX + xx // base].astype(np.int64)
+    ly, lx = yy % base, xx % base
+    h1, h2 = base // 2, base // 4
+    c1 = 2 * (ly >= h1) + (lx >= h1)
+    c2 = 2 * ((ly % h1) >= h2) + ((lx % h1) >= h2)
+    root = (mt & 1) != 0
+    split1 = root & (((mt >> (1 + c1)) & 1) != 0)
+    split2 = split1 & (((mt >> (5 + 4 * c1 + c2)) & 1) != 0)
+    return (root.astype(np.uint8) + split1 + split2).astype(np.uint8)
 
 
-def frame_star_tiled(verts, rgba8, vp32, W, H, g2, g3, params, bg=(1.0, 1.0, 1.0), threads=1, B=16):
-    """STAR-NT real frame with per-tile resolution: pass 1 at W x H; for each
-    base tile (B x B pixels) passes 2 and 3 come from the full-, half- or
-    quarter-resolution target (grid spacing g2, g3 of the tile), each target
-    upscaled bilinearly to the frame, before the features and the composite.
-    W and H must be multiples of 4."""
-    assert W % 4 == 0 and H % 4 == 0
-    g2 = np.asarray(g2, np.uint8)
-    g3 = np.asarray(g3, np.uint8)
-    TX = (W + B - 1) // B
-    yy, xx = np.divmod(np.arange(W * H), W)
-    tile = (yy // B) * TX + (xx // B)
-    gp2, gp3 = g2[tile], g3[tile]
-    res = {1: resolve(raster(verts, vp32, W, H, threads), rgba8, bg, threads)}
-    for g in (2, 4):
-        if np.any(g2 == g) or np.any(g3 == g):
-            res[g] = resolve(raster(verts, vp32, W // g, H // g, threads), rgba8, bg, threads)
-    r1 = res[1]
+def leaf_sizes(W, H, delta2=None, delta3=None):
+    """{(p, l): (W_p, H_p)} of passes p = 2, 3 at leaf levels l = 0..3."""
+    d = {2: DELTA2 if delta2 is None else delta2, 3: DELTA3 if delta3 is None else delta3}
+    out = {}
+    for p in (2, 3):
+        for l in range(4):
+            s = pass_scale(float(l), d[p])
+            out[(p, l)] = (pass_size(s, W), pass_size(s, H))
+    return out
+
+
+def frame_star_leaf(verts, rgba8, vp32, W, H, levels, params, bg=(1.0, 1.0, 1.0), threads=1,
+                    delta2=None, delta3=None):
+    """STAR-NT real frame with per-leaf resolution: pass 1 at W x H; a pixel
+    whose leaf is at level l takes pass 2 from the target of size
+    leaf_sizes[(2, l)] and pass 3 from that of leaf_sizes[(3, l)], each
+    target resolved over the whole frame and upscaled bilinearly to W x H,
+    before the features and the composite.  levels: [H*W] from leaf_levels."""
+    lv = np.asarray(levels, np.uint8).reshape(-1)
+    assert lv.size == W * H
+    sizes = leaf_sizes(W, H, delta2, delta3)
+    res = {(W, H): resolve(raster(verts, vp32, W, H, threads), rgba8, bg, threads)}
+    for l in range(4):
+        if np.any(lv == l):
+            for p in (2, 3):
+                sz = sizes[(p, l)]
+                if sz not in res:
+                    res[sz] = resolve(raster(verts, vp32, sz[0], sz[1], threads), rgba8, bg, threads)
+    r1 = res[(W, H)]
     layer2 = np.empty((W * H, 4))
     n_up = np.empty(W * H)
     a_up = np.empty(W * H)
     s_up = np.empty((W * H, 3))
     t_up = np.empty(W * H)
     flag = np.empty(W * H, np.uint8)
-    for g, r in res.items():
-        Wg, Hg = W // g, H // g
-        sel = gp2 == g
-        if sel.any():
-            layer2[sel] = upscale(r["layer2"], Wg, Hg, W, H)[sel]
-        sel = gp3 == g
-        if sel.any():
-            n_up[sel] = upscale(r["n"].astype(np.float64), Wg, Hg, W, H)[sel]
-            a_up[sel] = upscale(r["a_tail"].astype(np.float64), Wg, Hg, W, H)[sel]
-            s_up[sel] = upscale(r["s_tail"].astype(np.float64), Wg, Hg, W, H)[sel]
-            t_up[sel] = upscale(r["t_tail"], Wg, Hg, W, H)[sel]
-            flag[sel] = tail_flag(r["n"], Wg, Hg, W, H)[sel]
+    for l in range(4):
+        sel = lv == l
+        if not sel.any():
+            continue
+        (W2, H2), (W3, H3) = sizes[(2, l)], sizes[(3, l)]
+        r2, r3 = res[(W2, H2)], res[(W3, H3)]
+        layer2[sel] = upscale(r2["layer2"], W2, H2, W, H)[sel]
+        n_up[sel] = upscale(r3["n"].astype(np.float64), W3, H3, W, H)[sel]
+        a_up[sel] = upscale(r3["a_tail"].astype(np.float64), W3, H3, W, H)[sel]
+        s_up[sel] = upscale(r3["s_tail"].astype(np.float64), W3, H3, W, H)[sel]
+        t_up[sel] = upscale(r3["t_tail"], W3, H3, W, H)[sel]
+        flag[sel] = tail_flag(r3["n"], W3, H3, W, H)[sel]
     x, front = features(r1["id1"], rgba8, layer2, n_up, a_up, s_up, t_up, bg)
     f = mlp_forward(params64(params), x, flag)
     rgb = composite(front, f)

@@ -627,7 +627,7 @@ int32_t orc_pass_size(double s, int32_t n) { return (int32_t)ceil(s * (double)n)
 
 void orc_quadtree(const uint32_t *img, const int32_t *id1, int32_t W, int32_t H, int32_t B,
                   double tau_split, double tau_merge, int32_t relax_iters,
-                  const uint32_t *mask_prev, uint32_t *mask_out, uint32_t *hist, uint32_t *tile_hist)
+                  const uint32_t *mask_prev, uint32_t *mask_out, uint32_t *hist)
 {
     int TX = (W + B - 1) / B, TY = (H + B - 1) / B;
     int64_t NT = (int64_t)TX * TY;
@@ -706,10 +706,8 @@ void orc_quadtree(const uint32_t *img, const int32_t *id1, int32_t W, int32_t H,
         }
     }
     free(lev);
-    /* 3. histogram of occupied leaves per level (and per tile when asked) */
+    /* 3. histogram of occupied leaves per level */
     for (int l = 0; l < 4; ++l) hist[l] = 0;
-    if (tile_hist)
-        for (int64_t k = 0; k < 4 * NT; ++k) tile_hist[k] = 0;
     for (int64_t t = 0; t < NT; ++t) {
         int tx = (int)(t % TX), ty = (int)(t / TX);
         for (int l = 0; l < 4; ++l) {
@@ -724,31 +722,8 @@ void orc_quadtree(const uint32_t *img, const int32_t *id1, int32_t W, int32_t H,
                         for (int64_t x = tx * (int64_t)B + i * S; x < tx * (int64_t)B + (i + 1) * S && x < W; ++x)
                             if (id1[y * W + x] >= 0) occ = 1;
                     hist[l] += (uint32_t)occ;
-                    if (tile_hist) tile_hist[4 * t + l] += (uint32_t)occ;
                 }
         }
-    }
-}
-
-/* Per-tile resolution (the per-tile variant of Eq. 2): a base tile's own     */
-/* occupied leaves give wbar_t = (n1 + 2 n2 + 3 n3) / (n0 + n1 + n2 + n3) and */
-/* s = clamp(2^(wbar_t - delta), 1/4, 1), rounded in log2 to the grid        */
-/* spacing g = 1, 2 or 4 full-resolution pixels (the pass then runs at W/g): */
-/* g = 1 when delta - wbar_t < 1/2, g = 2 when < 3/2, else 4; a tile with no */
-/* occupied leaf takes g = 4.                                                 */
-
-void orc_tile_grid(const uint32_t *tile_hist, int64_t NT, double delta, uint8_t *g)
-{
-    for (int64_t t = 0; t < NT; ++t) {
-        const uint32_t *h = tile_hist + 4 * t;
-        double tot = (double)h[0] + (double)h[1] + (double)h[2] + (double)h[3];
-        if (tot <= 0.0) {
-            g[t] = 4;
-            continue;
-        }
-        double wbar = ((double)h[1] + 2.0 * (double)h[2] + 3.0 * (double)h[3]) / tot;
-        double e = delta - wbar;
-        g[t] = e < 0.5 ? 1 : (e < 1.5 ? 2 : 4);
     }
 }
 
