@@ -162,9 +162,11 @@ star_nt_status star_nt_raster(const star_nt_scene *scene, const star_nt_target *
                               const star_nt_bins *bins, const star_nt_frags *frags_or_null,
                               int32_t *d_status, void *stream);
 
-/* The front end of up to three passes at once (targets[i] into bins[i],
- * distinct workspaces), in the same three launches: the frame's passes share
- * each launch instead of running one after another.  No fragment lists. */
+/* The front end of up to STAR_NT_MAX_RASTER_PASSES passes at once (targets[i]
+ * into bins[i], distinct workspaces), in the same three launches: the frame's
+ * passes share each launch instead of running one after another.  No
+ * fragment lists. */
+#define STAR_NT_MAX_RASTER_PASSES 9
 star_nt_status star_nt_raster_passes(const star_nt_scene *scene, int32_t n_passes,
                                      const star_nt_target *targets, const star_nt_bins *bins,
                                      int32_t *d_status, void *stream);
@@ -376,6 +378,75 @@ star_nt_status star_nt_quadtree_static(const uint32_t *rgba8, const int32_t *id1
                                        int32_t H, const star_nt_params *params,
                                        const uint32_t *mask_prev, uint32_t *mask_out,
                                        star_nt_pass_state *state, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Per-leaf pass resolution: the per-tile variant of Sec. 3.2 / Eq. 2.       */
+/*                                                                           */
+/* Eq. 2 with the scene index wbar replaced by the level l of the quadtree   */
+/* leaf holding the pixel: s_p(l) = clamp(2^(l - delta_p), 1/4, 1) for the   */
+/* passes p = 2, 3.  A pixel takes pass 2 and pass 3 from the render target  */
+/* of its own leaf's scale (W_p = ceil(s W), H_p = ceil(s H), as for the     */
+/* global scale), upscaled bilinearly to W x H exactly as in               */
+/* star_nt_resolve; pass 1 stays at W x H.  The scales depend only on l and  */
+/* delta_p, so the set of targets is fixed for a frame size: a plan lists    */
+/* the distinct sizes (target 0 is W x H itself, shared with pass 1) and     */
+/* maps every (pass, level) to one of them.  A 16 x 16 tile of a target runs */
+/* only the passes that some pixel needs from it: a pixel needs the samples  */
+/* of nonzero bilinear weight of its pass-2 and pass-3 targets.  Leaf levels */
+/* are read from the quadtree masks (star_nt_quadtree's mask_out of the      */
+/* previous frame).                                                          */
+
+#define STAR_NT_E4M3 2 /* MLP operand type of star_nt_resolve_leaf: FP8 e4m3 */
+#define STAR_NT_LEAF_MAX_TARGETS 9
+
+typedef struct {
+    int32_t W, H;                                 /* full resolution */
+    int32_t base_tile;                            /* quadtree base tile side: 16 or 64 */
+    int32_t n_targets;                            /* 1 .. STAR_NT_LEAF_MAX_TARGETS */
+    int32_t size[STAR_NT_LEAF_MAX_TARGETS][2];    /* target sizes; size[0] = {W, H} */
+    int32_t target_of[2][4];                      /* [pass 2, pass 3][level] -> target index */
+} star_nt_leaf_plan;
+
+/* Host only: the plan of frame size W x H under params (delta2, delta3,
+ * base_tile); sizes in float64 as in star_nt_quadtree.  Targets are listed
+ * as first met over pass 2 then pass 3, levels 0..3, after target 0. */
+star_nt_status star_nt_leaf_plan_make(int32_t W, int32_t H, const star_nt_params *params,
+                                      star_nt_leaf_plan *plan);
+
+/* Workspace of star_nt_geometry_passes_leaf (one mode byte per target tile). */
+star_nt_status star_nt_leaf_ws_bytes(const star_nt_leaf_plan *plan, size_t *bytes);
+
+/* star_nt_geometry_passes_leaf: pass 1 and the per-leaf passes 2 and 3 of a
+ * real frame.  Two launches: the pass modes of every target tile from the
+ * masks, then one persistent launch over the tiles of all targets (work
+ * counter in bins[0]'s workspace, as star_nt_geometry_passes).
+ * bins[k]: target k binned by star_nt_raster_passes at size[k] (no merge),
+ *   n_targets distinct workspaces.  A bins header whose size differs from the
+ *   plan raises STAR_NT_ERR_ARG in d_status and its tiles are skipped.
+ * layers[k]: planes at target k's size.  layers[0] needs id1 and z1; every
+ *   target that some level maps pass 2 to needs id2; every target that some
+ *   level maps pass 3 to needs n, tail and t_tail (others may be NULL).
+ *   Planes of tiles no pixel needs are left as they were.
+ * masks: [ceil(W/B) * ceil(H/B)] quadtree split masks; ws: star_nt_leaf_ws_bytes
+ *   bytes (256-byte aligned); tuning: as star_nt_geometry_passes. */
+star_nt_status star_nt_geometry_passes_leaf(const star_nt_scene *scene,
+                                            const star_nt_leaf_plan *plan,
+                                            const star_nt_bins *bins,
+                                            const star_nt_layers *layers, const uint32_t *masks,
+                                            void *ws, size_t ws_bytes,
+                                            const star_nt_tuning *tuning, int32_t *d_status,
+                                            void *stream);
+
+/* star_nt_resolve_leaf: star_nt_resolve with each pixel's pass-2 and pass-3
+ * planes taken from the targets of its leaf level (layers and masks as in
+ * star_nt_geometry_passes_leaf).  mlp_type: STAR_NT_BF16 (star_nt_resolve's
+ * MLP) or STAR_NT_E4M3 (star_nt_resolve_fp8's).  Primitive ids read from the
+ * planes are bounds-checked against scene->n_tris. */
+star_nt_status star_nt_resolve_leaf(const star_nt_scene *scene, const star_nt_leaf_plan *plan,
+                                    const star_nt_layers *layers, const uint32_t *masks,
+                                    const star_nt_params *params, const star_nt_mlp *w,
+                                    int32_t mlp_type, float *rgba32f, uint32_t *rgba8,
+                                    int32_t *d_status, void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* star_nt_reproject -- interpolated frame by depth-based reprojection        */

@@ -104,6 +104,24 @@ inline BinsView bins_view(const star_nt_bins &b) {
   return v;
 }
 
+// Host check of a per-leaf plan: target 0 is the full resolution, every
+// target lies between a quarter of it and all of it on both axes (so a
+// 16-sample target tile maps to at most 64 + 5 full-resolution pixels per
+// axis), and every (pass, level) maps to a listed target.
+inline bool leaf_plan_valid(const star_nt_leaf_plan *p) {
+  if (!p || p->W <= 0 || p->H <= 0 || (p->base_tile != 16 && p->base_tile != 64)) return false;
+  if (p->n_targets < 1 || p->n_targets > STAR_NT_LEAF_MAX_TARGETS) return false;
+  if (p->size[0][0] != p->W || p->size[0][1] != p->H) return false;
+  for (int k = 0; k < p->n_targets; ++k) {
+    const long long w = p->size[k][0], h = p->size[k][1];
+    if (w < 1 || h < 1 || w > p->W || h > p->H || 4 * w < p->W || 4 * h < p->H) return false;
+  }
+  for (int q = 0; q < 2; ++q)
+    for (int l = 0; l < 4; ++l)
+      if (p->target_of[q][l] < 0 || p->target_of[q][l] >= p->n_targets) return false;
+  return true;
+}
+
 // First error wins.
 __device__ inline void raise_status(int32_t *status, int32_t code) {
   if (status) atomicCAS(status, STAR_NT_OK, code);

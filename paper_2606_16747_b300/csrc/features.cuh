@@ -6,6 +6,7 @@
 #include <cuda_bf16.h>
 
 #include "common.cuh"
+#include "qt_cells.cuh"
 
 namespace star {
 
@@ -100,27 +101,46 @@ struct FeatIn {
   const uint32_t *n3;
   const uint4 *tail3;
   const float *t3;
+
+  __device__ __forceinline__ bool rejected() const {  // a pass was rejected by its raster
+    return hd2->n_pixels <= 0 || hd3->n_pixels <= 0;
+  }
+};
+
+// Per-leaf variant: pass 2 and pass 3 of pixel (x, y) come from the targets
+// that the level of its quadtree leaf maps them to (per-pixel lookups in the
+// kernel's parameter memory).
+constexpr int kLeafMaxTargets = STAR_NT_LEAF_MAX_TARGETS;
+struct FeatInLeaf {
+  int W, H;
+  int B, tiles_x;                       // quadtree base tile side, tiles per row
+  uint32_t n_tris;                      // ids read from the planes are checked against it
+  const uint32_t *masks;
+  const uint32_t *rgba8;
+  const int32_t *id1;
+  int32_t target_of[2][4];              // [pass 2, pass 3][level]
+  int32_t size[kLeafMaxTargets][2];
+  const int32_t *id2[kLeafMaxTargets];
+  const uint32_t *n3[kLeafMaxTargets];
+  const uint4 *tail3[kLeafMaxTargets];
+  const float *t3[kLeafMaxTargets];
+
+  __device__ __forceinline__ bool rejected() const { return false; }
 };
 
 // Network input x[0..5] (x5 = tail flag) and front terms of pixel (x, y),
-// with passes 2 and 3 upscaled bilinearly.  All plane loads are issued before
-// any of them is used (the sample indices are clamped, so every load is
-// valid) to keep many requests in flight; zero bilinear weights then drop
-// their samples exactly.
-__device__ __forceinline__ void pixel_features(const FeatIn &in, float bg0, float bg1, float bg2,
-                                               float kappa, int x, int y, float (&xo)[6],
-                                               float4 &front) {
-  const int W = in.W, H = in.H;
-  const BinsHeader *hd2 = in.hd2, *hd3 = in.hd3;
-  const uint32_t *__restrict__ rgba8 = in.rgba8;
-  const int32_t *__restrict__ id1 = in.id1;
-  const int32_t *__restrict__ id2 = in.id2;
-  const uint32_t *__restrict__ n3 = in.n3;
-  const uint4 *__restrict__ tail3 = in.tail3;
-  const float *__restrict__ t3 = in.t3;
+// with pass 2 (W2 x H2) and pass 3 (W3 x H3) upscaled bilinearly.  All plane
+// loads are issued before any of them is used (the sample indices are
+// clamped, so every load is valid) to keep many requests in flight; zero
+// bilinear weights then drop their samples exactly.  A second-layer id is
+// used only below id_limit (0x80000000: any id >= 0).
+__device__ __forceinline__ void pixel_features_at(
+    int W, int H, const uint32_t *__restrict__ rgba8, const int32_t *__restrict__ id1,
+    int W2, int H2, const int32_t *__restrict__ id2, int W3, int H3,
+    const uint32_t *__restrict__ n3, const uint4 *__restrict__ tail3,
+    const float *__restrict__ t3, uint32_t id_limit, float bg0, float bg1, float bg2,
+    float kappa, int x, int y, float (&xo)[6], float4 &front) {
   const size_t p = (size_t)y * W + x;
-  const int W2 = hd2->size[0], H2 = hd2->size[1];
-  const int W3 = hd3->size[0], H3 = hd3->size[1];
   const Axis ax2 = upscale_axis(x, W2, W), ay2 = upscale_axis(y, H2, H);
   const Axis ax3 = upscale_axis(x, W3, W), ay3 = upscale_axis(y, H3, H);
   size_t q2[4], q3[4];
@@ -145,7 +165,7 @@ __device__ __forceinline__ void pixel_features(const FeatIn &in, float bg0, floa
   const uint32_t c1 = i1 >= 0 ? __ldg(rgba8 + i1) : 0u;
   uint32_t c2[4];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) c2[k] = i2[k] >= 0 ? __ldg(rgba8 + i2[k]) : 0u;
+  for (int k = 0; k < 4; ++k) c2[k] = (uint32_t)i2[k] < id_limit ? __ldg(rgba8 + i2[k]) : 0u;
 
   float r1, g1, b1, a1;
   unpack_rgba(c1, r1, g1, b1, a1);
@@ -155,7 +175,7 @@ __device__ __forceinline__ void pixel_features(const FeatIn &in, float bg0, floa
   float L2[4] = {0, 0, 0, 0};
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    if (w2[k] == 0.0f || i2[k] < 0) continue;
+    if (w2[k] == 0.0f || (uint32_t)i2[k] >= id_limit) continue;
     float r, g, b, a;
     unpack_rgba(c2[k], r, g, b, a);
     L2[0] += w2[k] * (a * r);
@@ -184,6 +204,28 @@ __device__ __forceinline__ void pixel_features(const FeatIn &in, float bg0, floa
   const bool flag = nexact > 2LL * ax3.den * ay3.den;
   feature_terms(a1, r1, g1, b1, L2[0], L2[1], L2[2], L2[3], nf, A, Sr, Sg, Sb, t, flag, bg0, bg1, bg2,
                 kappa, xo, front);
+}
+
+// Global pass sizes (Eq. 2 over the frame), read from the bins headers.
+__device__ __forceinline__ void pixel_features(const FeatIn &in, float bg0, float bg1, float bg2,
+                                               float kappa, int x, int y, float (&xo)[6],
+                                               float4 &front) {
+  pixel_features_at(in.W, in.H, in.rgba8, in.id1, in.hd2->size[0], in.hd2->size[1], in.id2,
+                    in.hd3->size[0], in.hd3->size[1], in.n3, in.tail3, in.t3, 0x80000000u, bg0, bg1,
+                    bg2, kappa, x, y, xo, front);
+}
+
+// Per-leaf pass sizes: the targets of the level of the pixel's leaf.
+__device__ __forceinline__ void pixel_features(const FeatInLeaf &in, float bg0, float bg1, float bg2,
+                                               float kappa, int x, int y, float (&xo)[6],
+                                               float4 &front) {
+  const int B = in.B;
+  const uint32_t m = __ldg(in.masks + (y / B) * in.tiles_x + x / B);
+  const int l = leaf_level(m, x % B, y % B, B);
+  const int k2 = in.target_of[0][l], k3 = in.target_of[1][l];
+  pixel_features_at(in.W, in.H, in.rgba8, in.id1, in.size[k2][0], in.size[k2][1], in.id2[k2],
+                    in.size[k3][0], in.size[k3][1], in.n3[k3], in.tail3[k3], in.t3[k3], in.n_tris,
+                    bg0, bg1, bg2, kappa, x, y, xo, front);
 }
 
 

@@ -339,6 +339,7 @@ cudaError_t preload_resolve_tc();
 cudaError_t preload_quadtree();
 cudaError_t preload_train();
 cudaError_t preload_baselines();
+cudaError_t preload_leaf();
 }  // namespace star
 
 extern "C" star_nt_status star_nt_preload(void) {
@@ -351,5 +352,6 @@ extern "C" star_nt_status star_nt_preload(void) {
   if ((r = preload_quadtree()) != cudaSuccess) e = r;
   if ((r = preload_train()) != cudaSuccess) e = r;
   if ((r = preload_baselines()) != cudaSuccess) e = r;
+  if ((r = preload_leaf()) != cudaSuccess) e = r;
   return e == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
 }

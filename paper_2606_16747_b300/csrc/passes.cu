@@ -2,141 +2,13 @@
 // second-nearest, tail statistics; Sec. 3, Sec. 3.3), the bilinear upscale of
 // the reduced passes (Sec. 3.2) and the network input / front terms of
 // Eq. 4.
-//
-// Tail statistics are accumulated over every fragment and the two nearest
-// are subtracted at the end: all sums are exact integers, and the tail
-// transmittance is carried as an integer sum of fixed-point -log2(1 - alpha)
-// (2^-32 units) plus a count of opaque fragments, so the result does not
-// depend on the order in which fragments arrive.
 #include <math.h>
 
 #include <cuda_bf16.h>
 
-#include "common.cuh"
-#include "features.cuh"
-#include "raster_tile.cuh"
+#include "pass_body.cuh"
 
 namespace star {
-
-enum PassMode { kTop1 = 1, kTop2 = 2, kTail = 3, kFused = 4 };
-
-struct PassOut {
-  int32_t *id1;
-  float *z1;
-  int32_t *id2;
-  uint32_t *n;
-  uint4 *tail;
-  float *t_tail;
-};
-
-// Per-thread state of one geometry pass over one tile.  MODE selects what is
-// kept: the nearest fragment, the two nearest, the two nearest plus tail sums,
-// or all of it plus the full-resolution network input (fused plain pipeline).
-struct PassAcc {
-  float z1, z2;
-  int i1, i2;
-  uint32_t N, opq;
-  unsigned long long rg, ba, lg;
-
-  __device__ __forceinline__ void reset() {
-    z1 = z2 = INFINITY;
-    i1 = i2 = 0x7fffffff;
-    N = opq = 0u;
-    rg = ba = lg = 0ull;
-  }
-
-  // A fragment deeper than the current k-th nearest cannot enter the top k:
-  // the passes without tail sums let the warp skip a triangle whose depth
-  // lower bound exceeds every lane's k-th depth (lanes outside the target
-  // never store, so they never hold a skip back); the tail passes must see
-  // every fragment and only skip the depth of such fragments.
-  template <int MODE>
-  __device__ __forceinline__ float bound(bool inside) const {
-    if (MODE >= kTail) return INFINITY;
-    return inside ? (MODE == kTop1 ? z1 : z2) : -INFINITY;
-  }
-
-  template <int MODE>
-  __device__ __forceinline__ void visit(const TriSetup &T, int id, long long e0, long long e2) {
-    if (MODE >= kTail) {
-      ++N;
-      rg += T.rg;
-      ba += T.ba;
-      lg += T.lg;
-      opq += T.opq;
-    }
-    if (MODE == kTop1) {
-      const float z = frag_depth(T, e0, e2);
-      if (z < z1 || (z == z1 && id < i1)) { z1 = z; i1 = id; }
-    } else if (!(T.zlo > z2)) {
-      const float z = frag_depth(T, e0, e2);
-      if (z < z2 || (z == z2 && id < i2)) {
-        if (z < z1 || (z == z1 && id < i1)) {
-          z2 = z1; i2 = i1; z1 = z; i1 = id;
-        } else {
-          z2 = z; i2 = id;
-        }
-      }
-    }
-  }
-
-  // Planes of pixel p (tail sums less the two nearest fragments).
-  template <int MODE>
-  __device__ __forceinline__ void finish(const TriSetup *__restrict__ setups,
-                                         const uint32_t *__restrict__ rgba8, const PassOut &po,
-                                         const FeatOut &fo, size_t p) {
-    const bool has1 = i1 != 0x7fffffff, has2 = i2 != 0x7fffffff;
-    if (po.id1) po.id1[p] = has1 ? i1 : -1;
-    if (po.z1) po.z1[p] = has1 ? z1 : 1.0f;
-    if (MODE >= kTop2 && po.id2) po.id2[p] = has2 ? i2 : -1;
-    if (MODE >= kTail) {
-      if (has1) {
-        const TriSetup &S = setups[i1];
-        rg -= S.rg; ba -= S.ba; lg -= S.lg; opq -= S.opq;
-      }
-      if (has2) {
-        const TriSetup &S = setups[i2];
-        rg -= S.rg; ba -= S.ba; lg -= S.lg; opq -= S.opq;
-      }
-      const uint32_t A = (uint32_t)(ba >> 32), Sr = (uint32_t)rg, Sg = (uint32_t)(rg >> 32),
-                     Sb = (uint32_t)ba;
-      const float t = tail_transmittance(lg, opq);
-      if (po.n) po.n[p] = N;
-      if (po.tail) po.tail[p] = make_uint4(A, Sr, Sg, Sb);
-      if (po.t_tail) po.t_tail[p] = t;
-      if (MODE == kFused) {
-        float r1 = 0, g1 = 0, b1 = 0, a1 = 0, r2 = 0, g2 = 0, b2 = 0, a2 = 0;
-        if (has1) unpack_rgba(__ldg(rgba8 + i1), r1, g1, b1, a1);
-        if (has2) unpack_rgba(__ldg(rgba8 + i2), r2, g2, b2, a2);
-        write_features(fo, p, a1, r1, g1, b1, a2 * r2, a2 * g2, a2 * b2, a2, (float)N, (float)A,
-                       (float)Sr, (float)Sg, (float)Sb, t, N > 2);
-      }
-    }
-  }
-};
-
-// One geometry pass over one tile (one CTA; the tile's triangles staged in
-// chunks by for_each_fragment).
-template <int MODE, int BW = 8>
-__device__ __forceinline__ void pass_body(const BinsView &bv, const uint32_t *__restrict__ rgba8,
-                                          const PassOut &po, const FeatOut &fo, TileStage &stage,
-                                          int tile) {
-  const BinsHeader *hd = bv.hd;
-  if ((int64_t)hd->n_pairs > bv.pair_capacity) return;
-  if (tile >= hd->n_tiles) return;
-  const int W = hd->size[0], H = hd->size[1];
-  const TilePixel tp = tile_pixel<BW>(tile, hd->tiles_x);
-  const bool inside = tp.px < W && tp.py < H;
-  PassAcc acc;
-  acc.reset();
-  for_each_fragment<BW, true>(
-      bv, tile, tp, stage, [&] { return acc.template bound<MODE>(inside); },
-      [&](const TriSetup &T, uint32_t id, long long e0, long long e2) {
-        acc.template visit<MODE>(T, (int)id, e0, e2);
-      });
-  if (!inside) return;
-  acc.template finish<MODE>(bv.setups, rgba8, po, fo, (size_t)tp.py * W + tp.px);
-}
 
 template <int MODE>
 __global__ void __launch_bounds__(256) k_pass(BinsView bv, const uint32_t *__restrict__ rgba8,

@@ -14,6 +14,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "qt_cells.cuh"
 
 namespace star {
 
@@ -142,35 +143,6 @@ __global__ void __launch_bounds__(256) k_qt_decide(const uint32_t *__restrict__ 
 // ---------------------------------------------------------------------------
 // Relaxation and the leaf histogram, bit-parallel over the 8 x 8 level-3
 // cells of a tile (bit 8 cy + cx of a 64-bit word).
-
-constexpr unsigned long long kCol0 = 0x0101010101010101ull, kCol7 = kCol0 << 7;
-constexpr unsigned long long kRow0 = 0xFFull, kRow7 = kRow0 << 56;
-
-// cells of level-1 quadrant q (child index 2 y_half + x_half)
-__device__ __forceinline__ unsigned long long quad_cells(int q) {
-  return 0x0F0F0F0Full << ((q & 1) * 4 + (q >> 1) * 32);
-}
-// cells of level-2 node q2 = 4 c1 + c2 (mask bit 5 + q2)
-__device__ __forceinline__ unsigned long long node2_cells(int q2) {
-  const int c1 = q2 >> 2, c2 = q2 & 3;
-  const int i = (c1 & 1) * 2 + (c2 & 1), j = (c1 >> 1) * 2 + (c2 >> 1);
-  return 0x0303ull << (2 * i + 16 * j);
-}
-
-// Cells whose leaf is at level >= 2 (d2) and at level 3 (d3) under mask m.
-__device__ __forceinline__ void deep_cells(uint32_t m, unsigned long long &d2, unsigned long long &d3) {
-  d2 = 0ull;
-  d3 = 0ull;
-  if (!(m & 1u)) return;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    if (!((m >> (1 + q)) & 1u)) continue;
-    d2 |= quad_cells(q);
-#pragma unroll
-    for (int c2 = 0; c2 < 4; ++c2)
-      if ((m >> (5 + 4 * q + c2)) & 1u) d3 |= node2_cells(4 * q + c2);
-  }
-}
 
 // One Jacobi relaxation step of a tile: a leaf splits when an edge-adjacent
 // cell (in the tile or across its border) lies two or more levels deeper.

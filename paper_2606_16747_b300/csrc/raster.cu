@@ -249,8 +249,9 @@ __device__ __forceinline__ void for_each_pair(const TriSetup *tri, int t0, int n
   }
 }
 
-// Up to three passes are binned by the same launches (blockIdx.y = pass).
-constexpr int kMaxPasses = 3;
+// Up to STAR_NT_MAX_RASTER_PASSES passes are binned by the same launches
+// (blockIdx.y = pass).
+constexpr int kMaxPasses = STAR_NT_MAX_RASTER_PASSES;
 struct PassSet {
   BinsView bv[kMaxPasses];
   const float *vp[kMaxPasses];

@@ -57,8 +57,9 @@ __device__ __forceinline__ uint32_t quantize8(float r, float g, float b) {
   return R | (G << 8) | (B << 16) | (255u << 24);
 }
 
+template <class In>
 __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
-    k_resolve(FeatIn in, float bg0, float bg1, float bg2, float kappa, const float *__restrict__ w1,
+    k_resolve(In in, float bg0, float bg1, float bg2, float kappa, const float *__restrict__ w1,
               const float *__restrict__ b1, const float *__restrict__ w2,
               const float *__restrict__ b2, const float *__restrict__ w3,
               const float *__restrict__ b3, float4 *__restrict__ out, uint32_t *__restrict__ out8,
@@ -71,7 +72,7 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
   const uint32_t bar = sbase + kQBar;
   uint32_t *s_tmem = reinterpret_cast<uint32_t *>(sm + kQBar + 8);
   volatile int *s_abort = reinterpret_cast<volatile int *>(sm + kQBar + 12);
-  if (in.hd2->n_pixels <= 0 || in.hd3->n_pixels <= 0) return;  // a pass was rejected
+  if (in.rejected()) return;  // a pass was rejected by its raster
 
   // weights and bias columns (bf16, zero padded), the ones and zero blocks
   for (int i = tid; i < (int)(kQBar - kQC) / 4; i += kRThreads)
@@ -285,8 +286,9 @@ __device__ __forceinline__ void put_row8(uint8_t *base, int lbo, const float *w,
   inv[n] = 1.0f / sc;  // exact: a power of two
 }
 
+template <class In>
 __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
-    k_resolve_fp8(FeatIn in, float bg0, float bg1, float bg2, float kappa,
+    k_resolve_fp8(In in, float bg0, float bg1, float bg2, float kappa,
                   const float *__restrict__ w1, const float *__restrict__ b1,
                   const float *__restrict__ w2, const float *__restrict__ b2,
                   const float *__restrict__ w3, const float *__restrict__ b3,
@@ -300,7 +302,7 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
   uint32_t *s_tmem = reinterpret_cast<uint32_t *>(sm + kF8Bar + 8);
   volatile int *s_abort = reinterpret_cast<volatile int *>(sm + kF8Bar + 12);
   float *sb = reinterpret_cast<float *>(sm + kF8B);
-  if (in.hd2->n_pixels <= 0 || in.hd3->n_pixels <= 0) return;  // a pass was rejected
+  if (in.rejected()) return;  // a pass was rejected by its raster
 
   // weights: e4m3 rows with power-of-two row scales, zero padded; biases fp32
   float *si = reinterpret_cast<float *>(sm + kF8S);
@@ -487,43 +489,55 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
 
 using namespace star;
 
-static star_nt_status launch_resolve(bool fp8, const star_nt_scene *scene, const star_nt_bins *b2,
-                                     const star_nt_bins *b3, const star_nt_layers *l1,
-                                     const star_nt_layers *l2, const star_nt_layers *l3, int32_t W,
-                                     int32_t H, const star_nt_params *params, const star_nt_mlp *w,
-                                     float *rgba32f, uint32_t *rgba8, int32_t *d_status,
-                                     void *stream) {
+// Launch of either resolve kernel on input In (the grid: one CTA per round
+// of two 128-pixel tiles, at most 8 CTAs per SM).
+template <class In>
+static star_nt_status launch_kernel(bool fp8, const In &in, const star_nt_params *params,
+                                    const star_nt_mlp *w, float *rgba32f, uint32_t *rgba8,
+                                    int32_t *d_status, void *stream) {
   static_assert(kQUsed + 1024 <= kQSmem, "shared memory map");
   static_assert(kF8Used + 1024 <= kQSmem, "shared memory map");
-  if (!scene || !b2 || !b3 || !b2->mem || !b3->mem || !params || !w || W <= 0 || H <= 0)
-    return STAR_NT_ERR_ARG;
-  if (!w->w1 || !w->b1 || !w->w2 || !w->b2 || !w->w3 || !w->b3 || (!rgba32f && !rgba8))
-    return STAR_NT_ERR_ARG;
-  if (!l1 || !l1->id1 || !l2 || !l2->id2 || !l3 || !l3->n || !l3->tail || !l3->t_tail)
-    return STAR_NT_ERR_ARG;
-  if (((uintptr_t)rgba32f & 15u) || ((uintptr_t)l3->tail & 15u)) return STAR_NT_ERR_ARG;
-  if (scene->n_tris > 0 && !scene->rgba8) return STAR_NT_ERR_ARG;
-  if ((long long)W * H > 0x7fffffffLL - 256) return STAR_NT_ERR_ARG;
-  auto kern = fp8 ? k_resolve_fp8 : k_resolve;
+  auto kern = fp8 ? k_resolve_fp8<In> : k_resolve<In>;
   static bool attr[2] = {false, false};
   if (!attr[fp8]) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kQSmem) != cudaSuccess)
       return STAR_NT_ERR_CUDA;
     attr[fp8] = true;
   }
-  BinsView v2 = bins_view(*b2), v3 = bins_view(*b3);
-  FeatIn in{W, H, v2.hd, v3.hd, scene->rgba8, l1->id1, l2->id2, l3->n,
-            reinterpret_cast<const uint4 *>(l3->tail), l3->t_tail};
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const long long rounds = ((long long)W * H + kRTiles * kRRows - 1) / (kRTiles * kRRows);
+  const long long rounds = ((long long)in.W * in.H + kRTiles * kRRows - 1) / (kRTiles * kRRows);
   long long grid = (long long)sms * kRCtasPerSm;
   if (grid > rounds) grid = rounds;
   kern<<<(unsigned)grid, kRThreads, kQSmem, (cudaStream_t)stream>>>(
       in, params->bg[0], params->bg[1], params->bg[2], params->kappa_n, w->w1, w->b1, w->w2, w->b2,
       w->w3, w->b3, reinterpret_cast<float4 *>(rgba32f), rgba8, d_status);
   return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
+}
+
+static bool mlp_ok(const star_nt_mlp *w) {
+  return w && w->w1 && w->b1 && w->w2 && w->b2 && w->w3 && w->b3;
+}
+
+static star_nt_status launch_resolve(bool fp8, const star_nt_scene *scene, const star_nt_bins *b2,
+                                     const star_nt_bins *b3, const star_nt_layers *l1,
+                                     const star_nt_layers *l2, const star_nt_layers *l3, int32_t W,
+                                     int32_t H, const star_nt_params *params, const star_nt_mlp *w,
+                                     float *rgba32f, uint32_t *rgba8, int32_t *d_status,
+                                     void *stream) {
+  if (!scene || !b2 || !b3 || !b2->mem || !b3->mem || !params || W <= 0 || H <= 0)
+    return STAR_NT_ERR_ARG;
+  if (!mlp_ok(w) || (!rgba32f && !rgba8)) return STAR_NT_ERR_ARG;
+  if (!l1 || !l1->id1 || !l2 || !l2->id2 || !l3 || !l3->n || !l3->tail || !l3->t_tail)
+    return STAR_NT_ERR_ARG;
+  if (((uintptr_t)rgba32f & 15u) || ((uintptr_t)l3->tail & 15u)) return STAR_NT_ERR_ARG;
+  if (scene->n_tris > 0 && !scene->rgba8) return STAR_NT_ERR_ARG;
+  if ((long long)W * H > 0x7fffffffLL - 256) return STAR_NT_ERR_ARG;
+  BinsView v2 = bins_view(*b2), v3 = bins_view(*b3);
+  FeatIn in{W, H, v2.hd, v3.hd, scene->rgba8, l1->id1, l2->id2, l3->n,
+            reinterpret_cast<const uint4 *>(l3->tail), l3->t_tail};
+  return launch_kernel(fp8, in, params, w, rgba32f, rgba8, d_status, stream);
 }
 
 extern "C" star_nt_status star_nt_resolve(const star_nt_scene *scene, const star_nt_bins *b2,
@@ -546,13 +560,58 @@ extern "C" star_nt_status star_nt_resolve_fp8(const star_nt_scene *scene, const 
                         stream);
 }
 
+extern "C" star_nt_status star_nt_resolve_leaf(const star_nt_scene *scene,
+                                               const star_nt_leaf_plan *plan,
+                                               const star_nt_layers *layers, const uint32_t *masks,
+                                               const star_nt_params *params, const star_nt_mlp *w,
+                                               int32_t mlp_type, float *rgba32f, uint32_t *rgba8,
+                                               int32_t *d_status, void *stream) {
+  if (!scene || !plan || !layers || !masks || !params || !mlp_ok(w) || (!rgba32f && !rgba8))
+    return STAR_NT_ERR_ARG;
+  if (mlp_type != STAR_NT_BF16 && mlp_type != STAR_NT_E4M3) return STAR_NT_ERR_ARG;
+  if (!leaf_plan_valid(plan)) return STAR_NT_ERR_ARG;
+  if (scene->n_tris < 0 || (scene->n_tris > 0 && !scene->rgba8)) return STAR_NT_ERR_ARG;
+  if ((uintptr_t)rgba32f & 15u) return STAR_NT_ERR_ARG;
+  const int W = plan->W, H = plan->H;
+  if ((long long)W * H > 0x7fffffffLL - 256) return STAR_NT_ERR_ARG;
+  if (!layers[0].id1) return STAR_NT_ERR_ARG;
+  FeatInLeaf in = {};
+  in.W = W;
+  in.H = H;
+  in.B = plan->base_tile;
+  in.tiles_x = (W + in.B - 1) / in.B;
+  in.n_tris = (uint32_t)scene->n_tris;
+  in.masks = masks;
+  in.rgba8 = scene->rgba8;
+  in.id1 = layers[0].id1;
+  for (int p = 0; p < 2; ++p)
+    for (int l = 0; l < 4; ++l) {
+      const int k = plan->target_of[p][l];
+      in.target_of[p][l] = k;
+      const star_nt_layers &L = layers[k];
+      if (p == 0 && !L.id2) return STAR_NT_ERR_ARG;
+      if (p == 1 && (!L.n || !L.tail || !L.t_tail || ((uintptr_t)L.tail & 15u))) return STAR_NT_ERR_ARG;
+    }
+  for (int k = 0; k < plan->n_targets; ++k) {
+    in.size[k][0] = plan->size[k][0];
+    in.size[k][1] = plan->size[k][1];
+    in.id2[k] = layers[k].id2;
+    in.n3[k] = layers[k].n;
+    in.tail3[k] = reinterpret_cast<const uint4 *>(layers[k].tail);
+    in.t3[k] = layers[k].t_tail;
+  }
+  return launch_kernel(mlp_type == STAR_NT_E4M3, in, params, w, rgba32f, rgba8, d_status, stream);
+}
+
 namespace star {
 // Loads this file's kernels onto the current device (see star_nt_preload).
 cudaError_t preload_resolve_tc() {
   cudaFuncAttributes a;
   cudaError_t e = cudaSuccess, r;
-  if ((r = cudaFuncGetAttributes(&a, k_resolve)) != cudaSuccess) e = r;
-  if ((r = cudaFuncGetAttributes(&a, k_resolve_fp8)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_resolve<FeatIn>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_resolve_fp8<FeatIn>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_resolve<FeatInLeaf>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_resolve_fp8<FeatInLeaf>)) != cudaSuccess) e = r;
   return e;
 }
 }  // namespace star

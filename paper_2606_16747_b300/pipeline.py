@@ -5,6 +5,8 @@ Owns the device buffers (torch allocations) and sequences the C-ABI calls:
   plain frame     raster (full res) -> fused build_inputs -> infer -> composite
   STAR-NT frame   raster x3 (full, s2, s3) -> geometry passes 1-3 -> upscale /
                   features -> infer -> composite -> quadtree (next s2, s3)
+  per-leaf frame  raster of the plan's targets -> pass modes + passes -> resolve
+                  (each pixel's passes 2, 3 at its leaf's scale) -> quadtree
   interpolated    reproject from the last real frame (Sec. 3.3, last paragraph)
 
 Pass resolutions and cameras live in device buffers with fixed addresses, so
@@ -29,7 +31,7 @@ def _i32(vals, device):
 class Renderer:
     def __init__(self, verts, rgba8, W, H, params=None, x_dtype=sn.F32, mlp=None,
                  pair_capacity=None, device="cuda", base_tile=None, fused=False,
-                 persistent=False, tuning=None, merge_scale2=1.0, merge_scale3=1.0):
+                 persistent=False, tuning=None, merge_scale2=1.0, merge_scale3=1.0, leaf=False):
         self.device = device
         sn.preload(torch.device(device).index)
         self.W, self.H = int(W), int(H)
@@ -55,6 +57,11 @@ class Renderer:
         self.merge_scale3 = float(merge_scale3)
         if self.fused and x_dtype != sn.BF16:
             raise ValueError("the fused resolve runs the BF16 tensor-core MLP")
+        # leaf: passes 2 and 3 per quadtree leaf (Eq. 2 at the leaf's level)
+        # instead of one scale per frame; runs the fused resolve
+        self.leaf = bool(leaf)
+        if self.leaf and not self.fused:
+            raise ValueError("the per-leaf frame runs the fused resolve (fused=True or 'fp8')")
         cap = pair_capacity if pair_capacity is not None else max(1 << 20, 96 * self.T)
         self.bins = [sn.BinsBuffer(self.W, self.H, self.T, cap, device) for _ in range(3)]
         P = self.P
@@ -82,6 +89,8 @@ class Renderer:
         self.n_tiles = math.ceil(self.W / B) * math.ceil(self.H / B)
         self.mask = [torch.zeros(self.n_tiles, **i32), torch.zeros(self.n_tiles, **i32)]
         self.qt_ws = torch.zeros(sn.quadtree_ws_bytes(self.W, self.H, B), dtype=torch.uint8, device=device)
+        if self.leaf:
+            self._init_leaf(cap)
         self.mlp_tensors = None
         if mlp is not None:
             self.set_mlp(mlp)
@@ -92,6 +101,39 @@ class Renderer:
         self.vp64_prev = torch.zeros(16, dtype=torch.float64, device=device)
         self.vp64_cur = torch.zeros(16, dtype=torch.float64, device=device)
         self.reproj_ws = torch.zeros(sn.REPROJECT_WS_BYTES, dtype=torch.uint8, device=device)
+
+    def _init_leaf(self, cap):
+        """Targets of the per-leaf plan: target 0 is the full resolution (its
+        bins and planes are those of pass 1 and the full-size pass 2 / 3
+        planes); the others get their own bins and planes.  The masks start
+        fully split (every leaf at level 3), so the first frame runs passes 2
+        and 3 at the scale of the finest leaves."""
+        dev = self.device
+        self.plan = sn.leaf_plan(self.W, self.H, self.params)
+        sizes = self.plan.sizes()
+        t2, t3 = set(self.plan.targets(2)), set(self.plan.targets(3))
+        self.leaf_sizes = [_i32([w, h], dev) for w, h in sizes]
+        self.leaf_bins = [self.bins[0]] + [sn.BinsBuffer(w, h, self.T, cap, dev) for w, h in sizes[1:]]
+        self.leaf_layers = []
+        for k, (w, h) in enumerate(sizes):
+            if k == 0:
+                d = dict(self.l1)
+                if 0 in t2:
+                    d["id2"] = self.l2["id2"]
+                if 0 in t3:
+                    d.update(self.l3)
+            else:
+                n = w * h
+                d = {}
+                if k in t2:
+                    d["id2"] = torch.full((n,), -1, dtype=torch.int32, device=dev)
+                if k in t3:
+                    d.update(n=torch.zeros(n, dtype=torch.int32, device=dev),
+                             tail=torch.zeros(4 * n, dtype=torch.int32, device=dev),
+                             t_tail=torch.ones(n, dtype=torch.float32, device=dev))
+            self.leaf_layers.append(d)
+        self.leaf_ws = torch.zeros(sn.leaf_ws_bytes(self.plan), dtype=torch.uint8, device=dev)
+        self.mask[0].fill_((1 << 21) - 1)
 
     # -- inputs -------------------------------------------------------------
     def set_mlp(self, w: dict):
@@ -127,9 +169,31 @@ class Renderer:
         for _, fn in self.plain_stages(stream):
             fn()
 
+    def leaf_stages(self, stream=None, update_tiles=True):
+        """The stages of one real frame with per-leaf pass resolution."""
+        def raster():
+            sn.raster_passes(self.scene, [(self.vp, self.leaf_sizes[k], w, h, self.leaf_bins[k], None)
+                                          for k, (w, h) in enumerate(self.plan.sizes())],
+                             self.status, stream)
+
+        st = [("raster", raster),
+              ("passes", lambda: sn.geometry_passes_leaf(self.scene, self.plan, self.leaf_bins,
+                                                         self.leaf_layers, self.mask[0], self.leaf_ws,
+                                                         self.tuning, self.status, stream)),
+              ("resolve", lambda: sn.resolve_leaf(self.scene, self.plan, self.leaf_layers, self.mask[0],
+                                                  self.params, self.mlp,
+                                                  sn.E4M3 if self.fused_fp8 else sn.BF16, self.rgba32f,
+                                                  self.rgba8_out, self.status, stream))]
+        if update_tiles:
+            st.append(("quadtree", lambda: self.update_tiles(stream)))
+        return st
+
     def star_stages(self, stream=None, update_tiles=True):
         """The stages of one real STAR-NT frame as (name, callable) pairs:
-        pass 1 at full resolution, passes 2 and 3 at the device-held sizes."""
+        pass 1 at full resolution, passes 2 and 3 at the device-held sizes
+        (or per leaf, for a per-leaf renderer)."""
+        if self.leaf:
+            return self.leaf_stages(stream, update_tiles)
         b1, b2, b3 = self.bins
 
         def raster():

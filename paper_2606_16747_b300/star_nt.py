@@ -17,7 +17,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libstar_nt.so")
 
 OK, ERR_ARG, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = range(6)
-F32, BF16 = 0, 1
+F32, BF16, E4M3 = 0, 1, 2
+LEAF_MAX_TARGETS = 9
 
 # every entry point declared in include/star_nt.h
 EXPORTS = ("star_nt_version", "star_nt_status_string", "star_nt_default_params",
@@ -27,7 +28,8 @@ EXPORTS = ("star_nt_version", "star_nt_status_string", "star_nt_default_params",
            "star_nt_geometry_pass_merged", "star_nt_abuffer", "star_nt_train_ws_bytes",
            "star_nt_mse_grad", "star_nt_mlp_backward", "star_nt_adam", "star_nt_raster_passes",
            "star_nt_resolve", "star_nt_geometry_passes", "star_nt_resolve_fp8", "star_nt_preload",
-           "star_nt_unsorted_over", "star_nt_wboit", "star_nt_wmse_grad")
+           "star_nt_unsorted_over", "star_nt_wboit", "star_nt_wmse_grad", "star_nt_leaf_plan_make",
+           "star_nt_leaf_ws_bytes", "star_nt_geometry_passes_leaf", "star_nt_resolve_leaf")
 
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
@@ -74,6 +76,18 @@ class Mlp(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("block_w", _I32), ("ctas_per_sm", _I32)]
+
+
+class LeafPlan(ctypes.Structure):
+    _fields_ = [("W", _I32), ("H", _I32), ("base_tile", _I32), ("n_targets", _I32),
+                ("size", (_I32 * 2) * LEAF_MAX_TARGETS), ("target_of", (_I32 * 4) * 2)]
+
+    def sizes(self):
+        return [(self.size[k][0], self.size[k][1]) for k in range(self.n_targets)]
+
+    def targets(self, p):
+        """Target index of pass p (2 or 3) at levels 0..3."""
+        return [self.target_of[p - 2][l] for l in range(4)]
 
 
 class PassState(ctypes.Structure):
@@ -135,6 +149,14 @@ def lib():
         L.star_nt_abuffer.argtypes = [ctypes.POINTER(Frags), _P, _I32, _I32, _P, _P, _P, _P]
         L.star_nt_unsorted_over.argtypes = [ctypes.POINTER(Frags), _P, _I32, _I32, _P, _P, _P]
         L.star_nt_wboit.argtypes = [ctypes.POINTER(Bins), ctypes.c_float, ctypes.c_float, _P, _P, _P, _P]
+        L.star_nt_leaf_plan_make.argtypes = [_I32, _I32, ctypes.POINTER(Params), ctypes.POINTER(LeafPlan)]
+        L.star_nt_leaf_ws_bytes.argtypes = [ctypes.POINTER(LeafPlan), ctypes.POINTER(ctypes.c_size_t)]
+        L.star_nt_geometry_passes_leaf.argtypes = [ctypes.POINTER(Scene), ctypes.POINTER(LeafPlan),
+                                                   ctypes.POINTER(Bins), ctypes.POINTER(Layers), _P, _P,
+                                                   ctypes.c_size_t, ctypes.POINTER(Tuning), _P, _P]
+        L.star_nt_resolve_leaf.argtypes = [ctypes.POINTER(Scene), ctypes.POINTER(LeafPlan),
+                                           ctypes.POINTER(Layers), _P, ctypes.POINTER(Params),
+                                           ctypes.POINTER(Mlp), _I32, _P, _P, _P, _P]
         L.star_nt_train_ws_bytes.argtypes = [_I64]
         L.star_nt_train_ws_bytes.restype = ctypes.c_size_t
         L.star_nt_mse_grad.argtypes = [_P, _P, _I64, _P, _P, _P, ctypes.c_size_t, _P]
@@ -334,6 +356,43 @@ def quadtree(rgba8, id1, W, H, params: Params, mask_prev, mask_out, state, ws, s
     _check("star_nt_quadtree", lib().star_nt_quadtree(_ptr(rgba8), _ptr(id1), W, H, ctypes.byref(params),
                                                       _ptr(mask_prev), _ptr(mask_out), _ptr(state),
                                                       _ptr(ws), ws.numel(), _stream(stream)))
+
+
+# ---------------------------------------------------------------------------
+# per-leaf pass resolution
+
+def leaf_plan(W, H, params: Params) -> LeafPlan:
+    p = LeafPlan()
+    _check("star_nt_leaf_plan_make", lib().star_nt_leaf_plan_make(W, H, ctypes.byref(params), ctypes.byref(p)))
+    return p
+
+
+def leaf_ws_bytes(plan: LeafPlan) -> int:
+    n = ctypes.c_size_t()
+    _check("star_nt_leaf_ws_bytes", lib().star_nt_leaf_ws_bytes(ctypes.byref(plan), ctypes.byref(n)))
+    return n.value
+
+
+def _layers_array(layers):
+    return (Layers * len(layers))(*[layers_struct(l) for l in layers])
+
+
+def geometry_passes_leaf(scene: Scene, plan: LeafPlan, bins, layers, masks, ws, tuning=None,
+                         status=None, stream=None):
+    """bins, layers: one per plan target (BinsBuffer, dict of planes)."""
+    b = (Bins * len(bins))(*[x.c for x in bins])
+    t = Tuning(*tuning) if tuning is not None else None
+    _check("star_nt_geometry_passes_leaf", lib().star_nt_geometry_passes_leaf(
+        ctypes.byref(scene), ctypes.byref(plan), b, _layers_array(layers), _ptr(masks), _ptr(ws),
+        ws.numel(), ctypes.byref(t) if t is not None else None, _ptr(status), _stream(stream)))
+
+
+def resolve_leaf(scene: Scene, plan: LeafPlan, layers, masks, params: Params, w: Mlp, mlp_type=BF16,
+                 rgba32f=None, rgba8=None, status=None, stream=None):
+    _check("star_nt_resolve_leaf", lib().star_nt_resolve_leaf(
+        ctypes.byref(scene), ctypes.byref(plan), _layers_array(layers), _ptr(masks),
+        ctypes.byref(params), ctypes.byref(w), int(mlp_type), _ptr(rgba32f), _ptr(rgba8), _ptr(status),
+        _stream(stream)))
 
 
 REPROJECT_WS_BYTES = 64

@@ -81,3 +81,40 @@ def test_bad_arguments_rejected_before_launch(sn):
     assert L.star_nt_quadtree(16, 16, 64, 64, ctypes.byref(p), 16, 16, 16, 272, 1 << 20, None) == sn.ERR_ARG  # ws alignment
     p.tau_merge = p.tau_split + 1.0
     assert L.star_nt_quadtree(16, 16, 64, 64, ctypes.byref(p), 16, 32, 16, 256, 1 << 20, None) == sn.ERR_ARG
+
+
+@pytest.mark.parametrize("W,H,d2,d3,B", [(1920, 1080, 2.2, 3.0, 16), (3840, 2160, 2.2, 3.0, 64),
+                                         (333, 197, 1.7, 2.6, 16), (96, 64, 0.0, 5.0, 64)])
+def test_leaf_plan_matches_oracle_sizes(sn, orc, W, H, d2, d3, B):
+    """The per-leaf plan (host code of the library) lists every (pass, level)
+    size the oracle's Eq. 2 gives, each distinct size once, full size first."""
+    p = sn.default_params(delta2=d2, delta3=d3, base_tile=B)
+    plan = sn.leaf_plan(W, H, p)
+    sizes = plan.sizes()
+    assert sizes[0] == (W, H) and len(set(sizes)) == len(sizes) == plan.n_targets
+    ref = orc.leaf_sizes(W, H, d2, d3)
+    for q in (2, 3):
+        for l, k in enumerate(plan.targets(q)):
+            assert sizes[k] == ref[(q, l)]
+    assert set(sizes) == {(W, H)} | set(ref.values())
+    assert sn.leaf_ws_bytes(plan) % 256 == 0
+
+
+def test_leaf_arguments_rejected(sn):
+    L = sn.lib()
+    p = sn.default_params(base_tile=32)
+    plan = sn.LeafPlan()
+    assert L.star_nt_leaf_plan_make(64, 64, ctypes.byref(p), ctypes.byref(plan)) == sn.ERR_ARG
+    plan = sn.leaf_plan(64, 64, sn.default_params())
+    n = ctypes.c_size_t()
+    bad = sn.LeafPlan.from_buffer_copy(plan)
+    bad.size[1][0] = 15                      # below a quarter of the width
+    assert L.star_nt_leaf_ws_bytes(ctypes.byref(bad), ctypes.byref(n)) == sn.ERR_ARG
+    bad = sn.LeafPlan.from_buffer_copy(plan)
+    bad.target_of[1][2] = bad.n_targets      # unlisted target
+    assert L.star_nt_leaf_ws_bytes(ctypes.byref(bad), ctypes.byref(n)) == sn.ERR_ARG
+    sc = sn.Scene(16, 16, 5)
+    assert L.star_nt_geometry_passes_leaf(ctypes.byref(sc), ctypes.byref(plan), None, None, 16, 256, 1 << 20,
+                                          None, None, None) == sn.ERR_ARG
+    assert L.star_nt_resolve_leaf(ctypes.byref(sc), ctypes.byref(plan), None, 16, None, None, 1, None, None,
+                                  None, None) == sn.ERR_ARG
