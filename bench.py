@@ -202,7 +202,7 @@ def run_ours(args, rank, world):
     star.check_status()
     state = star.pass_state()
 
-    psnr_measured = quality(sn, star, plain, W, H, cams, step)
+    q_step = step
     step += 1
     # per-stage times: each stage graph replayed REPS times back to back (the
     # host enqueues faster than a stage runs, so the device never waits) after
@@ -240,6 +240,67 @@ def run_ours(args, rank, world):
         star.merge_scale2 = args.merge_scale2
         star.check_status()
 
+    # the per-leaf variant: passes 2 and 3 at the Eq. 2 scale of each pixel's
+    # own leaf level, on the same cameras
+    leaf = None
+    leaf_info = None
+    if star.fused and not args.no_leaf:
+        leaf = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=x_dtype, base_tile=args.base_tile,
+                        fused=fused_kind, leaf=True)
+        leaf.interp_float = False
+
+        def set_leaf_cams(k):
+            leaf.set_cameras(vp32[2 * k], vp64[2 * k], vp64[2 * k + 1])
+
+        for k in range(4):
+            set_leaf_cams(k)
+            leaf.step()
+        leaf_tuned = None
+        if not args.no_tune:
+            from paper_2606_16747_b300 import autotune
+            leaf_tuned = autotune.tune(leaf)
+            leaf.tuning = (leaf_tuned["block_w"], leaf_tuned["ctas_per_sm"])
+        g_leaf = leaf.capture(leaf.step)
+        lstep = 4
+        for _ in range(args.warmup):
+            set_leaf_cams(lstep)
+            g_leaf.replay()
+            lstep += 1
+        ev = []
+        for _ in range(args.steps):
+            flush.fill_(1)
+            set_leaf_cams(lstep)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g_leaf.replay()
+            e1.record()
+            ev.append((e0, e1))
+            lstep += 1
+        torch.cuda.synchronize()
+        leaf.check_status()
+        leaf_ms = float(np.mean([a.elapsed_time(b) for a, b in ev])) / 2.0
+        active = leaf_active_tiles(leaf)
+        leaf_stage_ms = {}
+        for name, fn in leaf.star_stages() + [("reproject", leaf.interp_frame)]:
+            g = leaf.capture(fn)
+            g.replay()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(STAGE_REPS):
+                g.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            leaf_stage_ms[name] = round(e0.elapsed_time(e1) / STAGE_REPS, 5)
+        leaf.check_status()
+        leaf_info = {"ms_per_frame": round(leaf_ms, 5), "stages_ms": leaf_stage_ms,
+                     "targets": [list(t) for t in leaf.plan.sizes()],
+                     "pass2_target_by_level": leaf.plan.targets(2),
+                     "pass3_target_by_level": leaf.plan.targets(3),
+                     "active_tile_fraction": active, "pass_tuning": leaf_tuned,
+                     "leaf_level_area_fraction": leaf_level_fractions(leaf),
+                     "note": "Eq. 2 per quadtree leaf (scene index replaced by the leaf level); "
+                             "same cameras, same step structure (real + interpolated frame)"}
+
     # plain full-resolution FP32 pipeline on the same scene and cameras
     plain.set_cameras(vp32[0])
     g_plain = plain.capture(plain.plain_frame)
@@ -274,6 +335,8 @@ def run_ours(args, rank, world):
         if k >= args.warmup:
             wboit_ms.append(e0.elapsed_time(e1))
     plain.check_status()
+
+    psnr_measured = quality(sn, star, plain, W, H, cams, q_step, leaf)
 
     # end to end through the public API: host inputs in, frames out, every step
     e2e = end_to_end(sn, torch, sc, w, x_dtype, W, H, cams, args, star.tuning)
@@ -349,6 +412,7 @@ def run_ours(args, rank, world):
                      "peak_source": f"{N_SM} SM x {ALU_LANES_PER_SM} lanes x sm_max_mhz ({peaks_kind})",
                      "ops_per_fragment": OPS_PER_FRAGMENT, "launch_ms": round(dom_ms, 5)},
     }
+    line["per_leaf"] = leaf_info
     line["psnr_db_vs_exact_abuffer"] = psnr["psnr_db"]
     line["quality"] = {"mse_vs_exact_abuffer": psnr["mse"],
                        "error_reduction_vs_unsorted_pct": psnr["error_reduction_vs_unsorted_pct"],
@@ -356,6 +420,34 @@ def run_ours(args, rank, world):
                                "steps; unsorted_over = naive blending in submission order (E_random "
                                "of the Q measure); wboit = weighted blended OIT, one pass"}
     return line
+
+
+def leaf_active_tiles(r):
+    """Per plan target: the fraction of its tiles that ran pass 2 and/or 3 in
+    the last frame (target 0 always runs pass 1)."""
+    modes = r.leaf_ws.cpu().numpy()
+    out, o = [], 0
+    for w, h in r.plan.sizes():
+        n = ((w + 15) // 16) * ((h + 15) // 16)
+        out.append(round(float(np.mean(modes[o:o + n] != 0)), 4))
+        o += n
+    return out
+
+
+def leaf_level_fractions(r):
+    """Fraction of the base tiles' area per leaf level under the current
+    masks (bit 0 root split, bits 1..4 level-1 splits, bits 5..20 level-2)."""
+    m = r.mask[0].cpu().numpy().view(np.uint32).astype(np.int64)
+    root = (m & 1) != 0
+    a = [float(np.sum(~root)), 0.0, 0.0, 0.0]
+    for c1 in range(4):
+        s1 = root & (((m >> (1 + c1)) & 1) != 0)
+        a[1] += float(np.sum(root & ~s1)) / 4
+        for c2 in range(4):
+            s2 = s1 & (((m >> (5 + 4 * c1 + c2)) & 1) != 0)
+            a[2] += float(np.sum(s1 & ~s2)) / 16
+            a[3] += float(np.sum(s2)) / 16
+    return [round(v / m.size, 4) for v in a]
 
 
 def fragment_count(sn, r, vp, W, H, size=None):
@@ -446,17 +538,22 @@ def psnr_db(a, b):
     return round(10.0 * math.log10(1.0 / max(mse, 1e-30)), 3)
 
 
-def quality(sn, star, plain, W, H, cams, k):
+def quality(sn, star, plain, W, H, cams, k, leaf=None):
     """PSNR against the exact A-buffer: STAR-NT real frame 2k and interpolated
-    frame 2k + 1, and the plain pipeline at frame 2k (after the timed runs)."""
+    frame 2k + 1 (global and, when given, per-leaf pass scales), and the plain
+    pipeline at frame 2k (after the timed runs)."""
     import torch
-    star.set_cameras(cams[2 * k].vp32, cams[2 * k].vp64.reshape(16), cams[2 * k + 1].vp64.reshape(16))
-    keep = star.interp_float
-    star.interp_float = True
-    star.step()
-    star.interp_float = keep
-    real = star.rgba32f.view(-1, 4)[:, :3].clone()
-    interp = star.interp_out.view(-1, 4)[:, :3].clone()
+
+    def star_pair(r):
+        r.set_cameras(cams[2 * k].vp32, cams[2 * k].vp64.reshape(16), cams[2 * k + 1].vp64.reshape(16))
+        keep = r.interp_float
+        r.interp_float = True
+        r.step()
+        r.interp_float = keep
+        return r.rgba32f.view(-1, 4)[:, :3].clone(), r.interp_out.view(-1, 4)[:, :3].clone()
+
+    real, interp = star_pair(star)
+    leaf_pair = star_pair(leaf) if leaf is not None else None
     plain.set_cameras(cams[2 * k].vp32)
     plain.plain_frame()
     pl = plain.rgba32f.view(-1, 4)[:, :3].clone()
@@ -474,6 +571,9 @@ def quality(sn, star, plain, W, H, cams, k):
     ex_interp = exact_frame(sn, plain, cams[2 * k + 1].vp32, W, H)
     frames = {"star_real": (real, ex_real), "star_interpolated": (interp, ex_interp),
               "plain": (pl, ex_real), "wboit": (wb, ex_real), "unsorted_over": (un, ex_real)}
+    if leaf_pair is not None:
+        frames["leaf_real"] = (leaf_pair[0], ex_real)
+        frames["leaf_interpolated"] = (leaf_pair[1], ex_interp)
     mse = {k: float(torch.mean((a - b) ** 2).item()) for k, (a, b) in frames.items()}
     e_random = mse["unsorted_over"]
     return {"psnr_db": {k: round(10.0 * math.log10(1.0 / max(v, 1e-30)), 3) for k, v in mse.items()},
@@ -561,6 +661,7 @@ def main():
     ap.add_argument("--unfused", dest="fused", action="store_false",
                     help="separate upscale/features, MLP and composite kernels")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-leaf", action="store_true", help="skip the per-leaf pass-resolution variant")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))

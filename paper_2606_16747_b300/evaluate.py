@@ -1,6 +1,7 @@
 """Quality of a camera sequence against the exact A-buffer (the evaluation of
 Sec. 4 on the synthetic workloads): every frame of an orbit rendered by
-STAR-NT (real and interpolated frames alternating), by the plain
+STAR-NT (real and interpolated frames alternating; pass scales from Eq. 2
+over the frame, and per quadtree leaf), by the plain
 full-resolution neural pipeline, by weighted blended OIT and by naive
 unsorted blending, each compared with the exact A-buffer of its camera.
 
@@ -48,6 +49,18 @@ def exact_and_frags(r: Renderer, vp32):
     return out.view(P, 4)[:, :3].clone(), frags
 
 
+def leaf_active(r: Renderer):
+    """Per target of a per-leaf renderer: the fraction of its tiles that ran
+    pass 2 and/or 3 in the last frame."""
+    modes = r.leaf_ws.cpu().numpy()
+    out, o = [], 0
+    for w, h in r.plan.sizes():
+        n = ((w + 15) // 16) * ((h + 15) // 16)
+        out.append(float(np.mean(modes[o:o + n] != 0)))
+        o += n
+    return out
+
+
 def mse(a, b) -> float:
     return float(torch.mean((a - b) ** 2).item())
 
@@ -67,17 +80,26 @@ def main(argv=None):
     star = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=sn.BF16,
                     fused="fp8" if args.mlp == "fp8" else True, persistent=True,
                     base_tile=args.base_tile, merge_scale2=args.merge_scale2)
+    leaf = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=sn.BF16,
+                    fused="fp8" if args.mlp == "fp8" else True, base_tile=args.base_tile, leaf=True)
     ref = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=sn.F32)
     cams = scenes.orbit_cameras(W, H, args.frames + 1)
     bg = tuple(ref.params.bg)
-    err = {k: [] for k in ("star", "star_real", "star_interpolated", "plain", "wboit", "unsorted_over")}
+    err = {k: [] for k in ("star", "star_real", "star_interpolated", "leaf", "leaf_real", "leaf_interpolated",
+                           "plain", "wboit", "unsorted_over")}
+    active = []
     for f in range(0, args.frames, 2):   # real frame f, interpolated frame f + 1
         c_real, c_int = cams[f], cams[f + 1]
         star.set_cameras(c_real.vp32, c_real.vp64.reshape(16), c_int.vp64.reshape(16))
         star.step()
+        leaf.set_cameras(c_real.vp32, c_real.vp64.reshape(16), c_int.vp64.reshape(16))
+        leaf.step()
         torch.cuda.synchronize()
         real = star.rgba32f.view(-1, 4)[:, :3].clone()
         interp = star.interp_out.view(-1, 4)[:, :3].clone()
+        l_real = leaf.rgba32f.view(-1, 4)[:, :3].clone()
+        l_interp = leaf.interp_out.view(-1, 4)[:, :3].clone()
+        active.append(leaf_active(leaf))
         ex, frags = exact_and_frags(ref, c_real.vp32)
         ref.set_cameras(c_real.vp32)
         ref.plain_frame()
@@ -91,6 +113,9 @@ def main(argv=None):
         e_real = mse(real, ex)
         err["star_real"].append(e_real)
         err["star"].append(e_real)
+        e_lr = mse(l_real, ex)
+        err["leaf_real"].append(e_lr)
+        err["leaf"].append(e_lr)
         err["plain"].append(mse(plain, ex))
         err["wboit"].append(mse(wb.view(-1, 4)[:, :3], ex))
         err["unsorted_over"].append(mse(un.view(-1, 4)[:, :3], ex))
@@ -99,7 +124,11 @@ def main(argv=None):
             e_int = mse(interp, ex_i)
             err["star_interpolated"].append(e_int)
             err["star"].append(e_int)
+            e_li = mse(l_interp, ex_i)
+            err["leaf_interpolated"].append(e_li)
+            err["leaf"].append(e_li)
     star.check_status()
+    leaf.check_status()
     ref.check_status()
     mean = {k: float(np.mean(v)) for k, v in err.items()}
     e_rand = mean["unsorted_over"]
@@ -111,7 +140,9 @@ def main(argv=None):
                                           for k, v in mean.items() if k != "wboit"},
            "error_reduction_vs_unsorted_pct": {k: round(100 * (e_rand - v) / e_rand, 2)
                                                for k, v in mean.items() if k != "unsorted_over"},
-           "final_pass_state": star.pass_state()}
+           "final_pass_state": star.pass_state(),
+           "leaf_targets": [list(t) for t in leaf.plan.sizes()],
+           "leaf_active_tile_fraction_mean": [round(float(v), 4) for v in np.mean(np.array(active), axis=0)]}
     print(json.dumps(out))
 
 
