@@ -651,7 +651,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="hd", choices=["hd", "uhd", "small"])
     ap.add_argument("--mlp", default="bf16", choices=["bf16", "fp8", "f32"])
-    ap.add_argument("--base-tile", type=int, default=16)
+    ap.add_argument("--base-tile", type=int, default=64, choices=[16, 64],
+                    help="quadtree base tile (64: leaves of 8 to 64 pixels)")
     ap.add_argument("--separate-passes", dest="persistent", action="store_false",
                     help="three geometry-pass launches instead of one persistent launch")
     ap.add_argument("--no-tune", action="store_true", help="skip the pass-launch autotuner")

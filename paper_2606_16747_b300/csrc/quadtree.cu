@@ -220,42 +220,64 @@ __device__ __forceinline__ void count_leaves(uint32_t m, unsigned long long occ,
 }
 
 // The last relaxation (or a copy), then the histogram of occupied leaves; the
-// last block to finish applies Eq. 2 and writes the state.  A warp per tile
-// reads the tile's pass-1 ids for the occupancy; lane 0 does the rest.
-template <bool RELAX>
-__global__ void __launch_bounds__(256) k_qt_last(const int32_t *__restrict__ id1, int W, int H, int B,
+// last block to finish applies Eq. 2 and writes the state.  The tile's
+// pass-1 ids give the occupancy of its 64 level-3 cells (B/8 pixels wide):
+// for 16-pixel tiles a warp per tile (8 pixels per lane), for 64-pixel tiles
+// a block of 256 threads per tile (16 pixels per thread; every warp reads
+// 32 consecutive pixels of a row).  One thread per tile does the rest.
+template <bool RELAX, int B>
+__global__ void __launch_bounds__(256) k_qt_last(const int32_t *__restrict__ id1, int W, int H,
                                                  int tiles_x, int tiles_y,
                                                  const uint32_t *__restrict__ min,
                                                  uint32_t *__restrict__ mout,
                                                  uint32_t *__restrict__ hist, uint32_t *ticket,
                                                  double delta2, double delta3,
                                                  star_nt_pass_state *state) {
+  static_assert(B == 16 || B == 64, "base tile");
+  constexpr int kTilesPerBlock = B == 16 ? 8 : 1;
+  constexpr int kThreadsPerTile = 256 / kTilesPerBlock;
+  constexpr int kCs = B / 8;  // cell side
   __shared__ uint32_t s_hist[4];
+  __shared__ uint32_t s_occ[2];
   if (threadIdx.x < 4) s_hist[threadIdx.x] = 0u;
+  if (threadIdx.x < 2) s_occ[threadIdx.x] = 0u;
   __syncthreads();
-  const int tile = blockIdx.x * 8 + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (tile < tiles_x * tiles_y) {
-    const int tx = tile % tiles_x, ty = tile / tiles_x;
-    // occupancy of the tile's 64 level-3 cells (B/8 pixels wide)
-    const int cs = B / 8;
-    unsigned long long occ = 0;
-    for (int k = lane; k < B * B; k += 32) {
+  const int tile = blockIdx.x * kTilesPerBlock + (int)threadIdx.x / kThreadsPerTile;
+  const int t = (int)threadIdx.x % kThreadsPerTile;
+  const bool valid = tile < tiles_x * tiles_y;
+  const int tx = valid ? tile % tiles_x : 0, ty = valid ? tile / tiles_x : 0;
+  unsigned long long occ = 0;
+  if (valid) {
+#pragma unroll
+    for (int i = 0; i < B * B / kThreadsPerTile; ++i) {
+      const int k = i * kThreadsPerTile + t;
       const int lx = k % B, ly = k / B;
       const int x = tx * B + lx, y = ty * B + ly;
-      if (x < W && y < H && id1[(size_t)y * W + x] >= 0) occ |= 1ull << ((ly / cs) * 8 + (lx / cs));
+      if (x < W && y < H && __ldg(id1 + (size_t)y * W + x) >= 0)
+        occ |= 1ull << ((ly / kCs) * 8 + (lx / kCs));
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) occ |= __shfl_xor_sync(0xffffffffu, occ, o);
-    if (lane == 0) {
-      const uint32_t m = RELAX ? relax_tile(min, tile, tx, ty, tiles_x, tiles_y) : min[tile];
-      mout[tile] = m;
-      uint32_t cnt[4] = {0u, 0u, 0u, 0u};
-      count_leaves(m, occ, cnt);
-#pragma unroll
-      for (int l = 0; l < 4; ++l)
-        if (cnt[l]) atomicAdd(&s_hist[l], cnt[l]);
+  }
+  // OR over the tile's threads (whole warps: a 16-pixel tile is one warp)
+  uint32_t lo = __reduce_or_sync(0xffffffffu, (uint32_t)occ);
+  uint32_t hi = __reduce_or_sync(0xffffffffu, (uint32_t)(occ >> 32));
+  if (B == 64) {
+    if ((threadIdx.x & 31) == 0) {
+      if (lo) atomicOr(&s_occ[0], lo);
+      if (hi) atomicOr(&s_occ[1], hi);
     }
+    __syncthreads();
+    lo = s_occ[0];
+    hi = s_occ[1];
+  }
+  occ = ((unsigned long long)hi << 32) | lo;
+  if (valid && t == 0) {
+    const uint32_t m = RELAX ? relax_tile(min, tile, tx, ty, tiles_x, tiles_y) : min[tile];
+    mout[tile] = m;
+    uint32_t cnt[4] = {0u, 0u, 0u, 0u};
+    count_leaves(m, occ, cnt);
+#pragma unroll
+    for (int l = 0; l < 4; ++l)
+      if (cnt[l]) atomicAdd(&s_hist[l], cnt[l]);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -334,12 +356,17 @@ extern "C" star_nt_status star_nt_quadtree(const uint32_t *rgba8, const int32_t 
   }
   // the last relaxation (a plain copy when there is none), the histogram of
   // occupied leaves and Eq. 2, in one launch
-  if (iters > 0)
-    k_qt_last<true><<<wblocks, 256, 0, st>>>(id1, W, H, B, L.tiles_x, L.tiles_y, src, mask_out, hist,
-                                             ticket, params->delta2, params->delta3, state);
-  else
-    k_qt_last<false><<<wblocks, 256, 0, st>>>(id1, W, H, B, L.tiles_x, L.tiles_y, src, mask_out, hist,
-                                              ticket, params->delta2, params->delta3, state);
+  auto last = [&](auto kern, int blocks) {
+    kern<<<blocks, 256, 0, st>>>(id1, W, H, L.tiles_x, L.tiles_y, src, mask_out, hist, ticket,
+                                 params->delta2, params->delta3, state);
+  };
+  if (B == 16) {
+    if (iters > 0) last(k_qt_last<true, 16>, wblocks);
+    else last(k_qt_last<false, 16>, wblocks);
+  } else {
+    if (iters > 0) last(k_qt_last<true, 64>, nt);
+    else last(k_qt_last<false, 64>, nt);
+  }
   return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
 }
 
@@ -402,8 +429,10 @@ cudaError_t preload_quadtree() {
   cudaError_t e = cudaSuccess, r;
   if ((r = cudaFuncGetAttributes(&a, k_qt_decide)) != cudaSuccess) e = r;
   if ((r = cudaFuncGetAttributes(&a, k_qt_relax)) != cudaSuccess) e = r;
-  if ((r = cudaFuncGetAttributes(&a, k_qt_last<true>)) != cudaSuccess) e = r;
-  if ((r = cudaFuncGetAttributes(&a, k_qt_last<false>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_qt_last<true, 16>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_qt_last<false, 16>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_qt_last<true, 64>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_qt_last<false, 64>)) != cudaSuccess) e = r;
   return e;
 }
 }  // namespace star

@@ -69,7 +69,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--workload", default="hd", choices=["hd", "uhd", "small"])
     ap.add_argument("--frames", type=int, default=120)
-    ap.add_argument("--base-tile", type=int, default=16, choices=[16, 64])
+    ap.add_argument("--base-tile", type=int, default=64, choices=[16, 64])
     ap.add_argument("--merge-scale2", type=float, default=0.5)
     ap.add_argument("--mlp", default="bf16", choices=["bf16", "fp8"])
     args = ap.parse_args(argv)

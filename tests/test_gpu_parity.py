@@ -374,21 +374,22 @@ def blocky_image(rng, W, H, cell):
 
 @pytest.mark.parametrize("W,H,B,seed", [(200, 136, 16, 0), (1920, 1080, 16, 1), (1920, 1080, 64, 2),
                                         (333, 190, 64, 3)])
-def test_quadtree_bit_exact(orc, sn, W, H, B, seed):
+@pytest.mark.parametrize("iters", [2, 0])
+def test_quadtree_bit_exact(orc, sn, W, H, B, seed, iters):
     rng = np.random.default_rng(seed)
     TX, TY = math.ceil(W / B), math.ceil(H / B)
     img = blocky_image(rng, W, H, B // 4)
     id1 = np.where(rng.random(W * H) < 0.9, 0, -1).astype(np.int32)
     id1[: W * (H // 3)] = -1
     mprev = random_masks(rng, TX * TY)
-    params = sn.default_params(base_tile=B, tau_split=20.0, tau_merge=9.0)
+    params = sn.default_params(base_tile=B, tau_split=20.0, tau_merge=9.0, relax_iters=iters)
     ws = torch.zeros(sn.quadtree_ws_bytes(W, H, B), dtype=torch.uint8, device="cuda")
     mout = torch.zeros(TX * TY, dtype=torch.int32, device="cuda")
     state = torch.zeros(64, dtype=torch.uint8, device="cuda")
     sn.quadtree(dev(img.view(np.int32)), dev(id1), W, H, params, dev(mprev.view(np.int32)), mout,
                 state, ws)
     torch.cuda.synchronize()
-    mo, ho = orc.quadtree(img, id1, W, H, B, 20.0, 9.0, mprev)
+    mo, ho = orc.quadtree(img, id1, W, H, B, 20.0, 9.0, mprev, relax_iters=iters)
     assert np.array_equal(u32(mout), mo)
     st = sn.read_pass_state(state)
     assert st["hist"] == ho.tolist()
