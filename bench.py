@@ -40,8 +40,8 @@ OPS_PER_FRAGMENT = 32     # algorithmic integer/fp operations per fragment (see 
 KERNELS_PER_STEP = 3 + 1 + 1 + 3 + 2
 STAGE_REPS = 20
 # DRAM bytes (read + write) of one k_passes launch at 1080p, from the ncu
-# capture summarised in profiles/passes_hd.md (same kernel build)
-PASSES_DRAM_BYTES = 9361664
+# capture summarised in profiles/passes_hd.md (same kernel build, s3 = 0.68)
+PASSES_DRAM_BYTES = 13958656
 
 
 def load_peaks():
@@ -358,8 +358,12 @@ def run_ours(args, rank, world):
         dom_ms = stage_mean["passes"]
         vp_last = vp32[2 * (step - 1)]
         dom_frags = fragment_count(sn, star, vp_last, W, H)
-        for wp, hp in ((stage_state["W2"], stage_state["H2"]), (stage_state["W3"], stage_state["H3"])):
-            if (wp, hp) != (W, H):
+        # a pass merged into pass 1 shares pass 1's traversal (its fragments are
+        # pass 1's); a separate pass traverses the fragments at its own size
+        merged = [int(star.bins[k].mem[32:36].view(torch.int32).item()) for k in (1, 2)]
+        for (wp, hp), m in zip(((stage_state["W2"], stage_state["H2"]),
+                                (stage_state["W3"], stage_state["H3"])), merged):
+            if not m:
                 dom_frags += fragment_count(sn, star, vp_last, W, H, (wp, hp))
         dom_name = "k_passes (passes 1-3, one persistent launch)"
     else:
@@ -406,9 +410,9 @@ def run_ours(args, rank, world):
         "roofline": {"bound": "alu", "kernel": dom_name, "fragments": int(dom_frags),
                      "achieved": round(achieved, 4), "peak": round(alu_peak, 3), "unit": "Tops/s",
                      "frac": round(achieved / alu_peak, 5),
-                     "traffic": PASSES_DRAM_BYTES if "passes" in stage_mean else None,
+                     "traffic": PASSES_DRAM_BYTES if "passes" in stage_mean and args.workload == "hd" else None,
                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
-                                       "k_passes launch (profiles/passes_hd.md, 1080p orbit step 6)",
+                                       "k_passes launch (profiles/passes_hd.md, 1080p orbit step 6, s3 0.68)",
                      "peak_source": f"{N_SM} SM x {ALU_LANES_PER_SM} lanes x sm_max_mhz ({peaks_kind})",
                      "ops_per_fragment": OPS_PER_FRAGMENT, "launch_ms": round(dom_ms, 5)},
     }

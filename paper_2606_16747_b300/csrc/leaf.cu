@@ -103,14 +103,14 @@ __global__ void __launch_bounds__(256) k_leaf_modes(LeafModeArgs a,
         const int btx = bx0 + i % nbx, bty = by0 + i / nbx;
         const uint32_t m = __ldg(masks + (size_t)bty * a.base_tiles_x + btx);
         const unsigned long long r = rect_cells(x0, x1, y0, y1, btx * B, bty * B, B);
-#pragma unroll
-        for (int l = 0; l < 4; ++l) {
-          if (!(((lv2 | lv3) >> l) & 1u)) continue;
-          if (level_cells(m, l) & r) {
-            n2 |= ((lv2 >> l) & 1u) != 0u;
-            n3 |= ((lv3 >> l) & 1u) != 0u;
-          }
-        }
+        // levels present in the rectangle's cells (one pass over the mask)
+        unsigned long long d2, d3;
+        deep_cells(m, d2, d3);
+        const bool root = (m & 1u) != 0u;
+        const uint32_t present = ((!root && r) ? 1u : 0u) | ((root && (r & ~d2)) ? 2u : 0u) |
+                                 ((r & d2 & ~d3) ? 4u : 0u) | ((r & d3) ? 8u : 0u);
+        n2 |= (present & lv2) != 0u;
+        n3 |= (present & lv3) != 0u;
       }
     }
     n2 = __any_sync(0xffffffffu, n2);

@@ -37,19 +37,6 @@ __device__ __forceinline__ void deep_cells(uint32_t m, unsigned long long &d2, u
   }
 }
 
-// Cells whose leaf is at level l (0..3) under mask m.
-__device__ __forceinline__ unsigned long long level_cells(uint32_t m, int l) {
-  unsigned long long d2, d3;
-  deep_cells(m, d2, d3);
-  const bool root = (m & 1u) != 0u;
-  switch (l) {
-    case 0: return root ? 0ull : ~0ull;
-    case 1: return root ? ~d2 : 0ull;
-    case 2: return d2 & ~d3;
-    default: return d3;
-  }
-}
-
 // Level of the leaf holding pixel (lx, ly) of a base tile of side B.
 __device__ __forceinline__ int leaf_level(uint32_t m, int lx, int ly, int B) {
   if (!(m & 1u)) return 0;

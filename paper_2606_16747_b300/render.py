@@ -1,7 +1,7 @@
 """Render a camera sequence of one of the benchmark's workloads with the
 product configuration (persistent passes, fused tensor-core resolve, pass 2
-merged above half size), without timing: the command to put under a
-profiler.
+merged above half size, 64-pixel quadtree base tiles), or with per-leaf pass
+scales (--leaf), without timing: the command to put under a profiler.
 
     python -m paper_2606_16747_b300.render --workload hd --steps 8
 """
@@ -27,6 +27,8 @@ def main(argv=None):
     ap.add_argument("--mlp", default="bf16", choices=["bf16", "fp8"])
     ap.add_argument("--merge-scale2", type=float, default=0.5)
     ap.add_argument("--block-w", type=int, default=8, choices=[4, 8, 16])
+    ap.add_argument("--base-tile", type=int, default=64, choices=[16, 64])
+    ap.add_argument("--leaf", action="store_true", help="passes 2 and 3 at each leaf's Eq. 2 scale")
     args = ap.parse_args(argv)
     build.build()
     sc = scenes.hd_scene() if args.workload == "hd" else scenes.uhd_scene()
@@ -34,7 +36,8 @@ def main(argv=None):
     w = dict(np.load(os.path.join(HERE, "weights", "tail_mlp.npz")))
     r = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=sn.BF16,
                  fused="fp8" if args.mlp == "fp8" else True, persistent=True,
-                 tuning=(args.block_w, 0), merge_scale2=args.merge_scale2)
+                 tuning=(args.block_w, 0), merge_scale2=args.merge_scale2, base_tile=args.base_tile,
+                 leaf=args.leaf)
     cams = scenes.orbit_cameras(W, H, 2 * args.steps)
     vp32 = torch.tensor(np.stack([c.vp32 for c in cams]), device="cuda")
     vp64 = torch.tensor(np.stack([c.vp64.reshape(16) for c in cams]), device="cuda")
@@ -43,7 +46,10 @@ def main(argv=None):
         r.step()
     torch.cuda.synchronize()
     r.check_status()
-    print("rendered", args.steps, "steps; pass state", r.pass_state())
+    if args.leaf:
+        print("rendered", args.steps, "steps; targets", r.plan.sizes())
+    else:
+        print("rendered", args.steps, "steps; pass state", r.pass_state())
 
 
 if __name__ == "__main__":
