@@ -138,7 +138,7 @@ def run_ours(args, rank, world):
     fused_kind = (args.mlp if args.mlp == "fp8" else True) if args.fused and x_dtype == sn.BF16 else False
     star = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=x_dtype, base_tile=args.base_tile,
                     fused=fused_kind, persistent=args.persistent,
-                    merge_scale2=args.merge_scale2)
+                    merge_scale2=args.merge_scale2, merge_scale3=args.merge_scale3)
     star.interp_float = False   # a display takes the 8-bit interpolated frame
     plain = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=sn.F32)
     n_frames = 2 * (20 + 2 * args.warmup + 2 * args.steps)
@@ -222,10 +222,10 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         stage_ms[name] = [e0.elapsed_time(e1) / STAGE_REPS]
 
-    # the same step with pass 2 at the size Eq. 2 gives (no merge below full size)
+    # the same step with passes 2 and 3 at the sizes Eq. 2 gives (no merge below full size)
     eq2_ms = None
-    if star.merge_scale2 < 1.0:
-        star.merge_scale2 = 1.0
+    if star.merge_scale2 < 1.0 or star.merge_scale3 < 1.0:
+        star.merge_scale2 = star.merge_scale3 = 1.0
         g_eq2 = star.capture(star.step)
         for _ in range(args.warmup):
             set_cams(step)
@@ -237,7 +237,7 @@ def run_ours(args, rank, world):
             step += 1
         torch.cuda.synchronize()
         eq2_ms = float(np.mean([a.elapsed_time(b) for a, b in ev])) / 2.0
-        star.merge_scale2 = args.merge_scale2
+        star.merge_scale2, star.merge_scale3 = args.merge_scale2, args.merge_scale3
         star.check_status()
 
     # the per-leaf variant: passes 2 and 3 at the Eq. 2 scale of each pixel's
@@ -389,6 +389,7 @@ def run_ours(args, rank, world):
                    "resolve": "fused" if star.fused else "separate",
                    "passes": "persistent" if star.persistent else "separate",
                    "pass2_merge_scale": star.merge_scale2,
+                   "pass3_merge_scale": star.merge_scale3,
                    "pass_tuning": tuned,
                    "base_tile": args.base_tile, "l2": "flushed between steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
@@ -396,7 +397,7 @@ def run_ours(args, rank, world):
         "fragments_full_res": int(Fcount),
         "fragments_note": "mean full-resolution fragment count of the timed real frames",
         "eq2_sizes_ms_per_frame": round(eq2_ms, 5) if eq2_ms is not None else None,
-        "eq2_sizes_note": "the same step with pass 2 always at the Eq. 2 size (merge scale 1.0)",
+        "eq2_sizes_note": "the same step with passes 2 and 3 always at their Eq. 2 sizes (merge scales 1.0)",
         "plain_ms_per_frame": round(float(np.mean(plain_ms)), 5),
         "wboit_ms_per_frame": round(float(np.mean(wboit_ms)), 5),
         "speedup_vs_plain": round(float(np.mean(plain_ms)) / ms_frame, 4),
@@ -479,7 +480,7 @@ def end_to_end(sn, torch, sc, w, x_dtype, W, H, cams, args, tuning=None):
     r = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=x_dtype, base_tile=args.base_tile,
                  fused=(args.mlp if args.mlp == "fp8" else True) if args.fused and x_dtype == sn.BF16 else False,
                  persistent=args.persistent, tuning=tuning,
-                 merge_scale2=args.merge_scale2)
+                 merge_scale2=args.merge_scale2, merge_scale3=args.merge_scale3)
     r.interp_float = False      # both frames leave as 8-bit
     hv = torch.from_numpy(np.ascontiguousarray(sc.verts)).pin_memory()
     hc = torch.from_numpy(np.ascontiguousarray(sc.rgba8).view(np.int32)).pin_memory()
@@ -663,6 +664,8 @@ def main():
     ap.add_argument("--merge-scale2", type=float, default=0.5,
                     help="pass 2 at least this fraction of the full size runs inside pass 1 at full "
                          "size (1.0: only at full size, as Eq. 2 sizes it)")
+    ap.add_argument("--merge-scale3", type=float, default=0.7,
+                    help="the same for pass 3 (1.0: only at full size)")
     ap.add_argument("--unfused", dest="fused", action="store_false",
                     help="separate upscale/features, MLP and composite kernels")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -254,7 +254,9 @@ typedef struct {
  * persistent launch (the same results as star_nt_geometry_pass_merged, then
  * modes 2 and 3): CTAs take tiles of pass 1, then pass 2, then pass 3 from
  * a work counter kept in bins1's workspace, so uneven tiles and passes of
- * different sizes share the launch.  bins1..3 must be distinct. */
+ * different sizes share the launch.  bins1..3 must be distinct.  Returns
+ * without work on the device when bins2 is marked resolved (see
+ * star_nt_geometry_passes_resolve). */
 star_nt_status star_nt_geometry_passes(const star_nt_scene *scene, const star_nt_bins *bins1,
                                        const star_nt_bins *bins2, const star_nt_bins *bins3,
                                        const star_nt_layers *layers1,
@@ -312,6 +314,33 @@ star_nt_status star_nt_resolve_fp8(const star_nt_scene *scene, const star_nt_bin
                                    int32_t W, int32_t H, const star_nt_params *params,
                                    const star_nt_mlp *w, float *rgba32f, uint32_t *rgba8,
                                    int32_t *d_status, void *stream);
+
+/* star_nt_geometry_passes_resolve: star_nt_geometry_passes that, when both
+ * reduced passes are merged into pass 1 (their bins marked merged: every pass
+ * at the full resolution), also produces the frame: pass 1's tiles run the
+ * network input, the tail MLP on the tcgen05 tensor cores (bf16 operands,
+ * fp32 accumulation) and the composite of Eq. 4 for their pixels, and write
+ * rgba32f / rgba8 as star_nt_resolve would, bit for bit.  layers1's id1 and z1
+ * are written; the merged passes' planes are not.  bins2's header is then
+ * marked resolved, and a following star_nt_resolve or star_nt_resolve_fp8 on
+ * the same bins returns without work (use star_nt_resolve, not
+ * star_nt_upscale_features, after this call).  With a reduced pass not merged
+ * the call is star_nt_geometry_passes and the frame is left to
+ * star_nt_resolve.  Two launches: the fused one (which returns at once unless
+ * every pass is merged), then star_nt_geometry_passes' (which returns at once
+ * when the first resolved the frame).  params (bg, kappa_n), w and the frame
+ * outputs as star_nt_resolve; other arguments as star_nt_geometry_passes. */
+star_nt_status star_nt_geometry_passes_resolve(const star_nt_scene *scene,
+                                               const star_nt_bins *bins1,
+                                               const star_nt_bins *bins2,
+                                               const star_nt_bins *bins3,
+                                               const star_nt_layers *layers1,
+                                               const star_nt_layers *layers2,
+                                               const star_nt_layers *layers3,
+                                               const star_nt_params *params,
+                                               const star_nt_mlp *w, float *rgba32f,
+                                               uint32_t *rgba8, const star_nt_tuning *tuning,
+                                               int32_t *d_status, void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* star_nt_composite -- Eq. 4: C = C_exact,2 + T_2 f(x) + T_all C_b.          */

@@ -19,13 +19,6 @@ __device__ __forceinline__ void over_rgba8(uint32_t c, float &T, float &r, float
   T *= 1.0f - a;
 }
 
-__device__ __forceinline__ uint32_t to_rgba8(float r, float g, float b) {
-  const uint32_t R = __float2uint_rn(__saturatef(r) * 255.0f);
-  const uint32_t G = __float2uint_rn(__saturatef(g) * 255.0f);
-  const uint32_t B = __float2uint_rn(__saturatef(b) * 255.0f);
-  return R | (G << 8) | (B << 16) | (255u << 24);
-}
-
 // Naive blending: each pixel's fragments composited with "over" in the order
 // a renderer without OIT would submit them, increasing primitive id (the ids
 // of the synthetic scenes are unrelated to depth, so this is a random order).
@@ -105,7 +98,7 @@ __global__ void __launch_bounds__(256) k_wboit(BinsView bv, float znear, float z
   const float b = sb * inv * (1.0f - t) + t * bg2;
   const size_t p = (size_t)tp.py * W + tp.px;
   if (out) out[p] = make_float4(r, g, b, t);
-  if (out8) out8[p] = to_rgba8(r, g, b);
+  if (out8) out8[p] = quantize_rgba8(r, g, b);
 }
 
 }  // namespace star

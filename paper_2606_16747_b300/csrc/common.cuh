@@ -48,7 +48,8 @@ struct __align__(16) BinsHeader {
   int32_t merged;      // 1: the pass runs at full size and is taken over by pass 1
   uint32_t queue;      // work counter of the persistent pass launch (zero between launches)
   uint32_t queue_exit; // CTAs done with the launch (zero between launches)
-  uint32_t pad[5];
+  int32_t resolved;    // 1: the pass launch also produced the frame (pass 1 ran the network)
+  uint32_t pad[4];
 };
 static_assert(sizeof(BinsHeader) == 64, "BinsHeader layout");
 
@@ -121,6 +122,16 @@ inline bool leaf_plan_valid(const star_nt_leaf_plan *p) {
       if (p->target_of[q][l] < 0 || p->target_of[q][l] >= p->n_targets) return false;
   return true;
 }
+
+// 8-bit RGBA of a float colour: round half to even of clamp(c, 0, 1) * 255,
+// alpha 255.
+__device__ __forceinline__ uint32_t quantize_rgba8(float r, float g, float b) {
+  const uint32_t R = __float2uint_rn(__saturatef(r) * 255.0f);
+  const uint32_t G = __float2uint_rn(__saturatef(g) * 255.0f);
+  const uint32_t B = __float2uint_rn(__saturatef(b) * 255.0f);
+  return R | (G << 8) | (B << 16) | (255u << 24);
+}
+__device__ __forceinline__ uint32_t quantize_rgba8(float4 c) { return quantize_rgba8(c.x, c.y, c.z); }
 
 // First error wins.
 __device__ inline void raise_status(int32_t *status, int32_t code) {

@@ -102,8 +102,10 @@ struct FeatIn {
   const uint4 *tail3;
   const float *t3;
 
-  __device__ __forceinline__ bool rejected() const {  // a pass was rejected by its raster
-    return hd2->n_pixels <= 0 || hd3->n_pixels <= 0;
+  // nothing to do: a pass was rejected by its raster, or the pass launch
+  // already produced the frame
+  __device__ __forceinline__ bool rejected() const {
+    return hd2->n_pixels <= 0 || hd3->n_pixels <= 0 || hd2->resolved != 0;
   }
 };
 
@@ -148,7 +150,10 @@ __device__ __forceinline__ void pixel_features_at(
   q2[2] = (size_t)ay2.i1 * W2 + ax2.i0; q2[3] = (size_t)ay2.i1 * W2 + ax2.i1;
   q3[0] = (size_t)ay3.i0 * W3 + ax3.i0; q3[1] = (size_t)ay3.i0 * W3 + ax3.i1;
   q3[2] = (size_t)ay3.i1 * W3 + ax3.i0; q3[3] = (size_t)ay3.i1 * W3 + ax3.i1;
-  // issue every plane load
+  // issue every plane load.  A pass at the full size upscales by the identity
+  // (tap 0 with weight 1, the others with weight 0), so only tap 0 is read; the
+  // test is uniform over the launch.
+  const bool full2 = W2 == W && H2 == H, full3 = W3 == W && H3 == H;
   const int i1 = __ldg(id1 + p);
   int i2[4];
   uint32_t nn[4];
@@ -156,10 +161,20 @@ __device__ __forceinline__ void pixel_features_at(
   float tt[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    i2[k] = __ldg(id2 + q2[k]);
-    nn[k] = __ldg(n3 + q3[k]);
-    tl[k] = __ldg(tail3 + q3[k]);
-    tt[k] = __ldg(t3 + q3[k]);
+    if (k == 0 || !full2) {
+      i2[k] = __ldg(id2 + q2[k]);
+    } else {
+      i2[k] = -1;
+    }
+    if (k == 0 || !full3) {
+      nn[k] = __ldg(n3 + q3[k]);
+      tl[k] = __ldg(tail3 + q3[k]);
+      tt[k] = __ldg(t3 + q3[k]);
+    } else {
+      nn[k] = 0u;
+      tl[k] = make_uint4(0u, 0u, 0u, 0u);
+      tt[k] = 0.0f;
+    }
   }
   // colour gathers (independent of each other)
   const uint32_t c1 = i1 >= 0 ? __ldg(rgba8 + i1) : 0u;

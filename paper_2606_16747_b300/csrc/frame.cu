@@ -88,16 +88,6 @@ __global__ void __launch_bounds__(256, 2) k_mlp_f32(const float *__restrict__ w1
 }
 
 // ---------------------------------------------------------------------------
-// 8-bit RGBA of a float colour: round half to even of clamp(c, 0, 1) * 255,
-// alpha 255.
-__device__ __forceinline__ uint32_t quantize_rgba8(float4 c) {
-  const uint32_t R = __float2uint_rn(__saturatef(c.x) * 255.0f);
-  const uint32_t G = __float2uint_rn(__saturatef(c.y) * 255.0f);
-  const uint32_t B = __float2uint_rn(__saturatef(c.z) * 255.0f);
-  return R | (G << 8) | (B << 16) | (255u << 24);
-}
-
-// ---------------------------------------------------------------------------
 // Eq. 4 with the first and last terms already in front.rgb.
 __global__ void __launch_bounds__(256) k_composite(const float4 *__restrict__ front,
                                                    const float4 *__restrict__ f, long long P,
@@ -340,6 +330,7 @@ cudaError_t preload_quadtree();
 cudaError_t preload_train();
 cudaError_t preload_baselines();
 cudaError_t preload_leaf();
+cudaError_t preload_passes_resolve();
 }  // namespace star
 
 extern "C" star_nt_status star_nt_preload(void) {
@@ -353,5 +344,6 @@ extern "C" star_nt_status star_nt_preload(void) {
   if ((r = preload_train()) != cudaSuccess) e = r;
   if ((r = preload_baselines()) != cudaSuccess) e = r;
   if ((r = preload_leaf()) != cudaSuccess) e = r;
+  if ((r = preload_passes_resolve()) != cudaSuccess) e = r;
   return e == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
 }

@@ -79,6 +79,34 @@ struct PassAcc {
     }
   }
 
+  // Network input and front terms of pixel p once every pass ran at the full
+  // resolution (MODE kTail): the tail sums less the two nearest fragments, as
+  // finish<kFused> computes them; id1 and z1 are stored when po asks for them.
+  __device__ __forceinline__ void resolve_terms(const TriSetup *__restrict__ setups,
+                                                const uint32_t *__restrict__ rgba8, const PassOut &po,
+                                                float bg0, float bg1, float bg2, float kappa, size_t p,
+                                                float (&xv)[6], float4 &fr) {
+    const bool has1 = i1 != 0x7fffffff, has2 = i2 != 0x7fffffff;
+    if (po.id1) po.id1[p] = has1 ? i1 : -1;
+    if (po.z1) po.z1[p] = has1 ? z1 : 1.0f;
+    if (has1) {
+      const TriSetup &S = setups[i1];
+      rg -= S.rg; ba -= S.ba; lg -= S.lg; opq -= S.opq;
+    }
+    if (has2) {
+      const TriSetup &S = setups[i2];
+      rg -= S.rg; ba -= S.ba; lg -= S.lg; opq -= S.opq;
+    }
+    const uint32_t A = (uint32_t)(ba >> 32), Sr = (uint32_t)rg, Sg = (uint32_t)(rg >> 32),
+                   Sb = (uint32_t)ba;
+    const float t = tail_transmittance(lg, opq);
+    float r1 = 0, g1 = 0, b1 = 0, a1 = 0, r2 = 0, g2 = 0, b2 = 0, a2 = 0;
+    if (has1) unpack_rgba(__ldg(rgba8 + i1), r1, g1, b1, a1);
+    if (has2) unpack_rgba(__ldg(rgba8 + i2), r2, g2, b2, a2);
+    feature_terms(a1, r1, g1, b1, a2 * r2, a2 * g2, a2 * b2, a2, (float)N, (float)A, (float)Sr,
+                  (float)Sg, (float)Sb, t, N > 2, bg0, bg1, bg2, kappa, xv, fr);
+  }
+
   // Planes of pixel p (tail sums less the two nearest fragments).
   template <int MODE>
   __device__ __forceinline__ void finish(const TriSetup *__restrict__ setups,

@@ -56,6 +56,7 @@ __global__ void __launch_bounds__(256, MINB) k_passes(BinsView v1, BinsView v2, 
                                                    PassOut o2, PassOut o3, uint32_t *queue) {
   __shared__ TileStage stage;
   __shared__ int s_item;
+  if (v2.hd->resolved) return;  // star_nt_geometry_passes_resolve's launch did the passes
   const bool m2 = v2.hd->merged != 0, m3 = v3.hd->merged != 0;
   const int n1 = v1.hd->n_tiles, n2 = v2.hd->n_tiles, n3 = v3.hd->n_tiles;
   const int total = n1 + n2 + n3;

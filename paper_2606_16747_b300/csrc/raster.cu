@@ -294,6 +294,7 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(const float *__restri
     hd->n_pixels = W * H;
     hd->n_tris = n_tris;
     hd->merged = merged ? 1 : 0;
+    hd->resolved = 0;
     if (!size_ok) raise_status(status, STAR_NT_ERR_ARG);
   }
   if (!merged) {  // a merged pass is taken over by pass 1: no triangles binned

@@ -50,13 +50,6 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
   for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ uint32_t quantize8(float r, float g, float b) {
-  const uint32_t R = __float2uint_rn(__saturatef(r) * 255.0f);
-  const uint32_t G = __float2uint_rn(__saturatef(g) * 255.0f);
-  const uint32_t B = __float2uint_rn(__saturatef(b) * 255.0f);
-  return R | (G << 8) | (B << 16) | (255u << 24);
-}
-
 template <class In>
 __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
     k_resolve(In in, float bg0, float bg1, float bg2, float kappa, const float *__restrict__ w1,
@@ -72,7 +65,7 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
   const uint32_t bar = sbase + kQBar;
   uint32_t *s_tmem = reinterpret_cast<uint32_t *>(sm + kQBar + 8);
   volatile int *s_abort = reinterpret_cast<volatile int *>(sm + kQBar + 12);
-  if (in.rejected()) return;  // a pass was rejected by its raster
+  if (in.rejected()) return;  // a rejected pass, or the frame is already done
 
   // weights and bias columns (bf16, zero padded), the ones and zero blocks
   for (int i = tid; i < (int)(kQBar - kQC) / 4; i += kRThreads)
@@ -229,7 +222,7 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
         const float4 fr = front[t];
         const float r = fmaf(fr.w, f0, fr.x), g = fmaf(fr.w, f1, fr.y), b = fmaf(fr.w, f2, fr.z);
         if (out) out[p] = make_float4(r, g, b, 1.0f);
-        if (out8) out8[p] = quantize8(r, g, b);
+        if (out8) out8[p] = quantize_rgba8(r, g, b);
       }
     }
     fence_before();
@@ -302,7 +295,7 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
   uint32_t *s_tmem = reinterpret_cast<uint32_t *>(sm + kF8Bar + 8);
   volatile int *s_abort = reinterpret_cast<volatile int *>(sm + kF8Bar + 12);
   float *sb = reinterpret_cast<float *>(sm + kF8B);
-  if (in.rejected()) return;  // a pass was rejected by its raster
+  if (in.rejected()) return;  // a rejected pass, or the frame is already done
 
   // weights: e4m3 rows with power-of-two row scales, zero padded; biases fp32
   float *si = reinterpret_cast<float *>(sm + kF8S);
@@ -469,7 +462,7 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
         const float4 fr = front[t];
         const float r = fmaf(fr.w, f0, fr.x), g = fmaf(fr.w, f1, fr.y), b = fmaf(fr.w, f2, fr.z);
         if (out) out[p] = make_float4(r, g, b, 1.0f);
-        if (out8) out8[p] = quantize8(r, g, b);
+        if (out8) out8[p] = quantize_rgba8(r, g, b);
       }
     }
     fence_before();

@@ -71,6 +71,7 @@ def main(argv=None):
     ap.add_argument("--frames", type=int, default=120)
     ap.add_argument("--base-tile", type=int, default=64, choices=[16, 64])
     ap.add_argument("--merge-scale2", type=float, default=0.5)
+    ap.add_argument("--merge-scale3", type=float, default=0.7)
     ap.add_argument("--mlp", default="bf16", choices=["bf16", "fp8"])
     args = ap.parse_args(argv)
     build.build()
@@ -79,7 +80,8 @@ def main(argv=None):
     w = dict(np.load(os.path.join(HERE, "weights", "tail_mlp.npz")))
     star = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=sn.BF16,
                     fused="fp8" if args.mlp == "fp8" else True, persistent=True,
-                    base_tile=args.base_tile, merge_scale2=args.merge_scale2)
+                    base_tile=args.base_tile, merge_scale2=args.merge_scale2,
+                    merge_scale3=args.merge_scale3)
     leaf = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=sn.BF16,
                     fused="fp8" if args.mlp == "fp8" else True, base_tile=args.base_tile, leaf=True)
     ref = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=sn.F32)
@@ -133,7 +135,8 @@ def main(argv=None):
     mean = {k: float(np.mean(v)) for k, v in err.items()}
     e_rand = mean["unsorted_over"]
     out = {"workload": f"{args.workload} {W}x{H}, {sc.verts.shape[0]} triangles", "frames": args.frames,
-           "base_tile": args.base_tile, "pass2_merge_scale": args.merge_scale2, "mlp": args.mlp,
+           "base_tile": args.base_tile, "pass2_merge_scale": args.merge_scale2,
+           "pass3_merge_scale": args.merge_scale3, "mlp": args.mlp,
            "mean_mse": {k: float(f"{v:.4e}") for k, v in mean.items()},
            "psnr_of_mean_mse_db": {k: round(10 * math.log10(1 / v), 3) for k, v in mean.items()},
            "mse_reduction_vs_wboit_pct": {k: round(100 * (mean["wboit"] - v) / mean["wboit"], 2)

@@ -31,7 +31,8 @@ def _i32(vals, device):
 class Renderer:
     def __init__(self, verts, rgba8, W, H, params=None, x_dtype=sn.F32, mlp=None,
                  pair_capacity=None, device="cuda", base_tile=None, fused=False,
-                 persistent=False, tuning=None, merge_scale2=1.0, merge_scale3=1.0, leaf=False):
+                 persistent=False, tuning=None, merge_scale2=1.0, merge_scale3=1.0, leaf=False,
+                 fuse_passes=True):
         self.device = device
         sn.preload(torch.device(device).index)
         self.W, self.H = int(W), int(H)
@@ -51,6 +52,10 @@ class Renderer:
         # persistent: the three geometry passes in one launch (tuning: (block_w, ctas_per_sm))
         self.persistent = bool(persistent)
         self.tuning = tuning
+        # persistent + fused bf16 resolve: when every pass runs at full size the
+        # pass launch also runs the network and the composite (the resolve
+        # launch then returns at once)
+        self.fuse_passes = bool(fuse_passes)
         # a reduced pass at least this fraction of the full size (both axes)
         # is produced by pass 1 at the full size instead (1.0: only at full size)
         self.merge_scale2 = float(merge_scale2)
@@ -206,7 +211,11 @@ class Renderer:
                 self.status, stream)
 
         st = [("raster", raster)]
-        if self.persistent:
+        if self.persistent and self.fused and not self.fused_fp8 and self.fuse_passes:
+            st.append(("passes", lambda: sn.geometry_passes_resolve(
+                self.scene, b1, b2, b3, self.l1, self.l2, self.l3, self.params, self.mlp, self.rgba32f,
+                self.rgba8_out, self.tuning, self.status, stream)))
+        elif self.persistent:
             st.append(("passes", lambda: sn.geometry_passes(self.scene, b1, b2, b3, self.l1, self.l2,
                                                             self.l3, self.tuning, self.status,
                                                             stream)))

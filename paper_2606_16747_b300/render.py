@@ -26,6 +26,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=8, help="real + interpolated frame pairs")
     ap.add_argument("--mlp", default="bf16", choices=["bf16", "fp8"])
     ap.add_argument("--merge-scale2", type=float, default=0.5)
+    ap.add_argument("--merge-scale3", type=float, default=0.7)
     ap.add_argument("--block-w", type=int, default=8, choices=[4, 8, 16])
     ap.add_argument("--base-tile", type=int, default=64, choices=[16, 64])
     ap.add_argument("--leaf", action="store_true", help="passes 2 and 3 at each leaf's Eq. 2 scale")
@@ -36,7 +37,8 @@ def main(argv=None):
     w = dict(np.load(os.path.join(HERE, "weights", "tail_mlp.npz")))
     r = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=sn.BF16,
                  fused="fp8" if args.mlp == "fp8" else True, persistent=True,
-                 tuning=(args.block_w, 0), merge_scale2=args.merge_scale2, base_tile=args.base_tile,
+                 tuning=(args.block_w, 0), merge_scale2=args.merge_scale2,
+                 merge_scale3=args.merge_scale3, base_tile=args.base_tile,
                  leaf=args.leaf)
     cams = scenes.orbit_cameras(W, H, 2 * args.steps)
     vp32 = torch.tensor(np.stack([c.vp32 for c in cams]), device="cuda")

@@ -29,7 +29,8 @@ EXPORTS = ("star_nt_version", "star_nt_status_string", "star_nt_default_params",
            "star_nt_mse_grad", "star_nt_mlp_backward", "star_nt_adam", "star_nt_raster_passes",
            "star_nt_resolve", "star_nt_geometry_passes", "star_nt_resolve_fp8", "star_nt_preload",
            "star_nt_unsorted_over", "star_nt_wboit", "star_nt_wmse_grad", "star_nt_leaf_plan_make",
-           "star_nt_leaf_ws_bytes", "star_nt_geometry_passes_leaf", "star_nt_resolve_leaf")
+           "star_nt_leaf_ws_bytes", "star_nt_geometry_passes_leaf", "star_nt_resolve_leaf",
+           "star_nt_geometry_passes_resolve")
 
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
@@ -133,6 +134,9 @@ def lib():
             [ctypes.POINTER(Layers)] * 3 + [_P, _P]
         L.star_nt_geometry_passes.argtypes = [ctypes.POINTER(Scene)] + [ctypes.POINTER(Bins)] * 3 + \
             [ctypes.POINTER(Layers)] * 3 + [ctypes.POINTER(Tuning), _P, _P]
+        L.star_nt_geometry_passes_resolve.argtypes = [ctypes.POINTER(Scene)] + [ctypes.POINTER(Bins)] * 3 + \
+            [ctypes.POINTER(Layers)] * 3 + [ctypes.POINTER(Params), ctypes.POINTER(Mlp), _P, _P,
+                                            ctypes.POINTER(Tuning), _P, _P]
         L.star_nt_upscale_features.argtypes = [ctypes.POINTER(Scene)] + [ctypes.POINTER(Bins)] * 2 + \
             [ctypes.POINTER(Layers)] * 3 + [_I32, _I32, ctypes.POINTER(Params),
                                             ctypes.POINTER(Features), _P]
@@ -302,6 +306,16 @@ def geometry_passes(scene: Scene, bins1, bins2, bins3, layers1, layers2, layers3
         ctypes.byref(scene), ctypes.byref(bins1.c), ctypes.byref(bins2.c), ctypes.byref(bins3.c),
         *[ctypes.byref(l) for l in ls], ctypes.byref(t) if t is not None else None, _ptr(status),
         _stream(stream)))
+
+
+def geometry_passes_resolve(scene: Scene, bins1, bins2, bins3, layers1, layers2, layers3, params: Params,
+                            w: Mlp, rgba32f=None, rgba8=None, tuning=None, status=None, stream=None):
+    ls = [layers_struct(l) for l in (layers1, layers2, layers3)]
+    t = Tuning(*tuning) if tuning is not None else None
+    _check("star_nt_geometry_passes_resolve", lib().star_nt_geometry_passes_resolve(
+        ctypes.byref(scene), ctypes.byref(bins1.c), ctypes.byref(bins2.c), ctypes.byref(bins3.c),
+        *[ctypes.byref(l) for l in ls], ctypes.byref(params), ctypes.byref(w), _ptr(rgba32f), _ptr(rgba8),
+        ctypes.byref(t) if t is not None else None, _ptr(status), _stream(stream)))
 
 
 def upscale_features(scene: Scene, bins2, bins3, layers1, layers2, layers3, W, H, params: Params,

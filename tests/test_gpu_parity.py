@@ -658,6 +658,43 @@ def test_persistent_passes_equal_separate(sn, tuning, sizes):
         assert torch.equal(a, b)
 
 
+@pytest.mark.parametrize("tuning", [None, (16, 6), (4, 3)])
+@pytest.mark.parametrize("sizes", ["full", "reduced3", "reduced2"])
+def test_pass_launch_resolve_equals_resolve(orc, sn, tuning, sizes):
+    """star_nt_geometry_passes_resolve: with every pass at full size the pass
+    launch produces the frame itself, bit for bit the frame of the separate
+    resolve, and writes id1 and z1; with a reduced pass it leaves the frame to
+    the resolve (same frame again)."""
+    from paper_2606_16747_b300.pipeline import Renderer
+    sc = scenes.screen_scene(29, 3000, 333, 197, size_scale=0.7)   # ragged: partial tiles
+    W, H = sc.width, sc.height
+    s2 = (W, H) if sizes != "reduced2" else (201, 119)
+    s3 = (W, H) if sizes != "reduced3" else (97, 57)
+    mlp = scenes.mlp_xavier(4)
+    outs = []
+    for fuse in (False, True):
+        r = Renderer(sc.verts, sc.rgba8, W, H, mlp=mlp, x_dtype=sn.BF16, fused=True, persistent=True,
+                     tuning=tuning, fuse_passes=fuse)
+        r.set_camera(sc.cam.vp32)
+        r.state.view(torch.int32)[:6] = torch.tensor([W, H, *s2, *s3], dtype=torch.int32)
+        r.rgba32f.fill_(-1.0)
+        for _ in range(2):   # the second frame starts from the first's flags
+            r.star_frame(update_tiles=False)
+        torch.cuda.synchronize()
+        r.check_status()
+        resolved = int(r.bins[1].mem[44:48].view(torch.int32).item())   # BinsHeader.resolved
+        outs.append((r.rgba32f.clone(), r.rgba8_out.clone(), r.l1["id1"].clone(), r.l1["z1"].clone(),
+                     resolved))
+    assert outs[0][4] == 0 and outs[1][4] == (1 if sizes == "full" else 0)
+    for a, b in zip(outs[0][:4], outs[1][:4]):
+        assert torch.equal(a, b)
+    if sizes == "full" and tuning is None:
+        o = orc.frame_star(sc.verts, sc.rgba8, sc.cam.vp32, W, H, (W, H), (W, H), scenes.mlp_flat(mlp),
+                           threads=4)
+        rgb = outs[1][0].cpu().numpy().reshape(-1, 4)[:, :3]
+        assert np.max(np.abs(rgb - o["rgb"])) <= TOL_BF16
+
+
 @pytest.mark.gpu
 @pytest.mark.parametrize("persistent", [False, True])
 def test_pass2_merge_scale(sn, persistent):
