@@ -34,10 +34,20 @@ FALLBACK_PEAKS = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustain
 N_SM = 148
 ALU_LANES_PER_SM = 128
 OPS_PER_FRAGMENT = 32     # algorithmic integer/fp operations per fragment (see design notes)
-# kernels of one step (persistent passes, fused resolve): raster of the three
-# passes (set-up/count, tile scan, fill), passes 1-3 (one launch), resolve,
-# quadtree (decide, relax, relax + histogram + Eq. 2), reprojection (matrix, pixels)
-KERNELS_PER_STEP = 3 + 1 + 1 + 3 + 2
+
+
+def kernels_per_step(r) -> int:
+    """Kernel launches of one real + interpolated step of renderer r: raster of
+    the passes (set-up/count, tile scan, fill); the geometry passes (the fused
+    pass launch and the persistent launch, or the persistent launch alone, or
+    three launches); the resolve (one launch, or features + MLP + composite);
+    the quadtree (decide, relax, relax + histogram + Eq. 2); the reprojection
+    (matrix, pixels)."""
+    if r.persistent:
+        passes = 2 if (r.fused and not r.fused_fp8 and r.fuse_passes) else 1
+    else:
+        passes = 3
+    return 3 + passes + (1 if r.fused else 3) + 3 + 2
 STAGE_REPS = 20
 # DRAM bytes (read + write) of one k_passes launch at 1080p, from the ncu
 # capture summarised in profiles/passes_hd.md (same kernel build, s3 = 0.68)
@@ -365,7 +375,11 @@ def run_ours(args, rank, world):
                                 (stage_state["W3"], stage_state["H3"])), merged):
             if not m:
                 dom_frags += fragment_count(sn, star, vp_last, W, H, (wp, hp))
-        dom_name = "k_passes (passes 1-3, one persistent launch)"
+        if all(merged) and star.persistent and star.fused and not star.fused_fp8 and star.fuse_passes:
+            dom_name = ("k_passes_resolve (passes 1-3 at full size with the network input, tcgen05 "
+                        "MLP and composite of every pixel; only the traversal ops are counted)")
+        else:
+            dom_name = "k_passes (passes 1-3, one persistent launch)"
     else:
         dom_ms = stage_mean["pass1"]
         dom_frags = Fcount
@@ -405,7 +419,7 @@ def run_ours(args, rank, world):
         "pass_state": {k: state[k] for k in ("W2", "H2", "W3", "H3", "s2", "s3", "wbar", "hist")},
         "wall_s": round(wall, 3),
         "graph": "one CUDA graph per step (real + interpolated frame), replayed",
-        "gpu_launches": (KERNELS_PER_STEP + (0 if star.fused else 2) + (0 if star.persistent else 2)) * args.steps,
+        "gpu_launches": kernels_per_step(star) * args.steps,
         "clocks": clocks,
         "e2e": e2e,
         "roofline": {"bound": "alu", "kernel": dom_name, "fragments": int(dom_frags),

@@ -48,7 +48,7 @@ struct __align__(128) FusedSmem {
   uint8_t w3[1024];  // N = 16, K = 32 (bias in K 16, 17): 4 of 256
   unsigned long long bar;
   uint32_t tmem;
-  int abort;
+  volatile int abort;
 };
 
 // One pass-1 tile with every pass merged: traversal, network input, the three
@@ -99,9 +99,8 @@ __device__ __forceinline__ void pass_resolve_body(const BinsView &bv, const uint
     }
     mma_commit(bar);
   }
-  if (!mbar_wait(bar, ph)) fs.abort = 1;
+  mma_wait_cta(bar, ph, &fs.abort);
   ph ^= 1u;
-  fence_after();
   // eight columns (one K core column of H1) per tensor-memory load: the
   // register budget of the pass traversal leaves no room for wider loads
 #pragma unroll
@@ -130,9 +129,8 @@ __device__ __forceinline__ void pass_resolve_body(const BinsView &bv, const uint
     }
     mma_commit(bar);
   }
-  if (!fs.abort && !mbar_wait(bar, ph)) fs.abort = 1;
+  if (!fs.abort) mma_wait_cta(bar, ph, &fs.abort);  // fs.abort is uniform after a barrier
   ph ^= 1u;
-  fence_after();
 #pragma unroll
   for (int kc = 0; kc < 2; ++kc) {
     float d[8];
@@ -157,9 +155,8 @@ __device__ __forceinline__ void pass_resolve_body(const BinsView &bv, const uint
     }
     mma_commit(bar);
   }
-  if (!fs.abort && !mbar_wait(bar, ph)) fs.abort = 1;
+  if (!fs.abort) mma_wait_cta(bar, ph, &fs.abort);  // fs.abort is uniform after a barrier
   ph ^= 1u;
-  fence_after();
   // ---- composite, Eq. 4
   {
     uint32_t r[4];

@@ -142,9 +142,8 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
       }
       mma_commit(bar);
     }
-    if (!mbar_wait(bar, ph)) *s_abort = 1;
+    mma_wait_cta(bar, ph, s_abort);
     ph ^= 1u;
-    fence_after();
 #pragma unroll
     for (int t = 0; t < kRTiles; ++t) {
       float d[32];
@@ -173,9 +172,8 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
       }
       mma_commit(bar);
     }
-    if (!mbar_wait(bar, ph)) *s_abort = 1;
+    mma_wait_cta(bar, ph, s_abort);
     ph ^= 1u;
-    fence_after();
 #pragma unroll
     for (int t = 0; t < kRTiles; ++t) {
       float d[16];
@@ -203,9 +201,8 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
       }
       mma_commit(bar);
     }
-    if (!mbar_wait(bar, ph)) *s_abort = 1;
+    mma_wait_cta(bar, ph, s_abort);
     ph ^= 1u;
-    fence_after();
     // ---- composite, Eq. 4
 #pragma unroll
     for (int t = 0; t < kRTiles; ++t) {
@@ -372,9 +369,8 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
       }
       mma_commit(bar);
     }
-    if (!mbar_wait(bar, ph)) *s_abort = 1;
+    mma_wait_cta(bar, ph, s_abort);
     ph ^= 1u;
-    fence_after();
 #pragma unroll
     for (int t = 0; t < kRTiles; ++t) {
       float d[32];
@@ -407,9 +403,8 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
         mma_e4m3(tmem + 32 * t, smem_desc(sbase + kF8H1 + t * 6144, 2048, 128), dW2, idesc_e4m3(16), 0u);
       mma_commit(bar);
     }
-    if (!mbar_wait(bar, ph)) *s_abort = 1;
+    mma_wait_cta(bar, ph, s_abort);
     ph ^= 1u;
-    fence_after();
 #pragma unroll
     for (int t = 0; t < kRTiles; ++t) {
       float d[16];
@@ -442,9 +437,8 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
       }
       mma_commit(bar);
     }
-    if (!mbar_wait(bar, ph)) *s_abort = 1;
+    mma_wait_cta(bar, ph, s_abort);
     ph ^= 1u;
-    fence_after();
     // ---- composite, Eq. 4
 #pragma unroll
     for (int t = 0; t < kRTiles; ++t) {

@@ -44,6 +44,17 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
   return true;
 }
 
+// The CTA waits for an MMA commit: one thread polls the mbarrier (bounded;
+// sets *abort on expiry) while the others wait at the CTA barrier, which takes
+// no issue slots; the tcgen05 fences order the MMA's tensor-memory writes
+// before every thread's following tensor-memory loads.
+__device__ __forceinline__ void mma_wait_cta(uint32_t bar, uint32_t phase, volatile int *abort) {
+  if (threadIdx.x == 0 && !mbar_wait(bar, phase)) *abort = 1;
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                : "memory");
