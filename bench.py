@@ -52,6 +52,9 @@ STAGE_REPS = 20
 # DRAM bytes (read + write) of one k_passes launch at 1080p, from the ncu
 # capture summarised in profiles/passes_hd.md (same kernel build, s3 = 0.68)
 PASSES_DRAM_BYTES = 13958656
+# the same for one k_passes_resolve launch (passes at full size + MLP + composite),
+# profiles/passes_resolve_hd.md
+FUSED_DRAM_BYTES = 12969984
 
 
 def load_peaks():
@@ -425,9 +428,12 @@ def run_ours(args, rank, world):
         "roofline": {"bound": "alu", "kernel": dom_name, "fragments": int(dom_frags),
                      "achieved": round(achieved, 4), "peak": round(alu_peak, 3), "unit": "Tops/s",
                      "frac": round(achieved / alu_peak, 5),
-                     "traffic": PASSES_DRAM_BYTES if "passes" in stage_mean and args.workload == "hd" else None,
-                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
-                                       "k_passes launch (profiles/passes_hd.md, 1080p orbit step 6, s3 0.68)",
+                     "traffic": (None if "passes" not in stage_mean or args.workload != "hd" else
+                                 FUSED_DRAM_BYTES if dom_name.startswith("k_passes_resolve") else
+                                 PASSES_DRAM_BYTES),
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch of the "
+                                       "dominant kernel on the 1080p orbit (profiles/passes_resolve_hd.md, "
+                                       "profiles/passes_hd.md)",
                      "peak_source": f"{N_SM} SM x {ALU_LANES_PER_SM} lanes x sm_max_mhz ({peaks_kind})",
                      "ops_per_fragment": OPS_PER_FRAGMENT, "launch_ms": round(dom_ms, 5)},
     }
