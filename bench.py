@@ -615,6 +615,33 @@ def cpu_oracle_frame(sc, w, cam, threads):
                              threads=threads)
 
 
+def cpu_phases(sc, w, cam, threads, rows=None):
+    """Oracle time per phase of one plain full-resolution frame (ms): raster,
+    per-pixel sort + A-buffer + layer terms, and the neural path (features,
+    MLP, composite).  rows: only the first rows of the frame (a sample)."""
+    import oracle
+    from paper_2606_16747_b300 import scenes
+    W, H = sc.width, sc.height
+    t0 = time.perf_counter()
+    fr = oracle.raster(sc.verts, cam.vp32, W, H, threads)
+    t1 = time.perf_counter()
+    if rows is not None:   # keep the first rows' fragment lists only
+        P = W * rows
+        end = int(fr.offsets[P])
+        fr = oracle.Frags(W, rows, fr.counts[:P], fr.offsets[:P + 1], fr.z[:end], fr.prim[:end])
+    r = oracle.resolve(fr, sc.rgba8, (1.0, 1.0, 1.0), threads)
+    t2 = time.perf_counter()
+    flag = (r["n"] > 2).astype(np.uint8)
+    x, front = oracle.features(r["id1"], sc.rgba8, r["layer2"], r["n"].astype(np.float64),
+                               r["a_tail"].astype(np.float64), r["s_tail"].astype(np.float64),
+                               r["t_tail"], (1.0, 1.0, 1.0))
+    f = oracle.mlp_forward(oracle.params64(scenes.mlp_flat(w)), x, flag)
+    oracle.composite(front, f)
+    t3 = time.perf_counter()
+    return {"raster_ms": round((t1 - t0) * 1e3, 1), "sort_abuffer_layers_ms": round((t2 - t1) * 1e3, 1),
+            "neural_path_ms": round((t3 - t2) * 1e3, 1)}
+
+
 def run_cpu_baseline(args):
     """The oracle as it stands on the host cores, bounded sample of the workload."""
     from paper_2606_16747_b300 import scenes
@@ -629,9 +656,18 @@ def run_cpu_baseline(args):
         cpu_oracle_frame(sc, w, cams[n % 4], threads)
         n += 1
     dt = (time.perf_counter() - t0) / n
+    # phases on all cores, and on one core over the first 1/16 of the rows
+    # (raster of the whole frame, the rest on the sample)
+    phases = cpu_phases(sc, w, cams[0], threads)
+    rows = max(1, sc.height // 16)
+    single = cpu_phases(sc, w, cams[0], 1, rows=rows)
     return {"value": round(dt * 1e3, 3), "unit": "ms/frame", "cores": threads, "kind": "oracle",
             "sample": f"{n} full frames of the plain full-resolution neural pipeline ({desc}), "
-                      "float64 oracle, threads over rows"}
+                      "float64 oracle, threads over rows",
+            "phases_all_cores_ms": phases,
+            "phases_one_core_ms": single,
+            "phases_one_core_sample": f"raster of the full frame; the other phases on the first {rows} "
+                                      f"of {sc.height} rows"}
 
 
 def run_reference(args, rank, world):
