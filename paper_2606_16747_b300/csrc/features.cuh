@@ -130,57 +130,33 @@ struct FeatInLeaf {
   __device__ __forceinline__ bool rejected() const { return false; }
 };
 
-// Network input x[0..5] (x5 = tail flag) and front terms of pixel (x, y),
-// with pass 2 (W2 x H2) and pass 3 (W3 x H3) upscaled bilinearly.  All plane
-// loads are issued before any of them is used (the sample indices are
-// clamped, so every load is valid) to keep many requests in flight; zero
-// bilinear weights then drop their samples exactly.  A second-layer id is
-// used only below id_limit (0x80000000: any id >= 0).
-__device__ __forceinline__ void pixel_features_at(
-    int W, int H, const uint32_t *__restrict__ rgba8, const int32_t *__restrict__ id1,
-    int W2, int H2, const int32_t *__restrict__ id2, int W3, int H3,
-    const uint32_t *__restrict__ n3, const uint4 *__restrict__ tail3,
-    const float *__restrict__ t3, uint32_t id_limit, float bg0, float bg1, float bg2,
-    float kappa, int x, int y, float (&xo)[6], float4 &front) {
-  const size_t p = (size_t)y * W + x;
-  const Axis ax2 = upscale_axis(x, W2, W), ay2 = upscale_axis(y, H2, H);
-  const Axis ax3 = upscale_axis(x, W3, W), ay3 = upscale_axis(y, H3, H);
-  size_t q2[4], q3[4];
-  q2[0] = (size_t)ay2.i0 * W2 + ax2.i0; q2[1] = (size_t)ay2.i0 * W2 + ax2.i1;
-  q2[2] = (size_t)ay2.i1 * W2 + ax2.i0; q2[3] = (size_t)ay2.i1 * W2 + ax2.i1;
-  q3[0] = (size_t)ay3.i0 * W3 + ax3.i0; q3[1] = (size_t)ay3.i0 * W3 + ax3.i1;
-  q3[2] = (size_t)ay3.i1 * W3 + ax3.i0; q3[3] = (size_t)ay3.i1 * W3 + ax3.i1;
-  // issue every plane load.  A pass at the full size upscales by the identity
-  // (tap 0 with weight 1, the others with weight 0), so only tap 0 is read; the
-  // test is uniform over the launch.
-  const bool full2 = W2 == W && H2 == H, full3 = W3 == W && H3 == H;
-  const int i1 = __ldg(id1 + p);
+// Plane samples of one pixel: its pass-1 id, the ids at its four pass-2
+// bilinear taps and the pass-3 planes at its four pass-3 taps (taps ordered
+// (i0, j0), (i1, j0), (i0, j1), (i1, j1)).
+struct PixelTaps {
+  int i1;
   int i2[4];
   uint32_t nn[4];
   uint4 tl[4];
   float tt[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    if (k == 0 || !full2) {
-      i2[k] = __ldg(id2 + q2[k]);
-    } else {
-      i2[k] = -1;
-    }
-    if (k == 0 || !full3) {
-      nn[k] = __ldg(n3 + q3[k]);
-      tl[k] = __ldg(tail3 + q3[k]);
-      tt[k] = __ldg(t3 + q3[k]);
-    } else {
-      nn[k] = 0u;
-      tl[k] = make_uint4(0u, 0u, 0u, 0u);
-      tt[k] = 0.0f;
-    }
-  }
+};
+
+// Network input x[0..5] (x5 = tail flag) and front terms from a pixel's taps
+// and bilinear axes (pass 2: ax2, ay2; pass 3: ax3, ay3).  Zero bilinear
+// weights drop their samples exactly (so a tap of weight zero may hold any
+// value); a second-layer id is used only below id_limit (0x80000000: any
+// id >= 0).
+__device__ __forceinline__ void features_from_taps(const PixelTaps &tp, const Axis &ax2,
+                                                   const Axis &ay2, const Axis &ax3, const Axis &ay3,
+                                                   const uint32_t *__restrict__ rgba8,
+                                                   uint32_t id_limit, float bg0, float bg1,
+                                                   float bg2, float kappa, float (&xo)[6],
+                                                   float4 &front) {
   // colour gathers (independent of each other)
-  const uint32_t c1 = i1 >= 0 ? __ldg(rgba8 + i1) : 0u;
+  const uint32_t c1 = tp.i1 >= 0 ? __ldg(rgba8 + tp.i1) : 0u;
   uint32_t c2[4];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) c2[k] = (uint32_t)i2[k] < id_limit ? __ldg(rgba8 + i2[k]) : 0u;
+  for (int k = 0; k < 4; ++k) c2[k] = (uint32_t)tp.i2[k] < id_limit ? __ldg(rgba8 + tp.i2[k]) : 0u;
 
   float r1, g1, b1, a1;
   unpack_rgba(c1, r1, g1, b1, a1);
@@ -190,7 +166,7 @@ __device__ __forceinline__ void pixel_features_at(
   float L2[4] = {0, 0, 0, 0};
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    if (w2[k] == 0.0f || (uint32_t)i2[k] >= id_limit) continue;
+    if (w2[k] == 0.0f || (uint32_t)tp.i2[k] >= id_limit) continue;
     float r, g, b, a;
     unpack_rgba(c2[k], r, g, b, a);
     L2[0] += w2[k] * (a * r);
@@ -208,17 +184,61 @@ __device__ __forceinline__ void pixel_features_at(
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     if (wi3[k] == 0) continue;  // exact zero weight
-    nf += w3[k] * (float)nn[k];
-    A += w3[k] * (float)tl[k].x;
-    Sr += w3[k] * (float)tl[k].y;
-    Sg += w3[k] * (float)tl[k].z;
-    Sb += w3[k] * (float)tl[k].w;
-    t += w3[k] * tt[k];
-    nexact += wi3[k] * (long long)nn[k];
+    nf += w3[k] * (float)tp.nn[k];
+    A += w3[k] * (float)tp.tl[k].x;
+    Sr += w3[k] * (float)tp.tl[k].y;
+    Sg += w3[k] * (float)tp.tl[k].z;
+    Sb += w3[k] * (float)tp.tl[k].w;
+    t += w3[k] * tp.tt[k];
+    nexact += wi3[k] * (long long)tp.nn[k];
   }
   const bool flag = nexact > 2LL * ax3.den * ay3.den;
   feature_terms(a1, r1, g1, b1, L2[0], L2[1], L2[2], L2[3], nf, A, Sr, Sg, Sb, t, flag, bg0, bg1, bg2,
                 kappa, xo, front);
+}
+
+// Network input and front terms of pixel (x, y), with pass 2 (W2 x H2) and
+// pass 3 (W3 x H3) upscaled bilinearly from the planes in global memory.
+// All plane loads are issued before any of them is used (the sample indices
+// are clamped, so every load is valid) to keep many requests in flight.  A
+// pass at the full size upscales by the identity (tap 0 with weight 1, the
+// others with weight 0), so only tap 0 is read; the test is uniform over the
+// launch.
+__device__ __forceinline__ void pixel_features_at(
+    int W, int H, const uint32_t *__restrict__ rgba8, const int32_t *__restrict__ id1,
+    int W2, int H2, const int32_t *__restrict__ id2, int W3, int H3,
+    const uint32_t *__restrict__ n3, const uint4 *__restrict__ tail3,
+    const float *__restrict__ t3, uint32_t id_limit, float bg0, float bg1, float bg2,
+    float kappa, int x, int y, float (&xo)[6], float4 &front) {
+  const size_t p = (size_t)y * W + x;
+  const Axis ax2 = upscale_axis(x, W2, W), ay2 = upscale_axis(y, H2, H);
+  const Axis ax3 = upscale_axis(x, W3, W), ay3 = upscale_axis(y, H3, H);
+  size_t q2[4], q3[4];
+  q2[0] = (size_t)ay2.i0 * W2 + ax2.i0; q2[1] = (size_t)ay2.i0 * W2 + ax2.i1;
+  q2[2] = (size_t)ay2.i1 * W2 + ax2.i0; q2[3] = (size_t)ay2.i1 * W2 + ax2.i1;
+  q3[0] = (size_t)ay3.i0 * W3 + ax3.i0; q3[1] = (size_t)ay3.i0 * W3 + ax3.i1;
+  q3[2] = (size_t)ay3.i1 * W3 + ax3.i0; q3[3] = (size_t)ay3.i1 * W3 + ax3.i1;
+  const bool full2 = W2 == W && H2 == H, full3 = W3 == W && H3 == H;
+  PixelTaps tp;
+  tp.i1 = __ldg(id1 + p);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (k == 0 || !full2) {
+      tp.i2[k] = __ldg(id2 + q2[k]);
+    } else {
+      tp.i2[k] = -1;
+    }
+    if (k == 0 || !full3) {
+      tp.nn[k] = __ldg(n3 + q3[k]);
+      tp.tl[k] = __ldg(tail3 + q3[k]);
+      tp.tt[k] = __ldg(t3 + q3[k]);
+    } else {
+      tp.nn[k] = 0u;
+      tp.tl[k] = make_uint4(0u, 0u, 0u, 0u);
+      tp.tt[k] = 0.0f;
+    }
+  }
+  features_from_taps(tp, ax2, ay2, ax3, ay3, rgba8, id_limit, bg0, bg1, bg2, kappa, xo, front);
 }
 
 // Global pass sizes (Eq. 2 over the frame), read from the bins headers.
