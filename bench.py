@@ -151,7 +151,8 @@ def run_ours(args, rank, world):
     fused_kind = (args.mlp if args.mlp == "fp8" else True) if args.fused and x_dtype == sn.BF16 else False
     star = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=x_dtype, base_tile=args.base_tile,
                     fused=fused_kind, persistent=args.persistent,
-                    merge_scale2=args.merge_scale2, merge_scale3=args.merge_scale3)
+                    merge_scale2=args.merge_scale2, merge_scale3=args.merge_scale3,
+                    fixed_scales=args.fixed_scales)
     star.interp_float = False   # a display takes the 8-bit interpolated frame
     plain = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=sn.F32)
     n_frames = 2 * (20 + 2 * args.warmup + 2 * args.steps)
@@ -407,6 +408,7 @@ def run_ours(args, rank, world):
                    "passes": "persistent" if star.persistent else "separate",
                    "pass2_merge_scale": star.merge_scale2,
                    "pass3_merge_scale": star.merge_scale3,
+                   "fixed_scales": list(args.fixed_scales) if args.fixed_scales else None,
                    "pass_tuning": tuned,
                    "base_tile": args.base_tile, "l2": "flushed between steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
@@ -500,7 +502,8 @@ def end_to_end(sn, torch, sc, w, x_dtype, W, H, cams, args, tuning=None):
     r = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=x_dtype, base_tile=args.base_tile,
                  fused=(args.mlp if args.mlp == "fp8" else True) if args.fused and x_dtype == sn.BF16 else False,
                  persistent=args.persistent, tuning=tuning,
-                 merge_scale2=args.merge_scale2, merge_scale3=args.merge_scale3)
+                 merge_scale2=args.merge_scale2, merge_scale3=args.merge_scale3,
+                 fixed_scales=args.fixed_scales)
     r.interp_float = False      # both frames leave as 8-bit
     hv = torch.from_numpy(np.ascontiguousarray(sc.verts)).pin_memory()
     hc = torch.from_numpy(np.ascontiguousarray(sc.rgba8).view(np.int32)).pin_memory()
@@ -726,8 +729,16 @@ def main():
                     help="separate upscale/features, MLP and composite kernels")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-leaf", action="store_true", help="skip the per-leaf pass-resolution variant")
+    ap.add_argument("--fixed-scales", default=None,
+                    help="S2,S3: passes 2 and 3 at these fixed scales instead of Eq. 2's (the paper's "
+                         "ablation settings, e.g. 0.5,0.5 or 0.5,0.25); merges only at full size")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    if args.fixed_scales:
+        args.fixed_scales = tuple(float(v) for v in args.fixed_scales.split(","))
+        if len(args.fixed_scales) != 2 or not all(0.25 <= v <= 1.0 for v in args.fixed_scales):
+            raise SystemExit("--fixed-scales wants two scales in [0.25, 1]")
+        args.merge_scale2 = args.merge_scale3 = 1.0   # the passes run at the fixed sizes
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

@@ -32,7 +32,7 @@ class Renderer:
     def __init__(self, verts, rgba8, W, H, params=None, x_dtype=sn.F32, mlp=None,
                  pair_capacity=None, device="cuda", base_tile=None, fused=False,
                  persistent=False, tuning=None, merge_scale2=1.0, merge_scale3=1.0, leaf=False,
-                 fuse_passes=True):
+                 fuse_passes=True, fixed_scales=None):
         self.device = device
         sn.preload(torch.device(device).index)
         self.W, self.H = int(W), int(H)
@@ -90,6 +90,13 @@ class Renderer:
         # quadtree state: pass sizes live in ``state`` on the device
         self.state = torch.zeros(64, dtype=torch.uint8, device=device)
         self.state.view(torch.int32)[:6] = torch.tensor([self.W, self.H] * 3, dtype=torch.int32)
+        # fixed_scales (s2, s3): the pass sizes of every frame are ceil(s W) x
+        # ceil(s H) (the fixed settings of the paper's ablation) instead of
+        # Eq. 2's; the quadtree still runs and reports its histogram and w-bar
+        self.fixed_sizes = None
+        if fixed_scales is not None:
+            self.fixed_sizes = {p: _i32([math.ceil(s * self.W), math.ceil(s * self.H)], device)
+                                for p, s in zip((2, 3), fixed_scales)}
         B = self.params.base_tile
         self.n_tiles = math.ceil(self.W / B) * math.ceil(self.H / B)
         self.mask = [torch.zeros(self.n_tiles, **i32), torch.zeros(self.n_tiles, **i32)]
@@ -153,6 +160,8 @@ class Renderer:
         off = {1: None, 2: STATE_W2, 3: STATE_W3}[which]
         if off is None:
             return self.full_size
+        if self.fixed_sizes is not None:
+            return self.fixed_sizes[which]
         return self.state[off:off + 8].view(torch.int32)
 
     # -- frames -------------------------------------------------------------

@@ -658,6 +658,30 @@ def test_persistent_passes_equal_separate(sn, tuning, sizes):
         assert torch.equal(a, b)
 
 
+def test_fixed_scales(orc, sn):
+    """Fixed pass scales (the paper's ablation settings): every frame runs
+    passes 2 and 3 at ceil(s W) x ceil(s H) whatever the quadtree's Eq. 2 says,
+    and the frame is the oracle's at those sizes."""
+    from paper_2606_16747_b300.pipeline import Renderer
+    sc = scenes.screen_scene(43, 2500, 208, 144, size_scale=0.7, colours="coherent")
+    W, H = sc.width, sc.height
+    mlp = scenes.mlp_xavier(4)
+    r = Renderer(sc.verts, sc.rgba8, W, H, mlp=mlp, x_dtype=sn.BF16, fused=True, persistent=True,
+                 fixed_scales=(0.5, 0.25))
+    r.set_camera(sc.cam.vp32)
+    for _ in range(3):
+        r.star_frame()   # the quadtree updates its state; the sizes stay fixed
+    torch.cuda.synchronize()
+    r.check_status()
+    s2, s3 = (104, 72), (52, 36)
+    for k, sz in ((1, s2), (2, s3)):
+        hd = r.bins[k].header().cpu().numpy()
+        assert (int(hd[0]), int(hd[1])) == sz
+    o = orc.frame_star(sc.verts, sc.rgba8, sc.cam.vp32, W, H, s2, s3, scenes.mlp_flat(mlp), threads=4)
+    rgb = r.rgba32f.cpu().numpy().reshape(-1, 4)[:, :3]
+    assert np.max(np.abs(rgb - o["rgb"])) <= TOL_BF16
+
+
 @pytest.mark.parametrize("tuning", [None, (16, 6), (4, 3)])
 @pytest.mark.parametrize("sizes", ["full", "reduced3", "reduced2"])
 def test_pass_launch_resolve_equals_resolve(orc, sn, tuning, sizes):
