@@ -149,10 +149,11 @@ def run_ours(args, rank, world):
     x_dtype = sn.F32 if args.mlp == "f32" else sn.BF16
     # fused resolve: bf16 or fp8 operands on tcgen05 (f32 runs the separate kernels)
     fused_kind = (args.mlp if args.mlp == "fp8" else True) if args.fused and x_dtype == sn.BF16 else False
-    star = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=x_dtype, base_tile=args.base_tile,
+    params = sn.default_params(**({"tau_split": args.tau[0], "tau_merge": args.tau[1]} if args.tau else {}))
+    star = Renderer(sc.verts, sc.rgba8, W, H, params=params, mlp=w, x_dtype=x_dtype, base_tile=args.base_tile,
                     fused=fused_kind, persistent=args.persistent,
                     merge_scale2=args.merge_scale2, merge_scale3=args.merge_scale3,
-                    fixed_scales=args.fixed_scales)
+                    fixed_scales=args.fixed_scales, fuse_passes=args.fuse_passes)
     star.interp_float = False   # a display takes the 8-bit interpolated frame
     plain = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=sn.F32)
     n_frames = 2 * (20 + 2 * args.warmup + 2 * args.steps)
@@ -175,6 +176,8 @@ def run_ours(args, rank, world):
         from paper_2606_16747_b300 import autotune
         tuned = autotune.tune(star)
         star.tuning = (tuned["block_w"], tuned["ctas_per_sm"])
+        if "fuse_passes" in tuned and args.fuse_passes:
+            star.fuse_passes = tuned["fuse_passes"]
     stages = star.star_stages() + [("reproject", star.interp_frame)]
     g_step = star.capture(star.step)
     g_stage = [(name, star.capture(fn)) for name, fn in stages]
@@ -259,8 +262,9 @@ def run_ours(args, rank, world):
     leaf = None
     leaf_info = None
     if star.fused and not args.no_leaf:
-        leaf = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=x_dtype, base_tile=args.base_tile,
-                        fused=fused_kind, leaf=True)
+        leaf = Renderer(sc.verts, sc.rgba8, W, H, params=sn.default_params(
+                            **({"tau_split": args.tau[0], "tau_merge": args.tau[1]} if args.tau else {})),
+                        mlp=w, x_dtype=x_dtype, base_tile=args.base_tile, fused=fused_kind, leaf=True)
         leaf.interp_float = False
 
         def set_leaf_cams(k):
@@ -353,7 +357,7 @@ def run_ours(args, rank, world):
     psnr_measured = quality(sn, star, plain, W, H, cams, q_step, leaf)
 
     # end to end through the public API: host inputs in, frames out, every step
-    e2e = end_to_end(sn, torch, sc, w, x_dtype, W, H, cams, args, star.tuning)
+    e2e = end_to_end(sn, torch, sc, w, x_dtype, W, H, cams, args, star.tuning, star.fuse_passes)
 
     t_step = float(np.mean(step_ms))
     t_max = t_step
@@ -405,12 +409,15 @@ def run_ours(args, rank, world):
         "data": "synthetic seeded triangle soup, orbit camera",
         "config": {"workload": desc, "frames_per_step": 2, "mlp": args.mlp, "weights": wname,
                    "resolve": "fused" if star.fused else "separate",
+                   "pass_launch_resolves": bool(star.fuse_passes and star.fused and not star.fused_fp8
+                                                and star.persistent),
                    "passes": "persistent" if star.persistent else "separate",
                    "pass2_merge_scale": star.merge_scale2,
                    "pass3_merge_scale": star.merge_scale3,
                    "fixed_scales": list(args.fixed_scales) if args.fixed_scales else None,
                    "pass_tuning": tuned,
-                   "base_tile": args.base_tile, "l2": "flushed between steps (256 MB write)",
+                   "base_tile": args.base_tile, "tau_split_merge": [star.params.tau_split, star.params.tau_merge],
+                   "l2": "flushed between steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "fragments_per_s": round(Fcount / (ms_frame * 1e-3), 1),
         "fragments_full_res": int(Fcount),
@@ -493,17 +500,18 @@ def fragment_count(sn, r, vp, W, H, size=None):
     return int(frags["total"].cpu().numpy().view(np.uint32)[0])
 
 
-def end_to_end(sn, torch, sc, w, x_dtype, W, H, cams, args, tuning=None):
+def end_to_end(sn, torch, sc, w, x_dtype, W, H, cams, args, tuning=None, fuse_passes=True):
     """Same metric through the public API from host memory: per step the
     triangle soup and the cameras are copied host->device, one real and one
     interpolated frame are rendered (the captured step), and both 8-bit frames
     are read back."""
     from paper_2606_16747_b300.pipeline import Renderer
-    r = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=x_dtype, base_tile=args.base_tile,
+    params = sn.default_params(**({"tau_split": args.tau[0], "tau_merge": args.tau[1]} if args.tau else {}))
+    r = Renderer(sc.verts, sc.rgba8, W, H, params=params, mlp=w, x_dtype=x_dtype, base_tile=args.base_tile,
                  fused=(args.mlp if args.mlp == "fp8" else True) if args.fused and x_dtype == sn.BF16 else False,
                  persistent=args.persistent, tuning=tuning,
                  merge_scale2=args.merge_scale2, merge_scale3=args.merge_scale3,
-                 fixed_scales=args.fixed_scales)
+                 fixed_scales=args.fixed_scales, fuse_passes=fuse_passes)
     r.interp_float = False      # both frames leave as 8-bit
     hv = torch.from_numpy(np.ascontiguousarray(sc.verts)).pin_memory()
     hc = torch.from_numpy(np.ascontiguousarray(sc.rgba8).view(np.int32)).pin_memory()
@@ -725,15 +733,23 @@ def main():
                          "size (1.0: only at full size, as Eq. 2 sizes it)")
     ap.add_argument("--merge-scale3", type=float, default=0.7,
                     help="the same for pass 3 (1.0: only at full size)")
+    ap.add_argument("--no-fuse-passes", dest="fuse_passes", action="store_false",
+                    help="never let the pass launch produce the frame (always the separate resolve)")
     ap.add_argument("--unfused", dest="fused", action="store_false",
                     help="separate upscale/features, MLP and composite kernels")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-leaf", action="store_true", help="skip the per-leaf pass-resolution variant")
+    ap.add_argument("--tau", default=None,
+                    help="SPLIT,MERGE: quadtree thresholds (8-bit units) instead of the library's defaults")
     ap.add_argument("--fixed-scales", default=None,
                     help="S2,S3: passes 2 and 3 at these fixed scales instead of Eq. 2's (the paper's "
                          "ablation settings, e.g. 0.5,0.5 or 0.5,0.25); merges only at full size")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    if args.tau:
+        args.tau = tuple(float(v) for v in args.tau.split(","))
+        if len(args.tau) != 2 or not args.tau[1] < args.tau[0]:
+            raise SystemExit("--tau wants SPLIT,MERGE with MERGE < SPLIT")
     if args.fixed_scales:
         args.fixed_scales = tuple(float(v) for v in args.fixed_scales.split(","))
         if len(args.fixed_scales) != 2 or not all(0.25 <= v <= 1.0 for v in args.fixed_scales):

@@ -92,7 +92,7 @@ typedef struct {
 } star_nt_target;
 
 /* Parameters of the method.  Defaults (star_nt_default_params):
- * bg = (1, 1, 1), kappa_n = 1/64, tau_split = 48, tau_merge = 24,
+ * bg = (1, 1, 1), kappa_n = 1/64, tau_split = 24, tau_merge = 12,
  * delta2 = 2.2, delta3 = 3.0 (Eq. 2), base_tile = 16, relax_iters = 2. */
 typedef struct {
     float bg[3];       /* background colour C_b of Eq. 4 */

@@ -1,7 +1,9 @@
 """Autotuner of the persistent geometry-pass launch: tries tile shapes (the
 pixel block a warp owns inside a 16 x 16 tile) and resident CTAs per SM on
-the renderer's own workload, and keeps the fastest.  Results are stored per
-workload key in a JSON file next to this module."""
+the renderer's own workload, and keeps the fastest; then, with that shape,
+whether the pass launch should also produce the frame when every pass runs at
+full size (the network inside the pass launch against the separate resolve).
+Results are stored per workload key in a JSON file next to this module."""
 from __future__ import annotations
 
 import json
@@ -17,31 +19,61 @@ def workload_key(renderer) -> str:
     return f"{renderer.W}x{renderer.H}_T{renderer.T}"
 
 
+def time_stages(renderer, names, reps=10) -> float:
+    """Average ms of the named stages of one real frame, replayed back to back
+    as one graph."""
+    stages = dict(renderer.star_stages())
+    fns = [stages[n] for n in names]
+
+    def run():
+        for fn in fns:
+            fn()
+
+    g = renderer.capture(run)
+    g.replay()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
 def time_passes(renderer, tuning, reps=10) -> float:
     """Average ms of one persistent pass launch (graph replays back to back)."""
     old = renderer.tuning, renderer.persistent
     renderer.tuning, renderer.persistent = tuning, True
     try:
-        fn = dict(renderer.star_stages())["passes"]
-        g = renderer.capture(fn)
-        g.replay()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            g.replay()
-        e1.record()
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / reps
+        return time_stages(renderer, ["passes"], reps)
     finally:
         renderer.tuning, renderer.persistent = old
 
 
 def tune(renderer, candidates=CANDIDATES, reps=10) -> dict:
     """Time every candidate on the renderer's current frame state (bins and
-    pass sizes must be those of a real frame) and return the fastest."""
+    pass sizes must be those of a real frame) and return the fastest, with the
+    fused-resolve choice when the renderer can make it (a tie, for instance
+    when a reduced pass is not merged in the current frame, keeps it on)."""
     times = {f"{bw}x{32 // bw}/{k}": time_passes(renderer, (bw, k), reps) for bw, k in candidates}
     best = min(candidates, key=lambda c: times[f"{c[0]}x{32 // c[0]}/{c[1]}"])
-    return {"block_w": best[0], "ctas_per_sm": best[1], "ms": times}
+    out = {"block_w": best[0], "ctas_per_sm": best[1], "ms": times}
+    if getattr(renderer, "leaf", False) or not (renderer.fused and not renderer.fused_fp8):
+        return out
+    old = renderer.tuning, renderer.persistent, renderer.fuse_passes
+    renderer.tuning, renderer.persistent = best, True
+    try:
+        both = {}
+        for fuse in (True, False):
+            renderer.fuse_passes = fuse
+            # the raster resets the frame's resolved mark, so both settings
+            # start every replay from the same state
+            both[fuse] = time_stages(renderer, ["raster", "passes", "resolve"], reps)
+    finally:
+        renderer.tuning, renderer.persistent, renderer.fuse_passes = old
+    out["fuse_passes"] = both[True] <= both[False]
+    out["raster_passes_resolve_ms"] = {"pass launch resolves": both[True], "separate resolve": both[False]}
+    return out
 
 
 def load(key: str):

@@ -248,8 +248,8 @@ extern "C" void star_nt_default_params(star_nt_params *p) {
   if (!p) return;
   p->bg[0] = p->bg[1] = p->bg[2] = 1.0f;
   p->kappa_n = 1.0f / 64.0f;
-  p->tau_split = 48.0;
-  p->tau_merge = 24.0;
+  p->tau_split = 24.0;
+  p->tau_merge = 12.0;
   p->delta2 = 2.2;
   p->delta3 = 3.0;
   p->base_tile = 16;

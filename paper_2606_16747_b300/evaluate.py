@@ -73,16 +73,21 @@ def main(argv=None):
     ap.add_argument("--merge-scale2", type=float, default=0.5)
     ap.add_argument("--merge-scale3", type=float, default=0.7)
     ap.add_argument("--mlp", default="bf16", choices=["bf16", "fp8"])
+    ap.add_argument("--tau", default=None, help="SPLIT,MERGE quadtree thresholds (8-bit units)")
     args = ap.parse_args(argv)
     build.build()
     sc = {"hd": scenes.hd_scene, "uhd": scenes.uhd_scene, "small": scenes.small_scene}[args.workload]()
     W, H = sc.width, sc.height
     w = dict(np.load(os.path.join(HERE, "weights", "tail_mlp.npz")))
-    star = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=sn.BF16,
+    tau = {}
+    if args.tau:
+        ts, tm = (float(v) for v in args.tau.split(","))
+        tau = {"tau_split": ts, "tau_merge": tm}
+    star = Renderer(sc.verts, sc.rgba8, W, H, params=sn.default_params(**tau), mlp=w, x_dtype=sn.BF16,
                     fused="fp8" if args.mlp == "fp8" else True, persistent=True,
                     base_tile=args.base_tile, merge_scale2=args.merge_scale2,
                     merge_scale3=args.merge_scale3)
-    leaf = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=sn.BF16,
+    leaf = Renderer(sc.verts, sc.rgba8, W, H, params=sn.default_params(**tau), mlp=w, x_dtype=sn.BF16,
                     fused="fp8" if args.mlp == "fp8" else True, base_tile=args.base_tile, leaf=True)
     ref = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=sn.F32)
     cams = scenes.orbit_cameras(W, H, args.frames + 1)
@@ -135,7 +140,7 @@ def main(argv=None):
     mean = {k: float(np.mean(v)) for k, v in err.items()}
     e_rand = mean["unsorted_over"]
     out = {"workload": f"{args.workload} {W}x{H}, {sc.verts.shape[0]} triangles", "frames": args.frames,
-           "base_tile": args.base_tile, "pass2_merge_scale": args.merge_scale2,
+           "base_tile": args.base_tile, "tau_split_merge": [star.params.tau_split, star.params.tau_merge], "pass2_merge_scale": args.merge_scale2,
            "pass3_merge_scale": args.merge_scale3, "mlp": args.mlp,
            "mean_mse": {k: float(f"{v:.4e}") for k, v in mean.items()},
            "psnr_of_mean_mse_db": {k: round(10 * math.log10(1 / v), 3) for k, v in mean.items()},
