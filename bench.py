@@ -50,11 +50,11 @@ def kernels_per_step(r) -> int:
     return 3 + passes + (1 if r.fused else 3) + 3 + 2
 STAGE_REPS = 20
 # DRAM bytes (read + write) of one k_passes launch at 1080p, from the ncu
-# capture summarised in profiles/passes_hd.md (same kernel build, s3 = 0.68)
-PASSES_DRAM_BYTES = 13958656
+# capture summarised in profiles/passes_hd.md (same kernel build; pass 3 separate at s3 = 0.91)
+PASSES_DRAM_BYTES = 27639296
 # the same for one k_passes_resolve launch (passes at full size + MLP + composite),
 # profiles/passes_resolve_hd.md
-FUSED_DRAM_BYTES = 12969984
+FUSED_DRAM_BYTES = 12742144
 
 
 def load_peaks():
