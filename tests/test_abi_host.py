@@ -118,3 +118,51 @@ def test_leaf_arguments_rejected(sn):
                                           None, None, None) == sn.ERR_ARG
     assert L.star_nt_resolve_leaf(ctypes.byref(sc), ctypes.byref(plan), None, 16, None, None, 1, None, None,
                                   None, None) == sn.ERR_ARG
+
+
+def test_pass_launch_resolve_arguments_rejected(sn):
+    L = sn.lib()
+    sc = sn.Scene(16, 16, 5)
+    bins = sn.Bins(256, 1 << 20, 64, 64, 16, 1 << 10)
+    lay = sn.Layers(16, 16, 16, 16, 16, 16)
+    p = sn.default_params()
+    w = sn.Mlp(16, 16, 16, 16, 16, 16)
+    # no frame output, a misaligned frame, missing weights, the same workspace twice
+    assert L.star_nt_geometry_passes_resolve(ctypes.byref(sc), ctypes.byref(bins), ctypes.byref(bins),
+                                             ctypes.byref(bins), ctypes.byref(lay), ctypes.byref(lay),
+                                             ctypes.byref(lay), ctypes.byref(p), ctypes.byref(w), None,
+                                             None, None, None, None) == sn.ERR_ARG
+    b2 = sn.Bins(512, 1 << 20, 64, 64, 16, 1 << 10)
+    b3 = sn.Bins(768, 1 << 20, 64, 64, 16, 1 << 10)
+    assert L.star_nt_geometry_passes_resolve(ctypes.byref(sc), ctypes.byref(bins), ctypes.byref(b2),
+                                             ctypes.byref(b3), ctypes.byref(lay), ctypes.byref(lay),
+                                             ctypes.byref(lay), ctypes.byref(p), ctypes.byref(w), 24,
+                                             None, None, None, None) == sn.ERR_ARG
+    w0 = sn.Mlp(16, None, 16, 16, 16, 16)
+    assert L.star_nt_geometry_passes_resolve(ctypes.byref(sc), ctypes.byref(bins), ctypes.byref(b2),
+                                             ctypes.byref(b3), ctypes.byref(lay), ctypes.byref(lay),
+                                             ctypes.byref(lay), ctypes.byref(p), ctypes.byref(w0), 32,
+                                             None, None, None, None) == sn.ERR_ARG
+    assert L.star_nt_geometry_passes_resolve(ctypes.byref(sc), ctypes.byref(bins), ctypes.byref(bins),
+                                             ctypes.byref(b3), ctypes.byref(lay), ctypes.byref(lay),
+                                             ctypes.byref(lay), ctypes.byref(p), ctypes.byref(w), 32,
+                                             None, None, None, None) == sn.ERR_ARG
+    bad = sn.Tuning(5, 0)   # block width must be 4, 8 or 16
+    assert L.star_nt_geometry_passes_resolve(ctypes.byref(sc), ctypes.byref(bins), ctypes.byref(b2),
+                                             ctypes.byref(b3), ctypes.byref(lay), ctypes.byref(lay),
+                                             ctypes.byref(lay), ctypes.byref(p), ctypes.byref(w), 32,
+                                             None, ctypes.byref(bad), None, None) == sn.ERR_ARG
+
+
+def test_leaf_passes_workspace_checked(sn):
+    L = sn.lib()
+    plan = sn.leaf_plan(64, 64, sn.default_params())
+    need = sn.leaf_ws_bytes(plan)
+    sc = sn.Scene(16, 16, 5)
+    bins = (sn.Bins * plan.n_targets)()
+    lays = (sn.Layers * plan.n_targets)()
+    # a workspace one byte short, then a misaligned one
+    assert L.star_nt_geometry_passes_leaf(ctypes.byref(sc), ctypes.byref(plan), bins, lays, 16, 256,
+                                          need - 1, None, None, None) == sn.ERR_ARG
+    assert L.star_nt_geometry_passes_leaf(ctypes.byref(sc), ctypes.byref(plan), bins, lays, 16, 272,
+                                          need, None, None, None) == sn.ERR_ARG

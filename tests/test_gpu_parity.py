@@ -658,6 +658,34 @@ def test_persistent_passes_equal_separate(sn, tuning, sizes):
         assert torch.equal(a, b)
 
 
+def test_pass_launch_resolve_empty_and_overflow(sn):
+    """The pass launch that produces the frame: a scene whose triangles are
+    all behind the camera gives the background everywhere; too small a pair
+    capacity raises STAR_NT_ERR_CAPACITY in the status word (nothing hangs,
+    nothing is written out of bounds)."""
+    from paper_2606_16747_b300.pipeline import Renderer
+    sc = scenes.screen_scene(29, 600, 200, 136, size_scale=0.7)
+    W, H = sc.width, sc.height
+    behind = sc.verts.copy()
+    behind[..., 3] = -1.0      # w < 0: every triangle culled
+    r = Renderer(behind, sc.rgba8, W, H, mlp=scenes.mlp_xavier(4), x_dtype=sn.BF16, fused=True,
+                 persistent=True, params=sn.default_params(bg=(0.25, 0.5, 0.75)))
+    r.set_camera(sc.cam.vp32)
+    r.star_frame(update_tiles=False)
+    torch.cuda.synchronize()
+    r.check_status()
+    assert int(r.bins[1].mem[44:48].view(torch.int32).item()) == 1   # the pass launch resolved it
+    rgb = r.rgba32f.cpu().numpy().reshape(-1, 4)
+    assert np.array_equal(rgb[:, :3], np.tile(np.float32([0.25, 0.5, 0.75]), (W * H, 1)))
+    assert (r.l1["id1"].cpu().numpy() == -1).all()
+    small = Renderer(sc.verts, sc.rgba8, W, H, mlp=scenes.mlp_xavier(4), x_dtype=sn.BF16, fused=True,
+                     persistent=True, pair_capacity=64)
+    small.set_camera(sc.cam.vp32)
+    small.star_frame(update_tiles=False)
+    torch.cuda.synchronize()
+    assert int(small.status.item()) == sn.ERR_CAPACITY
+
+
 def test_fixed_scales(orc, sn):
     """Fixed pass scales (the paper's ablation settings): every frame runs
     passes 2 and 3 at ceil(s W) x ceil(s H) whatever the quadtree's Eq. 2 says,
