@@ -148,7 +148,7 @@ def run_ours(args, rank, world):
     w, wname = mlp_weights()
     x_dtype = sn.F32 if args.mlp == "f32" else sn.BF16
     # fused resolve: bf16 or fp8 operands on tcgen05 (f32 runs the separate kernels)
-    fused_kind = (args.mlp if args.mlp == "fp8" else True) if args.fused and x_dtype == sn.BF16 else False
+    fused_kind = (args.mlp if args.mlp in ("fp8", "fp8x2") else True) if args.fused and x_dtype == sn.BF16 else False
     params = sn.default_params(**({"tau_split": args.tau[0], "tau_merge": args.tau[1]} if args.tau else {}))
     star = Renderer(sc.verts, sc.rgba8, W, H, params=params, mlp=w, x_dtype=x_dtype, base_tile=args.base_tile,
                     fused=fused_kind, persistent=args.persistent,
@@ -402,7 +402,7 @@ def run_ours(args, rank, world):
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": {"bf16": "f32+bf16", "fp8": "f32+e4m3", "f32": "f32"}[args.mlp],
+        "dtype": {"bf16": "f32+bf16", "fp8": "f32+e4m3", "fp8x2": "f32+e4m3x2", "f32": "f32"}[args.mlp],
         "data": "synthetic seeded triangle soup, orbit camera",
         "config": {"workload": desc, "frames_per_step": 2, "mlp": args.mlp, "weights": wname,
                    "resolve": "fused" if star.fused else "separate",
@@ -521,7 +521,7 @@ def end_to_end(sn, torch, sc, w, x_dtype, W, H, cams, args, tuning=None, fuse_pa
     from paper_2606_16747_b300.pipeline import Renderer
     params = sn.default_params(**({"tau_split": args.tau[0], "tau_merge": args.tau[1]} if args.tau else {}))
     r = Renderer(sc.verts, sc.rgba8, W, H, params=params, mlp=w, x_dtype=x_dtype, base_tile=args.base_tile,
-                 fused=(args.mlp if args.mlp == "fp8" else True) if args.fused and x_dtype == sn.BF16 else False,
+                 fused=(args.mlp if args.mlp in ("fp8", "fp8x2") else True) if args.fused and x_dtype == sn.BF16 else False,
                  persistent=args.persistent, tuning=tuning,
                  merge_scale2=args.merge_scale2, merge_scale3=args.merge_scale3,
                  fixed_scales=args.fixed_scales, fuse_passes=fuse_passes)
@@ -735,7 +735,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="hd", choices=["hd", "uhd", "small"])
-    ap.add_argument("--mlp", default="bf16", choices=["bf16", "fp8", "f32"])
+    ap.add_argument("--mlp", default="bf16", choices=["bf16", "fp8", "fp8x2", "f32"])
     ap.add_argument("--base-tile", type=int, default=64, choices=[16, 64],
                     help="quadtree base tile (64: leaves of 8 to 64 pixels)")
     ap.add_argument("--separate-passes", dest="persistent", action="store_false",

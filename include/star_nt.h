@@ -315,6 +315,20 @@ star_nt_status star_nt_resolve_fp8(const star_nt_scene *scene, const star_nt_bin
                                    const star_nt_mlp *w, float *rgba32f, uint32_t *rgba8,
                                    int32_t *d_status, void *stream);
 
+/* star_nt_resolve_fp8x2 -- star_nt_resolve_fp8 with compensated operands:    */
+/* every weight and activation as a pair of e4m3 values hi + lo (hi = e4m3 of */
+/* the scaled value, lo = e4m3 of the remainder) under one power-of-two row   */
+/* scale, and the four products hi.hi + lo.hi + hi.lo + lo.lo accumulated in  */
+/* fp32 on the tensor cores (kind::f8f6f4).  Each operand keeps about 2^-8    */
+/* relative rounding, as a bf16 operand does, for four times the e4m3 MMA     */
+/* work.  Same arguments and errors as star_nt_resolve.                       */
+star_nt_status star_nt_resolve_fp8x2(const star_nt_scene *scene, const star_nt_bins *bins2,
+                                     const star_nt_bins *bins3, const star_nt_layers *layers1,
+                                     const star_nt_layers *layers2, const star_nt_layers *layers3,
+                                     int32_t W, int32_t H, const star_nt_params *params,
+                                     const star_nt_mlp *w, float *rgba32f, uint32_t *rgba8,
+                                     int32_t *d_status, void *stream);
+
 /* star_nt_geometry_passes_resolve: star_nt_geometry_passes that, when both
  * reduced passes are merged into pass 1 (their bins marked merged: every pass
  * at the full resolution), also produces the frame: pass 1's tiles run the
@@ -425,7 +439,8 @@ star_nt_status star_nt_quadtree_static(const uint32_t *rgba8, const int32_t *id1
 /* are read from the quadtree masks (star_nt_quadtree's mask_out of the      */
 /* previous frame).                                                          */
 
-#define STAR_NT_E4M3 2 /* MLP operand type of star_nt_resolve_leaf: FP8 e4m3 */
+#define STAR_NT_E4M3 2   /* MLP operand type of star_nt_resolve_leaf: FP8 e4m3 */
+#define STAR_NT_E4M3X2 3 /* ... compensated FP8: e4m3 pairs (star_nt_resolve_fp8x2) */
 #define STAR_NT_LEAF_MAX_TARGETS 9
 
 typedef struct {
@@ -469,7 +484,8 @@ star_nt_status star_nt_geometry_passes_leaf(const star_nt_scene *scene,
 /* star_nt_resolve_leaf: star_nt_resolve with each pixel's pass-2 and pass-3
  * planes taken from the targets of its leaf level (layers and masks as in
  * star_nt_geometry_passes_leaf).  mlp_type: STAR_NT_BF16 (star_nt_resolve's
- * MLP) or STAR_NT_E4M3 (star_nt_resolve_fp8's).  Primitive ids read from the
+ * MLP), STAR_NT_E4M3 (star_nt_resolve_fp8's) or STAR_NT_E4M3X2
+ * (star_nt_resolve_fp8x2's).  Primitive ids read from the
  * planes are bounds-checked against scene->n_tris. */
 star_nt_status star_nt_resolve_leaf(const star_nt_scene *scene, const star_nt_leaf_plan *plan,
                                     const star_nt_layers *layers, const uint32_t *masks,

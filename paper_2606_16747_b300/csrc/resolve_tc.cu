@@ -472,24 +472,312 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
                  : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// Compensated FP8: every operand, weights and activations, as a pair of e4m3
+// values hi + lo under one power-of-two row scale (split4_e4m3), and the four
+// products hi.hi + lo.hi + hi.lo + lo.lo accumulated in fp32 by the tensor
+// cores.  Each operand then carries about 2^-8 relative rounding, as a bf16
+// operand does, for four times the e4m3 MMA work.  Layer 1 packs the four
+// products into the K = 32 of one MMA (the 5 inputs in each 8-element group:
+// A = [xh | xl | xh | xl], B = [wh | wh | wl | wl]); layer 2 takes four MMAs
+// (H1 hi / lo against W2 hi / lo); layer 3 two (A = [H2 hi | H2 lo] against
+// [W3 hi | W3 hi] and [W3 lo | W3 lo]).
+
+// shared memory map (bytes from a 1024-aligned base).  Per tile 8192 bytes
+// hold X (two core columns), then H1 hi and lo (two core columns each), then
+// H2 hi and lo (one each); each is written after the MMAs that read the
+// previous one completed.
+constexpr uint32_t kC8T = 0;       // tile t: kC8T + 8192 t
+constexpr uint32_t kC8W1 = 16384;  // N=32, K=32: 2 x 512
+constexpr uint32_t kC8W2 = 17408;  // hi, then lo: N=16, K=32: 2 x 256 each
+constexpr uint32_t kC8W3 = 18432;  // [hi | hi], then [lo | lo]: N=16, K=32: 2 x 256 each
+constexpr uint32_t kC8B = 19456;   // b1[32], b2[16], b3[16]
+constexpr uint32_t kC8S = 19712;   // inverse weight-row scales: 1/s1[32], 1/s2[16], 1/s3[16]
+constexpr uint32_t kC8Bar = 19968; // mma barrier, tmem slot, abort flag
+constexpr uint32_t kC8Used = 19984;
+
+// one e4m3 byte into the K-major core-matrix layout of a B operand
+__device__ __forceinline__ void put_b8(uint8_t *base, int n, int k, int lbo, uint8_t q) {
+  base[(k >> 4) * lbo + n * 16 + (k & 15)] = q;
+}
+
+// the row scale of row n of a [rows][cols] weight matrix (1/s stored in inv)
+__device__ __forceinline__ float weight_row_scale(const float *w, int n, int cols, float *inv) {
+  float mx = 0.0f;
+  for (int k = 0; k < cols; ++k) mx = fmaxf(mx, fabsf(w[n * cols + k]));
+  const float sc = row_scale(mx);
+  inv[n] = 1.0f / sc;  // exact: a power of two
+  return sc;
+}
+
+template <class In>
+__global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
+    k_resolve_fp8x2(In in, float bg0, float bg1, float bg2, float kappa,
+                    const float *__restrict__ w1, const float *__restrict__ b1,
+                    const float *__restrict__ w2, const float *__restrict__ b2,
+                    const float *__restrict__ w3, const float *__restrict__ b3,
+                    float4 *__restrict__ out, uint32_t *__restrict__ out8, int32_t *status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                            ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t sbase = smem_u32(sm);
+  const uint32_t bar = sbase + kC8Bar;
+  uint32_t *s_tmem = reinterpret_cast<uint32_t *>(sm + kC8Bar + 8);
+  volatile int *s_abort = reinterpret_cast<volatile int *>(sm + kC8Bar + 12);
+  float *sb = reinterpret_cast<float *>(sm + kC8B);
+  float *si = reinterpret_cast<float *>(sm + kC8S);
+  if (in.rejected()) return;  // a rejected pass, or the frame is already done
+
+  // weights: e4m3 pairs with power-of-two row scales, zero padded; biases fp32
+  for (int i = tid; i < (int)(kC8B - kC8W1) / 4; i += kRThreads)
+    reinterpret_cast<uint32_t *>(sm + kC8W1)[i] = 0u;
+  __syncthreads();
+  if (tid < 32) {
+    const int n = tid;
+    const float sc = weight_row_scale(w1, n, 5, si);
+    for (int k = 0; k < 5; ++k) {
+      uint8_t h, l;
+      split_w8(w1[n * 5 + k] * sc, h, l);
+      put_b8(sm + kC8W1, n, k, 512, h);
+      put_b8(sm + kC8W1, n, k + 8, 512, h);
+      put_b8(sm + kC8W1, n, k + 16, 512, l);
+      put_b8(sm + kC8W1, n, k + 24, 512, l);
+    }
+  } else if (tid < 48) {
+    const int n = tid - 32;
+    const float sc = weight_row_scale(w2, n, 32, si + 32);
+    for (int k = 0; k < 32; ++k) {
+      uint8_t h, l;
+      split_w8(w2[n * 32 + k] * sc, h, l);
+      put_b8(sm + kC8W2, n, k, 256, h);
+      put_b8(sm + kC8W2 + 512, n, k, 256, l);
+    }
+  } else if (tid < 51) {
+    const int n = tid - 48;
+    const float sc = weight_row_scale(w3, n, 16, si + 48);
+    for (int k = 0; k < 16; ++k) {
+      uint8_t h, l;
+      split_w8(w3[n * 16 + k] * sc, h, l);
+      put_b8(sm + kC8W3, n, k, 256, h);
+      put_b8(sm + kC8W3, n, k + 16, 256, h);
+      put_b8(sm + kC8W3 + 512, n, k, 256, l);
+      put_b8(sm + kC8W3 + 512, n, k + 16, 256, l);
+    }
+  } else if (tid < 64) {
+    si[tid] = 0.0f;
+  }
+  if (tid < 32) sb[tid] = b1[tid];
+  if (tid < 16) sb[32 + tid] = b2[tid];
+  if (tid < 16) sb[48 + tid] = tid < 3 ? b3[tid] : 0.0f;
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    *s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(s_tmem)),
+                 "r"(kRTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *s_tmem;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const int row = tid;
+
+  const uint64_t dW1 = smem_desc(sbase + kC8W1, 512, 128);
+  const uint64_t dW2h = smem_desc(sbase + kC8W2, 256, 128);
+  const uint64_t dW2l = smem_desc(sbase + kC8W2 + 512, 256, 128);
+  const uint64_t dW3h = smem_desc(sbase + kC8W3, 256, 128);
+  const uint64_t dW3l = smem_desc(sbase + kC8W3 + 512, 256, 128);
+  const int P = in.W * in.H;  // < 2^31, checked by the host
+  const int nrounds = (P + kRTiles * kRRows - 1) / (kRTiles * kRRows);
+  uint32_t ph = 0u;
+
+  for (int round = blockIdx.x; round < nrounds; round += gridDim.x) {
+    const int base = round * (kRTiles * kRRows);
+    float4 front[kRTiles];
+    bool flag[kRTiles];
+    float sh[kRTiles];  // row scale of the operand of the next MMA
+#pragma unroll
+    for (int t = 0; t < kRTiles; ++t) {
+      const int p = base + t * kRRows + row;
+      float xv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      front[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (p < P) {
+        const int y = (int)((unsigned)p / (unsigned)in.W), x = p - y * in.W;
+        pixel_features(in, bg0, bg1, bg2, kappa, x, y, xv, front[t]);
+      }
+      flag[t] = xv[5] != 0.0f;
+      float mx = 0.0f;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) mx = fmaxf(mx, fabsf(xv[k]));
+      sh[t] = row_scale(mx);
+      uint32_t h0, l0, h1, l1;
+      split4_e4m3(xv[0] * sh[t], xv[1] * sh[t], xv[2] * sh[t], xv[3] * sh[t], h0, l0);
+      split4_e4m3(xv[4] * sh[t], 0.f, 0.f, 0.f, h1, l1);
+      const uint4 q = make_uint4(h0, h1, l0, l1);  // K 0..15: xh, 0, xl, 0
+      uint8_t *a = sm + kC8T + t * 8192 + row * 16;
+      *reinterpret_cast<uint4 *>(a) = q;
+      *reinterpret_cast<uint4 *>(a + 2048) = q;  // K 16..31: the same
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    // ---- layer 1: [xh | xl | xh | xl] (K = 32) against [wh | wh | wl | wl]
+    if (tid == 0) {
+      fence_after();
+#pragma unroll
+      for (int t = 0; t < kRTiles; ++t)
+        mma_e4m3(tmem + 32 * t, smem_desc(sbase + kC8T + t * 8192, 2048, 128), dW1, idesc_e4m3(32), 0u);
+      mma_commit(bar);
+    }
+    mma_wait_cta(bar, ph, s_abort);
+    ph ^= 1u;
+#pragma unroll
+    for (int t = 0; t < kRTiles; ++t) {
+      float d[32];
+      tmem_ld32(tmem + lane_base + 32 * t, d);
+      const float k1 = 1.0f / sh[t];  // exact: a power of two
+      float mx = 0.0f;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        d[j] = fmaxf(fmaf(d[j], k1 * si[j], sb[j]), 0.0f);
+        mx = fmaxf(mx, d[j]);
+      }
+      sh[t] = row_scale(mx);
+      uint32_t ph8[8], pl8[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        split4_e4m3(d[4 * j] * sh[t], d[4 * j + 1] * sh[t], d[4 * j + 2] * sh[t], d[4 * j + 3] * sh[t],
+                    ph8[j], pl8[j]);
+      uint8_t *h = sm + kC8T + t * 8192 + row * 16;
+      *reinterpret_cast<uint4 *>(h) = make_uint4(ph8[0], ph8[1], ph8[2], ph8[3]);
+      *reinterpret_cast<uint4 *>(h + 2048) = make_uint4(ph8[4], ph8[5], ph8[6], ph8[7]);
+      *reinterpret_cast<uint4 *>(h + 4096) = make_uint4(pl8[0], pl8[1], pl8[2], pl8[3]);
+      *reinterpret_cast<uint4 *>(h + 6144) = make_uint4(pl8[4], pl8[5], pl8[6], pl8[7]);
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    if (*s_abort) break;
+    // ---- layer 2: (H1 hi + H1 lo) (W2 hi + W2 lo), four MMAs of K = 32
+    if (tid == 0) {
+      fence_after();
+#pragma unroll
+      for (int t = 0; t < kRTiles; ++t) {
+        const uint64_t ah = smem_desc(sbase + kC8T + t * 8192, 2048, 128);
+        const uint64_t al = smem_desc(sbase + kC8T + t * 8192 + 4096, 2048, 128);
+        mma_e4m3(tmem + 32 * t, ah, dW2h, idesc_e4m3(16), 0u);
+        mma_e4m3(tmem + 32 * t, al, dW2h, idesc_e4m3(16), 1u);
+        mma_e4m3(tmem + 32 * t, ah, dW2l, idesc_e4m3(16), 1u);
+        mma_e4m3(tmem + 32 * t, al, dW2l, idesc_e4m3(16), 1u);
+      }
+      mma_commit(bar);
+    }
+    mma_wait_cta(bar, ph, s_abort);
+    ph ^= 1u;
+#pragma unroll
+    for (int t = 0; t < kRTiles; ++t) {
+      float d[16];
+      tmem_ld16(tmem + lane_base + 32 * t, d);
+      const float k2 = 1.0f / sh[t];
+      float mx = 0.0f;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        d[j] = fmaxf(fmaf(d[j], k2 * si[32 + j], sb[32 + j]), 0.0f);
+        mx = fmaxf(mx, d[j]);
+      }
+      sh[t] = row_scale(mx);
+      uint32_t ph4[4], pl4[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        split4_e4m3(d[4 * j] * sh[t], d[4 * j + 1] * sh[t], d[4 * j + 2] * sh[t], d[4 * j + 3] * sh[t],
+                    ph4[j], pl4[j]);
+      uint8_t *h = sm + kC8T + t * 8192 + row * 16;
+      *reinterpret_cast<uint4 *>(h) = make_uint4(ph4[0], ph4[1], ph4[2], ph4[3]);
+      *reinterpret_cast<uint4 *>(h + 2048) = make_uint4(pl4[0], pl4[1], pl4[2], pl4[3]);
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    if (*s_abort) break;
+    // ---- layer 3: [H2 hi | H2 lo] against [W3 hi | W3 hi] + [W3 lo | W3 lo],
+    // D3 in columns 16..31
+    if (tid == 0) {
+      fence_after();
+#pragma unroll
+      for (int t = 0; t < kRTiles; ++t) {
+        const uint64_t a = smem_desc(sbase + kC8T + t * 8192, 2048, 128);
+        mma_e4m3(tmem + 32 * t + 16, a, dW3h, idesc_e4m3(16), 0u);
+        mma_e4m3(tmem + 32 * t + 16, a, dW3l, idesc_e4m3(16), 1u);
+      }
+      mma_commit(bar);
+    }
+    mma_wait_cta(bar, ph, s_abort);
+    ph ^= 1u;
+    // ---- composite, Eq. 4
+#pragma unroll
+    for (int t = 0; t < kRTiles; ++t) {
+      float d[4];
+      tmem_ld4(tmem + lane_base + 32 * t + 16, d);
+      const int p = base + t * kRRows + row;
+      if (p < P) {
+        const float k3 = 1.0f / sh[t];
+        float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+        if (flag[t]) {
+          f0 = fmaxf(fmaf(d[0], k3 * si[48], sb[48]), 0.0f);
+          f1 = fmaxf(fmaf(d[1], k3 * si[49], sb[49]), 0.0f);
+          f2 = fmaxf(fmaf(d[2], k3 * si[50], sb[50]), 0.0f);
+        }
+        const float4 fr = front[t];
+        const float r = fmaf(fr.w, f0, fr.x), g = fmaf(fr.w, f1, fr.y), b = fmaf(fr.w, f2, fr.z);
+        if (out) out[p] = make_float4(r, g, b, 1.0f);
+        if (out8) out8[p] = quantize_rgba8(r, g, b);
+      }
+    }
+    fence_before();
+    __syncthreads();
+    if (*s_abort) break;
+  }
+  if (*s_abort && tid == 0) raise_status(status, STAR_NT_ERR_TIMEOUT);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kRTmemCols)
+                 : "memory");
+}
+
 }  // namespace star
 
 using namespace star;
 
-// Launch of either resolve kernel on input In (the grid: one CTA per round
-// of two 128-pixel tiles, at most 8 CTAs per SM).
+// MLP operand kinds of the resolve kernels
+enum ResolveKind { kResolveBf16 = 0, kResolveFp8 = 1, kResolveFp8x2 = 2 };
+
+// Launch of a resolve kernel on input In (the grid: one CTA per round of two
+// 128-pixel tiles, at most 8 CTAs per SM).
 template <class In>
-static star_nt_status launch_kernel(bool fp8, const In &in, const star_nt_params *params,
+static star_nt_status launch_kernel(int kind, const In &in, const star_nt_params *params,
                                     const star_nt_mlp *w, float *rgba32f, uint32_t *rgba8,
                                     int32_t *d_status, void *stream) {
   static_assert(kQUsed + 1024 <= kQSmem, "shared memory map");
   static_assert(kF8Used + 1024 <= kQSmem, "shared memory map");
-  auto kern = fp8 ? k_resolve_fp8<In> : k_resolve<In>;
-  static bool attr[2] = {false, false};
-  if (!attr[fp8]) {
+  static_assert(kC8Used + 1024 <= kQSmem, "shared memory map");
+  auto kern = kind == kResolveFp8x2 ? k_resolve_fp8x2<In>
+              : kind == kResolveFp8 ? k_resolve_fp8<In>
+                                    : k_resolve<In>;
+  static bool attr[3] = {false, false, false};
+  if (!attr[kind]) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kQSmem) != cudaSuccess)
       return STAR_NT_ERR_CUDA;
-    attr[fp8] = true;
+    attr[kind] = true;
   }
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
@@ -507,7 +795,7 @@ static bool mlp_ok(const star_nt_mlp *w) {
   return w && w->w1 && w->b1 && w->w2 && w->b2 && w->w3 && w->b3;
 }
 
-static star_nt_status launch_resolve(bool fp8, const star_nt_scene *scene, const star_nt_bins *b2,
+static star_nt_status launch_resolve(int kind, const star_nt_scene *scene, const star_nt_bins *b2,
                                      const star_nt_bins *b3, const star_nt_layers *l1,
                                      const star_nt_layers *l2, const star_nt_layers *l3, int32_t W,
                                      int32_t H, const star_nt_params *params, const star_nt_mlp *w,
@@ -524,7 +812,7 @@ static star_nt_status launch_resolve(bool fp8, const star_nt_scene *scene, const
   BinsView v2 = bins_view(*b2), v3 = bins_view(*b3);
   FeatIn in{W, H, v2.hd, v3.hd, scene->rgba8, l1->id1, l2->id2, l3->n,
             reinterpret_cast<const uint4 *>(l3->tail), l3->t_tail};
-  return launch_kernel(fp8, in, params, w, rgba32f, rgba8, d_status, stream);
+  return launch_kernel(kind, in, params, w, rgba32f, rgba8, d_status, stream);
 }
 
 extern "C" star_nt_status star_nt_resolve(const star_nt_scene *scene, const star_nt_bins *b2,
@@ -533,8 +821,8 @@ extern "C" star_nt_status star_nt_resolve(const star_nt_scene *scene, const star
                                           int32_t W, int32_t H, const star_nt_params *params,
                                           const star_nt_mlp *w, float *rgba32f, uint32_t *rgba8,
                                           int32_t *d_status, void *stream) {
-  return launch_resolve(false, scene, b2, b3, l1, l2, l3, W, H, params, w, rgba32f, rgba8, d_status,
-                        stream);
+  return launch_resolve(kResolveBf16, scene, b2, b3, l1, l2, l3, W, H, params, w, rgba32f, rgba8,
+                        d_status, stream);
 }
 
 extern "C" star_nt_status star_nt_resolve_fp8(const star_nt_scene *scene, const star_nt_bins *b2,
@@ -543,8 +831,18 @@ extern "C" star_nt_status star_nt_resolve_fp8(const star_nt_scene *scene, const 
                                               int32_t W, int32_t H, const star_nt_params *params,
                                               const star_nt_mlp *w, float *rgba32f, uint32_t *rgba8,
                                               int32_t *d_status, void *stream) {
-  return launch_resolve(true, scene, b2, b3, l1, l2, l3, W, H, params, w, rgba32f, rgba8, d_status,
-                        stream);
+  return launch_resolve(kResolveFp8, scene, b2, b3, l1, l2, l3, W, H, params, w, rgba32f, rgba8,
+                        d_status, stream);
+}
+
+extern "C" star_nt_status star_nt_resolve_fp8x2(const star_nt_scene *scene, const star_nt_bins *b2,
+                                                const star_nt_bins *b3, const star_nt_layers *l1,
+                                                const star_nt_layers *l2, const star_nt_layers *l3,
+                                                int32_t W, int32_t H, const star_nt_params *params,
+                                                const star_nt_mlp *w, float *rgba32f,
+                                                uint32_t *rgba8, int32_t *d_status, void *stream) {
+  return launch_resolve(kResolveFp8x2, scene, b2, b3, l1, l2, l3, W, H, params, w, rgba32f, rgba8,
+                        d_status, stream);
 }
 
 extern "C" star_nt_status star_nt_resolve_leaf(const star_nt_scene *scene,
@@ -555,7 +853,8 @@ extern "C" star_nt_status star_nt_resolve_leaf(const star_nt_scene *scene,
                                                int32_t *d_status, void *stream) {
   if (!scene || !plan || !layers || !masks || !params || !mlp_ok(w) || (!rgba32f && !rgba8))
     return STAR_NT_ERR_ARG;
-  if (mlp_type != STAR_NT_BF16 && mlp_type != STAR_NT_E4M3) return STAR_NT_ERR_ARG;
+  if (mlp_type != STAR_NT_BF16 && mlp_type != STAR_NT_E4M3 && mlp_type != STAR_NT_E4M3X2)
+    return STAR_NT_ERR_ARG;
   if (!leaf_plan_valid(plan)) return STAR_NT_ERR_ARG;
   if (scene->n_tris < 0 || (scene->n_tris > 0 && !scene->rgba8)) return STAR_NT_ERR_ARG;
   if ((uintptr_t)rgba32f & 15u) return STAR_NT_ERR_ARG;
@@ -587,7 +886,10 @@ extern "C" star_nt_status star_nt_resolve_leaf(const star_nt_scene *scene,
     in.tail3[k] = reinterpret_cast<const uint4 *>(layers[k].tail);
     in.t3[k] = layers[k].t_tail;
   }
-  return launch_kernel(mlp_type == STAR_NT_E4M3, in, params, w, rgba32f, rgba8, d_status, stream);
+  const int kind = mlp_type == STAR_NT_E4M3X2 ? kResolveFp8x2
+                   : mlp_type == STAR_NT_E4M3 ? kResolveFp8
+                                              : kResolveBf16;
+  return launch_kernel(kind, in, params, w, rgba32f, rgba8, d_status, stream);
 }
 
 namespace star {
@@ -599,6 +901,8 @@ cudaError_t preload_resolve_tc() {
   if ((r = cudaFuncGetAttributes(&a, k_resolve_fp8<FeatIn>)) != cudaSuccess) e = r;
   if ((r = cudaFuncGetAttributes(&a, k_resolve<FeatInLeaf>)) != cudaSuccess) e = r;
   if ((r = cudaFuncGetAttributes(&a, k_resolve_fp8<FeatInLeaf>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_resolve_fp8x2<FeatIn>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_resolve_fp8x2<FeatInLeaf>)) != cudaSuccess) e = r;
   return e;
 }
 }  // namespace star

@@ -119,6 +119,30 @@ __device__ __forceinline__ uint32_t pack4_e4m3(float v0, float v1, float v2, flo
   return r;
 }
 
+// four e4m3 bytes back to fp32, byte i -> v[i] (exact: every e4m3 value is
+// an f16 value)
+__device__ __forceinline__ void unpack4_e4m3(uint32_t q, float (&v)[4]) {
+  asm("{\n .reg .b16 a, b, h0, h1, h2, h3;\n .reg .b32 p, q;\n"
+      " mov.b32 {a, b}, %4;\n"
+      " cvt.rn.f16x2.e4m3x2 p, a;\n"
+      " cvt.rn.f16x2.e4m3x2 q, b;\n"
+      " mov.b32 {h0, h1}, p;\n"
+      " mov.b32 {h2, h3}, q;\n"
+      " cvt.f32.f16 %0, h0;\n cvt.f32.f16 %1, h1;\n cvt.f32.f16 %2, h2;\n cvt.f32.f16 %3, h3;\n}\n"
+      : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3])
+      : "r"(q));
+}
+
+// v = hi + lo + r with hi = e4m3(v), lo = e4m3(v - hi): |r| <= 2^-8 |v| for
+// normal lo (e4m3 rounds to 2^-4 of the value), 2^-10 below the normal range
+__device__ __forceinline__ void split4_e4m3(float v0, float v1, float v2, float v3, uint32_t &hi,
+                                            uint32_t &lo) {
+  hi = pack4_e4m3(v0, v1, v2, v3);
+  float d[4];
+  unpack4_e4m3(hi, d);
+  lo = pack4_e4m3(v0 - d[0], v1 - d[1], v2 - d[2], v3 - d[3]);
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                : "memory");
@@ -197,6 +221,14 @@ __device__ __forceinline__ void put_w(uint8_t *base, int n, int k, int lbo, floa
 // (16 elements per 16-byte core-matrix row)
 __device__ __forceinline__ void put_w8(uint8_t *base, int n, int k, int lbo, float v) {
   base[(k >> 4) * lbo + n * 16 + (k & 15)] = (uint8_t)(pack4_e4m3(v, 0.f, 0.f, 0.f) & 255u);
+}
+
+// the e4m3 pair (hi, lo) of split4_e4m3 for one weight, as bytes
+__device__ __forceinline__ void split_w8(float v, uint8_t &hi, uint8_t &lo) {
+  uint32_t h, l;
+  split4_e4m3(v, 0.f, 0.f, 0.f, h, l);
+  hi = (uint8_t)(h & 255u);
+  lo = (uint8_t)(l & 255u);
 }
 
 // A bias enters an MMA as two weight columns (k, k + 1) against an A operand

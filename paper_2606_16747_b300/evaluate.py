@@ -72,7 +72,7 @@ def main(argv=None):
     ap.add_argument("--base-tile", type=int, default=64, choices=[16, 64])
     ap.add_argument("--merge-scale2", type=float, default=0.5)
     ap.add_argument("--merge-scale3", type=float, default=0.7)
-    ap.add_argument("--mlp", default="bf16", choices=["bf16", "fp8"])
+    ap.add_argument("--mlp", default="bf16", choices=["bf16", "fp8", "fp8x2"])
     ap.add_argument("--tau", default=None, help="SPLIT,MERGE quadtree thresholds (8-bit units)")
     args = ap.parse_args(argv)
     build.build()
@@ -84,11 +84,11 @@ def main(argv=None):
         ts, tm = (float(v) for v in args.tau.split(","))
         tau = {"tau_split": ts, "tau_merge": tm}
     star = Renderer(sc.verts, sc.rgba8, W, H, params=sn.default_params(**tau), mlp=w, x_dtype=sn.BF16,
-                    fused="fp8" if args.mlp == "fp8" else True, persistent=True,
+                    fused=args.mlp if args.mlp in ("fp8", "fp8x2") else True, persistent=True,
                     base_tile=args.base_tile, merge_scale2=args.merge_scale2,
                     merge_scale3=args.merge_scale3)
     leaf = Renderer(sc.verts, sc.rgba8, W, H, params=sn.default_params(**tau), mlp=w, x_dtype=sn.BF16,
-                    fused="fp8" if args.mlp == "fp8" else True, base_tile=args.base_tile, leaf=True)
+                    fused=args.mlp if args.mlp in ("fp8", "fp8x2") else True, base_tile=args.base_tile, leaf=True)
     ref = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=sn.F32)
     cams = scenes.orbit_cameras(W, H, args.frames + 1)
     bg = tuple(ref.params.bg)

@@ -46,9 +46,13 @@ class Renderer:
             self.params.base_tile = base_tile
         self.x_dtype = x_dtype
         # fused: upscale + features + MLP on tcgen05 + composite in one kernel
-        # (True or "bf16": bf16 operands; "fp8": e4m3 operands)
+        # (True or "bf16": bf16 operands; "fp8": e4m3 operands; "fp8x2":
+        # compensated e4m3 pairs)
+        if fused not in (False, None, True, "bf16", "fp8", "fp8x2"):
+            raise ValueError(f"fused: {fused!r}")
         self.fused = bool(fused)
-        self.fused_fp8 = fused == "fp8"
+        self.fused_fp8 = fused in ("fp8", "fp8x2")
+        self.mlp_kind = fused if self.fused_fp8 else "bf16"
         # persistent: the three geometry passes in one launch (tuning: (block_w, ctas_per_sm))
         self.persistent = bool(persistent)
         self.tuning = tuning
@@ -66,7 +70,7 @@ class Renderer:
         # instead of one scale per frame; runs the fused resolve
         self.leaf = bool(leaf)
         if self.leaf and not self.fused:
-            raise ValueError("the per-leaf frame runs the fused resolve (fused=True or 'fp8')")
+            raise ValueError("the per-leaf frame runs the fused resolve (fused=True, 'fp8' or 'fp8x2')")
         cap = pair_capacity if pair_capacity is not None else max(1 << 20, 96 * self.T)
         self.bins = [sn.BinsBuffer(self.W, self.H, self.T, cap, device) for _ in range(3)]
         P = self.P
@@ -196,7 +200,8 @@ class Renderer:
                                                          self.tuning, self.status, stream)),
               ("resolve", lambda: sn.resolve_leaf(self.scene, self.plan, self.leaf_layers, self.mask[0],
                                                   self.params, self.mlp,
-                                                  sn.E4M3 if self.fused_fp8 else sn.BF16, self.rgba32f,
+                                                  {"bf16": sn.BF16, "fp8": sn.E4M3,
+                                                   "fp8x2": sn.E4M3X2}[self.mlp_kind], self.rgba32f,
                                                   self.rgba8_out, self.status, stream))]
         if update_tiles:
             st.append(("quadtree", lambda: self.update_tiles(stream)))
@@ -237,7 +242,7 @@ class Renderer:
                    ("pass3", lambda: sn.geometry_pass(self.scene, b3, 3, self.l3, self.status,
                                                       stream))]
         if self.fused:
-            res = sn.resolve_fp8 if self.fused_fp8 else sn.resolve
+            res = {"bf16": sn.resolve, "fp8": sn.resolve_fp8, "fp8x2": sn.resolve_fp8x2}[self.mlp_kind]
             st.append(("resolve", lambda: res(self.scene, b2, b3, self.l1, self.l2, self.l3,
                                               self.W, self.H, self.params, self.mlp,
                                               self.rgba32f, self.rgba8_out, self.status, stream)))

@@ -24,7 +24,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--workload", default="hd", choices=["hd", "uhd"])
     ap.add_argument("--steps", type=int, default=8, help="real + interpolated frame pairs")
-    ap.add_argument("--mlp", default="bf16", choices=["bf16", "fp8"])
+    ap.add_argument("--mlp", default="bf16", choices=["bf16", "fp8", "fp8x2"])
     ap.add_argument("--merge-scale2", type=float, default=0.5)
     ap.add_argument("--merge-scale3", type=float, default=0.7)
     ap.add_argument("--block-w", type=int, default=8, choices=[4, 8, 16])
@@ -36,7 +36,7 @@ def main(argv=None):
     W, H = sc.width, sc.height
     w = dict(np.load(os.path.join(HERE, "weights", "tail_mlp.npz")))
     r = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=sn.BF16,
-                 fused="fp8" if args.mlp == "fp8" else True, persistent=True,
+                 fused=args.mlp if args.mlp in ("fp8", "fp8x2") else True, persistent=True,
                  tuning=(args.block_w, 0), merge_scale2=args.merge_scale2,
                  merge_scale3=args.merge_scale3, base_tile=args.base_tile,
                  leaf=args.leaf)

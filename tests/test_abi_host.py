@@ -166,3 +166,28 @@ def test_leaf_passes_workspace_checked(sn):
                                           need - 1, None, None, None) == sn.ERR_ARG
     assert L.star_nt_geometry_passes_leaf(ctypes.byref(sc), ctypes.byref(plan), bins, lays, 16, 272,
                                           need, None, None, None) == sn.ERR_ARG
+
+
+def test_resolve_entry_points_reject_bad_arguments(sn):
+    """The three resolve variants (bf16, e4m3, compensated e4m3) share their
+    argument checks; the per-leaf resolve takes only the listed MLP types."""
+    L = sn.lib()
+    sc = sn.Scene(16, 16, 5)
+    bins = sn.Bins(256, 1 << 20, 64, 64, 16, 1 << 10)
+    lay = sn.Layers(16, 16, 16, 16, 16, 16)
+    p = sn.default_params()
+    w = sn.Mlp(16, 16, 16, 16, 16, 16)
+    w0 = sn.Mlp(16, 16, 16, None, 16, 16)
+    for fn in (L.star_nt_resolve, L.star_nt_resolve_fp8, L.star_nt_resolve_fp8x2):
+        args = [ctypes.byref(sc), ctypes.byref(bins), ctypes.byref(bins), ctypes.byref(lay),
+                ctypes.byref(lay), ctypes.byref(lay), 64, 64, ctypes.byref(p)]
+        assert fn(*args, ctypes.byref(w), None, None, None, None) == sn.ERR_ARG       # no output
+        assert fn(*args, ctypes.byref(w0), 32, None, None, None) == sn.ERR_ARG        # missing b2
+        assert fn(*args, ctypes.byref(w), 24, None, None, None) == sn.ERR_ARG         # misaligned
+        args[6] = 0
+        assert fn(*args, ctypes.byref(w), 32, None, None, None) == sn.ERR_ARG         # empty frame
+    plan = sn.leaf_plan(64, 64, sn.default_params())
+    for t in (sn.F32, sn.E4M3X2 + 1):
+        assert L.star_nt_resolve_leaf(ctypes.byref(sc), ctypes.byref(plan), ctypes.byref(lay), 16,
+                                      ctypes.byref(p), ctypes.byref(w), t, 32, None, None,
+                                      None) == sn.ERR_ARG

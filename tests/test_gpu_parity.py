@@ -817,6 +817,45 @@ def test_fused_resolve_fp8(orc, sn, weights):
         assert e0.max() <= 1e-5
 
 
+# Compensated FP8: e4m3 hi + lo pairs for every operand, the four products
+# accumulated in fp32 on the tensor cores.  Each operand keeps about 2^-8
+# relative rounding (hi to 2^-4, lo to 2^-4 of the remainder), the size of a
+# bf16 operand's 2^-9 rounding of both operands, so the frame meets the same
+# 2/255 bar as the bf16 path.
+TOL_MLP = 2.0 / 255.0
+
+
+@pytest.mark.parametrize("weights", ["xavier", "trained"])
+def test_fused_resolve_fp8x2(orc, sn, weights):
+    from paper_2606_16747_b300.pipeline import Renderer
+    sc = scenes.screen_scene(29, 3000, 333, 197, size_scale=0.7)   # ragged: partial tiles
+    W, H = sc.width, sc.height
+    if weights == "xavier":
+        mlp = scenes.mlp_xavier(4)
+    else:
+        path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                            "paper_2606_16747_b300", "weights", "tail_mlp.npz")
+        mlp = dict(np.load(path))
+    o = orc.frame_star(sc.verts, sc.rgba8, sc.cam.vp32, W, H, (201, 119), (97, 57), scenes.mlp_flat(mlp),
+                       threads=4)
+    errs = {}
+    for kind in ("fp8x2", "fp8"):
+        r = Renderer(sc.verts, sc.rgba8, W, H, mlp=mlp, x_dtype=sn.BF16, fused=kind)
+        r.set_camera(sc.cam.vp32)
+        r.state.view(torch.int32)[:6] = torch.tensor([W, H, 201, 119, 97, 57], dtype=torch.int32)
+        r.star_frame(update_tiles=False)
+        torch.cuda.synchronize()
+        r.check_status()
+        errs[kind] = np.abs(r.rgba32f.cpu().numpy().reshape(-1, 4)[:, :3] - o["rgb"])
+    err = errs["fp8x2"]
+    assert err.max() <= TOL_MLP, err.max() * 255
+    no_tail = np.asarray(o["flag"]).ravel() == 0
+    if no_tail.any():
+        assert err[no_tail].max() <= 1e-5
+    # the compensation removes most of the plain e4m3 error
+    assert err.max() < 0.5 * errs["fp8"].max()
+
+
 # ---------------------------------------------------------------------------
 # Comparison renderers of the evaluation (Sec. 4)
 
