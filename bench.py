@@ -57,6 +57,60 @@ PASSES_DRAM_BYTES = 27639296
 FUSED_DRAM_BYTES = 12742144
 
 
+def stage_rooflines(star, torch, stage_state, stage_mean, hbm_gbs):
+    """Each stage's achieved fraction of the HBM roofline: the algorithmic bytes
+    of its launches at the sizes in force when the stage graphs ran, over the
+    stage's measured time.  Per unit:
+      raster   (bin count, tile scan, bin fill; per pass that is binned): 52 B of
+               vertices and colour + 112 B of set-up written and 112 B read back
+               per triangle, 8 B per (triangle, tile) pair (count, list entry),
+               16 B per tile (count, offset, cursor, cleared count);
+      passes   id1, z1 per full-resolution pixel (8 B), id2 (4 B) per pixel of
+               pass 2, n, tail, t_tail (24 B) per pixel of pass 3 (merged passes
+               at the full size), 20 B of frame per pixel when the launch also
+               resolves the frame; set-ups and pair lists read once;
+      resolve  id1 4 B + frame 20 B per pixel, id2 4 B per pixel of pass 2 and
+               24 B per pixel of pass 3 (the bilinear taps' planes read once);
+      quadtree id1 4 B per pixel, 256 corner samples of 4 B and the mask per
+               base tile;
+      reproject z1 4 B + previous frame 16 B + 8-bit frame 4 B per pixel, + 16 B
+               when the float copy of the interpolated frame is kept.
+    The passes are ALU-bound (the headline roofline), the resolve issue-bound;
+    their HBM fractions say how far from the memory bound they are."""
+    W, H, T = star.W, star.H, star.T
+    P = W * H
+    hdr = [star.bins[k].mem[:64].view(torch.int32).cpu().numpy() for k in range(3)]
+    binned = [h for h in hdr if int(h[8]) == 0 and int(h[4]) > 0]
+    pairs = sum(int(np.uint32(h[6])) for h in binned)
+    tiles = sum(int(h[4]) for h in binned)
+    P2 = P if int(hdr[1][8]) else stage_state["W2"] * stage_state["H2"]
+    P3 = P if int(hdr[2][8]) else stage_state["W3"] * stage_state["H3"]
+    resolved = bool(int(hdr[1][11]))
+    B = star.params.base_tile
+    qt_tiles = ((W + B - 1) // B) * ((H + B - 1) // B)
+    work = {
+        "raster": len(binned) * T * 276 + 8 * pairs + 16 * tiles,
+        "passes": 8 * P + 4 * P2 + 24 * P3 + (20 * P if resolved else 0) + len(binned) * T * 112
+                  + 4 * pairs,
+        "resolve": None if resolved else 24 * P + 4 * P2 + 24 * P3,
+        "quadtree": 4 * P + qt_tiles * (1024 + 8),
+        "reproject": P * (24 + (16 if star.interp_float else 0)),
+    }
+    out = {}
+    for name, b in work.items():
+        ms = stage_mean.get(name)
+        if ms is None:
+            continue
+        if b is None:
+            out[name] = {"bytes": None, "ms": round(ms, 5),
+                         "note": "the pass launch produced the frame; this launch returns at once"}
+            continue
+        gbs = b / (ms * 1e-3) / 1e9
+        out[name] = {"bytes": int(b), "ms": round(ms, 5), "achieved_gbs": round(gbs, 1),
+                     "frac": round(gbs / hbm_gbs, 4)}
+    return out
+
+
 def load_peaks():
     try:
         with open(MEASURED_PEAKS) as f:
@@ -204,10 +258,15 @@ def run_ours(args, rank, world):
     sampler = ClockSampler(torch.cuda.current_device()).start()
     wall0 = time.perf_counter()
     events = []
-    for _ in range(args.steps):
+    # per timed step, whether the pass launch produced the frame (bins2 header
+    # word 11), copied on the device after the step's end event
+    resolved_log = torch.zeros(args.steps, dtype=torch.int32, device=dev)
+    for k in range(args.steps):
         events.append(timed(g_step.replay, step))
+        resolved_log[k:k + 1].copy_(star.bins[1].mem[44:48].view(torch.int32))
         step += 1
     torch.cuda.synchronize()
+    resolved_steps = resolved_log.cpu().numpy().astype(bool)
     wall = time.perf_counter() - wall0
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in events]
@@ -429,6 +488,7 @@ def run_ours(args, rank, world):
         "wall_s": round(wall, 3),
         "graph": "one CUDA graph per step (real + interpolated frame), replayed",
         "gpu_launches": kernels_per_step(star) * args.steps,
+        "frames_resolved_by_pass_launch": int(resolved_steps.sum()),
         "clocks": clocks,
         "e2e": e2e,
         "roofline": {"bound": "alu", "kernel": dom_name, "fragments": int(dom_frags),
@@ -443,6 +503,10 @@ def run_ours(args, rank, world):
                      "peak_source": f"{N_SM} SM x {ALU_LANES_PER_SM} lanes x sm_max_mhz ({peaks_kind})",
                      "ops_per_fragment": OPS_PER_FRAGMENT, "launch_ms": round(dom_ms, 5)},
     }
+    line["stage_roofline"] = {"bound": "hbm", "peak": peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]),
+                              "unit": "GB/s", "peak_source": f"hbm_gbs ({peaks_kind})",
+                              "stages": stage_rooflines(star, torch, stage_state, stage_mean,
+                                                        peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]))}
     line["per_leaf"] = leaf_info
     line["psnr_db_vs_exact_abuffer"] = psnr["psnr_db"]
     line["quality"] = {"mse_vs_exact_abuffer": psnr["mse"],
