@@ -229,7 +229,7 @@ def run_ours(args, rank, world):
     if args.persistent and not args.no_tune:
         from paper_2606_16747_b300 import autotune
         tuned = autotune.tune(star)
-        star.tuning = (tuned["block_w"], tuned["ctas_per_sm"])
+        star.tuning = (tuned["block_w"], tuned["ctas_per_sm"], tuned["pixels_per_thread"])
         if "fuse_passes" in tuned and args.fuse_passes:
             star.fuse_passes = tuned["fuse_passes"]
     stages = star.star_stages() + [("reproject", star.interp_frame)]
@@ -336,7 +336,8 @@ def run_ours(args, rank, world):
         if not args.no_tune:
             from paper_2606_16747_b300 import autotune
             leaf_tuned = autotune.tune(leaf)
-            leaf.tuning = (leaf_tuned["block_w"], leaf_tuned["ctas_per_sm"])
+            leaf.tuning = (leaf_tuned["block_w"], leaf_tuned["ctas_per_sm"],
+                           leaf_tuned["pixels_per_thread"])
         g_leaf = leaf.capture(leaf.step)
         lstep = 4
         for _ in range(args.warmup):

@@ -239,15 +239,27 @@ star_nt_status star_nt_geometry_pass_merged(const star_nt_scene *scene, const st
                                             const star_nt_layers *layers2,
                                             const star_nt_layers *layers3, int32_t *d_status,
                                             void *stream);
-/* Tile shape and launch size of star_nt_geometry_passes (NULL: defaults).
- * block_w: width of the pixel block a warp owns inside a 16 x 16 tile
- *   (4, 8 or 16; the block is block_w x 32/block_w); default 8.
- * ctas_per_sm: 0 or 8: full occupancy with an 8-CTA-per-SM register budget
- *   (32 per thread); 1..7: a 6-CTA budget (40 per thread) and the grid capped
- *   at that many CTAs per SM.  Default 0. */
+/* Tile shape and launch size of the persistent geometry-pass launches
+ * (star_nt_geometry_passes, star_nt_geometry_passes_resolve and
+ * star_nt_geometry_passes_leaf; NULL: the defaults).
+ * block_w: width of the pixel block a warp owns inside a 16 x 16 tile (4, 8
+ *   or 16); default 8.
+ * pixels_per_thread: 1: CTAs of 256 threads, one pixel each, the warp's block
+ *   block_w x 32/block_w; 2: CTAs of 128 threads, two pixels each (rows r and
+ *   r + 32/block_w of a block_w x 64/block_w block), which share the
+ *   triangle loads and the loop; 0: 2.
+ * ctas_per_sm: one pixel per thread: 0 or 8: full occupancy with an 8-CTA
+ *   register budget (32 per thread); 1..7: a 6-CTA budget (40 per thread)
+ *   and the grid capped at that many CTAs per SM.  Two pixels per thread:
+ *   0: 10 CTAs per SM (48 registers); 1..10: the grid capped at that many.
+ *   The launch that also resolves the frame runs at most 6 (one pixel) or 8
+ *   (two pixels: 8 x 64 columns, all of tensor memory) CTAs per SM.
+ *   Default 0.
+ * Results do not depend on the tuning. */
 typedef struct {
     int32_t block_w;
     int32_t ctas_per_sm;
+    int32_t pixels_per_thread;
 } star_nt_tuning;
 
 /* star_nt_geometry_passes: the three geometry passes of a real frame in one

@@ -1,6 +1,7 @@
 """Autotuner of the persistent geometry-pass launch: tries tile shapes (the
-pixel block a warp owns inside a 16 x 16 tile) and resident CTAs per SM on
-the renderer's own workload, and keeps the fastest; then, with that shape,
+pixel block a warp owns inside a 16 x 16 tile), one or two pixels per thread
+and resident CTAs per SM on the renderer's own workload, and keeps the
+fastest; then, with that shape,
 whether the pass launch should also produce the frame when every pass runs at
 full size (the network inside the pass launch against the separate resolve).
 Results are stored per workload key in a JSON file next to this module."""
@@ -12,7 +13,13 @@ import os
 import torch
 
 TUNED_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
-CANDIDATES = [(8, 0), (16, 0), (4, 0), (8, 6), (16, 6), (4, 6)]
+# (block_w, ctas_per_sm, pixels_per_thread) of star_nt_tuning
+CANDIDATES = [(8, 0, 2), (4, 0, 2), (16, 0, 2), (8, 0, 1), (4, 0, 1), (8, 6, 1), (4, 6, 1)]
+
+
+def candidate_key(c) -> str:
+    bw, k, pix = c
+    return f"{bw}x{32 // bw}/{k}/{pix}px"
 
 
 def workload_key(renderer) -> str:
@@ -55,9 +62,9 @@ def tune(renderer, candidates=CANDIDATES, reps=10) -> dict:
     pass sizes must be those of a real frame) and return the fastest, with the
     fused-resolve choice when the renderer can make it (a tie, for instance
     when a reduced pass is not merged in the current frame, keeps it on)."""
-    times = {f"{bw}x{32 // bw}/{k}": time_passes(renderer, (bw, k), reps) for bw, k in candidates}
-    best = min(candidates, key=lambda c: times[f"{c[0]}x{32 // c[0]}/{c[1]}"])
-    out = {"block_w": best[0], "ctas_per_sm": best[1], "ms": times}
+    times = {candidate_key(c): time_passes(renderer, tuple(c), reps) for c in candidates}
+    best = tuple(min(candidates, key=lambda c: times[candidate_key(c)]))
+    out = {"block_w": best[0], "ctas_per_sm": best[1], "pixels_per_thread": best[2], "ms": times}
     if getattr(renderer, "leaf", False) or not (renderer.fused and not renderer.fused_fp8):
         return out
     old = renderer.tuning, renderer.persistent, renderer.fuse_passes
@@ -80,7 +87,7 @@ def load(key: str):
     try:
         with open(TUNED_PATH) as f:
             d = json.load(f).get(key)
-        return (d["block_w"], d["ctas_per_sm"]) if d else None
+        return (d["block_w"], d["ctas_per_sm"], d.get("pixels_per_thread", 1)) if d else None
     except (OSError, ValueError, KeyError):
         return None
 

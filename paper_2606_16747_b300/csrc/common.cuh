@@ -109,6 +109,19 @@ inline BinsView bins_view(const star_nt_bins &b) {
 // target lies between a quarter of it and all of it on both axes (so a
 // 16-sample target tile maps to at most 64 + 5 full-resolution pixels per
 // axis), and every (pass, level) maps to a listed target.
+// Host: a persistent pass launch's tuning (NULL: the defaults), decoded.
+struct PassTuning {
+  int bw, per_sm, pix;
+};
+inline bool pass_tuning(const star_nt_tuning *t, PassTuning &o) {
+  o.bw = t ? t->block_w : 8;
+  o.per_sm = t ? t->ctas_per_sm : 0;
+  o.pix = t && t->pixels_per_thread ? t->pixels_per_thread : 2;
+  if (o.bw != 4 && o.bw != 8 && o.bw != 16) return false;
+  if (o.pix != 1 && o.pix != 2) return false;
+  return o.per_sm >= 0 && o.per_sm <= (o.pix == 2 ? 10 : 8);
+}
+
 inline bool leaf_plan_valid(const star_nt_leaf_plan *p) {
   if (!p || p->W <= 0 || p->H <= 0 || (p->base_tile != 16 && p->base_tile != 64)) return false;
   if (p->n_targets < 1 || p->n_targets > STAR_NT_LEAF_MAX_TARGETS) return false;

@@ -132,8 +132,8 @@ struct LeafPassArgs {
 // the full resolution first).  Target 0 always runs pass 1 and adds the two
 // nearest / the tail sums where its mode asks; the other targets run only
 // where some pixel needs them.
-template <int BW, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_passes_leaf(LeafPassArgs a,
+template <int BW, int MINB, int PIX = 1>
+__global__ void __launch_bounds__(PIX == 2 ? 128 : 256, MINB) k_passes_leaf(LeafPassArgs a,
                                                         const uint8_t *__restrict__ modes,
                                                         const uint32_t *__restrict__ rgba8,
                                                         uint32_t *queue, int32_t *status) {
@@ -163,9 +163,15 @@ __global__ void __launch_bounds__(256, MINB) k_passes_leaf(LeafPassArgs a,
       continue;  // binned at another size than the plan's: skipped
     }
     const uint32_t m = __ldg(modes + item);
-    if (m & 2u) pass_body<kTail, BW>(bv, rgba8, a.out[k], FeatOut{}, stage, tile);
-    else if (m & 1u) pass_body<kTop2, BW>(bv, rgba8, a.out[k], FeatOut{}, stage, tile);
-    else if (k == 0) pass_body<kTop1, BW>(bv, rgba8, a.out[0], FeatOut{}, stage, tile);
+    if (PIX == 2) {
+      if (m & 2u) pass_body2<kTail, BW>(bv, rgba8, a.out[k], stage, tile);
+      else if (m & 1u) pass_body2<kTop2, BW>(bv, rgba8, a.out[k], stage, tile);
+      else if (k == 0) pass_body2<kTop1, BW>(bv, rgba8, a.out[0], stage, tile);
+    } else {
+      if (m & 2u) pass_body<kTail, BW>(bv, rgba8, a.out[k], FeatOut{}, stage, tile);
+      else if (m & 1u) pass_body<kTop2, BW>(bv, rgba8, a.out[k], FeatOut{}, stage, tile);
+      else if (k == 0) pass_body<kTop1, BW>(bv, rgba8, a.out[0], FeatOut{}, stage, tile);
+    }
   }
 }
 
@@ -234,10 +240,9 @@ extern "C" star_nt_status star_nt_geometry_passes_leaf(const star_nt_scene *scen
   if (scene->n_tris < 0 || (scene->n_tris > 0 && !scene->rgba8)) return STAR_NT_ERR_ARG;
   size_t need = 0;
   if (star_nt_leaf_ws_bytes(plan, &need) != STAR_NT_OK || ws_bytes < need) return STAR_NT_ERR_ARG;
-  const int bw = tuning ? tuning->block_w : 8;
-  const int per_sm = tuning ? tuning->ctas_per_sm : 0;
-  if (bw != 4 && bw != 8 && bw != 16) return STAR_NT_ERR_ARG;
-  if (per_sm < 0 || per_sm > 8) return STAR_NT_ERR_ARG;
+  PassTuning tu;
+  if (!pass_tuning(tuning, tu)) return STAR_NT_ERR_ARG;
+  const int bw = tu.bw, per_sm = tu.per_sm;
   const int n = plan->n_targets;
   LeafModeArgs ma = {};
   LeafPassArgs pa = {};
@@ -283,12 +288,18 @@ extern "C" star_nt_status star_nt_geometry_passes_leaf(const star_nt_scene *scen
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  auto launch = [&](auto kern) {
+  auto launch = [&](auto kern, int threads = 256) {
     int occ = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, 0);
     const int c = per_sm > 0 ? (per_sm < occ ? per_sm : occ) : occ;
-    kern<<<sms * (c > 0 ? c : 1), 256, 0, st>>>(pa, modes, scene->rgba8, queue, d_status);
+    kern<<<sms * (c > 0 ? c : 1), threads, 0, st>>>(pa, modes, scene->rgba8, queue, d_status);
   };
+  if (tu.pix == 2) {  // two pixels per thread, as star_nt_geometry_passes
+    if (bw == 8) launch(k_passes_leaf<8, 10, 2>, 128);
+    else if (bw == 16) launch(k_passes_leaf<16, 10, 2>, 128);
+    else launch(k_passes_leaf<4, 10, 2>, 128);
+    return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
+  }
   const bool wide = per_sm == 0 || per_sm == 8;  // register budget as star_nt_geometry_passes
   if (bw == 8) wide ? launch(k_passes_leaf<8, 8>) : launch(k_passes_leaf<8, 6>);
   else if (bw == 16) wide ? launch(k_passes_leaf<16, 8>) : launch(k_passes_leaf<16, 6>);
@@ -308,6 +319,9 @@ cudaError_t preload_leaf() {
   if ((r = cudaFuncGetAttributes(&a, k_passes_leaf<4, 8>)) != cudaSuccess) e = r;
   if ((r = cudaFuncGetAttributes(&a, k_passes_leaf<8, 8>)) != cudaSuccess) e = r;
   if ((r = cudaFuncGetAttributes(&a, k_passes_leaf<16, 8>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_passes_leaf<4, 10, 2>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_passes_leaf<8, 10, 2>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_passes_leaf<16, 10, 2>)) != cudaSuccess) e = r;
   return e;
 }
 }  // namespace star

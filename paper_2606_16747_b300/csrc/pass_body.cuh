@@ -165,4 +165,30 @@ __device__ __forceinline__ void pass_body(const BinsView &bv, const uint32_t *__
   acc.template finish<MODE>(bv.setups, rgba8, po, fo, (size_t)tp.py * W + tp.px);
 }
 
+// pass_body with two pixels per thread (a CTA of 128 threads per tile; see
+// tile_pixel): the triangle loads and the loop are shared by both pixels.
+template <int MODE, int BW = 8>
+__device__ __forceinline__ void pass_body2(const BinsView &bv, const uint32_t *__restrict__ rgba8,
+                                           const PassOut &po, TileStage &stage, int tile) {
+  constexpr int BH = 32 / BW;
+  const BinsHeader *hd = bv.hd;
+  if ((int64_t)hd->n_pairs > bv.pair_capacity) return;
+  if (tile >= hd->n_tiles) return;
+  const int W = hd->size[0], H = hd->size[1];
+  const TilePixel tp = tile_pixel<BW, 2>(tile, hd->tiles_x);
+  const bool in0 = tp.px < W && tp.py < H, in1 = tp.px < W && tp.py + BH < H;
+  PassAcc a0, a1;
+  a0.reset();
+  a1.reset();
+  for_each_fragment<BW, true, 2>(
+      bv, tile, tp, stage,
+      [&] { return fmaxf(a0.template bound<MODE>(in0), a1.template bound<MODE>(in1)); },
+      [&](int j, const TriSetup &T, uint32_t id, long long e0, long long e2) {
+        if (j == 0) a0.template visit<MODE>(T, (int)id, e0, e2);
+        else a1.template visit<MODE>(T, (int)id, e0, e2);
+      });
+  if (in0) a0.template finish<MODE>(bv.setups, rgba8, po, FeatOut{}, (size_t)tp.py * W + tp.px);
+  if (in1) a1.template finish<MODE>(bv.setups, rgba8, po, FeatOut{}, (size_t)(tp.py + BH) * W + tp.px);
+}
+
 }  // namespace star

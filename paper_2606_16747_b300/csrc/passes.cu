@@ -95,6 +95,52 @@ __global__ void __launch_bounds__(256, MINB) k_passes(BinsView v1, BinsView v2, 
   }
 }
 
+// k_passes with two pixels per thread (pass_body2): CTAs of 128 threads, one
+// tile each; MINB 10 gives a 48-register budget.
+template <int BW, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_passes2(BinsView v1, BinsView v2, BinsView v3,
+                                                    const uint32_t *__restrict__ rgba8, PassOut o1,
+                                                    PassOut o2, PassOut o3, uint32_t *queue) {
+  __shared__ TileStage stage;
+  __shared__ int s_item;
+  if (v2.hd->resolved) return;  // star_nt_geometry_passes_resolve's launch did the passes
+  const bool m2 = v2.hd->merged != 0, m3 = v3.hd->merged != 0;
+  const int n1 = v1.hd->n_tiles, n2 = v2.hd->n_tiles, n3 = v3.hd->n_tiles;
+  const int total = n1 + n2 + n3;
+  PassOut om = o1;
+  om.id2 = m2 ? o2.id2 : nullptr;
+  om.n = m3 ? o3.n : nullptr;
+  om.tail = m3 ? o3.tail : nullptr;
+  om.t_tail = m3 ? o3.t_tail : nullptr;
+  o2.id1 = nullptr;
+  o2.z1 = nullptr;
+  o3.id1 = nullptr;
+  o3.z1 = nullptr;
+  o3.id2 = nullptr;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(queue, 1u);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= total) {
+      if (threadIdx.x == 0 && atomicAdd(queue + 1, 1u) == gridDim.x - 1) {
+        queue[0] = 0u;
+        queue[1] = 0u;
+      }
+      break;
+    }
+    if (item < n1) {
+      if (m3) pass_body2<kTail, BW>(v1, rgba8, om, stage, item);
+      else if (m2) pass_body2<kTop2, BW>(v1, rgba8, om, stage, item);
+      else pass_body2<kTop1, BW>(v1, rgba8, o1, stage, item);
+    } else if (item < n1 + n2) {
+      pass_body2<kTop2, BW>(v2, rgba8, o2, stage, item - n1);
+    } else {
+      pass_body2<kTail, BW>(v3, rgba8, o3, stage, item - n1 - n2);
+    }
+  }
+}
+
 // Full-resolution features from pass 1 (full res) and the bilinear upscale
 // of passes 2 and 3 (their own resolutions, read from their bins headers).
 __global__ void __launch_bounds__(256) k_features(FeatIn in, FeatOut fo) {
@@ -218,10 +264,9 @@ extern "C" star_nt_status star_nt_geometry_passes(const star_nt_scene *scene,
   if (!layers_ok(l1) || !layers_ok(l2) || !layers_ok(l3)) return STAR_NT_ERR_ARG;
   if (scene->n_tris > 0 && !scene->rgba8) return STAR_NT_ERR_ARG;
   if (b1->mem == b2->mem || b1->mem == b3->mem || b2->mem == b3->mem) return STAR_NT_ERR_ARG;
-  const int bw = tuning ? tuning->block_w : 8;
-  int per_sm = tuning ? tuning->ctas_per_sm : 0;
-  if (bw != 4 && bw != 8 && bw != 16) return STAR_NT_ERR_ARG;
-  if (per_sm < 0 || per_sm > 8) return STAR_NT_ERR_ARG;
+  PassTuning tu;
+  if (!pass_tuning(tuning, tu)) return STAR_NT_ERR_ARG;
+  const int bw = tu.bw, per_sm = tu.per_sm;
   cudaStream_t st = (cudaStream_t)stream;
   BinsView v1 = bins_view(*b1), v2 = bins_view(*b2), v3 = bins_view(*b3);
   PassOut o1 = pass_out(l1), o2 = pass_out(l2), o3 = pass_out(l3);
@@ -230,12 +275,18 @@ extern "C" star_nt_status star_nt_geometry_passes(const star_nt_scene *scene,
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  auto launch = [&](auto kern) {
+  auto launch = [&](auto kern, int threads = 256) {
     int occ = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, 0);
     const int k = per_sm > 0 ? (per_sm < occ ? per_sm : occ) : occ;
-    kern<<<sms * (k > 0 ? k : 1), 256, 0, st>>>(v1, v2, v3, scene->rgba8, o1, o2, o3, queue);
+    kern<<<sms * (k > 0 ? k : 1), threads, 0, st>>>(v1, v2, v3, scene->rgba8, o1, o2, o3, queue);
   };
+  if (tu.pix == 2) {  // two pixels per thread, the 10-CTA budget
+    if (bw == 8) launch(k_passes2<8, 10>, 128);
+    else if (bw == 16) launch(k_passes2<16, 10>, 128);
+    else launch(k_passes2<4, 10>, 128);
+    return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
+  }
   // ctas_per_sm 0 or 8: the 8-CTA register budget at full occupancy; 1..7: the
   // 6-CTA budget, grid capped at that many CTAs per SM
   const bool wide = per_sm == 0 || per_sm == 8;
@@ -315,6 +366,9 @@ cudaError_t preload_passes() {
   if ((r = cudaFuncGetAttributes(&a, k_passes<4, 8>)) != cudaSuccess) e = r;
   if ((r = cudaFuncGetAttributes(&a, k_passes<8, 8>)) != cudaSuccess) e = r;
   if ((r = cudaFuncGetAttributes(&a, k_passes<16, 8>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_passes2<4, 10>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_passes2<8, 10>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_passes2<16, 10>)) != cudaSuccess) e = r;
   if ((r = cudaFuncGetAttributes(&a, k_features)) != cudaSuccess) e = r;
   return e;
 }

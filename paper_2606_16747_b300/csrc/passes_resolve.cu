@@ -181,16 +181,159 @@ __device__ __forceinline__ void pass_resolve_body(const BinsView &bv, const uint
   __syncthreads();  // tensor memory and the operand tiles are free for the next tile
 }
 
+// pass_resolve_body with two pixels per thread (a CTA of 128 threads per
+// tile, see tile_pixel): thread t owns row t of both MLP tiles, its first
+// pixel in tile 0 and its second in tile 1; warp w reads tensor-memory lanes
+// 32 w .. 32 w + 31 of both.
+template <int BW>
+__device__ __forceinline__ void pass_resolve_body2(const BinsView &bv, const uint32_t *__restrict__ rgba8,
+                                                   const PassOut &po, const ResolveArgs &ra,
+                                                   FusedSmem &fs, uint32_t tmem, uint32_t &ph,
+                                                   int tile) {
+  constexpr int BH = 32 / BW;
+  const BinsHeader *hd = bv.hd;
+  if ((int64_t)hd->n_pairs > bv.pair_capacity) return;
+  if (tile >= hd->n_tiles) return;
+  const int W = hd->size[0], H = hd->size[1];
+  const TilePixel tp = tile_pixel<BW, 2>(tile, hd->tiles_x);
+  const bool in0 = tp.px < W && tp.py < H, in1 = tp.px < W && tp.py + BH < H;
+  PassAcc a0, a1;
+  a0.reset();
+  a1.reset();
+  for_each_fragment<BW, true, 2>(
+      bv, tile, tp, fs.u.stage, [&] { return INFINITY; },  // tail sums: every fragment
+      [&](int j, const TriSetup &T, uint32_t id, long long e0, long long e2) {
+        if (j == 0) a0.template visit<kTail>(T, (int)id, e0, e2);
+        else a1.template visit<kTail>(T, (int)id, e0, e2);
+      });
+  float xv0[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, xv1[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  float4 front0 = make_float4(0.f, 0.f, 0.f, 0.f), front1 = front0;
+  const size_t p0 = (size_t)tp.py * W + tp.px, p1 = p0 + (size_t)BH * W;
+  if (in0) a0.resolve_terms(bv.setups, rgba8, po, ra.bg0, ra.bg1, ra.bg2, ra.kappa, p0, xv0, front0);
+  if (in1) a1.resolve_terms(bv.setups, rgba8, po, ra.bg0, ra.bg1, ra.bg2, ra.kappa, p1, xv1, front1);
+  const bool flag0 = xv0[5] != 0.0f, flag1 = xv1[5] != 0.0f;
+  const int tid = threadIdx.x, warp = tid >> 5, row = tid;
+  __syncthreads();  // every warp is done with the staging area
+  *reinterpret_cast<uint4 *>(fs.u.h[0] + row * 16) =
+      make_uint4(pack_bf16(xv0[0], xv0[1]), pack_bf16(xv0[2], xv0[3]), pack_bf16(xv0[4], xv0[5]), 0u);
+  *reinterpret_cast<uint4 *>(fs.u.h[1] + row * 16) =
+      make_uint4(pack_bf16(xv1[0], xv1[1]), pack_bf16(xv1[2], xv1[3]), pack_bf16(xv1[4], xv1[5]), 0u);
+  const uint32_t bar = smem_u32(&fs.bar);
+  const uint32_t lane_tmem = tmem + ((uint32_t)(warp * 32) << 16);
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  // ---- layer 1: [X | ones] (K = 16) against [W1 | b1], N = 32
+  if (tid == 0) {
+    fence_after();
+    const uint64_t dW1 = smem_desc(smem_u32(fs.w1), 512, 128);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const uint32_t a = smem_u32(fs.u.h[k]);
+      mma_bf16(tmem + 32 * k, smem_desc(a, smem_u32(fs.ones) - a, 128), dW1, idesc_bf16(32), 0u);
+    }
+    mma_commit(bar);
+  }
+  mma_wait_cta(bar, ph, &fs.abort);
+  ph ^= 1u;
+#pragma unroll
+  for (int t = 0; t < 2; ++t)
+#pragma unroll
+    for (int kc = 0; kc < 4; ++kc) {
+      float d[8];
+      tmem_ld8(lane_tmem + 32 * t + 8 * kc, d);
+      *reinterpret_cast<uint4 *>(fs.u.h[t] + kc * 2048 + row * 16) =
+          make_uint4(pack_relu_bf16(d[0], d[1]), pack_relu_bf16(d[2], d[3]), pack_relu_bf16(d[4], d[5]),
+                     pack_relu_bf16(d[6], d[7]));
+    }
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  // ---- layer 2: [H1 | ones | 0] (K = 48) against [W2 | b2], N = 16, over D1
+  if (tid == 0 && !fs.abort) {
+    fence_after();
+    const uint32_t w2 = smem_u32(fs.w2);
+    const uint64_t dOnes = smem_desc(smem_u32(fs.ones), 2048, 128);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const uint32_t a = smem_u32(fs.u.h[k]);
+      mma_bf16(tmem + 32 * k, smem_desc(a, 2048, 128), smem_desc(w2, 256, 128), idesc_bf16(16), 0u);
+      mma_bf16(tmem + 32 * k, smem_desc(a + 4096, 2048, 128), smem_desc(w2 + 512, 256, 128),
+               idesc_bf16(16), 1u);
+      mma_bf16(tmem + 32 * k, dOnes, smem_desc(w2 + 1024, 256, 128), idesc_bf16(16), 1u);
+    }
+    mma_commit(bar);
+  }
+  if (!fs.abort) mma_wait_cta(bar, ph, &fs.abort);  // fs.abort is uniform after a barrier
+  ph ^= 1u;
+#pragma unroll
+  for (int t = 0; t < 2; ++t)
+#pragma unroll
+    for (int kc = 0; kc < 2; ++kc) {
+      float d[8];
+      tmem_ld8(lane_tmem + 32 * t + 8 * kc, d);
+      *reinterpret_cast<uint4 *>(fs.u.h[t] + kc * 2048 + row * 16) =
+          make_uint4(pack_relu_bf16(d[0], d[1]), pack_relu_bf16(d[2], d[3]), pack_relu_bf16(d[4], d[5]),
+                     pack_relu_bf16(d[6], d[7]));
+    }
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  // ---- layer 3: [H2 | ones | 0] (K = 32) against [W3 | b3], D3 in columns 16..31
+  if (tid == 0 && !fs.abort) {
+    fence_after();
+    const uint32_t w3 = smem_u32(fs.w3);
+    const uint64_t dOnes = smem_desc(smem_u32(fs.ones), 2048, 128);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      mma_bf16(tmem + 32 * k + 16, smem_desc(smem_u32(fs.u.h[k]), 2048, 128), smem_desc(w3, 256, 128),
+               idesc_bf16(16), 0u);
+      mma_bf16(tmem + 32 * k + 16, dOnes, smem_desc(w3 + 512, 256, 128), idesc_bf16(16), 1u);
+    }
+    mma_commit(bar);
+  }
+  if (!fs.abort) mma_wait_cta(bar, ph, &fs.abort);  // fs.abort is uniform after a barrier
+  ph ^= 1u;
+  // ---- composite, Eq. 4
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(lane_tmem + 32 * t + 16));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const bool in = t ? in1 : in0, flag = t ? flag1 : flag0;
+    const float4 front = t ? front1 : front0;
+    const size_t p = t ? p1 : p0;
+    if (in) {
+      float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+      if (flag) {
+        f0 = fmaxf(__uint_as_float(r[0]), 0.0f);
+        f1 = fmaxf(__uint_as_float(r[1]), 0.0f);
+        f2 = fmaxf(__uint_as_float(r[2]), 0.0f);
+      }
+      const float cr = fmaf(front.w, f0, front.x), cg = fmaf(front.w, f1, front.y),
+                  cb = fmaf(front.w, f2, front.z);
+      if (ra.out) ra.out[p] = make_float4(cr, cg, cb, 1.0f);
+      if (ra.out8) ra.out8[p] = quantize_rgba8(cr, cg, cb);
+    }
+  }
+  fence_before();
+  __syncthreads();  // tensor memory and the operand tiles are free for the next tile
+}
+
 // The fused launch: with both reduced passes merged, every pass-1 tile runs
 // pass_resolve_body (items from a work counter, as k_passes); otherwise every
 // CTA returns at once and star_nt_geometry_passes' launch that follows does
 // the passes.  Tensor memory is allocated by every CTA at the start (and
 // released on either exit); the constant operands are staged once per CTA.
-template <int BW>
-__global__ void __launch_bounds__(256, 6) k_passes_resolve(BinsView v1, BinsView v2, BinsView v3,
-                                                        const uint32_t *__restrict__ rgba8,
-                                                        PassOut o1, ResolveArgs ra, uint32_t *queue,
-                                                        int32_t *status) {
+// PIX = 1: 256 threads, 6 CTAs per SM (the 40-register budget); PIX = 2:
+// 128 threads with two pixels each, 8 CTAs per SM (8 x 64 columns: all of
+// tensor memory).
+template <int BW, int PIX = 1>
+__global__ void __launch_bounds__(PIX == 2 ? 128 : 256, PIX == 2 ? 8 : 6)
+    k_passes_resolve(BinsView v1, BinsView v2, BinsView v3, const uint32_t *__restrict__ rgba8,
+                     PassOut o1, ResolveArgs ra, uint32_t *queue, int32_t *status) {
   extern __shared__ uint8_t smem_raw[];  // FusedSmem, 128-byte aligned
   FusedSmem &fs = *reinterpret_cast<FusedSmem *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) &
                                                  ~(uintptr_t)127);
@@ -250,7 +393,8 @@ __global__ void __launch_bounds__(256, 6) k_passes_resolve(BinsView v1, BinsView
         }
         break;
       }
-      pass_resolve_body<BW>(v1, rgba8, om, ra, fs, tmem, ph, item);
+      if (PIX == 2) pass_resolve_body2<BW>(v1, rgba8, om, ra, fs, tmem, ph, item);
+      else pass_resolve_body<BW>(v1, rgba8, om, ra, fs, tmem, ph, item);
     }
     if (fs.abort && tid == 0) raise_status(status, STAR_NT_ERR_TIMEOUT);
   }
@@ -296,10 +440,9 @@ extern "C" star_nt_status star_nt_geometry_passes_resolve(
   if (!aligned16(rgba32f)) return STAR_NT_ERR_ARG;
   if (scene->n_tris > 0 && !scene->rgba8) return STAR_NT_ERR_ARG;
   if (b1->mem == b2->mem || b1->mem == b3->mem || b2->mem == b3->mem) return STAR_NT_ERR_ARG;
-  const int bw = tuning ? tuning->block_w : 8;
-  const int per_sm = tuning ? tuning->ctas_per_sm : 0;
-  if (bw != 4 && bw != 8 && bw != 16) return STAR_NT_ERR_ARG;
-  if (per_sm < 0 || per_sm > 8) return STAR_NT_ERR_ARG;
+  PassTuning tu;
+  if (!pass_tuning(tuning, tu)) return STAR_NT_ERR_ARG;
+  const int bw = tu.bw, per_sm = tu.per_sm;
   cudaStream_t st = (cudaStream_t)stream;
   BinsView v1 = bins_view(*b1), v2 = bins_view(*b2), v3 = bins_view(*b3);
   PassOut o1 = pass_out_of(l1);
@@ -309,15 +452,24 @@ extern "C" star_nt_status star_nt_geometry_passes_resolve(
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // 6 CTAs per SM (the 40-register budget; 6 x 64 tensor-memory columns of the
-  // SM's 512), or fewer when tuned
-  const int c = per_sm > 0 && per_sm < 6 ? per_sm : 6;
+  // one pixel per thread: 6 CTAs of 256 threads per SM (the 40-register
+  // budget; 6 x 64 tensor-memory columns of the SM's 512); two pixels per
+  // thread: 8 CTAs of 128 threads (8 x 64 columns); fewer when tuned
+  const int cmax = tu.pix == 2 ? 8 : 6;
+  const int c = per_sm > 0 && per_sm < cmax ? per_sm : cmax;
+  const int threads = tu.pix == 2 ? 128 : 256;
   auto launch = [&](auto kern) {
-    kern<<<sms * c, 256, kFusedSmemBytes, st>>>(v1, v2, v3, scene->rgba8, o1, ra, queue, d_status);
+    kern<<<sms * c, threads, kFusedSmemBytes, st>>>(v1, v2, v3, scene->rgba8, o1, ra, queue, d_status);
   };
-  if (bw == 8) launch(k_passes_resolve<8>);
-  else if (bw == 16) launch(k_passes_resolve<16>);
-  else launch(k_passes_resolve<4>);
+  if (tu.pix == 2) {
+    if (bw == 8) launch(k_passes_resolve<8, 2>);
+    else if (bw == 16) launch(k_passes_resolve<16, 2>);
+    else launch(k_passes_resolve<4, 2>);
+  } else {
+    if (bw == 8) launch(k_passes_resolve<8>);
+    else if (bw == 16) launch(k_passes_resolve<16>);
+    else launch(k_passes_resolve<4>);
+  }
   if (cudaGetLastError() != cudaSuccess) return STAR_NT_ERR_CUDA;
   // the passes themselves when a reduced pass is not merged (returns at once
   // when the launch above resolved the frame)
@@ -332,6 +484,9 @@ cudaError_t preload_passes_resolve() {
   if ((r = cudaFuncGetAttributes(&a, k_passes_resolve<4>)) != cudaSuccess) e = r;
   if ((r = cudaFuncGetAttributes(&a, k_passes_resolve<8>)) != cudaSuccess) e = r;
   if ((r = cudaFuncGetAttributes(&a, k_passes_resolve<16>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_passes_resolve<4, 2>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_passes_resolve<8, 2>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_passes_resolve<16, 2>)) != cudaSuccess) e = r;
   return e;
 }
 }  // namespace star

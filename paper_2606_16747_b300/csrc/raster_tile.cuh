@@ -19,7 +19,10 @@ struct TilePixel {
   int tx0, ty0;  // origin of the tile
 };
 
-template <int BW = 8>
+// PIX = 2: a CTA of 128 threads owns the tile; warp w owns a BW x (64 / BW)
+// block and lane l the pixels (l % BW, l / BW) and (l % BW, l / BW + 32 / BW)
+// of it (px, py is the first).
+template <int BW = 8, int PIX = 1>
 __device__ __forceinline__ TilePixel tile_pixel(int tile, int tiles_x) {
   constexpr int BH = 32 / BW, PER_ROW = kTile / BW;
   const int tx = tile % tiles_x, ty = tile / tiles_x;
@@ -28,7 +31,7 @@ __device__ __forceinline__ TilePixel tile_pixel(int tile, int tiles_x) {
   t.tx0 = tx * kTile;
   t.ty0 = ty * kTile;
   t.bx0 = t.tx0 + (w % PER_ROW) * BW;
-  t.by0 = t.ty0 + (w / PER_ROW) * BH;
+  t.by0 = t.ty0 + (w / PER_ROW) * (PIX * BH);
   t.px = t.bx0 + (l % BW);
   t.py = t.by0 + (l / BW);
   return t;
@@ -59,9 +62,8 @@ __device__ __forceinline__ float frag_depth(const TriSetup &T, long long e0b, lo
 // May the triangle cover a pixel centre of the BW x (32 / BW) block at
 // (bx0, by0)?  False only when it certainly does not (bounding box, or one
 // edge function negative at every centre of the block).
-template <int BW = 8>
+template <int BW = 8, int BH = 32 / BW>
 __device__ __forceinline__ bool block_maybe(const TriSetup &T, int bx0, int by0) {
-  constexpr int BH = 32 / BW;
   if (T.xb < bx0 || T.xa > bx0 + BW - 1 || T.yb < by0 || T.ya > by0 + BH - 1) return false;
   const int Pxlo = bx0 * kSub + kSub / 2, Pxhi = Pxlo + (BW - 1) * kSub;
   const int Pylo = by0 * kSub + kSub / 2, Pyhi = Pylo + (BH - 1) * kSub;
@@ -95,9 +97,13 @@ struct TileStage {
 // every fragment.  With SORTED, each staged chunk is ordered by depth lower
 // bound (ties by binned position) first, so that near triangles come first
 // and raise the bounds early; the set of fragments visited is the same.
-template <int BW = 8, bool SORTED = false, class Bound, class Visit>
+//
+// PIX = 2 (two pixels per thread, see tile_pixel): visit(j, T, prim_id, e0, e2)
+// for pixel j of the thread; bound() is then the larger of its two bounds.
+template <int BW = 8, bool SORTED = false, int PIX = 1, class Bound, class Visit>
 __device__ __forceinline__ void for_each_fragment(const BinsView &bv, int tile, const TilePixel &tp,
                                                   TileStage &st, Bound &&bound, Visit &&visit) {
+  constexpr int BH = 32 / BW;
   const int Px = tp.px * kSub + kSub / 2, Py = tp.py * kSub + kSub / 2;
   const int warp = threadIdx.x >> 5;
   const uint32_t beg = bv.tile_offset[tile], end = bv.tile_offset[tile + 1];
@@ -144,7 +150,7 @@ __device__ __forceinline__ void for_each_fragment(const BinsView &bv, int tile, 
     int m = 0;
     for (int k0 = 0; k0 < n; k0 += 32) {
       const int k = k0 + lane;
-      const bool hit = k < n && block_maybe<BW>(st.tri[k], tp.bx0, tp.by0);
+      const bool hit = k < n && block_maybe<BW, PIX * BH>(st.tri[k], tp.bx0, tp.by0);
       const uint32_t b = __ballot_sync(0xffffffffu, hit);
       if (hit) st.list[warp][m + __popc(b & ((1u << lane) - 1u))] = (uint8_t)k;
       m += __popc(b);
@@ -157,8 +163,20 @@ __device__ __forceinline__ void for_each_fragment(const BinsView &bv, int tile, 
       const long long e0 = (long long)T.dx[0] * Py + T.c[0] - (long long)T.dy[0] * Px;
       const long long e1 = (long long)T.dx[1] * Py + T.c[1] - (long long)T.dy[1] * Px;
       const long long e2 = (long long)T.dx[2] * Py + T.c[2] - (long long)T.dy[2] * Px;
-      if ((e0 | e1 | e2) < 0) continue;
-      visit(T, st.id[k], e0, e2);
+      if constexpr (PIX == 1) {
+        if ((e0 | e1 | e2) < 0) continue;
+        visit(T, st.id[k], e0, e2);
+      } else {
+        // the second pixel, BH rows below: each edge function grows by dx BH kSub
+        const long long f0 = e0 + (long long)T.dx[0] * (BH * kSub);
+        const long long f1 = e1 + (long long)T.dx[1] * (BH * kSub);
+        const long long f2 = e2 + (long long)T.dx[2] * (BH * kSub);
+        const bool a = (e0 | e1 | e2) >= 0, b = (f0 | f1 | f2) >= 0;
+        if (!(a || b)) continue;
+        const uint32_t id = st.id[k];
+        if (a) visit(0, T, id, e0, e2);
+        if (b) visit(1, T, id, f0, f2);
+      }
     }
   }
 }

@@ -53,7 +53,8 @@ class Renderer:
         self.fused = bool(fused)
         self.fused_fp8 = fused in ("fp8", "fp8x2")
         self.mlp_kind = fused if self.fused_fp8 else "bf16"
-        # persistent: the three geometry passes in one launch (tuning: (block_w, ctas_per_sm))
+        # persistent: the three geometry passes in one launch (tuning: star_nt_tuning's
+        # (block_w, ctas_per_sm, pixels_per_thread))
         self.persistent = bool(persistent)
         self.tuning = tuning
         # persistent + fused bf16 resolve: when every pass runs at full size the

@@ -37,7 +37,7 @@ def main(argv=None):
     w = dict(np.load(os.path.join(HERE, "weights", "tail_mlp.npz")))
     r = Renderer(sc.verts, sc.rgba8, W, H, mlp=w, x_dtype=sn.BF16,
                  fused=args.mlp if args.mlp in ("fp8", "fp8x2") else True, persistent=True,
-                 tuning=(args.block_w, 0), merge_scale2=args.merge_scale2,
+                 tuning=(args.block_w, 0, 0), merge_scale2=args.merge_scale2,
                  merge_scale3=args.merge_scale3, base_tile=args.base_tile,
                  leaf=args.leaf)
     cams = scenes.orbit_cameras(W, H, 2 * args.steps)

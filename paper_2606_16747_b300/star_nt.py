@@ -76,7 +76,7 @@ class Mlp(ctypes.Structure):
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("block_w", _I32), ("ctas_per_sm", _I32)]
+    _fields_ = [("block_w", _I32), ("ctas_per_sm", _I32), ("pixels_per_thread", _I32)]
 
 
 class LeafPlan(ctypes.Structure):

@@ -147,11 +147,17 @@ def test_pass_launch_resolve_arguments_rejected(sn):
                                              ctypes.byref(b3), ctypes.byref(lay), ctypes.byref(lay),
                                              ctypes.byref(lay), ctypes.byref(p), ctypes.byref(w), 32,
                                              None, None, None, None) == sn.ERR_ARG
-    bad = sn.Tuning(5, 0)   # block width must be 4, 8 or 16
-    assert L.star_nt_geometry_passes_resolve(ctypes.byref(sc), ctypes.byref(bins), ctypes.byref(b2),
-                                             ctypes.byref(b3), ctypes.byref(lay), ctypes.byref(lay),
-                                             ctypes.byref(lay), ctypes.byref(p), ctypes.byref(w), 32,
-                                             None, ctypes.byref(bad), None, None) == sn.ERR_ARG
+    # block width 4, 8 or 16; one or two pixels per thread; at most 8 (one
+    # pixel) or 10 (two) CTAs per SM
+    for bad in (sn.Tuning(5, 0, 0), sn.Tuning(8, 0, 3), sn.Tuning(8, 9, 1), sn.Tuning(8, 11, 2),
+                sn.Tuning(8, -1, 2)):
+        assert L.star_nt_geometry_passes_resolve(ctypes.byref(sc), ctypes.byref(bins), ctypes.byref(b2),
+                                                 ctypes.byref(b3), ctypes.byref(lay), ctypes.byref(lay),
+                                                 ctypes.byref(lay), ctypes.byref(p), ctypes.byref(w), 32,
+                                                 None, ctypes.byref(bad), None, None) == sn.ERR_ARG
+        assert L.star_nt_geometry_passes(ctypes.byref(sc), ctypes.byref(bins), ctypes.byref(b2),
+                                         ctypes.byref(b3), ctypes.byref(lay), ctypes.byref(lay),
+                                         ctypes.byref(lay), ctypes.byref(bad), None, None) == sn.ERR_ARG
 
 
 def test_leaf_passes_workspace_checked(sn):

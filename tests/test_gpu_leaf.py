@@ -156,7 +156,7 @@ def test_leaf_frames_repeat_and_graph_replay(sn):
     graph replays give the same frame; the quadtree then updates the masks in
     place and the next frame follows them."""
     sc = scenes.screen_scene(41, 2500, 208, 144, size_scale=0.7, colours="coherent")
-    r = leaf_renderer(sn, sc, None, tuning=(16, 6))
+    r = leaf_renderer(sn, sc, None, tuning=(16, 6, 1))
     r.star_frame(update_tiles=False)
     torch.cuda.synchronize()
     first = r.rgba32f.clone()

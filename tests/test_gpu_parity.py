@@ -632,7 +632,7 @@ def test_fused_resolve_equals_separate_kernels(orc, sn):
     assert np.max(np.abs(rgb - o["rgb"])) <= TOL_BF16
 
 
-@pytest.mark.parametrize("tuning", [None, (16, 0), (4, 3)])
+@pytest.mark.parametrize("tuning", [None, (16, 0, 1), (4, 3, 1), (8, 0, 2), (4, 10, 2), (16, 5, 2)])
 @pytest.mark.parametrize("sizes", [((131, 91), (57, 40)), ("full", (57, 40)), ("full", "full")])
 def test_persistent_passes_equal_separate(sn, tuning, sizes):
     """The three passes in one persistent launch give the same planes bit for
@@ -710,7 +710,7 @@ def test_fixed_scales(orc, sn):
     assert np.max(np.abs(rgb - o["rgb"])) <= TOL_BF16
 
 
-@pytest.mark.parametrize("tuning", [None, (16, 6), (4, 3)])
+@pytest.mark.parametrize("tuning", [None, (16, 6, 1), (4, 3, 1), (8, 0, 1), (16, 4, 2)])
 @pytest.mark.parametrize("sizes", ["full", "reduced3", "reduced2"])
 def test_pass_launch_resolve_equals_resolve(orc, sn, tuning, sizes):
     """star_nt_geometry_passes_resolve: with every pass at full size the pass
