@@ -294,10 +294,11 @@ extern "C" star_nt_status star_nt_geometry_passes_leaf(const star_nt_scene *scen
     const int c = per_sm > 0 ? (per_sm < occ ? per_sm : occ) : occ;
     kern<<<sms * (c > 0 ? c : 1), threads, 0, st>>>(pa, modes, scene->rgba8, queue, d_status);
   };
-  if (tu.pix == 2) {  // two pixels per thread, as star_nt_geometry_passes
-    if (bw == 8) launch(k_passes_leaf<8, 10, 2>, 128);
-    else if (bw == 16) launch(k_passes_leaf<16, 10, 2>, 128);
-    else launch(k_passes_leaf<4, 10, 2>, 128);
+  if (tu.pix == 2) {  // two pixels per thread, budgets as star_nt_geometry_passes
+    const bool wide2 = per_sm == 0 || per_sm == 10;
+    if (bw == 8) wide2 ? launch(k_passes_leaf<8, 10, 2>, 128) : launch(k_passes_leaf<8, 8, 2>, 128);
+    else if (bw == 16) wide2 ? launch(k_passes_leaf<16, 10, 2>, 128) : launch(k_passes_leaf<16, 8, 2>, 128);
+    else wide2 ? launch(k_passes_leaf<4, 10, 2>, 128) : launch(k_passes_leaf<4, 8, 2>, 128);
     return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
   }
   const bool wide = per_sm == 0 || per_sm == 8;  // register budget as star_nt_geometry_passes
@@ -322,6 +323,9 @@ cudaError_t preload_leaf() {
   if ((r = cudaFuncGetAttributes(&a, k_passes_leaf<4, 10, 2>)) != cudaSuccess) e = r;
   if ((r = cudaFuncGetAttributes(&a, k_passes_leaf<8, 10, 2>)) != cudaSuccess) e = r;
   if ((r = cudaFuncGetAttributes(&a, k_passes_leaf<16, 10, 2>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_passes_leaf<4, 8, 2>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_passes_leaf<8, 8, 2>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_passes_leaf<16, 8, 2>)) != cudaSuccess) e = r;
   return e;
 }
 }  // namespace star
