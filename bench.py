@@ -49,12 +49,13 @@ def kernels_per_step(r) -> int:
         passes = 3
     return 3 + passes + (1 if r.fused else 3) + 3 + 2
 STAGE_REPS = 20
-# DRAM bytes (read + write) of one k_passes launch at 1080p, from the ncu
-# capture summarised in profiles/passes_hd.md (same kernel build; pass 3 separate at s3 = 0.91)
-PASSES_DRAM_BYTES = 27639296
-# the same for one k_passes_resolve launch (passes at full size + MLP + composite),
-# profiles/passes_resolve_hd.md
-FUSED_DRAM_BYTES = 12742144
+# DRAM bytes (read + write) of one k_passes launch at 1080p (two pixels per
+# thread), from the ncu capture summarised in profiles/passes_hd.md (pass 3
+# separate at s3 = 0.91)
+PASSES_DRAM_BYTES = 21024256
+# the same for one k_passes_resolve launch (passes at full size + MLP + composite;
+# two pixels per thread), profiles/passes_resolve_hd.md
+FUSED_DRAM_BYTES = 8200192
 
 
 def stage_rooflines(star, torch, stage_state, stage_mean, hbm_gbs):
@@ -437,11 +438,14 @@ def run_ours(args, rank, world):
                                 (stage_state["W3"], stage_state["H3"])), merged):
             if not m:
                 dom_frags += fragment_count(sn, star, vp_last, W, H, (wp, hp))
+        pix = star.tuning[2] if star.tuning is not None and len(star.tuning) > 2 and star.tuning[2] else 2
         if all(merged) and star.persistent and star.fused and not star.fused_fp8 and star.fuse_passes:
-            dom_name = ("k_passes_resolve (passes 1-3 at full size with the network input, tcgen05 "
-                        "MLP and composite of every pixel; only the traversal ops are counted)")
+            dom_name = (f"k_passes_resolve ({pix} pixel(s) per thread; passes 1-3 at full size with the "
+                        "network input, tcgen05 MLP and composite of every pixel; only the traversal ops "
+                        "are counted)")
         else:
-            dom_name = "k_passes (passes 1-3, one persistent launch)"
+            dom_name = (f"{'k_passes2' if pix == 2 else 'k_passes'} (passes 1-3, one persistent launch, "
+                        f"{pix} pixel(s) per thread)")
     else:
         dom_ms = stage_mean["pass1"]
         dom_frags = Fcount
