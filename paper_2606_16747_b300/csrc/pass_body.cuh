@@ -169,7 +169,8 @@ __device__ __forceinline__ void pass_body(const BinsView &bv, const uint32_t *__
 // tile_pixel): the triangle loads and the loop are shared by both pixels.
 template <int MODE, int BW = 8>
 __device__ __forceinline__ void pass_body2(const BinsView &bv, const uint32_t *__restrict__ rgba8,
-                                           const PassOut &po, TileStage &stage, int tile) {
+                                           const PassOut &po, TileStage &stage, int tile,
+                                           const FeatOut &fo = FeatOut{}) {
   constexpr int BH = 32 / BW;
   const BinsHeader *hd = bv.hd;
   if ((int64_t)hd->n_pairs > bv.pair_capacity) return;
@@ -187,8 +188,8 @@ __device__ __forceinline__ void pass_body2(const BinsView &bv, const uint32_t *_
         if (j == 0) a0.template visit<MODE>(T, (int)id, e0, e2);
         else a1.template visit<MODE>(T, (int)id, e0, e2);
       });
-  if (in0) a0.template finish<MODE>(bv.setups, rgba8, po, FeatOut{}, (size_t)tp.py * W + tp.px);
-  if (in1) a1.template finish<MODE>(bv.setups, rgba8, po, FeatOut{}, (size_t)(tp.py + BH) * W + tp.px);
+  if (in0) a0.template finish<MODE>(bv.setups, rgba8, po, fo, (size_t)tp.py * W + tp.px);
+  if (in1) a1.template finish<MODE>(bv.setups, rgba8, po, fo, (size_t)(tp.py + BH) * W + tp.px);
 }
 
 }  // namespace star

@@ -10,36 +10,37 @@
 
 namespace star {
 
+// One tile per CTA of 128 threads, two pixels per thread (pass_body2).
 template <int MODE>
-__global__ void __launch_bounds__(256) k_pass(BinsView bv, const uint32_t *__restrict__ rgba8,
+__global__ void __launch_bounds__(128, 8) k_pass(BinsView bv, const uint32_t *__restrict__ rgba8,
                                               PassOut po, FeatOut fo) {
   __shared__ TileStage stage;
-  pass_body<MODE>(bv, rgba8, po, fo, stage, blockIdx.x);
+  pass_body2<MODE>(bv, rgba8, po, stage, blockIdx.x, fo);
 }
 
 // Pass 1 at full resolution; when pass 2 and/or pass 3 are marked merged
 // (their size equals the full size) it keeps the two nearest fragments and
 // the tail sums as well and writes their planes at full resolution.
-__global__ void __launch_bounds__(256, 6) k_pass_merged(BinsView bv, const BinsHeader *hd2,
-                                                     const BinsHeader *hd3,
-                                                     const uint32_t *__restrict__ rgba8, PassOut o1,
-                                                     PassOut o2, PassOut o3) {
+__global__ void __launch_bounds__(128, 10) k_pass_merged(BinsView bv, const BinsHeader *hd2,
+                                                      const BinsHeader *hd3,
+                                                      const uint32_t *__restrict__ rgba8, PassOut o1,
+                                                      PassOut o2, PassOut o3) {
   __shared__ TileStage stage;
   const bool m2 = hd2->merged != 0, m3 = hd3->merged != 0;
   if (!m2 && !m3) {
-    pass_body<kTop1>(bv, rgba8, o1, FeatOut{}, stage, blockIdx.x);
+    pass_body2<kTop1>(bv, rgba8, o1, stage, blockIdx.x);
     return;
   }
   PassOut o = o1;
   o.id2 = m2 ? o2.id2 : nullptr;
   if (!m3) {  // two layers, no tail sums: the top-2 traversal with its depth skip
-    pass_body<kTop2>(bv, rgba8, o, FeatOut{}, stage, blockIdx.x);
+    pass_body2<kTop2>(bv, rgba8, o, stage, blockIdx.x);
     return;
   }
   o.n = o3.n;
   o.tail = o3.tail;
   o.t_tail = o3.t_tail;
-  pass_body<kTail>(bv, rgba8, o, FeatOut{}, stage, blockIdx.x);
+  pass_body2<kTail>(bv, rgba8, o, stage, blockIdx.x);
 }
 
 // All geometry passes of a real frame in one persistent launch: CTAs take
@@ -211,15 +212,15 @@ extern "C" star_nt_status star_nt_geometry_pass(const star_nt_scene *scene, cons
   switch (mode) {
     case 1:
       if (!layers->id1 && !layers->z1) return STAR_NT_ERR_ARG;
-      k_pass<kTop1><<<tiles, 256, 0, st>>>(v, scene->rgba8, o, fo);
+      k_pass<kTop1><<<tiles, 128, 0, st>>>(v, scene->rgba8, o, fo);
       break;
     case 2:
       if (!layers->id2) return STAR_NT_ERR_ARG;
-      k_pass<kTop2><<<tiles, 256, 0, st>>>(v, scene->rgba8, o, fo);
+      k_pass<kTop2><<<tiles, 128, 0, st>>>(v, scene->rgba8, o, fo);
       break;
     case 3:
       if (!layers->n || !layers->tail || !layers->t_tail) return STAR_NT_ERR_ARG;
-      k_pass<kTail><<<tiles, 256, 0, st>>>(v, scene->rgba8, o, fo);
+      k_pass<kTail><<<tiles, 128, 0, st>>>(v, scene->rgba8, o, fo);
       break;
     default:
       return STAR_NT_ERR_ARG;
@@ -245,7 +246,7 @@ extern "C" star_nt_status star_nt_geometry_pass_merged(const star_nt_scene *scen
   BinsView v1 = bins_view(*b1), v2 = bins_view(*b2), v3 = bins_view(*b3);
   PassOut o1 = pass_out(l1);
   o1.id2 = nullptr; o1.n = nullptr; o1.tail = nullptr; o1.t_tail = nullptr;
-  k_pass_merged<<<tiles_of(b1), 256, 0, (cudaStream_t)stream>>>(v1, v2.hd, v3.hd, scene->rgba8, o1,
+  k_pass_merged<<<tiles_of(b1), 128, 0, (cudaStream_t)stream>>>(v1, v2.hd, v3.hd, scene->rgba8, o1,
                                                                 pass_out(l2), pass_out(l3));
   return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
 }
@@ -332,7 +333,7 @@ extern "C" star_nt_status star_nt_build_inputs(const star_nt_scene *scene, const
   const bool fused = (b1->mem == b2->mem) && (b2->mem == b3->mem);
   if (fused) {
     BinsView v1 = bins_view(*b1);
-    k_pass<kFused><<<tiles_of(b1), 256, 0, (cudaStream_t)stream>>>(v1, scene->rgba8, pass_out(l1), fo);
+    k_pass<kFused><<<tiles_of(b1), 128, 0, (cudaStream_t)stream>>>(v1, scene->rgba8, pass_out(l1), fo);
     return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
   }
   if (!l1 || !l1->id1 || !l2 || !l2->id2 || !l3 || !l3->n || !l3->tail || !l3->t_tail)
