@@ -160,10 +160,10 @@ __device__ __forceinline__ void pass_resolve_body(const BinsView &bv, const uint
   // ---- composite, Eq. 4
   {
     uint32_t r[4];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+    asm volatile("{\n tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n tcgen05.wait::ld.sync.aligned;\n}"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(lane_tmem + 16));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                 : "r"(lane_tmem + 16)
+                 : "memory");
     if (inside) {
       float f0 = 0.f, f1 = 0.f, f2 = 0.f;
       if (flag) {
@@ -298,10 +298,10 @@ __device__ __forceinline__ void pass_resolve_body2(const BinsView &bv, const uin
 #pragma unroll
   for (int t = 0; t < 2; ++t) {
     uint32_t r[4];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+    asm volatile("{\n tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n tcgen05.wait::ld.sync.aligned;\n}"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(lane_tmem + 32 * t + 16));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                 : "r"(lane_tmem + 32 * t + 16)
+                 : "memory");
     const bool in = t ? in1 : in0, flag = t ? flag1 : flag0;
     const float4 front = t ? front1 : front0;
     const size_t p = t ? p1 : p0;
