@@ -176,7 +176,8 @@ __global__ void __launch_bounds__(32) k_reproject_matrix(const double *__restric
 __global__ void __launch_bounds__(256) k_reproject(const float4 *__restrict__ prev,
                                                    const float *__restrict__ z1,
                                                    const float *__restrict__ Eg, int W, int H,
-                                                   float4 *__restrict__ out, uint32_t *__restrict__ q) {
+                                                   float rW, float rH, float4 *__restrict__ out,
+                                                   uint32_t *__restrict__ q) {
   __shared__ float sE[16];
   if (threadIdx.x < 16) sE[threadIdx.x] = Eg[threadIdx.x];
   __syncthreads();
@@ -184,8 +185,10 @@ __global__ void __launch_bounds__(256) k_reproject(const float4 *__restrict__ pr
   const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
   if (x >= W || y >= H) return;
   const size_t p = (size_t)y * W + x;
-  const float nx = (float)(2 * x + 1) / (float)W - 1.0f;
-  const float ny = 1.0f - (float)(2 * y + 1) / (float)H;
+  // pixel-centre NDC with the reciprocals of W and H taken once per frame
+  // (the kernel's four divisions per pixel were most of its issue slots)
+  const float nx = fmaf((float)(2 * x + 1), rW, -1.0f);
+  const float ny = fmaf(-(float)(2 * y + 1), rH, 1.0f);
   const float d = z1[p];
   const float a0 = fmaf(sE[0], nx, fmaf(sE[1], ny, fmaf(sE[2], d, sE[3])));
   const float a1 = fmaf(sE[4], nx, fmaf(sE[5], ny, fmaf(sE[6], d, sE[7])));
@@ -197,8 +200,9 @@ __global__ void __launch_bounds__(256) k_reproject(const float4 *__restrict__ pr
     if (q) q[p] = quantize_rgba8(v);
     return;
   }
-  float dx = 0.5f * (float)W * (a0 - nx * a3) / den;
-  float dy = -0.5f * (float)H * (a1 - ny * a3) / den;
+  const float rden = __frcp_rn(den);  // correctly rounded, as 1 / den
+  float dx = 0.5f * (float)W * (a0 - nx * a3) * rden;
+  float dy = -0.5f * (float)H * (a1 - ny * a3) * rden;
   dx = fminf(fmaxf(dx, -2.0f * W - 2.0f), 2.0f * W + 2.0f);
   dy = fminf(fmaxf(dy, -2.0f * H - 2.0f), 2.0f * H + 2.0f);
   const float fx0 = floorf(dx), fy0 = floorf(dy);
@@ -304,6 +308,7 @@ extern "C" star_nt_status star_nt_reproject(const float *prev_rgba, const float 
   k_reproject_matrix<<<1, 32, 0, st>>>(vp_prev, vp_cur, E);
   dim3 grid((W + 31) / 32, (H + 7) / 8);
   k_reproject<<<grid, 256, 0, st>>>(reinterpret_cast<const float4 *>(prev_rgba), prev_z1, E, W, H,
+                                    1.0f / (float)W, 1.0f / (float)H,
                                     reinterpret_cast<float4 *>(out_rgba), out_rgba8);
   return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
 }
