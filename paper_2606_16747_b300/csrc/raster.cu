@@ -249,6 +249,64 @@ __device__ __forceinline__ void for_each_pair(const TriSetup *tri, int t0, int n
   }
 }
 
+// The fill's walk of for_each_pair, in rounds of kFillBatch candidates per
+// thread: the candidates' tile tests first, then their cursor increments
+// (independent atomics, all in flight together), then the pair writes, so
+// that a thread waits for one atomic round trip per round instead of one per
+// candidate.  The pairs written are the same; their order within a tile is
+// not fixed in either form.
+constexpr int kFillBatch = 4;
+__device__ __forceinline__ void fill_pairs(const TriSetup *tri, int t0, int n_tris, int tiles_x,
+                                           int *s_off, const BinsView &bv) {
+  const int tid = threadIdx.x;
+  if (tid < 32) {
+    int tx0 = 0, ty0 = 0, ntx = 1;
+    const int nt = t0 + tid < n_tris ? tile_span(tri[tid], tx0, ty0, ntx) : 0;
+    int v = nt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, v, o);
+      if (tid >= o) v += y;
+    }
+    s_off[tid + 1] = v;
+    if (tid == 0) s_off[0] = 0;
+  }
+  __syncthreads();
+  const int total = s_off[kBinTris];
+  for (int q0 = tid; q0 < total; q0 += kBinThreads * kFillBatch) {
+    int tile[kFillBatch], tr[kFillBatch];
+#pragma unroll
+    for (int b = 0; b < kFillBatch; ++b) {
+      tile[b] = -1;
+      tr[b] = 0;
+      const int q = q0 + b * kBinThreads;
+      if (q < total) {
+        int lo = 0, hi = kBinTris - 1;  // largest j with s_off[j] <= q
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (s_off[mid] <= q) lo = mid; else hi = mid - 1;
+        }
+        const TriSetup &T = tri[lo];
+        int ax0, ay0, anx;
+        tile_span(T, ax0, ay0, anx);
+        const int k = q - s_off[lo];
+        const int tx = ax0 + k % anx, ty = ay0 + k / anx;
+        if (tile_hit(T, tx, ty)) {
+          tile[b] = ty * tiles_x + tx;
+          tr[b] = t0 + lo;
+        }
+      }
+    }
+    uint32_t pos[kFillBatch];
+#pragma unroll
+    for (int b = 0; b < kFillBatch; ++b)
+      pos[b] = tile[b] >= 0 ? atomicAdd(bv.tile_cursor + tile[b], 1u) : 0u;
+#pragma unroll
+    for (int b = 0; b < kFillBatch; ++b)
+      if (tile[b] >= 0) bv.pairs[pos[b]] = (uint32_t)tr[b];
+  }
+}
+
 // Up to STAR_NT_MAX_RASTER_PASSES passes are binned by the same launches
 // (blockIdx.y = pass).
 constexpr int kMaxPasses = STAR_NT_MAX_RASTER_PASSES;
@@ -329,9 +387,7 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_fill(PassSet ps, int n_tris
   for (int i = threadIdx.x; i < nb * 7; i += kBinThreads)
     reinterpret_cast<uint4 *>(s_tri)[i] = __ldg(reinterpret_cast<const uint4 *>(bv.setups + t0) + i);
   __syncthreads();
-  for_each_pair(s_tri, t0, n_tris, hd->tiles_x, s_off, [&](int t, int tile) {
-    bv.pairs[atomicAdd(bv.tile_cursor + tile, 1u)] = (uint32_t)t;
-  });
+  fill_pairs(s_tri, t0, n_tris, hd->tiles_x, s_off, bv);
 }
 
 // Exclusive scan of the tile counts, one block of 1024 threads per pass, in
