@@ -103,9 +103,11 @@ struct FeatIn {
   const float *t3;
 
   // nothing to do: a pass was rejected by its raster, or the pass launch
-  // already produced the frame
+  // already produced the frame (the three words are loaded together: a CTA
+  // that returns at once waits for one round trip, not three)
   __device__ __forceinline__ bool rejected() const {
-    return hd2->n_pixels <= 0 || hd3->n_pixels <= 0 || hd2->resolved != 0;
+    const int r = hd2->resolved, n2 = hd2->n_pixels, n3 = hd3->n_pixels;
+    return (r != 0) | (n2 <= 0) | (n3 <= 0);
   }
 };
 
