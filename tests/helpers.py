@@ -72,3 +72,43 @@ def watertight_mesh(rng, W, H, gx, gy, jitter_grid=4, shuffle=True):
     if shuffle:
         tris = tris[rng.permutation(len(tris))]
     return np.ascontiguousarray(tris)
+
+
+# depth levels of the tie scenes: exact in float32, and 0.5 + 2^-16 sits exactly
+# one depth margin (2^-16) behind 0.5, the edge case of a triangle whose depth
+# lower bound equals another fragment's depth
+TIE_DEPTHS = (0.5, 0.5 + 2.0 ** -16, 0.5 + 2.0 ** -15, 0.75)
+
+
+def tied_rect_scene(rng, W, H, n_rects, depths=TIE_DEPTHS, alpha=(20, 235)):
+    """Axis-aligned rectangles at a few shared depths, each split along its
+    main diagonal into two triangles, the triangles submitted in a random
+    order (primitive id = position in the returned arrays).  Rectangle corners
+    are whole pixels, widths odd and heights even, so no pixel centre lies on
+    a rectangle's border or on its diagonal: each centre inside a rectangle is
+    covered by exactly one of its two triangles, whatever the tie rule.
+
+    Returns verts [2n][3][4], rgba8 [2n], and per rectangle (x0, y0, x1, y1, z,
+    id_a, id_b), where id_a is the triangle (x0,y0) (x1,y0) (x1,y1) and id_b the
+    triangle (x0,y0) (x1,y1) (x0,y1)."""
+    rects, tris, cols = [], [], []
+    for _ in range(n_rects):
+        w = 2 * int(rng.integers(1, max(2, W // 2))) + 1
+        h = 2 * int(rng.integers(1, max(2, H // 2)))
+        x0 = int(rng.integers(-w // 2, W - w // 2))
+        y0 = int(rng.integers(-h // 2, H - h // 2))
+        z = float(depths[int(rng.integers(0, len(depths)))])
+        rects.append((x0, y0, x0 + w, y0 + h, z))
+        for _t in range(2):
+            cols.append(rgba(*[int(v) for v in rng.integers(0, 256, 3)], int(rng.integers(alpha[0], alpha[1] + 1))))
+    for (x0, y0, x1, y1, z) in rects:
+        tris += [tri((x0, y0), (x1, y0), (x1, y1), (z, z, z)), tri((x0, y0), (x1, y1), (x0, y1), (z, z, z))]
+    perm = rng.permutation(len(tris))          # new position of each triangle
+    verts = np.zeros((len(tris), 3, 4), np.float32)
+    rgba8 = np.zeros(len(tris), np.uint32)
+    for k, pos in enumerate(perm):
+        verts[pos] = tris[k]
+        rgba8[pos] = cols[k]
+    meta = [(x0, y0, x1, y1, z, int(perm[2 * i]), int(perm[2 * i + 1]))
+            for i, (x0, y0, x1, y1, z) in enumerate(rects)]
+    return verts, rgba8, meta
