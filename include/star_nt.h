@@ -422,10 +422,13 @@ star_nt_status star_nt_quadtree(const uint32_t *rgba8, const int32_t *id1, int32
  * bytes, held on every GPU that loads the library until the process exits),
  * enough for STAR_NT_QT_STATIC_MAX_TILES base tiles; larger frames return
  * STAR_NT_ERR_CAPACITY.  Arguments and results are those of star_nt_quadtree
- * minus ws / ws_bytes; nothing is allocated.  The first call on a device looks
- * up the array's device address with that device current (make that first
- * call before any stream capture).  All calls share the one array and it
- * keeps the last call's contents (the parts that must start at zero are
+ * minus ws / ws_bytes; nothing is allocated.  The array's device address
+ * belongs to a CUDA context: the first call made in a context (the device's
+ * primary context, or a context the host application created and made
+ * current) looks the address up with that context current and caches it
+ * under the context's id, so make that first call before any stream capture
+ * in that context.  All calls share the one array on a device's context and
+ * it keeps the last call's contents (the parts that must start at zero are
  * cleared by each call), so calls that overlap on the GPU race: serialise
  * them, for instance on one stream. */
 #define STAR_NT_QT_STATIC_MAX_TILES 65536

@@ -382,25 +382,70 @@ constexpr int kQtStaticMaxTiles = 65536;
 constexpr size_t kQtStaticBytes = 256 + 2 * 4 * (size_t)kQtStaticMaxTiles;
 static __device__ __align__(256) unsigned char g_qt_scratch[kQtStaticBytes];
 
-constexpr int kMaxDevices = 64;
+// The array's device address belongs to a CUDA context, not to a device: a
+// host application may run its own (non-primary) context on the device, and a
+// device reset replaces the primary context.  The address is therefore looked
+// up once per context, with that context current, and cached under the
+// context's unique id (never reused within a process).  The driver calls come
+// through the runtime's entry-point query, so the library does not link the
+// driver library itself.
+typedef int (*CtxGetCurrentFn)(void **ctx);                      // cuCtxGetCurrent
+typedef int (*CtxGetIdFn)(void *ctx, unsigned long long *id);    // cuCtxGetId
+constexpr int kQtAddrSlots = 64;
+struct QtAddrSlot {
+  unsigned long long ctx_id;  // 0: empty
+  void *addr;
+};
 static std::mutex g_qt_mutex;
-static void *g_qt_addr[kMaxDevices];  // device address of g_qt_scratch, per device
+static QtAddrSlot g_qt_addr[kQtAddrSlots];
+static int g_qt_next = 0;
+static CtxGetCurrentFn g_ctx_current = nullptr;
+static CtxGetIdFn g_ctx_id = nullptr;
 
-// Device address of the array on the current device, looked up once per
-// device (with that device current) and cached.
-static cudaError_t qt_scratch_address(void **out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_qt_mutex);
-  if (!g_qt_addr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_qt_scratch);
-    if (e != cudaSuccess) return e;
-    g_qt_addr[dev] = p;
+// Id of the context current on this thread (0 when none is current yet).
+static cudaError_t current_ctx_id(unsigned long long *id) {
+  if (!g_ctx_current || !g_ctx_id) {
+    void *f = nullptr, *g = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q1);
+    if (e != cudaSuccess || q1 != cudaDriverEntryPointSuccess || !f) return cudaErrorNotSupported;
+    e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &g, 12000, cudaEnableDefault, &q2);
+    if (e != cudaSuccess || q2 != cudaDriverEntryPointSuccess || !g) return cudaErrorNotSupported;
+    g_ctx_current = (CtxGetCurrentFn)f;
+    g_ctx_id = (CtxGetIdFn)g;
   }
-  *out = g_qt_addr[dev];
+  void *ctx = nullptr;
+  if (g_ctx_current(&ctx) != 0) return cudaErrorUnknown;
+  *id = 0;
+  if (ctx && g_ctx_id(ctx, id) != 0) return cudaErrorUnknown;
+  return cudaSuccess;
+}
+
+// Device address of the array in the context current on this thread: looked
+// up on the first call in each context and cached.
+static cudaError_t qt_scratch_address(void **out) {
+  std::lock_guard<std::mutex> lock(g_qt_mutex);
+  unsigned long long id = 0;
+  cudaError_t e = current_ctx_id(&id);
+  if (e != cudaSuccess) return e;
+  if (id) {
+    for (int k = 0; k < kQtAddrSlots; ++k)
+      if (g_qt_addr[k].ctx_id == id) {
+        *out = g_qt_addr[k].addr;
+        return cudaSuccess;
+      }
+  }
+  // not seen yet (or no context current: the runtime then makes the device's
+  // primary context current here)
+  void *p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_qt_scratch);
+  if (e != cudaSuccess) return e;
+  if (!id && (e = current_ctx_id(&id)) != cudaSuccess) return e;
+  if (id) {
+    g_qt_addr[g_qt_next] = QtAddrSlot{id, p};
+    g_qt_next = (g_qt_next + 1) % kQtAddrSlots;
+  }
+  *out = p;
   return cudaSuccess;
 }
 }  // namespace star
