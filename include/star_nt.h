@@ -523,9 +523,10 @@ star_nt_status star_nt_resolve_leaf(const star_nt_scene *scene, const star_nt_le
 /* display needs only the 8-bit frame); prev_z1: [W*H];                      */
 /* vp_prev, vp_cur: device, 16 float64 row-major view-projections; ws: device */
 /* scratch of STAR_NT_REPROJECT_WS_BYTES bytes (16-byte aligned) that holds  */
-/* VP_prev inv(VP_cur) - I for the call (two launches: that matrix in       */
-/* float64, then the per-pixel pass in float32 on offsets from the pixel).  */
-#define STAR_NT_REPROJECT_WS_BYTES 64
+/* the call's offset coefficients (two launches: the coefficients from       */
+/* VP_prev inv(VP_cur) in float64, then the per-pixel pass, whose sample      */
+/* offsets are float-float, accurate to about 1e-9 pixel).  W, H <= 32768.   */
+#define STAR_NT_REPROJECT_WS_BYTES 128
 star_nt_status star_nt_reproject(const float *prev_rgba, const float *prev_z1,
                                  const double *vp_prev, const double *vp_cur, int32_t W,
                                  int32_t H, float *out_rgba, uint32_t *out_rgba8, void *ws,

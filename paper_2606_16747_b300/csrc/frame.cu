@@ -102,10 +102,19 @@ __global__ void __launch_bounds__(256) k_composite(const float4 *__restrict__ fr
 
 // ---------------------------------------------------------------------------
 // Reprojection.  With M = VP_prev inv(VP_cur) and E = M - I, the previous
-// clip position of v = (ndc_x, ndc_y, d, 1) is v + E v, so the screen offset
-// is dx = (W/2) (E0 v - ndc_x E3 v) / (1 + E3 v) (and likewise in y).  Every
-// term is small for small camera motion, which keeps float32 accurate where
-// absolute pixel coordinates would not be.
+// clip position of v = (ndc_x, ndc_y, d, 1) is v + E v.  With the pixel
+// centre written as px = x + 1/2 - W/2, py = y + 1/2 - H/2 (ndc_x = 2 px / W,
+// ndc_y = -2 py / H), the screen offset of the sample is
+//   dx = (b0 - px a3) / (1 + a3),  dy = (b1 - py a3) / (1 + a3),
+//   b0 = (W/2) E_0 v,  b1 = -(H/2) E_1 v,  a3 = E_3 v,
+// each b_k and a3 linear in (px, py, d, 1) with coefficients taken once per
+// call in float64.  Under camera motion the depth and constant terms of b0
+// and b1 cancel (at a 2 degree orbit step at 3840 wide, about 700 px each
+// against an offset of 120 px), so float32 would lose about 1e-4 px there:
+// the per-pixel arithmetic is float-float (hi + lo pairs, error-free products
+// by FMA, error-free sums), which keeps the sample position to about 1e-9 px;
+// only the bilinear weights and the blend are plain float32.
+//
 // inv(a) by cofactors: twelve 2x2 minors of rows 0-1 (s) and rows 2-3 (c),
 // the determinant, then one entry of the adjugate per thread.  Sixteen
 // threads; every value is the same expression as a one-thread evaluation.
@@ -147,12 +156,14 @@ __device__ __forceinline__ double adjugate(const double *a, const double *s, con
   }
 }
 
-// E = VP_prev inv(VP_cur) - I, once per call, in float64, rounded to float32.
-// One warp: threads 0..15 own one matrix entry each.
+// Coefficients of b0, b1, a3 in (px, py, d, 1), once per call in float64,
+// each stored as a float pair (hi, lo), hi + lo = the float64 value to about
+// 2^-48 of it: C[row][term][2], rows b0, b1, a3.  One warp: threads 0..15
+// own one entry of E each; threads 0..11 then one coefficient each.
 __global__ void __launch_bounds__(32) k_reproject_matrix(const double *__restrict__ vp_prev,
-                                                         const double *__restrict__ vp_cur,
-                                                         float *__restrict__ E) {
-  __shared__ double a[16], sc[12], inv[16], s_id;
+                                                         const double *__restrict__ vp_cur, int W,
+                                                         int H, float *__restrict__ C) {
+  __shared__ double a[16], sc[12], inv[16], E[16], s_id;
   const int t = threadIdx.x;
   if (t < 16) a[t] = vp_cur[t];
   __syncwarp();
@@ -169,45 +180,121 @@ __global__ void __launch_bounds__(32) k_reproject_matrix(const double *__restric
     const int r = t >> 2, c = t & 3;
     double m = 0.0;
     for (int k = 0; k < 4; ++k) m += vp_prev[4 * r + k] * inv[4 * k + c];
-    E[t] = (float)(m - (r == c ? 1.0 : 0.0));
+    E[t] = m - (r == c ? 1.0 : 0.0);
   }
+  __syncwarp();
+  if (t < 12) {
+    const int row = t >> 2, term = t & 3;
+    const double w = (double)W, h = (double)H;
+    double v;
+    if (row == 0) {        // b0 = (W/2) E_0 v
+      const double f[4] = {1.0, -w / h, 0.5 * w, 0.5 * w};
+      v = f[term] * E[term];
+    } else if (row == 1) { // b1 = -(H/2) E_1 v
+      const double f[4] = {-h / w, 1.0, -0.5 * h, -0.5 * h};
+      v = f[term] * E[4 + term];
+    } else {               // a3 = E_3 v
+      const double f[4] = {2.0 / w, -2.0 / h, 1.0, 1.0};
+      v = f[term] * E[12 + term];
+    }
+    const float hi = (float)v;
+    C[2 * t] = hi;
+    C[2 * t + 1] = (float)(v - (double)hi);
+  }
+}
+
+// float-float helpers: a value is hi + lo with |lo| <= ulp(hi) / 2.  The
+// intrinsics keep every rounding explicit (no contraction into FMAs).
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float v = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, v)), __fsub_rn(b, v));
+}
+__device__ __forceinline__ FF ff_norm(float s, float e) {  // |s| >= |e|
+  const float h = __fadd_rn(s, e);
+  return FF{h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+// c[0..7] = (hi, lo) of the coefficients of (px, py, d, 1): the row's value
+__device__ __forceinline__ FF ff_row(const float *c, float px, float py, float d) {
+  float s = __fmul_rn(c[0], px);
+  float e = __fmaf_rn(c[1], px, __fmaf_rn(c[0], px, -s));
+  const float t[2] = {py, d};
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float p = __fmul_rn(c[2 + 2 * k], t[k]);
+    const float q = __fmaf_rn(c[3 + 2 * k], t[k], __fmaf_rn(c[2 + 2 * k], t[k], -p));
+    float s2, e2;
+    two_sum(s, p, s2, e2);
+    e = __fadd_rn(e, __fadd_rn(q, e2));
+    s = s2;
+  }
+  float s2, e2;
+  two_sum(s, c[6], s2, e2);
+  e = __fadd_rn(e, __fadd_rn(c[7], e2));
+  return ff_norm(s2, e);
+}
+// (b - t a) / den, b, a, den float-float, t a float: one Newton correction of
+// the float quotient
+__device__ __forceinline__ FF ff_offset(FF b, float t, FF a, FF den, float rden) {
+  const float p = __fmul_rn(a.hi, t);
+  const float q = __fmaf_rn(a.lo, t, __fmaf_rn(a.hi, t, -p));
+  float s, e;
+  two_sum(b.hi, -p, s, e);
+  const FF num = ff_norm(s, __fadd_rn(e, __fsub_rn(b.lo, q)));
+  const float q1 = __fmul_rn(num.hi, rden);
+  const float m = __fmul_rn(q1, den.hi);
+  const float me = __fmaf_rn(q1, den.hi, -m);
+  const float r = __fsub_rn(__fsub_rn(__fsub_rn(num.hi, m), me), __fmaf_rn(q1, den.lo, -num.lo));
+  return ff_norm(q1, __fmul_rn(r, rden));
+}
+// integer part and fractional weight of x + o (o float-float, |o| < 2^22)
+__device__ __forceinline__ void ff_split(int x, FF o, int &i, float &f) {
+  float fl = floorf(o.hi);
+  float fr = __fadd_rn(__fsub_rn(o.hi, fl), o.lo);
+  if (fr < 0.0f) { fr = __fadd_rn(fr, 1.0f); fl -= 1.0f; }
+  if (fr >= 1.0f) { fr = __fsub_rn(fr, 1.0f); fl += 1.0f; }
+  i = x + (int)fl;
+  f = fr;
 }
 
 __global__ void __launch_bounds__(256) k_reproject(const float4 *__restrict__ prev,
                                                    const float *__restrict__ z1,
-                                                   const float *__restrict__ Eg, int W, int H,
-                                                   float rW, float rH, float4 *__restrict__ out,
+                                                   const float *__restrict__ Cg, int W, int H,
+                                                   float4 *__restrict__ out,
                                                    uint32_t *__restrict__ q) {
-  __shared__ float sE[16];
-  if (threadIdx.x < 16) sE[threadIdx.x] = Eg[threadIdx.x];
+  __shared__ float sC[24];
+  if (threadIdx.x < 24) sC[threadIdx.x] = Cg[threadIdx.x];
   __syncthreads();
   const int x = blockIdx.x * 32 + (threadIdx.x & 31);
   const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
   if (x >= W || y >= H) return;
   const size_t p = (size_t)y * W + x;
-  // pixel-centre NDC with the reciprocals of W and H taken once per frame
-  // (the kernel's four divisions per pixel were most of its issue slots)
-  const float nx = fmaf((float)(2 * x + 1), rW, -1.0f);
-  const float ny = fmaf(-(float)(2 * y + 1), rH, 1.0f);
+  // pixel centre relative to the image centre: exact half-integers
+  const float px = 0.5f * (float)(2 * x + 1 - W), py = 0.5f * (float)(2 * y + 1 - H);
   const float d = z1[p];
-  const float a0 = fmaf(sE[0], nx, fmaf(sE[1], ny, fmaf(sE[2], d, sE[3])));
-  const float a1 = fmaf(sE[4], nx, fmaf(sE[5], ny, fmaf(sE[6], d, sE[7])));
-  const float a3 = fmaf(sE[12], nx, fmaf(sE[13], ny, fmaf(sE[14], d, sE[15])));
-  const float den = 1.0f + a3;
-  if (!(den > 0.0f)) {
+  const FF a3 = ff_row(sC + 16, px, py, d);
+  float s, e;
+  two_sum(1.0f, a3.hi, s, e);
+  const FF den = ff_norm(s, __fadd_rn(e, a3.lo));
+  if (!(den.hi > 0.0f)) {
     const float4 v = prev[p];
     if (out) out[p] = v;
     if (q) q[p] = quantize_rgba8(v);
     return;
   }
-  const float rden = __frcp_rn(den);  // correctly rounded, as 1 / den
-  float dx = 0.5f * (float)W * (a0 - nx * a3) * rden;
-  float dy = -0.5f * (float)H * (a1 - ny * a3) * rden;
-  dx = fminf(fmaxf(dx, -2.0f * W - 2.0f), 2.0f * W + 2.0f);
-  dy = fminf(fmaxf(dy, -2.0f * H - 2.0f), 2.0f * H + 2.0f);
-  const float fx0 = floorf(dx), fy0 = floorf(dy);
-  const float fx = dx - fx0, fy = dy - fy0;
-  const int ix = x + (int)fx0, iy = y + (int)fy0;
+  const float rden = __frcp_rn(den.hi);
+  FF dx = ff_offset(ff_row(sC, px, py, d), px, a3, den, rden);
+  FF dy = ff_offset(ff_row(sC + 8, px, py, d), py, a3, den, rden);
+  const float lx = 2.0f * W + 2.0f, ly = 2.0f * H + 2.0f;  // far outside: clamped to the edge anyway
+  if (!(fabsf(dx.hi) <= lx)) dx = FF{copysignf(lx, dx.hi), 0.0f};
+  if (!(fabsf(dy.hi) <= ly)) dy = FF{copysignf(ly, dy.hi), 0.0f};
+  int ix, iy;
+  float fx, fy;
+  ff_split(x, dx, ix, fx);
+  ff_split(y, dy, iy, fy);
   const int x0 = min(max(ix, 0), W - 1), x1 = min(max(ix + 1, 0), W - 1);
   const int y0 = min(max(iy, 0), H - 1), y1 = min(max(iy + 1, 0), H - 1);
   const float4 v00 = prev[(size_t)y0 * W + x0], v10 = prev[(size_t)y0 * W + x1];
@@ -235,6 +322,7 @@ cudaError_t star_launch_mlp_bf16(const star_nt_mlp *w, const void *x, float *f, 
                                  int32_t *d_status, cudaStream_t st);
 
 extern "C" int32_t star_nt_version(void) { return STAR_NT_VERSION; }
+
 
 extern "C" const char *star_nt_status_string(int32_t s) {
   switch (s) {
@@ -297,18 +385,18 @@ extern "C" star_nt_status star_nt_reproject(const float *prev_rgba, const float 
                                             const double *vp_prev, const double *vp_cur, int32_t W,
                                             int32_t H, float *out_rgba, uint32_t *out_rgba8,
                                             void *ws, void *stream) {
-  if (W <= 0 || H <= 0 || !prev_rgba || !prev_z1 || !vp_prev || !vp_cur || (!out_rgba && !out_rgba8) ||
+  if (W <= 0 || H <= 0 || W > 32768 || H > 32768 || !prev_rgba || !prev_z1 || !vp_prev || !vp_cur ||
+      (!out_rgba && !out_rgba8) ||
       !ws || prev_rgba == out_rgba)
     return STAR_NT_ERR_ARG;
   if (((uintptr_t)prev_rgba & 15u) || ((uintptr_t)out_rgba & 15u) || ((uintptr_t)vp_prev & 7u) ||
       ((uintptr_t)vp_cur & 7u) || ((uintptr_t)ws & 15u))
     return STAR_NT_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
-  float *E = reinterpret_cast<float *>(ws);
-  k_reproject_matrix<<<1, 32, 0, st>>>(vp_prev, vp_cur, E);
+  float *C = reinterpret_cast<float *>(ws);
+  k_reproject_matrix<<<1, 32, 0, st>>>(vp_prev, vp_cur, W, H, C);
   dim3 grid((W + 31) / 32, (H + 7) / 8);
-  k_reproject<<<grid, 256, 0, st>>>(reinterpret_cast<const float4 *>(prev_rgba), prev_z1, E, W, H,
-                                    1.0f / (float)W, 1.0f / (float)H,
+  k_reproject<<<grid, 256, 0, st>>>(reinterpret_cast<const float4 *>(prev_rgba), prev_z1, C, W, H,
                                     reinterpret_cast<float4 *>(out_rgba), out_rgba8);
   return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
 }

@@ -419,7 +419,7 @@ def resolve_leaf(scene: Scene, plan: LeafPlan, layers, masks, params: Params, w:
         _stream(stream)))
 
 
-REPROJECT_WS_BYTES = 64
+REPROJECT_WS_BYTES = 128
 
 
 def reproject(prev_rgba, prev_z1, vp_prev, vp_cur, W, H, out_rgba, ws=None, stream=None,

@@ -11,7 +11,6 @@ from paper_2606_16747_b300 import scenes
 pytestmark = pytest.mark.gpu
 
 TOL_BF16 = 2.0 / 255.0   # bf16 MLP, frame error <= MLP error (scaled by T_2 <= 1)
-TOL_FP8_MAX = 20.0 / 255.0
 
 
 @pytest.fixture(scope="module")
