@@ -115,6 +115,22 @@ void star_nt_default_params(star_nt_params *p);
  * device of another architecture). */
 star_nt_status star_nt_preload(void);
 
+/* star_nt_set_wait_limit: bound, in nanoseconds, of every wait of the
+ * tensor-core kernels (star_nt_infer in BF16, the resolves, the pass launch
+ * that produces the frame) for an MMA or a TMA copy.  Default 1e9 (one
+ * second), at most STAR_NT_MAX_WAIT_LIMIT_NS, else STAR_NT_ERR_ARG.  A wait
+ * that runs out raises STAR_NT_ERR_TIMEOUT in the call's status word; the
+ * kernel then stops its work, lets the MMA or copy it has in flight complete
+ * (under a second, fixed one-second bound), frees its tensor memory and
+ * returns, so the device stays usable.  0 makes every such wait run out at
+ * once (to exercise that path).  Process-wide; read when a call enqueues its
+ * launch, so a captured CUDA graph keeps the value in force at capture.
+ * The paper has no counterpart: this is the library's failure detection.
+ * star_nt_wait_limit returns the value in force. */
+#define STAR_NT_MAX_WAIT_LIMIT_NS 60000000000ull
+star_nt_status star_nt_set_wait_limit(uint64_t ns);
+uint64_t star_nt_wait_limit(void);
+
 /* ------------------------------------------------------------------------ */
 /* star_nt_raster -- geometry front end of one pass (Sec. 3, Fig. 1).         */
 /*                                                                           */

@@ -146,6 +146,10 @@ __device__ __forceinline__ uint32_t quantize_rgba8(float r, float g, float b) {
 }
 __device__ __forceinline__ uint32_t quantize_rgba8(float4 c) { return quantize_rgba8(c.x, c.y, c.z); }
 
+// Bound, in nanoseconds, of the tensor-core kernels' waits for an MMA commit
+// or a TMA copy (star_nt_set_wait_limit); passed to each launch.
+unsigned long long wait_limit_ns();
+
 // First error wins.
 __device__ inline void raise_status(int32_t *status, int32_t code) {
   if (status) atomicCAS(status, STAR_NT_OK, code);

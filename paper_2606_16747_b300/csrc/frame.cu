@@ -3,6 +3,8 @@
 // and the small C-ABI utilities.
 #include <math.h>
 
+#include <atomic>
+
 #include "common.cuh"
 
 namespace star {
@@ -323,6 +325,20 @@ cudaError_t star_launch_mlp_bf16(const star_nt_mlp *w, const void *x, float *f, 
 
 extern "C" int32_t star_nt_version(void) { return STAR_NT_VERSION; }
 
+// Bound of the tensor-core kernels' waits, read at every launch.
+static std::atomic<unsigned long long> g_wait_limit_ns{1000000000ull};
+
+namespace star {
+unsigned long long wait_limit_ns() { return g_wait_limit_ns.load(std::memory_order_relaxed); }
+}  // namespace star
+
+extern "C" star_nt_status star_nt_set_wait_limit(uint64_t ns) {
+  if (ns > STAR_NT_MAX_WAIT_LIMIT_NS) return STAR_NT_ERR_ARG;
+  g_wait_limit_ns.store(ns, std::memory_order_relaxed);
+  return STAR_NT_OK;
+}
+
+extern "C" uint64_t star_nt_wait_limit(void) { return g_wait_limit_ns.load(std::memory_order_relaxed); }
 
 extern "C" const char *star_nt_status_string(int32_t s) {
   switch (s) {

@@ -12,8 +12,9 @@
 // ReLU while packing to bf16, and write the next layer's operand to shared
 // memory.  Operands use the no-swizzle K-major layout: 8-row x 16-byte core
 // matrices, LBO = distance between K-adjacent core matrices, SBO = between
-// 8-row groups.  Every mbarrier wait is bounded (1 s); on expiry the kernel
-// sets STAR_NT_ERR_TIMEOUT, stops, frees its tensor memory and returns.
+// 8-row groups.  Every mbarrier wait is bounded (star_nt_set_wait_limit); on
+// expiry the kernel sets STAR_NT_ERR_TIMEOUT, stops, lets the MMA or copy in
+// flight land (a second, fixed bound), frees its tensor memory and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -49,7 +50,7 @@ __global__ void __launch_bounds__(kMlpThreads, kMlpCtasPerSm)
                const float *__restrict__ b1, const float *__restrict__ w2,
                const float *__restrict__ b2, const float *__restrict__ w3,
                const float *__restrict__ b3, float4 *__restrict__ F, long long P,
-               int32_t *status) {
+               int32_t *status, unsigned long long wait_ns) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                             ~(uintptr_t)1023);
@@ -118,7 +119,7 @@ __global__ void __launch_bounds__(kMlpThreads, kMlpCtasPerSm)
     const uint32_t xs = sbase + kSX + buf * 2048;
     // ---- layer 1
     if (tid == 0) {
-      if (!mbar_wait(buf ? bar_tma1 : bar_tma0, ph_tma[buf])) {
+      if (!mbar_wait(buf ? bar_tma1 : bar_tma0, ph_tma[buf], wait_ns)) {
         *s_abort = 1;
       } else {
         tma_pending = false;
@@ -138,7 +139,10 @@ __global__ void __launch_bounds__(kMlpThreads, kMlpCtasPerSm)
     }
     __syncthreads();
     if (*s_abort) break;
-    if (!mbar_wait(bar_mma, ph_mma)) *s_abort = 1;
+    if (!mbar_wait(bar_mma, ph_mma, wait_ns)) {  // stop, but let the MMA finish first
+      *s_abort = 1;
+      mbar_wait(bar_mma, ph_mma, kDrainNs);
+    }
     ph_mma ^= 1u;
     fence_after();
     const float flag = __bfloat162float(
@@ -167,7 +171,10 @@ __global__ void __launch_bounds__(kMlpThreads, kMlpCtasPerSm)
       mma_bf16(tmem + 32, dOnes, dW2[2], idesc_bf16(16), 1u);
       mma_commit(bar_mma);
     }
-    if (!mbar_wait(bar_mma, ph_mma)) *s_abort = 1;
+    if (!mbar_wait(bar_mma, ph_mma, wait_ns)) {  // stop, but let the MMA finish first
+      *s_abort = 1;
+      mbar_wait(bar_mma, ph_mma, kDrainNs);
+    }
     ph_mma ^= 1u;
     fence_after();
     {
@@ -193,7 +200,10 @@ __global__ void __launch_bounds__(kMlpThreads, kMlpCtasPerSm)
       mma_bf16(tmem + 48, dOnes, dW3[1], idesc_bf16(16), 1u);
       mma_commit(bar_mma);
     }
-    if (!mbar_wait(bar_mma, ph_mma)) *s_abort = 1;
+    if (!mbar_wait(bar_mma, ph_mma, wait_ns)) {  // stop, but let the MMA finish first
+      *s_abort = 1;
+      mbar_wait(bar_mma, ph_mma, kDrainNs);
+    }
     ph_mma ^= 1u;
     fence_after();
     {
@@ -218,7 +228,7 @@ __global__ void __launch_bounds__(kMlpThreads, kMlpCtasPerSm)
   }
   if (*s_abort && tid == 0) {
     raise_status(status, STAR_NT_ERR_TIMEOUT);
-    if (tma_pending) mbar_wait(pend_bar, pend_ph);  // let the copy land before exiting
+    if (tma_pending) mbar_wait(pend_bar, pend_ph, kDrainNs);  // let the copy land before exiting
   }
   fence_before();
   __syncthreads();
@@ -277,7 +287,7 @@ cudaError_t star_launch_mlp_bf16(const star_nt_mlp *w, const void *x, float *f, 
   if (grid > ntiles) grid = ntiles;
   k_mlp_bf16<<<(unsigned)grid, kMlpThreads, kSmemBytes, st>>>(map, w->w1, w->b1, w->w2, w->b2, w->w3,
                                                               w->b3, reinterpret_cast<float4 *>(f), P,
-                                                              d_status);
+                                                              d_status, wait_limit_ns());
   return cudaGetLastError();
 }
 

@@ -26,6 +26,7 @@ struct ResolveArgs {
   float bg0, bg1, bg2, kappa;
   float4 *out;
   uint32_t *out8;
+  unsigned long long wait_ns;  // bound of the MMA waits
 };
 
 // Static shared memory of the launch: the tile's staging area, reused for the
@@ -99,7 +100,7 @@ __device__ __forceinline__ void pass_resolve_body(const BinsView &bv, const uint
     }
     mma_commit(bar);
   }
-  mma_wait_cta(bar, ph, &fs.abort);
+  mma_wait_cta(bar, ph, &fs.abort, ra.wait_ns);
   ph ^= 1u;
   // eight columns (one K core column of H1) per tensor-memory load: the
   // register budget of the pass traversal leaves no room for wider loads
@@ -129,7 +130,7 @@ __device__ __forceinline__ void pass_resolve_body(const BinsView &bv, const uint
     }
     mma_commit(bar);
   }
-  if (!fs.abort) mma_wait_cta(bar, ph, &fs.abort);  // fs.abort is uniform after a barrier
+  if (!fs.abort) mma_wait_cta(bar, ph, &fs.abort, ra.wait_ns);  // fs.abort is uniform after a barrier
   ph ^= 1u;
 #pragma unroll
   for (int kc = 0; kc < 2; ++kc) {
@@ -155,7 +156,7 @@ __device__ __forceinline__ void pass_resolve_body(const BinsView &bv, const uint
     }
     mma_commit(bar);
   }
-  if (!fs.abort) mma_wait_cta(bar, ph, &fs.abort);  // fs.abort is uniform after a barrier
+  if (!fs.abort) mma_wait_cta(bar, ph, &fs.abort, ra.wait_ns);  // fs.abort is uniform after a barrier
   ph ^= 1u;
   // ---- composite, Eq. 4
   {
@@ -234,7 +235,7 @@ __device__ __forceinline__ void pass_resolve_body2(const BinsView &bv, const uin
     }
     mma_commit(bar);
   }
-  mma_wait_cta(bar, ph, &fs.abort);
+  mma_wait_cta(bar, ph, &fs.abort, ra.wait_ns);
   ph ^= 1u;
 #pragma unroll
   for (int t = 0; t < 2; ++t)
@@ -264,7 +265,7 @@ __device__ __forceinline__ void pass_resolve_body2(const BinsView &bv, const uin
     }
     mma_commit(bar);
   }
-  if (!fs.abort) mma_wait_cta(bar, ph, &fs.abort);  // fs.abort is uniform after a barrier
+  if (!fs.abort) mma_wait_cta(bar, ph, &fs.abort, ra.wait_ns);  // fs.abort is uniform after a barrier
   ph ^= 1u;
 #pragma unroll
   for (int t = 0; t < 2; ++t)
@@ -292,7 +293,7 @@ __device__ __forceinline__ void pass_resolve_body2(const BinsView &bv, const uin
     }
     mma_commit(bar);
   }
-  if (!fs.abort) mma_wait_cta(bar, ph, &fs.abort);  // fs.abort is uniform after a barrier
+  if (!fs.abort) mma_wait_cta(bar, ph, &fs.abort, ra.wait_ns);  // fs.abort is uniform after a barrier
   ph ^= 1u;
   // ---- composite, Eq. 4
 #pragma unroll
@@ -447,7 +448,8 @@ extern "C" star_nt_status star_nt_geometry_passes_resolve(
   BinsView v1 = bins_view(*b1), v2 = bins_view(*b2), v3 = bins_view(*b3);
   PassOut o1 = pass_out_of(l1);
   ResolveArgs ra = {w->w1, w->b1, w->w2, w->b2, w->w3, w->b3, params->bg[0], params->bg[1],
-                    params->bg[2], params->kappa_n, reinterpret_cast<float4 *>(rgba32f), rgba8};
+                    params->bg[2], params->kappa_n, reinterpret_cast<float4 *>(rgba32f), rgba8,
+                    wait_limit_ns()};
   uint32_t *queue = &v1.hd->queue;  // queue[0] work counter, queue[1] exit count
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);

@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
               const float *__restrict__ b1, const float *__restrict__ w2,
               const float *__restrict__ b2, const float *__restrict__ w3,
               const float *__restrict__ b3, float4 *__restrict__ out, uint32_t *__restrict__ out8,
-              int32_t *status) {
+              int32_t *status, unsigned long long wait_ns) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                             ~(uintptr_t)1023);
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
       }
       mma_commit(bar);
     }
-    mma_wait_cta(bar, ph, s_abort);
+    mma_wait_cta(bar, ph, s_abort, wait_ns);
     ph ^= 1u;
 #pragma unroll
     for (int t = 0; t < kRTiles; ++t) {
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
       }
       mma_commit(bar);
     }
-    mma_wait_cta(bar, ph, s_abort);
+    mma_wait_cta(bar, ph, s_abort, wait_ns);
     ph ^= 1u;
 #pragma unroll
     for (int t = 0; t < kRTiles; ++t) {
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
       }
       mma_commit(bar);
     }
-    mma_wait_cta(bar, ph, s_abort);
+    mma_wait_cta(bar, ph, s_abort, wait_ns);
     ph ^= 1u;
     // ---- composite, Eq. 4
 #pragma unroll
@@ -282,7 +282,8 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
                   const float *__restrict__ w1, const float *__restrict__ b1,
                   const float *__restrict__ w2, const float *__restrict__ b2,
                   const float *__restrict__ w3, const float *__restrict__ b3,
-                  float4 *__restrict__ out, uint32_t *__restrict__ out8, int32_t *status) {
+                  float4 *__restrict__ out, uint32_t *__restrict__ out8, int32_t *status,
+              unsigned long long wait_ns) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                             ~(uintptr_t)1023);
@@ -369,7 +370,7 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
       }
       mma_commit(bar);
     }
-    mma_wait_cta(bar, ph, s_abort);
+    mma_wait_cta(bar, ph, s_abort, wait_ns);
     ph ^= 1u;
 #pragma unroll
     for (int t = 0; t < kRTiles; ++t) {
@@ -403,7 +404,7 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
         mma_e4m3(tmem + 32 * t, smem_desc(sbase + kF8H1 + t * 6144, 2048, 128), dW2, idesc_e4m3(16), 0u);
       mma_commit(bar);
     }
-    mma_wait_cta(bar, ph, s_abort);
+    mma_wait_cta(bar, ph, s_abort, wait_ns);
     ph ^= 1u;
 #pragma unroll
     for (int t = 0; t < kRTiles; ++t) {
@@ -437,7 +438,7 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
       }
       mma_commit(bar);
     }
-    mma_wait_cta(bar, ph, s_abort);
+    mma_wait_cta(bar, ph, s_abort, wait_ns);
     ph ^= 1u;
     // ---- composite, Eq. 4
 #pragma unroll
@@ -516,7 +517,8 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
                     const float *__restrict__ w1, const float *__restrict__ b1,
                     const float *__restrict__ w2, const float *__restrict__ b2,
                     const float *__restrict__ w3, const float *__restrict__ b3,
-                    float4 *__restrict__ out, uint32_t *__restrict__ out8, int32_t *status) {
+                    float4 *__restrict__ out, uint32_t *__restrict__ out8, int32_t *status,
+              unsigned long long wait_ns) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                             ~(uintptr_t)1023);
@@ -637,7 +639,7 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
         mma_e4m3(tmem + 32 * t, smem_desc(sbase + kC8T + t * 8192, 2048, 128), dW1, idesc_e4m3(32), 0u);
       mma_commit(bar);
     }
-    mma_wait_cta(bar, ph, s_abort);
+    mma_wait_cta(bar, ph, s_abort, wait_ns);
     ph ^= 1u;
 #pragma unroll
     for (int t = 0; t < kRTiles; ++t) {
@@ -680,7 +682,7 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
       }
       mma_commit(bar);
     }
-    mma_wait_cta(bar, ph, s_abort);
+    mma_wait_cta(bar, ph, s_abort, wait_ns);
     ph ^= 1u;
 #pragma unroll
     for (int t = 0; t < kRTiles; ++t) {
@@ -719,7 +721,7 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
       }
       mma_commit(bar);
     }
-    mma_wait_cta(bar, ph, s_abort);
+    mma_wait_cta(bar, ph, s_abort, wait_ns);
     ph ^= 1u;
     // ---- composite, Eq. 4
 #pragma unroll
@@ -787,7 +789,7 @@ static star_nt_status launch_kernel(int kind, const In &in, const star_nt_params
   if (grid > rounds) grid = rounds;
   kern<<<(unsigned)grid, kRThreads, kQSmem, (cudaStream_t)stream>>>(
       in, params->bg[0], params->bg[1], params->bg[2], params->kappa_n, w->w1, w->b1, w->w2, w->b2,
-      w->w3, w->b3, reinterpret_cast<float4 *>(rgba32f), rgba8, d_status);
+      w->w3, w->b3, reinterpret_cast<float4 *>(rgba32f), rgba8, d_status, wait_limit_ns());
   return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
 }
 

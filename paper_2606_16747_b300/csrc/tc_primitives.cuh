@@ -8,7 +8,11 @@
 
 namespace star {
 
-constexpr unsigned long long kWaitNs = 1000000000ull;  // bound of every mbarrier wait
+// Waits for an MMA commit or a TMA copy are bounded by a limit given at
+// launch (star_nt_set_wait_limit, one second by default).  When one runs out
+// the kernel stops its work; before it frees tensor memory or exits it still
+// waits for the work it has in flight, under this second, fixed bound.
+constexpr unsigned long long kDrainNs = 1000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -35,21 +39,29 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t phase) {
   return ok != 0;
 }
 
-// bounded wait: false when the phase did not complete within kWaitNs
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
+// bounded wait: false when the phase did not complete within limit_ns
+// (limit 0: false at once, without polling)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, unsigned long long limit_ns) {
+  if (limit_ns == 0) return false;
   if (mbar_try(bar, phase)) return true;
   const unsigned long long t0 = globaltimer();
   while (!mbar_try(bar, phase))
-    if (globaltimer() - t0 > kWaitNs) return false;
+    if (globaltimer() - t0 > limit_ns) return false;
   return true;
 }
 
-// The CTA waits for an MMA commit: one thread polls the mbarrier (bounded;
-// sets *abort on expiry) while the others wait at the CTA barrier, which takes
+// The CTA waits for an MMA commit: one thread polls the mbarrier (bounded by
+// limit_ns; on expiry it sets *abort and then drains the commit under
+// kDrainNs, so that no MMA still writes tensor memory or reads the operands
+// when the CTA goes on) while the others wait at the CTA barrier, which takes
 // no issue slots; the tcgen05 fences order the MMA's tensor-memory writes
 // before every thread's following tensor-memory loads.
-__device__ __forceinline__ void mma_wait_cta(uint32_t bar, uint32_t phase, volatile int *abort) {
-  if (threadIdx.x == 0 && !mbar_wait(bar, phase)) *abort = 1;
+__device__ __forceinline__ void mma_wait_cta(uint32_t bar, uint32_t phase, volatile int *abort,
+                                             unsigned long long limit_ns) {
+  if (threadIdx.x == 0 && !mbar_wait(bar, phase, limit_ns)) {
+    *abort = 1;
+    mbar_wait(bar, phase, kDrainNs);
+  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");

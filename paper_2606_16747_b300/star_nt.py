@@ -30,7 +30,8 @@ EXPORTS = ("star_nt_version", "star_nt_status_string", "star_nt_default_params",
            "star_nt_resolve", "star_nt_geometry_passes", "star_nt_resolve_fp8", "star_nt_preload",
            "star_nt_unsorted_over", "star_nt_wboit", "star_nt_wmse_grad", "star_nt_leaf_plan_make",
            "star_nt_leaf_ws_bytes", "star_nt_geometry_passes_leaf", "star_nt_resolve_leaf",
-           "star_nt_geometry_passes_resolve", "star_nt_resolve_fp8x2")
+           "star_nt_geometry_passes_resolve", "star_nt_resolve_fp8x2", "star_nt_set_wait_limit",
+           "star_nt_wait_limit")
 
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
@@ -98,6 +99,7 @@ class PassState(ctypes.Structure):
 
 
 PASS_STATE_BYTES = ctypes.sizeof(PassState)
+
 
 _lib = None
 
@@ -169,9 +171,11 @@ def lib():
         L.star_nt_mlp_backward.argtypes = [ctypes.POINTER(Mlp), _P, _P, _I64, _P, _P, ctypes.c_size_t, _P]
         L.star_nt_adam.argtypes = [_P, _P, _P, _P, _I64, _I64, ctypes.c_float, ctypes.c_float,
                                    ctypes.c_float, ctypes.c_float, _P, _P]
+        L.star_nt_set_wait_limit.argtypes = [ctypes.c_uint64]
+        L.star_nt_wait_limit.restype = ctypes.c_uint64
         for name in EXPORTS:
             if name not in ("star_nt_default_params", "star_nt_status_string", "star_nt_version",
-                            "star_nt_train_ws_bytes"):
+                            "star_nt_train_ws_bytes", "star_nt_wait_limit"):
                 getattr(L, name).restype = _I32
         _lib = L
     return _lib
@@ -195,6 +199,16 @@ def _ptr(t):
 def _stream(stream=None):
     s = stream if stream is not None else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
+
+
+def set_wait_limit(ns: int):
+    """Bound, in nanoseconds, of the tensor-core kernels' waits (process-wide;
+    0 makes them run out at once)."""
+    _check("star_nt_set_wait_limit", lib().star_nt_set_wait_limit(int(ns)))
+
+
+def wait_limit() -> int:
+    return int(lib().star_nt_wait_limit())
 
 
 def default_params(**kw) -> Params:
@@ -492,3 +506,4 @@ def adam(params, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, bf
     _check("star_nt_adam", lib().star_nt_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), params.numel(),
                                               int(step), lr, beta1, beta2, eps, _ptr(bf16_rounded),
                                               _stream(stream)))
+

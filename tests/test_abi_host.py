@@ -47,6 +47,22 @@ def test_version_status_and_defaults(sn):
     assert p.tau_merge < p.tau_split
 
 
+def test_wait_limit(sn):
+    """The bound of the tensor-core waits: default one second, settable,
+    bounded above; rejected values leave it unchanged."""
+    assert sn.wait_limit() == 10 ** 9
+    L = sn.lib()
+    try:
+        sn.set_wait_limit(0)
+        assert sn.wait_limit() == 0
+        assert L.star_nt_set_wait_limit(60 * 10 ** 9 + 1) == sn.ERR_ARG
+        assert sn.wait_limit() == 0
+        sn.set_wait_limit(5 * 10 ** 8)
+        assert sn.wait_limit() == 5 * 10 ** 8
+    finally:
+        sn.set_wait_limit(10 ** 9)
+
+
 def test_workspace_sizes(sn):
     L = sn.lib()
     n = ctypes.c_size_t()
@@ -197,3 +213,4 @@ def test_resolve_entry_points_reject_bad_arguments(sn):
         assert L.star_nt_resolve_leaf(ctypes.byref(sc), ctypes.byref(plan), ctypes.byref(lay), 16,
                                       ctypes.byref(p), ctypes.byref(w), t, 32, None, None,
                                       None) == sn.ERR_ARG
+
