@@ -609,6 +609,129 @@ star_nt_status star_nt_adam(float *params, const float *grad, float *m, float *v
                             int64_t step, float lr, float beta1, float beta2, float eps,
                             float *bf16_rounded, void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* Context: the whole STAR-NT step of Fig. 1 through one call.               */
+/*                                                                           */
+/* A context belongs to one device.  It holds the method's parameters, the   */
+/* frame options below, the launch tuning of the persistent pass launches    */
+/* (star_nt_tuning; star_nt_tune chooses it on the caller's own workload),   */
+/* and a second stream with two events of its own.  The caller allocates one */
+/* device workspace of star_nt_workspace_size bytes for a frame size and a   */
+/* largest scene and binds it; it then holds every buffer the frame path     */
+/* keeps between frames (the three pass workspaces, the pass planes, the     */
+/* quadtree masks and state, the reprojection scratch), so a step needs no   */
+/* other buffer than its inputs and outputs and one captured CUDA graph      */
+/* replays every frame.  The library allocates no device memory; the context */
+/* itself is host memory plus a stream and two events, created by            */
+/* star_nt_create on the device and released by star_nt_destroy.  A context  */
+/* is not thread-safe: one thread at a time, one workspace, one frame size.  */
+
+typedef struct star_nt_ctx star_nt_ctx;
+
+/* Options of the frame path.  Defaults (star_nt_default_frame_options):
+ * mlp_type STAR_NT_BF16, merge scales 1 (a reduced pass is merged into pass
+ * 1 only at full size, as Eq. 2 sizes it), fuse_passes 1. */
+typedef struct {
+    int32_t mlp_type;     /* STAR_NT_BF16, STAR_NT_E4M3 or STAR_NT_E4M3X2 (the resolves' MLP) */
+    float merge_scale2;   /* star_nt_target.merge_scale of pass 2, in (0, 1] */
+    float merge_scale3;   /* ... of pass 3 */
+    int32_t fuse_passes;  /* BF16: with every pass at full size the pass launch
+                             produces the frame (star_nt_geometry_passes_resolve) */
+} star_nt_frame_options;
+void star_nt_default_frame_options(star_nt_frame_options *o);
+
+/* star_nt_create: a context on `device` with params (NULL: the defaults) and
+ * options (NULL: the defaults).  STAR_NT_ERR_ARG for an invalid device,
+ * parameters or options; STAR_NT_ERR_CUDA when no CUDA device is usable.
+ * star_nt_destroy waits for the context's side stream and releases it. */
+star_nt_status star_nt_create(int32_t device, const star_nt_params *params,
+                              const star_nt_frame_options *options, star_nt_ctx **out);
+star_nt_status star_nt_destroy(star_nt_ctx *ctx);
+
+/* Bytes of the device workspace of frames of W x H pixels with up to T
+ * triangles (W, H <= 16384).  Each pass workspace holds max(2^20, 96 T)
+ * (triangle, tile) pairs; a scene that needs more raises
+ * STAR_NT_ERR_CAPACITY in the frame's status word. */
+star_nt_status star_nt_workspace_size(const star_nt_ctx *ctx, int32_t W, int32_t H, int32_t T,
+                                      size_t *bytes);
+
+/* Binds a workspace (256-byte aligned, at least star_nt_workspace_size
+ * bytes) to the context for frames of W x H and up to T triangles, and
+ * enqueues its initialisation on `stream`: the first frame runs every pass
+ * at full size, every quadtree leaf at level 0.  Binding again starts a new
+ * sequence. */
+star_nt_status star_nt_bind_workspace(star_nt_ctx *ctx, int32_t W, int32_t H, int32_t T, void *ws,
+                                      size_t ws_bytes, void *stream);
+
+/* Cameras of one step (device memory).  vp: float32[16] view-projection of
+ * the real frame (as star_nt_target.view_proj); vp64: the same camera in
+ * float64 (the reprojection's source camera); vp64_interp: float64[16]
+ * camera of the interpolated frame, or NULL for a step without one. */
+typedef struct {
+    const float *vp;
+    const double *vp64;
+    const double *vp64_interp;
+} star_nt_cameras;
+
+/* Outputs of one step: the real frame (both required: the reprojection and
+ * the quadtree read them) and the interpolated frame (either or both when
+ * vp64_interp is given), layouts as star_nt_resolve and star_nt_reproject. */
+typedef struct {
+    float *rgba32f;
+    uint32_t *rgba8;
+    float *interp_rgba32f;
+    uint32_t *interp_rgba8;
+} star_nt_frame_out;
+
+/* star_nt_frame: one STAR-NT step (Fig. 1) on `stream`: the real frame
+ * (star_nt_raster_passes of pass 1 at W x H and of passes 2 and 3 at the
+ * sizes the quadtree chose on the previous frame; the pass launch; the
+ * resolve: upscale, network, composite), then the interpolated frame
+ * reprojected from it (star_nt_reproject, on the context's side stream,
+ * forked from and joined back to `stream`) beside the quadtree update of
+ * Sec. 3.1-3.2 that sets the next frame's pass sizes.  The call enqueues
+ * only; the step is complete when `stream` reaches its end.  It can be
+ * captured into a CUDA graph on `stream` (fixed addresses, the fork and join
+ * through the context's events).  Device-side conditions go to d_status. */
+star_nt_status star_nt_frame(star_nt_ctx *ctx, const star_nt_scene *scene, const star_nt_mlp *w,
+                             const star_nt_cameras *cams, const star_nt_frame_out *out,
+                             int32_t *d_status, void *stream);
+
+/* star_nt_tune: chooses the context's launch tuning on its current frame
+ * state (call it after a few frames, so that the quadtree's pass sizes are
+ * representative): every candidate tile shape and residency of the
+ * persistent pass launch is timed with CUDA events over ten pass launches,
+ * the fastest kept; then, with BF16 and fuse_passes, the raster, pass launch
+ * and resolve are timed with the pass launch producing the frame and with
+ * the separate resolve, and the faster kept.  Synchronises `stream` (not
+ * allowed inside a capture: STAR_NT_ERR_ARG); writes the outputs of frames
+ * it renders; leaves the quadtree state unchanged.  report may be NULL. */
+#define STAR_NT_TUNE_CANDIDATES 9
+typedef struct {
+    star_nt_tuning candidates[STAR_NT_TUNE_CANDIDATES];
+    float passes_ms[STAR_NT_TUNE_CANDIDATES];  /* mean ms of one pass launch */
+    float frame_ms[2];                         /* raster + passes + resolve: [0] separate resolve,
+                                                  [1] the pass launch produces the frame */
+    star_nt_tuning chosen;
+    int32_t fuse_passes;
+} star_nt_tune_report;
+star_nt_status star_nt_tune(star_nt_ctx *ctx, const star_nt_scene *scene, const star_nt_mlp *w,
+                            const star_nt_cameras *cams, const star_nt_frame_out *out,
+                            int32_t *d_status, void *stream, star_nt_tune_report *report);
+
+/* The context's tuning (either pointer may be NULL), and setting it by hand
+ * (STAR_NT_ERR_ARG for a tuning star_nt_geometry_passes rejects). */
+star_nt_status star_nt_ctx_tuning(const star_nt_ctx *ctx, star_nt_tuning *tuning,
+                                  int32_t *fuse_passes);
+star_nt_status star_nt_ctx_set_tuning(star_nt_ctx *ctx, const star_nt_tuning *tuning,
+                                      int32_t fuse_passes);
+
+/* Device addresses, inside the bound workspace, of the pass state the
+ * quadtree leaves for the next frame, the quadtree masks, and the real
+ * frame's nearest-layer ids and depths (any pointer may be NULL). */
+star_nt_status star_nt_ctx_pass_state(const star_nt_ctx *ctx, star_nt_pass_state **state,
+                                      uint32_t **masks, int32_t **id1, float **z1);
+
 #ifdef __cplusplus
 }
 #endif

@@ -31,7 +31,9 @@ EXPORTS = ("star_nt_version", "star_nt_status_string", "star_nt_default_params",
            "star_nt_unsorted_over", "star_nt_wboit", "star_nt_wmse_grad", "star_nt_leaf_plan_make",
            "star_nt_leaf_ws_bytes", "star_nt_geometry_passes_leaf", "star_nt_resolve_leaf",
            "star_nt_geometry_passes_resolve", "star_nt_resolve_fp8x2", "star_nt_set_wait_limit",
-           "star_nt_wait_limit")
+           "star_nt_wait_limit", "star_nt_default_frame_options", "star_nt_create", "star_nt_destroy",
+           "star_nt_workspace_size", "star_nt_bind_workspace", "star_nt_frame", "star_nt_tune",
+           "star_nt_ctx_tuning", "star_nt_ctx_set_tuning", "star_nt_ctx_pass_state")
 
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
@@ -100,6 +102,26 @@ class PassState(ctypes.Structure):
 
 PASS_STATE_BYTES = ctypes.sizeof(PassState)
 
+
+class FrameOptions(ctypes.Structure):
+    _fields_ = [("mlp_type", _I32), ("merge_scale2", ctypes.c_float), ("merge_scale3", ctypes.c_float),
+                ("fuse_passes", _I32)]
+
+
+class Cameras(ctypes.Structure):
+    _fields_ = [("vp", _P), ("vp64", _P), ("vp64_interp", _P)]
+
+
+class FrameOut(ctypes.Structure):
+    _fields_ = [("rgba32f", _P), ("rgba8", _P), ("interp_rgba32f", _P), ("interp_rgba8", _P)]
+
+
+TUNE_CANDIDATES = 9
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [("candidates", Tuning * TUNE_CANDIDATES), ("passes_ms", ctypes.c_float * TUNE_CANDIDATES),
+                ("frame_ms", ctypes.c_float * 2), ("chosen", Tuning), ("fuse_passes", _I32)]
 
 _lib = None
 
@@ -171,11 +193,26 @@ def lib():
         L.star_nt_mlp_backward.argtypes = [ctypes.POINTER(Mlp), _P, _P, _I64, _P, _P, ctypes.c_size_t, _P]
         L.star_nt_adam.argtypes = [_P, _P, _P, _P, _I64, _I64, ctypes.c_float, ctypes.c_float,
                                    ctypes.c_float, ctypes.c_float, _P, _P]
+        L.star_nt_default_frame_options.argtypes = [ctypes.POINTER(FrameOptions)]
+        L.star_nt_default_frame_options.restype = None
+        L.star_nt_create.argtypes = [_I32, ctypes.POINTER(Params), ctypes.POINTER(FrameOptions),
+                                     ctypes.POINTER(_P)]
+        L.star_nt_destroy.argtypes = [_P]
+        L.star_nt_workspace_size.argtypes = [_P, _I32, _I32, _I32, ctypes.POINTER(ctypes.c_size_t)]
+        L.star_nt_bind_workspace.argtypes = [_P, _I32, _I32, _I32, _P, ctypes.c_size_t, _P]
+        L.star_nt_frame.argtypes = [_P, ctypes.POINTER(Scene), ctypes.POINTER(Mlp), ctypes.POINTER(Cameras),
+                                    ctypes.POINTER(FrameOut), _P, _P]
+        L.star_nt_tune.argtypes = L.star_nt_frame.argtypes + [ctypes.POINTER(TuneReport)]
+        L.star_nt_ctx_tuning.argtypes = [_P, ctypes.POINTER(Tuning), ctypes.POINTER(_I32)]
+        L.star_nt_ctx_set_tuning.argtypes = [_P, ctypes.POINTER(Tuning), _I32]
+        L.star_nt_ctx_pass_state.argtypes = [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                             ctypes.POINTER(_P)]
         L.star_nt_set_wait_limit.argtypes = [ctypes.c_uint64]
         L.star_nt_wait_limit.restype = ctypes.c_uint64
         for name in EXPORTS:
             if name not in ("star_nt_default_params", "star_nt_status_string", "star_nt_version",
-                            "star_nt_train_ws_bytes", "star_nt_wait_limit"):
+                            "star_nt_train_ws_bytes", "star_nt_wait_limit",
+                            "star_nt_default_frame_options"):
                 getattr(L, name).restype = _I32
         _lib = L
     return _lib
@@ -507,3 +544,95 @@ def adam(params, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, bf
                                               int(step), lr, beta1, beta2, eps, _ptr(bf16_rounded),
                                               _stream(stream)))
 
+
+# ---------------------------------------------------------------------------
+# context: the whole step through star_nt_frame
+
+class Context:
+    """A star_nt_ctx on one device: create, bind one workspace (a torch
+    allocation of star_nt_workspace_size bytes), then one call per step
+    (real frame, interpolated frame, quadtree update); star_nt_tune chooses
+    the launch tuning on the workload."""
+
+    def __init__(self, device=None, params: Params = None, mlp_type=BF16, merge_scale2=1.0, merge_scale3=1.0,
+                 fuse_passes=True):
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        opt = FrameOptions()
+        lib().star_nt_default_frame_options(ctypes.byref(opt))
+        opt.mlp_type, opt.merge_scale2, opt.merge_scale3 = int(mlp_type), float(merge_scale2), float(merge_scale3)
+        opt.fuse_passes = 1 if fuse_passes else 0
+        self.params = params if params is not None else default_params()
+        h = _P()
+        _check("star_nt_create", lib().star_nt_create(self.device, ctypes.byref(self.params), ctypes.byref(opt),
+                                                      ctypes.byref(h)))
+        self.h = h
+        self.ws = None
+
+    def workspace_size(self, W, H, T) -> int:
+        n = ctypes.c_size_t()
+        _check("star_nt_workspace_size", lib().star_nt_workspace_size(self.h, W, H, T, ctypes.byref(n)))
+        return n.value
+
+    def bind(self, W, H, T, stream=None):
+        n = self.workspace_size(W, H, T)
+        self.ws = torch.empty(n, dtype=torch.uint8, device=f"cuda:{self.device}")
+        _check("star_nt_bind_workspace", lib().star_nt_bind_workspace(self.h, W, H, T, self.ws.data_ptr(), n,
+                                                                      _stream(stream)))
+        self.W, self.H, self.T = W, H, T
+
+    @staticmethod
+    def _args(cams, out):
+        c = Cameras(*[t.data_ptr() if t is not None else None for t in cams])
+        o = FrameOut(*[t.data_ptr() if t is not None else None for t in out])
+        return c, o
+
+    def frame(self, scene: Scene, w: Mlp, vp, vp64, vp64_interp, rgba32f, rgba8, interp_rgba32f=None,
+              interp_rgba8=None, status=None, stream=None):
+        c, o = self._args((vp, vp64, vp64_interp), (rgba32f, rgba8, interp_rgba32f, interp_rgba8))
+        _check("star_nt_frame", lib().star_nt_frame(self.h, ctypes.byref(scene), ctypes.byref(w), ctypes.byref(c),
+                                                    ctypes.byref(o), _ptr(status), _stream(stream)))
+
+    def tune(self, scene: Scene, w: Mlp, vp, vp64, rgba32f, rgba8, status=None, stream=None) -> dict:
+        c, o = self._args((vp, vp64, None), (rgba32f, rgba8, None, None))
+        r = TuneReport()
+        _check("star_nt_tune", lib().star_nt_tune(self.h, ctypes.byref(scene), ctypes.byref(w), ctypes.byref(c),
+                                                  ctypes.byref(o), _ptr(status), _stream(stream), ctypes.byref(r)))
+        key = lambda t: f"{t.block_w}x{32 // t.block_w}/{t.ctas_per_sm}/{t.pixels_per_thread}px"
+        return {"block_w": r.chosen.block_w, "ctas_per_sm": r.chosen.ctas_per_sm,
+                "pixels_per_thread": r.chosen.pixels_per_thread, "fuse_passes": bool(r.fuse_passes),
+                "ms": {key(r.candidates[k]): r.passes_ms[k] for k in range(TUNE_CANDIDATES)},
+                "raster_passes_resolve_ms": {"pass launch resolves": r.frame_ms[1], "separate resolve": r.frame_ms[0]}}
+
+    def tuning(self):
+        t, f = Tuning(), _I32()
+        _check("star_nt_ctx_tuning", lib().star_nt_ctx_tuning(self.h, ctypes.byref(t), ctypes.byref(f)))
+        return (t.block_w, t.ctas_per_sm, t.pixels_per_thread), bool(f.value)
+
+    def set_tuning(self, tuning, fuse_passes=True):
+        t = Tuning(*tuning)
+        _check("star_nt_ctx_set_tuning", lib().star_nt_ctx_set_tuning(self.h, ctypes.byref(t), 1 if fuse_passes else 0))
+
+    def views(self) -> dict:
+        """The pass state, masks and nearest-layer planes inside the bound
+        workspace, as tensors viewing it."""
+        st, m, i1, z = _P(), _P(), _P(), _P()
+        _check("star_nt_ctx_pass_state", lib().star_nt_ctx_pass_state(self.h, ctypes.byref(st), ctypes.byref(m),
+                                                                      ctypes.byref(i1), ctypes.byref(z)))
+        base = self.ws.data_ptr()
+        P = self.W * self.H
+        B = self.params.base_tile
+        nt = ((self.W + B - 1) // B) * ((self.H + B - 1) // B)
+        at = lambda p, n: self.ws[p.value - base:p.value - base + n]
+        return {"state": at(st, PASS_STATE_BYTES), "masks": at(m, 4 * nt).view(torch.int32),
+                "id1": at(i1, 4 * P).view(torch.int32), "z1": at(z, 4 * P).view(torch.float32)}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().star_nt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

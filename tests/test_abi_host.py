@@ -214,3 +214,29 @@ def test_resolve_entry_points_reject_bad_arguments(sn):
                                       ctypes.byref(p), ctypes.byref(w), t, 32, None, None,
                                       None) == sn.ERR_ARG
 
+
+def test_context_calls_reject_bad_arguments(sn):
+    """The context calls check their arguments on the host; without a CUDA
+    device star_nt_create reports STAR_NT_ERR_CUDA and allocates nothing."""
+    import torch
+    L = sn.lib()
+    h = ctypes.c_void_p()
+    assert L.star_nt_create(0, None, None, None) == sn.ERR_ARG
+    bad = sn.FrameOptions(7, 1.0, 1.0, 1)
+    assert L.star_nt_create(0, None, ctypes.byref(bad), ctypes.byref(h)) == sn.ERR_ARG
+    bad = sn.FrameOptions(sn.BF16, 0.0, 1.0, 1)
+    assert L.star_nt_create(0, None, ctypes.byref(bad), ctypes.byref(h)) == sn.ERR_ARG
+    p = sn.default_params(base_tile=32)
+    assert L.star_nt_create(0, ctypes.byref(p), None, ctypes.byref(h)) == sn.ERR_ARG
+    if not torch.cuda.is_available():
+        assert L.star_nt_create(0, None, None, ctypes.byref(h)) == sn.ERR_CUDA and not h.value
+    n = ctypes.c_size_t()
+    assert L.star_nt_destroy(None) == sn.ERR_ARG
+    assert L.star_nt_workspace_size(None, 64, 64, 10, ctypes.byref(n)) == sn.ERR_ARG
+    assert L.star_nt_bind_workspace(None, 64, 64, 10, 256, 1 << 20, None) == sn.ERR_ARG
+    assert L.star_nt_frame(None, None, None, None, None, None, None) == sn.ERR_ARG
+    assert L.star_nt_tune(None, None, None, None, None, None, None, None) == sn.ERR_ARG
+    assert L.star_nt_ctx_tuning(None, None, None) == sn.ERR_ARG
+    o = sn.FrameOptions()
+    L.star_nt_default_frame_options(ctypes.byref(o))
+    assert (o.mlp_type, o.merge_scale2, o.merge_scale3, o.fuse_passes) == (sn.BF16, 1.0, 1.0, 1)
