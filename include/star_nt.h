@@ -358,6 +358,23 @@ star_nt_status star_nt_resolve_fp8x2(const star_nt_scene *scene, const star_nt_b
                                      const star_nt_mlp *w, float *rgba32f, uint32_t *rgba8,
                                      int32_t *d_status, void *stream);
 
+/* star_nt_resolve_mlp -- star_nt_resolve with the MLP operand type chosen by  */
+/* mlp_type: STAR_NT_BF16 (star_nt_resolve), STAR_NT_E4M3 (star_nt_resolve_fp8: */
+/* per-row scales), STAR_NT_E4M3X2 (star_nt_resolve_fp8x2), or the per-tensor  */
+/* scaled FP8 variants STAR_NT_E4M3_TENSOR and STAR_NT_E4M3X2_TENSOR: one       */
+/* power-of-two scale per weight tensor (its largest |w| at most 448, the e4m3 */
+/* maximum) and one per activation tensor, fixed for the launch by interval    */
+/* bounds through the network from the input box (x0 = kappa_n N with N <=    */
+/* 448 fragments, the other features <= 1), so no activation saturates; each  */
+/* accumulator is rescaled by one exact factor per tensor.  Other arguments   */
+/* and errors as star_nt_resolve; STAR_NT_ERR_ARG for another mlp_type.       */
+star_nt_status star_nt_resolve_mlp(const star_nt_scene *scene, const star_nt_bins *bins2,
+                                   const star_nt_bins *bins3, const star_nt_layers *layers1,
+                                   const star_nt_layers *layers2, const star_nt_layers *layers3,
+                                   int32_t W, int32_t H, const star_nt_params *params,
+                                   const star_nt_mlp *w, int32_t mlp_type, float *rgba32f,
+                                   uint32_t *rgba8, int32_t *d_status, void *stream);
+
 /* star_nt_geometry_passes_resolve: star_nt_geometry_passes that, when both
  * reduced passes are merged into pass 1 (their bins marked merged: every pass
  * at the full resolution), also produces the frame: pass 1's tiles run the
@@ -473,6 +490,8 @@ star_nt_status star_nt_quadtree_static(const uint32_t *rgba8, const int32_t *id1
 
 #define STAR_NT_E4M3 2   /* MLP operand type of star_nt_resolve_leaf: FP8 e4m3 */
 #define STAR_NT_E4M3X2 3 /* ... compensated FP8: e4m3 pairs (star_nt_resolve_fp8x2) */
+#define STAR_NT_E4M3_TENSOR 4   /* ... e4m3 with per-tensor scales (star_nt_resolve_mlp) */
+#define STAR_NT_E4M3X2_TENSOR 5 /* ... compensated e4m3 with per-tensor scales */
 #define STAR_NT_LEAF_MAX_TARGETS 9
 
 typedef struct {
@@ -515,9 +534,7 @@ star_nt_status star_nt_geometry_passes_leaf(const star_nt_scene *scene,
 
 /* star_nt_resolve_leaf: star_nt_resolve with each pixel's pass-2 and pass-3
  * planes taken from the targets of its leaf level (layers and masks as in
- * star_nt_geometry_passes_leaf).  mlp_type: STAR_NT_BF16 (star_nt_resolve's
- * MLP), STAR_NT_E4M3 (star_nt_resolve_fp8's) or STAR_NT_E4M3X2
- * (star_nt_resolve_fp8x2's).  Primitive ids read from the
+ * star_nt_geometry_passes_leaf).  mlp_type: as star_nt_resolve_mlp.  Primitive ids read from the
  * planes are bounds-checked against scene->n_tris. */
 star_nt_status star_nt_resolve_leaf(const star_nt_scene *scene, const star_nt_leaf_plan *plan,
                                     const star_nt_layers *layers, const uint32_t *masks,
@@ -632,7 +649,7 @@ typedef struct star_nt_ctx star_nt_ctx;
  * mlp_type STAR_NT_BF16, merge scales 1 (a reduced pass is merged into pass
  * 1 only at full size, as Eq. 2 sizes it), fuse_passes 1. */
 typedef struct {
-    int32_t mlp_type;     /* STAR_NT_BF16, STAR_NT_E4M3 or STAR_NT_E4M3X2 (the resolves' MLP) */
+    int32_t mlp_type;     /* the resolve's MLP operand type, as star_nt_resolve_mlp */
     float merge_scale2;   /* star_nt_target.merge_scale of pass 2, in (0, 1] */
     float merge_scale3;   /* ... of pass 3 */
     int32_t fuse_passes;  /* BF16: with every pass at full size the pass launch

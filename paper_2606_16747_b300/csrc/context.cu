@@ -158,7 +158,9 @@ extern "C" void star_nt_default_frame_options(star_nt_frame_options *o) {
 }
 
 static bool options_valid(const star_nt_frame_options &o) {
-  if (o.mlp_type != STAR_NT_BF16 && o.mlp_type != STAR_NT_E4M3 && o.mlp_type != STAR_NT_E4M3X2) return false;
+  if (o.mlp_type != STAR_NT_BF16 && o.mlp_type != STAR_NT_E4M3 && o.mlp_type != STAR_NT_E4M3X2 &&
+      o.mlp_type != STAR_NT_E4M3_TENSOR && o.mlp_type != STAR_NT_E4M3X2_TENSOR)
+    return false;
   return o.merge_scale2 > 0.0f && o.merge_scale2 <= 1.0f && o.merge_scale3 > 0.0f && o.merge_scale3 <= 1.0f;
 }
 
@@ -295,13 +297,9 @@ static star_nt_status real_frame(const star_nt_ctx *c, const CtxViews &v, const 
                                   &c->tuning, d_status, st);
     if (s != STAR_NT_OK) return s;
   }
-  if (resolve) {
-    auto res = c->opt.mlp_type == STAR_NT_E4M3X2 ? star_nt_resolve_fp8x2
-               : c->opt.mlp_type == STAR_NT_E4M3 ? star_nt_resolve_fp8
-                                                 : star_nt_resolve;
-    s = res(scene, &v.bins[1], &v.bins[2], &v.l1, &v.l2, &v.l3, c->W, c->H, &c->params, w, rgba32f, rgba8,
-            d_status, st);
-  }
+  if (resolve)
+    s = star_nt_resolve_mlp(scene, &v.bins[1], &v.bins[2], &v.l1, &v.l2, &v.l3, c->W, c->H, &c->params, w,
+                            c->opt.mlp_type, rgba32f, rgba8, d_status, st);
   return s;
 }
 

@@ -254,7 +254,8 @@ constexpr uint32_t kF8W3 = 15872;     // N=16, K=32 (3 rows, K 16 used): 2 x 256
 constexpr uint32_t kF8B = 16384;      // b1[32], b2[16], b3[16]
 constexpr uint32_t kF8S = 16640;      // inverse weight-row scales: 1/s1[32], 1/s2[16], 1/s3[16]
 constexpr uint32_t kF8Bar = 16896;    // mma barrier, tmem slot, abort flag
-constexpr uint32_t kF8Used = 16912;
+constexpr uint32_t kF8T = 16912;      // per-tensor scales (X, H1, H2, W1, W2, W3) and their scratch
+constexpr uint32_t kF8Used = 17200;
 
 // power of two s with max |v| * s <= 448 (1 when max is 0)
 __device__ __forceinline__ float row_scale(float mx) {
@@ -265,18 +266,86 @@ __device__ __forceinline__ float row_scale(float mx) {
   return ldexpf(1.0f, k);
 }
 
+// Per-tensor scaling: one power-of-two scale per weight tensor (its largest
+// |w| mapped to at most 448, the e4m3 maximum) and one per activation tensor,
+// fixed for the launch by interval bounds through the network: the input
+// box x0 <= kappa 448 (448 fragments), the other features <= 1; then
+// |h1_j| <= sum_k |W1_jk| xmax_k + |b1_j| and |h2_j| <= sum_k |W2_jk| h1max_k
+// + |b2_j|.  No activation can saturate, and each tensor shares one exact
+// rescale in the epilogue.  Written to sc[0..5] = scales of X, H1, H2, W1,
+// W2, W3 by the CTA of 128 threads (all call; sc[8..68) is scratch).
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ void tensor_scales(const float *__restrict__ w1, const float *__restrict__ b1,
+                              const float *__restrict__ w2, const float *__restrict__ b2,
+                              const float *__restrict__ w3, float kappa, float *sc) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;  // 4 warps
+  const float x0max = fmaxf(kappa * 448.0f, 1.0f);
+  // largest |w| of each weight tensor: strided over the CTA, then per warp
+  float a1 = 0.f, a2 = 0.f, a3 = 0.f;
+  for (int i = tid; i < 32 * 5; i += blockDim.x) a1 = fmaxf(a1, fabsf(w1[i]));
+  for (int i = tid; i < 16 * 32; i += blockDim.x) a2 = fmaxf(a2, fabsf(w2[i]));
+  for (int i = tid; i < 3 * 16; i += blockDim.x) a3 = fmaxf(a3, fabsf(w3[i]));
+  a1 = warp_max(a1);
+  a2 = warp_max(a2);
+  a3 = warp_max(a3);
+  if (lane == 0) {
+    sc[56 + warp] = a1;
+    sc[60 + warp] = a2;
+    sc[64 + warp] = a3;
+  }
+  // bound of each hidden unit of layer 1 (warp 0, one unit per lane)
+  if (warp == 0) {
+    float h = fabsf(b1[lane]);
+    for (int k = 0; k < 5; ++k) h = fmaf(fabsf(w1[lane * 5 + k]), k == 0 ? x0max : 1.0f, h);
+    sc[8 + lane] = h;
+  }
+  __syncthreads();
+  // layer 2 (warp 0, lanes 0..15), then the maxima
+  if (warp == 0) {
+    float h = 0.f;
+    if (lane < 16) {
+      h = fabsf(b2[lane]);
+      for (int k = 0; k < 32; ++k) h = fmaf(fabsf(w2[lane * 32 + k]), sc[8 + k], h);
+    }
+    const float m2 = warp_max(h);
+    const float m1 = warp_max(sc[8 + lane]);
+    if (lane == 0) {
+      float t1 = 0.f, t2 = 0.f, t3 = 0.f;
+      for (int k = 0; k < 4; ++k) {
+        t1 = fmaxf(t1, sc[56 + k]);
+        t2 = fmaxf(t2, sc[60 + k]);
+        t3 = fmaxf(t3, sc[64 + k]);
+      }
+      sc[0] = row_scale(x0max);
+      sc[1] = row_scale(m1);
+      sc[2] = row_scale(m2);
+      sc[3] = row_scale(t1);
+      sc[4] = row_scale(t2);
+      sc[5] = row_scale(t3);
+    }
+  }
+  __syncthreads();
+}
+
 // row n of a [rows][cols] weight matrix into an e4m3 B operand (row scale
 // s = row_scale(max |w_n.|), stored as 1/s in inv)
 __device__ __forceinline__ void put_row8(uint8_t *base, int lbo, const float *w, int n, int cols,
-                                         float *inv) {
+                                         float *inv, float fixed = 0.0f) {
   float mx = 0.0f;
-  for (int k = 0; k < cols; ++k) mx = fmaxf(mx, fabsf(w[n * cols + k]));
-  const float sc = row_scale(mx);
+  if (!(fixed > 0.0f))
+    for (int k = 0; k < cols; ++k) mx = fmaxf(mx, fabsf(w[n * cols + k]));
+  const float sc = fixed > 0.0f ? fixed : row_scale(mx);
   for (int k = 0; k < cols; ++k) put_w8(base, n, k, lbo, w[n * cols + k] * sc);
   inv[n] = 1.0f / sc;  // exact: a power of two
 }
 
-template <class In>
+// TENSOR: per-tensor scales (tensor_scales) instead of per-row ones.
+template <class In, bool TENSOR>
 __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
     k_resolve_fp8(In in, float bg0, float bg1, float bg2, float kappa,
                   const float *__restrict__ w1, const float *__restrict__ b1,
@@ -295,14 +364,17 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
   float *sb = reinterpret_cast<float *>(sm + kF8B);
   if (in.rejected()) return;  // a rejected pass, or the frame is already done
 
-  // weights: e4m3 rows with power-of-two row scales, zero padded; biases fp32
+  // weights: e4m3 rows with power-of-two row (or tensor) scales, zero
+  // padded; biases fp32
   float *si = reinterpret_cast<float *>(sm + kF8S);
+  float *ts = reinterpret_cast<float *>(sm + kF8T);
   for (int i = tid; i < (int)(kF8B - kF8Z) / 4; i += kRThreads)
     reinterpret_cast<uint32_t *>(sm + kF8Z)[i] = 0u;
   __syncthreads();
-  if (tid < 32) put_row8(sm + kF8W1, 512, w1, tid, 5, si);
-  else if (tid < 48) put_row8(sm + kF8W2, 256, w2, tid - 32, 32, si + 32);
-  else if (tid < 51) put_row8(sm + kF8W3, 256, w3, tid - 48, 16, si + 48);
+  if (TENSOR) tensor_scales(w1, b1, w2, b2, w3, kappa, ts);
+  if (tid < 32) put_row8(sm + kF8W1, 512, w1, tid, 5, si, TENSOR ? ts[3] : 0.0f);
+  else if (tid < 48) put_row8(sm + kF8W2, 256, w2, tid - 32, 32, si + 32, TENSOR ? ts[4] : 0.0f);
+  else if (tid < 51) put_row8(sm + kF8W3, 256, w3, tid - 48, 16, si + 48, TENSOR ? ts[5] : 0.0f);
   else if (tid < 64) si[tid] = 0.0f;
   if (tid < 32) sb[tid] = b1[tid];
   if (tid < 16) sb[32 + tid] = b2[tid];
@@ -349,10 +421,14 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
         pixel_features(in, bg0, bg1, bg2, kappa, x, y, xv, front[t]);
       }
       flag[t] = xv[5] != 0.0f;
-      float mx = 0.0f;
+      if (TENSOR) {
+        sx[t] = ts[0];
+      } else {
+        float mx = 0.0f;
 #pragma unroll
-      for (int k = 0; k < 5; ++k) mx = fmaxf(mx, fabsf(xv[k]));
-      sx[t] = row_scale(mx);
+        for (int k = 0; k < 5; ++k) mx = fmaxf(mx, fabsf(xv[k]));
+        sx[t] = row_scale(mx);
+      }
       const uint32_t q0 = pack4_e4m3(xv[0] * sx[t], xv[1] * sx[t], xv[2] * sx[t], xv[3] * sx[t]);
       const uint32_t q1 = pack4_e4m3(xv[4] * sx[t], 0.f, 0.f, 0.f);
       *reinterpret_cast<uint4 *>(sm + kF8X + t * 6144 + row * 16) = make_uint4(q0, q1, 0u, 0u);
@@ -383,7 +459,7 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
         d[j] = fmaxf(fmaf(d[j], k1 * si[j], sb[j]), 0.0f);
         mx = fmaxf(mx, d[j]);
       }
-      sh[t] = row_scale(mx);
+      sh[t] = TENSOR ? ts[1] : row_scale(mx);
       uint32_t pk[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j)
@@ -417,7 +493,7 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
         d[j] = fmaxf(fmaf(d[j], k2 * si[32 + j], sb[32 + j]), 0.0f);
         mx = fmaxf(mx, d[j]);
       }
-      sh[t] = row_scale(mx);
+      sh[t] = TENSOR ? ts[2] : row_scale(mx);
       uint32_t pk[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j)
@@ -495,7 +571,8 @@ constexpr uint32_t kC8W3 = 18432;  // [hi | hi], then [lo | lo]: N=16, K=32: 2 x
 constexpr uint32_t kC8B = 19456;   // b1[32], b2[16], b3[16]
 constexpr uint32_t kC8S = 19712;   // inverse weight-row scales: 1/s1[32], 1/s2[16], 1/s3[16]
 constexpr uint32_t kC8Bar = 19968; // mma barrier, tmem slot, abort flag
-constexpr uint32_t kC8Used = 19984;
+constexpr uint32_t kC8TS = 19984;  // per-tensor scales (X, H1, H2, W1, W2, W3) and their scratch
+constexpr uint32_t kC8Used = 20272;
 
 // one e4m3 byte into the K-major core-matrix layout of a B operand
 __device__ __forceinline__ void put_b8(uint8_t *base, int n, int k, int lbo, uint8_t q) {
@@ -503,15 +580,17 @@ __device__ __forceinline__ void put_b8(uint8_t *base, int n, int k, int lbo, uin
 }
 
 // the row scale of row n of a [rows][cols] weight matrix (1/s stored in inv)
-__device__ __forceinline__ float weight_row_scale(const float *w, int n, int cols, float *inv) {
+__device__ __forceinline__ float weight_row_scale(const float *w, int n, int cols, float *inv,
+                                                 float fixed = 0.0f) {
   float mx = 0.0f;
-  for (int k = 0; k < cols; ++k) mx = fmaxf(mx, fabsf(w[n * cols + k]));
-  const float sc = row_scale(mx);
+  if (!(fixed > 0.0f))
+    for (int k = 0; k < cols; ++k) mx = fmaxf(mx, fabsf(w[n * cols + k]));
+  const float sc = fixed > 0.0f ? fixed : row_scale(mx);
   inv[n] = 1.0f / sc;  // exact: a power of two
   return sc;
 }
 
-template <class In>
+template <class In, bool TENSOR>
 __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
     k_resolve_fp8x2(In in, float bg0, float bg1, float bg2, float kappa,
                     const float *__restrict__ w1, const float *__restrict__ b1,
@@ -531,13 +610,16 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
   float *si = reinterpret_cast<float *>(sm + kC8S);
   if (in.rejected()) return;  // a rejected pass, or the frame is already done
 
-  // weights: e4m3 pairs with power-of-two row scales, zero padded; biases fp32
+  // weights: e4m3 pairs with power-of-two row (or tensor) scales, zero
+  // padded; biases fp32
+  float *ts = reinterpret_cast<float *>(sm + kC8TS);
   for (int i = tid; i < (int)(kC8B - kC8W1) / 4; i += kRThreads)
     reinterpret_cast<uint32_t *>(sm + kC8W1)[i] = 0u;
   __syncthreads();
+  if (TENSOR) tensor_scales(w1, b1, w2, b2, w3, kappa, ts);
   if (tid < 32) {
     const int n = tid;
-    const float sc = weight_row_scale(w1, n, 5, si);
+    const float sc = weight_row_scale(w1, n, 5, si, TENSOR ? ts[3] : 0.0f);
     for (int k = 0; k < 5; ++k) {
       uint8_t h, l;
       split_w8(w1[n * 5 + k] * sc, h, l);
@@ -548,7 +630,7 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
     }
   } else if (tid < 48) {
     const int n = tid - 32;
-    const float sc = weight_row_scale(w2, n, 32, si + 32);
+    const float sc = weight_row_scale(w2, n, 32, si + 32, TENSOR ? ts[4] : 0.0f);
     for (int k = 0; k < 32; ++k) {
       uint8_t h, l;
       split_w8(w2[n * 32 + k] * sc, h, l);
@@ -557,7 +639,7 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
     }
   } else if (tid < 51) {
     const int n = tid - 48;
-    const float sc = weight_row_scale(w3, n, 16, si + 48);
+    const float sc = weight_row_scale(w3, n, 16, si + 48, TENSOR ? ts[5] : 0.0f);
     for (int k = 0; k < 16; ++k) {
       uint8_t h, l;
       split_w8(w3[n * 16 + k] * sc, h, l);
@@ -616,10 +698,14 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
         pixel_features(in, bg0, bg1, bg2, kappa, x, y, xv, front[t]);
       }
       flag[t] = xv[5] != 0.0f;
-      float mx = 0.0f;
+      if (TENSOR) {
+        sh[t] = ts[0];
+      } else {
+        float mx = 0.0f;
 #pragma unroll
-      for (int k = 0; k < 5; ++k) mx = fmaxf(mx, fabsf(xv[k]));
-      sh[t] = row_scale(mx);
+        for (int k = 0; k < 5; ++k) mx = fmaxf(mx, fabsf(xv[k]));
+        sh[t] = row_scale(mx);
+      }
       uint32_t h0, l0, h1, l1;
       split4_e4m3(xv[0] * sh[t], xv[1] * sh[t], xv[2] * sh[t], xv[3] * sh[t], h0, l0);
       split4_e4m3(xv[4] * sh[t], 0.f, 0.f, 0.f, h1, l1);
@@ -652,7 +738,7 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
         d[j] = fmaxf(fmaf(d[j], k1 * si[j], sb[j]), 0.0f);
         mx = fmaxf(mx, d[j]);
       }
-      sh[t] = row_scale(mx);
+      sh[t] = TENSOR ? ts[1] : row_scale(mx);
       uint32_t ph8[8], pl8[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j)
@@ -695,7 +781,7 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
         d[j] = fmaxf(fmaf(d[j], k2 * si[32 + j], sb[32 + j]), 0.0f);
         mx = fmaxf(mx, d[j]);
       }
-      sh[t] = row_scale(mx);
+      sh[t] = TENSOR ? ts[2] : row_scale(mx);
       uint32_t ph4[4], pl4[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j)
@@ -761,7 +847,26 @@ __global__ void __launch_bounds__(kRThreads, kRCtasPerSm)
 using namespace star;
 
 // MLP operand kinds of the resolve kernels
-enum ResolveKind { kResolveBf16 = 0, kResolveFp8 = 1, kResolveFp8x2 = 2 };
+enum ResolveKind {
+  kResolveBf16 = 0,
+  kResolveFp8 = 1,     // e4m3, per-row scales
+  kResolveFp8x2 = 2,   // compensated e4m3, per-row scales
+  kResolveFp8T = 3,    // e4m3, per-tensor scales
+  kResolveFp8x2T = 4,  // compensated e4m3, per-tensor scales
+  kResolveKinds = 5
+};
+
+// The resolve kind of an MLP operand type of the C ABI (-1: none).
+static int resolve_kind(int32_t mlp_type) {
+  switch (mlp_type) {
+    case STAR_NT_BF16: return kResolveBf16;
+    case STAR_NT_E4M3: return kResolveFp8;
+    case STAR_NT_E4M3X2: return kResolveFp8x2;
+    case STAR_NT_E4M3_TENSOR: return kResolveFp8T;
+    case STAR_NT_E4M3X2_TENSOR: return kResolveFp8x2T;
+    default: return -1;
+  }
+}
 
 // Launch of a resolve kernel on input In (the grid: one CTA per round of two
 // 128-pixel tiles, at most 8 CTAs per SM).
@@ -772,10 +877,12 @@ static star_nt_status launch_kernel(int kind, const In &in, const star_nt_params
   static_assert(kQUsed + 1024 <= kQSmem, "shared memory map");
   static_assert(kF8Used + 1024 <= kQSmem, "shared memory map");
   static_assert(kC8Used + 1024 <= kQSmem, "shared memory map");
-  auto kern = kind == kResolveFp8x2 ? k_resolve_fp8x2<In>
-              : kind == kResolveFp8 ? k_resolve_fp8<In>
-                                    : k_resolve<In>;
-  static bool attr[3] = {false, false, false};
+  auto kern = kind == kResolveFp8x2T ? k_resolve_fp8x2<In, true>
+              : kind == kResolveFp8T  ? k_resolve_fp8<In, true>
+              : kind == kResolveFp8x2 ? k_resolve_fp8x2<In, false>
+              : kind == kResolveFp8   ? k_resolve_fp8<In, false>
+                                      : k_resolve<In>;
+  static bool attr[kResolveKinds] = {false, false, false, false, false};
   if (!attr[kind]) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kQSmem) != cudaSuccess)
       return STAR_NT_ERR_CUDA;
@@ -847,6 +954,18 @@ extern "C" star_nt_status star_nt_resolve_fp8x2(const star_nt_scene *scene, cons
                         d_status, stream);
 }
 
+extern "C" star_nt_status star_nt_resolve_mlp(const star_nt_scene *scene, const star_nt_bins *b2,
+                                              const star_nt_bins *b3, const star_nt_layers *l1,
+                                              const star_nt_layers *l2, const star_nt_layers *l3,
+                                              int32_t W, int32_t H, const star_nt_params *params,
+                                              const star_nt_mlp *w, int32_t mlp_type, float *rgba32f,
+                                              uint32_t *rgba8, int32_t *d_status, void *stream) {
+  const int kind = resolve_kind(mlp_type);
+  if (kind < 0) return STAR_NT_ERR_ARG;
+  return launch_resolve(kind, scene, b2, b3, l1, l2, l3, W, H, params, w, rgba32f, rgba8, d_status,
+                        stream);
+}
+
 extern "C" star_nt_status star_nt_resolve_leaf(const star_nt_scene *scene,
                                                const star_nt_leaf_plan *plan,
                                                const star_nt_layers *layers, const uint32_t *masks,
@@ -855,8 +974,8 @@ extern "C" star_nt_status star_nt_resolve_leaf(const star_nt_scene *scene,
                                                int32_t *d_status, void *stream) {
   if (!scene || !plan || !layers || !masks || !params || !mlp_ok(w) || (!rgba32f && !rgba8))
     return STAR_NT_ERR_ARG;
-  if (mlp_type != STAR_NT_BF16 && mlp_type != STAR_NT_E4M3 && mlp_type != STAR_NT_E4M3X2)
-    return STAR_NT_ERR_ARG;
+  const int kind = resolve_kind(mlp_type);
+  if (kind < 0) return STAR_NT_ERR_ARG;
   if (!leaf_plan_valid(plan)) return STAR_NT_ERR_ARG;
   if (scene->n_tris < 0 || (scene->n_tris > 0 && !scene->rgba8)) return STAR_NT_ERR_ARG;
   if ((uintptr_t)rgba32f & 15u) return STAR_NT_ERR_ARG;
@@ -888,9 +1007,6 @@ extern "C" star_nt_status star_nt_resolve_leaf(const star_nt_scene *scene,
     in.tail3[k] = reinterpret_cast<const uint4 *>(layers[k].tail);
     in.t3[k] = layers[k].t_tail;
   }
-  const int kind = mlp_type == STAR_NT_E4M3X2 ? kResolveFp8x2
-                   : mlp_type == STAR_NT_E4M3 ? kResolveFp8
-                                              : kResolveBf16;
   return launch_kernel(kind, in, params, w, rgba32f, rgba8, d_status, stream);
 }
 
@@ -900,11 +1016,15 @@ cudaError_t preload_resolve_tc() {
   cudaFuncAttributes a;
   cudaError_t e = cudaSuccess, r;
   if ((r = cudaFuncGetAttributes(&a, k_resolve<FeatIn>)) != cudaSuccess) e = r;
-  if ((r = cudaFuncGetAttributes(&a, k_resolve_fp8<FeatIn>)) != cudaSuccess) e = r;
   if ((r = cudaFuncGetAttributes(&a, k_resolve<FeatInLeaf>)) != cudaSuccess) e = r;
-  if ((r = cudaFuncGetAttributes(&a, k_resolve_fp8<FeatInLeaf>)) != cudaSuccess) e = r;
-  if ((r = cudaFuncGetAttributes(&a, k_resolve_fp8x2<FeatIn>)) != cudaSuccess) e = r;
-  if ((r = cudaFuncGetAttributes(&a, k_resolve_fp8x2<FeatInLeaf>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_resolve_fp8<FeatIn, false>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_resolve_fp8<FeatInLeaf, false>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_resolve_fp8x2<FeatIn, false>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_resolve_fp8x2<FeatInLeaf, false>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_resolve_fp8<FeatIn, true>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_resolve_fp8<FeatInLeaf, true>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_resolve_fp8x2<FeatIn, true>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_resolve_fp8x2<FeatInLeaf, true>)) != cudaSuccess) e = r;
   return e;
 }
 }  // namespace star

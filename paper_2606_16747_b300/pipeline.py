@@ -22,6 +22,9 @@ import torch
 from . import star_nt as sn
 
 STATE_W2, STATE_W3 = 8, 16   # byte offsets of {W2, H2} and {W3, H3} in star_nt_pass_state
+# MLP operand types of the fused resolve
+MLP_TYPES = {"bf16": sn.BF16, "fp8": sn.E4M3, "fp8x2": sn.E4M3X2, "fp8t": sn.E4M3_TENSOR,
+             "fp8x2t": sn.E4M3X2_TENSOR}
 
 
 def _i32(vals, device):
@@ -47,11 +50,12 @@ class Renderer:
         self.x_dtype = x_dtype
         # fused: upscale + features + MLP on tcgen05 + composite in one kernel
         # (True or "bf16": bf16 operands; "fp8": e4m3 operands; "fp8x2":
-        # compensated e4m3 pairs)
-        if fused not in (False, None, True, "bf16", "fp8", "fp8x2"):
+        # compensated e4m3 pairs; "fp8t", "fp8x2t": the same with per-tensor
+        # scales)
+        if fused not in (False, None, True) and fused not in MLP_TYPES:
             raise ValueError(f"fused: {fused!r}")
         self.fused = bool(fused)
-        self.fused_fp8 = fused in ("fp8", "fp8x2")
+        self.fused_fp8 = fused in MLP_TYPES and fused != "bf16"
         self.mlp_kind = fused if self.fused_fp8 else "bf16"
         # persistent: the three geometry passes in one launch (tuning: star_nt_tuning's
         # (block_w, ctas_per_sm, pixels_per_thread))
@@ -200,10 +204,8 @@ class Renderer:
                                                          self.leaf_layers, self.mask[0], self.leaf_ws,
                                                          self.tuning, self.status, stream)),
               ("resolve", lambda: sn.resolve_leaf(self.scene, self.plan, self.leaf_layers, self.mask[0],
-                                                  self.params, self.mlp,
-                                                  {"bf16": sn.BF16, "fp8": sn.E4M3,
-                                                   "fp8x2": sn.E4M3X2}[self.mlp_kind], self.rgba32f,
-                                                  self.rgba8_out, self.status, stream))]
+                                                  self.params, self.mlp, MLP_TYPES[self.mlp_kind],
+                                                  self.rgba32f, self.rgba8_out, self.status, stream))]
         if update_tiles:
             st.append(("quadtree", lambda: self.update_tiles(stream)))
         return st
@@ -243,7 +245,10 @@ class Renderer:
                    ("pass3", lambda: sn.geometry_pass(self.scene, b3, 3, self.l3, self.status,
                                                       stream))]
         if self.fused:
-            res = {"bf16": sn.resolve, "fp8": sn.resolve_fp8, "fp8x2": sn.resolve_fp8x2}[self.mlp_kind]
+            res = {"bf16": sn.resolve, "fp8": sn.resolve_fp8, "fp8x2": sn.resolve_fp8x2}.get(self.mlp_kind)
+            if res is None:
+                t = MLP_TYPES[self.mlp_kind]
+                res = lambda *a: sn.resolve_mlp(*a[:10], t, *a[10:])
             st.append(("resolve", lambda: res(self.scene, b2, b3, self.l1, self.l2, self.l3,
                                               self.W, self.H, self.params, self.mlp,
                                               self.rgba32f, self.rgba8_out, self.status, stream)))

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libstar_nt.so")
 
 OK, ERR_ARG, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = range(6)
-F32, BF16, E4M3, E4M3X2 = 0, 1, 2, 3
+F32, BF16, E4M3, E4M3X2, E4M3_TENSOR, E4M3X2_TENSOR = 0, 1, 2, 3, 4, 5
 LEAF_MAX_TARGETS = 9
 
 # every entry point declared in include/star_nt.h
@@ -33,7 +33,7 @@ EXPORTS = ("star_nt_version", "star_nt_status_string", "star_nt_default_params",
            "star_nt_geometry_passes_resolve", "star_nt_resolve_fp8x2", "star_nt_set_wait_limit",
            "star_nt_wait_limit", "star_nt_default_frame_options", "star_nt_create", "star_nt_destroy",
            "star_nt_workspace_size", "star_nt_bind_workspace", "star_nt_frame", "star_nt_tune",
-           "star_nt_ctx_tuning", "star_nt_ctx_set_tuning", "star_nt_ctx_pass_state")
+           "star_nt_ctx_tuning", "star_nt_ctx_set_tuning", "star_nt_ctx_pass_state", "star_nt_resolve_mlp")
 
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
@@ -169,6 +169,9 @@ def lib():
                                             _P, _P, _P, _P]
         L.star_nt_resolve_fp8.argtypes = L.star_nt_resolve.argtypes
         L.star_nt_resolve_fp8x2.argtypes = L.star_nt_resolve.argtypes
+        L.star_nt_resolve_mlp.argtypes = [ctypes.POINTER(Scene)] + [ctypes.POINTER(Bins)] * 2 + \
+            [ctypes.POINTER(Layers)] * 3 + [_I32, _I32, ctypes.POINTER(Params), ctypes.POINTER(Mlp), _I32,
+                                            _P, _P, _P, _P]
         L.star_nt_infer.argtypes = [ctypes.POINTER(Mlp), _I32, _P, _P, _I64, _P, _P]
         L.star_nt_composite.argtypes = [_P, _P, _I64, _P, _P, _P]
         L.star_nt_quadtree_ws_bytes.argtypes = [_I32, _I32, _I32, ctypes.POINTER(ctypes.c_size_t)]
@@ -404,6 +407,15 @@ def resolve_fp8x2(scene: Scene, bins2, bins3, layers1, layers2, layers3, W, H, p
     _check("star_nt_resolve_fp8x2", lib().star_nt_resolve_fp8x2(
         ctypes.byref(scene), ctypes.byref(bins2.c), ctypes.byref(bins3.c), *[ctypes.byref(l) for l in ls],
         W, H, ctypes.byref(params), ctypes.byref(w), _ptr(rgba32f), _ptr(rgba8), _ptr(status),
+        _stream(stream)))
+
+
+def resolve_mlp(scene: Scene, bins2, bins3, layers1, layers2, layers3, W, H, params: Params, w: Mlp, mlp_type,
+                rgba32f=None, rgba8=None, status=None, stream=None):
+    ls = [layers_struct(l) for l in (layers1, layers2, layers3)]
+    _check("star_nt_resolve_mlp", lib().star_nt_resolve_mlp(
+        ctypes.byref(scene), ctypes.byref(bins2.c), ctypes.byref(bins3.c), *[ctypes.byref(l) for l in ls],
+        W, H, ctypes.byref(params), ctypes.byref(w), int(mlp_type), _ptr(rgba32f), _ptr(rgba8), _ptr(status),
         _stream(stream)))
 
 

@@ -125,7 +125,7 @@ def test_leaf_frame_matches_oracle(orc, sn, B):
 
 
 @pytest.mark.parametrize("level", [0, 1, 2, 3])
-@pytest.mark.parametrize("fused", [True, "fp8", "fp8x2"])
+@pytest.mark.parametrize("fused", [True, "fp8", "fp8x2", "fp8t", "fp8x2t"])
 def test_uniform_levels_equal_global_renderer(sn, level, fused):
     """All leaves at one level: the per-leaf frame is the global-scale frame
     at that level's sizes, bit for bit (same planes, same resolve arithmetic)."""

@@ -789,8 +789,9 @@ def test_pass2_merge_scale(sn, persistent):
 # are the oracle's, and every pixel is finite and in range.
 
 
+@pytest.mark.parametrize("kind", ["fp8", "fp8t"])
 @pytest.mark.parametrize("weights", ["xavier", "trained"])
-def test_fused_resolve_fp8_tailless_pixels(orc, sn, weights):
+def test_fused_resolve_fp8_tailless_pixels(orc, sn, weights, kind):
     from paper_2606_16747_b300.pipeline import Renderer
     sc = scenes.screen_scene(29, 600, 333, 197, size_scale=0.7)    # ragged; pixels with and without a tail
     W, H = sc.width, sc.height
@@ -800,7 +801,7 @@ def test_fused_resolve_fp8_tailless_pixels(orc, sn, weights):
         path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                             "paper_2606_16747_b300", "weights", "tail_mlp.npz")
         mlp = dict(np.load(path))
-    r = Renderer(sc.verts, sc.rgba8, W, H, mlp=mlp, x_dtype=sn.BF16, fused="fp8")
+    r = Renderer(sc.verts, sc.rgba8, W, H, mlp=mlp, x_dtype=sn.BF16, fused=kind)
     r.set_camera(sc.cam.vp32)
     r.state.view(torch.int32)[:6] = torch.tensor([W, H, 201, 119, 97, 57], dtype=torch.int32)
     r.star_frame(update_tiles=False)
@@ -823,8 +824,9 @@ def test_fused_resolve_fp8_tailless_pixels(orc, sn, weights):
 TOL_MLP = 2.0 / 255.0
 
 
+@pytest.mark.parametrize("scaling", ["row", "tensor"])
 @pytest.mark.parametrize("weights", ["xavier", "trained"])
-def test_fused_resolve_fp8x2(orc, sn, weights):
+def test_fused_resolve_fp8x2(orc, sn, weights, scaling):
     from paper_2606_16747_b300.pipeline import Renderer
     sc = scenes.screen_scene(29, 3000, 333, 197, size_scale=0.7)   # ragged: partial tiles
     W, H = sc.width, sc.height
@@ -837,7 +839,8 @@ def test_fused_resolve_fp8x2(orc, sn, weights):
     o = orc.frame_star(sc.verts, sc.rgba8, sc.cam.vp32, W, H, (201, 119), (97, 57), scenes.mlp_flat(mlp),
                        threads=4)
     errs = {}
-    for kind in ("fp8x2", "fp8"):
+    kinds = ("fp8x2", "fp8") if scaling == "row" else ("fp8x2t", "fp8t")
+    for kind in kinds:
         r = Renderer(sc.verts, sc.rgba8, W, H, mlp=mlp, x_dtype=sn.BF16, fused=kind)
         r.set_camera(sc.cam.vp32)
         r.state.view(torch.int32)[:6] = torch.tensor([W, H, 201, 119, 97, 57], dtype=torch.int32)
@@ -845,13 +848,13 @@ def test_fused_resolve_fp8x2(orc, sn, weights):
         torch.cuda.synchronize()
         r.check_status()
         errs[kind] = np.abs(r.rgba32f.cpu().numpy().reshape(-1, 4)[:, :3] - o["rgb"])
-    err = errs["fp8x2"]
+    err = errs[kinds[0]]
     assert err.max() <= TOL_MLP, err.max() * 255
     no_tail = np.asarray(o["flag"]).ravel() == 0
     if no_tail.any():
         assert err[no_tail].max() <= 1e-5
     # the compensation removes most of the plain e4m3 error
-    assert err.max() < 0.5 * errs["fp8"].max()
+    assert err.max() < 0.5 * errs[kinds[1]].max()
 
 
 # ---------------------------------------------------------------------------
