@@ -87,6 +87,11 @@ def _declare(L):
     L.orc_inverse4.argtypes = [_P, _P]
     L.orc_inverse4.restype = ctypes.c_int
     L.orc_reproject.argtypes = [_P, _P, _P, _P, _I32, _I32, _P]
+    L.orc_dfaoit_features.argtypes = [_P, _P, _P, _P, _I64, _I64, _D, _P, _P]
+    L.orc_dfaoit_features.restype = None
+    L.orc_mlp_dfaoit_forward.argtypes = [_P, _P, _P, _I64, _P]
+    L.orc_mlp_dfaoit_mse_grad.argtypes = [_P, _P, _P, _I64, _P]
+    L.orc_mlp_dfaoit_mse_grad.restype = _D
 
 
 def _c(a, dtype):
@@ -160,6 +165,64 @@ def resolve(fr: Frags, rgba8, bg=(1.0, 1.0, 1.0), threads=1) -> dict:
                                             W, b[0], b[1], _ptr(bg), *[_ptr(out[k]) for k in order]),
                     bands))
     return out
+
+
+# ---------------------------------------------------------------------------
+# The DFAOIT comparison network (Sec. 3.3): its eleven listed features, the
+# 11 -> 32 -> 16 -> 3 network with a sigmoid output, and its composite
+# C = C_t + C_b prod(1 - a_i).
+
+DFAOIT_PARAMS = 963
+DFAOIT_SHAPES = (("w1", (32, 11)), ("b1", (32,)), ("w2", (16, 32)), ("b2", (16,)), ("w3", (3, 16)),
+                 ("b3", (3,)))
+
+
+def dfaoit_features(fr: Frags, rgba8, kappa=KAPPA_N, threads=1):
+    """(x [P, 11], t_all [P]) of every pixel (orc_dfaoit_features)."""
+    L = lib()
+    P = fr.W * fr.H
+    rgba8 = _c(rgba8, np.uint32)
+    x = np.empty((P, 11), np.float64)
+    t_all = np.empty(P, np.float64)
+    bands = _bands(fr.H, threads)
+    with ThreadPoolExecutor(len(bands)) as ex:
+        list(ex.map(lambda b: L.orc_dfaoit_features(_ptr(fr.offsets), _ptr(fr.z), _ptr(fr.prim), _ptr(rgba8),
+                                                    b[0] * fr.W, b[1] * fr.W, float(kappa), _ptr(x),
+                                                    _ptr(t_all)), bands))
+    return x, t_all
+
+
+def mlp_dfaoit_forward(params, x, flag=None):
+    L = lib()
+    params = _c(params, np.float64)
+    assert params.size == DFAOIT_PARAMS
+    x = _c(x, np.float64)
+    n = x.shape[0]
+    f = np.empty((n, 3), np.float64)
+    fl = None if flag is None else _c(flag, np.uint8)
+    L.orc_mlp_dfaoit_forward(_ptr(params), _ptr(x), _ptr(fl), n, _ptr(f))
+    return f
+
+
+def mlp_dfaoit_mse_grad(params, x, y):
+    L = lib()
+    params = _c(params, np.float64)
+    x = _c(x, np.float64)
+    y = _c(y, np.float64)
+    g = np.empty(DFAOIT_PARAMS, np.float64)
+    loss = L.orc_mlp_dfaoit_mse_grad(_ptr(params), _ptr(x), _ptr(y), x.shape[0], _ptr(g))
+    return loss, g
+
+
+def frame_dfaoit(verts, rgba8, vp32, W, H, params, bg=(1.0, 1.0, 1.0), threads=1):
+    """The DFAOIT comparison frame at full resolution: features, network
+    (f = 0 where a pixel has no fragment), C = f + t_all C_b."""
+    fr = raster(verts, vp32, W, H, threads)
+    x, t_all = dfaoit_features(fr, rgba8, threads=threads)
+    flag = (fr.counts > 0).astype(np.uint8)
+    f = mlp_dfaoit_forward(params, x, flag)
+    rgb = f + t_all[:, None] * np.asarray(bg, np.float64)[None, :]
+    return dict(x=x, t_all=t_all, flag=flag, f=f, rgb=rgb, frags=fr)
 
 
 def unsorted_over(fr: Frags, rgba8, bg=(1.0, 1.0, 1.0)):

@@ -507,6 +507,159 @@ double orc_mlp_mse_grad(const double *prm, const double *x, const double *y, int
     return loss;
 }
 
+/* ------------------------------------------------------------------------ */
+/* The comparison network of Sec. 3.3: the original DFAOIT predicts the     */
+/* whole transparency colour C_t from the features the paper lists for it   */
+/* (the exact Porter-Duff blend of the two front fragments, the average     */
+/* colour and average opacity of the remaining n-2 fragments, the           */
+/* accumulated premultiplied colour and the fragment count), composited as  */
+/* C = C_t + C_b prod_i (1 - a_i), with a sigmoid output.  The list has     */
+/* eleven scalars although the text says ten; all eleven are kept:          */
+/*   x[0..2] = a1 c1 + (1 - a1) a2 c2          (two front fragments, over)  */
+/*   x[3..5] = sum_{i>=3} c_i / (n - 2)         (tail colour, straight mean) */
+/*   x[6]    = sum_{i>=3} a_i / (n - 2)         (tail opacity, mean)         */
+/*   x[7..9] = sum_{i>=3} a_i c_i               (tail, premultiplied sum)    */
+/*   x[10]   = kappa_n n                                                      */
+/* (tail means 0 when n <= 2), fragments in (z, primitive id) order, and     */
+/* t_all = prod_i (1 - a_i).                                                  */
+
+void orc_dfaoit_features(const int64_t *offsets, const float *z, const int32_t *prim,
+                         const uint32_t *rgba8, int64_t p0, int64_t p1, double kappa_n, double *x,
+                         double *t_all)
+{
+    int64_t cap = 0;
+    orc_frag *buf = 0;
+    for (int64_t p = p0; p < p1; ++p) {
+        int64_t n = offsets[p + 1] - offsets[p];
+        if (n > cap) {
+            cap = 2 * n;
+            buf = (orc_frag *)realloc(buf, sizeof(orc_frag) * (size_t)cap);
+        }
+        for (int64_t i = 0; i < n; ++i) {
+            buf[i].z = z[offsets[p] + i];
+            buf[i].prim = prim[offsets[p] + i];
+        }
+        qsort(buf, (size_t)n, sizeof(orc_frag), orc_frag_cmp);
+        double *xp = x + 11 * p;
+        for (int k = 0; k < 11; ++k) xp[k] = 0.0;
+        double a1 = 0, a2 = 0;
+        if (n >= 1) a1 = ch(rgba8[buf[0].prim], 3);
+        if (n >= 2) a2 = ch(rgba8[buf[1].prim], 3);
+        for (int k = 0; k < 3; ++k) {
+            double c1 = n >= 1 ? ch(rgba8[buf[0].prim], k) : 0.0;
+            double c2 = n >= 2 ? ch(rgba8[buf[1].prim], k) : 0.0;
+            xp[k] = a1 * c1 + (1.0 - a1) * a2 * c2;
+        }
+        double T = 1.0;
+        for (int64_t i = 0; i < n; ++i) T *= 1.0 - ch(rgba8[buf[i].prim], 3);
+        t_all[p] = T;
+        if (n > 2) {
+            double sc[3] = {0, 0, 0}, sa = 0.0, sp[3] = {0, 0, 0};
+            for (int64_t i = 2; i < n; ++i) {
+                uint32_t c = rgba8[buf[i].prim];
+                double al = ch(c, 3);
+                sa += al;
+                for (int k = 0; k < 3; ++k) {
+                    sc[k] += ch(c, k);
+                    sp[k] += al * ch(c, k);
+                }
+            }
+            double m = (double)(n - 2);
+            for (int k = 0; k < 3; ++k) {
+                xp[3 + k] = sc[k] / m;
+                xp[7 + k] = sp[k];
+            }
+            xp[6] = sa / m;
+        }
+        xp[10] = kappa_n * (double)n;
+    }
+    free(buf);
+}
+
+/* Parameters w1[32][11], b1[32], w2[16][32], b2[16], w3[3][16], b3[3]; ReLU
+ * hidden layers, sigmoid output; f = 0 where flag == 0 (no fragment). */
+enum { DW1 = 0, DB1 = 352, DW2 = 384, DB2 = 896, DW3 = 912, DB3 = 960, DNP = 963 };
+
+static double sigmoid(double v) { return 1.0 / (1.0 + exp(-v)); }
+
+static void orc_dfaoit_one(const double *prm, const double *x, double *h1, double *h2, double *f)
+{
+    for (int o = 0; o < 32; ++o) {
+        double s = prm[DB1 + o];
+        for (int i = 0; i < 11; ++i) s += prm[DW1 + 11 * o + i] * x[i];
+        h1[o] = relu(s);
+    }
+    for (int o = 0; o < 16; ++o) {
+        double s = prm[DB2 + o];
+        for (int i = 0; i < 32; ++i) s += prm[DW2 + 32 * o + i] * h1[i];
+        h2[o] = relu(s);
+    }
+    for (int o = 0; o < 3; ++o) {
+        double s = prm[DB3 + o];
+        for (int i = 0; i < 16; ++i) s += prm[DW3 + 16 * o + i] * h2[i];
+        f[o] = sigmoid(s);
+    }
+}
+
+void orc_mlp_dfaoit_forward(const double *prm, const double *x, const uint8_t *flag, int64_t n,
+                            double *f)
+{
+    double h1[32], h2[16];
+    for (int64_t p = 0; p < n; ++p) {
+        if (flag && !flag[p]) {
+            f[3 * p] = f[3 * p + 1] = f[3 * p + 2] = 0.0;
+            continue;
+        }
+        orc_dfaoit_one(prm, x + 11 * p, h1, h2, f + 3 * p);
+    }
+}
+
+/* MSE over n samples x 3 channels and its gradient with respect to the 963
+ * parameters; the sigmoid's derivative is f (1 - f). */
+double orc_mlp_dfaoit_mse_grad(const double *prm, const double *x, const double *y, int64_t n,
+                               double *grad)
+{
+    double h1[32], h2[16], f[3];
+    double loss = 0.0;
+    memset(grad, 0, sizeof(double) * DNP);
+    if (n == 0)
+        return 0.0;
+    double scale = 1.0 / (3.0 * (double)n);
+    for (int64_t p = 0; p < n; ++p) {
+        const double *xp = x + 11 * p;
+        orc_dfaoit_one(prm, xp, h1, h2, f);
+        double g3[3], g2[16], g1[32];
+        for (int o = 0; o < 3; ++o) {
+            double d = f[o] - y[3 * p + o];
+            loss += d * d * scale;
+            g3[o] = 2.0 * d * scale * f[o] * (1.0 - f[o]);
+        }
+        for (int o = 0; o < 3; ++o) {
+            grad[DB3 + o] += g3[o];
+            for (int i = 0; i < 16; ++i) grad[DW3 + 16 * o + i] += g3[o] * h2[i];
+        }
+        for (int i = 0; i < 16; ++i) {
+            double s = 0.0;
+            for (int o = 0; o < 3; ++o) s += prm[DW3 + 16 * o + i] * g3[o];
+            g2[i] = h2[i] > 0.0 ? s : 0.0;
+        }
+        for (int o = 0; o < 16; ++o) {
+            grad[DB2 + o] += g2[o];
+            for (int i = 0; i < 32; ++i) grad[DW2 + 32 * o + i] += g2[o] * h1[i];
+        }
+        for (int i = 0; i < 32; ++i) {
+            double s = 0.0;
+            for (int o = 0; o < 16; ++o) s += prm[DW2 + 32 * o + i] * g2[o];
+            g1[i] = h1[i] > 0.0 ? s : 0.0;
+        }
+        for (int o = 0; o < 32; ++o) {
+            grad[DB1 + o] += g1[o];
+            for (int i = 0; i < 11; ++i) grad[DW1 + 11 * o + i] += g1[o] * xp[i];
+        }
+    }
+    return loss;
+}
+
 /* Adam (Kingma and Ba) with bias correction; step counts from 1. */
 void orc_adam(double *prm, const double *g, double *m, double *v, int64_t n, int64_t step,
               double lr, double b1, double b2, double eps)
