@@ -453,6 +453,7 @@ def measure(args, workload, steps, warmup, rank, world, leaf_variant=True, main=
     del leaf
     precision = (precision_record(sn, torch, star, sc, w, W, H, vp32[2 * q_step])
                  if star.fused and star.persistent and x_dtype == sn.BF16 else None)
+    dfaoit = dfaoit_record(sn, torch, plain, sc, W, H, vp32[2 * q_step], flush)
 
     # end to end through the public API: the context call, host inputs in and
     # both 8-bit frames out every step
@@ -557,6 +558,7 @@ def measure(args, workload, steps, warmup, rank, world, leaf_variant=True, main=
                                                         peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]))}
     line["per_leaf"] = leaf_info
     line["precision"] = precision
+    line["dfaoit"] = dfaoit
     line["psnr_db_vs_exact_abuffer"] = psnr["psnr_db"]
     line["quality"] = {"mse_vs_exact_abuffer": psnr["mse"],
                        "error_reduction_vs_unsorted_pct": psnr["error_reduction_vs_unsorted_pct"],
@@ -615,6 +617,72 @@ def precision_record(sn, torch, star, sc, w, W, H, vp, reps=20):
                      "p999_err_255": round(float(torch.topk(err, k).values[-1]) * 255.0, 4)}
     rec["reference"] = ("frame of the float32 MLP path on the same planes (separate kernels; within 1e-5 "
                         "of the float64 oracle by the parity tests); bar 2/255")
+    return rec
+
+
+def dfaoit_record(sn, torch, plain, sc, W, H, vp, flush, reps=20):
+    """The DFAOIT comparison network (Sec. 3.3; Table 2's inference columns)
+    beside STAR-NT's tail network on the same frame: the bf16 tensor-core
+    inference of each on every pixel (5 inputs, 16 B per pixel, against 11
+    inputs, 32 B per pixel), the DFAOIT frame (raster, 11-feature pass,
+    network, composite) and, with trained weights, its PSNR against the exact
+    A-buffer."""
+    from paper_2606_16747_b300 import train as tr
+    P = W * H
+    path = os.path.join(ROOT, "paper_2606_16747_b300", "weights", "dfaoit_mlp.npz")
+    trained = os.path.exists(path)
+    wd = dict(np.load(path)) if trained else tr.dfaoit_initial_weights(0)
+    wt = {k: torch.as_tensor(np.asarray(v, np.float32)).cuda() for k, v in wd.items()}
+    mlp10 = sn.mlp_struct(wt)
+    x5 = torch.zeros(P * 8, dtype=torch.bfloat16, device="cuda")
+    x10 = torch.zeros(P * 16, dtype=torch.bfloat16, device="cuda")
+    front5 = torch.empty(P * 4, device="cuda")
+    front10 = torch.empty(P * 4, device="cuda")
+    f = torch.empty(P * 4, device="cuda")
+    out = torch.empty(P * 4, device="cuda")
+    plain.set_cameras(vp)
+    b = plain.bins[0]
+    sn.raster(plain.scene, plain.vp, plain.full_size, W, H, b, None, plain.status)
+    sn.build_inputs(plain.scene, b, b, b, plain.l1, None, None, W, H, plain.params, x5, sn.BF16, front5,
+                    plain.status)
+    sn.build_inputs_dfaoit(plain.scene, b, None, W, H, plain.params, x10, sn.BF16, front10, plain.status)
+    torch.cuda.synchronize()
+    plain.check_status()
+
+    def time_graph(fn):
+        g = plain.capture(fn)
+        g.replay()
+        ev = []
+        for _ in range(reps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.replay()
+            e1.record()
+            ev.append((e0, e1))
+        torch.cuda.synchronize()
+        return float(np.mean([a.elapsed_time(c) for a, c in ev]))
+
+    ms5 = time_graph(lambda: sn.infer(plain.mlp, sn.BF16, x5, f, P, plain.status))
+    ms10 = time_graph(lambda: sn.infer_dfaoit(mlp10, sn.BF16, x10, f, P, plain.status))
+
+    def dfaoit_frame():
+        sn.raster(plain.scene, plain.vp, plain.full_size, W, H, b, None, plain.status)
+        sn.build_inputs_dfaoit(plain.scene, b, None, W, H, plain.params, x10, sn.BF16, front10, plain.status)
+        sn.infer_dfaoit(mlp10, sn.BF16, x10, f, P, plain.status)
+        sn.composite(front10, f, P, out, None)
+    frame_ms = time_graph(dfaoit_frame)
+    plain.check_status()
+    rec = {"inference_ms_5f": round(ms5, 5), "inference_ms_10f": round(ms10, 5),
+           "inference_speedup_10_to_5": round(ms10 / ms5, 4),
+           "input_bytes_per_pixel": {"5f": 16, "10f": 32},
+           "dfaoit_frame_ms": round(frame_ms, 5), "weights": "trained" if trained else "xavier_seed0",
+           "note": "bf16 tensor-core inference over every pixel of the frame (L2 flushed before each); "
+                   "the paper's ten features are eleven listed scalars, all eleven are inputs"}
+    if trained:
+        dfaoit_frame()
+        ex = exact_frame(sn, plain, vp, W, H)
+        rec["psnr_db_vs_exact_abuffer"] = psnr_db(out.view(P, 4)[:, :3], ex)
     return rec
 
 

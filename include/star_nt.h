@@ -610,7 +610,7 @@ star_nt_status star_nt_abuffer(const star_nt_frags *frags, const uint32_t *rgba8
  * star_nt_adam: bias-corrected Adam step `step` (from 1) on the float32
  *   master parameters; bf16_rounded (may be NULL) receives them rounded to
  *   bfloat16 precision, stored as float32 (the weights of the next forward). */
-size_t star_nt_train_ws_bytes(int64_t B);
+size_t star_nt_train_ws_bytes(int64_t B);  /* serves both networks' backward passes */
 star_nt_status star_nt_mse_grad(const float *f, const float *y, int64_t B, float *dy, float *loss,
                                 void *ws, size_t ws_bytes, void *stream);
 /* star_nt_wmse_grad: star_nt_mse_grad with a weight per sample, w [B] float32:
@@ -625,6 +625,48 @@ star_nt_status star_nt_mlp_backward(const star_nt_mlp *w, const float *x, const 
 star_nt_status star_nt_adam(float *params, const float *grad, float *m, float *v, int64_t n,
                             int64_t step, float lr, float beta1, float beta2, float eps,
                             float *bf16_rounded, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* The DFAOIT comparison network (Sec. 3.3; Table 2's "Inf. DFAOIT" column):  */
+/* the original method predicts the whole transparency colour C_t from the    */
+/* features the paper lists for it, with ReLU hidden layers of 32 and 16      */
+/* units and a sigmoid output, and composites C = C_t + C_b prod(1 - a_i).    */
+/* The list (the exact blend of the two front fragments, the average colour  */
+/* and average opacity of the remaining n - 2 fragments, their accumulated    */
+/* premultiplied colour, the fragment count) has eleven scalars although the */
+/* text counts ten; all eleven are inputs here:                              */
+/*   x[0..2]  a1 c1 + (1 - a1) a2 c2                                          */
+/*   x[3..5]  sum_tail c_i / (n - 2)      x[6]  sum_tail a_i / (n - 2)        */
+/*   x[7..9]  sum_tail a_i c_i            x[10] kappa_n n                     */
+/*   x[11]    1 when the pixel has a fragment (else f = 0), x[12..15] = 0     */
+/* with the fragments in (z, primitive id) order and the tail means 0 when   */
+/* n <= 2.                                                                    */
+
+/* star_nt_build_inputs_dfaoit: one full-resolution pass over bins (binned by
+ * star_nt_raster at W x H) writing x ([W*H][16] float32, or bfloat16 256-byte
+ * aligned: out->x_dtype) and front = (T_all C_b, 1) per pixel (out->front,
+ * [W*H][4]), so that star_nt_composite(front, f) gives C_t + T_all C_b.
+ * layers1 (optional) receives id1 and z1. */
+star_nt_status star_nt_build_inputs_dfaoit(const star_nt_scene *scene, const star_nt_bins *bins,
+                                           const star_nt_layers *layers1, int32_t W, int32_t H,
+                                           const star_nt_params *params,
+                                           const star_nt_features *out, int32_t *d_status,
+                                           void *stream);
+
+/* star_nt_infer_dfaoit: the network on P rows of x ([P][16] float32, or
+ * bfloat16 on the tcgen05 tensor cores: two TMA boxes per 128-row tile, the
+ * bias inside a second K = 16 MMA) into f ([P][4] float32, rgb and 0); w
+ * holds w1 [32][11], b1 [32], w2 [16][32], b2 [16], w3 [3][16], b3 [3]. */
+star_nt_status star_nt_infer_dfaoit(const star_nt_mlp *w, int32_t x_dtype, const void *x, float *f,
+                                    int64_t P, int32_t *d_status, void *stream);
+
+/* star_nt_dfaoit_backward: star_nt_mlp_backward for this network: gradient of
+ * L with respect to its 963 parameters (w1, b1, w2, b2, w3, b3 order) for x
+ * [B][16] float32 and dy [B][4]; the sigmoid's derivative f (1 - f);
+ * ws of star_nt_train_ws_bytes(B) bytes. */
+star_nt_status star_nt_dfaoit_backward(const star_nt_mlp *w, const float *x, const float *dy,
+                                       int64_t B, float *grad, void *ws, size_t ws_bytes,
+                                       void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* Context: the whole STAR-NT step of Fig. 1 through one call.               */

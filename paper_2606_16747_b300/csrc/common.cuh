@@ -29,7 +29,7 @@ struct __align__(16) TriSetup {
   unsigned long long ba;      // a8*b8 | a8 << 32
   unsigned long long lg;      // round(-log2(1 - a8/255) * 2^32), 0 when opaque
   float zlo;                  // lower bound of every fragment depth of the triangle
-  uint32_t pad;
+  uint32_t c8;                // straight colour: r8 | g8 << 8 | b8 << 16
 };
 static_assert(sizeof(TriSetup) == 112, "TriSetup layout");
 

@@ -91,6 +91,54 @@ __device__ __forceinline__ void write_features(const FeatOut &fo, size_t p, floa
   store_features(fo, p, x, fr);
 }
 
+// Network input of the DFAOIT comparison network and its composite terms
+// (Sec. 3.3: the features the paper lists for the original method), at full
+// resolution: x = [a1 c1 + (1 - a1) a2 c2 (3), the tail's straight colour mean
+// C / (255 m) (3) and opacity mean A / (255 m), the tail's premultiplied sum
+// S / 255^2 (3), kappa N] with m = N - 2 tail fragments (means 0 without a
+// tail), the flag N >= 1 at element 11; front = (T_all C_b, 1) with T_all =
+// (1 - a1)(1 - a2) t_tail, so that star_nt_composite gives C_t + T_all C_b.
+// x: [P][16] float32 or bfloat16.
+__device__ __forceinline__ void write_dfaoit_features(const FeatOut &fo, size_t p, float a1, float r1,
+                                                      float g1, float b1, float pr2, float pg2, float pb2,
+                                                      float a2, uint32_t N, float A, float Sr, float Sg,
+                                                      float Sb, float Cr, float Cg, float Cb, float t) {
+  float x[16];
+  x[0] = a1 * r1 + (1.0f - a1) * pr2;
+  x[1] = a1 * g1 + (1.0f - a1) * pg2;
+  x[2] = a1 * b1 + (1.0f - a1) * pb2;
+  const float inv_m = N > 2 ? __frcp_rn(255.0f * (float)(N - 2)) : 0.0f;
+  constexpr float k255sq = 1.0f / 65025.0f;
+  x[3] = Cr * inv_m;
+  x[4] = Cg * inv_m;
+  x[5] = Cb * inv_m;
+  x[6] = A * inv_m;
+  x[7] = Sr * k255sq;
+  x[8] = Sg * k255sq;
+  x[9] = Sb * k255sq;
+  x[10] = (float)N * fo.kappa;
+  x[11] = N >= 1 ? 1.0f : 0.0f;
+#pragma unroll
+  for (int k = 12; k < 16; ++k) x[k] = 0.0f;
+  const float Tall = (1.0f - a1) * (1.0f - a2) * t;
+  fo.front[p] = make_float4(Tall * fo.bg0, Tall * fo.bg1, Tall * fo.bg2, 1.0f);
+  if (fo.x_dtype == STAR_NT_F32) {
+    float4 *X = reinterpret_cast<float4 *>(fo.x) + 4 * p;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) X[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+  } else {
+    uint32_t h[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      __nv_bfloat162 v = __floats2bfloat162_rn(x[2 * q], x[2 * q + 1]);
+      h[q] = *reinterpret_cast<uint32_t *>(&v);
+    }
+    uint4 *X = reinterpret_cast<uint4 *>(fo.x) + 2 * p;
+    X[0] = make_uint4(h[0], h[1], h[2], h[3]);
+    X[1] = make_uint4(h[4], h[5], h[6], h[7]);
+  }
+}
+
 // Inputs of the full-resolution features: pass 1 at full resolution, passes
 // 2 and 3 at their own resolutions (read from their bins headers).
 struct FeatIn {

@@ -440,6 +440,7 @@ cudaError_t preload_train();
 cudaError_t preload_baselines();
 cudaError_t preload_leaf();
 cudaError_t preload_passes_resolve();
+cudaError_t preload_dfaoit();
 }  // namespace star
 
 extern "C" star_nt_status star_nt_preload(void) {
@@ -454,5 +455,6 @@ extern "C" star_nt_status star_nt_preload(void) {
   if ((r = preload_baselines()) != cudaSuccess) e = r;
   if ((r = preload_leaf()) != cudaSuccess) e = r;
   if ((r = preload_passes_resolve()) != cudaSuccess) e = r;
+  if ((r = preload_dfaoit()) != cudaSuccess) e = r;
   return e == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
 }

@@ -15,6 +15,10 @@
 // 8-row groups.  Every mbarrier wait is bounded (star_nt_set_wait_limit); on
 // expiry the kernel sets STAR_NT_ERR_TIMEOUT, stops, lets the MMA or copy in
 // flight land (a second, fixed bound), frees its tensor memory and returns.
+// The same kernel, templated on the input count and the output activation,
+// runs the DFAOIT comparison network (11 inputs, sigmoid output): its X rows
+// are 16 bf16 wide, loaded as two TMA boxes of one core column each, and
+// layer 1 takes two K = 16 MMAs (the inputs, then the bias block).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -30,27 +34,47 @@ constexpr int kRows = 128;
 constexpr uint32_t kTmemCols = 64;          // D1: 0..31, D2: 32..47, D3: 48..63
 constexpr int kMlpCtasPerSm = 8;            // 8 x 64 columns = all of tensor memory
 
-// shared memory map (bytes from a 1024-aligned base)
-constexpr uint32_t kSX = 0;         // 2 X tiles of 2048 (TMA targets)
-constexpr uint32_t kSC = 4096;      // ones block: rows (1, 1, 0, ...)
-constexpr uint32_t kSZ = 6144;      // zero block
-constexpr uint32_t kSH1 = 8192;     // 4 core columns x 2048
-constexpr uint32_t kSH2 = 16384;    // 2 core columns x 2048
-constexpr uint32_t kSW1 = 20480;    // N=32, K=16 (bias in K 8, 9): 2 x 512
-constexpr uint32_t kSW2 = 21504;    // N=16, K=48 (bias in K 32, 33): 6 x 256
-constexpr uint32_t kSW3 = 23040;    // N=16, K=32 (bias in K 16, 17): 4 x 256
-constexpr uint32_t kSBar = 24064;   // tma[2], mma, tmem slot, abort flag
-constexpr uint32_t kSmemUsed = 24096;
-// requested dynamic shared memory: caps residency at 8 CTAs per SM so that
-// the 8 x 64 tensor-memory columns always suffice
-constexpr uint32_t kSmemBytes = 26 * 1024;
+// Shared memory map (bytes from a 1024-aligned base) of the network with NIN
+// inputs: NIN = 5 (the tail MLP, X rows of 8 bf16: the inputs and the tail
+// flag) or NIN = 11 (the DFAOIT comparison network, X rows of 16 bf16, the
+// flag at element 11).  An X tile is XB bytes: one core column (K 0..7) for
+// NIN = 5, two (K 0..7, K 8..15) for NIN = 11.
+template <int NIN>
+struct MlpMap {
+  static constexpr uint32_t XB = NIN == 5 ? 2048 : 4096;
+  static constexpr uint32_t SX = 0;                 // 2 X tiles (TMA targets)
+  static constexpr uint32_t SC = 2 * XB;            // ones block: rows (1, 1, 0, ...)
+  static constexpr uint32_t SZ = SC + 2048;         // zero block
+  static constexpr uint32_t SH1 = SZ + 2048;        // 4 core columns x 2048
+  static constexpr uint32_t SH2 = SH1 + 8192;       // 2 core columns x 2048
+  // W1: N = 32; K = 16 (inputs 0..7, bias in K 8, 9) for NIN = 5, K = 32
+  // (inputs 0..15, bias in K 16, 17) for NIN = 11: core columns of 512
+  static constexpr uint32_t KB1 = NIN == 5 ? 8 : 16;  // K of b1's hi part
+  static constexpr uint32_t SW1 = SH2 + 4096;
+  static constexpr uint32_t SW2 = SW1 + (NIN == 5 ? 1024 : 2048);  // N=16, K=48 (bias in K 32, 33): 6 x 256
+  static constexpr uint32_t SW3 = SW2 + 1536;       // N=16, K=32 (bias in K 16, 17): 4 x 256
+  static constexpr uint32_t SBar = SW3 + 1024;      // tma[2], mma, tmem slot, abort flag
+  static constexpr uint32_t Used = SBar + 32;
+  // requested dynamic shared memory: caps residency at 8 CTAs per SM (NIN = 5)
+  // or 7 (NIN = 11), so that 64 tensor-memory columns per CTA always suffice
+  static constexpr uint32_t Bytes = NIN == 5 ? 26 * 1024 : 30 * 1024;
+  // byte offset of the flag within an X tile row's core column
+  static constexpr uint32_t FlagCol = NIN == 5 ? 0 : 2048;
+  static constexpr uint32_t FlagByte = NIN == 5 ? 10 : 6;
+};
+static_assert(MlpMap<5>::SW1 == 20480 && MlpMap<5>::SBar == 24064, "shared memory map of the tail MLP");
 
+// NIN inputs; SIGMOID: sigmoid output (the DFAOIT network), else ReLU.
+template <int NIN, bool SIGMOID>
 __global__ void __launch_bounds__(kMlpThreads, kMlpCtasPerSm)
     k_mlp_bf16(const __grid_constant__ CUtensorMap xmap, const float *__restrict__ w1,
                const float *__restrict__ b1, const float *__restrict__ w2,
                const float *__restrict__ b2, const float *__restrict__ w3,
                const float *__restrict__ b3, float4 *__restrict__ F, long long P,
                int32_t *status, unsigned long long wait_ns) {
+  using M = MlpMap<NIN>;
+  constexpr uint32_t kSX = M::SX, kSC = M::SC, kSZ = M::SZ, kSH1 = M::SH1, kSH2 = M::SH2, kSW1 = M::SW1,
+                     kSW2 = M::SW2, kSW3 = M::SW3, kSBar = M::SBar, kXB = M::XB;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                             ~(uintptr_t)1023);
@@ -65,10 +89,10 @@ __global__ void __launch_bounds__(kMlpThreads, kMlpCtasPerSm)
     reinterpret_cast<uint32_t *>(sm + kSC)[i] = 0u;
   __syncthreads();
   put_ones_block(sm + kSC, tid, kMlpThreads);
-  for (int i = tid; i < 32 * 5; i += kMlpThreads) put_w(sm + kSW1, i / 5, i % 5, 512, w1[i]);
+  for (int i = tid; i < 32 * NIN; i += kMlpThreads) put_w(sm + kSW1, i / NIN, i % NIN, 512, w1[i]);
   for (int i = tid; i < 16 * 32; i += kMlpThreads) put_w(sm + kSW2, i / 32, i % 32, 256, w2[i]);
   for (int i = tid; i < 3 * 16; i += kMlpThreads) put_w(sm + kSW3, i / 16, i % 16, 256, w3[i]);
-  if (tid < 32) put_bias(sm + kSW1, tid, 8, 512, b1[tid]);
+  if (tid < 32) put_bias(sm + kSW1, tid, M::KB1, 512, b1[tid]);
   if (tid < 16) put_bias(sm + kSW2, tid, 32, 256, b2[tid]);
   if (tid < 3) put_bias(sm + kSW3, tid, 16, 256, b3[tid]);
   if (tid == 0) {
@@ -100,6 +124,7 @@ __global__ void __launch_bounds__(kMlpThreads, kMlpCtasPerSm)
   bool tma_pending = false;          // a TMA load in flight (thread 0)
   uint32_t pend_bar = 0, pend_ph = 0;
   const uint64_t dW1 = smem_desc(sbase + kSW1, 512, 128);
+  const uint64_t dW1b = smem_desc(sbase + kSW1 + 1024, 512, 128);  // NIN = 11: K 16..31 (bias)
   const uint64_t dW2[3] = {smem_desc(sbase + kSW2, 256, 128), smem_desc(sbase + kSW2 + 512, 256, 128),
                            smem_desc(sbase + kSW2 + 1024, 256, 128)};
   const uint64_t dW3[2] = {smem_desc(sbase + kSW3, 256, 128), smem_desc(sbase + kSW3 + 512, 256, 128)};
@@ -108,15 +133,16 @@ __global__ void __launch_bounds__(kMlpThreads, kMlpCtasPerSm)
   const uint64_t dOnes = smem_desc(sbase + kSC, kSZ - kSC, 128);  // K block: ones, then zeros
 
   if (tid == 0 && tile < ntiles) {
-    mbar_expect_tx(bar_tma0, 2048);
+    mbar_expect_tx(bar_tma0, kXB);
     tma_load_2d(sbase + kSX, &xmap, 0, (int)(tile * kRows), bar_tma0);
+    if (NIN == 11) tma_load_2d(sbase + kSX + 2048, &xmap, 8, (int)(tile * kRows), bar_tma0);
     tma_pending = true;
     pend_bar = bar_tma0;
     pend_ph = 0u;
   }
   while (tile < ntiles) {
     const long long next = tile + gridDim.x;
-    const uint32_t xs = sbase + kSX + buf * 2048;
+    const uint32_t xs = sbase + kSX + buf * kXB;
     // ---- layer 1
     if (tid == 0) {
       if (!mbar_wait(buf ? bar_tma1 : bar_tma0, ph_tma[buf], wait_ns)) {
@@ -125,12 +151,21 @@ __global__ void __launch_bounds__(kMlpThreads, kMlpCtasPerSm)
         tma_pending = false;
         ph_tma[buf] ^= 1u;
         fence_after();
-        mma_bf16(tmem + 0, smem_desc(xs, sbase + kSC - xs, 128), dW1, idesc_bf16(32), 0u);
+        if (NIN == 5) {
+          // [X | ones] (K = 16) against [W1 | b1]
+          mma_bf16(tmem + 0, smem_desc(xs, sbase + kSC - xs, 128), dW1, idesc_bf16(32), 0u);
+        } else {
+          // X (K = 16, two core columns) against W1, then [ones | 0] against b1
+          mma_bf16(tmem + 0, smem_desc(xs, 2048, 128), dW1, idesc_bf16(32), 0u);
+          mma_bf16(tmem + 0, smem_desc(sbase + kSC, kSZ - kSC, 128), dW1b, idesc_bf16(32), 1u);
+        }
         mma_commit(bar_mma);
         if (next < ntiles) {
           const uint32_t nb = buf ? bar_tma0 : bar_tma1;
-          mbar_expect_tx(nb, 2048);
-          tma_load_2d(sbase + kSX + (buf ^ 1) * 2048, &xmap, 0, (int)(next * kRows), nb);
+          const uint32_t nx = sbase + kSX + (buf ^ 1) * kXB;
+          mbar_expect_tx(nb, kXB);
+          tma_load_2d(nx, &xmap, 0, (int)(next * kRows), nb);
+          if (NIN == 11) tma_load_2d(nx + 2048, &xmap, 8, (int)(next * kRows), nb);
           tma_pending = true;
           pend_bar = nb;
           pend_ph = ph_tma[buf ^ 1];
@@ -145,8 +180,8 @@ __global__ void __launch_bounds__(kMlpThreads, kMlpCtasPerSm)
     }
     ph_mma ^= 1u;
     fence_after();
-    const float flag = __bfloat162float(
-        *reinterpret_cast<const __nv_bfloat16 *>(sm + kSX + buf * 2048 + row * 16 + 10));
+    const float flag = __bfloat162float(*reinterpret_cast<const __nv_bfloat16 *>(
+        sm + kSX + buf * kXB + M::FlagCol + row * 16 + M::FlagByte));
     {
       float d[32];
       tmem_ld32(tmem + lane_base + 0, d);
@@ -213,9 +248,15 @@ __global__ void __launch_bounds__(kMlpThreads, kMlpCtasPerSm)
       if (p < P) {
         float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
         if (flag != 0.0f) {
-          o.x = fmaxf(d[0], 0.0f);
-          o.y = fmaxf(d[1], 0.0f);
-          o.z = fmaxf(d[2], 0.0f);
+          if (SIGMOID) {
+            o.x = 1.0f / (1.0f + __expf(-d[0]));
+            o.y = 1.0f / (1.0f + __expf(-d[1]));
+            o.z = 1.0f / (1.0f + __expf(-d[2]));
+          } else {
+            o.x = fmaxf(d[0], 0.0f);
+            o.y = fmaxf(d[1], 0.0f);
+            o.z = fmaxf(d[2], 0.0f);
+          }
         }
         F[p] = o;
       }
@@ -256,17 +297,22 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 using namespace star;
 
-cudaError_t star_launch_mlp_bf16(const star_nt_mlp *w, const void *x, float *f, int64_t P,
-                                 int32_t *d_status, cudaStream_t st) {
-  static_assert(kSmemUsed + 1024 <= kSmemBytes, "shared memory map");
+// Launch of k_mlp_bf16<NIN, SIGMOID> over P rows of X (bf16, rows of 8
+// elements for NIN = 5, 16 for NIN = 11; 256-byte aligned).
+template <int NIN, bool SIGMOID>
+static cudaError_t launch_mlp_bf16(const star_nt_mlp *w, const void *x, float *f, int64_t P,
+                                   int32_t *d_status, cudaStream_t st) {
+  using M = MlpMap<NIN>;
+  static_assert(M::Used + 1024 <= M::Bytes, "shared memory map");
   if (P <= 0) return cudaSuccess;
   if (P > 0x7fffffffLL) return cudaErrorInvalidValue;
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
   CUtensorMap map;
-  const cuuint64_t dims[2] = {8, (cuuint64_t)P};
-  const cuuint64_t strides[1] = {16};
-  const cuuint32_t box[2] = {8, (cuuint32_t)kRows};
+  constexpr cuuint64_t kCols = NIN == 5 ? 8 : 16;
+  const cuuint64_t dims[2] = {kCols, (cuuint64_t)P};
+  const cuuint64_t strides[1] = {2 * kCols};
+  const cuuint32_t box[2] = {8, (cuuint32_t)kRows};   // one core column of a 128-row tile
   const cuuint32_t estr[2] = {1, 1};
   if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(x), dims, strides, box, estr,
           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -274,7 +320,7 @@ cudaError_t star_launch_mlp_bf16(const star_nt_mlp *w, const void *x, float *f, 
     return cudaErrorInvalidValue;
   static bool attr = false;
   if (!attr) {
-    if (cudaFuncSetAttribute(k_mlp_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) !=
+    if (cudaFuncSetAttribute(k_mlp_bf16<NIN, SIGMOID>, cudaFuncAttributeMaxDynamicSharedMemorySize, M::Bytes) !=
         cudaSuccess)
       return cudaErrorInvalidValue;
     attr = true;
@@ -285,10 +331,20 @@ cudaError_t star_launch_mlp_bf16(const star_nt_mlp *w, const void *x, float *f, 
   const long long ntiles = (P + kRows - 1) / kRows;
   long long grid = (long long)sms * kMlpCtasPerSm;
   if (grid > ntiles) grid = ntiles;
-  k_mlp_bf16<<<(unsigned)grid, kMlpThreads, kSmemBytes, st>>>(map, w->w1, w->b1, w->w2, w->b2, w->w3,
-                                                              w->b3, reinterpret_cast<float4 *>(f), P,
-                                                              d_status, wait_limit_ns());
+  k_mlp_bf16<NIN, SIGMOID><<<(unsigned)grid, kMlpThreads, M::Bytes, st>>>(
+      map, w->w1, w->b1, w->w2, w->b2, w->w3, w->b3, reinterpret_cast<float4 *>(f), P, d_status,
+      wait_limit_ns());
   return cudaGetLastError();
+}
+
+cudaError_t star_launch_mlp_bf16(const star_nt_mlp *w, const void *x, float *f, int64_t P,
+                                 int32_t *d_status, cudaStream_t st) {
+  return launch_mlp_bf16<5, false>(w, x, f, P, d_status, st);
+}
+
+cudaError_t star_launch_dfaoit_bf16(const star_nt_mlp *w, const void *x, float *f, int64_t P,
+                                    int32_t *d_status, cudaStream_t st) {
+  return launch_mlp_bf16<11, true>(w, x, f, P, d_status, st);
 }
 
 namespace star {
@@ -296,7 +352,8 @@ namespace star {
 cudaError_t preload_mlp_tc() {
   cudaFuncAttributes a;
   cudaError_t e = cudaSuccess, r;
-  if ((r = cudaFuncGetAttributes(&a, k_mlp_bf16)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_mlp_bf16<5, false>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_mlp_bf16<11, true>)) != cudaSuccess) e = r;
   return e;
 }
 }  // namespace star

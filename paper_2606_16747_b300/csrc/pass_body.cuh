@@ -17,7 +17,16 @@
 
 namespace star {
 
-enum PassMode { kTop1 = 1, kTop2 = 2, kTail = 3, kFused = 4 };
+// kFusedDfaoit: the plain pipeline's single pass with the network input of
+// the DFAOIT comparison network (its tail sums add the straight colours).
+enum PassMode { kTop1 = 1, kTop2 = 2, kTail = 3, kFused = 4, kFusedDfaoit = 5 };
+
+// r8 | g8 << 21 | b8 << 42: per-channel sums of straight colours fit 21 bits
+// for up to 8224 fragments per pixel
+__device__ __forceinline__ unsigned long long spread_rgb(uint32_t c8) {
+  return (unsigned long long)(c8 & 255u) | ((unsigned long long)((c8 >> 8) & 255u) << 21) |
+         ((unsigned long long)((c8 >> 16) & 255u) << 42);
+}
 
 struct PassOut {
   int32_t *id1;
@@ -36,12 +45,14 @@ struct PassAcc {
   int i1, i2;
   uint32_t N, opq;
   unsigned long long rg, ba, lg;
+  unsigned long long cs;  // straight colour sums (kFusedDfaoit only)
 
   __device__ __forceinline__ void reset() {
     z1 = z2 = INFINITY;
     i1 = i2 = 0x7fffffff;
     N = opq = 0u;
     rg = ba = lg = 0ull;
+    cs = 0ull;
   }
 
   // A fragment deeper than the current k-th nearest cannot enter the top k:
@@ -63,6 +74,7 @@ struct PassAcc {
       ba += T.ba;
       lg += T.lg;
       opq += T.opq;
+      if (MODE == kFusedDfaoit) cs += spread_rgb(T.c8);
     }
     if (MODE == kTop1) {
       const float z = frag_depth(T, e0, e2);
@@ -120,10 +132,12 @@ struct PassAcc {
       if (has1) {
         const TriSetup &S = setups[i1];
         rg -= S.rg; ba -= S.ba; lg -= S.lg; opq -= S.opq;
+        if (MODE == kFusedDfaoit) cs -= spread_rgb(S.c8);
       }
       if (has2) {
         const TriSetup &S = setups[i2];
         rg -= S.rg; ba -= S.ba; lg -= S.lg; opq -= S.opq;
+        if (MODE == kFusedDfaoit) cs -= spread_rgb(S.c8);
       }
       const uint32_t A = (uint32_t)(ba >> 32), Sr = (uint32_t)rg, Sg = (uint32_t)(rg >> 32),
                      Sb = (uint32_t)ba;
@@ -131,12 +145,17 @@ struct PassAcc {
       if (po.n) po.n[p] = N;
       if (po.tail) po.tail[p] = make_uint4(A, Sr, Sg, Sb);
       if (po.t_tail) po.t_tail[p] = t;
-      if (MODE == kFused) {
+      if (MODE == kFused || MODE == kFusedDfaoit) {
         float r1 = 0, g1 = 0, b1 = 0, a1 = 0, r2 = 0, g2 = 0, b2 = 0, a2 = 0;
         if (has1) unpack_rgba(__ldg(rgba8 + i1), r1, g1, b1, a1);
         if (has2) unpack_rgba(__ldg(rgba8 + i2), r2, g2, b2, a2);
-        write_features(fo, p, a1, r1, g1, b1, a2 * r2, a2 * g2, a2 * b2, a2, (float)N, (float)A,
-                       (float)Sr, (float)Sg, (float)Sb, t, N > 2);
+        if (MODE == kFused)
+          write_features(fo, p, a1, r1, g1, b1, a2 * r2, a2 * g2, a2 * b2, a2, (float)N, (float)A,
+                         (float)Sr, (float)Sg, (float)Sb, t, N > 2);
+        else
+          write_dfaoit_features(fo, p, a1, r1, g1, b1, a2 * r2, a2 * g2, a2 * b2, a2, N, (float)A,
+                                (float)Sr, (float)Sg, (float)Sb, (float)(uint32_t)(cs & 0x1FFFFFu),
+                                (float)(uint32_t)((cs >> 21) & 0x1FFFFFu), (float)(uint32_t)(cs >> 42), t);
       }
     }
   }

@@ -352,6 +352,25 @@ extern "C" star_nt_status star_nt_build_inputs(const star_nt_scene *scene, const
   return star_nt_upscale_features(scene, b2, b3, l1, l2, l3, W, H, params, out, stream);
 }
 
+extern "C" star_nt_status star_nt_build_inputs_dfaoit(const star_nt_scene *scene, const star_nt_bins *bins,
+                                                      const star_nt_layers *layers1, int32_t W, int32_t H,
+                                                      const star_nt_params *params,
+                                                      const star_nt_features *out, int32_t *d_status,
+                                                      void *stream) {
+  (void)d_status;
+  FeatOut fo;
+  if (!scene || !bins || !bins->mem || !make_feat(params, out, fo)) return STAR_NT_ERR_ARG;
+  if (W <= 0 || H <= 0 || bins->max_w < W || bins->max_h < H) return STAR_NT_ERR_ARG;
+  if (!layers_ok(layers1)) return STAR_NT_ERR_ARG;
+  if (scene->n_tris > 0 && !scene->rgba8) return STAR_NT_ERR_ARG;
+  if (fo.x_dtype == STAR_NT_BF16 && ((uintptr_t)out->x & 255u)) return STAR_NT_ERR_ARG;  // TMA source
+  BinsView v = bins_view(*bins);
+  PassOut o = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  if (layers1) o = pass_out(layers1);
+  k_pass<kFusedDfaoit><<<tiles_of(bins), 128, 0, (cudaStream_t)stream>>>(v, scene->rgba8, o, fo);
+  return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
+}
+
 namespace star {
 // Loads this file's kernels onto the current device (see star_nt_preload).
 cudaError_t preload_passes() {
@@ -361,6 +380,7 @@ cudaError_t preload_passes() {
   if ((r = cudaFuncGetAttributes(&a, k_pass<kTop2>)) != cudaSuccess) e = r;
   if ((r = cudaFuncGetAttributes(&a, k_pass<kTail>)) != cudaSuccess) e = r;
   if ((r = cudaFuncGetAttributes(&a, k_pass<kFused>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_pass<kFusedDfaoit>)) != cudaSuccess) e = r;
   if ((r = cudaFuncGetAttributes(&a, k_pass_merged)) != cudaSuccess) e = r;
   if ((r = cudaFuncGetAttributes(&a, k_passes<4, 6>)) != cudaSuccess) e = r;
   if ((r = cudaFuncGetAttributes(&a, k_passes<8, 6>)) != cudaSuccess) e = r;

@@ -165,7 +165,7 @@ __device__ __forceinline__ void triangle_setup_x4(int t, bool store, const float
   S.opq = a8 == 255 ? 1u : 0u;
   S.rg = (a8 * r8) | ((a8 * g8) << 32);
   S.ba = (a8 * b8) | (a8 << 32);
-  S.pad = 0;
+  S.c8 = (uint32_t)col & 0xFFFFFFu;
   S.lg = g_lg.v[a8];
 }
 

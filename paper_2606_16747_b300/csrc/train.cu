@@ -119,73 +119,105 @@ __global__ void k_sum_partials(const float *__restrict__ partial, int n, float *
 }
 
 // ---------------------------------------------------------------------------
-// Backpropagation.  Stage 1: per sample, recompute the forward pass and the
-// per-layer gradients g3 = dL/dz3, g2 = dL/dz2, g1 = dL/dz1 (z: pre-ReLU),
-// stored with the activations: row = [h1(32) h2(16) g1(32) g2(16) g3(3) x(5)].
-// Stage 2: per chunk of samples, every parameter's partial sum.  Stage 3:
-// the partial sums added in chunk order (deterministic).
-constexpr int kRow = 104;   // 32 + 16 + 32 + 16 + 3 + 5, padded
+// Backpropagation of the networks NIN -> 32 -> 16 -> 3 with ReLU hidden
+// layers: the tail MLP (NIN = 5, ReLU output, 771 parameters) and the DFAOIT
+// comparison network (NIN = 11, sigmoid output, 963 parameters).  Stage 1:
+// per sample, recompute the forward pass and the per-layer gradients
+// g3 = dL/dz3, g2 = dL/dz2, g1 = dL/dz1 (z: pre-activation), stored with the
+// activations: row = [h1(32) h2(16) g1(32) g2(16) g3(3) x(NIN)].  Stage 2: per
+// chunk of samples, every parameter's partial sum.  Stage 3: the partial sums
+// added in chunk order (deterministic).
+template <int NIN>
+struct Net {
+  static constexpr int kRow = (99 + NIN + 3) / 4 * 4;  // row length, padded to 4 floats
+  static constexpr int kW1 = 0, kB1 = 32 * NIN, kW2 = kB1 + 32, kB2 = kW2 + 512, kW3 = kB2 + 16,
+                       kB3 = kW3 + 48, kParams = kB3 + 3;
+  static constexpr int kXStride = NIN == 5 ? 2 : 4;     // float4 per input row ([P][8] or [P][16])
+};
 constexpr int kChunkS = 1024;
+constexpr int kRowMax = Net<11>::kRow;
+constexpr int kParamsMax = Net<11>::kParams;
 
+template <int NIN, bool SIGMOID>
 __global__ void __launch_bounds__(256) k_mlp_bwd_rows(const float *__restrict__ w1, const float *__restrict__ b1,
                                                       const float *__restrict__ w2, const float *__restrict__ b2,
                                                       const float *__restrict__ w3, const float *__restrict__ b3,
                                                       const float4 *__restrict__ X, const float4 *__restrict__ dY,
                                                       long long B, float *__restrict__ rows) {
-  __shared__ float s[776];
-  for (int i = threadIdx.x; i < 160; i += 256) s[i] = w1[i];
-  for (int i = threadIdx.x; i < 512; i += 256) s[192 + i] = w2[i];
-  if (threadIdx.x < 32) s[160 + threadIdx.x] = b1[threadIdx.x];
-  if (threadIdx.x < 16) s[704 + threadIdx.x] = b2[threadIdx.x];
-  if (threadIdx.x < 48) s[720 + threadIdx.x] = w3[threadIdx.x];
-  if (threadIdx.x < 3) s[768 + threadIdx.x] = b3[threadIdx.x];
+  using N = Net<NIN>;
+  __shared__ float s[N::kParams + 1];
+  for (int i = threadIdx.x; i < 32 * NIN; i += 256) s[N::kW1 + i] = w1[i];
+  for (int i = threadIdx.x; i < 512; i += 256) s[N::kW2 + i] = w2[i];
+  if (threadIdx.x < 32) s[N::kB1 + threadIdx.x] = b1[threadIdx.x];
+  if (threadIdx.x < 16) s[N::kB2 + threadIdx.x] = b2[threadIdx.x];
+  if (threadIdx.x < 48) s[N::kW3 + threadIdx.x] = w3[threadIdx.x];
+  if (threadIdx.x < 3) s[N::kB3 + threadIdx.x] = b3[threadIdx.x];
   __syncthreads();
   const long long i = (long long)blockIdx.x * 256 + threadIdx.x;
   if (i >= B) return;
-  const float4 xa = X[2 * i], xb = X[2 * i + 1];
-  const float x[5] = {xa.x, xa.y, xa.z, xa.w, xb.x};
+  float x[NIN];
+  {
+    float v[4 * N::kXStride];
+#pragma unroll
+    for (int q = 0; q < N::kXStride; ++q) {
+      const float4 a = X[N::kXStride * i + q];
+      v[4 * q] = a.x;
+      v[4 * q + 1] = a.y;
+      v[4 * q + 2] = a.z;
+      v[4 * q + 3] = a.w;
+    }
+#pragma unroll
+    for (int k = 0; k < NIN; ++k) x[k] = v[k];
+  }
   float h1[32], h2[16], z3[3];
 #pragma unroll
   for (int o = 0; o < 32; ++o) {
-    float a = s[160 + o];
+    float a = s[N::kB1 + o];
 #pragma unroll
-    for (int k = 0; k < 5; ++k) a = fmaf(s[5 * o + k], x[k], a);
+    for (int k = 0; k < NIN; ++k) a = fmaf(s[N::kW1 + NIN * o + k], x[k], a);
     h1[o] = fmaxf(a, 0.0f);
   }
 #pragma unroll
   for (int o = 0; o < 16; ++o) {
-    float a = s[704 + o];
+    float a = s[N::kB2 + o];
 #pragma unroll
-    for (int k = 0; k < 32; ++k) a = fmaf(s[192 + 32 * o + k], h1[k], a);
+    for (int k = 0; k < 32; ++k) a = fmaf(s[N::kW2 + 32 * o + k], h1[k], a);
     h2[o] = fmaxf(a, 0.0f);
   }
 #pragma unroll
   for (int o = 0; o < 3; ++o) {
-    float a = s[768 + o];
+    float a = s[N::kB3 + o];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) a = fmaf(s[720 + 16 * o + k], h2[k], a);
+    for (int k = 0; k < 16; ++k) a = fmaf(s[N::kW3 + 16 * o + k], h2[k], a);
     z3[o] = a;
   }
   const float4 d = dY[i];
   const float dd[3] = {d.x, d.y, d.z};
   float g3[3], g2[16], g1[32];
 #pragma unroll
-  for (int o = 0; o < 3; ++o) g3[o] = z3[o] > 0.0f ? dd[o] : 0.0f;
+  for (int o = 0; o < 3; ++o) {
+    if (SIGMOID) {
+      const float f = 1.0f / (1.0f + expf(-z3[o]));
+      g3[o] = dd[o] * f * (1.0f - f);
+    } else {
+      g3[o] = z3[o] > 0.0f ? dd[o] : 0.0f;
+    }
+  }
 #pragma unroll
   for (int k = 0; k < 16; ++k) {
     float a = 0.0f;
 #pragma unroll
-    for (int o = 0; o < 3; ++o) a = fmaf(s[720 + 16 * o + k], g3[o], a);
+    for (int o = 0; o < 3; ++o) a = fmaf(s[N::kW3 + 16 * o + k], g3[o], a);
     g2[k] = h2[k] > 0.0f ? a : 0.0f;
   }
 #pragma unroll
   for (int k = 0; k < 32; ++k) {
     float a = 0.0f;
 #pragma unroll
-    for (int o = 0; o < 16; ++o) a = fmaf(s[192 + 32 * o + k], g2[o], a);
+    for (int o = 0; o < 16; ++o) a = fmaf(s[N::kW2 + 32 * o + k], g2[o], a);
     g1[k] = h1[k] > 0.0f ? a : 0.0f;
   }
-  float *row = rows + (size_t)i * kRow;
+  float *row = rows + (size_t)i * N::kRow;
 #pragma unroll
   for (int k = 0; k < 32; ++k) row[k] = h1[k];
 #pragma unroll
@@ -197,39 +229,43 @@ __global__ void __launch_bounds__(256) k_mlp_bwd_rows(const float *__restrict__ 
 #pragma unroll
   for (int k = 0; k < 3; ++k) row[96 + k] = g3[k];
 #pragma unroll
-  for (int k = 0; k < 5; ++k) row[99 + k] = x[k];
+  for (int k = 0; k < NIN; ++k) row[99 + k] = x[k];
 }
 
 // parameter p (in w1, b1, w2, b2, w3, b3 order) as a product of two row
 // entries (second index < 0: bias, factor 1)
+template <int NIN>
 __device__ __forceinline__ void param_factors(int p, int &a, int &b) {
-  if (p < 160) { a = 48 + p / 5; b = 99 + p % 5; return; }           // dW1[o][k] = g1[o] x[k]
-  if (p < 192) { a = 48 + (p - 160); b = -1; return; }                // db1
-  if (p < 704) { const int q = p - 192; a = 80 + q / 32; b = q % 32; return; }  // dW2 = g2 h1
-  if (p < 720) { a = 80 + (p - 704); b = -1; return; }                // db2
-  if (p < 768) { const int q = p - 720; a = 96 + q / 16; b = 32 + q % 16; return; }  // dW3 = g3 h2
-  a = 96 + (p - 768); b = -1;                                         // db3
+  using N = Net<NIN>;
+  if (p < N::kB1) { a = 48 + p / NIN; b = 99 + p % NIN; return; }            // dW1[o][k] = g1[o] x[k]
+  if (p < N::kW2) { a = 48 + (p - N::kB1); b = -1; return; }                 // db1
+  if (p < N::kB2) { const int q = p - N::kW2; a = 80 + q / 32; b = q % 32; return; }  // dW2 = g2 h1
+  if (p < N::kW3) { a = 80 + (p - N::kB2); b = -1; return; }                 // db2
+  if (p < N::kB3) { const int q = p - N::kW3; a = 96 + q / 16; b = 32 + q % 16; return; }  // dW3 = g3 h2
+  a = 96 + (p - N::kB3); b = -1;                                             // db3
 }
 
+template <int NIN>
 __global__ void __launch_bounds__(256) k_mlp_bwd_partial(const float *__restrict__ rows, long long B,
                                                          float *__restrict__ partial) {
-  __shared__ float s_rows[32 * kRow];
+  using N = Net<NIN>;
+  __shared__ float s_rows[32 * N::kRow];
   const long long s0 = (long long)blockIdx.x * kChunkS;
   float acc[4] = {0.f, 0.f, 0.f, 0.f};
   int fa[4], fb[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int p = threadIdx.x + 256 * j;
-    if (p < 771) param_factors(p, fa[j], fb[j]);
+    if (p < N::kParams) param_factors<NIN>(p, fa[j], fb[j]);
     else { fa[j] = 0; fb[j] = -2; }
   }
   for (long long c = s0; c < s0 + kChunkS && c < B; c += 32) {
     const int m = (int)min((long long)32, B - c);
     __syncthreads();
-    for (int k = threadIdx.x; k < m * kRow; k += 256) s_rows[k] = rows[(size_t)c * kRow + k];
+    for (int k = threadIdx.x; k < m * N::kRow; k += 256) s_rows[k] = rows[(size_t)c * N::kRow + k];
     __syncthreads();
     for (int r = 0; r < m; ++r) {
-      const float *row = s_rows + r * kRow;
+      const float *row = s_rows + r * N::kRow;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         if (fb[j] == -2) continue;
@@ -240,15 +276,16 @@ __global__ void __launch_bounds__(256) k_mlp_bwd_partial(const float *__restrict
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int p = threadIdx.x + 256 * j;
-    if (p < 771) partial[(size_t)blockIdx.x * 771 + p] = acc[j];
+    if (p < N::kParams) partial[(size_t)blockIdx.x * N::kParams + p] = acc[j];
   }
 }
 
-__global__ void k_mlp_bwd_reduce(const float *__restrict__ partial, int chunks, float *__restrict__ grad) {
+__global__ void k_mlp_bwd_reduce(const float *__restrict__ partial, int chunks, int n_params,
+                                 float *__restrict__ grad) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= 771) return;
+  if (p >= n_params) return;
   float t = 0.0f;
-  for (int c = 0; c < chunks; ++c) t += partial[(size_t)c * 771 + p];
+  for (int c = 0; c < chunks; ++c) t += partial[(size_t)c * n_params + p];
   grad[p] = t;
 }
 
@@ -294,9 +331,9 @@ static int mse_blocks(int64_t B) {
 
 extern "C" size_t star_nt_train_ws_bytes(int64_t B) {
   if (B <= 0) return 0;
-  const size_t rows = (size_t)B * kRow * 4;
+  const size_t rows = (size_t)B * kRowMax * 4;
   const size_t chunks = (size_t)((B + kChunkS - 1) / kChunkS);
-  return align_up(rows, 256) + align_up(chunks * 771 * 4, 256) + align_up(4 * 1024, 256);
+  return align_up(rows, 256) + align_up(chunks * kParamsMax * 4, 256) + align_up(4 * 1024, 256);
 }
 
 static star_nt_status mse_grad(const float *f, const float *y, const float *w, int64_t B, float *dy,
@@ -326,23 +363,36 @@ extern "C" star_nt_status star_nt_wmse_grad(const float *f, const float *y, cons
   return mse_grad(f, y, w, B, dy, loss, ws, ws_bytes, stream);
 }
 
-extern "C" star_nt_status star_nt_mlp_backward(const star_nt_mlp *w, const float *x, const float *dy,
-                                               int64_t B, float *grad, void *ws, size_t ws_bytes,
-                                               void *stream) {
+template <int NIN, bool SIGMOID>
+static star_nt_status mlp_backward(const star_nt_mlp *w, const float *x, const float *dy, int64_t B,
+                                   float *grad, void *ws, size_t ws_bytes, void *stream) {
+  using N = Net<NIN>;
   if (!w || !w->w1 || !w->b1 || !w->w2 || !w->b2 || !w->w3 || !w->b3 || !x || !dy || !grad || B <= 0 ||
       !ws || ws_bytes < star_nt_train_ws_bytes(B))
     return STAR_NT_ERR_ARG;
   if (((uintptr_t)x & 15u) || ((uintptr_t)dy & 15u) || ((uintptr_t)ws & 255u)) return STAR_NT_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   float *rows = reinterpret_cast<float *>(ws);
-  float *partial = reinterpret_cast<float *>((char *)ws + align_up((size_t)B * kRow * 4, 256));
+  float *partial = reinterpret_cast<float *>((char *)ws + align_up((size_t)B * kRowMax * 4, 256));
   const int chunks = (int)((B + kChunkS - 1) / kChunkS);
-  k_mlp_bwd_rows<<<(unsigned)((B + 255) / 256), 256, 0, st>>>(
+  k_mlp_bwd_rows<NIN, SIGMOID><<<(unsigned)((B + 255) / 256), 256, 0, st>>>(
       w->w1, w->b1, w->w2, w->b2, w->w3, w->b3, reinterpret_cast<const float4 *>(x),
       reinterpret_cast<const float4 *>(dy), B, rows);
-  k_mlp_bwd_partial<<<chunks, 256, 0, st>>>(rows, B, partial);
-  k_mlp_bwd_reduce<<<4, 256, 0, st>>>(partial, chunks, grad);
+  k_mlp_bwd_partial<NIN><<<chunks, 256, 0, st>>>(rows, B, partial);
+  k_mlp_bwd_reduce<<<(N::kParams + 255) / 256, 256, 0, st>>>(partial, chunks, N::kParams, grad);
   return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
+}
+
+extern "C" star_nt_status star_nt_mlp_backward(const star_nt_mlp *w, const float *x, const float *dy,
+                                               int64_t B, float *grad, void *ws, size_t ws_bytes,
+                                               void *stream) {
+  return mlp_backward<5, false>(w, x, dy, B, grad, ws, ws_bytes, stream);
+}
+
+extern "C" star_nt_status star_nt_dfaoit_backward(const star_nt_mlp *w, const float *x, const float *dy,
+                                                  int64_t B, float *grad, void *ws, size_t ws_bytes,
+                                                  void *stream) {
+  return mlp_backward<11, true>(w, x, dy, B, grad, ws, ws_bytes, stream);
 }
 
 extern "C" star_nt_status star_nt_adam(float *params, const float *grad, float *m, float *v, int64_t n,
@@ -364,8 +414,10 @@ cudaError_t preload_train() {
   if ((r = cudaFuncGetAttributes(&a, k_abuffer)) != cudaSuccess) e = r;
   if ((r = cudaFuncGetAttributes(&a, k_mse)) != cudaSuccess) e = r;
   if ((r = cudaFuncGetAttributes(&a, k_sum_partials)) != cudaSuccess) e = r;
-  if ((r = cudaFuncGetAttributes(&a, k_mlp_bwd_rows)) != cudaSuccess) e = r;
-  if ((r = cudaFuncGetAttributes(&a, k_mlp_bwd_partial)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_mlp_bwd_rows<5, false>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_mlp_bwd_partial<5>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_mlp_bwd_rows<11, true>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_mlp_bwd_partial<11>)) != cudaSuccess) e = r;
   if ((r = cudaFuncGetAttributes(&a, k_mlp_bwd_reduce)) != cudaSuccess) e = r;
   if ((r = cudaFuncGetAttributes(&a, k_adam)) != cudaSuccess) e = r;
   return e;

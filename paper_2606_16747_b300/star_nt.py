@@ -33,7 +33,8 @@ EXPORTS = ("star_nt_version", "star_nt_status_string", "star_nt_default_params",
            "star_nt_geometry_passes_resolve", "star_nt_resolve_fp8x2", "star_nt_set_wait_limit",
            "star_nt_wait_limit", "star_nt_default_frame_options", "star_nt_create", "star_nt_destroy",
            "star_nt_workspace_size", "star_nt_bind_workspace", "star_nt_frame", "star_nt_tune",
-           "star_nt_ctx_tuning", "star_nt_ctx_set_tuning", "star_nt_ctx_pass_state", "star_nt_resolve_mlp")
+           "star_nt_ctx_tuning", "star_nt_ctx_set_tuning", "star_nt_ctx_pass_state", "star_nt_resolve_mlp",
+           "star_nt_build_inputs_dfaoit", "star_nt_infer_dfaoit", "star_nt_dfaoit_backward")
 
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
@@ -210,6 +211,11 @@ def lib():
         L.star_nt_ctx_set_tuning.argtypes = [_P, ctypes.POINTER(Tuning), _I32]
         L.star_nt_ctx_pass_state.argtypes = [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
                                              ctypes.POINTER(_P)]
+        L.star_nt_build_inputs_dfaoit.argtypes = [ctypes.POINTER(Scene), ctypes.POINTER(Bins),
+                                                  ctypes.POINTER(Layers), _I32, _I32, ctypes.POINTER(Params),
+                                                  ctypes.POINTER(Features), _P, _P]
+        L.star_nt_infer_dfaoit.argtypes = [ctypes.POINTER(Mlp), _I32, _P, _P, _I64, _P, _P]
+        L.star_nt_dfaoit_backward.argtypes = [ctypes.POINTER(Mlp), _P, _P, _I64, _P, _P, ctypes.c_size_t, _P]
         L.star_nt_set_wait_limit.argtypes = [ctypes.c_uint64]
         L.star_nt_wait_limit.restype = ctypes.c_uint64
         for name in EXPORTS:
@@ -417,6 +423,27 @@ def resolve_mlp(scene: Scene, bins2, bins3, layers1, layers2, layers3, W, H, par
         ctypes.byref(scene), ctypes.byref(bins2.c), ctypes.byref(bins3.c), *[ctypes.byref(l) for l in ls],
         W, H, ctypes.byref(params), ctypes.byref(w), int(mlp_type), _ptr(rgba32f), _ptr(rgba8), _ptr(status),
         _stream(stream)))
+
+
+def build_inputs_dfaoit(scene: Scene, bins, layers1, W, H, params: Params, x, x_dtype, front, status=None,
+                        stream=None):
+    """The DFAOIT comparison network's input x [W*H][16] and front terms."""
+    feat = Features(x.data_ptr(), x_dtype, front.data_ptr())
+    l = layers_struct(layers1)
+    _check("star_nt_build_inputs_dfaoit", lib().star_nt_build_inputs_dfaoit(
+        ctypes.byref(scene), ctypes.byref(bins.c), ctypes.byref(l) if l is not None else None, W, H,
+        ctypes.byref(params), ctypes.byref(feat), _ptr(status), _stream(stream)))
+
+
+def infer_dfaoit(w: Mlp, x_dtype, x, f, P, status=None, stream=None):
+    _check("star_nt_infer_dfaoit", lib().star_nt_infer_dfaoit(ctypes.byref(w), x_dtype, _ptr(x), _ptr(f), int(P),
+                                                              _ptr(status), _stream(stream)))
+
+
+def dfaoit_backward(w: Mlp, x, dy, B, grad, ws, stream=None):
+    _check("star_nt_dfaoit_backward", lib().star_nt_dfaoit_backward(ctypes.byref(w), _ptr(x), _ptr(dy), int(B),
+                                                                    _ptr(grad), _ptr(ws), ws.numel(),
+                                                                    _stream(stream)))
 
 
 def mlp_struct(w) -> Mlp:
