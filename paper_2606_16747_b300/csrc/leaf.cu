@@ -137,7 +137,10 @@ __global__ void __launch_bounds__(PIX == 2 ? 128 : 256, MINB) k_passes_leaf(Leaf
                                                         const uint8_t *__restrict__ modes,
                                                         const uint32_t *__restrict__ rgba8,
                                                         uint32_t *queue, int32_t *status) {
-  __shared__ TileStage stage;
+  __shared__ union {
+    TileStage t;  // one pixel per thread: for_each_fragment
+    WalkStage w;  // two pixels per thread: walk_tile2
+  } stage;
   __shared__ int s_item;
   const int total = a.tile_start[a.n_targets];
   for (;;) {
@@ -164,13 +167,13 @@ __global__ void __launch_bounds__(PIX == 2 ? 128 : 256, MINB) k_passes_leaf(Leaf
     }
     const uint32_t m = __ldg(modes + item);
     if (PIX == 2) {
-      if (m & 2u) pass_body2<kTail, BW>(bv, rgba8, a.out[k], stage, tile);
-      else if (m & 1u) pass_body2<kTop2, BW>(bv, rgba8, a.out[k], stage, tile);
-      else if (k == 0) pass_body2<kTop1, BW>(bv, rgba8, a.out[0], stage, tile);
+      if (m & 2u) pass_body2<kTail, BW>(bv, rgba8, a.out[k], stage.w, tile);
+      else if (m & 1u) pass_body2<kTop2, BW>(bv, rgba8, a.out[k], stage.w, tile);
+      else if (k == 0) pass_body2<kTop1, BW>(bv, rgba8, a.out[0], stage.w, tile);
     } else {
-      if (m & 2u) pass_body<kTail, BW>(bv, rgba8, a.out[k], FeatOut{}, stage, tile);
-      else if (m & 1u) pass_body<kTop2, BW>(bv, rgba8, a.out[k], FeatOut{}, stage, tile);
-      else if (k == 0) pass_body<kTop1, BW>(bv, rgba8, a.out[0], FeatOut{}, stage, tile);
+      if (m & 2u) pass_body<kTail, BW>(bv, rgba8, a.out[k], FeatOut{}, stage.t, tile);
+      else if (m & 1u) pass_body<kTop2, BW>(bv, rgba8, a.out[k], FeatOut{}, stage.t, tile);
+      else if (k == 0) pass_body<kTop1, BW>(bv, rgba8, a.out[0], FeatOut{}, stage.t, tile);
     }
   }
 }

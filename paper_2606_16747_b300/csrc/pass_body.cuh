@@ -14,6 +14,7 @@
 #include "common.cuh"
 #include "features.cuh"
 #include "raster_tile.cuh"
+#include "tile_walk.cuh"
 
 namespace star {
 
@@ -66,29 +67,36 @@ struct PassAcc {
     return inside ? (MODE == kTop1 ? z1 : z2) : -INFINITY;
   }
 
+  // A fragment of T: the tail sums (MODE >= kTail).
   template <int MODE>
-  __device__ __forceinline__ void visit(const TriSetup &T, int id, long long e0, long long e2) {
-    if (MODE >= kTail) {
-      ++N;
-      rg += T.rg;
-      ba += T.ba;
-      lg += T.lg;
-      opq += T.opq;
-      if (MODE == kFusedDfaoit) cs += spread_rgb(T.c8);
-    }
-    if (MODE == kTop1) {
-      const float z = frag_depth(T, e0, e2);
+  __device__ __forceinline__ void accumulate(const TriSetup &T) {
+    ++N;
+    rg += T.rg;
+    ba += T.ba;
+    lg += T.lg;
+    opq += T.opq;
+    if (MODE == kFusedDfaoit) cs += spread_rgb(T.c8);
+  }
+
+  // A fragment at depth z offered to the KM nearest, ordered by (depth, id).
+  template <int KM>
+  __device__ __forceinline__ void insert(float z, int id) {
+    if (KM == kTop1) {
       if (z < z1 || (z == z1 && id < i1)) { z1 = z; i1 = id; }
-    } else if (!(T.zlo > z2)) {
-      const float z = frag_depth(T, e0, e2);
-      if (z < z2 || (z == z2 && id < i2)) {
-        if (z < z1 || (z == z1 && id < i1)) {
-          z2 = z1; i2 = i1; z1 = z; i1 = id;
-        } else {
-          z2 = z; i2 = id;
-        }
+    } else if (z < z2 || (z == z2 && id < i2)) {
+      if (z < z1 || (z == z1 && id < i1)) {
+        z2 = z1; i2 = i1; z1 = z; i1 = id;
+      } else {
+        z2 = z; i2 = id;
       }
     }
+  }
+
+  template <int MODE>
+  __device__ __forceinline__ void visit(const TriSetup &T, int id, long long e0, long long e2) {
+    if (MODE >= kTail) accumulate<MODE>(T);
+    if (MODE == kTop1) insert<kTop1>(frag_depth(T, e0, e2), id);
+    else if (!(T.zlo > z2)) insert<kTop2>(frag_depth(T, e0, e2), id);
   }
 
   // Network input and front terms of pixel p once every pass ran at the full
@@ -184,11 +192,12 @@ __device__ __forceinline__ void pass_body(const BinsView &bv, const uint32_t *__
   acc.template finish<MODE>(bv.setups, rgba8, po, fo, (size_t)tp.py * W + tp.px);
 }
 
-// pass_body with two pixels per thread (a CTA of 128 threads per tile; see
-// tile_pixel): the triangle loads and the loop are shared by both pixels.
+// pass_body with two pixels per thread (a CTA of 128 threads per tile, see
+// tile_pixel and walk_tile2): the triangle loads and the loop are shared by
+// both pixels.
 template <int MODE, int BW = 8>
 __device__ __forceinline__ void pass_body2(const BinsView &bv, const uint32_t *__restrict__ rgba8,
-                                           const PassOut &po, TileStage &stage, int tile,
+                                           const PassOut &po, WalkStage &stage, int tile,
                                            const FeatOut &fo = FeatOut{}) {
   constexpr int BH = 32 / BW;
   const BinsHeader *hd = bv.hd;
@@ -200,13 +209,7 @@ __device__ __forceinline__ void pass_body2(const BinsView &bv, const uint32_t *_
   PassAcc a0, a1;
   a0.reset();
   a1.reset();
-  for_each_fragment<BW, true, 2>(
-      bv, tile, tp, stage,
-      [&] { return fmaxf(a0.template bound<MODE>(in0), a1.template bound<MODE>(in1)); },
-      [&](int j, const TriSetup &T, uint32_t id, long long e0, long long e2) {
-        if (j == 0) a0.template visit<MODE>(T, (int)id, e0, e2);
-        else a1.template visit<MODE>(T, (int)id, e0, e2);
-      });
+  walk_tile2<MODE, BW>(bv, tile, tp, stage, in0, in1, a0, a1);
   if (in0) a0.template finish<MODE>(bv.setups, rgba8, po, fo, (size_t)tp.py * W + tp.px);
   if (in1) a1.template finish<MODE>(bv.setups, rgba8, po, fo, (size_t)(tp.py + BH) * W + tp.px);
 }

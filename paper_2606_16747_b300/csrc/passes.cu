@@ -14,7 +14,7 @@ namespace star {
 template <int MODE>
 __global__ void __launch_bounds__(128, 8) k_pass(BinsView bv, const uint32_t *__restrict__ rgba8,
                                               PassOut po, FeatOut fo) {
-  __shared__ TileStage stage;
+  __shared__ WalkStage stage;
   pass_body2<MODE>(bv, rgba8, po, stage, blockIdx.x, fo);
 }
 
@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(128, 10) k_pass_merged(BinsView bv, const Bins
                                                       const BinsHeader *hd3,
                                                       const uint32_t *__restrict__ rgba8, PassOut o1,
                                                       PassOut o2, PassOut o3) {
-  __shared__ TileStage stage;
+  __shared__ WalkStage stage;
   const bool m2 = hd2->merged != 0, m3 = hd3->merged != 0;
   if (!m2 && !m3) {
     pass_body2<kTop1>(bv, rgba8, o1, stage, blockIdx.x);
@@ -102,7 +102,7 @@ template <int BW, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_passes2(BinsView v1, BinsView v2, BinsView v3,
                                                     const uint32_t *__restrict__ rgba8, PassOut o1,
                                                     PassOut o2, PassOut o3, uint32_t *queue) {
-  __shared__ TileStage stage;
+  __shared__ WalkStage stage;
   __shared__ int s_item;
   if (v2.hd->resolved) return;  // star_nt_geometry_passes_resolve's launch did the passes
   const bool m2 = v2.hd->merged != 0, m3 = v3.hd->merged != 0;

@@ -39,7 +39,8 @@ struct ResolveArgs {
 constexpr uint32_t kTmemCols = 64;  // 32 columns per MLP tile
 struct __align__(128) FusedSmem {
   union {
-    TileStage stage;
+    TileStage stage;   // one pixel per thread: for_each_fragment
+    WalkStage wstage;  // two pixels per thread: walk_tile2
     uint8_t h[2][8192];
   } u;
   __align__(128) uint8_t ones[2048];
@@ -201,12 +202,7 @@ __device__ __forceinline__ void pass_resolve_body2(const BinsView &bv, const uin
   PassAcc a0, a1;
   a0.reset();
   a1.reset();
-  for_each_fragment<BW, true, 2>(
-      bv, tile, tp, fs.u.stage, [&] { return INFINITY; },  // tail sums: every fragment
-      [&](int j, const TriSetup &T, uint32_t id, long long e0, long long e2) {
-        if (j == 0) a0.template visit<kTail>(T, (int)id, e0, e2);
-        else a1.template visit<kTail>(T, (int)id, e0, e2);
-      });
+  walk_tile2<kTail, BW>(bv, tile, tp, fs.u.wstage, in0, in1, a0, a1);
   float xv0[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, xv1[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   float4 front0 = make_float4(0.f, 0.f, 0.f, 0.f), front1 = front0;
   const size_t p0 = (size_t)tp.py * W + tp.px, p1 = p0 + (size_t)BH * W;
@@ -336,8 +332,9 @@ __global__ void __launch_bounds__(PIX == 2 ? 128 : 256, PIX == 2 ? 8 : 6)
     k_passes_resolve(BinsView v1, BinsView v2, BinsView v3, const uint32_t *__restrict__ rgba8,
                      PassOut o1, ResolveArgs ra, uint32_t *queue, int32_t *status) {
   extern __shared__ uint8_t smem_raw[];  // FusedSmem, 128-byte aligned
-  FusedSmem &fs = *reinterpret_cast<FusedSmem *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) &
-                                                 ~(uintptr_t)127);
+  // rounded up to 128 bytes by pointer arithmetic on the shared array, so
+  // that the compiler keeps every access in the shared address space
+  FusedSmem &fs = *reinterpret_cast<FusedSmem *>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
   __shared__ int s_item;
   const int tid = threadIdx.x;
   if (tid < 32) {
