@@ -762,7 +762,10 @@ star_nt_status star_nt_frame(star_nt_ctx *ctx, const star_nt_scene *scene, const
  * persistent pass launch is timed with CUDA events over ten pass launches,
  * the fastest kept; then, with BF16 and fuse_passes, the raster, pass launch
  * and resolve are timed with the pass launch producing the frame and with
- * the separate resolve, and the faster kept.  Synchronises `stream` (not
+ * the separate resolve, and the faster kept when the current frame has both
+ * reduced passes merged (otherwise the pass launch returns at once either
+ * way, the timings do not compare the two, and the pass launch keeps
+ * producing the frames that merge).  Synchronises `stream` (not
  * allowed inside a capture: STAR_NT_ERR_ARG); writes the outputs of frames
  * it renders; leaves the quadtree state unchanged.  report may be NULL. */
 #define STAR_NT_TUNE_CANDIDATES 9
@@ -773,6 +776,7 @@ typedef struct {
                                                   [1] the pass launch produces the frame */
     star_nt_tuning chosen;
     int32_t fuse_passes;
+    int32_t frame_merged;                      /* 1: both reduced passes merged in the timed frame */
 } star_nt_tune_report;
 star_nt_status star_nt_tune(star_nt_ctx *ctx, const star_nt_scene *scene, const star_nt_mlp *w,
                             const star_nt_cameras *cams, const star_nt_frame_out *out,

@@ -58,11 +58,19 @@ def time_passes(renderer, tuning, reps=10) -> float:
         renderer.tuning, renderer.persistent = old
 
 
+def all_merged(renderer) -> bool:
+    """Whether the renderer's last raster took both reduced passes over into
+    pass 1 (the merged word of the pass-2 and pass-3 bins headers)."""
+    return all(int(renderer.bins[k].mem[32:36].view(torch.int32).item()) != 0 for k in (1, 2))
+
+
 def tune(renderer, candidates=CANDIDATES, reps=10) -> dict:
     """Time every candidate on the renderer's current frame state (bins and
     pass sizes must be those of a real frame) and return the fastest, with the
-    fused-resolve choice when the renderer can make it (a tie, for instance
-    when a reduced pass is not merged in the current frame, keeps it on)."""
+    fused-resolve choice when the renderer can make it.  That choice is only
+    measured on a frame whose reduced passes are both merged: otherwise the
+    pass launch returns at once in either setting and the comparison says
+    nothing, so the launch that resolves stays on."""
     times = {candidate_key(c): time_passes(renderer, tuple(c), reps) for c in candidates}
     best = tuple(min(candidates, key=lambda c: times[candidate_key(c)]))
     out = {"block_w": best[0], "ctas_per_sm": best[1], "pixels_per_thread": best[2], "ms": times}
@@ -79,8 +87,10 @@ def tune(renderer, candidates=CANDIDATES, reps=10) -> dict:
             both[fuse] = time_stages(renderer, ["raster", "passes", "resolve"], reps)
     finally:
         renderer.tuning, renderer.persistent, renderer.fuse_passes = old
-    out["fuse_passes"] = both[True] <= both[False]
-    out["raster_passes_resolve_ms"] = {"pass launch resolves": both[True], "separate resolve": both[False]}
+    merged = all_merged(renderer)
+    out["fuse_passes"] = both[True] <= both[False] or not merged
+    out["raster_passes_resolve_ms"] = {"pass launch resolves": both[True], "separate resolve": both[False],
+                                       "frame merged": merged}
     return out
 
 

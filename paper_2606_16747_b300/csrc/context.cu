@@ -10,6 +10,7 @@
 // the real frame (pass 1 at full size, passes 2 and 3 at the sizes the
 // quadtree chose on the previous frame, network, composite), the interpolated
 // frame that reprojects it, and the quadtree update for the next frame.
+#include <stddef.h>
 #include <string.h>
 
 #include <new>
@@ -398,7 +399,15 @@ extern "C" star_nt_status star_nt_tune(star_nt_ctx *c, const star_nt_scene *scen
         if (s == STAR_NT_OK) s = real_frame(c, v, scene, w, out->rgba32f, out->rgba8, d_status, st);
       });
     }
-    r.fuse_passes = r.frame_ms[1] <= r.frame_ms[0] ? 1 : 0;
+    // the merged words of the pass-2 and pass-3 bins headers after the raster
+    int32_t mg[2] = {0, 0};
+    for (int q = 0; q < 2 && s == STAR_NT_OK; ++q)
+      if (cudaMemcpyAsync(&mg[q], static_cast<char *>(v.bins[q + 1].mem) + offsetof(BinsHeader, merged),
+                          sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        s = STAR_NT_ERR_CUDA;
+    if (s == STAR_NT_OK && cudaStreamSynchronize(st) != cudaSuccess) s = STAR_NT_ERR_CUDA;
+    r.frame_merged = mg[0] != 0 && mg[1] != 0 ? 1 : 0;
+    r.fuse_passes = r.frame_ms[1] <= r.frame_ms[0] || !r.frame_merged ? 1 : 0;
   }
   if (s != STAR_NT_OK || cudaGetLastError() != cudaSuccess) {
     c->tuning = keep;

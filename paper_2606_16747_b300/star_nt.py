@@ -122,7 +122,8 @@ TUNE_CANDIDATES = 9
 
 class TuneReport(ctypes.Structure):
     _fields_ = [("candidates", Tuning * TUNE_CANDIDATES), ("passes_ms", ctypes.c_float * TUNE_CANDIDATES),
-                ("frame_ms", ctypes.c_float * 2), ("chosen", Tuning), ("fuse_passes", _I32)]
+                ("frame_ms", ctypes.c_float * 2), ("chosen", Tuning), ("fuse_passes", _I32),
+                ("frame_merged", _I32)]
 
 _lib = None
 
@@ -640,7 +641,8 @@ class Context:
         return {"block_w": r.chosen.block_w, "ctas_per_sm": r.chosen.ctas_per_sm,
                 "pixels_per_thread": r.chosen.pixels_per_thread, "fuse_passes": bool(r.fuse_passes),
                 "ms": {key(r.candidates[k]): r.passes_ms[k] for k in range(TUNE_CANDIDATES)},
-                "raster_passes_resolve_ms": {"pass launch resolves": r.frame_ms[1], "separate resolve": r.frame_ms[0]}}
+                "raster_passes_resolve_ms": {"pass launch resolves": r.frame_ms[1], "separate resolve": r.frame_ms[0],
+                                             "frame merged": bool(r.frame_merged)}}
 
     def tuning(self):
         t, f = Tuning(), _I32()
