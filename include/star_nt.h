@@ -267,8 +267,9 @@ star_nt_status star_nt_geometry_pass_merged(const star_nt_scene *scene, const st
  * ctas_per_sm: one pixel per thread: 0 or 8: full occupancy with an 8-CTA
  *   register budget (32 per thread); 1..7: a 6-CTA budget (40 per thread)
  *   and the grid capped at that many CTAs per SM.  Two pixels per thread:
- *   0 or 10: full occupancy with a 10-CTA budget (48 registers); 1..9: an
- *   8-CTA budget (64 registers) and the grid capped at that many.
+ *   0 or 8: full occupancy with an 8-CTA budget (64 registers); 10: a
+ *   10-CTA budget (48 registers); 1..7 and 9: the 8-CTA budget and the grid
+ *   capped at that many.
  *   The launch that also resolves the frame runs at most 6 (one pixel) or 8
  *   (two pixels: 8 x 64 columns, all of tensor memory) CTAs per SM.
  *   Default 0.

@@ -14,7 +14,7 @@ import torch
 
 TUNED_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.json")
 # (block_w, ctas_per_sm, pixels_per_thread) of star_nt_tuning
-CANDIDATES = [(8, 0, 2), (4, 0, 2), (16, 0, 2), (8, 8, 2), (4, 8, 2), (8, 0, 1), (4, 0, 1), (8, 6, 1),
+CANDIDATES = [(8, 0, 2), (4, 0, 2), (16, 0, 2), (8, 10, 2), (4, 10, 2), (8, 0, 1), (4, 0, 1), (8, 6, 1),
               (4, 6, 1)]
 
 

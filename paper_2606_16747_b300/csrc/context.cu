@@ -367,7 +367,7 @@ extern "C" star_nt_status star_nt_tune(star_nt_ctx *c, const star_nt_scene *scen
   if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
     return STAR_NT_ERR_ARG;  // the tuner synchronises: not inside a capture
   static const star_nt_tuning kCand[STAR_NT_TUNE_CANDIDATES] = {
-      {8, 0, 2}, {4, 0, 2}, {16, 0, 2}, {8, 8, 2}, {4, 8, 2}, {8, 0, 1}, {4, 0, 1}, {8, 6, 1}, {4, 6, 1}};
+      {8, 0, 2}, {4, 0, 2}, {16, 0, 2}, {8, 10, 2}, {4, 10, 2}, {8, 0, 1}, {4, 0, 1}, {8, 6, 1}, {4, 6, 1}};
   const CtxViews v = ctx_views(c, cams->vp);
   const star_nt_tuning keep = c->tuning;
   const int32_t keep_fuse = c->fuse_passes;

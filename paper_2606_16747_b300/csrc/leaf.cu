@@ -298,7 +298,7 @@ extern "C" star_nt_status star_nt_geometry_passes_leaf(const star_nt_scene *scen
     kern<<<sms * (c > 0 ? c : 1), threads, 0, st>>>(pa, modes, scene->rgba8, queue, d_status);
   };
   if (tu.pix == 2) {  // two pixels per thread, budgets as star_nt_geometry_passes
-    const bool wide2 = per_sm == 0 || per_sm == 10;
+    const bool wide2 = per_sm == 10;
     if (bw == 8) wide2 ? launch(k_passes_leaf<8, 10, 2>, 128) : launch(k_passes_leaf<8, 8, 2>, 128);
     else if (bw == 16) wide2 ? launch(k_passes_leaf<16, 10, 2>, 128) : launch(k_passes_leaf<16, 8, 2>, 128);
     else wide2 ? launch(k_passes_leaf<4, 10, 2>, 128) : launch(k_passes_leaf<4, 8, 2>, 128);

@@ -97,7 +97,8 @@ __global__ void __launch_bounds__(256, MINB) k_passes(BinsView v1, BinsView v2, 
 }
 
 // k_passes with two pixels per thread (pass_body2): CTAs of 128 threads, one
-// tile each; MINB 10 gives a 48-register budget, 8 a 64-register one.
+// tile each; MINB 8 gives a 64-register budget (the default), 10 a 48-register
+// one (the walk then spills a little).
 template <int BW, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_passes2(BinsView v1, BinsView v2, BinsView v3,
                                                     const uint32_t *__restrict__ rgba8, PassOut o1,
@@ -282,8 +283,8 @@ extern "C" star_nt_status star_nt_geometry_passes(const star_nt_scene *scene,
     const int k = per_sm > 0 ? (per_sm < occ ? per_sm : occ) : occ;
     kern<<<sms * (k > 0 ? k : 1), threads, 0, st>>>(v1, v2, v3, scene->rgba8, o1, o2, o3, queue);
   };
-  if (tu.pix == 2) {  // two pixels per thread: 0 or 10 the 10-CTA budget, 1..9 the 8-CTA one
-    const bool wide2 = per_sm == 0 || per_sm == 10;
+  if (tu.pix == 2) {  // two pixels per thread: 10 the 10-CTA budget, 0..9 the 8-CTA one
+    const bool wide2 = per_sm == 10;
     if (bw == 8) wide2 ? launch(k_passes2<8, 10>, 128) : launch(k_passes2<8, 8>, 128);
     else if (bw == 16) wide2 ? launch(k_passes2<16, 10>, 128) : launch(k_passes2<16, 8>, 128);
     else wide2 ? launch(k_passes2<4, 10>, 128) : launch(k_passes2<4, 8>, 128);
