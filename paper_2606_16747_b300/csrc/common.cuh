@@ -49,13 +49,16 @@ struct __align__(16) BinsHeader {
   uint32_t queue;      // work counter of the persistent pass launch (zero between launches)
   uint32_t queue_exit; // CTAs done with the launch (zero between launches)
   int32_t resolved;    // 1: the pass launch also produced the frame (pass 1 ran the network)
-  uint32_t pad[4];
+  uint32_t ents;       // (triangle, tile) pairs recorded by the count launch (zero between calls)
+  uint32_t pad[3];
 };
 static_assert(sizeof(BinsHeader) == 64, "BinsHeader layout");
 
-// Offsets of the parts of a bins workspace.
+// Offsets of the parts of a bins workspace.  ent / ent_rank: the count
+// launch's record of every (triangle, tile) pair with its rank inside its
+// tile, scattered into pairs once the tile offsets are known.
 struct BinsLayout {
-  size_t header, setups, tile_count, tile_offset, tile_cursor, pairs, scan_tmp, total;
+  size_t header, setups, tile_count, tile_offset, ent, ent_rank, pairs, scan_tmp, total;
   int32_t max_tiles;
 };
 
@@ -70,7 +73,8 @@ inline BinsLayout bins_layout(int32_t max_w, int32_t max_h, int32_t max_tris, in
   L.setups = o;      o = align_up(o + sizeof(TriSetup) * (size_t)max_tris, 256);
   L.tile_count = o;  o = align_up(o + 4 * (size_t)(L.max_tiles + 4), 256);  // + ticket, + vector tail
   L.tile_offset = o; o = align_up(o + 4 * (size_t)(L.max_tiles + 1), 256);
-  L.tile_cursor = o; o = align_up(o + 4 * (size_t)L.max_tiles, 256);
+  L.ent = o;         o = align_up(o + 8 * (size_t)pairs, 256);
+  L.ent_rank = o;    o = align_up(o + 4 * (size_t)pairs, 256);
   L.pairs = o;       o = align_up(o + 4 * (size_t)pairs, 256);
   L.scan_tmp = o;    o = align_up(o + 4 * 8192, 256);
   L.total = o;
@@ -81,7 +85,9 @@ inline BinsLayout bins_layout(int32_t max_w, int32_t max_h, int32_t max_tris, in
 struct BinsView {
   BinsHeader *hd;
   TriSetup *setups;
-  uint32_t *tile_count, *tile_offset, *tile_cursor, *pairs, *scan_tmp;
+  uint32_t *tile_count, *tile_offset, *pairs, *scan_tmp;
+  uint2 *ent;         // (triangle, tile) of recorded pair e
+  uint32_t *ent_rank;  // its rank inside the tile
   int32_t max_tiles;
   int32_t max_w, max_h;
   int64_t pair_capacity;
@@ -95,7 +101,8 @@ inline BinsView bins_view(const star_nt_bins &b) {
   v.setups = (TriSetup *)(m + L.setups);
   v.tile_count = (uint32_t *)(m + L.tile_count);
   v.tile_offset = (uint32_t *)(m + L.tile_offset);
-  v.tile_cursor = (uint32_t *)(m + L.tile_cursor);
+  v.ent = (uint2 *)(m + L.ent);
+  v.ent_rank = (uint32_t *)(m + L.ent_rank);
   v.pairs = (uint32_t *)(m + L.pairs);
   v.scan_tmp = (uint32_t *)(m + L.scan_tmp);
   v.max_tiles = L.max_tiles;

@@ -207,19 +207,24 @@ __device__ __forceinline__ int tile_span(const TriSetup &T, int &tx0, int &ty0, 
 }
 
 constexpr int kBinThreads = 128;
-constexpr int kBinTris = 32;  // triangles per binning block: four threads per triangle walk pairs
+constexpr int kBinTris = 32;  // triangles per binning block: four threads per triangle
 
 // (triangle, tile) candidates of one block's kBinTris triangles, whose
 // set-ups are staged in shared memory (tri[i] = triangle t0 + i), flattened
 // so that all kBinThreads threads walk an equal share: a warp scan of the
-// per-triangle candidate counts, then a binary search per candidate.  Calls
-// emit(triangle, tile) for every candidate that passes tile_hit.
-template <class Emit>
-__device__ __forceinline__ void for_each_pair(const TriSetup *tri, int t0, int n_tris, int tiles_x,
-                                              int *s_off, Emit &&emit) {
-  static_assert(kBinTris == 32 && kBinThreads == 4 * kBinTris,
-                "one warp scans the candidate counts; four set-up lanes per triangle");
-  const int tid = threadIdx.x;
+// per-triangle candidate counts, then a binary search per candidate; a
+// candidate that passes tile_hit is a pair.  The walk runs in rounds of
+// kCountBatch candidates per thread: the
+// candidates' tile tests first, then their tile-count increments (independent
+// atomics, all in flight together; each returns the pair's rank inside its
+// tile), then one reservation per warp and round in the pair record for the
+// warp's hits and their writes.  The fill then only scatters the record.  The order
+// of a tile's pairs is not fixed.
+constexpr int kCountBatch = 4;
+__device__ __forceinline__ void count_pairs(const TriSetup *tri, int t0, int n_tris, int tiles_x,
+                                            int *s_off, const BinsView &bv) {
+  static_assert(kBinTris == 32 && kBinThreads == 4 * kBinTris, "one warp scans the candidate counts");
+  const int tid = threadIdx.x, lane = tid & 31;
   if (tid < 32) {
     int tx0 = 0, ty0 = 0, ntx = 1;
     const int nt = t0 + tid < n_tris ? tile_span(tri[tid], tx0, ty0, ntx) : 0;
@@ -234,52 +239,14 @@ __device__ __forceinline__ void for_each_pair(const TriSetup *tri, int t0, int n
   }
   __syncthreads();
   const int total = s_off[kBinTris];
-  for (int q = tid; q < total; q += kBinThreads) {
-    int lo = 0, hi = kBinTris - 1;  // largest j with s_off[j] <= q
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (s_off[mid] <= q) lo = mid; else hi = mid - 1;
-    }
-    const TriSetup &T = tri[lo];
-    int ax0, ay0, anx;
-    tile_span(T, ax0, ay0, anx);
-    const int k = q - s_off[lo];
-    const int tx = ax0 + k % anx, ty = ay0 + k / anx;
-    if (tile_hit(T, tx, ty)) emit(t0 + lo, ty * tiles_x + tx);
-  }
-}
-
-// The fill's walk of for_each_pair, in rounds of kFillBatch candidates per
-// thread: the candidates' tile tests first, then their cursor increments
-// (independent atomics, all in flight together), then the pair writes, so
-// that a thread waits for one atomic round trip per round instead of one per
-// candidate.  The pairs written are the same; their order within a tile is
-// not fixed in either form.
-constexpr int kFillBatch = 4;
-__device__ __forceinline__ void fill_pairs(const TriSetup *tri, int t0, int n_tris, int tiles_x,
-                                           int *s_off, const BinsView &bv) {
-  const int tid = threadIdx.x;
-  if (tid < 32) {
-    int tx0 = 0, ty0 = 0, ntx = 1;
-    const int nt = t0 + tid < n_tris ? tile_span(tri[tid], tx0, ty0, ntx) : 0;
-    int v = nt;
+  const int64_t cap = bv.pair_capacity;
+  for (int r0 = 0; r0 < total; r0 += kBinThreads * kCountBatch) {  // uniform over the block
+    int tile[kCountBatch], tr[kCountBatch];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, v, o);
-      if (tid >= o) v += y;
-    }
-    s_off[tid + 1] = v;
-    if (tid == 0) s_off[0] = 0;
-  }
-  __syncthreads();
-  const int total = s_off[kBinTris];
-  for (int q0 = tid; q0 < total; q0 += kBinThreads * kFillBatch) {
-    int tile[kFillBatch], tr[kFillBatch];
-#pragma unroll
-    for (int b = 0; b < kFillBatch; ++b) {
+    for (int b = 0; b < kCountBatch; ++b) {
       tile[b] = -1;
       tr[b] = 0;
-      const int q = q0 + b * kBinThreads;
+      const int q = r0 + b * kBinThreads + tid;
       if (q < total) {
         int lo = 0, hi = kBinTris - 1;  // largest j with s_off[j] <= q
         while (lo < hi) {
@@ -297,13 +264,32 @@ __device__ __forceinline__ void fill_pairs(const TriSetup *tri, int t0, int n_tr
         }
       }
     }
-    uint32_t pos[kFillBatch];
+    uint32_t rank[kCountBatch];
+    int cnt = 0;
 #pragma unroll
-    for (int b = 0; b < kFillBatch; ++b)
-      pos[b] = tile[b] >= 0 ? atomicAdd(bv.tile_cursor + tile[b], 1u) : 0u;
+    for (int b = 0; b < kCountBatch; ++b) {
+      rank[b] = tile[b] >= 0 ? atomicAdd(bv.tile_count + tile[b], 1u) : 0u;
+      cnt += tile[b] >= 0 ? 1 : 0;
+    }
+    int incl = cnt;  // this thread's hits after the warp's earlier lanes'
 #pragma unroll
-    for (int b = 0; b < kFillBatch; ++b)
-      if (tile[b] >= 0) bv.pairs[pos[b]] = (uint32_t)tr[b];
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int wsum = __shfl_sync(0xffffffffu, incl, 31);
+    uint32_t base = 0u;
+    if (lane == 0 && wsum) base = atomicAdd(&bv.hd->ents, (uint32_t)wsum);
+    uint32_t e = __shfl_sync(0xffffffffu, base, 0) + (uint32_t)(incl - cnt);
+#pragma unroll
+    for (int b = 0; b < kCountBatch; ++b) {
+      if (tile[b] < 0) continue;
+      if ((int64_t)e < cap) {  // beyond capacity the fill raises STAR_NT_ERR_CAPACITY
+        bv.ent[e] = make_uint2((uint32_t)tr[b], (uint32_t)tile[b]);
+        bv.ent_rank[e] = rank[b];
+      }
+      ++e;
+    }
   }
 }
 
@@ -364,39 +350,35 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(const float *__restri
     const int nb = min(kBinTris, n_tris - t0);
     for (int i = threadIdx.x; i < nb * 7; i += kBinThreads)
       reinterpret_cast<uint4 *>(bv.setups + t0)[i] = reinterpret_cast<const uint4 *>(s_tri)[i];
-    for_each_pair(s_tri, t0, n_tris, tiles_x, s_off,
-                  [&](int, int tile) { atomicAdd(bv.tile_count + tile, 1u); });
+    count_pairs(s_tri, t0, n_tris, tiles_x, s_off, bv);
   }
 }
 
-// Pair lists; positions come from the per-tile cursors, which the tile scan
-// initialised to the tile offsets.  The block's set-ups are staged in shared
-// memory first.
-__global__ void __launch_bounds__(kBinThreads) k_bin_fill(PassSet ps, int n_tris, int32_t *status) {
-  __shared__ int s_off[kBinTris + 1];
-  __shared__ TriSetup s_tri[kBinTris];
+// Pair lists: every recorded pair goes to its tile's offset plus its rank
+// (a scatter over the record; positions are distinct by construction).
+constexpr int kFillThreads = 256;
+__global__ void __launch_bounds__(kFillThreads) k_bin_fill(PassSet ps, int32_t *status) {
   const BinsView &bv = ps.bv[blockIdx.y];
   const BinsHeader *hd = bv.hd;
   if (hd->n_tiles == 0) return;  // empty or merged pass
-  if ((int64_t)hd->n_pairs > bv.pair_capacity) {
+  const uint32_t n = hd->n_pairs;
+  if ((int64_t)n > bv.pair_capacity) {
     if (blockIdx.x == 0 && threadIdx.x == 0) raise_status(status, STAR_NT_ERR_CAPACITY);
     return;
   }
-  const int t0 = blockIdx.x * kBinTris;
-  const int nb = min(kBinTris, n_tris - t0);
-  for (int i = threadIdx.x; i < nb * 7; i += kBinThreads)
-    reinterpret_cast<uint4 *>(s_tri)[i] = __ldg(reinterpret_cast<const uint4 *>(bv.setups + t0) + i);
-  __syncthreads();
-  fill_pairs(s_tri, t0, n_tris, hd->tiles_x, s_off, bv);
+  for (uint32_t i = blockIdx.x * kFillThreads + threadIdx.x; i < n; i += gridDim.x * kFillThreads) {
+    const uint2 en = __ldg(bv.ent + i);
+    bv.pairs[__ldg(bv.tile_offset + en.y) + __ldg(bv.ent_rank + i)] = en.x;
+  }
 }
 
 // Exclusive scan of the tile counts, one block of 1024 threads per pass, in
 // rounds of 4096 counts: thread t holds counts [4 (r 1024 + t), +4) of round
 // r, so that every load and store of a warp is one coalesced 512-byte run.
 // The loads of up to four rounds are in flight together.  Writes the
-// offsets, the fill cursors (initialised to the offsets) and the total pair
-// count, and zeroes the counts it consumed: the workspace leaves every call
-// with zero counts, ready for the next (no clearing launch).
+// offsets and the total pair count, and zeroes the counts it consumed and the
+// pair record's counter: the workspace leaves every call with zero counters,
+// ready for the next (no clearing launch).
 constexpr int kScanRounds = 4;
 
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *s_warp, uint32_t *total);
@@ -427,13 +409,11 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(PassSet ps) {
       const uint4 o = make_uint4(ex, ex + v[r].x, ex + v[r].x + v[r].y, ex + v[r].x + v[r].y + v[r].z);
       if (i + 3 < n) {
         *reinterpret_cast<uint4 *>(bv.tile_offset + i) = o;
-        *reinterpret_cast<uint4 *>(bv.tile_cursor + i) = o;
         *reinterpret_cast<uint4 *>(bv.tile_count + i) = make_uint4(0u, 0u, 0u, 0u);
       } else if (i < n) {
         const uint32_t oo[4] = {o.x, o.y, o.z, o.w};
         for (int e = 0; e < n - i; ++e) {
           bv.tile_offset[i + e] = oo[e];
-          bv.tile_cursor[i + e] = oo[e];
           bv.tile_count[i + e] = 0u;  // consumed: zero again for the next call
         }
       }
@@ -443,7 +423,8 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(PassSet ps) {
   }
   if (tid == 0) {
     bv.tile_offset[n] = carry;
-    bv.hd->n_pairs = carry;
+    bv.hd->n_pairs = carry;  // = the pairs the count recorded
+    bv.hd->ents = 0u;        // zero again for the next call
   }
 }
 
@@ -658,7 +639,12 @@ extern "C" star_nt_status star_nt_raster_passes(const star_nt_scene *scene, int3
   const dim3 grid(T > 0 ? (T + kBinTris - 1) / kBinTris : 1, n_passes);
   k_bin_count<<<grid, kBinThreads, 0, st>>>(scene->verts, scene->rgba8, T, ps, d_status);
   k_scan_tiles<<<n_passes, 1024, 0, st>>>(ps);
-  k_bin_fill<<<grid, kBinThreads, 0, st>>>(ps, T, d_status);
+  {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    k_bin_fill<<<dim3(4 * sms, n_passes), kFillThreads, 0, st>>>(ps, d_status);
+  }
   return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
 }
 

@@ -69,7 +69,8 @@ def test_workspace_sizes(sn):
     assert L.star_nt_bins_bytes(1920, 1080, 20000, 1 << 20, ctypes.byref(n)) == sn.OK
     a = n.value
     assert L.star_nt_bins_bytes(1920, 1080, 20000, 2 << 20, ctypes.byref(n)) == sn.OK
-    assert n.value - a == 4 << 20
+    # per pair: the pair list (4 B) and the count launch's record of it (8 B + 4 B rank)
+    assert n.value - a == 16 << 20
     assert L.star_nt_bins_bytes(0, 1080, 10, 10, ctypes.byref(n)) == sn.ERR_ARG
     assert L.star_nt_bins_bytes(100, 100, 10, 10, None) == sn.ERR_ARG
     assert sn.quadtree_ws_bytes(1920, 1080, 16) >= 2 * 120 * 68 * 4
