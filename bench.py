@@ -819,11 +819,14 @@ def end_to_end(sn, torch, sc, w, W, H, cams, args, params, tuning, fuse_passes, 
                  rgba32f=torch.empty(P * 4, device="cuda"), out8=torch.empty(P, dtype=torch.int32, device="cuda"),
                  interp8=torch.empty(P, dtype=torch.int32, device="cuda"),
                  host8=torch.empty(2, P, dtype=torch.int32).pin_memory(),
-                 copied_in=torch.cuda.Event(), rendered=torch.cuda.Event(), copied_out=torch.cuda.Event(),
-                 out_pending=False)
+                 copied_in=torch.cuda.Event(), rendered=torch.cuda.Event(),
+                 copied_out=[torch.cuda.Event(), torch.cuda.Event()], out_pending=False)
         d["scene"] = sn.Scene(d["verts"].data_ptr(), d["rgba8"].data_ptr(), T)
         sets.append(d)
-    main, cin, cout = torch.cuda.current_stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    # one copy-out stream per frame: two DMA streams read back 57 GB/s on the
+    # B300 against 44 with one
+    main, cin = torch.cuda.current_stream(), torch.cuda.Stream()
+    cout = [torch.cuda.Stream(), torch.cuda.Stream()]
 
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
 
@@ -834,7 +837,8 @@ def end_to_end(sn, torch, sc, w, W, H, cams, args, params, tuning, fuse_passes, 
     def copy_in(d, k):
         with torch.cuda.stream(cin):
             if d["out_pending"]:         # its last frames were read back already
-                cin.wait_event(d["copied_out"])
+                for ev in d["copied_out"]:
+                    cin.wait_event(ev)
             d["verts"].copy_(hv, non_blocking=True)
             d["rgba8"].copy_(hc, non_blocking=True)
             d["vp"].copy_(hcam32[2 * k], non_blocking=True)
@@ -868,11 +872,11 @@ def end_to_end(sn, torch, sc, w, W, H, cams, args, params, tuning, fuse_passes, 
             main.wait_event(d["copied_in"])
             g.replay()
             d["rendered"].record(main)
-            with torch.cuda.stream(cout):
-                cout.wait_event(d["rendered"])
-                d["host8"][0].copy_(d["out8"], non_blocking=True)
-                d["host8"][1].copy_(d["interp8"], non_blocking=True)
-                d["copied_out"].record(cout)
+            for f, src in enumerate((d["out8"], d["interp8"])):
+                with torch.cuda.stream(cout[f]):
+                    cout[f].wait_event(d["rendered"])
+                    d["host8"][f].copy_(src, non_blocking=True)
+                    d["copied_out"][f].record(cout[f])
             d["out_pending"] = True
         torch.cuda.synchronize()
 
