@@ -59,7 +59,7 @@ STAGE_REPS = 20
 # dram__bytes_write.sum); per workload, None where no capture of the current
 # kernel exists.  k_passes2: the persistent passes with pass 3 separate;
 # k_passes_resolve: every pass at full size, with the network and composite.
-PASSES_DRAM_BYTES = {"hd": 25763328, "uhd": 190772736}
+PASSES_DRAM_BYTES = {"hd": 15031552, "uhd": None}
 FUSED_DRAM_BYTES = {"hd": 7411968, "uhd": 192553984}
 
 
