@@ -207,7 +207,7 @@ __device__ __forceinline__ int tile_span(const TriSetup &T, int &tx0, int &ty0, 
 }
 
 constexpr int kBinThreads = 128;
-constexpr int kBinTris = 32;  // triangles per binning block: four threads per triangle
+constexpr int kBinTris = 16;  // triangles per binning block: four threads per triangle set it up
 
 // (triangle, tile) candidates of one block's kBinTris triangles, whose
 // set-ups are staged in shared memory (tri[i] = triangle t0 + i), flattened
@@ -223,18 +223,18 @@ constexpr int kBinTris = 32;  // triangles per binning block: four threads per t
 constexpr int kCountBatch = 4;
 __device__ __forceinline__ void count_pairs(const TriSetup *tri, int t0, int n_tris, int tiles_x,
                                             int *s_off, const BinsView &bv) {
-  static_assert(kBinTris == 32 && kBinThreads == 4 * kBinTris, "one warp scans the candidate counts");
+  static_assert(kBinTris <= 32 && kBinThreads >= 4 * kBinTris, "one warp scans the candidate counts");
   const int tid = threadIdx.x, lane = tid & 31;
   if (tid < 32) {
     int tx0 = 0, ty0 = 0, ntx = 1;
-    const int nt = t0 + tid < n_tris ? tile_span(tri[tid], tx0, ty0, ntx) : 0;
+    const int nt = tid < kBinTris && t0 + tid < n_tris ? tile_span(tri[tid], tx0, ty0, ntx) : 0;
     int v = nt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int y = __shfl_up_sync(0xffffffffu, v, o);
       if (tid >= o) v += y;
     }
-    s_off[tid + 1] = v;
+    if (tid < kBinTris) s_off[tid + 1] = v;
     if (tid == 0) s_off[0] = 0;
   }
   __syncthreads();
@@ -343,9 +343,9 @@ __global__ void __launch_bounds__(kBinThreads) k_bin_count(const float *__restri
   }
   if (!merged) {  // a merged pass is taken over by pass 1: no triangles binned
     const int t0 = blockIdx.x * kBinTris;
-    const int j = threadIdx.x >> 2;  // four lanes per triangle
-    triangle_setup_x4(t0 + j, t0 + j < n_tris, verts, rgba8, ps.vp[blockIdx.y], W, H, size_ok,
-                      s_tri + j);
+    const int j = threadIdx.x >> 2;  // four lanes per triangle (all warps take part)
+    triangle_setup_x4(t0 + j, j < kBinTris && t0 + j < n_tris, verts, rgba8, ps.vp[blockIdx.y], W, H,
+                      size_ok, s_tri + (j < kBinTris ? j : 0));
     __syncthreads();
     const int nb = min(kBinTris, n_tris - t0);
     for (int i = threadIdx.x; i < nb * 7; i += kBinThreads)
