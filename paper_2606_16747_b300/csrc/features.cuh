@@ -23,7 +23,9 @@ __device__ __forceinline__ float tail_transmittance(unsigned long long lg, uint3
   const uint32_t k = (uint32_t)(lg >> 32);
   if (k >= 160u) return 0.0f;
   const float frac = __uint2float_rn((uint32_t)lg) * 2.3283064365386963e-10f;  // 2^-32
-  return ldexpf(exp2f(-frac), -(int)k);
+  const float e = exp2f(-frac);
+  // e in [0.5, 1]: e 2^-k is normal for k <= 125, where one multiply by 2^-k is exact
+  return k <= 125u ? e * __int_as_float((int)(127u - k) << 23) : ldexpf(e, -(int)k);
 }
 
 // straight RGBA8 to float (c8 / 255, by a multiply: within one rounding of
