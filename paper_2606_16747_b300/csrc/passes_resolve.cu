@@ -236,12 +236,14 @@ __device__ __forceinline__ void pass_resolve_body2(const BinsView &bv, const uin
 #pragma unroll
   for (int t = 0; t < 2; ++t)
 #pragma unroll
-    for (int kc = 0; kc < 4; ++kc) {
-      float d[8];
-      tmem_ld8(lane_tmem + 32 * t + 8 * kc, d);
-      *reinterpret_cast<uint4 *>(fs.u.h[t] + kc * 2048 + row * 16) =
-          make_uint4(pack_relu_bf16(d[0], d[1]), pack_relu_bf16(d[2], d[3]), pack_relu_bf16(d[4], d[5]),
-                     pack_relu_bf16(d[6], d[7]));
+    for (int kc = 0; kc < 4; kc += 2) {  // two K core columns of H1 per tensor-memory load
+      float d[16];
+      tmem_ld16(lane_tmem + 32 * t + 8 * kc, d);
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        *reinterpret_cast<uint4 *>(fs.u.h[t] + (kc + h) * 2048 + row * 16) =
+            make_uint4(pack_relu_bf16(d[8 * h], d[8 * h + 1]), pack_relu_bf16(d[8 * h + 2], d[8 * h + 3]),
+                       pack_relu_bf16(d[8 * h + 4], d[8 * h + 5]), pack_relu_bf16(d[8 * h + 6], d[8 * h + 7]));
     }
   fence_async_smem();
   fence_before();
@@ -264,15 +266,15 @@ __device__ __forceinline__ void pass_resolve_body2(const BinsView &bv, const uin
   if (!fs.abort) mma_wait_cta(bar, ph, &fs.abort, ra.wait_ns);  // fs.abort is uniform after a barrier
   ph ^= 1u;
 #pragma unroll
-  for (int t = 0; t < 2; ++t)
+  for (int t = 0; t < 2; ++t) {  // both K core columns of H2 in one tensor-memory load
+    float d[16];
+    tmem_ld16(lane_tmem + 32 * t, d);
 #pragma unroll
-    for (int kc = 0; kc < 2; ++kc) {
-      float d[8];
-      tmem_ld8(lane_tmem + 32 * t + 8 * kc, d);
-      *reinterpret_cast<uint4 *>(fs.u.h[t] + kc * 2048 + row * 16) =
-          make_uint4(pack_relu_bf16(d[0], d[1]), pack_relu_bf16(d[2], d[3]), pack_relu_bf16(d[4], d[5]),
-                     pack_relu_bf16(d[6], d[7]));
-    }
+    for (int h = 0; h < 2; ++h)
+      *reinterpret_cast<uint4 *>(fs.u.h[t] + h * 2048 + row * 16) =
+          make_uint4(pack_relu_bf16(d[8 * h], d[8 * h + 1]), pack_relu_bf16(d[8 * h + 2], d[8 * h + 3]),
+                     pack_relu_bf16(d[8 * h + 4], d[8 * h + 5]), pack_relu_bf16(d[8 * h + 6], d[8 * h + 7]));
+  }
   fence_async_smem();
   fence_before();
   __syncthreads();
