@@ -60,7 +60,7 @@ STAGE_REPS = 20
 # kernel exists.  k_passes2: the persistent passes with pass 3 separate;
 # k_passes_resolve: every pass at full size, with the network and composite.
 PASSES_DRAM_BYTES = {"hd": 15031552, "uhd": None}
-FUSED_DRAM_BYTES = {"hd": 7411968, "uhd": 192553984}
+FUSED_DRAM_BYTES = {"hd": 7815680, "uhd": 189930240}
 
 
 def stage_rooflines(star, torch, stage_state, stage_mean, hbm_gbs):
