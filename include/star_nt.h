@@ -606,8 +606,13 @@ star_nt_status star_nt_abuffer(const star_nt_frags *frags, const uint32_t *rgba8
  *   L = mean over B x 3 of (f - y)^2 (one float).
  * star_nt_mlp_backward: gradient of L with respect to the 771 parameters
  *   (w1, b1, w2, b2, w3, b3 order) for inputs x [B][8] float32 (STAR_NT_F32
- *   layout) and dy; the forward pass is recomputed in float32 with w;
- *   deterministic (fixed summation order).
+ *   layout) and dy; the forward pass and the per-layer gradients are
+ *   recomputed in float32 with w, and the weight and bias gradients, sums
+ *   over the batch of products of a layer's input and its gradient, are one
+ *   contraction on the tcgen05 tensor cores (bf16 operands split three ways,
+ *   hi + mid + lo, fp32 accumulation: float32 accuracy); deterministic (fixed
+ *   summation order).  d_status (device int32, may be NULL) receives
+ *   STAR_NT_ERR_TIMEOUT if a tensor-core wait runs out; grad is then NaN.
  * star_nt_adam: bias-corrected Adam step `step` (from 1) on the float32
  *   master parameters; bf16_rounded (may be NULL) receives them rounded to
  *   bfloat16 precision, stored as float32 (the weights of the next forward). */
@@ -622,7 +627,7 @@ star_nt_status star_nt_wmse_grad(const float *f, const float *y, const float *w,
                                  float *loss, void *ws, size_t ws_bytes, void *stream);
 star_nt_status star_nt_mlp_backward(const star_nt_mlp *w, const float *x, const float *dy,
                                     int64_t B, float *grad, void *ws, size_t ws_bytes,
-                                    void *stream);
+                                    int32_t *d_status, void *stream);
 star_nt_status star_nt_adam(float *params, const float *grad, float *m, float *v, int64_t n,
                             int64_t step, float lr, float beta1, float beta2, float eps,
                             float *bf16_rounded, void *stream);
@@ -664,10 +669,11 @@ star_nt_status star_nt_infer_dfaoit(const star_nt_mlp *w, int32_t x_dtype, const
 /* star_nt_dfaoit_backward: star_nt_mlp_backward for this network: gradient of
  * L with respect to its 963 parameters (w1, b1, w2, b2, w3, b3 order) for x
  * [B][16] float32 and dy [B][4]; the sigmoid's derivative f (1 - f);
- * ws of star_nt_train_ws_bytes(B) bytes. */
+ * ws of star_nt_train_ws_bytes(B) bytes; the same tensor-core contraction
+ * and d_status. */
 star_nt_status star_nt_dfaoit_backward(const star_nt_mlp *w, const float *x, const float *dy,
                                        int64_t B, float *grad, void *ws, size_t ws_bytes,
-                                       void *stream);
+                                       int32_t *d_status, void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* Context: the whole STAR-NT step of Fig. 1 through one call.               */

@@ -6,6 +6,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "tc_primitives.cuh"
 
 namespace star {
 
@@ -121,163 +122,294 @@ __global__ void k_sum_partials(const float *__restrict__ partial, int n, float *
 // ---------------------------------------------------------------------------
 // Backpropagation of the networks NIN -> 32 -> 16 -> 3 with ReLU hidden
 // layers: the tail MLP (NIN = 5, ReLU output, 771 parameters) and the DFAOIT
-// comparison network (NIN = 11, sigmoid output, 963 parameters).  Stage 1:
-// per sample, recompute the forward pass and the per-layer gradients
-// g3 = dL/dz3, g2 = dL/dz2, g1 = dL/dz1 (z: pre-activation), stored with the
-// activations: row = [h1(32) h2(16) g1(32) g2(16) g3(3) x(NIN)].  Stage 2: per
-// chunk of samples, every parameter's partial sum.  Stage 3: the partial sums
-// added in chunk order (deterministic).
+// comparison network (NIN = 11, sigmoid output, 963 parameters).
+//
+// Per sample i the forward pass is recomputed and the gradients at the three
+// layers' pre-activations, g3 = dL/dz3, g2 = dL/dz2, g1 = dL/dz1, follow by
+// the chain rule (CUDA cores: a few hundred multiply-adds per sample with
+// K = NIN, 32 and 16).  With a_i = (x_i, h1_i, h2_i, 1), the inputs of the
+// three layers and the bias input (NIN + 49 values), and g_i = (g1_i, g2_i,
+// g3_i) (51 values), every parameter's gradient is one entry of the
+// contraction over the batch
+//     D = sum_i a_i g_i^T:  dW1[o][k] = D[x_k][g1_o], db1[o] = D[1][g1_o],
+//     dW2[o][k] = D[h1_k][g2_o], db2[o] = D[1][g2_o], dW3, db3 alike,
+// which runs on the tcgen05 tensor cores.  A CTA of 128 threads (one sample
+// each) writes a_i into rows 0..63 and g_i into rows 64..127 of sample
+// column i of an operand P (128 rows x 128 samples) in shared memory, and
+// accumulates P P_g^T (M = 128, N = 64: P's g rows as the B operand, K = the
+// samples) in tensor memory over the tiles it takes; rows 0..63 of the
+// accumulator are D (rows 64..127 hold g g^T, unused).  The operands are bf16:
+// each float32 value v is carried as three planes, hi = bf16(v), mid =
+// bf16(v - hi), lo = bf16(v - hi - mid) (round to nearest, 24 significant bits
+// together), and the six products hi.hi, hi.mid, mid.hi, hi.lo, lo.hi,
+// mid.mid leave out terms below 2^-26 of each product, so D agrees with a
+// float32 evaluation up to rounding order.  Each CTA writes its D entries as
+// one row of partial sums; the rows are added in CTA order (deterministic).
 template <int NIN>
 struct Net {
-  static constexpr int kRow = (99 + NIN + 3) / 4 * 4;  // row length, padded to 4 floats
   static constexpr int kW1 = 0, kB1 = 32 * NIN, kW2 = kB1 + 32, kB2 = kW2 + 512, kW3 = kB2 + 16,
                        kB3 = kW3 + 48, kParams = kB3 + 3;
   static constexpr int kXStride = NIN == 5 ? 2 : 4;     // float4 per input row ([P][8] or [P][16])
+  static constexpr int kA = NIN + 49;                   // a_i: x, h1, h2, 1
+  static_assert(kA <= 64, "a_i fits rows 0..63");
 };
-constexpr int kChunkS = 1024;
-constexpr int kRowMax = Net<11>::kRow;
 constexpr int kParamsMax = Net<11>::kParams;
 
-template <int NIN, bool SIGMOID>
-__global__ void __launch_bounds__(256) k_mlp_bwd_rows(const float *__restrict__ w1, const float *__restrict__ b1,
-                                                      const float *__restrict__ w2, const float *__restrict__ b2,
-                                                      const float *__restrict__ w3, const float *__restrict__ b3,
-                                                      const float4 *__restrict__ X, const float4 *__restrict__ dY,
-                                                      long long B, float *__restrict__ rows) {
+// operand P in shared memory, K-major without swizzle: 8 x 8 bf16 core
+// matrices (8 rows of 16 bytes); the 16 row groups of one 8-sample chunk
+// lie 128 bytes apart, chunks kGradChunk apart (16 bytes more than the
+// chunk, so that the 32 lanes of a warp, 32 consecutive samples, store one
+// row into 16 different banks)
+constexpr int kGradTile = 128;                       // samples per tile (one per thread)
+constexpr uint32_t kGradChunk = 16 * 128 + 16;       // bytes between 8-sample chunks
+constexpr uint32_t kGradPlane = 16 * kGradChunk;     // one bf16 plane of P (33,024 bytes)
+constexpr uint32_t kGradSmem = 3 * kGradPlane + 4 * 1024;  // hi, mid, lo planes; the weights
+constexpr int kGradCtasPerSm = 2;
+
+// v = hi + mid + lo to 24 significant bits; row r of sample column col
+__device__ __forceinline__ void put_split3(uint8_t *col, int r, float v) {
+  const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+  const float r1 = v - __bfloat162float(hi);
+  const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+  const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+  uint8_t *p = col + (r >> 3) * 128 + (r & 7) * 16;
+  *reinterpret_cast<__nv_bfloat16 *>(p) = hi;
+  *reinterpret_cast<__nv_bfloat16 *>(p + kGradPlane) = mid;
+  *reinterpret_cast<__nv_bfloat16 *>(p + 2 * kGradPlane) = lo;
+}
+
+// forward pass of sample i (weights in s, Net<NIN> layout); zeros for i >= B
+template <int NIN>
+__device__ __forceinline__ void sample_forward(const float *s, const float4 *__restrict__ X, long long i,
+                                               long long B, float (&x)[NIN], float (&h1)[32], float (&h2)[16],
+                                               float (&z3)[3]) {
   using N = Net<NIN>;
-  __shared__ float s[N::kParams + 1];
-  for (int i = threadIdx.x; i < 32 * NIN; i += 256) s[N::kW1 + i] = w1[i];
-  for (int i = threadIdx.x; i < 512; i += 256) s[N::kW2 + i] = w2[i];
-  if (threadIdx.x < 32) s[N::kB1 + threadIdx.x] = b1[threadIdx.x];
-  if (threadIdx.x < 16) s[N::kB2 + threadIdx.x] = b2[threadIdx.x];
-  if (threadIdx.x < 48) s[N::kW3 + threadIdx.x] = w3[threadIdx.x];
-  if (threadIdx.x < 3) s[N::kB3 + threadIdx.x] = b3[threadIdx.x];
-  __syncthreads();
-  const long long i = (long long)blockIdx.x * 256 + threadIdx.x;
-  if (i >= B) return;
-  float x[NIN];
+  if (i >= B) {
+#pragma unroll
+    for (int k = 0; k < NIN; ++k) x[k] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) h1[k] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) h2[k] = 0.0f;
+    z3[0] = z3[1] = z3[2] = 0.0f;
+    return;
+  }
   {
     float v[4 * N::kXStride];
 #pragma unroll
     for (int q = 0; q < N::kXStride; ++q) {
-      const float4 a = X[N::kXStride * i + q];
-      v[4 * q] = a.x;
-      v[4 * q + 1] = a.y;
-      v[4 * q + 2] = a.z;
-      v[4 * q + 3] = a.w;
+      const float4 t = X[N::kXStride * i + q];
+      v[4 * q] = t.x;
+      v[4 * q + 1] = t.y;
+      v[4 * q + 2] = t.z;
+      v[4 * q + 3] = t.w;
     }
 #pragma unroll
     for (int k = 0; k < NIN; ++k) x[k] = v[k];
   }
-  float h1[32], h2[16], z3[3];
 #pragma unroll
   for (int o = 0; o < 32; ++o) {
-    float a = s[N::kB1 + o];
+    float t = s[N::kB1 + o];
 #pragma unroll
-    for (int k = 0; k < NIN; ++k) a = fmaf(s[N::kW1 + NIN * o + k], x[k], a);
-    h1[o] = fmaxf(a, 0.0f);
+    for (int k = 0; k < NIN; ++k) t = fmaf(s[N::kW1 + NIN * o + k], x[k], t);
+    h1[o] = fmaxf(t, 0.0f);
   }
 #pragma unroll
   for (int o = 0; o < 16; ++o) {
-    float a = s[N::kB2 + o];
+    float t = s[N::kB2 + o];
 #pragma unroll
-    for (int k = 0; k < 32; ++k) a = fmaf(s[N::kW2 + 32 * o + k], h1[k], a);
-    h2[o] = fmaxf(a, 0.0f);
+    for (int k = 0; k < 32; ++k) t = fmaf(s[N::kW2 + 32 * o + k], h1[k], t);
+    h2[o] = fmaxf(t, 0.0f);
   }
 #pragma unroll
   for (int o = 0; o < 3; ++o) {
-    float a = s[N::kB3 + o];
+    float t = s[N::kB3 + o];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) a = fmaf(s[N::kW3 + 16 * o + k], h2[k], a);
-    z3[o] = a;
+    for (int k = 0; k < 16; ++k) t = fmaf(s[N::kW3 + 16 * o + k], h2[k], t);
+    z3[o] = t;
   }
-  const float4 d = dY[i];
-  const float dd[3] = {d.x, d.y, d.z};
-  float g3[3], g2[16], g1[32];
+}
+
+// sample column col of P: rows 0..NIN+48 a = (x, h1, h2, 1), rows 64..114
+// g = (g1, g2, g3), the backward pass written row by row as it goes (the
+// hidden activations survive only as their ReLU masks); zeros for i >= B
+template <int NIN, bool SIGMOID>
+__device__ __forceinline__ void sample_write(const float *s, uint8_t *col, const float (&x)[NIN],
+                                             const float (&h1)[32], const float (&h2)[16], const float (&z3)[3],
+                                             const float4 *__restrict__ dY, long long i, long long B) {
+  using N = Net<NIN>;
+  const bool valid = i < B;
+  uint32_t m1 = 0u, m2 = 0u;
 #pragma unroll
-  for (int o = 0; o < 3; ++o) {
-    if (SIGMOID) {
-      const float f = 1.0f / (1.0f + expf(-z3[o]));
-      g3[o] = dd[o] * f * (1.0f - f);
-    } else {
-      g3[o] = z3[o] > 0.0f ? dd[o] : 0.0f;
-    }
+  for (int k = 0; k < NIN; ++k) put_split3(col, k, x[k]);
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    put_split3(col, NIN + k, h1[k]);
+    m1 |= (h1[k] > 0.0f ? 1u : 0u) << k;
   }
 #pragma unroll
   for (int k = 0; k < 16; ++k) {
-    float a = 0.0f;
-#pragma unroll
-    for (int o = 0; o < 3; ++o) a = fmaf(s[N::kW3 + 16 * o + k], g3[o], a);
-    g2[k] = h2[k] > 0.0f ? a : 0.0f;
+    put_split3(col, NIN + 32 + k, h2[k]);
+    m2 |= (h2[k] > 0.0f ? 1u : 0u) << k;
   }
+  put_split3(col, NIN + 48, valid ? 1.0f : 0.0f);
+  float g3[3] = {0.0f, 0.0f, 0.0f};
+  if (valid) {
+    const float4 d = dY[i];
+    const float dd[3] = {d.x, d.y, d.z};
 #pragma unroll
-  for (int k = 0; k < 32; ++k) {
-    float a = 0.0f;
-#pragma unroll
-    for (int o = 0; o < 16; ++o) a = fmaf(s[N::kW2 + 32 * o + k], g2[o], a);
-    g1[k] = h1[k] > 0.0f ? a : 0.0f;
-  }
-  float *row = rows + (size_t)i * N::kRow;
-#pragma unroll
-  for (int k = 0; k < 32; ++k) row[k] = h1[k];
-#pragma unroll
-  for (int k = 0; k < 16; ++k) row[32 + k] = h2[k];
-#pragma unroll
-  for (int k = 0; k < 32; ++k) row[48 + k] = g1[k];
-#pragma unroll
-  for (int k = 0; k < 16; ++k) row[80 + k] = g2[k];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) row[96 + k] = g3[k];
-#pragma unroll
-  for (int k = 0; k < NIN; ++k) row[99 + k] = x[k];
-}
-
-// parameter p (in w1, b1, w2, b2, w3, b3 order) as a product of two row
-// entries (second index < 0: bias, factor 1)
-template <int NIN>
-__device__ __forceinline__ void param_factors(int p, int &a, int &b) {
-  using N = Net<NIN>;
-  if (p < N::kB1) { a = 48 + p / NIN; b = 99 + p % NIN; return; }            // dW1[o][k] = g1[o] x[k]
-  if (p < N::kW2) { a = 48 + (p - N::kB1); b = -1; return; }                 // db1
-  if (p < N::kB2) { const int q = p - N::kW2; a = 80 + q / 32; b = q % 32; return; }  // dW2 = g2 h1
-  if (p < N::kW3) { a = 80 + (p - N::kB2); b = -1; return; }                 // db2
-  if (p < N::kB3) { const int q = p - N::kW3; a = 96 + q / 16; b = 32 + q % 16; return; }  // dW3 = g3 h2
-  a = 96 + (p - N::kB3); b = -1;                                             // db3
-}
-
-template <int NIN>
-__global__ void __launch_bounds__(256) k_mlp_bwd_partial(const float *__restrict__ rows, long long B,
-                                                         float *__restrict__ partial) {
-  using N = Net<NIN>;
-  __shared__ float s_rows[32 * N::kRow];
-  const long long s0 = (long long)blockIdx.x * kChunkS;
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  int fa[4], fb[4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int p = threadIdx.x + 256 * j;
-    if (p < N::kParams) param_factors<NIN>(p, fa[j], fb[j]);
-    else { fa[j] = 0; fb[j] = -2; }
-  }
-  for (long long c = s0; c < s0 + kChunkS && c < B; c += 32) {
-    const int m = (int)min((long long)32, B - c);
-    __syncthreads();
-    for (int k = threadIdx.x; k < m * N::kRow; k += 256) s_rows[k] = rows[(size_t)c * N::kRow + k];
-    __syncthreads();
-    for (int r = 0; r < m; ++r) {
-      const float *row = s_rows + r * N::kRow;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        if (fb[j] == -2) continue;
-        acc[j] = fmaf(row[fa[j]], fb[j] >= 0 ? row[fb[j]] : 1.0f, acc[j]);
+    for (int o = 0; o < 3; ++o) {
+      if (SIGMOID) {
+        const float f = 1.0f / (1.0f + expf(-z3[o]));
+        g3[o] = dd[o] * f * (1.0f - f);
+      } else {
+        g3[o] = z3[o] > 0.0f ? dd[o] : 0.0f;
       }
     }
   }
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int p = threadIdx.x + 256 * j;
-    if (p < N::kParams) partial[(size_t)blockIdx.x * N::kParams + p] = acc[j];
+  for (int o = 0; o < 3; ++o) put_split3(col, 64 + 48 + o, g3[o]);
+  float g2[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    float t = 0.0f;
+#pragma unroll
+    for (int o = 0; o < 3; ++o) t = fmaf(s[N::kW3 + 16 * o + k], g3[o], t);
+    g2[k] = (m2 >> k) & 1u ? t : 0.0f;
+    put_split3(col, 64 + 32 + k, g2[k]);
   }
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    float t = 0.0f;
+#pragma unroll
+    for (int o = 0; o < 16; ++o) t = fmaf(s[N::kW2 + 32 * o + k], g2[o], t);
+    put_split3(col, 64 + k, (m1 >> k) & 1u ? t : 0.0f);
+  }
+}
+
+template <int NIN, bool SIGMOID>
+__global__ void __launch_bounds__(128, kGradCtasPerSm)
+    k_mlp_grad_tc(const float *__restrict__ w1, const float *__restrict__ b1, const float *__restrict__ w2,
+                  const float *__restrict__ b2, const float *__restrict__ w3, const float *__restrict__ b3,
+                  const float4 *__restrict__ X, const float4 *__restrict__ dY, long long B, int n_tiles,
+                  float *__restrict__ partial, unsigned long long wait_ns, int32_t *status) {
+  using N = Net<NIN>;
+  extern __shared__ __align__(128) uint8_t smem[];  // P: hi, mid, lo planes; then the weights
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  float *s = reinterpret_cast<float *>(smem + 3 * kGradPlane);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(64)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  for (int i = tid; i < 32 * NIN; i += 128) s[N::kW1 + i] = w1[i];
+  for (int i = tid; i < 512; i += 128) s[N::kW2 + i] = w2[i];
+  if (tid < 32) s[N::kB1 + tid] = b1[tid];
+  if (tid < 16) s[N::kB2 + tid] = b2[tid];
+  if (tid < 48) s[N::kW3 + tid] = w3[tid];
+  if (tid < 3) s[N::kB3 + tid] = b3[tid];
+  // the rows of P past a_i and g_i stay zero
+  for (uint32_t i = tid; i < 3 * kGradPlane / 16; i += 128)
+    reinterpret_cast<uint4 *>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (tid == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_slot, p0 = smem_u32(smem);
+  uint8_t *col = smem + (tid >> 3) * kGradChunk + (tid & 7) * 2;  // this thread's sample column
+  uint32_t ph = 0u;
+  int done = 0;  // tiles accumulated (CTA-uniform)
+  bool pending = false;
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const long long i = (long long)tile * kGradTile + tid;
+    float x[NIN], h1[32], h2[16], z3[3];
+    sample_forward<NIN>(s, X, i, B, x, h1, h2, z3);  // overlaps the previous tile's MMAs
+    if (pending) {  // the previous tile's MMAs have read P
+      mma_wait_cta(smem_u32(&bar), ph, &abort_flag, wait_ns);
+      ph ^= 1u;
+      pending = false;
+    }
+    if (abort_flag) break;  // uniform: read after the CTA barrier of the wait
+    sample_write<NIN, SIGMOID>(s, col, x, h1, h2, z3, dY, i, B);
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      fence_after();
+      // (A plane, B plane): hi.hi, hi.mid, mid.hi, hi.lo, lo.hi, mid.mid
+      constexpr uint32_t pa[6] = {0, 0, 1, 0, 2, 1}, pb[6] = {0, 1, 0, 2, 0, 1};
+#pragma unroll 1
+      for (int j = 0; j < kGradTile / 16; ++j) {  // K steps of 16 samples: two 8-sample chunks
+        const uint32_t off = 2u * (uint32_t)j * kGradChunk;
+#pragma unroll
+        for (int q = 0; q < 6; ++q)
+          mma_bf16(tmem, smem_desc(p0 + pa[q] * kGradPlane + off, kGradChunk, 128),
+                   smem_desc(p0 + pb[q] * kGradPlane + off + 8 * 128, kGradChunk, 128), idesc_bf16(64),
+                   (done > 0 || j > 0 || q > 0) ? 1u : 0u);
+      }
+      mma_commit(smem_u32(&bar));
+    }
+    pending = true;
+    ++done;
+  }
+  if (pending) {
+    mma_wait_cta(smem_u32(&bar), ph, &abort_flag, wait_ns);
+    ph ^= 1u;
+  }
+  // rows 0..63 of the accumulator (tensor-memory lanes of warps 0 and 1):
+  // thread m holds D[m][0..63], m the index of a_i, the column that of g_i
+  if (warp < 2) {
+    float d[64];
+    if (done > 0) {
+      float t[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), t);
+#pragma unroll
+      for (int n = 0; n < 32; ++n) d[n] = t[n];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + 32u, t);
+#pragma unroll
+      for (int n = 0; n < 32; ++n) d[32 + n] = t[n];
+    } else {
+#pragma unroll
+      for (int n = 0; n < 64; ++n) d[n] = 0.0f;
+    }
+    if (abort_flag) {  // an incomplete sum: the gradient reads as NaN
+#pragma unroll
+      for (int n = 0; n < 64; ++n) d[n] = __int_as_float(0x7fc00000);
+    }
+    float *out = partial + (size_t)blockIdx.x * N::kParams;
+    const int m = tid;
+    if (m < NIN) {
+#pragma unroll
+      for (int o = 0; o < 32; ++o) out[N::kW1 + NIN * o + m] = d[o];
+    } else if (m < NIN + 32) {
+#pragma unroll
+      for (int o = 0; o < 16; ++o) out[N::kW2 + 32 * o + (m - NIN)] = d[32 + o];
+    } else if (m < NIN + 48) {
+#pragma unroll
+      for (int o = 0; o < 3; ++o) out[N::kW3 + 16 * o + (m - NIN - 32)] = d[48 + o];
+    } else if (m == NIN + 48) {
+#pragma unroll
+      for (int o = 0; o < 32; ++o) out[N::kB1 + o] = d[o];
+#pragma unroll
+      for (int o = 0; o < 16; ++o) out[N::kB2 + o] = d[32 + o];
+#pragma unroll
+      for (int o = 0; o < 3; ++o) out[N::kB3 + o] = d[48 + o];
+    }
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64) : "memory");
+  if (tid == 0 && abort_flag) raise_status(status, STAR_NT_ERR_TIMEOUT);
 }
 
 __global__ void k_mlp_bwd_reduce(const float *__restrict__ partial, int chunks, int n_params,
@@ -329,11 +461,12 @@ static int mse_blocks(int64_t B) {
   return (int)(g > 1024 ? 1024 : (g < 1 ? 1 : g));
 }
 
+// the backward's per-CTA partial sums (at most one row per tile), then the
+// loss partials of star_nt_mse_grad in the last 4 KB
 extern "C" size_t star_nt_train_ws_bytes(int64_t B) {
   if (B <= 0) return 0;
-  const size_t rows = (size_t)B * kRowMax * 4;
-  const size_t chunks = (size_t)((B + kChunkS - 1) / kChunkS);
-  return align_up(rows, 256) + align_up(chunks * kParamsMax * 4, 256) + align_up(4 * 1024, 256);
+  const size_t tiles = (size_t)((B + kGradTile - 1) / kGradTile);
+  return align_up(tiles * kParamsMax * 4, 256) + align_up(4 * 1024, 256);
 }
 
 static star_nt_status mse_grad(const float *f, const float *y, const float *w, int64_t B, float *dy,
@@ -365,34 +498,44 @@ extern "C" star_nt_status star_nt_wmse_grad(const float *f, const float *y, cons
 
 template <int NIN, bool SIGMOID>
 static star_nt_status mlp_backward(const star_nt_mlp *w, const float *x, const float *dy, int64_t B,
-                                   float *grad, void *ws, size_t ws_bytes, void *stream) {
+                                   float *grad, void *ws, size_t ws_bytes, int32_t *d_status, void *stream) {
   using N = Net<NIN>;
   if (!w || !w->w1 || !w->b1 || !w->w2 || !w->b2 || !w->w3 || !w->b3 || !x || !dy || !grad || B <= 0 ||
       !ws || ws_bytes < star_nt_train_ws_bytes(B))
     return STAR_NT_ERR_ARG;
   if (((uintptr_t)x & 15u) || ((uintptr_t)dy & 15u) || ((uintptr_t)ws & 255u)) return STAR_NT_ERR_ARG;
+  const long long n_tiles = (B + kGradTile - 1) / kGradTile;
+  if (n_tiles > (1ll << 30)) return STAR_NT_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
-  float *rows = reinterpret_cast<float *>(ws);
-  float *partial = reinterpret_cast<float *>((char *)ws + align_up((size_t)B * kRowMax * 4, 256));
-  const int chunks = (int)((B + kChunkS - 1) / kChunkS);
-  k_mlp_bwd_rows<NIN, SIGMOID><<<(unsigned)((B + 255) / 256), 256, 0, st>>>(
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_mlp_grad_tc<NIN, SIGMOID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kGradSmem) != cudaSuccess)
+      return STAR_NT_ERR_CUDA;
+    attr = true;
+  }
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = (int)(n_tiles < (long long)sms * kGradCtasPerSm ? n_tiles : (long long)sms * kGradCtasPerSm);
+  float *partial = reinterpret_cast<float *>(ws);
+  k_mlp_grad_tc<NIN, SIGMOID><<<grid, 128, kGradSmem, st>>>(
       w->w1, w->b1, w->w2, w->b2, w->w3, w->b3, reinterpret_cast<const float4 *>(x),
-      reinterpret_cast<const float4 *>(dy), B, rows);
-  k_mlp_bwd_partial<NIN><<<chunks, 256, 0, st>>>(rows, B, partial);
-  k_mlp_bwd_reduce<<<(N::kParams + 255) / 256, 256, 0, st>>>(partial, chunks, N::kParams, grad);
+      reinterpret_cast<const float4 *>(dy), B, (int)n_tiles, partial, wait_limit_ns(), d_status);
+  k_mlp_bwd_reduce<<<(N::kParams + 255) / 256, 256, 0, st>>>(partial, grid, N::kParams, grad);
   return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
 }
 
 extern "C" star_nt_status star_nt_mlp_backward(const star_nt_mlp *w, const float *x, const float *dy,
                                                int64_t B, float *grad, void *ws, size_t ws_bytes,
-                                               void *stream) {
-  return mlp_backward<5, false>(w, x, dy, B, grad, ws, ws_bytes, stream);
+                                               int32_t *d_status, void *stream) {
+  return mlp_backward<5, false>(w, x, dy, B, grad, ws, ws_bytes, d_status, stream);
 }
 
 extern "C" star_nt_status star_nt_dfaoit_backward(const star_nt_mlp *w, const float *x, const float *dy,
                                                   int64_t B, float *grad, void *ws, size_t ws_bytes,
-                                                  void *stream) {
-  return mlp_backward<11, true>(w, x, dy, B, grad, ws, ws_bytes, stream);
+                                                  int32_t *d_status, void *stream) {
+  return mlp_backward<11, true>(w, x, dy, B, grad, ws, ws_bytes, d_status, stream);
 }
 
 extern "C" star_nt_status star_nt_adam(float *params, const float *grad, float *m, float *v, int64_t n,
@@ -414,10 +557,8 @@ cudaError_t preload_train() {
   if ((r = cudaFuncGetAttributes(&a, k_abuffer)) != cudaSuccess) e = r;
   if ((r = cudaFuncGetAttributes(&a, k_mse)) != cudaSuccess) e = r;
   if ((r = cudaFuncGetAttributes(&a, k_sum_partials)) != cudaSuccess) e = r;
-  if ((r = cudaFuncGetAttributes(&a, k_mlp_bwd_rows<5, false>)) != cudaSuccess) e = r;
-  if ((r = cudaFuncGetAttributes(&a, k_mlp_bwd_partial<5>)) != cudaSuccess) e = r;
-  if ((r = cudaFuncGetAttributes(&a, k_mlp_bwd_rows<11, true>)) != cudaSuccess) e = r;
-  if ((r = cudaFuncGetAttributes(&a, k_mlp_bwd_partial<11>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_mlp_grad_tc<5, false>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_mlp_grad_tc<11, true>)) != cudaSuccess) e = r;
   if ((r = cudaFuncGetAttributes(&a, k_mlp_bwd_reduce)) != cudaSuccess) e = r;
   if ((r = cudaFuncGetAttributes(&a, k_adam)) != cudaSuccess) e = r;
   return e;

@@ -195,7 +195,7 @@ def lib():
         L.star_nt_train_ws_bytes.restype = ctypes.c_size_t
         L.star_nt_mse_grad.argtypes = [_P, _P, _I64, _P, _P, _P, ctypes.c_size_t, _P]
         L.star_nt_wmse_grad.argtypes = [_P, _P, _P, _I64, _P, _P, _P, ctypes.c_size_t, _P]
-        L.star_nt_mlp_backward.argtypes = [ctypes.POINTER(Mlp), _P, _P, _I64, _P, _P, ctypes.c_size_t, _P]
+        L.star_nt_mlp_backward.argtypes = [ctypes.POINTER(Mlp), _P, _P, _I64, _P, _P, ctypes.c_size_t, _P, _P]
         L.star_nt_adam.argtypes = [_P, _P, _P, _P, _I64, _I64, ctypes.c_float, ctypes.c_float,
                                    ctypes.c_float, ctypes.c_float, _P, _P]
         L.star_nt_default_frame_options.argtypes = [ctypes.POINTER(FrameOptions)]
@@ -216,7 +216,7 @@ def lib():
                                                   ctypes.POINTER(Layers), _I32, _I32, ctypes.POINTER(Params),
                                                   ctypes.POINTER(Features), _P, _P]
         L.star_nt_infer_dfaoit.argtypes = [ctypes.POINTER(Mlp), _I32, _P, _P, _I64, _P, _P]
-        L.star_nt_dfaoit_backward.argtypes = [ctypes.POINTER(Mlp), _P, _P, _I64, _P, _P, ctypes.c_size_t, _P]
+        L.star_nt_dfaoit_backward.argtypes = [ctypes.POINTER(Mlp), _P, _P, _I64, _P, _P, ctypes.c_size_t, _P, _P]
         L.star_nt_set_wait_limit.argtypes = [ctypes.c_uint64]
         L.star_nt_wait_limit.restype = ctypes.c_uint64
         for name in EXPORTS:
@@ -441,10 +441,10 @@ def infer_dfaoit(w: Mlp, x_dtype, x, f, P, status=None, stream=None):
                                                               _ptr(status), _stream(stream)))
 
 
-def dfaoit_backward(w: Mlp, x, dy, B, grad, ws, stream=None):
+def dfaoit_backward(w: Mlp, x, dy, B, grad, ws, status=None, stream=None):
     _check("star_nt_dfaoit_backward", lib().star_nt_dfaoit_backward(ctypes.byref(w), _ptr(x), _ptr(dy), int(B),
                                                                     _ptr(grad), _ptr(ws), ws.numel(),
-                                                                    _stream(stream)))
+                                                                    _ptr(status), _stream(stream)))
 
 
 def mlp_struct(w) -> Mlp:
@@ -572,10 +572,10 @@ def mse_grad(f, y, B, dy, loss, ws, stream=None, w=None):
                                                             _stream(stream)))
 
 
-def mlp_backward(w: Mlp, x, dy, B, grad, ws, stream=None):
+def mlp_backward(w: Mlp, x, dy, B, grad, ws, status=None, stream=None):
     _check("star_nt_mlp_backward", lib().star_nt_mlp_backward(ctypes.byref(w), _ptr(x), _ptr(dy), int(B),
                                                               _ptr(grad), _ptr(ws), ws.numel(),
-                                                              _stream(stream)))
+                                                              _ptr(status), _stream(stream)))
 
 
 def adam(params, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, bf16_rounded=None,

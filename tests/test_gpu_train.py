@@ -151,3 +151,65 @@ def test_weighted_mse_kernel(sn):
     assert abs(float(l1.item()) - (wd[:, None] * e * e).sum() / (3 * B)) <= 1e-5 * (1 + abs(float(l1.item())))
     assert np.allclose(dy1.cpu().numpy()[:, :3], 2 * wd[:, None] * e / (3 * B), rtol=1e-5, atol=1e-9)
     assert np.all(dy1.cpu().numpy()[:, 3] == 0)
+
+
+def _grad(sn, flat, x, y):
+    from paper_2606_16747_b300 import train
+    X, Y = torch.tensor(x.reshape(-1), device="cuda"), torch.tensor(y.reshape(-1), device="cuda")
+    p = torch.tensor(flat, device="cuda", requires_grad=True)
+    loss = train.MSEFunction.apply(train.TailMLPFunction.apply(X, p), Y)
+    loss.backward()
+    return float(loss.item()), p.grad.cpu().numpy()
+
+
+@pytest.mark.parametrize("B", [1, 127, 129, 100003])
+def test_backward_batch_sizes(orc, sn, B):
+    """The tensor-core contraction over the batch: a single partial tile, a
+    ragged last tile, and (100,003 samples: 782 tiles) several tiles per CTA
+    accumulated in tensor memory; the gradient within float32 rounding of
+    the oracle's float64 one."""
+    rng = np.random.default_rng(B)
+    x, y = _synthetic(rng, B)
+    flat = scenes.mlp_flat(scenes.mlp_xavier(7))
+    flat[160:192] += 0.1
+    lo, go = orc.mlp_mse_grad(flat.astype(np.float64), x[:, :5].astype(np.float64), y[:, :3].astype(np.float64))
+    loss, g = _grad(sn, flat, x, y)
+    assert loss == pytest.approx(lo, rel=1e-5)
+    scale = np.abs(go).max()
+    assert np.max(np.abs(g - go)) <= 1e-5 * scale + 1e-9
+
+
+def test_backward_expired_wait(sn):
+    """A tensor-core wait that runs out (bound 0) reports STAR_NT_ERR_TIMEOUT
+    and poisons the gradient with NaN instead of returning a partial sum; the
+    next call with the default bound gives the same bits as before."""
+    rng = np.random.default_rng(3)
+    B = 3000
+    x, y = _synthetic(rng, B)
+    flat = scenes.mlp_flat(scenes.mlp_xavier(8))
+    params = torch.tensor(flat, device="cuda")
+    from paper_2606_16747_b300 import train
+    X = torch.tensor(x.reshape(-1), device="cuda")
+    dy = torch.tensor(rng.standard_normal((B, 4)).astype(np.float32).reshape(-1), device="cuda")
+    ws = torch.empty(sn.train_ws_bytes(B), dtype=torch.uint8, device="cuda")
+    mlp = train.mlp_from_flat(params)
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    g0 = torch.empty(771, device="cuda")
+    sn.mlp_backward(mlp, X, dy, B, g0, ws, status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == sn.OK and torch.isfinite(g0).all()
+    g1 = torch.empty(771, device="cuda")
+    sn.set_wait_limit(0)
+    try:
+        sn.mlp_backward(mlp, X, dy, B, g1, ws, status)
+        torch.cuda.synchronize()
+    finally:
+        sn.set_wait_limit(10 ** 9)
+    assert int(status.item()) == sn.ERR_TIMEOUT
+    assert torch.isnan(g1).all()
+    status.zero_()
+    g2 = torch.empty(771, device="cuda")
+    sn.mlp_backward(mlp, X, dy, B, g2, ws, status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == sn.OK
+    assert torch.equal(g0, g2)
