@@ -412,13 +412,28 @@ __global__ void __launch_bounds__(128, kGradCtasPerSm)
   if (tid == 0 && abort_flag) raise_status(status, STAR_NT_ERR_TIMEOUT);
 }
 
-__global__ void k_mlp_bwd_reduce(const float *__restrict__ partial, int chunks, int n_params,
-                                 float *__restrict__ grad) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= n_params) return;
+// grad[p] = the sum over rows c of partial[c][p] in a fixed order: warp w of
+// a block adds rows w, w + 16, w + 32, ... for its block's 32 parameters
+// (lane = parameter), then warp 0 adds the 16 warp sums in warp order
+constexpr int kReduceWarps = 16;
+__global__ void __launch_bounds__(32 * kReduceWarps) k_mlp_bwd_reduce(const float *__restrict__ partial, int rows,
+                                                                     int n_params, float *__restrict__ grad) {
+  __shared__ float s[kReduceWarps][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int p = blockIdx.x * 32 + lane;
   float t = 0.0f;
-  for (int c = 0; c < chunks; ++c) t += partial[(size_t)c * n_params + p];
-  grad[p] = t;
+  if (p < n_params) {
+#pragma unroll 4
+    for (int c = warp; c < rows; c += kReduceWarps) t += partial[(size_t)c * n_params + p];
+  }
+  s[warp][lane] = t;
+  __syncthreads();
+  if (warp == 0 && p < n_params) {
+    float u = 0.0f;
+#pragma unroll
+    for (int w = 0; w < kReduceWarps; ++w) u += s[w][lane];
+    grad[p] = u;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -522,7 +537,7 @@ static star_nt_status mlp_backward(const star_nt_mlp *w, const float *x, const f
   k_mlp_grad_tc<NIN, SIGMOID><<<grid, 128, kGradSmem, st>>>(
       w->w1, w->b1, w->w2, w->b2, w->w3, w->b3, reinterpret_cast<const float4 *>(x),
       reinterpret_cast<const float4 *>(dy), B, (int)n_tiles, partial, wait_limit_ns(), d_status);
-  k_mlp_bwd_reduce<<<(N::kParams + 255) / 256, 256, 0, st>>>(partial, grid, N::kParams, grad);
+  k_mlp_bwd_reduce<<<(N::kParams + 31) / 32, 32 * kReduceWarps, 0, st>>>(partial, grid, N::kParams, grad);
   return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
 }
 
