@@ -59,8 +59,8 @@ STAGE_REPS = 20
 # dram__bytes_write.sum); per workload, None where no capture of the current
 # kernel exists.  k_passes2: the persistent passes with pass 3 separate;
 # k_passes_resolve: every pass at full size, with the network and composite.
-PASSES_DRAM_BYTES = {"hd": 15031552, "uhd": None}
-FUSED_DRAM_BYTES = {"hd": 7815680, "uhd": 189930240}
+PASSES_DRAM_BYTES = {"hd": 14948608, "uhd": 172221696}
+FUSED_DRAM_BYTES = {"hd": 7855872, "uhd": 190114560}
 
 
 def stage_rooflines(star, torch, stage_state, stage_mean, hbm_gbs):

@@ -81,14 +81,19 @@ struct PassAcc {
   // A fragment at depth z offered to the KM nearest, ordered by (depth, id).
   template <int KM>
   __device__ __forceinline__ void insert(float z, int id) {
+    const bool lt1 = z < z1 || (z == z1 && id < i1);
     if (KM == kTop1) {
-      if (z < z1 || (z == z1 && id < i1)) { z1 = z; i1 = id; }
-    } else if (z < z2 || (z == z2 && id < i2)) {
-      if (z < z1 || (z == z1 && id < i1)) {
-        z2 = z1; i2 = i1; z1 = z; i1 = id;
-      } else {
-        z2 = z; i2 = id;
-      }
+      z1 = lt1 ? z : z1;
+      i1 = lt1 ? id : i1;
+    } else {
+      // (z1, i1) precedes (z2, i2), so lt1 implies lt2
+      const bool lt2 = z < z2 || (z == z2 && id < i2);
+      const float nz2 = lt1 ? z1 : z;
+      const int ni2 = lt1 ? i1 : id;
+      z2 = lt2 ? nz2 : z2;
+      i2 = lt2 ? ni2 : i2;
+      z1 = lt1 ? z : z1;
+      i1 = lt1 ? id : i1;
     }
   }
 

@@ -152,6 +152,10 @@ __device__ __forceinline__ void walk_tile2(const BinsView &bv, int tile, const T
   const int lx = tp.px - tp.tx0, ly = tp.py - tp.ty0;  // the second pixel is BH rows below
   const int bxl = tp.bx0 - tp.tx0, byl = tp.by0 - tp.ty0;
   const int Px = tp.px * kSub + kSub / 2, Py0 = tp.py * kSub + kSub / 2, Py1 = Py0 + BH * kSub;
+  // a pixel outside the target never stores: its bounds start below every
+  // depth, so it never evaluates one
+  if (!in0) a0.z1 = a0.z2 = -INFINITY;
+  if (!in1) a1.z1 = a1.z2 = -INFINITY;
   const uint32_t beg = bv.tile_offset[tile], end = bv.tile_offset[tile + 1];
   for (uint32_t base = beg; base < end; base += kWalkChunk) {
     const int n = (int)min((uint32_t)kWalkChunk, end - base);
@@ -169,9 +173,9 @@ __device__ __forceinline__ void walk_tile2(const BinsView &bv, int tile, const T
     for (int i = 0; i < m; ++i) {  // m is warp-uniform
       const int k = st.list[warp][i];
       const TriSetup &T = st.tri[k];
-      // the k-th depth of each pixel; a pixel outside the target never stores
-      const float b0 = in0 ? (KM == 1 ? a0.z1 : a0.z2) : -INFINITY;
-      const float b1 = in1 ? (KM == 1 ? a1.z1 : a1.z2) : -INFINITY;
+      // the k-th depth of each pixel
+      const float b0 = KM == 1 ? a0.z1 : a0.z2;
+      const float b1 = KM == 1 ? a1.z1 : a1.z2;
       // without tail sums no later triangle of the round can matter once this
       // one lies behind every lane's bound (sorted keys, falling bounds)
       if (!TAIL && __all_sync(0xffffffffu, T.zlo > fmaxf(b0, b1))) break;
