@@ -22,8 +22,10 @@
 // Each staging round sorts the tile's binned triangles by depth lower bound
 // (ties by binned position), so that near triangles come first: a pixel then
 // evaluates the depth of a fragment only while the fragment may still enter
-// its k nearest, and the passes without tail sums stop a warp's walk at the
-// first triangle that lies behind every lane's k-th depth.
+// its k nearest.  From the first triangle that lies behind every lane's k-th
+// depth on, no later one of the round can enter any pixel's k nearest: the
+// passes without tail sums stop the warp's walk there, and the tail passes
+// finish the round in a loop that only tests coverage and adds tail sums.
 #pragma once
 
 #include "raster_tile.cuh"
@@ -170,15 +172,17 @@ __device__ __forceinline__ void walk_tile2(const BinsView &bv, int tile, const T
       m += __popc(b);
     }
     __syncwarp();
-    for (int i = 0; i < m; ++i) {  // m is warp-uniform
+    int i = 0;
+    for (; i < m; ++i) {  // m is warp-uniform
       const int k = st.list[warp][i];
       const TriSetup &T = st.tri[k];
       // the k-th depth of each pixel
       const float b0 = KM == 1 ? a0.z1 : a0.z2;
       const float b1 = KM == 1 ? a1.z1 : a1.z2;
-      // without tail sums no later triangle of the round can matter once this
-      // one lies behind every lane's bound (sorted keys, falling bounds)
-      if (!TAIL && __all_sync(0xffffffffu, T.zlo > fmaxf(b0, b1))) break;
+      // once this triangle lies behind every lane's bound, so does every
+      // later one of the round (sorted keys, falling bounds): no depth is
+      // needed any more, only the tail sums below
+      if (__all_sync(0xffffffffu, T.zlo > fmaxf(b0, b1))) break;
       const int4 te = st.te[k];
       const int dx0 = T.dx[0], dx1 = T.dx[1], dx2 = T.dx[2];
       const int ga = te.x + dx0 * ly - T.dy[0] * lx;
@@ -195,6 +199,18 @@ __device__ __forceinline__ void walk_tile2(const BinsView &bv, int tile, const T
       if (c1) {
         if (TAIL) a1.template accumulate<MODE>(T);
         if (!(T.zlo > b1)) a1.template insert<KM>(frag_depth_tile(T, ha, hc, (uint32_t)te.w, Px, Py1), id);
+      }
+    }
+    if (TAIL) {
+      for (; i < m; ++i) {  // the rest of the round: coverage and tail sums
+        const TriSetup &T = st.tri[st.list[warp][i]];
+        const int4 te = st.te[st.list[warp][i]];
+        const int dx0 = T.dx[0], dx1 = T.dx[1], dx2 = T.dx[2];
+        const int ga = te.x + dx0 * ly - T.dy[0] * lx;
+        const int gb = te.y + dx1 * ly - T.dy[1] * lx;
+        const int gc = te.z + dx2 * ly - T.dy[2] * lx;
+        if ((ga | gb | gc) >= 0) a0.template accumulate<MODE>(T);
+        if (((ga + dx0 * BH) | (gb + dx1 * BH) | (gc + dx2 * BH)) >= 0) a1.template accumulate<MODE>(T);
       }
     }
   }
