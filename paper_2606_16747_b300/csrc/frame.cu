@@ -219,38 +219,33 @@ __device__ __forceinline__ FF ff_norm(float s, float e) {  // |s| >= |e|
   const float h = __fadd_rn(s, e);
   return FF{h, __fsub_rn(e, __fsub_rn(h, s))};
 }
-// c[0..7] = (hi, lo) of the coefficients of (px, py, d, 1): the row's value
-__device__ __forceinline__ FF ff_row(const float *c, float px, float py, float d) {
-  float s = __fmul_rn(c[0], px);
-  float e = __fmaf_rn(c[1], px, __fmaf_rn(c[0], px, -s));
-  const float t[2] = {py, d};
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const float p = __fmul_rn(c[2 + 2 * k], t[k]);
-    const float q = __fmaf_rn(c[3 + 2 * k], t[k], __fmaf_rn(c[2 + 2 * k], t[k], -p));
-    float s2, e2;
-    two_sum(s, p, s2, e2);
-    e = __fadd_rn(e, __fadd_rn(q, e2));
-    s = s2;
-  }
-  float s2, e2;
-  two_sum(s, c[6], s2, e2);
-  e = __fadd_rn(e, __fadd_rn(c[7], e2));
-  return ff_norm(s2, e);
+// hi + lo of c t for a float-float coefficient c and a float t (the product
+// of the hi parts error-free by FMA)
+__device__ __forceinline__ FF ff_mul_f(float ch, float cl, float t) {
+  const float p = __fmul_rn(ch, t);
+  return FF{p, __fmaf_rn(cl, t, __fmaf_rn(ch, t, -p))};
 }
-// (b - t a) / den, b, a, den float-float, t a float: one Newton correction of
-// the float quotient
-__device__ __forceinline__ FF ff_offset(FF b, float t, FF a, FF den, float rden) {
-  const float p = __fmul_rn(a.hi, t);
-  const float q = __fmaf_rn(a.lo, t, __fmaf_rn(a.hi, t, -p));
+// a row's value L + c2 d, where L = (c0 px) + (c1 py + c3) comes as the
+// block's column and row terms (unnormalised float-float pairs) and c2 d is
+// taken here
+__device__ __forceinline__ FF ff_row_split(FF col, FF row, float c2h, float c2l, float d) {
   float s, e;
-  two_sum(b.hi, -p, s, e);
-  const FF num = ff_norm(s, __fadd_rn(e, __fsub_rn(b.lo, q)));
-  const float q1 = __fmul_rn(num.hi, rden);
-  const float m = __fmul_rn(q1, den.hi);
-  const float me = __fmaf_rn(q1, den.hi, -m);
-  const float r = __fsub_rn(__fsub_rn(__fsub_rn(num.hi, m), me), __fmaf_rn(q1, den.lo, -num.lo));
-  return ff_norm(q1, __fmul_rn(r, rden));
+  two_sum(row.hi, col.hi, s, e);
+  e = __fadd_rn(e, __fadd_rn(row.lo, col.lo));
+  const FF pd = ff_mul_f(c2h, c2l, d);
+  float s2, e2;
+  two_sum(s, pd.hi, s2, e2);
+  return ff_norm(s2, __fadd_rn(e, __fadd_rn(pd.lo, e2)));
+}
+// (b - t a) inv, inv a float-float reciprocal of the denominator
+__device__ __forceinline__ FF ff_offset_inv(FF b, float t, FF a, FF inv) {
+  const FF ta = ff_mul_f(a.hi, a.lo, t);
+  float s, e;
+  two_sum(b.hi, -ta.hi, s, e);
+  const FF num = ff_norm(s, __fadd_rn(e, __fsub_rn(b.lo, ta.lo)));
+  const float q = __fmul_rn(num.hi, inv.hi);
+  const float r = __fmaf_rn(num.hi, inv.hi, -q);
+  return ff_norm(q, __fadd_rn(r, __fmaf_rn(num.hi, inv.lo, __fmul_rn(num.lo, inv.hi))));
 }
 // integer part and fractional weight of x + o (o float-float, |o| < 2^22)
 __device__ __forceinline__ void ff_split(int x, FF o, int &i, float &f) {
@@ -267,17 +262,34 @@ __global__ void __launch_bounds__(256) k_reproject(const float4 *__restrict__ pr
                                                    const float *__restrict__ Cg, int W, int H,
                                                    float4 *__restrict__ out,
                                                    uint32_t *__restrict__ q) {
-  __shared__ float sC[24];
-  if (threadIdx.x < 24) sC[threadIdx.x] = Cg[threadIdx.x];
+  // per block of 32 x 8 pixels, each coefficient row's (px) and (py, 1)
+  // parts once: s_col[row][column] = c0 px, s_row[row][y] = c1 py + c3
+  __shared__ FF s_col[3][32], s_row[3][8];
+  const int t = threadIdx.x;
+  if (t < 96) {
+    const int k = t >> 5, c = t & 31;
+    const int xc = (int)blockIdx.x * 32 + c;
+    const float px = 0.5f * (float)(2 * xc + 1 - W);
+    s_col[k][c] = ff_mul_f(__ldg(Cg + 8 * k), __ldg(Cg + 8 * k + 1), px);
+  } else if (t < 120) {
+    const int k = (t - 96) >> 3, r = (t - 96) & 7;
+    const int yr = (int)blockIdx.y * 8 + r;
+    const float py = 0.5f * (float)(2 * yr + 1 - H);
+    const FF p = ff_mul_f(__ldg(Cg + 8 * k + 2), __ldg(Cg + 8 * k + 3), py);
+    float s, e;
+    two_sum(p.hi, __ldg(Cg + 8 * k + 6), s, e);
+    s_row[k][r] = FF{s, __fadd_rn(e, __fadd_rn(p.lo, __ldg(Cg + 8 * k + 7)))};
+  }
   __syncthreads();
-  const int x = blockIdx.x * 32 + (threadIdx.x & 31);
-  const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
+  const int lx = t & 31, ly = t >> 5;
+  const int x = blockIdx.x * 32 + lx;
+  const int y = blockIdx.y * 8 + ly;
   if (x >= W || y >= H) return;
   const size_t p = (size_t)y * W + x;
   // pixel centre relative to the image centre: exact half-integers
   const float px = 0.5f * (float)(2 * x + 1 - W), py = 0.5f * (float)(2 * y + 1 - H);
   const float d = z1[p];
-  const FF a3 = ff_row(sC + 16, px, py, d);
+  const FF a3 = ff_row_split(s_col[2][lx], s_row[2][ly], __ldg(Cg + 20), __ldg(Cg + 21), d);
   float s, e;
   two_sum(1.0f, a3.hi, s, e);
   const FF den = ff_norm(s, __fadd_rn(e, a3.lo));
@@ -287,12 +299,15 @@ __global__ void __launch_bounds__(256) k_reproject(const float4 *__restrict__ pr
     if (q) q[p] = quantize_rgba8(v);
     return;
   }
-  const float rden = __frcp_rn(den.hi);
-  FF dx = ff_offset(ff_row(sC, px, py, d), px, a3, den, rden);
-  FF dy = ff_offset(ff_row(sC + 8, px, py, d), py, a3, den, rden);
-  const float lx = 2.0f * W + 2.0f, ly = 2.0f * H + 2.0f;  // far outside: clamped to the edge anyway
-  if (!(fabsf(dx.hi) <= lx)) dx = FF{copysignf(lx, dx.hi), 0.0f};
-  if (!(fabsf(dy.hi) <= ly)) dy = FF{copysignf(ly, dy.hi), 0.0f};
+  // 1 / den to float-float: one Newton step from the float reciprocal
+  const float r0 = __frcp_rn(den.hi);
+  const float res = __fmaf_rn(-den.lo, r0, __fmaf_rn(-den.hi, r0, 1.0f));
+  const FF inv = ff_norm(r0, __fmul_rn(r0, res));
+  FF dx = ff_offset_inv(ff_row_split(s_col[0][lx], s_row[0][ly], __ldg(Cg + 4), __ldg(Cg + 5), d), px, a3, inv);
+  FF dy = ff_offset_inv(ff_row_split(s_col[1][lx], s_row[1][ly], __ldg(Cg + 12), __ldg(Cg + 13), d), py, a3, inv);
+  const float lxb = 2.0f * W + 2.0f, lyb = 2.0f * H + 2.0f;  // far outside: clamped to the edge anyway
+  if (!(fabsf(dx.hi) <= lxb)) dx = FF{copysignf(lxb, dx.hi), 0.0f};
+  if (!(fabsf(dy.hi) <= lyb)) dy = FF{copysignf(lyb, dy.hi), 0.0f};
   int ix, iy;
   float fx, fy;
   ff_split(x, dx, ix, fx);
