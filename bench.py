@@ -38,7 +38,7 @@ FALLBACK_PEAKS = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustain
                   "sm_max_mhz": 2032.0}
 N_SM = 148
 ALU_LANES_PER_SM = 128
-OPS_PER_FRAGMENT = 32     # algorithmic integer/fp operations per fragment (see design notes)
+OPS_PER_FRAGMENT = 31     # algorithmic integer/fp operations per fragment (see design notes)
 
 
 def kernels_per_step(r) -> int:
@@ -59,8 +59,8 @@ STAGE_REPS = 20
 # dram__bytes_write.sum); per workload, None where no capture of the current
 # kernel exists.  k_passes2: the persistent passes with pass 3 separate;
 # k_passes_resolve: every pass at full size, with the network and composite.
-PASSES_DRAM_BYTES = {"hd": 14944256, "uhd": 172247808}
-FUSED_DRAM_BYTES = {"hd": 7908608, "uhd": 190296832}
+PASSES_DRAM_BYTES = {"hd": 16009216, "uhd": 173463808}
+FUSED_DRAM_BYTES = {"hd": 7838208, "uhd": 190099456}
 
 
 def stage_rooflines(star, torch, stage_state, stage_mean, hbm_gbs):

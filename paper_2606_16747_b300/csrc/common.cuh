@@ -24,10 +24,11 @@ struct __align__(16) TriSetup {
   float z0, dz1, dz2, r;      // depth plane: z = (z0 + b1 dz1) + b2 dz2, r = 1/area
   int16_t xa, xb, ya, yb;     // covered-pixel bounding box (clamped), empty if xa > xb
   uint32_t own;               // bit e set: edge e owns ties; kOwnSmall: area < 2^31
-  uint32_t opq;               // 1 when a8 == 255
+  uint32_t opq;               // 1 when a8 == 255 (the comparison renderers' opaque count)
   unsigned long long rg;      // a8*r8 | (a8*g8) << 32
   unsigned long long ba;      // a8*b8 | a8 << 32
-  unsigned long long lg;      // round(-log2(1 - a8/255) * 2^32), 0 when opaque
+  unsigned long long lg;      // round(-log2(1 - a8/255) * 2^32); 160 * 2^32 when opaque (a sum
+                              // holding it has tail transmittance exactly 0)
   float zlo;                  // lower bound of every fragment depth of the triangle
   uint32_t c8;                // straight colour: r8 | g8 << 8 | b8 << 16
 };

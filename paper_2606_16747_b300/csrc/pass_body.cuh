@@ -44,14 +44,14 @@ struct PassOut {
 struct PassAcc {
   float z1, z2;
   int i1, i2;
-  uint32_t N, opq;
+  uint32_t N;
   unsigned long long rg, ba, lg;
   unsigned long long cs;  // straight colour sums (kFusedDfaoit only)
 
   __device__ __forceinline__ void reset() {
     z1 = z2 = INFINITY;
     i1 = i2 = 0x7fffffff;
-    N = opq = 0u;
+    N = 0u;
     rg = ba = lg = 0ull;
     cs = 0ull;
   }
@@ -74,7 +74,6 @@ struct PassAcc {
     rg += T.rg;
     ba += T.ba;
     lg += T.lg;
-    opq += T.opq;
     if (MODE == kFusedDfaoit) cs += spread_rgb(T.c8);
   }
 
@@ -116,15 +115,15 @@ struct PassAcc {
     if (po.z1) po.z1[p] = has1 ? z1 : 1.0f;
     if (has1) {
       const TriSetup &S = setups[i1];
-      rg -= S.rg; ba -= S.ba; lg -= S.lg; opq -= S.opq;
+      rg -= S.rg; ba -= S.ba; lg -= S.lg;
     }
     if (has2) {
       const TriSetup &S = setups[i2];
-      rg -= S.rg; ba -= S.ba; lg -= S.lg; opq -= S.opq;
+      rg -= S.rg; ba -= S.ba; lg -= S.lg;
     }
     const uint32_t A = (uint32_t)(ba >> 32), Sr = (uint32_t)rg, Sg = (uint32_t)(rg >> 32),
                    Sb = (uint32_t)ba;
-    const float t = tail_transmittance(lg, opq);
+    const float t = tail_transmittance(lg, 0u);
     float r1 = 0, g1 = 0, b1 = 0, a1 = 0, r2 = 0, g2 = 0, b2 = 0, a2 = 0;
     if (has1) unpack_rgba(__ldg(rgba8 + i1), r1, g1, b1, a1);
     if (has2) unpack_rgba(__ldg(rgba8 + i2), r2, g2, b2, a2);
@@ -144,17 +143,17 @@ struct PassAcc {
     if (MODE >= kTail) {
       if (has1) {
         const TriSetup &S = setups[i1];
-        rg -= S.rg; ba -= S.ba; lg -= S.lg; opq -= S.opq;
+        rg -= S.rg; ba -= S.ba; lg -= S.lg;
         if (MODE == kFusedDfaoit) cs -= spread_rgb(S.c8);
       }
       if (has2) {
         const TriSetup &S = setups[i2];
-        rg -= S.rg; ba -= S.ba; lg -= S.lg; opq -= S.opq;
+        rg -= S.rg; ba -= S.ba; lg -= S.lg;
         if (MODE == kFusedDfaoit) cs -= spread_rgb(S.c8);
       }
       const uint32_t A = (uint32_t)(ba >> 32), Sr = (uint32_t)rg, Sg = (uint32_t)(rg >> 32),
                      Sb = (uint32_t)ba;
-      const float t = tail_transmittance(lg, opq);
+      const float t = tail_transmittance(lg, 0u);
       if (po.n) po.n[p] = N;
       if (po.tail) po.tail[p] = make_uint4(A, Sr, Sg, Sb);
       if (po.t_tail) po.t_tail[p] = t;

@@ -38,7 +38,9 @@ constexpr LgTable make_lg_table() {
     const double v = series_log2(255.0 / (255.0 - a)) * 4294967296.0;
     t.v[a] = (unsigned long long)(v + 0.5);
   }
-  t.v[255] = 0ull;  // opaque: counted apart
+  // opaque: past the exponent at which the tail transmittance is exactly 0,
+  // so a sum holding an opaque fragment gives 0
+  t.v[255] = 160ull << 32;
   return t;
 }
 
