@@ -299,8 +299,10 @@ __global__ void __launch_bounds__(256) k_reproject(const float4 *__restrict__ pr
     if (q) q[p] = quantize_rgba8(v);
     return;
   }
-  // 1 / den to float-float: one Newton step from the float reciprocal
-  const float r0 = __frcp_rn(den.hi);
+  // 1 / den to float-float: one Newton step from the approximate float
+  // reciprocal (relative error 2^-22 squared by the step)
+  float r0;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(den.hi));
   const float res = __fmaf_rn(-den.lo, r0, __fmaf_rn(-den.hi, r0, 1.0f));
   const FF inv = ff_norm(r0, __fmul_rn(r0, res));
   FF dx = ff_offset_inv(ff_row_split(s_col[0][lx], s_row[0][ly], __ldg(Cg + 4), __ldg(Cg + 5), d), px, a3, inv);
@@ -314,14 +316,17 @@ __global__ void __launch_bounds__(256) k_reproject(const float4 *__restrict__ pr
   ff_split(y, dy, iy, fy);
   const int x0 = min(max(ix, 0), W - 1), x1 = min(max(ix + 1, 0), W - 1);
   const int y0 = min(max(iy, 0), H - 1), y1 = min(max(iy + 1, 0), H - 1);
-  const float4 v00 = prev[(size_t)y0 * W + x0], v10 = prev[(size_t)y0 * W + x1];
-  const float4 v01 = prev[(size_t)y1 * W + x0], v11 = prev[(size_t)y1 * W + x1];
+  // W, H <= 32768: pixel indices fit 32 bits
+  const float4 *r0p = prev + y0 * W, *r1p = prev + y1 * W;
+  const float4 v00 = r0p[x0], v10 = r0p[x1], v01 = r1p[x0], v11 = r1p[x1];
   float4 o;
   o.x = (1.f - fy) * ((1.f - fx) * v00.x + fx * v10.x) + fy * ((1.f - fx) * v01.x + fx * v11.x);
   o.y = (1.f - fy) * ((1.f - fx) * v00.y + fx * v10.y) + fy * ((1.f - fx) * v01.y + fx * v11.y);
   o.z = (1.f - fy) * ((1.f - fx) * v00.z + fx * v10.z) + fy * ((1.f - fx) * v01.z + fx * v11.z);
-  o.w = (1.f - fy) * ((1.f - fx) * v00.w + fx * v10.w) + fy * ((1.f - fx) * v01.w + fx * v11.w);
-  if (out) out[p] = o;
+  if (out) {  // the 8-bit copy takes no alpha
+    o.w = (1.f - fy) * ((1.f - fx) * v00.w + fx * v10.w) + fy * ((1.f - fx) * v01.w + fx * v11.w);
+    out[p] = o;
+  }
   if (q) q[p] = quantize_rgba8(o);
 }
 
