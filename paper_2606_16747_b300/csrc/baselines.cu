@@ -58,8 +58,9 @@ __device__ __forceinline__ float wboit_weight(float d, float a) {
 
 // WBOIT in one pass over the binned tiles of a full-resolution target: per
 // pixel the sums of (a c) w and a w with w = w(d, a), and the product of
-// (1 - a) (kept, order-free, as a fixed-point -log2 sum and an opaque count,
-// as in the tail statistics); then
+// (1 - a) (kept, order-free, as a fixed-point -log2 sum and an opaque count;
+// the sum alone also gives 0 for an opaque fragment, as in the tail
+// statistics); then
 // C = (sum (a c) w / max(sum a w, 1e-5)) (1 - T) + T C_b.
 // View depth from NDC z in [0, 1]: d = n f / (f - z (f - n)).
 __global__ void __launch_bounds__(256) k_wboit(BinsView bv, float znear, float zfar, float bg0,
