@@ -203,6 +203,8 @@ star_nt_status star_nt_raster_passes(const star_nt_scene *scene, int32_t n_passe
 /*           T_2 = (1 - a1)(1 - a2).                                         */
 /* When the three bins are the same object every pass runs at full           */
 /* resolution in one fused kernel (the plain neural OIT pipeline).           */
+/* The tail sums are exact integers (uint32 per channel) for up to 66,052    */
+/* fragments per pixel, where sum a8 c8 reaches 2^32; beyond that they wrap. */
 
 /* Per-pass planes at the pass's resolution; members may be NULL when not
  * wanted.  tail is [P][4] uint32: sum a8, sum a8 r8, sum a8 g8, sum a8 b8. */
