@@ -633,6 +633,14 @@ star_nt_status star_nt_mlp_backward(const star_nt_mlp *w, const float *x, const 
 star_nt_status star_nt_adam(float *params, const float *grad, float *m, float *v, int64_t n,
                             int64_t step, float lr, float beta1, float beta2, float eps,
                             float *bf16_rounded, void *stream);
+/* star_nt_gather_rows: the minibatch rows of a training step (Sec. 3.3 trains
+ * on randomly drawn samples): dst[i] = src[idx[i]] for i < n, rows of
+ * row_bytes bytes (a multiple of 4); src [n_src] rows, idx [n] int64, all
+ * device memory (src, dst 4-byte aligned, idx 8-byte aligned).  An index
+ * outside [0, n_src) writes a zero row and STAR_NT_ERR_ARG to d_status (device
+ * int32, may be NULL). */
+star_nt_status star_nt_gather_rows(const void *src, int64_t n_src, int32_t row_bytes, const int64_t *idx,
+                                   int64_t n, void *dst, int32_t *d_status, void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* The DFAOIT comparison network (Sec. 3.3; Table 2's "Inf. DFAOIT" column):  */

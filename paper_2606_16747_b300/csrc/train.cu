@@ -553,6 +553,57 @@ extern "C" star_nt_status star_nt_dfaoit_backward(const star_nt_mlp *w, const fl
   return mlp_backward<11, true>(w, x, dy, B, grad, ws, ws_bytes, d_status, stream);
 }
 
+// ---------------------------------------------------------------------------
+// Minibatch rows: dst[i] = src[idx[i]] for rows of row_bytes bytes, in 16-byte
+// chunks when rows and both bases allow it, else 4-byte words; one thread per
+// chunk (grid-stride).  An index outside [0, n_src) is reported in the status
+// word and its row is written as zeros.
+template <class T>
+__global__ void __launch_bounds__(256) k_gather_rows(const T *__restrict__ src, long long n_src,
+                                                     const int64_t *__restrict__ idx, long long n, int per_row,
+                                                     T *__restrict__ dst, int32_t *status) {
+  const long long total = n * per_row;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total;
+       k += (long long)gridDim.x * blockDim.x) {
+    const long long i = k / per_row;
+    const int c = (int)(k - i * per_row);
+    const long long r = __ldg(idx + i);
+    T v;
+    if (r >= 0 && r < n_src) {
+      v = __ldg(src + r * per_row + c);
+    } else {
+      v = T();
+      if (c == 0) raise_status(status, STAR_NT_ERR_ARG);
+    }
+    dst[k] = v;
+  }
+}
+
+extern "C" star_nt_status star_nt_gather_rows(const void *src, int64_t n_src, int32_t row_bytes,
+                                              const int64_t *idx, int64_t n, void *dst, int32_t *d_status,
+                                              void *stream) {
+  if (!src || !idx || !dst || n_src <= 0 || n < 0 || row_bytes <= 0 || (row_bytes & 3) ||
+      row_bytes > (1 << 20) || ((uintptr_t)src & 3u) || ((uintptr_t)dst & 3u) || ((uintptr_t)idx & 7u))
+    return STAR_NT_ERR_ARG;
+  if (n == 0) return STAR_NT_OK;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool wide = (row_bytes & 15) == 0 && !((uintptr_t)src & 15u) && !((uintptr_t)dst & 15u);
+  const int per_row = wide ? row_bytes / 16 : row_bytes / 4;
+  const long long total = (long long)n * per_row;
+  long long grid = (total + 255) / 256;
+  if (grid > (long long)sms * 16) grid = (long long)sms * 16;
+  if (wide)
+    k_gather_rows<uint4><<<(unsigned)grid, 256, 0, st>>>(static_cast<const uint4 *>(src), n_src, idx, n, per_row,
+                                                          static_cast<uint4 *>(dst), d_status);
+  else
+    k_gather_rows<uint32_t><<<(unsigned)grid, 256, 0, st>>>(static_cast<const uint32_t *>(src), n_src, idx, n,
+                                                             per_row, static_cast<uint32_t *>(dst), d_status);
+  return cudaGetLastError() == cudaSuccess ? STAR_NT_OK : STAR_NT_ERR_CUDA;
+}
+
 extern "C" star_nt_status star_nt_adam(float *params, const float *grad, float *m, float *v, int64_t n,
                                        int64_t step, float lr, float beta1, float beta2, float eps,
                                        float *bf16_rounded, void *stream) {
@@ -576,6 +627,8 @@ cudaError_t preload_train() {
   if ((r = cudaFuncGetAttributes(&a, k_mlp_grad_tc<11, true>)) != cudaSuccess) e = r;
   if ((r = cudaFuncGetAttributes(&a, k_mlp_bwd_reduce)) != cudaSuccess) e = r;
   if ((r = cudaFuncGetAttributes(&a, k_adam)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_gather_rows<uint4>)) != cudaSuccess) e = r;
+  if ((r = cudaFuncGetAttributes(&a, k_gather_rows<uint32_t>)) != cudaSuccess) e = r;
   return e;
 }
 }  // namespace star

@@ -34,7 +34,8 @@ EXPORTS = ("star_nt_version", "star_nt_status_string", "star_nt_default_params",
            "star_nt_wait_limit", "star_nt_default_frame_options", "star_nt_create", "star_nt_destroy",
            "star_nt_workspace_size", "star_nt_bind_workspace", "star_nt_frame", "star_nt_tune",
            "star_nt_ctx_tuning", "star_nt_ctx_set_tuning", "star_nt_ctx_pass_state", "star_nt_resolve_mlp",
-           "star_nt_build_inputs_dfaoit", "star_nt_infer_dfaoit", "star_nt_dfaoit_backward")
+           "star_nt_build_inputs_dfaoit", "star_nt_infer_dfaoit", "star_nt_dfaoit_backward",
+           "star_nt_gather_rows")
 
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
@@ -198,6 +199,7 @@ def lib():
         L.star_nt_mlp_backward.argtypes = [ctypes.POINTER(Mlp), _P, _P, _I64, _P, _P, ctypes.c_size_t, _P, _P]
         L.star_nt_adam.argtypes = [_P, _P, _P, _P, _I64, _I64, ctypes.c_float, ctypes.c_float,
                                    ctypes.c_float, ctypes.c_float, _P, _P]
+        L.star_nt_gather_rows.argtypes = [_P, _I64, _I32, _P, _I64, _P, _P, _P]
         L.star_nt_default_frame_options.argtypes = [ctypes.POINTER(FrameOptions)]
         L.star_nt_default_frame_options.restype = None
         L.star_nt_create.argtypes = [_I32, ctypes.POINTER(Params), ctypes.POINTER(FrameOptions),
@@ -576,6 +578,17 @@ def mlp_backward(w: Mlp, x, dy, B, grad, ws, status=None, stream=None):
     _check("star_nt_mlp_backward", lib().star_nt_mlp_backward(ctypes.byref(w), _ptr(x), _ptr(dy), int(B),
                                                               _ptr(grad), _ptr(ws), ws.numel(),
                                                               _ptr(status), _stream(stream)))
+
+
+def gather_rows(src, idx, dst, status=None, stream=None):
+    """dst[i] = src[idx[i]] (row-major tensors with equal row sizes; idx int64)."""
+    n_src = src.shape[0]
+    row_bytes = src.numel() * src.element_size() // max(1, n_src)
+    if dst.shape[0] != idx.numel() or dst.numel() * dst.element_size() != idx.numel() * row_bytes:
+        raise ValueError("gather_rows: dst must hold idx.numel() rows of the source's size")
+    _check("star_nt_gather_rows", lib().star_nt_gather_rows(_ptr(src), int(n_src), int(row_bytes), _ptr(idx),
+                                                            int(idx.numel()), _ptr(dst), _ptr(status),
+                                                            _stream(stream)))
 
 
 def adam(params, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, bf16_rounded=None,

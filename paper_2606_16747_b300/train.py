@@ -240,7 +240,7 @@ def train(x, y, steps=3000, batch=65536, lr=3e-3, seed=0, init=None, log=print, 
     forward uses the bf16-rounded copy.  w [N]: per-sample loss weights.
     net: "tail" (the 5-input tail MLP) or "dfaoit" (the comparison network)."""
     device = x.device
-    g = torch.Generator(device="cpu").manual_seed(seed)
+    g = torch.Generator(device=device).manual_seed(seed)   # indices drawn on the device: no host sync
     fn = TailMLPFunction if net == "tail" else DfaoitMLPFunction
     if net == "tail":
         flat0 = scenes.mlp_flat(init if init is not None else initial_weights(seed))
@@ -252,15 +252,20 @@ def train(x, y, steps=3000, batch=65536, lr=3e-3, seed=0, init=None, log=print, 
     m = torch.zeros_like(master)
     v = torch.zeros_like(master)
     N = x.shape[0]
+    xb = torch.empty((batch,) + tuple(x.shape[1:]), dtype=x.dtype, device=device)
+    yb = torch.empty((batch,) + tuple(y.shape[1:]), dtype=y.dtype, device=device)
+    wb = torch.empty((batch, 1), dtype=w.dtype, device=device) if w is not None else None
     history = []
     t0 = time.time()
     for step in range(1, steps + 1):
-        idx = torch.randint(0, N, (batch,), generator=g).to(device)
-        xb = x[idx].reshape(-1)
-        yb = y[idx].reshape(-1)
+        idx = torch.randint(0, N, (batch,), generator=g, device=device)
+        sn.gather_rows(x, idx, xb)          # the library's row gather (one launch per array)
+        sn.gather_rows(y, idx, yb)
+        if w is not None:
+            sn.gather_rows(w.view(-1, 1), idx, wb)
         p = rounded.clone().requires_grad_(True)
-        f = fn.apply(xb, p)
-        loss = MSEFunction.apply(f, yb, w[idx].contiguous() if w is not None else None)
+        f = fn.apply(xb.reshape(-1), p)
+        loss = MSEFunction.apply(f, yb.reshape(-1), wb.reshape(-1) if w is not None else None)
         loss.backward()
         lr_t = lr * 0.5 * (1.0 + math.cos(math.pi * (step - 1) / steps))
         sn.adam(master, p.grad, m, v, step, lr=lr_t, bf16_rounded=rounded)

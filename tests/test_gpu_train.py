@@ -213,3 +213,32 @@ def test_backward_expired_wait(sn):
     torch.cuda.synchronize()
     assert int(status.item()) == sn.OK
     assert torch.equal(g0, g2)
+
+
+@pytest.mark.parametrize("cols,dtype", [(1, torch.float32), (4, torch.float32), (8, torch.float32),
+                                        (16, torch.float32), (3, torch.int32), (8, torch.bfloat16)])
+def test_gather_rows(sn, cols, dtype):
+    """The minibatch gather against torch indexing: 16-byte chunks where rows
+    allow them, 4-byte words otherwise; repeated indices; an index out of
+    range gives a zero row and STAR_NT_ERR_ARG."""
+    rng = np.random.default_rng(cols)
+    n_src, n = 10007, 4099
+    src = torch.tensor(rng.standard_normal((n_src, cols)), device="cuda").to(dtype).contiguous()
+    if src.numel() * src.element_size() // n_src % 4:
+        pytest.skip("rows must be a multiple of 4 bytes")
+    idx = torch.tensor(rng.integers(0, n_src, n), dtype=torch.int64, device="cuda")
+    dst = torch.empty((n, cols), dtype=dtype, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    sn.gather_rows(src, idx, dst, status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == sn.OK
+    assert torch.equal(dst, src[idx])
+    idx[7] = n_src
+    idx[9] = -1
+    sn.gather_rows(src, idx, dst, status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == sn.ERR_ARG
+    assert (dst[7] == 0).all() and (dst[9] == 0).all()
+    keep = torch.ones(n, dtype=torch.bool, device="cuda")
+    keep[7] = keep[9] = False
+    assert torch.equal(dst[keep], src[idx[keep]])
