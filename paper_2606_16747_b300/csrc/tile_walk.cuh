@@ -41,6 +41,7 @@ struct WalkStage {
   uint32_t id[kWalkChunk];
   float key[kWalkChunk];
   uint8_t list[4][kWalkChunk];  // per-warp lists of staged triangles touching the block
+  uint8_t perm[kWalkChunk];     // perm[r] = slot of the triangle of rank r
 };
 
 // g and r of the three edges at the centre of the tile's pixel (0, 0).
@@ -64,37 +65,39 @@ __device__ __forceinline__ int4 tile_edge_bases(const int4 &p0, const int4 &p1, 
   return make_int4(g[0], g[1], g[2], (int)rem);
 }
 
-// Stages binned entries [base, base + n), n <= kWalkChunk <= blockDim.x,
-// sorted by (depth lower bound, binned position): thread t < n reads entry t's
-// key, ranks it among the round's keys, copies the set-up to its rank with
-// 16-byte asynchronous copies and stores the tile's edge bases beside it.
+// Stages binned entries [base, base + n), n <= kWalkChunk <= blockDim.x:
+// thread t < n copies entry t's set-up to slot t with 16-byte asynchronous
+// copies as soon as its id is known, stores its key and the tile's edge
+// bases beside it, then ranks the key among the round's keys (ties by binned
+// position): perm[r] is the slot of rank r, so the round is walked sorted by
+// (depth lower bound, binned position).
 __device__ __forceinline__ void walk_stage(const BinsView &bv, uint32_t base, int n, WalkStage &st,
                                            int tx0, int ty0) {
   const int t = threadIdx.x;
-  uint32_t id = 0u;
   float kt = 0.0f;
   if (t < n) {
-    id = __ldg(bv.pairs + base + t);
+    const uint32_t id = __ldg(bv.pairs + base + t);
+    const int4 *g = reinterpret_cast<const int4 *>(bv.setups + id);
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(st.tri + t);
+#pragma unroll
+    for (int p = 0; p < 7; ++p)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d + 16u * p), "l"(g + p) : "memory");
     kt = __ldg(&bv.setups[id].zlo);
     st.key[t] = kt;
+    st.id[t] = id;
+    st.te[t] = tile_edge_bases(__ldg(g), __ldg(g + 1), __ldg(g + 2), tx0, ty0);
   }
-  __syncthreads();
+  __syncthreads();  // the keys
   if (t < n) {
     int r = 0;
     for (int j = 0; j < n; ++j) {
       const float kj = st.key[j];
       r += (kj < kt || (kj == kt && j < t)) ? 1 : 0;
     }
-    const uint32_t d = (uint32_t)__cvta_generic_to_shared(st.tri + r);
-    const int4 *g = reinterpret_cast<const int4 *>(bv.setups + id);
-#pragma unroll
-    for (int p = 0; p < 7; ++p)
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d + 16u * p), "l"(g + p) : "memory");
-    st.id[r] = id;
-    st.te[r] = tile_edge_bases(__ldg(g), __ldg(g + 1), __ldg(g + 2), tx0, ty0);
+    st.perm[r] = (uint8_t)t;
   }
   asm volatile("cp.async.wait_all;" ::: "memory");
-  __syncthreads();
+  __syncthreads();  // the permutation and the set-ups
 }
 
 // May the triangle cover a pixel centre of the BW x BH2 block at tile-local
@@ -164,9 +167,10 @@ __device__ __forceinline__ void walk_tile2(const BinsView &bv, int tile, const T
     if (base != beg) __syncthreads();  // the walks of the previous round are over
     walk_stage(bv, base, n, st, tp.tx0, tp.ty0);
     int m = 0;
-    for (int k0 = 0; k0 < n; k0 += 32) {
-      const int k = k0 + lane;
-      const bool hit = k < n && block_maybe32<BW, 2 * BH>(st.tri[k], st.te[k], tp.bx0, tp.by0, bxl, byl);
+    for (int r0 = 0; r0 < n; r0 += 32) {  // in rank order; the lists hold slots
+      const int r = r0 + lane;
+      const int k = r < n ? st.perm[r] : 0;
+      const bool hit = r < n && block_maybe32<BW, 2 * BH>(st.tri[k], st.te[k], tp.bx0, tp.by0, bxl, byl);
       const uint32_t b = __ballot_sync(0xffffffffu, hit);
       if (hit) st.list[warp][m + __popc(b & ((1u << lane) - 1u))] = (uint8_t)k;
       m += __popc(b);
