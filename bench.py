@@ -59,8 +59,8 @@ STAGE_REPS = 20
 # dram__bytes_write.sum); per workload, None where no capture of the current
 # kernel exists.  k_passes2: the persistent passes with pass 3 separate;
 # k_passes_resolve: every pass at full size, with the network and composite.
-PASSES_DRAM_BYTES = {"hd": 16009216, "uhd": 173463808}
-FUSED_DRAM_BYTES = {"hd": 7838208, "uhd": 190099456}
+PASSES_DRAM_BYTES = {"hd": 15214080, "uhd": 172249088}
+FUSED_DRAM_BYTES = {"hd": 7832576, "uhd": 190118912}
 
 
 def stage_rooflines(star, torch, stage_state, stage_mean, hbm_gbs):
