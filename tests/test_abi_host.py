@@ -241,3 +241,29 @@ def test_context_calls_reject_bad_arguments(sn):
     o = sn.FrameOptions()
     L.star_nt_default_frame_options(ctypes.byref(o))
     assert (o.mlp_type, o.merge_scale2, o.merge_scale3, o.fuse_passes) == (sn.BF16, 1.0, 1.0, 1)
+
+
+def test_training_arguments_rejected(sn):
+    """The minibatch gather and the backward pass reject bad arguments on the
+    host (fake device addresses: nothing is dereferenced or launched); an
+    empty gather returns at once."""
+    L = sn.lib()
+    g = L.star_nt_gather_rows
+    assert g(None, 10, 16, 4096, 10, 8192, None, None) == sn.ERR_ARG          # no source
+    assert g(4096, 10, 6, 4096, 10, 8192, None, None) == sn.ERR_ARG           # row not whole words
+    assert g(4098, 10, 16, 4096, 10, 8192, None, None) == sn.ERR_ARG          # source misaligned
+    assert g(4096, 10, 16, 4100, 10, 8192, None, None) == sn.ERR_ARG          # indices misaligned
+    assert g(4096, 0, 16, 4096, 10, 8192, None, None) == sn.ERR_ARG           # empty source
+    assert g(4096, 10, 16, 4096, -1, 8192, None, None) == sn.ERR_ARG          # negative count
+    assert g(4096, 10, 16, 4096, 0, 8192, None, None) == sn.OK                # nothing to do
+    B = 100
+    need = sn.train_ws_bytes(B)
+    assert need > 0
+    w = sn.Mlp(*([4096] * 6))
+    bwd = L.star_nt_mlp_backward
+    assert bwd(None, 4096, 8192, B, 12288, 16384, need, None, None) == sn.ERR_ARG        # no weights
+    assert bwd(ctypes.byref(w), 4096, 8192, B, 12288, 16384, need - 4, None, None) == sn.ERR_ARG  # small ws
+    assert bwd(ctypes.byref(w), 4100, 8192, B, 12288, 16384, need, None, None) == sn.ERR_ARG  # x misaligned
+    assert bwd(ctypes.byref(w), 4096, 8192, B, 12288, 16400, need, None, None) == sn.ERR_ARG  # ws misaligned
+    assert L.star_nt_dfaoit_backward(ctypes.byref(w), 4096, 8192, 0, 12288, 16384, need, None,
+                                     None) == sn.ERR_ARG                                      # empty batch
