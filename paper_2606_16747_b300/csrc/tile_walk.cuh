@@ -37,16 +37,19 @@ constexpr int kWalkChunk = 128;  // triangles staged per round (one per thread)
 // Shared-memory staging area of one tile CTA.
 struct WalkStage {
   TriSetup tri[kWalkChunk];
-  int4 te[kWalkChunk];  // g of edges 0..2 (clamped) and r_0 | r_1 << 8 | r_2 << 16
+  int4 te[kWalkChunk];  // g of edges 0..2 (clamped) and the depth biases u_0 | u_2 << 16 (below)
   uint32_t id[kWalkChunk];
   float key[kWalkChunk];
   uint8_t list[4][kWalkChunk];  // per-warp lists of staged triangles touching the block
   uint8_t perm[kWalkChunk];     // perm[r] = slot of the triangle of rank r
 };
 
-// g and r of the three edges at the centre of the tile's pixel (0, 0).
-__device__ __forceinline__ int4 tile_edge_bases(const int4 &p0, const int4 &p1, const int4 &p2, int tx0,
-                                                int ty0) {
+// g of the three edges at the centre of the tile's pixel (0, 0), and for
+// edges 0 and 2 the term u_e = r_e - (own_e - 1) in [0, 256] that turns
+// 256 (g_e + dx_e y - dy_e x) into the edge function's value without its tie
+// bias (the value the fragment depth takes).
+__device__ __forceinline__ int4 tile_edge_bases(const int4 &p0, const int4 &p1, const int4 &p2, uint32_t own,
+                                                int tx0, int ty0) {
   // the set-up's first 48 bytes: dx[3], dy[3], c[3] (int64, low word first)
   const int dx[3] = {p0.x, p0.y, p0.z}, dy[3] = {p0.w, p1.x, p1.y};
   const long long c[3] = {(long long)(((unsigned long long)(uint32_t)p1.w << 32) | (uint32_t)p1.z),
@@ -54,15 +57,16 @@ __device__ __forceinline__ int4 tile_edge_bases(const int4 &p0, const int4 &p1, 
                           (long long)(((unsigned long long)(uint32_t)p2.w << 32) | (uint32_t)p2.z)};
   const int Px0 = tx0 * kSub + kSub / 2, Py0 = ty0 * kSub + kSub / 2;
   int g[3];
-  uint32_t rem = 0u;
+  uint32_t r[3];
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
     const long long E = (long long)dx[e] * Py0 + c[e] - (long long)dy[e] * Px0;
     const long long q = E >> 8;  // floor(E / 256): arithmetic shift
-    rem |= (uint32_t)(E & 255) << (8 * e);
+    r[e] = (uint32_t)(E & 255);
     g[e] = (int)(q < -(1ll << 30) ? -(1ll << 30) : (q > (1ll << 30) ? (1ll << 30) : q));
   }
-  return make_int4(g[0], g[1], g[2], (int)rem);
+  const uint32_t u0 = r[0] - (own & 1u) + 1u, u2 = r[2] - ((own >> 2) & 1u) + 1u;
+  return make_int4(g[0], g[1], g[2], (int)(u0 | u2 << 16));
 }
 
 // Stages binned entries [base, base + n), n <= kWalkChunk <= blockDim.x:
@@ -85,7 +89,7 @@ __device__ __forceinline__ void walk_stage(const BinsView &bv, uint32_t base, in
     kt = __ldg(&bv.setups[id].zlo);
     st.key[t] = kt;
     st.id[t] = id;
-    st.te[t] = tile_edge_bases(__ldg(g), __ldg(g + 1), __ldg(g + 2), tx0, ty0);
+    st.te[t] = tile_edge_bases(__ldg(g), __ldg(g + 1), __ldg(g + 2), (uint32_t)__ldg(g + 4).z, tx0, ty0);
   }
   __syncthreads();  // the keys
   if (t < n) {
@@ -119,15 +123,17 @@ __device__ __forceinline__ bool block_maybe32(const TriSetup &T, const int4 &te,
 }
 
 // Canonical float32 depth of a covered pixel (the arithmetic of frag_depth)
-// from the pixel's tile-relative values of edges 0 and 2 (ga, gc), or, for a
-// triangle whose area does not fit int32, from the int64 edge functions at
-// the pixel centre (Px, Py).
-__device__ __forceinline__ float frag_depth_tile(const TriSetup &T, int ga, int gc, uint32_t rem, int Px,
+// from the pixel's tile-relative values of edges 0 and 2 (ga, gc) and their
+// depth biases (u = u_0 | u_2 << 16), or, for a triangle whose area does not
+// fit int32, from the int64 edge functions at the pixel centre (Px, Py).
+// 256 g + u, taken modulo 2^32, is the edge function's value without its tie
+// bias: it fits int32 when the area does.
+__device__ __forceinline__ float frag_depth_tile(const TriSetup &T, int ga, int gc, uint32_t u, int Px,
                                                  int Py) {
   float f20, f01;
   if (T.own & kOwnSmall) {
-    const int e01 = (int)(((uint32_t)ga << 8) + (rem & 255u)) - (int)(T.own & 1u) + 1;
-    const int e20 = (int)(((uint32_t)gc << 8) + ((rem >> 16) & 255u)) - (int)((T.own >> 2) & 1u) + 1;
+    const int e01 = (int)(((uint32_t)ga << 8) + (u & 0xFFFFu));
+    const int e20 = (int)(((uint32_t)gc << 8) + (u >> 16));
     f20 = __int2float_rn(e20);
     f01 = __int2float_rn(e01);
   } else {
