@@ -77,6 +77,18 @@ struct PassAcc {
     if (MODE == kFusedDfaoit) cs += spread_rgb(T.c8);
   }
 
+  // A fragment with the tail constants rg, ba, lg (and colour c8) of its
+  // triangle, loaded once by the caller.
+  template <int MODE>
+  __device__ __forceinline__ void accumulate_terms(unsigned long long trg, unsigned long long tba,
+                                                   unsigned long long tlg, uint32_t c8) {
+    ++N;
+    rg += trg;
+    ba += tba;
+    lg += tlg;
+    if (MODE == kFusedDfaoit) cs += spread_rgb(c8);
+  }
+
   // A fragment at depth z offered to the KM nearest, ordered by (depth, id).
   template <int KM>
   __device__ __forceinline__ void insert(float z, int id) {

@@ -202,12 +202,14 @@ __device__ __forceinline__ void walk_tile2(const BinsView &bv, int tile, const T
       const bool c0 = (ga | gb | gc) >= 0, c1 = (ha | hb | hc) >= 0;
       if (!(c0 || c1)) continue;
       const int id = (int)st.id[k];
+      const unsigned long long trg = T.rg, tba = T.ba, tlg = T.lg;
+      const uint32_t tc8 = MODE == 5 ? T.c8 : 0u;  // kFusedDfaoit
       if (c0) {
-        if (TAIL) a0.template accumulate<MODE>(T);
+        if (TAIL) a0.template accumulate_terms<MODE>(trg, tba, tlg, tc8);
         if (!(T.zlo > b0)) a0.template insert<KM>(frag_depth_tile(T, ga, gc, (uint32_t)te.w, Px, Py0), id);
       }
       if (c1) {
-        if (TAIL) a1.template accumulate<MODE>(T);
+        if (TAIL) a1.template accumulate_terms<MODE>(trg, tba, tlg, tc8);
         if (!(T.zlo > b1)) a1.template insert<KM>(frag_depth_tile(T, ha, hc, (uint32_t)te.w, Px, Py1), id);
       }
     }
@@ -219,8 +221,11 @@ __device__ __forceinline__ void walk_tile2(const BinsView &bv, int tile, const T
         const int ga = te.x + dx0 * ly - T.dy[0] * lx;
         const int gb = te.y + dx1 * ly - T.dy[1] * lx;
         const int gc = te.z + dx2 * ly - T.dy[2] * lx;
-        if ((ga | gb | gc) >= 0) a0.template accumulate<MODE>(T);
-        if (((ga + dx0 * BH) | (gb + dx1 * BH) | (gc + dx2 * BH)) >= 0) a1.template accumulate<MODE>(T);
+        const unsigned long long trg = T.rg, tba = T.ba, tlg = T.lg;
+        const uint32_t tc8 = MODE == 5 ? T.c8 : 0u;  // kFusedDfaoit
+        if ((ga | gb | gc) >= 0) a0.template accumulate_terms<MODE>(trg, tba, tlg, tc8);
+        if (((ga + dx0 * BH) | (gb + dx1 * BH) | (gc + dx2 * BH)) >= 0)
+          a1.template accumulate_terms<MODE>(trg, tba, tlg, tc8);
       }
     }
   }
