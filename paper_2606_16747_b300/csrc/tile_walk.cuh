@@ -124,14 +124,16 @@ __device__ __forceinline__ bool block_maybe32(const TriSetup &T, const int4 &te,
 
 // Canonical float32 depth of a covered pixel (the arithmetic of frag_depth)
 // from the pixel's tile-relative values of edges 0 and 2 (ga, gc) and their
-// depth biases (u = u_0 | u_2 << 16), or, for a triangle whose area does not
+// depth terms (u = u_0 | u_2 << 16), or, for a triangle whose area does not
 // fit int32, from the int64 edge functions at the pixel centre (Px, Py).
 // 256 g + u, taken modulo 2^32, is the edge function's value without its tie
-// bias: it fits int32 when the area does.
-__device__ __forceinline__ float frag_depth_tile(const TriSetup &T, int ga, int gc, uint32_t u, int Px,
-                                                 int Py) {
+// bias: it fits int32 when the area does.  The depth plane pl = (z0, dz1,
+// dz2, r) and the ownership bits own are the triangle's, loaded once by the
+// caller for both of its pixels.
+__device__ __forceinline__ float frag_depth_tile(const TriSetup &T, float4 pl, uint32_t own, int ga, int gc,
+                                                 uint32_t u, int Px, int Py) {
   float f20, f01;
-  if (T.own & kOwnSmall) {
+  if (own & kOwnSmall) {
     const int e01 = (int)(((uint32_t)ga << 8) + (u & 0xFFFFu));
     const int e20 = (int)(((uint32_t)gc << 8) + (u >> 16));
     f20 = __int2float_rn(e20);
@@ -139,12 +141,12 @@ __device__ __forceinline__ float frag_depth_tile(const TriSetup &T, int ga, int 
   } else {
     const long long e0b = (long long)T.dx[0] * Py + T.c[0] - (long long)T.dy[0] * Px;
     const long long e2b = (long long)T.dx[2] * Py + T.c[2] - (long long)T.dy[2] * Px;
-    f20 = __ll2float_rn(e2b - (long long)((T.own >> 2) & 1u) + 1);
-    f01 = __ll2float_rn(e0b - (long long)(T.own & 1u) + 1);
+    f20 = __ll2float_rn(e2b - (long long)((own >> 2) & 1u) + 1);
+    f01 = __ll2float_rn(e0b - (long long)(own & 1u) + 1);
   }
-  const float b1 = __fmul_rn(f20, T.r);
-  const float b2 = __fmul_rn(f01, T.r);
-  const float z = __fadd_rn(__fadd_rn(T.z0, __fmul_rn(b1, T.dz1)), __fmul_rn(b2, T.dz2));
+  const float b1 = __fmul_rn(f20, pl.w);
+  const float b2 = __fmul_rn(f01, pl.w);
+  const float z = __fadd_rn(__fadd_rn(pl.x, __fmul_rn(b1, pl.y)), __fmul_rn(b2, pl.z));
   return __fadd_rn(z, 0.0f);
 }
 
@@ -204,13 +206,15 @@ __device__ __forceinline__ void walk_tile2(const BinsView &bv, int tile, const T
       const int id = (int)st.id[k];
       const unsigned long long trg = T.rg, tba = T.ba, tlg = T.lg;
       const uint32_t tc8 = MODE == 5 ? T.c8 : 0u;  // kFusedDfaoit
+      const float4 pl = make_float4(T.z0, T.dz1, T.dz2, T.r);
+      const uint32_t own = T.own;
       if (c0) {
         if (TAIL) a0.template accumulate_terms<MODE>(trg, tba, tlg, tc8);
-        if (!(T.zlo > b0)) a0.template insert<KM>(frag_depth_tile(T, ga, gc, (uint32_t)te.w, Px, Py0), id);
+        if (!(T.zlo > b0)) a0.template insert<KM>(frag_depth_tile(T, pl, own, ga, gc, (uint32_t)te.w, Px, Py0), id);
       }
       if (c1) {
         if (TAIL) a1.template accumulate_terms<MODE>(trg, tba, tlg, tc8);
-        if (!(T.zlo > b1)) a1.template insert<KM>(frag_depth_tile(T, ha, hc, (uint32_t)te.w, Px, Py1), id);
+        if (!(T.zlo > b1)) a1.template insert<KM>(frag_depth_tile(T, pl, own, ha, hc, (uint32_t)te.w, Px, Py1), id);
       }
     }
     if (TAIL) {
