@@ -59,8 +59,8 @@ STAGE_REPS = 20
 # dram__bytes_write.sum); per workload, None where no capture of the current
 # kernel exists.  k_passes2: the persistent passes with pass 3 separate;
 # k_passes_resolve: every pass at full size, with the network and composite.
-PASSES_DRAM_BYTES = {"hd": 15214080, "uhd": 172249088}
-FUSED_DRAM_BYTES = {"hd": 7832576, "uhd": 190118912}
+PASSES_DRAM_BYTES = {"hd": 14934272, "uhd": 172245504}
+FUSED_DRAM_BYTES = {"hd": 8356864, "uhd": 191712000}
 
 
 def stage_rooflines(star, torch, stage_state, stage_mean, hbm_gbs):
