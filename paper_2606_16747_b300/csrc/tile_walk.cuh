@@ -151,10 +151,12 @@ __device__ __forceinline__ float frag_depth_tile(const TriSetup &T, float4 pl, u
 }
 
 // The traversal of one tile for both pixels of every thread.  Acc is the
-// per-pixel state (PassAcc): accumulate<MODE>(T) adds a fragment to the tail
-// sums (MODE >= kTail), insert<KM>(z, id) offers it to the k nearest, z1 and z2
-// are the nearest depths so far.  Called by all 128 threads, after a CTA
-// barrier that follows every earlier use of st.
+// per-pixel state (PassAcc): accumulate_terms<MODE>(rg, ba, lg, c8) adds a
+// fragment with its triangle's tail constants to the tail sums (MODE >=
+// kTail), insert<KM>(z, id) offers it to the k nearest, z1 and z2 are the
+// nearest depths so far.  A walked triangle's tail constants, depth plane and
+// ownership bits are read from the staging area once for both pixels.  Called
+// by all 128 threads, after a CTA barrier that follows every earlier use of st.
 template <int MODE, int BW, class Acc>
 __device__ __forceinline__ void walk_tile2(const BinsView &bv, int tile, const TilePixel &tp, WalkStage &st,
                                            bool in0, bool in1, Acc &a0, Acc &a1) {
